@@ -1,0 +1,267 @@
+/*
+ * splat.h -- C ABI of the GB300 (sm_103a) differentiable tile-based RGB-D
+ * Gaussian rasterizer: the data-parallel hot path of MAC-Ego3D
+ * (arXiv 2412.09723).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Memory:   the caller owns all memory.  Every array pointer is a DEVICE
+ *           pointer (cudaMalloc / torch CUDA tensor, float32 or int32,
+ *           C-contiguous) unless the comment says "host".  Structs describing
+ *           arrays are passed by host pointer.  The library never allocates;
+ *           calls that need scratch space take a workspace pointer whose size
+ *           the matching *_workspace_size() query returns (256-byte aligned).
+ * Streams:  every call is asynchronous and ordered on `stream` (NULL = the
+ *           legacy default stream).  No call synchronises with the host, so
+ *           every call can be captured into a CUDA graph.  Counts that depend
+ *           on the data (duplicates K, association pairs M) are written to
+ *           device int64 slots; reading them is an explicit caller action.
+ * Errors:   each call returns SPLAT_OK or an error code for argument errors
+ *           (SPLAT_EINVAL) and launch errors (SPLAT_ECUDA); the text of the
+ *           last error on the calling thread is splat_last_error().  Errors
+ *           only the device can detect (a capacity overflow) are written to
+ *           the caller's device `status` word (int32, 0 = ok) and must be
+ *           checked after synchronising.  Entry points never write outside the
+ *           buffers their sizes describe, even on overflow.
+ * Geometry: world-to-camera pose `w2c` is a device float[16], row-major 4x4
+ *           [R t; 0 1]; camera space is x right, y down, z forward.  Pixel
+ *           (x, y) has its centre at (x + 0.5, y + 0.5).  Tiles are 16x16
+ *           pixels, tile id = ty * ceil(W/16) + tx.
+ *
+ * Paper anchors: map representation and the rendering equation, Sec. 3.3;
+ * depth rendering for the geometric loss, Sec. 3.5 (Optimization, Eq. optim);
+ * map optimisation by differentiable rendering, Sec. 3.4 step 4; inter-agent
+ * association and alignment, Sec. 3.5 steps 2-3; batched differentiable
+ * rendering across agents, Sec. 3.6.  The paper fixes no rasterizer constant;
+ * this library uses: alpha = min(0.99, opacity * exp(power)), skip alpha <
+ * 1/255, stop before a Gaussian that would take transmittance below 1e-4,
+ * +0.3 px^2 low-pass on the 2D covariance, EWA Jacobian with x/z, y/z clamped
+ * to 1.3 tan(fov/2), near plane z_near (culls z <= z_near), radius
+ * ceil(3 sqrt(lambda_max)).
+ */
+#ifndef SPLAT_H
+#define SPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *splat_stream_t;
+
+enum {
+  SPLAT_OK = 0,
+  SPLAT_EINVAL = 1,    /* null pointer, bad size or misaligned buffer */
+  SPLAT_ECAPACITY = 2, /* (device status) an output buffer was too small */
+  SPLAT_ECUDA = 3,     /* a kernel launch or CUDA runtime call failed */
+  SPLAT_ETIMEOUT = 4   /* (device status) a bounded wait gave up */
+};
+
+/* Pinhole camera.  tan(fov_x / 2) = width / (2 fx). */
+typedef struct {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float z_near;
+} splat_camera;
+
+/* Gaussian map, structure of arrays (Sec. 3.3: mean x, covariance from
+ * scale s and rotation, opacity lambda, colour c).  quat is (w, x, y, z) and
+ * need not be normalised; scale = exp(log_scale); opacity =
+ * sigmoid(opacity_logit).  quat must be 16-byte aligned. */
+typedef struct {
+  const float *mean;          /* [n,3] world */
+  const float *log_scale;     /* [n,3] */
+  const float *quat;          /* [n,4] */
+  const float *opacity_logit; /* [n]   */
+  const float *rgb;           /* [n,3] */
+  int64_t n;
+} splat_gaussians;
+
+/* Gradients with the same shapes as splat_gaussians (accumulated, +=). */
+typedef struct {
+  float *mean, *log_scale, *quat, *opacity_logit, *rgb;
+} splat_gaussians_grad;
+
+/* Per-Gaussian projection (all rows of a culled Gaussian are zero).
+ * xyzo and conic and rect must be 16-byte aligned. */
+typedef struct {
+  float *xyzo;            /* [n,4] u, v (pixels), depth z, opacity        */
+  float *conic;           /* [n,4] inverse 2D covariance a, b, c, and the
+                             smallest exponent at which this Gaussian's
+                             alpha can still reach 1/255 (minus a margin)  */
+  int32_t *radius;        /* [n] ceil(3 sqrt(lambda_max)); 0 = culled      */
+  int32_t *rect;          /* [n,4] tile xmin, ymin, xmax, ymax (half open) */
+  int32_t *tiles_touched; /* [n] (xmax - xmin) * (ymax - ymin)             */
+} splat_projected;
+
+/* Per-pixel render outputs, row-major [H,W] (rgb [H,W,3]). */
+typedef struct {
+  float *rgb;
+  float *depth;      /* sum z_i alpha_i T_i (not normalised)            */
+  float *sil;        /* sum alpha_i T_i                                 */
+  float *t_final;    /* transmittance after the last contributor         */
+  int32_t *n_contrib;/* position in the tile list of the last
+                        contributor, plus one (0 = none)                */
+  int32_t *max_id;   /* Gaussian with the largest alpha_i T_i; -1 = none;
+                        ties keep the front-most                         */
+} splat_image;
+
+/* Version of this ABI (incremented on any incompatible change). */
+int32_t splat_abi_version(void);
+
+/* Text of the last error returned on the calling thread ("" if none). */
+const char *splat_last_error(void);
+
+/*
+ * splat_project -- per-Gaussian activation and EWA projection (Sec. 3.3, the
+ * f_i^proj of the rendering equation; frustum part of the candidate
+ * selection of Sec. 3.4 step 1).
+ *   s = exp(log_scale), R = R(q/|q|) (identity if |q| = 0),
+ *   Sigma = R diag(s^2) R^T, opacity = sigmoid(logit), p = W x + t;
+ *   culled if p_z <= z_near;  Sigma2 = J W Sigma W^T J^T + 0.3 I;
+ *   culled if det(Sigma2) <= 0; conic = Sigma2^-1; (u, v) = (fx p_x/p_z + cx,
+ *   fy p_y/p_z + cy); radius r = ceil(3 sqrt(lambda_max(Sigma2)));
+ *   rect = [floor((u-r)/16), floor((u+r)/16)+1) x (same in v), clamped to
+ *   the tile grid; culled if the rect is empty.
+ * g: device arrays; cam: host; w2c: device float[16]; out: device arrays of
+ * g->n rows.  Errors: SPLAT_EINVAL (null or misaligned pointer, n < 0,
+ * non-positive image size), SPLAT_ECUDA.
+ */
+int splat_project(const splat_gaussians *g, const splat_camera *cam, const float *w2c,
+                  const splat_projected *out, splat_stream_t stream);
+
+/*
+ * splat_bin_sort -- duplicate every visible Gaussian into each tile of its
+ * rect and sort the (tile, depth) keys (the tile binning and front-to-back
+ * order the rendering equation of Sec. 3.3 composites in).
+ * Result: for every tile t, vals[ranges[2t] .. ranges[2t+1]) are the ids of
+ * the Gaussians whose rect holds t, in ascending (depth, id) order; tiles
+ * follow each other in tile-id order; an empty tile has range (0, 0).
+ * keys (optional, may be NULL) receives (uint64)tile << 32 | bits(depth).
+ *   proj:     output of splat_project for n Gaussians (device)
+ *   cam:      host; only width/height are used
+ *   keys:     device uint64[capacity] or NULL
+ *   vals:     device uint32[capacity]
+ *   capacity: number of slots in keys/vals (< 2^31)
+ *   k_dev:    device int64[1]: receives K, the number of duplicates
+ *   ranges:   device uint32[2 * n_tiles]
+ *   status:   device int32[1]: set to SPLAT_ECAPACITY when K > capacity (the
+ *             sorted lists are then incomplete; resize and call again);
+ *             never cleared by the library
+ *   ws:       device workspace of splat_bin_sort_workspace_size() bytes
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+size_t splat_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t n_tiles);
+int splat_bin_sort(const splat_projected *proj, int64_t n, const splat_camera *cam,
+                   uint64_t *keys, uint32_t *vals, int64_t capacity, int64_t *k_dev,
+                   uint32_t *ranges, int32_t *status, void *ws, size_t ws_bytes,
+                   splat_stream_t stream);
+
+/*
+ * splat_render_fwd -- per-pixel front-to-back alpha compositing of colour,
+ * depth and silhouette over the pixel's tile list (rendering equation of
+ * Sec. 3.3; rendered depth of Sec. 3.5), recording the final transmittance
+ * and the maximum-weight Gaussian used for association (Sec. 3.5 step 2).
+ *   C = sum c_i w_i + T_final bg, D = sum z_i w_i, S = sum w_i,
+ *   w_i = alpha_i T_i, T_{i+1} = T_i (1 - alpha_i).
+ *   proj/vals/ranges: outputs of splat_project and splat_bin_sort;
+ *   rgb: device [n,3] Gaussian colours; bg: HOST float[3] background;
+ *   out: device image arrays of cam->height x cam->width pixels.
+ * Deterministic (no atomics).  Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_render_fwd(const splat_projected *proj, const float *rgb, int64_t n,
+                     const uint32_t *vals, const uint32_t *ranges, const splat_camera *cam,
+                     const float *bg, const splat_image *out, splat_stream_t stream);
+
+/*
+ * splat_render_bwd -- adjoint of splat_project + splat_render_fwd for
+ * per-pixel upstream gradients (map optimisation by differentiable rendering,
+ * Sec. 3.4 step 4; gradients through renders for alignment and joint
+ * optimisation, Sec. 3.5 steps 3-4).
+ *   d_rgb [H,W,3], d_depth [H,W], d_sil [H,W] (d_depth, d_sil may be NULL).
+ *   fwd: the image of the forward call (t_final, n_contrib are read).
+ *   out: Gaussian-parameter gradients, ACCUMULATED (+=); the caller zeroes.
+ *   d_pose: device float[6] or NULL, ACCUMULATED: gradient w.r.t. (rho, phi)
+ *     of the left perturbation w2c <- exp(delta^) w2c.
+ *   d2d: device float[n,10] or NULL: receives the screen-space gradients
+ *     (du, dv, d conic a, b, c, d opacity, d rgb[3], d depth) (overwritten).
+ *   ws: workspace of splat_render_bwd_workspace_size(n) bytes (used for the
+ *     screen-space gradients when d2d is NULL).
+ * Atomics make the summation order, and so the last bits, vary between runs.
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+size_t splat_render_bwd_workspace_size(int64_t n);
+int splat_render_bwd(const splat_gaussians *g, const splat_projected *proj,
+                     const splat_camera *cam, const float *w2c, const uint32_t *vals,
+                     const uint32_t *ranges, const splat_image *fwd, const float *bg,
+                     const float *d_rgb, const float *d_depth, const float *d_sil,
+                     const splat_gaussians_grad *out, float *d_pose, float *d2d, void *ws,
+                     size_t ws_bytes, splat_stream_t stream);
+
+/*
+ * splat_loss_l1 -- the L1 colour and depth terms of Eq. (optim) (Sec. 3.5):
+ *   L = w_rgb mean|C - C*| + w_depth mean|D - D*|, sign(0) = 0.
+ * Writes dL/dC [npix,3] and dL/dD [npix] (overwritten) and ADDS L to
+ * loss[0] (device float).  Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_loss_l1(const float *rgb, const float *depth, const float *target_rgb,
+                  const float *target_depth, int64_t npix, float w_rgb, float w_depth,
+                  float *d_rgb, float *d_depth, float *loss, splat_stream_t stream);
+
+/*
+ * splat_adam -- one bias-corrected Adam step on n resident float32
+ * parameters (map optimisation, Sec. 3.4 step 4, following SplaTAM):
+ *   m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ *   p -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
+ * Errors: SPLAT_EINVAL (step < 1), SPLAT_ECUDA.
+ */
+int splat_adam(float *param, const float *grad, float *m, float *v, int64_t n, int32_t step,
+               float lr, float beta1, float beta2, float eps, splat_stream_t stream);
+
+/*
+ * splat_pose_step -- Adam on the 6-vector pose gradient followed by the
+ * retraction w2c <- exp(delta^) w2c (render-driven tracking / alignment).
+ *   w2c: device float[16] updated in place; d_pose: device float[6];
+ *   m, v: device float[6] moments; lr_t, lr_r: step sizes for rho and phi.
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_pose_step(float *w2c, const float *d_pose, float *m, float *v, int32_t step,
+                    float lr_t, float lr_r, float beta1, float beta2, float eps,
+                    splat_stream_t stream);
+
+/*
+ * splat_assoc -- render-based Gaussian association between two maps
+ * (Sec. 3.5 step 2): at every pixel where both renders have a maximum-weight
+ * Gaussian (id >= 0) and both final transmittances are <= t_max, the pair
+ * (id_a, id_b) is formed; the result is the set of distinct pairs in
+ * ascending (id_a, id_b) order with the number of pixels of each.
+ *   id_a, t_a, id_b, t_b: device [npix]; n_a, n_b: number of Gaussians of
+ *   each map (ids must be < n_a, n_b);
+ *   pairs: device int32[capacity,2]; counts: device int32[capacity];
+ *   m_dev: device int64[1] receives M; status: device int32[1], set to
+ *   SPLAT_ECAPACITY when M > capacity (the first `capacity` pairs are kept).
+ *   ws: workspace of splat_assoc_workspace_size(npix) bytes.
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+size_t splat_assoc_workspace_size(int64_t npix);
+int splat_assoc(const int32_t *id_a, const float *t_a, const int32_t *id_b, const float *t_b,
+                int64_t npix, int64_t n_a, int64_t n_b, float t_max, int32_t *pairs,
+                int32_t *counts, int64_t capacity, int64_t *m_dev, int32_t *status, void *ws,
+                size_t ws_bytes, splat_stream_t stream);
+
+/*
+ * splat_exp_f32 -- the exponential every kernel above uses, over n device
+ * floats (exposed so that its agreement with the CPU oracle and its error
+ * against the true exp can be tested).  Cody & Waite range reduction with a
+ * two-part ln 2, degree-7 Taylor polynomial, scaling by 2^k; x > 88 -> inf,
+ * x < -87 -> 0.  Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_exp_f32(const float *x, float *y, int64_t n, splat_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPLAT_H */

@@ -1,0 +1,210 @@
+"""Thin Python binding of libsplat_gb300.so (include/splat.h).
+
+Argument marshalling only: every function here passes torch CUDA tensors'
+device pointers and sizes to the C ABI entry point of the same name and
+raises on a non-zero return code.  There is no CPU path: without a CUDA
+device or without the compiled library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+_c_i32, _c_i64, _c_f, _c_p, _c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
+
+SPLAT_OK, SPLAT_EINVAL, SPLAT_ECAPACITY, SPLAT_ECUDA, SPLAT_ETIMEOUT = 0, 1, 2, 3, 4
+
+
+class SplatError(RuntimeError):
+    def __init__(self, name, code, msg):
+        super().__init__(f"{name} failed with code {code}: {msg}")
+        self.code = code
+
+
+class CCamera(ctypes.Structure):
+    _fields_ = [("width", _c_i32), ("height", _c_i32), ("fx", _c_f), ("fy", _c_f), ("cx", _c_f), ("cy", _c_f),
+                ("z_near", _c_f)]
+
+
+class CGaussians(ctypes.Structure):
+    _fields_ = [("mean", _c_p), ("log_scale", _c_p), ("quat", _c_p), ("opacity_logit", _c_p), ("rgb", _c_p),
+                ("n", _c_i64)]
+
+
+class CGaussiansGrad(ctypes.Structure):
+    _fields_ = [("mean", _c_p), ("log_scale", _c_p), ("quat", _c_p), ("opacity_logit", _c_p), ("rgb", _c_p)]
+
+
+class CProjected(ctypes.Structure):
+    _fields_ = [("xyzo", _c_p), ("conic", _c_p), ("radius", _c_p), ("rect", _c_p), ("tiles_touched", _c_p)]
+
+
+class CImage(ctypes.Structure):
+    _fields_ = [("rgb", _c_p), ("depth", _c_p), ("sil", _c_p), ("t_final", _c_p), ("n_contrib", _c_p),
+                ("max_id", _c_p)]
+
+
+_SIGS = {
+    "splat_abi_version": ([], _c_i32),
+    "splat_last_error": ([], ctypes.c_char_p),
+    "splat_project": ([_c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_bin_sort_workspace_size": ([_c_i64, _c_i64, _c_i32], _c_sz),
+    "splat_bin_sort": ([_c_p, _c_i64, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
+    "splat_render_fwd": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_render_bwd_workspace_size": ([_c_i64], _c_sz),
+    "splat_render_bwd": ([_c_p] * 15 + [_c_sz, _c_p], ctypes.c_int),
+    "splat_loss_l1": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_f, _c_f, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_adam": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_i32, _c_f, _c_f, _c_f, _c_f, _c_p], ctypes.c_int),
+    "splat_pose_step": ([_c_p, _c_p, _c_p, _c_p, _c_i32, _c_f, _c_f, _c_f, _c_f, _c_f, _c_p], ctypes.c_int),
+    "splat_assoc_workspace_size": ([_c_i64], _c_sz),
+    "splat_assoc": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_i64, _c_i64, _c_f, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p,
+                     _c_sz, _c_p], ctypes.c_int),
+    "splat_exp_f32": ([_c_p, _c_p, _c_i64, _c_p], ctypes.c_int),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(require_cuda: bool = True):
+    """Load (building first if stale) the CUDA library.  Raises when no CUDA
+    device is present and `require_cuda` is set."""
+    global _lib
+    if require_cuda and not torch.cuda.is_available():
+        raise RuntimeError("libsplat_gb300 needs a CUDA device (GB300, sm_103a); there is no CPU fallback")
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _p(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("splat: expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("splat: expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(name, rc):
+    if rc != SPLAT_OK:
+        msg = load().splat_last_error().decode()
+        raise SplatError(name, rc, msg)
+
+
+def camera_struct(cam) -> CCamera:
+    return CCamera(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, cam.z_near)
+
+
+def gaussians_struct(mean, log_scale, quat, opacity_logit, rgb) -> CGaussians:
+    return CGaussians(_p(mean), _p(log_scale), _p(quat), _p(opacity_logit), _p(rgb), mean.shape[0])
+
+
+def projected_struct(proj) -> CProjected:
+    return CProjected(_p(proj["xyzo"]), _p(proj["conic"]), _p(proj["radius"]), _p(proj["rect"]),
+                      _p(proj["tiles_touched"]))
+
+
+def image_struct(img) -> CImage:
+    return CImage(_p(img["rgb"]), _p(img["depth"]), _p(img["sil"]), _p(img["t_final"]), _p(img["n_contrib"]),
+                  _p(img["max_id"]))
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def splat_abi_version() -> int:
+    return int(load().splat_abi_version())
+
+
+def splat_project(gaussians: CGaussians, cam: CCamera, w2c, proj: CProjected, stream=None):
+    _check("splat_project", load().splat_project(ctypes.byref(gaussians), ctypes.byref(cam), _p(w2c),
+                                                 ctypes.byref(proj), _stream(stream)))
+
+
+def splat_bin_sort_workspace_size(n, capacity, n_tiles) -> int:
+    return int(load().splat_bin_sort_workspace_size(n, capacity, n_tiles))
+
+
+def splat_bin_sort(proj: CProjected, n, cam: CCamera, keys, vals, capacity, k_dev, ranges, status, ws, stream=None):
+    _check("splat_bin_sort", load().splat_bin_sort(
+        ctypes.byref(proj), n, ctypes.byref(cam), _p(keys), _p(vals), capacity, _p(k_dev), _p(ranges), _p(status),
+        _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def splat_render_fwd(proj: CProjected, rgb, n, vals, ranges, cam: CCamera, bg, image: CImage, stream=None):
+    bgc = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    _check("splat_render_fwd", load().splat_render_fwd(
+        ctypes.byref(proj), _p(rgb), n, _p(vals), _p(ranges), ctypes.byref(cam), bgc, ctypes.byref(image),
+        _stream(stream)))
+
+
+def splat_render_bwd_workspace_size(n) -> int:
+    return int(load().splat_render_bwd_workspace_size(n))
+
+
+def splat_render_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, vals, ranges, image: CImage, bg,
+                     d_rgb, d_depth, d_sil, grads: CGaussiansGrad, d_pose, d2d, ws, stream=None):
+    bgc = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    wsb = 0 if ws is None else ws.numel() * ws.element_size()
+    _check("splat_render_bwd", load().splat_render_bwd(
+        ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(vals), _p(ranges),
+        ctypes.byref(image), bgc, _p(d_rgb), _p(d_depth), _p(d_sil), ctypes.byref(grads), _p(d_pose), _p(d2d),
+        _p(ws), wsb, _stream(stream)))
+
+
+def splat_loss_l1(rgb, depth, target_rgb, target_depth, w_rgb, w_depth, d_rgb, d_depth, loss, stream=None):
+    _check("splat_loss_l1", load().splat_loss_l1(
+        _p(rgb), _p(depth), _p(target_rgb), _p(target_depth), depth.numel(), w_rgb, w_depth, _p(d_rgb), _p(d_depth),
+        _p(loss), _stream(stream)))
+
+
+def splat_adam(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    _check("splat_adam", load().splat_adam(_p(param), _p(grad), _p(m), _p(v), param.numel(), step, lr, beta1, beta2,
+                                           eps, _stream(stream)))
+
+
+def splat_pose_step(w2c, d_pose, m, v, step, lr_t, lr_r, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    _check("splat_pose_step", load().splat_pose_step(_p(w2c), _p(d_pose), _p(m), _p(v), step, lr_t, lr_r, beta1,
+                                                     beta2, eps, _stream(stream)))
+
+
+def splat_assoc_workspace_size(npix) -> int:
+    return int(load().splat_assoc_workspace_size(npix))
+
+
+def splat_assoc(id_a, t_a, id_b, t_b, n_a, n_b, t_max, pairs, counts, capacity, m_dev, status, ws, stream=None):
+    _check("splat_assoc", load().splat_assoc(
+        _p(id_a), _p(t_a), _p(id_b), _p(t_b), id_a.numel(), n_a, n_b, t_max, _p(pairs), _p(counts), capacity,
+        _p(m_dev), _p(status), _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def splat_exp_f32(x, y, stream=None):
+    _check("splat_exp_f32", load().splat_exp_f32(_p(x), _p(y), x.numel(), _stream(stream)))

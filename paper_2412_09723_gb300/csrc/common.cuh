@@ -1,0 +1,96 @@
+// common.cuh -- definitions shared by the kernels of the splat library.
+//
+// Build note: every translation unit is compiled with --fmad=false, so that a
+// product followed by a sum is never fused behind the source's back.  Fused
+// multiply-adds appear only where they are written (__fmaf_rn), at the places
+// the operation-order specification names; this is what makes the tile rects,
+// the sort keys, the alpha decisions and the maximum-weight ids reproducible
+// bit for bit on any IEEE-754 implementation that follows the same order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/splat.h"
+
+namespace splat {
+
+constexpr int kTile = 16;
+constexpr int kTilePixels = kTile * kTile;
+
+// Rasterizer constants (the paper fixes none; 3DGS-style readings).
+constexpr float kAlphaCap = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTStop = 1e-4f;
+constexpr float kLowPass = 0.3f;
+constexpr float kClip = 1.3f;
+// Margin (in exponent units) below which the alpha floor is certainly missed;
+// covers the error of logf and of the exponential (both far below 1e-5).
+constexpr float kPowerCutMargin = 1e-3f;
+
+// ----------------------------------------------------------------------------
+// Exponential: Cody & Waite range reduction x = k ln2 + r (ln2 split in a
+// 15-significant-bit head and a tail), exp(r) by the degree-7 Taylor
+// polynomial in Horner form with fused multiply-adds, 2^k from exponent bits.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ float exp_core(float x) {  // x in [-87, 88]
+  const float k = rintf(__fmul_rn(x, 1.44269502f));
+  float r = __fmaf_rn(-k, 0.693145751953125f, x);
+  r = __fmaf_rn(-k, 1.42860677e-06f, r);
+  float p = 1.98412701e-04f;
+  p = __fmaf_rn(p, r, 1.38888892e-03f);
+  p = __fmaf_rn(p, r, 8.33333377e-03f);
+  p = __fmaf_rn(p, r, 4.16666679e-02f);
+  p = __fmaf_rn(p, r, 1.66666672e-01f);
+  p = __fmaf_rn(p, r, 0.5f);
+  p = __fmaf_rn(p, r, 1.0f);
+  p = __fmaf_rn(p, r, 1.0f);
+  const int ki = __float2int_rz(k);
+  return __fmul_rn(p, __int_as_float((ki + 127) << 23));
+}
+
+__device__ __forceinline__ float exp_full(float x) {
+  if (x != x) return x;
+  if (x > 88.0f) return __int_as_float(0x7f800000);
+  if (x < -87.0f) return 0.0f;
+  return exp_core(x);
+}
+
+// Status word helpers (sticky: only ever raised).
+__device__ __forceinline__ void raise_status(int32_t* status, int32_t code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ----------------------------------------------------------------------------
+// Host-side error plumbing.
+// ----------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+int fail(int code, const char* fmt, ...);
+int check_launch(const char* what);
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ----------------------------------------------------------------------------
+// Device-wide primitives (binsort.cu).
+// ----------------------------------------------------------------------------
+// Exclusive prefix sum of n uint32 (n_dev, when not null, overrides n with a
+// device-resident count <= n).  Scratch: scan_workspace_size(n) bytes.
+size_t scan_workspace_size(int64_t n);
+int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* ws, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs on bits [begin_bit, end_bit).
+// Keys are uint32 or uint64, values uint32 (or absent: vals == nullptr).
+// `count_dev` (optional) holds the number of valid items (<= capacity) on the
+// device.  The result ends in (keys0, vals0) when the number of passes is even,
+// else in (keys1, vals1); radix_sort returns 0 or 1 accordingly.
+size_t radix_workspace_size(int64_t capacity);
+template <typename Key>
+int radix_sort(Key* keys0, uint32_t* vals0, Key* keys1, uint32_t* vals1, int64_t capacity,
+               const int64_t* count_dev, int begin_bit, int end_bit, void* ws, cudaStream_t s,
+               int* result_buffer);
+int radix_passes(int begin_bit, int end_bit);
+
+}  // namespace splat

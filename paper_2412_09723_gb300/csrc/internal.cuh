@@ -1,0 +1,54 @@
+// internal.cuh -- kernel-side views of the ABI structs and launcher
+// declarations shared between the translation units of the library.
+#pragma once
+
+#include "common.cuh"
+
+namespace splat {
+
+struct CamK {
+  int width, height, tiles_x, tiles_y;
+  float fx, fy, cx, cy, znear;
+};
+
+struct GaussiansK {
+  const float* mean;
+  const float* log_scale;
+  const float* quat;
+  const float* opacity_logit;
+  const float* rgb;
+  int64_t n;
+};
+
+struct ProjectedK {
+  float* xyzo;
+  float* conic;
+  int32_t* radius;
+  int32_t* rect;
+  int32_t* tiles_touched;
+};
+
+struct GradK {
+  float* mean;
+  float* log_scale;
+  float* quat;
+  float* opacity_logit;
+  float* rgb;
+};
+
+inline CamK make_camk(const splat_camera& c) {
+  CamK k;
+  k.width = c.width;
+  k.height = c.height;
+  k.tiles_x = (c.width + kTile - 1) / kTile;
+  k.tiles_y = (c.height + kTile - 1) / kTile;
+  k.fx = c.fx; k.fy = c.fy; k.cx = c.cx; k.cy = c.cy; k.znear = c.z_near;
+  return k;
+}
+
+int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, const ProjectedK& out,
+                       cudaStream_t s);
+int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
+                       const float* d2d, const GradK& out, float* d_pose, cudaStream_t s);
+
+}  // namespace splat

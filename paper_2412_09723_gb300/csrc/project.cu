@@ -1,0 +1,324 @@
+// project.cu -- per-Gaussian activation + EWA projection (forward) and its
+// adjoint, including the SE(3) pose gradient.
+//
+// Forward (Sec. 3.3: the projection f_i^proj of each Gaussian onto the image
+// plane; the frustum cull of the candidate selection of Sec. 3.4 step 1):
+// one thread per Gaussian, 56 B read, 56 B written.  Every operation follows
+// the written operation order (plain IEEE mul/add/div/sqrt, no contraction),
+// so that the rect, the depth key and the alpha inputs agree bit for bit with
+// any implementation of the same order.
+//
+// Adjoint (map optimisation by differentiable rendering, Sec. 3.4 step 4;
+// pose gradients for render-driven tracking and the relative transform of
+// Sec. 3.5 step 3): one thread per Gaussian chains the screen-space gradients
+// (du, dv, d conic, d opacity, d depth) back to mean, log-scale, quaternion and
+// opacity logit, and the pose 6-vector is reduced per block before one atomic
+// per component.
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace splat {
+
+struct ProjMath {
+  float s[3], qn[4], qnorm;
+  float R[9], M[9], Sig[9];
+  float p[3];
+  float J00, J02, J11, J12, tx, ty;
+  bool clamp_x, clamp_y;
+  float Tm[6];
+  float ca, cb, cc, det;
+  float u, v, lam, radius;
+  int rect[4];
+  int tiles;
+  bool visible;
+};
+
+__device__ __forceinline__ void project_math(const float* __restrict__ mean,
+                                             const float* __restrict__ log_scale,
+                                             const float* __restrict__ quat, float logit,
+                                             const float* W, const CamK& cam, ProjMath& m) {
+  m.visible = false;
+  m.tiles = 0;
+  for (int k = 0; k < 3; ++k) m.s[k] = exp_full(log_scale[k]);
+  const float4 q = *reinterpret_cast<const float4*>(quat);
+  const float n2 = ((q.x * q.x + q.y * q.y) + q.z * q.z) + q.w * q.w;
+  if (n2 == 0.0f) {
+    m.qnorm = 0.0f;
+    m.qn[0] = 1.0f; m.qn[1] = 0.0f; m.qn[2] = 0.0f; m.qn[3] = 0.0f;
+  } else {
+    m.qnorm = sqrtf(n2);
+    m.qn[0] = q.x / m.qnorm; m.qn[1] = q.y / m.qnorm;
+    m.qn[2] = q.z / m.qnorm; m.qn[3] = q.w / m.qnorm;
+  }
+  const float r = m.qn[0], a = m.qn[1], b = m.qn[2], c = m.qn[3];
+  m.R[0] = 1.0f - 2.0f * (b * b + c * c);
+  m.R[1] = 2.0f * (a * b - r * c);
+  m.R[2] = 2.0f * (a * c + r * b);
+  m.R[3] = 2.0f * (a * b + r * c);
+  m.R[4] = 1.0f - 2.0f * (a * a + c * c);
+  m.R[5] = 2.0f * (b * c - r * a);
+  m.R[6] = 2.0f * (a * c - r * b);
+  m.R[7] = 2.0f * (b * c + r * a);
+  m.R[8] = 1.0f - 2.0f * (a * a + b * b);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) m.M[3 * i + j] = m.R[3 * i + j] * m.s[j];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      m.Sig[3 * i + j] = (m.M[3 * i] * m.M[3 * j] + m.M[3 * i + 1] * m.M[3 * j + 1]) +
+                         m.M[3 * i + 2] * m.M[3 * j + 2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    m.p[i] = ((W[4 * i] * mean[0] + W[4 * i + 1] * mean[1]) + W[4 * i + 2] * mean[2]) + W[4 * i + 3];
+  const float z = m.p[2];
+  if (!(z > cam.znear)) return;
+  const float lim_x = kClip * ((float)cam.width / (2.0f * cam.fx));
+  const float lim_y = kClip * ((float)cam.height / (2.0f * cam.fy));
+  const float txz = m.p[0] / z;
+  const float tyz = m.p[1] / z;
+  m.clamp_x = !(txz >= -lim_x && txz <= lim_x);
+  m.clamp_y = !(tyz >= -lim_y && tyz <= lim_y);
+  m.tx = fminf(lim_x, fmaxf(-lim_x, txz)) * z;
+  m.ty = fminf(lim_y, fmaxf(-lim_y, tyz)) * z;
+  const float zz = z * z;
+  m.J00 = cam.fx / z;
+  m.J02 = -(cam.fx * m.tx) / zz;
+  m.J11 = cam.fy / z;
+  m.J12 = -(cam.fy * m.ty) / zz;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    m.Tm[j] = m.J00 * W[j] + m.J02 * W[8 + j];
+    m.Tm[3 + j] = m.J11 * W[4 + j] + m.J12 * W[8 + j];
+  }
+  float U[6];
+#pragma unroll
+  for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      U[3 * a2 + j] = (m.Tm[3 * a2] * m.Sig[j] + m.Tm[3 * a2 + 1] * m.Sig[3 + j]) +
+                      m.Tm[3 * a2 + 2] * m.Sig[6 + j];
+  const float s00 = (U[0] * m.Tm[0] + U[1] * m.Tm[1]) + U[2] * m.Tm[2];
+  const float s01 = (U[0] * m.Tm[3] + U[1] * m.Tm[4]) + U[2] * m.Tm[5];
+  const float s11 = (U[3] * m.Tm[3] + U[4] * m.Tm[4]) + U[5] * m.Tm[5];
+  m.ca = s00 + kLowPass;
+  m.cb = s01;
+  m.cc = s11 + kLowPass;
+  m.det = m.ca * m.cc - m.cb * m.cb;
+  if (!(m.det > 0.0f)) return;
+  m.u = cam.fx * txz + cam.cx;
+  m.v = cam.fy * tyz + cam.cy;
+  const float mid = 0.5f * (m.ca + m.cc);
+  const float disc = mid * mid - m.det;
+  const float lmax = mid + sqrtf(fmaxf(disc, 0.0f));
+  const float rr = ceilf(3.0f * sqrtf(lmax));
+  m.radius = rr;
+  const float gx = (float)cam.tiles_x, gy = (float)cam.tiles_y;
+  m.rect[0] = (int)fminf(fmaxf(floorf((m.u - rr) / 16.0f), 0.0f), gx);
+  m.rect[1] = (int)fminf(fmaxf(floorf((m.v - rr) / 16.0f), 0.0f), gy);
+  m.rect[2] = (int)fminf(fmaxf(floorf((m.u + rr) / 16.0f) + 1.0f, 0.0f), gx);
+  m.rect[3] = (int)fminf(fmaxf(floorf((m.v + rr) / 16.0f) + 1.0f, 0.0f), gy);
+  m.tiles = (m.rect[2] - m.rect[0]) * (m.rect[3] - m.rect[1]);
+  if (m.tiles == 0) return;
+  m.lam = 1.0f / (1.0f + exp_full(-logit));
+  m.visible = true;
+}
+
+__global__ void __launch_bounds__(256) project_fwd_kernel(GaussiansK g, CamK cam, const float* __restrict__ w2c,
+                                                          ProjectedK out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n) return;
+  float W[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) W[k] = __ldg(w2c + k);
+  ProjMath m;
+  project_math(g.mean + 3 * i, g.log_scale + 3 * i, g.quat + 4 * i, g.opacity_logit[i], W, cam, m);
+  float4 xyzo = make_float4(0.f, 0.f, 0.f, 0.f), con = make_float4(0.f, 0.f, 0.f, 0.f);
+  int4 rect = make_int4(0, 0, 0, 0);
+  int radius = 0, tiles = 0;
+  if (m.visible) {
+    xyzo = make_float4(m.u, m.v, m.p[2], m.lam);
+    con.x = m.cc / m.det;
+    con.y = -m.cb / m.det;
+    con.z = m.ca / m.det;
+    // smallest exponent at which opacity * exp(power) can still reach 1/255
+    con.w = (logf(kAlphaMin) - logf(m.lam)) - kPowerCutMargin;
+    radius = (int)m.radius;
+    rect = make_int4(m.rect[0], m.rect[1], m.rect[2], m.rect[3]);
+    tiles = m.tiles;
+  }
+  reinterpret_cast<float4*>(out.xyzo)[i] = xyzo;
+  reinterpret_cast<float4*>(out.conic)[i] = con;
+  reinterpret_cast<int4*>(out.rect)[i] = rect;
+  out.radius[i] = radius;
+  out.tiles_touched[i] = tiles;
+}
+
+// ----------------------------------------------------------------------------
+// Adjoint.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) project_bwd_kernel(GaussiansK g, CamK cam, const float* __restrict__ w2c,
+                                                          const float* __restrict__ conic,
+                                                          const float* __restrict__ d2d, GradK out,
+                                                          float* __restrict__ d_pose) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (i < g.n) {
+    float W[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) W[k] = __ldg(w2c + k);
+    ProjMath m;
+    project_math(g.mean + 3 * i, g.log_scale + 3 * i, g.quat + 4 * i, g.opacity_logit[i], W, cam, m);
+    if (m.visible) {
+      const float* d = d2d + 10 * i;
+      const float du = d[0], dv = d[1], dqa = d[2], dqb = d[3], dqc = d[4], dlam = d[5], dz = d[9];
+      out.rgb[3 * i + 0] += d[6];
+      out.rgb[3 * i + 1] += d[7];
+      out.rgb[3 * i + 2] += d[8];
+      out.opacity_logit[i] += dlam * m.lam * (1.0f - m.lam);
+      // conic Q = cov^-1 with cov = [[ca, cb], [cb, cc]]; the off-diagonal conic
+      // entry is one scalar used twice, so the full-matrix gradient of Q is
+      // [[dqa, dqb/2], [dqb/2, dqc]] and d cov = -Q dQ Q.
+      const float4 Q = reinterpret_cast<const float4*>(conic)[i];
+      const float qa = Q.x, qb = Q.y, qc = Q.z;
+      const float h = 0.5f * dqb;
+      const float t00 = qa * dqa + qb * h, t01 = qa * h + qb * dqc;
+      const float t10 = qb * dqa + qc * h, t11 = qb * h + qc * dqc;
+      const float g00 = -(t00 * qa + t01 * qb);
+      const float g01 = -(t00 * qb + t01 * qc);
+      const float g11 = -(t10 * qb + t11 * qc);
+      // cov = Tm Sig Tm^T: dTm = 2 G Tm Sig, dSig = Tm^T G Tm  (G symmetric 2x2)
+      float TS[6];
+#pragma unroll
+      for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          TS[3 * a2 + j] = m.Tm[3 * a2] * m.Sig[j] + m.Tm[3 * a2 + 1] * m.Sig[3 + j] + m.Tm[3 * a2 + 2] * m.Sig[6 + j];
+      float dTm[6];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dTm[j] = 2.0f * (g00 * TS[j] + g01 * TS[3 + j]);
+        dTm[3 + j] = 2.0f * (g01 * TS[j] + g11 * TS[3 + j]);
+      }
+      float dSig[9];
+#pragma unroll
+      for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+        for (int b3 = 0; b3 < 3; ++b3) {
+          const float x0 = m.Tm[a3], x1 = m.Tm[3 + a3];
+          const float y0 = m.Tm[b3], y1 = m.Tm[3 + b3];
+          dSig[3 * a3 + b3] = x0 * (g00 * y0 + g01 * y1) + x1 * (g01 * y0 + g11 * y1);
+        }
+      // Tm rows: (J00 W0 + J02 W2), (J11 W1 + J12 W2)
+      const float dJ00 = dTm[0] * W[0] + dTm[1] * W[1] + dTm[2] * W[2];
+      const float dJ02 = dTm[0] * W[8] + dTm[1] * W[9] + dTm[2] * W[10];
+      const float dJ11 = dTm[3] * W[4] + dTm[4] * W[5] + dTm[5] * W[6];
+      const float dJ12 = dTm[3] * W[8] + dTm[4] * W[9] + dTm[5] * W[10];
+      // gradient of the rotation block through Tm: dW_ij = sum_a J_ai dTm_aj
+      float dWr[9];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dWr[j] = m.J00 * dTm[j];
+        dWr[3 + j] = m.J11 * dTm[3 + j];
+        dWr[6 + j] = m.J02 * dTm[j] + m.J12 * dTm[3 + j];
+      }
+      const float z = m.p[2];
+      const float iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+      float gz = -cam.fx * iz2 * dJ00 - cam.fy * iz2 * dJ11 + 2.0f * cam.fx * m.tx * iz3 * dJ02 +
+                 2.0f * cam.fy * m.ty * iz3 * dJ12;
+      const float gtx = -cam.fx * iz2 * dJ02;
+      const float gty = -cam.fy * iz2 * dJ12;
+      float gp0 = 0.f, gp1 = 0.f;
+      if (m.clamp_x) gz += gtx * (m.tx * iz); else gp0 += gtx;
+      if (m.clamp_y) gz += gty * (m.ty * iz); else gp1 += gty;
+      gp0 += du * cam.fx * iz;
+      gp1 += dv * cam.fy * iz;
+      gz -= (du * cam.fx * m.p[0] + dv * cam.fy * m.p[1]) * iz2;
+      gz += dz;
+      const float gp[3] = {gp0, gp1, gz};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) out.mean[3 * i + j] += W[j] * gp[0] + W[4 + j] * gp[1] + W[8 + j] * gp[2];
+      // Sig = M M^T, M = R diag(s)
+      float dM[9];
+#pragma unroll
+      for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          dM[3 * a3 + j] = 2.0f * (dSig[3 * a3] * m.M[j] + dSig[3 * a3 + 1] * m.M[3 + j] + dSig[3 * a3 + 2] * m.M[6 + j]);
+      float dR[9];
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float gs = dM[j] * m.R[j] + dM[3 + j] * m.R[3 + j] + dM[6 + j] * m.R[6 + j];
+        out.log_scale[3 * i + j] += gs * m.s[j];
+        dR[j] = dM[j] * m.s[j];
+        dR[3 + j] = dM[3 + j] * m.s[j];
+        dR[6 + j] = dM[6 + j] * m.s[j];
+      }
+      if (m.qnorm > 0.0f) {
+        const float r = m.qn[0], a = m.qn[1], b = m.qn[2], c = m.qn[3];
+        float gq[4];
+        gq[0] = 2.0f * (c * (dR[3] - dR[1]) + b * (dR[2] - dR[6]) + a * (dR[7] - dR[5]));
+        gq[1] = 2.0f * (b * (dR[1] + dR[3]) + c * (dR[2] + dR[6]) + r * (dR[7] - dR[5])) - 4.0f * a * (dR[4] + dR[8]);
+        gq[2] = 2.0f * (a * (dR[1] + dR[3]) + r * (dR[2] - dR[6]) + c * (dR[5] + dR[7])) - 4.0f * b * (dR[0] + dR[8]);
+        gq[3] = 2.0f * (r * (dR[3] - dR[1]) + a * (dR[2] + dR[6]) + b * (dR[5] + dR[7])) - 4.0f * c * (dR[0] + dR[4]);
+        const float dot = r * gq[0] + a * gq[1] + b * gq[2] + c * gq[3];
+        const float inv = 1.0f / m.qnorm;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) out.quat[4 * i + k] += (gq[k] - m.qn[k] * dot) * inv;
+      }
+      // pose: rho = dL/dp ; phi = p x dL/dp + vee(dW W^T)
+      float A[9];
+#pragma unroll
+      for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+        for (int b3 = 0; b3 < 3; ++b3)
+          A[3 * a3 + b3] = dWr[3 * a3] * W[4 * b3] + dWr[3 * a3 + 1] * W[4 * b3 + 1] + dWr[3 * a3 + 2] * W[4 * b3 + 2];
+      pose[0] = gp[0];
+      pose[1] = gp[1];
+      pose[2] = gp[2];
+      pose[3] = m.p[1] * gp[2] - m.p[2] * gp[1] + (A[7] - A[5]);
+      pose[4] = m.p[2] * gp[0] - m.p[0] * gp[2] + (A[2] - A[6]);
+      pose[5] = m.p[0] * gp[1] - m.p[1] * gp[0] + (A[3] - A[1]);
+    }
+  }
+  if (d_pose == nullptr) return;
+  // block reduction of the pose gradient: warp shuffles, then one warp
+  __shared__ float red[6][8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    float x = pose[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[k][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float x = lane < nw ? red[k][lane] : 0.0f;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0 && x != 0.0f) atomicAdd(d_pose + k, x);
+    }
+  }
+}
+
+int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, const ProjectedK& out,
+                       cudaStream_t s) {
+  if (g.n == 0) return SPLAT_OK;
+  project_fwd_kernel<<<ceil_div(g.n, 256), 256, 0, s>>>(g, cam, w2c, out);
+  return check_launch("project_fwd_kernel");
+}
+
+int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
+                       const float* d2d, const GradK& out, float* d_pose, cudaStream_t s) {
+  if (g.n == 0) return SPLAT_OK;
+  project_bwd_kernel<<<ceil_div(g.n, 256), 256, 0, s>>>(g, cam, w2c, conic, d2d, out, d_pose);
+  return check_launch("project_bwd_kernel");
+}
+
+}  // namespace splat

@@ -1,0 +1,343 @@
+"""CUDA path vs the CPU oracle, through the C ABI, on the same seeded inputs.
+
+Integer and bit-level outputs (projection, tile rects, sort keys, Gaussian
+ids, tile ranges, contributor counts, maximum-weight ids, association pairs)
+must match exactly; rendered colour / depth / silhouette / transmittance to
+1e-4 absolute; gradients to |g - g_ref| <= 1e-3 |g_ref| + 1e-3 rms(g_ref)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_09723_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL_GRAD = 1e-3
+ATOL_IMG = 1e-4
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_09723_gb300 import binding
+
+    binding.load()
+    return torch.device("cuda:0")
+
+
+def _params(sc, dev):
+    return tuple(torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev) for a in sc.arrays())
+
+
+def _w(w2c, dev):
+    return torch.as_tensor(np.ascontiguousarray(w2c, np.float32), device=dev)
+
+
+def _cases():
+    small = scenes.workload_small_forward()
+    ragged_cam = scenes.Camera(200, 150, 120.0, 120.0, 100.0, 75.0)
+    ragged = (scenes.scene_room(20000, 5), scenes.perturbed_w2c(6, 0.1, 10.0), ragged_cam, np.float32([0.2, 0.3, 0.4]))
+    return {"small_2k_128x96": small, "room_20k_200x150_ragged": ragged}
+
+
+CASES = _cases()
+
+
+def _full_vga():
+    sc, w2c, _, cam, bg = scenes.workload_track_map()
+    return sc, w2c, cam, bg
+
+
+def _render_gpu(sc, w2c, cam, bg, dev, want_keys=True):
+    from paper_2412_09723_gb300 import rasterizer as R
+
+    p = _params(sc, dev)
+    fb = R.FrameBuffers(sc.n, cam, dev, want_keys=want_keys)
+    R.render_forward(p, _w(w2c, dev), cam, tuple(float(x) for x in bg), fb)
+    torch.cuda.synchronize()
+    return p, fb
+
+
+def _bits(a):
+    a = np.ascontiguousarray(a)
+    return a.view(np.uint32) if a.dtype == np.float32 else a
+
+
+def _assert_grad_close(got, ref, name):
+    got, ref = np.asarray(got, np.float64).ravel(), np.asarray(ref, np.float64).ravel()
+    rms = float(np.sqrt(np.mean(ref ** 2))) if ref.size else 0.0
+    err = np.abs(got - ref)
+    bound = RTOL_GRAD * np.abs(ref) + RTOL_GRAD * rms
+    bad = err > bound
+    assert not bad.any(), f"{name}: {bad.sum()} of {bad.size} out of tolerance; worst {np.max(err / (bound + 1e-30))}"
+
+
+# ---------------------------------------------------------------------------
+def test_exp_bit_exact(dev):
+    from paper_2412_09723_gb300 import binding as B
+
+    bits = np.arange(0, 2 ** 32, 1031, dtype=np.uint64).astype(np.uint32)
+    x = bits.view(np.float32)
+    x = x[np.isfinite(x)]
+    x = np.concatenate([x, np.float32([0.0, -0.0, 88.0, 88.00001, -87.0, -87.00001, np.inf, -np.inf])])
+    xt = torch.as_tensor(x, device=dev)
+    yt = torch.empty_like(xt)
+    B.splat_exp_f32(xt, yt)
+    y = yt.cpu().numpy()
+    ref = oracle.exp_f32(x)
+    assert np.array_equal(_bits(y), _bits(ref))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_project_bit_exact(dev, case):
+    sc, w2c, cam, bg = CASES[case]
+    p, fb = _render_gpu(sc, w2c, cam, bg, dev)
+    ref = oracle.project(sc, w2c, cam)
+    got = {k: v.cpu().numpy() for k, v in fb.proj.items()}
+    assert np.array_equal(_bits(got["xyzo"]), _bits(ref["xyzo"]))
+    assert np.array_equal(_bits(got["conic"][:, :3]), _bits(ref["conic"][:, :3]))
+    for k in ("radius", "rect", "tiles_touched"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def _check_bins(fb, sc, w2c, cam):
+    keys, vals, ranges = oracle.bin_sort(sc, w2c, cam)
+    k = int(fb.k_dev.item())
+    assert k == len(vals)
+    assert int(fb.status.item()) == 0
+    assert np.array_equal(fb.vals[:k].cpu().numpy().view(np.uint32), vals)
+    assert np.array_equal(fb.keys[:k].cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(fb.ranges.cpu().numpy().view(np.uint32), ranges)
+
+
+def _check_image(fb, ref):
+    got = {k: v.cpu().numpy() for k, v in fb.image.items()}
+    for k in ("rgb", "depth", "sil", "t_final"):
+        d = np.abs(got[k].astype(np.float64) - ref[k])
+        assert d.max() <= ATOL_IMG, (k, d.max())
+    assert np.array_equal(got["n_contrib"], ref["n_contrib"])
+    assert np.array_equal(got["max_id"], ref["max_id"])
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_bin_sort_and_render_fwd(dev, case):
+    sc, w2c, cam, bg = CASES[case]
+    p, fb = _render_gpu(sc, w2c, cam, bg, dev)
+    _check_bins(fb, sc, w2c, cam)
+    _check_image(fb, oracle.render_fwd(sc, w2c, cam, bg))
+
+
+def test_full_size_vga_forward(dev):
+    sc, w2c, cam, bg = _full_vga()
+    p, fb = _render_gpu(sc, w2c, cam, bg, dev)
+    _check_bins(fb, sc, w2c, cam)
+    _check_image(fb, oracle.render_fwd(sc, w2c, cam, bg))
+
+
+def _bwd_gpu(p, fb, w2c, cam, bg, g, dev):
+    from paper_2412_09723_gb300 import binding as B
+
+    grads = [torch.zeros_like(t) for t in p]
+    d_pose = torch.zeros(6, dtype=torch.float32, device=dev)
+    d2d = torch.zeros(sc_n(p), 10, dtype=torch.float32, device=dev)
+    gr, gd, gs = (torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev) for a in g)
+    B.splat_render_bwd(B.gaussians_struct(*p), fb.cproj, fb.ccam, _w(w2c, dev), fb.vals, fb.ranges, fb.cimg, bg,
+                       gr, gd, gs, B.CGaussiansGrad(*(B._p(t) for t in grads)), d_pose, d2d, None)
+    torch.cuda.synchronize()
+    return [t.cpu().numpy() for t in grads], d_pose.cpu().numpy(), d2d.cpu().numpy()
+
+
+def sc_n(p):
+    return p[0].shape[0]
+
+
+def _upstream(cam, seed):
+    rng = np.random.default_rng(seed)
+    H, W = cam.height, cam.width
+    return (rng.normal(size=(H, W, 3)).astype(np.float32), rng.normal(size=(H, W)).astype(np.float32),
+            rng.normal(size=(H, W)).astype(np.float32))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_render_bwd(dev, case):
+    sc, w2c, cam, bg = CASES[case]
+    p, fb = _render_gpu(sc, w2c, cam, bg, dev)
+    g = _upstream(cam, 11)
+    grads, d_pose, d2d = _bwd_gpu(p, fb, w2c, cam, bg, g, dev)
+    ref = oracle.render_bwd(sc, w2c, cam, bg, *g)
+    _assert_grad_close(d2d, ref["d2d"], "d2d")
+    for name, got in zip(("mean", "log_scale", "quat", "opacity_logit", "rgb"), grads):
+        _assert_grad_close(got, ref[name], name)
+    _assert_grad_close(d_pose, ref["pose"], "pose")
+
+
+def test_full_size_vga_backward(dev):
+    sc, w2c, cam, bg = _full_vga()
+    p, fb = _render_gpu(sc, w2c, cam, bg, dev, want_keys=False)
+    g = _upstream(cam, 12)
+    grads, d_pose, d2d = _bwd_gpu(p, fb, w2c, cam, bg, g, dev)
+    ref = oracle.render_bwd(sc, w2c, cam, bg, *g)
+    for name, got in zip(("mean", "log_scale", "quat", "opacity_logit", "rgb"), grads):
+        _assert_grad_close(got, ref[name], name)
+    _assert_grad_close(d_pose, ref["pose"], "pose")
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_empty_map(dev):
+    sc = scenes.scene_uniform(0, 0)
+    cam = scenes.Camera(40, 24, 50.0, 50.0, 20.0, 12.0)
+    p, fb = _render_gpu(sc, np.eye(4, dtype=np.float32), cam, (0.1, 0.2, 0.3), dev)
+    assert int(fb.k_dev.item()) == 0
+    assert not fb.ranges.any()
+    rgb = fb.image["rgb"].cpu().numpy()
+    assert np.allclose(rgb, np.float32([0.1, 0.2, 0.3]))
+    assert (fb.image["max_id"].cpu().numpy() == -1).all()
+
+
+def test_all_behind_camera(dev):
+    sc = scenes.scene_uniform(500, 1)
+    sc.mean[:, 2] = -sc.mean[:, 2]
+    cam = scenes.CAM_SMALL
+    p, fb = _render_gpu(sc, np.eye(4, dtype=np.float32), cam, (0, 0, 0), dev)
+    assert int(fb.k_dev.item()) == 0
+    assert (fb.proj["radius"].cpu().numpy() == 0).all()
+    assert (fb.image["t_final"].cpu().numpy() == 1).all()
+
+
+def test_zero_opacity_background(dev):
+    sc, w2c, cam, _ = scenes.workload_small_forward(seed=9)
+    sc.opacity_logit[:] = -np.inf
+    p, fb = _render_gpu(sc, w2c, cam, (0.25, 0.5, 0.75), dev)
+    assert np.array_equal(fb.image["rgb"].cpu().numpy(), np.broadcast_to(np.float32([0.25, 0.5, 0.75]), (96, 128, 3)))
+    assert (fb.image["t_final"].cpu().numpy() == 1).all() and (fb.image["max_id"].cpu().numpy() == -1).all()
+    assert (fb.image["n_contrib"].cpu().numpy() == 0).all()
+
+
+def test_capacity_overflow_is_reported(dev):
+    from paper_2412_09723_gb300 import binding as B
+    from paper_2412_09723_gb300 import rasterizer as R
+
+    sc, w2c, cam, bg = scenes.workload_small_forward()
+    p = _params(sc, dev)
+    fb = R.FrameBuffers(sc.n, cam, dev, capacity=1000)
+    R.project(B.gaussians_struct(*p), _w(w2c, dev), fb)
+    fb.status.zero_()
+    B.splat_bin_sort(fb.cproj, fb.n, fb.ccam, None, fb.vals, fb.capacity, fb.k_dev, fb.ranges, fb.status, fb.bin_ws)
+    torch.cuda.synchronize()
+    k_true = len(oracle.bin_sort(sc, w2c, cam)[1])
+    assert int(fb.k_dev.item()) == k_true > 1000
+    assert int(fb.status.item()) == B.SPLAT_ECAPACITY
+    r = fb.ranges.cpu().numpy().view(np.uint32)
+    assert r.max() <= 1000
+
+
+def test_single_tile_image(dev):
+    sc = scenes.scene_uniform(300, 4)
+    cam = scenes.Camera(13, 9, 12.0, 12.0, 6.5, 4.5)
+    p, fb = _render_gpu(sc, np.eye(4, dtype=np.float32), cam, (0, 0, 0), dev)
+    _check_bins(fb, sc, np.eye(4, dtype=np.float32), cam)
+    _check_image(fb, oracle.render_fwd(sc, np.eye(4, dtype=np.float32), cam, np.zeros(3, np.float32)))
+
+
+# ---------------------------------------------------------------------------
+# loss, Adam, pose step, association
+# ---------------------------------------------------------------------------
+def test_loss_l1(dev):
+    from paper_2412_09723_gb300 import binding as B
+
+    rng = np.random.default_rng(0)
+    H, W = 37, 53
+    a = [rng.uniform(size=s).astype(np.float32) for s in ((H, W, 3), (H, W), (H, W, 3), (H, W))]
+    a[2][:3] = a[0][:3]  # exact ties -> zero subgradient
+    t = [torch.as_tensor(x, device=dev) for x in a]
+    gr, gd = torch.empty_like(t[0]), torch.empty_like(t[1])
+    loss = torch.zeros(1, device=dev)
+    B.splat_loss_l1(t[0], t[1], t[2], t[3], 1.0, 0.5, gr, gd, loss)
+    L, rgr, rgd = oracle.loss_l1(a[0], a[1], a[2], a[3], 1.0, 0.5)
+    assert np.array_equal(gr.cpu().numpy(), rgr) and np.array_equal(gd.cpu().numpy(), rgd)
+    assert float(loss.item()) == pytest.approx(L, rel=1e-5)
+
+
+def test_adam(dev):
+    from paper_2412_09723_gb300 import binding as B
+
+    rng = np.random.default_rng(1)
+    n = 10007
+    p, g, m, v = (rng.normal(size=n).astype(np.float32) for _ in range(4))
+    v = np.abs(v)
+    tp, tg, tm, tv = (torch.as_tensor(x.copy(), device=dev) for x in (p, g, m, v))
+    B.splat_adam(tp, tg, tm, tv, 3, 1e-3)
+    rp, rm, rv = oracle.adam(p, g, m, v, 3, 1e-3)
+    np.testing.assert_allclose(tp.cpu().numpy(), rp, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(tm.cpu().numpy(), rm, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(tv.cpu().numpy(), rv, rtol=1e-6, atol=1e-7)
+
+
+def test_pose_step_matches_host_retraction(dev):
+    from paper_2412_09723_gb300 import binding as B
+    from paper_2412_09723_gb300.rasterizer import se3_exp
+
+    w0 = scenes.perturbed_w2c(3, 0.2, 15.0)
+    w = _w(w0, dev)
+    g = torch.tensor([0.3, -0.2, 0.1, 0.05, -0.4, 0.2], device=dev)
+    m, v = torch.zeros(6, device=dev), torch.zeros(6, device=dev)
+    B.splat_pose_step(w, g, m, v, 1, 0.01, 0.002)
+    # first Adam step = -lr sign(g)
+    d = -np.sign(g.cpu().numpy()) * np.array([0.01] * 3 + [0.002] * 3)
+    ref = se3_exp(torch.tensor(d)).numpy() @ w0.astype(np.float64)
+    np.testing.assert_allclose(w.cpu().numpy(), ref, atol=2e-6)
+
+
+def test_assoc_two_maps(dev):
+    from paper_2412_09723_gb300 import binding as B
+
+    cam = scenes.Camera(160, 120, 130.0, 130.0, 80.0, 60.0)
+    a = scenes.scene_room(30000, 7)
+    b = scenes.scene_room(25000, 8)
+    w2c = scenes.perturbed_w2c(9, 0.05, 3.0)
+    ra = oracle.render_fwd(a, w2c, cam, np.zeros(3))
+    rb = oracle.render_fwd(b, w2c, cam, np.zeros(3))
+    ref_pairs, ref_counts = oracle.assoc(ra["max_id"], ra["t_final"], rb["max_id"], rb["t_final"], 0.5)
+    t = [torch.as_tensor(x, device=dev) for x in (ra["max_id"], ra["t_final"], rb["max_id"], rb["t_final"])]
+    npix = cam.npix
+    cap = npix
+    pairs = torch.zeros(cap, 2, dtype=torch.int32, device=dev)
+    counts = torch.zeros(cap, dtype=torch.int32, device=dev)
+    m_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(B.splat_assoc_workspace_size(npix), dtype=torch.uint8, device=dev)
+    B.splat_assoc(t[0], t[1], t[2], t[3], a.n, b.n, 0.5, pairs, counts, cap, m_dev, status, ws)
+    m = int(m_dev.item())
+    assert m == len(ref_pairs) > 100
+    assert np.array_equal(pairs[:m].cpu().numpy(), ref_pairs)
+    assert np.array_equal(counts[:m].cpu().numpy(), ref_counts)
+    assert int(status.item()) == 0
+    # too small a capacity: status raised, the first pairs kept
+    status.zero_()
+    B.splat_assoc(t[0], t[1], t[2], t[3], a.n, b.n, 0.5, pairs, counts, 10, m_dev, status, ws)
+    assert int(status.item()) == B.SPLAT_ECAPACITY and int(m_dev.item()) == m
+    assert np.array_equal(pairs[:10].cpu().numpy(), ref_pairs[:10])
+
+
+# ---------------------------------------------------------------------------
+# autograd wrapper
+# ---------------------------------------------------------------------------
+def test_autograd_matches_oracle(dev):
+    from paper_2412_09723_gb300 import rasterizer as R
+
+    sc, w2c, cam, bg = CASES["room_20k_200x150_ragged"]
+    p = [t.clone().requires_grad_(True) for t in _params(sc, dev)]
+    delta = torch.zeros(6, device=dev, requires_grad=True)
+    rgb, depth, sil, tfin, mid = R.render(*p, _w(w2c, dev), cam, tuple(float(x) for x in bg), delta)
+    g = _upstream(cam, 13)
+    gt = [torch.as_tensor(x, device=dev) for x in g]
+    L = (rgb * gt[0]).sum() + (depth * gt[1]).sum() + (sil * gt[2]).sum()
+    L.backward()
+    ref = oracle.render_bwd(sc, w2c, cam, bg, *g)
+    for name, t in zip(("mean", "log_scale", "quat", "opacity_logit", "rgb"), p):
+        _assert_grad_close(t.grad.cpu().numpy(), ref[name], name)
+    _assert_grad_close(delta.grad.cpu().numpy(), ref["pose"], "pose")
