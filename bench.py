@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the differentiable RGB-D splat hot path on GB300.
+
+Metric: fwd+bwd RGB-D splat frames/s (with p50/p99 step latency) on the
+single-agent tracking + mapping workload: a 300k-Gaussian room map (means on
+six walls, 2 cm off-plane), 640x480 frames (fx = fy = 525), loss = L1 RGB +
+0.5 L1 depth against a target rendered from a pose perturbed by 1 cm / 0.5
+degrees.  One step = project -> bin/sort -> render -> loss -> backward to
+every Gaussian parameter and the SE(3) pose -> Adam on the map -> pose step
+-> render-based association against the target's ids.  Inputs are synthetic
+and seeded.  Between timed steps the L2 cache is flushed by writing 256 MiB.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own agent (independent maps; weak scaling;
+no collective on the data path); rank 0 prints one JSON line.
+`--impl reference` times the CPU oracle on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd RGB-D splat frames/s and p50/p99 step latency, served vs plain"
+UNIT = "frames/s"
+WORKLOAD = "track_map_300k_640x480"
+N_GAUSSIANS = 300_000
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic FP32 operations per unit (one FMA counts as one operation; the
+# peak below is the FP32 issue rate).  Units: a "walked" (pixel, Gaussian)
+# pair is a list position before the pixel's last contributor (its quadratic
+# form is evaluated and tested); a "contributing" pair passed both tests and
+# is composited (forward) or differentiated (backward).
+OPS_WALK = 9
+OPS_CONTRIB_FWD = 25
+OPS_CONTRIB_BWD = 63
+SMS, FP32_LANES = 152, 128
+
+
+def _parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed CPU oracle sample")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    ap.add_argument("--no-profile", action="store_true", help="do not time kernels individually (no roofline)")
+    return ap.parse_args()
+
+
+def _dist():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_step(oracle, sc, w2c, cam, bg, target, lr, rows=None):
+    """One oracle step (fwd + L1 loss + bwd + Adam + assoc) of the whole frame,
+    or of the band of pixel rows `rows` = (row0, row1)."""
+    import numpy as np
+
+    r0, r1 = rows or (0, cam.height)
+    out = oracle.render_fwd(sc, w2c, cam, bg, rows=(r0, r1))
+    L, g_rgb, g_depth = oracle.loss_l1(out["rgb"][r0:r1], out["depth"][r0:r1], target["rgb"][r0:r1],
+                                       target["depth"][r0:r1], 1.0, 0.5)
+    G_rgb = np.zeros_like(out["rgb"])
+    G_depth = np.zeros_like(out["depth"])
+    G_rgb[r0:r1], G_depth[r0:r1] = g_rgb, g_depth
+    grads = oracle.render_bwd(sc, w2c, cam, bg, G_rgb, G_depth, rows=(r0, r1))
+    for name in ("mean", "log_scale", "quat", "opacity_logit", "rgb"):
+        p = getattr(sc, name)
+        z = np.zeros_like(p)
+        newp, _, _ = oracle.adam(p, grads[name], z, z, 1, lr[name])
+        setattr(sc, name, newp.reshape(p.shape))
+    oracle.assoc(out["max_id"][r0:r1], out["t_final"][r0:r1], target["max_id"][r0:r1], target["t_final"][r0:r1],
+                 0.5)
+    return L
+
+
+def _cpu_workload():
+    from paper_2412_09723_gb300 import scenes
+
+    sc, w2c, w2c_target, cam, bg = scenes.workload_track_map()
+    return sc, w2c, w2c_target, cam, bg
+
+
+def cpu_baseline_sample():
+    """Time the oracle as it stands (single-threaded) on one full frame of the
+    workload: fwd + loss + bwd + Adam + association."""
+    import oracle
+    from paper_2412_09723_gb300.agent import DEFAULT_LR
+
+    oracle.lib()
+    sc, w2c, w2c_t, cam, bg = _cpu_workload()
+    target = oracle.render_fwd(sc, w2c_t, cam, bg)
+    t0 = time.perf_counter()
+    _oracle_step(oracle, sc, w2c, cam, bg, target, DEFAULT_LR)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full frame (fwd + L1 loss + bwd + Adam + assoc) of {WORKLOAD}, single-threaded, "
+                      f"{dt:.2f} s"}
+
+
+REF_BAND_ROWS = 16
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm.  Each step is a bounded sample of
+    the workload: one 16-row band of the frame (fwd + loss + bwd + Adam +
+    assoc, with the projection of the whole map), cycling down the frame; the
+    frame rate is the band's share of a frame divided by the step time."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2412_09723_gb300.agent import DEFAULT_LR
+
+    oracle.lib()
+    sc, w2c, w2c_t, cam, bg = _cpu_workload()
+    target = oracle.render_fwd(sc, w2c_t, cam, bg)
+    nb = cam.height // REF_BAND_ROWS
+    times = []
+    for k in range(args.warmup + args.steps):
+        b = k % nb
+        t0 = time.perf_counter()
+        _oracle_step(oracle, sc, w2c, cam, bg, target, DEFAULT_LR, rows=(b * REF_BAND_ROWS, (b + 1) * REF_BAND_ROWS))
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    frac = REF_BAND_ROWS / cam.height
+    value = frac * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSSIANS, "width": cam.width, "height": cam.height},
+            "p50_ms": 1e3 * statistics.median(times), "p99_ms": 1e3 * _pct(times, 99),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"per step one {REF_BAND_ROWS}-row band of {WORKLOAD} (fwd + L1 loss + bwd + "
+                                       "Adam + assoc; the whole map projected), single-threaded CPU oracle; "
+                                       "frames/s = band fraction / step time"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _pct(xs, q):
+    s = sorted(xs)
+    if not s:
+        return float("nan")
+    k = min(len(s) - 1, max(0, int(math.ceil(q / 100.0 * len(s))) - 1))
+    return s[k]
+
+
+def _source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel's source is unchanged since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e:
+        return None
+    src = [os.path.join(ROOT, p) for p in e.get("sources", [])]
+    if not src or any(not os.path.exists(p) for p in src) or _source_hash(src) != e.get("source_hash"):
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = _parse()
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2412_09723_gb300 import binding as B
+    from paper_2412_09723_gb300 import scenes
+    from paper_2412_09723_gb300.agent import Agent
+
+    B.load()
+    seed = 1 + 100 * rank
+    sc, w2c, w2c_target, cam, bg = scenes.workload_track_map(seed=seed)
+    agent = Agent(sc, w2c, cam, dev, want_used=True)
+    agent.render_observation_from(w2c_target)
+    agent.size_capacity(1.5)
+    torch.cuda.synchronize()
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        agent.step()
+    torch.cuda.synchronize()
+    # algorithmic units of the render kernels (from the warm state; constant up to the pose drift)
+    q_walk = int(agent.fb.image["n_contrib"].sum().item())
+    q_used = int(agent.fb.image["n_used"].sum().item())
+
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = B.splat_kernel_launches()
+    B.splat_profile_read()  # drop stale records
+    B.splat_profile_enable(not args.no_profile)
+    t_wall0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_(float(k))
+        evs[k][0].record()
+        agent.step()
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    B.splat_profile_enable(False)
+    launches = B.splat_kernel_launches() - launches0
+    prof = B.splat_profile_read()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    status = agent.status()
+    if status != 0:
+        raise SystemExit(f"device status {status} (capacity overflow) during the timed steps")
+    mx = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    total_ms_max = float(mx.item())
+    value = world * K / (total_ms_max / 1e3)
+
+    # dominant kernel and its roofline
+    kernels = sorted(prof.items(), key=lambda kv: -kv[1][1])
+    top, (top_n, top_ms) = kernels[0] if kernels else ("none", (1, 0.0))
+    avg_s = top_ms / top_n / 1e3
+    peaks, peak_kind = _peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak_tops = SMS * FP32_LANES * sm_mhz * 1e6 / 1e12
+    if top == "render_bwd_kernel":
+        ops = OPS_WALK * q_walk + OPS_CONTRIB_BWD * q_used
+    elif top == "render_fwd_kernel":
+        ops = OPS_WALK * q_walk + OPS_CONTRIB_FWD * q_used
+    else:
+        ops = None
+    roofline = None
+    if ops is not None:
+        ach = ops / avg_s / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": alu_peak_tops, "unit": "TFLOP/s",
+                    "frac": ach / alu_peak_tops, "traffic": _traffic_for(top), "kernel": top,
+                    "peak_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz "
+                                   f"({peak_kind} max SM clock); one FMA = one op",
+                    "units": {"walked_pairs": q_walk, "contributing_pairs": q_used},
+                    "avg_launch_ms": avg_s * 1e3}
+    tot_prof = sum(v[1] for v in prof.values()) or 1.0
+    breakdown = {k: {"launches": n, "ms_per_step": ms / K, "share": ms / tot_prof} for k, (n, ms) in kernels}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        H, W = cam.height, cam.width
+        h_rgb = agent.obs_rgb.cpu().pin_memory()
+        h_depth = agent.obs_depth.cpu().pin_memory()
+        h_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+        h_pose = torch.empty(4, 4, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        Ke = max(1, min(K, 200))
+        t_e2e = []
+        for k in range(Ke):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            agent.set_observation(h_rgb.to(dev, non_blocking=True), h_depth.to(dev, non_blocking=True))
+            agent.step()
+            h_loss.copy_(agent.loss, non_blocking=True)
+            h_pose.copy_(agent.w2c, non_blocking=True)
+            torch.cuda.synchronize()
+            t_e2e.append(time.perf_counter() - t0)
+        e2e = {"value": world * Ke / sum(t_e2e), "unit": UNIT, "h2d_bytes_per_step": 4 * H * W * 4,
+               "d2h_bytes_per_step": 4 + 64, "steps": Ke, "p50_ms": 1e3 * statistics.median(t_e2e),
+               "p99_ms": 1e3 * _pct(t_e2e, 99)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+                "ms_per_step": total_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSSIANS, "width": cam.width,
+                           "height": cam.height, "duplicates_K": int(agent.fb.k_dev.item()),
+                           "l2": "flushed between steps (256 MiB write)", "mode": "eager stream-ordered",
+                           "parallelism": f"{world} independent agent(s), one per GPU"},
+                "p50_ms": statistics.median(step_ms), "p99_ms": _pct(step_ms, 99),
+                "wall_s_timed": t_wall, "gpu_launches": launches, "roofline": roofline, "kernels": breakdown,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

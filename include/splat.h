@@ -107,6 +107,8 @@ typedef struct {
                         contributor, plus one (0 = none)                */
   int32_t *max_id;   /* Gaussian with the largest alpha_i T_i; -1 = none;
                         ties keep the front-most                         */
+  int32_t *n_used;   /* optional (may be NULL): number of Gaussians that
+                        contributed to the pixel                         */
 } splat_image;
 
 /* Version of this ABI (incremented on any incompatible change). */
@@ -114,6 +116,27 @@ int32_t splat_abi_version(void);
 
 /* Text of the last error returned on the calling thread ("" if none). */
 const char *splat_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (host-side
+ * count of launch calls; kernels replayed from a captured graph are not
+ * counted again). */
+uint64_t splat_kernel_launches(void);
+
+/* Per-kernel timing (tracing aid; the paper reports per-frame timings only,
+ * Sec. 4.4).  While enabled, every kernel launch of this library is bracketed
+ * by a CUDA event pair recorded on its launching stream.  Do not enable it
+ * while a stream is being captured into a graph.  Returns SPLAT_OK. */
+int splat_profile_enable(int on);
+
+/* Waits for the recorded events, then returns, per kernel name, the number of
+ * timed launches and their summed duration in milliseconds, and forgets the
+ * records.  names (host, names_bytes) receives the kernel names separated by
+ * '\n' (truncated to fit); launches (host int64[max_kernels]) and ms (host
+ * double[max_kernels]) the figures in the same order; *n_kernels (host) the
+ * number of distinct kernels (which may exceed max_kernels).
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA (an event could not be read). */
+int splat_profile_read(char *names, size_t names_bytes, int64_t *launches, double *ms,
+                       int32_t max_kernels, int32_t *n_kernels);
 
 /*
  * splat_project -- per-Gaussian activation and EWA projection (Sec. 3.3, the
@@ -215,20 +238,23 @@ int splat_loss_l1(const float *rgb, const float *depth, const float *target_rgb,
  * splat_adam -- one bias-corrected Adam step on n resident float32
  * parameters (map optimisation, Sec. 3.4 step 4, following SplaTAM):
  *   m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
- *   p -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
- * Errors: SPLAT_EINVAL (step < 1), SPLAT_ECUDA.
+ *   p -= lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps).
+ * step: DEVICE int32[1] holding t >= 1 (read on the device, so that a
+ * captured graph can be replayed with an advancing count).
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
  */
-int splat_adam(float *param, const float *grad, float *m, float *v, int64_t n, int32_t step,
+int splat_adam(float *param, const float *grad, float *m, float *v, int64_t n, const int32_t *step,
                float lr, float beta1, float beta2, float eps, splat_stream_t stream);
 
 /*
  * splat_pose_step -- Adam on the 6-vector pose gradient followed by the
  * retraction w2c <- exp(delta^) w2c (render-driven tracking / alignment).
  *   w2c: device float[16] updated in place; d_pose: device float[6];
- *   m, v: device float[6] moments; lr_t, lr_r: step sizes for rho and phi.
+ *   m, v: device float[6] moments; step: DEVICE int32[1] holding t >= 1;
+ *   lr_t, lr_r: step sizes for rho and phi.
  * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
  */
-int splat_pose_step(float *w2c, const float *d_pose, float *m, float *v, int32_t step,
+int splat_pose_step(float *w2c, const float *d_pose, float *m, float *v, const int32_t *step,
                     float lr_t, float lr_r, float beta1, float beta2, float eps,
                     splat_stream_t stream);
 

@@ -60,9 +60,9 @@ def _declare(L):
     for suf in ("f32", "f64"):
         getattr(L, f"oracle_project_{suf}").argtypes = [_I64] + [_P] * 13
         getattr(L, f"oracle_project_{suf}").restype = ctypes.c_int
-        getattr(L, f"oracle_render_fwd_{suf}").argtypes = [_I64] + [_P] * 17
+        getattr(L, f"oracle_render_fwd_{suf}").argtypes = [_I64] + [_P] * 17 + [_I32, _I32]
         getattr(L, f"oracle_render_fwd_{suf}").restype = ctypes.c_int
-        getattr(L, f"oracle_render_bwd_{suf}").argtypes = [_I64] + [_P] * 19
+        getattr(L, f"oracle_render_bwd_{suf}").argtypes = [_I64] + [_P] * 19 + [_I32, _I32]
         getattr(L, f"oracle_render_bwd_{suf}").restype = ctypes.c_int
     L.oracle_bin_f32.argtypes = [_I64] + [_P] * 7 + [_I64, _P, _P, _P]
     L.oracle_bin_f32.restype = _I64
@@ -140,10 +140,10 @@ def bin_sort(scene, w2c, cam):
     return keys[:k], vals[:k], ranges
 
 
-def render_fwd(scene, w2c, cam, bg, dtype=np.float32):
+def render_fwd(scene, w2c, cam, bg, dtype=np.float32, rows=None):
     """Forward render: rgb [H,W,3], depth, sil, t_final [H,W], n_contrib, max_id
-    [H,W] int32, the hash of all discrete decisions and the number of
-    contributing (pixel, Gaussian) pairs."""
+    [H,W] int32, the hash of all discrete decisions and the summed n_contrib.
+    `rows` = (row0, row1) renders only that band (other pixels stay zero)."""
     H, W = cam.height, cam.width
     args = _scene_args(scene, dtype) + [_c(scene.rgb, dtype)]
     w = _c(w2c, dtype)
@@ -157,18 +157,19 @@ def render_fwd(scene, w2c, cam, bg, dtype=np.float32):
     getattr(lib(), f"oracle_render_fwd_{_suffix(dtype)}")(
         scene.n, *map(_ptr, args), _ptr(w), _ptr(ci), _ptr(cf), _ptr(b), _ptr(out["rgb"]),
         _ptr(out["depth"]), _ptr(out["sil"]), _ptr(out["t_final"]), _ptr(out["n_contrib"]),
-        _ptr(out["max_id"]), _ptr(sig), _ptr(npairs))
+        _ptr(out["max_id"]), _ptr(sig), _ptr(npairs), *(rows or (0, H)))
     out["signature"] = int(sig[0])
     out["n_pairs"] = int(npairs[0])
     return out
 
 
-def render_bwd(scene, w2c, cam, bg, g_rgb, g_depth=None, g_sil=None, dtype=np.float32):
+def render_bwd(scene, w2c, cam, bg, g_rgb, g_depth=None, g_sil=None, dtype=np.float32, rows=None):
     """Adjoint of render_fwd for upstream per-pixel gradients.  Returns the
     gradients of mean, log_scale, quat, opacity_logit, rgb, the 6-vector pose
     gradient (rho, phi) of the left perturbation exp(delta^) w2c, and the
     per-Gaussian screen-space gradients d2d [N,10] = (du, dv, dconic a, b, c,
-    dopacity, drgb[3], ddepth)."""
+    dopacity, drgb[3], ddepth).  `rows` = (row0, row1) differentiates only the
+    pixels of that band."""
     n = scene.n
     args = _scene_args(scene, dtype) + [_c(scene.rgb, dtype)]
     w = _c(w2c, dtype)
@@ -183,7 +184,7 @@ def render_bwd(scene, w2c, cam, bg, g_rgb, g_depth=None, g_sil=None, dtype=np.fl
     getattr(lib(), f"oracle_render_bwd_{_suffix(dtype)}")(
         n, *map(_ptr, args), _ptr(w), _ptr(ci), _ptr(cf), _ptr(b), _ptr(gr), _ptr(gd), _ptr(gs),
         _ptr(out["mean"]), _ptr(out["log_scale"]), _ptr(out["quat"]), _ptr(out["opacity_logit"]),
-        _ptr(out["rgb"]), _ptr(out["pose"]), _ptr(out["d2d"]))
+        _ptr(out["rgb"]), _ptr(out["pose"]), _ptr(out["d2d"]), *(rows or (0, cam.height)))
     return out
 
 

@@ -281,14 +281,16 @@ std::vector<Proj<T>> project_all(const Scene<T>& S, const T* w2c, const Cam<T>& 
 
 // O2 + O3: per-tile candidate lists ordered by (depth, gid).  The depth order
 // in float is the order of the float bit patterns (depth > 0).
+// Only tile rows [ty0, ty1) are filled (all rows by default).
 template <typename T>
-std::vector<std::vector<int32_t>> bin_all(const std::vector<Proj<T>>& P, const Cam<T>& cam) {
+std::vector<std::vector<int32_t>> bin_all(const std::vector<Proj<T>>& P, const Cam<T>& cam, int ty0 = 0,
+                                          int ty1 = 1 << 30) {
   const int ntx = cam.tiles_x(), nty = cam.tiles_y();
   std::vector<std::vector<int32_t>> bins((size_t)ntx * nty);
   for (size_t g = 0; g < P.size(); ++g) {
     const Proj<T>& p = P[g];
     if (p.tiles == 0) continue;
-    for (int ty = p.rect[1]; ty < p.rect[3]; ++ty)
+    for (int ty = std::max(p.rect[1], ty0); ty < std::min(p.rect[3], ty1); ++ty)
       for (int tx = p.rect[0]; tx < p.rect[2]; ++tx) bins[(size_t)ty * ntx + tx].push_back((int32_t)g);
   }
   for (auto& b : bins)
@@ -389,12 +391,14 @@ Scene<T> make_scene(int64_t n, const T* mean, const T* ls, const T* q, const T* 
 // ---------------------------------------------------------------------------
 // Forward render of one view.
 // ---------------------------------------------------------------------------
+// Pixel rows [row0, row1) are rendered (a band of the image; the rest of the
+// outputs is left untouched).
 template <typename T>
 int render_fwd(const Scene<T>& S, const T* w2c, const Cam<T>& cam, const T* bg,
                T* out_rgb, T* out_depth, T* out_sil, T* out_tfin, int32_t* out_n,
-               int32_t* out_id, uint64_t* signature, int64_t* n_pairs) {
+               int32_t* out_id, uint64_t* signature, int64_t* n_pairs, int row0, int row1) {
   auto P = project_all(S, w2c, cam);
-  auto bins = bin_all(P, cam);
+  auto bins = bin_all(P, cam, row0 / TILE, (row1 + TILE - 1) / TILE);
   const int ntx = cam.tiles_x();
   Sig sig;
   int64_t pairs = 0;
@@ -402,7 +406,7 @@ int render_fwd(const Scene<T>& S, const T* w2c, const Cam<T>& cam, const T* bg,
     sig.add(P[g].radius);
     for (int k = 0; k < 4; ++k) sig.add(P[g].rect[k]);
   }
-  for (int y = 0; y < cam.height; ++y)
+  for (int y = row0; y < row1; ++y)
     for (int x = 0; x < cam.width; ++x) {
       const auto& list = bins[(size_t)(y / TILE) * ntx + (x / TILE)];
       PixOut<T> o = composite_pixel<T>(x, y, list, P, S.rgb, bg, nullptr, signature ? &sig : nullptr);
@@ -584,13 +588,13 @@ void project_adjoint(int64_t g, const Scene<T>& S, const T* w2c, const Cam<T>& c
 template <typename T>
 int render_bwd(const Scene<T>& S, const T* w2c, const Cam<T>& cam, const T* bg, const T* g_rgb,
                const T* g_depth, const T* g_sil, T* d_mean, T* d_ls, T* d_q, T* d_logit, T* d_rgb,
-               T* d_pose, T* d2d) {
+               T* d_pose, T* d2d, int row0, int row1) {
   auto P = project_all(S, w2c, cam);
-  auto bins = bin_all(P, cam);
+  auto bins = bin_all(P, cam, row0 / TILE, (row1 + TILE - 1) / TILE);
   const int ntx = cam.tiles_x();
   std::vector<Grad2D<T>> G2((size_t)S.n);
   std::vector<Contrib<T>> rec;
-  for (int y = 0; y < cam.height; ++y)
+  for (int y = row0; y < row1; ++y)
     for (int x = 0; x < cam.width; ++x) {
       const auto& list = bins[(size_t)(y / TILE) * ntx + (x / TILE)];
       rec.clear();
@@ -679,15 +683,19 @@ int64_t oracle_bin_f32(int64_t n, const float* mean, const float* log_scale, con
                               const T* logit, const T* rgb, const T* w2c, const int32_t* cam_i,  \
                               const T* cam_f, const T* bg, T* out_rgb, T* out_depth, T* out_sil, \
                               T* out_tfin, int32_t* out_n, int32_t* out_id, uint64_t* signature, \
-                              int64_t* n_pairs) {                                                \
+                              int64_t* n_pairs, int32_t row0, int32_t row1) {                    \
     const Cam<T> cam = make_cam<T>(cam_i, cam_f);                                                \
     Scene<T> S = make_scene<T>(n, mean, log_scale, quat, logit, rgb);                            \
+    row0 = std::max(0, row0);                                                                    \
+    row1 = std::min(cam.height, row1);                                                           \
     return render_fwd<T>(S, w2c, cam, bg, out_rgb, out_depth, out_sil, out_tfin, out_n, out_id,  \
-                         signature, n_pairs);                                                    \
+                         signature, n_pairs, row0, row1);                                        \
   }
 ORACLE_FWD(f32, float)
 ORACLE_FWD(f64, double)
 
+// Rows [row0, row1) of the image are rendered / differentiated (pass 0 and the height for
+// the whole frame).
 // Gradients are accumulated (+=) into caller-zeroed buffers.  d2d (optional) receives the
 // per-Gaussian screen-space gradients [n,10] = du, dv, dconic_a, dconic_b, dconic_c,
 // dlambda, drgb[3], ddepth.
@@ -696,11 +704,13 @@ ORACLE_FWD(f64, double)
                               const T* logit, const T* rgb, const T* w2c, const int32_t* cam_i,   \
                               const T* cam_f, const T* bg, const T* g_rgb, const T* g_depth,      \
                               const T* g_sil, T* d_mean, T* d_log_scale, T* d_quat, T* d_logit,   \
-                              T* d_rgb, T* d_pose, T* d2d) {                                      \
+                              T* d_rgb, T* d_pose, T* d2d, int32_t row0, int32_t row1) {          \
     const Cam<T> cam = make_cam<T>(cam_i, cam_f);                                                 \
     Scene<T> S = make_scene<T>(n, mean, log_scale, quat, logit, rgb);                             \
+    row0 = std::max(0, row0);                                                                     \
+    row1 = std::min(cam.height, row1);                                                            \
     return render_bwd<T>(S, w2c, cam, bg, g_rgb, g_depth, g_sil, d_mean, d_log_scale, d_quat,     \
-                         d_logit, d_rgb, d_pose, d2d);                                            \
+                         d_logit, d_rgb, d_pose, d2d, row0, row1);                                \
   }
 ORACLE_BWD(f32, float)
 ORACLE_BWD(f64, double)

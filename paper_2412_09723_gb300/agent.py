@@ -1,0 +1,159 @@
+"""One agent's resident state and its tracking + mapping step.
+
+An agent keeps its Gaussian map, the map's Adam moments, its camera pose
+(world-to-camera, device float[16]) with the pose's Adam moments, the current
+RGB-D observation and every work buffer on the device.  One step is the whole
+hot path of the method for one frame:
+
+  splat_project -> splat_bin_sort -> splat_render_fwd      (render, Sec. 3.3)
+  -> splat_loss_l1 (L1 colour + w_depth L1 depth, L1 terms of Eq. optim)
+  -> splat_render_bwd (gradients to every Gaussian parameter and the pose)
+  -> splat_adam per parameter group (mapping, Sec. 3.4 step 4)
+  -> splat_pose_step (render-driven tracking)
+  -> splat_assoc of the rendered maximum-weight ids against the observation's
+     ids (render-based association, Sec. 3.5 step 2).
+
+`step()` issues only stream-ordered launches (no host synchronisation unless
+asked for), so it can run back to back, be timed with events, or be captured.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+from . import binding as B
+from .rasterizer import FrameBuffers, bin_sort, project
+from .scenes import Camera
+
+# SplaTAM-style learning rates (the optimiser the paper follows, Sec. 3.4).
+DEFAULT_LR = dict(mean=1e-4, log_scale=1e-3, quat=1e-3, opacity_logit=5e-2, rgb=2.5e-3)
+DEFAULT_POSE_LR = (2e-3, 4e-4)  # translation, rotation
+
+
+@dataclasses.dataclass
+class StepConfig:
+    w_rgb: float = 1.0
+    w_depth: float = 0.5
+    lr: dict = dataclasses.field(default_factory=lambda: dict(DEFAULT_LR))
+    pose_lr: tuple = DEFAULT_POSE_LR
+    track: bool = True
+    map: bool = True
+    assoc: bool = True
+    t_max: float = 0.5
+    bg: tuple = (0.0, 0.0, 0.0)
+
+
+class Agent:
+    """Resident map + optimiser state + buffers of one agent."""
+
+    def __init__(self, scene, w2c, cam: Camera, device, cfg: StepConfig | None = None, capacity: int | None = None,
+                 want_used: bool = False):
+        self.cfg = cfg or StepConfig()
+        self.cam = cam
+        self.device = device
+        self.params = [torch.as_tensor(a, dtype=torch.float32, device=device).contiguous() for a in scene.arrays()]
+        self.n = self.params[0].shape[0]
+        self.grads = [torch.zeros_like(p) for p in self.params]
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+        self.w2c = torch.as_tensor(w2c, dtype=torch.float32, device=device).contiguous().clone()
+        self.d_pose = torch.zeros(6, dtype=torch.float32, device=device)
+        self.pose_m = torch.zeros(6, dtype=torch.float32, device=device)
+        self.pose_v = torch.zeros(6, dtype=torch.float32, device=device)
+        self.fb = FrameBuffers(self.n, cam, device, capacity=capacity, want_used=want_used)
+        H, W = cam.height, cam.width
+        self.obs_rgb = torch.zeros(H, W, 3, dtype=torch.float32, device=device)
+        self.obs_depth = torch.zeros(H, W, dtype=torch.float32, device=device)
+        self.obs_id = torch.full((H, W), -1, dtype=torch.int32, device=device)
+        self.obs_tfinal = torch.ones(H, W, dtype=torch.float32, device=device)
+        self.g_rgb = torch.zeros(H, W, 3, dtype=torch.float32, device=device)
+        self.g_depth = torch.zeros(H, W, dtype=torch.float32, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        npix = cam.npix
+        self.assoc_cap = npix
+        self.pairs = torch.zeros(npix, 2, dtype=torch.int32, device=device)
+        self.counts = torch.zeros(npix, dtype=torch.int32, device=device)
+        self.m_dev = torch.zeros(1, dtype=torch.int64, device=device)
+        self.assoc_status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.assoc_ws = torch.empty(max(1, B.splat_assoc_workspace_size(npix)), dtype=torch.uint8, device=device)
+        self.cg = B.gaussians_struct(*self.params)
+        self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads))
+        self.steps_done = 0
+        self.t_dev = torch.zeros(1, dtype=torch.int32, device=device)  # Adam step, advanced on the device
+
+    # -- observation ---------------------------------------------------------
+    def set_observation(self, rgb, depth, ids=None, t_final=None, stream=None):
+        """Copy an RGB-D frame (and optionally its id / transmittance images)
+        into the resident observation buffers (stream-ordered)."""
+        s = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(s):
+            self.obs_rgb.copy_(rgb, non_blocking=True)
+            self.obs_depth.copy_(depth, non_blocking=True)
+            if ids is not None:
+                self.obs_id.copy_(ids, non_blocking=True)
+            if t_final is not None:
+                self.obs_tfinal.copy_(t_final, non_blocking=True)
+
+    def render_observation_from(self, w2c_obs, stream=None):
+        """Render the map from `w2c_obs` into the observation buffers (used to
+        make synthetic targets)."""
+        fb = FrameBuffers(self.n, self.cam, self.device, capacity=self.fb.capacity)
+        B.splat_project(self.cg, fb.ccam, torch.as_tensor(w2c_obs, dtype=torch.float32, device=self.device), fb.cproj,
+                        stream)
+        bin_sort(fb, stream)
+        B.splat_render_fwd(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg, stream)
+        self.set_observation(fb.image["rgb"], fb.image["depth"], fb.image["max_id"], fb.image["t_final"], stream)
+        return fb
+
+    # -- the step ------------------------------------------------------------
+    def size_capacity(self, headroom: float = 1.5, stream=None):
+        """Project + count duplicates once (host read) and size the duplicate
+        buffers with headroom, so that later steps need no host read."""
+        project(self.cg, self.w2c, self.fb, stream)
+        k = bin_sort(self.fb, stream, sync_check=True)
+        if k * headroom > self.fb.capacity:
+            self.fb._alloc(int(k * headroom) + 1024)
+        return k
+
+    def forward(self, stream=None, sync_check: bool = False):
+        fb = self.fb
+        project(self.cg, self.w2c, fb, stream)
+        bin_sort(fb, stream, sync_check=sync_check)
+        B.splat_render_fwd(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg, stream)
+
+    def step(self, stream=None, sync_check: bool = False):
+        cfg = self.cfg
+        fb = self.fb
+        s = torch.cuda.current_stream() if stream is None else stream
+        self.forward(s, sync_check)
+        with torch.cuda.stream(s):
+            self.loss.zero_()
+            for g in self.grads:
+                g.zero_()
+            self.d_pose.zero_()
+        B.splat_loss_l1(fb.image["rgb"], fb.image["depth"], self.obs_rgb, self.obs_depth, cfg.w_rgb, cfg.w_depth,
+                        self.g_rgb, self.g_depth, self.loss, s)
+        B.splat_render_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.vals, fb.ranges, fb.cimg, cfg.bg, self.g_rgb,
+                           self.g_depth, None, self.cgr, self.d_pose, None, fb.bwd_ws, s)
+        self.steps_done += 1
+        with torch.cuda.stream(s):
+            self.t_dev.add_(1)
+        t = self.t_dev
+        if cfg.map:
+            for name, p, g, m, v in zip(("mean", "log_scale", "quat", "opacity_logit", "rgb"), self.params, self.grads,
+                                        self.m, self.v):
+                B.splat_adam(p, g, m, v, t, cfg.lr[name], stream=s)
+        if cfg.track:
+            B.splat_pose_step(self.w2c, self.d_pose, self.pose_m, self.pose_v, t, cfg.pose_lr[0], cfg.pose_lr[1],
+                              stream=s)
+        if cfg.assoc:
+            with torch.cuda.stream(s):
+                self.assoc_status.zero_()
+            B.splat_assoc(fb.image["max_id"], fb.image["t_final"], self.obs_id, self.obs_tfinal, self.n, self.n,
+                          cfg.t_max, self.pairs, self.counts, self.assoc_cap, self.m_dev, self.assoc_status,
+                          self.assoc_ws, s)
+
+    def status(self) -> int:
+        """Sticky device status of the last steps (host read)."""
+        return int(self.fb.status.item()) | int(self.assoc_status.item())

@@ -46,12 +46,15 @@ class CProjected(ctypes.Structure):
 
 class CImage(ctypes.Structure):
     _fields_ = [("rgb", _c_p), ("depth", _c_p), ("sil", _c_p), ("t_final", _c_p), ("n_contrib", _c_p),
-                ("max_id", _c_p)]
+                ("max_id", _c_p), ("n_used", _c_p)]
 
 
 _SIGS = {
     "splat_abi_version": ([], _c_i32),
     "splat_last_error": ([], ctypes.c_char_p),
+    "splat_kernel_launches": ([], ctypes.c_uint64),
+    "splat_profile_enable": ([ctypes.c_int], ctypes.c_int),
+    "splat_profile_read": ([_c_p, _c_sz, _c_p, _c_p, _c_i32, _c_p], ctypes.c_int),
     "splat_project": ([_c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_bin_sort_workspace_size": ([_c_i64, _c_i64, _c_i32], _c_sz),
     "splat_bin_sort": ([_c_p, _c_i64, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
@@ -59,8 +62,8 @@ _SIGS = {
     "splat_render_bwd_workspace_size": ([_c_i64], _c_sz),
     "splat_render_bwd": ([_c_p] * 15 + [_c_sz, _c_p], ctypes.c_int),
     "splat_loss_l1": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_f, _c_f, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
-    "splat_adam": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_i32, _c_f, _c_f, _c_f, _c_f, _c_p], ctypes.c_int),
-    "splat_pose_step": ([_c_p, _c_p, _c_p, _c_p, _c_i32, _c_f, _c_f, _c_f, _c_f, _c_f, _c_p], ctypes.c_int),
+    "splat_adam": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_f, _c_f, _c_f, _c_f, _c_p], ctypes.c_int),
+    "splat_pose_step": ([_c_p, _c_p, _c_p, _c_p, _c_p, _c_f, _c_f, _c_f, _c_f, _c_f, _c_p], ctypes.c_int),
     "splat_assoc_workspace_size": ([_c_i64], _c_sz),
     "splat_assoc": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_i64, _c_i64, _c_f, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p,
                      _c_sz, _c_p], ctypes.c_int),
@@ -134,7 +137,7 @@ def projected_struct(proj) -> CProjected:
 
 def image_struct(img) -> CImage:
     return CImage(_p(img["rgb"]), _p(img["depth"]), _p(img["sil"]), _p(img["t_final"]), _p(img["n_contrib"]),
-                  _p(img["max_id"]))
+                  _p(img["max_id"]), _p(img.get("n_used")))
 
 
 # ---------------------------------------------------------------------------
@@ -142,6 +145,25 @@ def image_struct(img) -> CImage:
 # ---------------------------------------------------------------------------
 def splat_abi_version() -> int:
     return int(load().splat_abi_version())
+
+
+def splat_kernel_launches() -> int:
+    return int(load().splat_kernel_launches())
+
+
+def splat_profile_enable(on: bool):
+    _check("splat_profile_enable", load().splat_profile_enable(1 if on else 0))
+
+
+def splat_profile_read(max_kernels: int = 64) -> dict:
+    """{kernel name: (timed launches, total ms)} since the last read."""
+    names = ctypes.create_string_buffer(8192)
+    launches = (ctypes.c_int64 * max_kernels)()
+    ms = (ctypes.c_double * max_kernels)()
+    nk = ctypes.c_int32(0)
+    _check("splat_profile_read", load().splat_profile_read(names, 8192, launches, ms, max_kernels, ctypes.byref(nk)))
+    keys = [k for k in names.value.decode().split("\n") if k]
+    return {k: (int(launches[i]), float(ms[i])) for i, k in enumerate(keys[:max_kernels])}
 
 
 def splat_project(gaussians: CGaussians, cam: CCamera, w2c, proj: CProjected, stream=None):
@@ -187,13 +209,15 @@ def splat_loss_l1(rgb, depth, target_rgb, target_depth, w_rgb, w_depth, d_rgb, d
 
 
 def splat_adam(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
-    _check("splat_adam", load().splat_adam(_p(param), _p(grad), _p(m), _p(v), param.numel(), step, lr, beta1, beta2,
-                                           eps, _stream(stream)))
+    """`step`: device int32[1] tensor holding the Adam step t >= 1."""
+    _check("splat_adam", load().splat_adam(_p(param), _p(grad), _p(m), _p(v), param.numel(), _p(step), lr, beta1,
+                                           beta2, eps, _stream(stream)))
 
 
 def splat_pose_step(w2c, d_pose, m, v, step, lr_t, lr_r, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
-    _check("splat_pose_step", load().splat_pose_step(_p(w2c), _p(d_pose), _p(m), _p(v), step, lr_t, lr_r, beta1,
-                                                     beta2, eps, _stream(stream)))
+    """`step`: device int32[1] tensor holding the Adam step t >= 1."""
+    _check("splat_pose_step", load().splat_pose_step(_p(w2c), _p(d_pose), _p(m), _p(v), _p(step), lr_t, lr_r,
+                                                     beta1, beta2, eps, _stream(stream)))
 
 
 def splat_assoc_workspace_size(npix) -> int:

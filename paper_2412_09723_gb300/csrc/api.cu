@@ -73,9 +73,16 @@ __global__ void __launch_bounds__(256) loss_l1_kernel(const float* __restrict__ 
 // ----------------------------------------------------------------------------
 // Adam
 // ----------------------------------------------------------------------------
+// 1 - beta^t in float, from a device-resident step count.
+__device__ __forceinline__ float bias_correction(float beta, const int32_t* step) {
+  return 1.0f - powf(beta, (float)(*step));
+}
+
 __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, const float* __restrict__ g,
                                                    float* __restrict__ m, float* __restrict__ v, int64_t n, float lr,
-                                                   float b1, float b2, float bc1, float bc2, float eps) {
+                                                   float b1, float b2, const int32_t* __restrict__ step, float eps) {
+  const float bc1 = bias_correction(b1, step);
+  const float bc2 = bias_correction(b2, step);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.0f - b1) * gi;
@@ -90,9 +97,11 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, const 
 
 // Adam on the 6-vector pose gradient, then w2c <- exp(delta^) w2c.
 __global__ void pose_step_kernel(float* __restrict__ w2c, const float* __restrict__ g, float* __restrict__ m,
-                                 float* __restrict__ v, float lr_t, float lr_r, float b1, float b2, float bc1,
-                                 float bc2, float eps) {
+                                 float* __restrict__ v, float lr_t, float lr_r, float b1, float b2,
+                                 const int32_t* __restrict__ step, float eps) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const float bc1 = bias_correction(b1, step);
+  const float bc2 = bias_correction(b2, step);
   float d[6];
   for (int k = 0; k < 6; ++k) {
     const float mi = b1 * m[k] + (1.0f - b1) * g[k];
@@ -266,30 +275,26 @@ extern "C" int splat_loss_l1(const float* rgb, const float* depth, const float* 
   const float sc = w_rgb / (float)(3 * npix);
   const float sd = w_depth / (float)npix;
   const int blocks = (int)std::min<int64_t>((npix + 255) / 256, 152 * 8);
-  loss_l1_kernel<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(rgb, depth, target_rgb, target_depth,
-                                                                              npix, sc, sd, d_rgb, d_depth, loss);
+  SPLAT_LAUNCH("loss_l1_kernel", reinterpret_cast<cudaStream_t>(stream), loss_l1_kernel<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(rgb, depth, target_rgb, target_depth,
+                                                                              npix, sc, sd, d_rgb, d_depth, loss));
   return check_launch("loss_l1_kernel");
 }
 
-extern "C" int splat_adam(float* param, const float* grad, float* m, float* v, int64_t n, int32_t step, float lr,
-                          float beta1, float beta2, float eps, splat_stream_t stream) {
-  if (!param || !grad || !m || !v || n < 0 || step < 1) return fail(SPLAT_EINVAL, "splat_adam: bad argument");
+extern "C" int splat_adam(float* param, const float* grad, float* m, float* v, int64_t n, const int32_t* step,
+                          float lr, float beta1, float beta2, float eps, splat_stream_t stream) {
+  if (!param || !grad || !m || !v || !step || n < 0) return fail(SPLAT_EINVAL, "splat_adam: bad argument");
   if (n == 0) return SPLAT_OK;
-  const float bc1 = 1.0f - powf(beta1, (float)step);
-  const float bc2 = 1.0f - powf(beta2, (float)step);
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-  adam_kernel<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(param, grad, m, v, n, lr, beta1, beta2, bc1,
-                                                                           bc2, eps);
+  SPLAT_LAUNCH("adam_kernel", reinterpret_cast<cudaStream_t>(stream), adam_kernel<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(param, grad, m, v, n, lr, beta1, beta2, step,
+                                                                           eps));
   return check_launch("adam_kernel");
 }
 
-extern "C" int splat_pose_step(float* w2c, const float* d_pose, float* m, float* v, int32_t step, float lr_t,
+extern "C" int splat_pose_step(float* w2c, const float* d_pose, float* m, float* v, const int32_t* step, float lr_t,
                                float lr_r, float beta1, float beta2, float eps, splat_stream_t stream) {
-  if (!w2c || !d_pose || !m || !v || step < 1) return fail(SPLAT_EINVAL, "splat_pose_step: bad argument");
-  const float bc1 = 1.0f - powf(beta1, (float)step);
-  const float bc2 = 1.0f - powf(beta2, (float)step);
-  pose_step_kernel<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(w2c, d_pose, m, v, lr_t, lr_r, beta1, beta2,
-                                                                          bc1, bc2, eps);
+  if (!w2c || !d_pose || !m || !v || !step) return fail(SPLAT_EINVAL, "splat_pose_step: bad argument");
+  SPLAT_LAUNCH("pose_step_kernel", reinterpret_cast<cudaStream_t>(stream), pose_step_kernel<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(w2c, d_pose, m, v, lr_t, lr_r, beta1, beta2,
+                                                                          step, eps));
   return check_launch("pose_step_kernel");
 }
 
@@ -312,27 +317,27 @@ extern "C" int splat_assoc(const int32_t* id_a, const float* t_a, const int32_t*
   carve_assoc(npix, static_cast<char*>(ws), &w);
   const int ba = bits_for(n_a), bb = bits_for(n_b);
   const int nb = ceil_div(npix, 256);
-  assoc_flag_kernel<<<nb, 256, 0, s>>>(id_a, t_a, id_b, t_b, npix, t_max, w.flag);
+  SPLAT_LAUNCH("assoc_flag_kernel", s, assoc_flag_kernel<<<nb, 256, 0, s>>>(id_a, t_a, id_b, t_b, npix, t_max, w.flag));
   int rc = exclusive_scan_u32(w.flag, w.pos, npix, w.scan, s);
   if (rc) return rc;
-  assoc_compact_kernel<<<nb, 256, 0, s>>>(id_a, id_b, w.flag, w.pos, npix, bb, w.k0, w.count);
+  SPLAT_LAUNCH("assoc_compact_kernel", s, assoc_compact_kernel<<<nb, 256, 0, s>>>(id_a, id_b, w.flag, w.pos, npix, bb, w.k0, w.count));
   if ((rc = check_launch("assoc_compact_kernel"))) return rc;
   int which = 0;
   if ((rc = radix_sort<uint64_t>(w.k0, nullptr, w.k1, nullptr, npix, w.count, 0, ba + bb, w.radix, s, &which)))
     return rc;
   const uint64_t* keys = which ? w.k1 : w.k0;
-  assoc_head_kernel<<<nb, 256, 0, s>>>(keys, w.count, npix, w.head);
+  SPLAT_LAUNCH("assoc_head_kernel", s, assoc_head_kernel<<<nb, 256, 0, s>>>(keys, w.count, npix, w.head));
   if ((rc = exclusive_scan_u32(w.head, w.uidx, npix, w.scan, s))) return rc;
-  assoc_starts_kernel<<<nb, 256, 0, s>>>(w.head, w.uidx, w.count, npix, capacity, w.starts, m_dev, status);
+  SPLAT_LAUNCH("assoc_starts_kernel", s, assoc_starts_kernel<<<nb, 256, 0, s>>>(w.head, w.uidx, w.count, npix, capacity, w.starts, m_dev, status));
   if ((rc = check_launch("assoc_starts_kernel"))) return rc;
   if (capacity == 0) return SPLAT_OK;
-  assoc_write_kernel<<<nb, 256, 0, s>>>(keys, w.starts, m_dev, capacity, bb, pairs, counts);
+  SPLAT_LAUNCH("assoc_write_kernel", s, assoc_write_kernel<<<nb, 256, 0, s>>>(keys, w.starts, m_dev, capacity, bb, pairs, counts));
   return check_launch("assoc_write_kernel");
 }
 
 extern "C" int splat_exp_f32(const float* x, float* y, int64_t n, splat_stream_t stream) {
   if (!x || !y || n < 0) return fail(SPLAT_EINVAL, "splat_exp_f32: bad argument");
   if (n == 0) return SPLAT_OK;
-  exp_kernel<<<ceil_div(n, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, y, n);
+  SPLAT_LAUNCH("exp_kernel", reinterpret_cast<cudaStream_t>(stream), exp_kernel<<<ceil_div(n, 256), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(x, y, n));
   return check_launch("exp_kernel");
 }

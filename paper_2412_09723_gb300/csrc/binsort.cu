@@ -130,9 +130,9 @@ int exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* ws, c
   if (n <= 0) return SPLAT_OK;
   const int64_t nparts = (n + kScanTile - 1) / kScanTile;
   uint32_t* partials = static_cast<uint32_t*>(ws);
-  scan_reduce_kernel<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, partials);
-  scan_partials_kernel<<<1, 1024, 0, s>>>(partials, nparts);
-  scan_down_kernel<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, out, n, partials);
+  SPLAT_LAUNCH("scan_reduce_kernel", s, scan_reduce_kernel<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, partials));
+  SPLAT_LAUNCH("scan_partials_kernel", s, scan_partials_kernel<<<1, 1024, 0, s>>>(partials, nparts));
+  SPLAT_LAUNCH("scan_down_kernel", s, scan_down_kernel<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, out, n, partials));
   return check_launch("exclusive_scan_u32");
 }
 
@@ -264,11 +264,11 @@ int radix_sort(Key* keys0, uint32_t* vals0, Key* keys1, uint32_t* vals1, int64_t
   for (int p = 0; p < passes; ++p) {
     const int nbits = std::min(bits_per, end_bit - shift);
     const int64_t used = (int64_t)(1 << nbits) * nb;
-    radix_hist_kernel<Key><<<(unsigned)nb, kRadixThreads, 0, s>>>(kin, capacity, count_dev, shift, nbits, counts, nb);
+    SPLAT_LAUNCH("radix_hist_kernel", s, radix_hist_kernel<Key><<<(unsigned)nb, kRadixThreads, 0, s>>>(kin, capacity, count_dev, shift, nbits, counts, nb));
     int rc = exclusive_scan_u32(counts, offsets, used, scan_ws, s);
     if (rc) return rc;
-    radix_scatter_kernel<Key><<<(unsigned)nb, kRadixThreads, 0, s>>>(kin, vin, kout, vout, capacity, count_dev, shift,
-                                                                     nbits, offsets, nb);
+    SPLAT_LAUNCH("radix_scatter_kernel", s, radix_scatter_kernel<Key><<<(unsigned)nb, kRadixThreads, 0, s>>>(kin, vin, kout, vout, capacity, count_dev, shift,
+                                                                     nbits, offsets, nb));
     rc = check_launch("radix_scatter_kernel");
     if (rc) return rc;
     std::swap(kin, kout);
@@ -432,35 +432,35 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
   const float4* xyzo = reinterpret_cast<const float4*>(proj->xyzo);
   const int nb = std::max(1, ceil_div(n, 256));
   // 1. depth keys of the visible Gaussians (culled ones sort last), K total
-  if (n > 0) depth_keys_kernel<<<nb, 256, 0, s>>>(xyzo, proj->tiles_touched, n, w.dk0, w.dv0, w.k_total);
+  if (n > 0) SPLAT_LAUNCH("depth_keys_kernel", s, depth_keys_kernel<<<nb, 256, 0, s>>>(xyzo, proj->tiles_touched, n, w.dk0, w.dv0, w.k_total));
   int rc = check_launch("depth_keys_kernel");
   if (rc) return rc;
-  finalize_count_kernel<<<1, 1, 0, s>>>(w.k_total, capacity, k_dev, w.cnt_dev, status);
+  SPLAT_LAUNCH("finalize_count_kernel", s, finalize_count_kernel<<<1, 1, 0, s>>>(w.k_total, capacity, k_dev, w.cnt_dev, status));
   if ((rc = check_launch("finalize_count_kernel"))) return rc;
   if (n == 0) return SPLAT_OK;
   int which = 0;
   if ((rc = radix_sort<uint32_t>(w.dk0, w.dv0, w.dk1, w.dv1, n, nullptr, 0, 32, w.radix, s, &which))) return rc;
   const uint32_t* order = which ? w.dv1 : w.dv0;
   // 2. duplicate offsets in depth order, emission
-  gather_counts_kernel<<<nb, 256, 0, s>>>(order, proj->tiles_touched, n, w.cnt);
+  SPLAT_LAUNCH("gather_counts_kernel", s, gather_counts_kernel<<<nb, 256, 0, s>>>(order, proj->tiles_touched, n, w.cnt));
   if ((rc = exclusive_scan_u32(w.cnt, w.offs, n, w.scan, s))) return rc;
   if (capacity == 0) return SPLAT_OK;
   const int tb = tile_bits(n_tiles);
   const int passes = radix_passes(0, tb);
   uint32_t* v0 = (passes & 1) ? w.valt : vals;
   uint32_t* v1 = (passes & 1) ? vals : w.valt;
-  emit_kernel<<<nb, 256, 0, s>>>(order, w.cnt, w.offs, reinterpret_cast<const int4*>(proj->rect), n, ck.tiles_x,
-                                 capacity, w.tk0, v0);
+  SPLAT_LAUNCH("emit_kernel", s, emit_kernel<<<nb, 256, 0, s>>>(order, w.cnt, w.offs, reinterpret_cast<const int4*>(proj->rect), n, ck.tiles_x,
+                                 capacity, w.tk0, v0));
   if ((rc = check_launch("emit_kernel"))) return rc;
   // 3. stable sort by tile id
   if ((rc = radix_sort<uint32_t>(w.tk0, v0, w.tk1, v1, capacity, w.cnt_dev, 0, tb, w.radix, s, &which))) return rc;
   const uint32_t* tk = which ? w.tk1 : w.tk0;
   // 4. ranges, optional full keys
   const int kb = std::max(1, ceil_div(capacity, 256));
-  ranges_kernel<<<kb, 256, 0, s>>>(tk, w.cnt_dev, capacity, ranges);
+  SPLAT_LAUNCH("ranges_kernel", s, ranges_kernel<<<kb, 256, 0, s>>>(tk, w.cnt_dev, capacity, ranges));
   if ((rc = check_launch("ranges_kernel"))) return rc;
   if (keys) {
-    full_keys_kernel<<<kb, 256, 0, s>>>(tk, vals, xyzo, w.cnt_dev, capacity, keys);
+    SPLAT_LAUNCH("full_keys_kernel", s, full_keys_kernel<<<kb, 256, 0, s>>>(tk, vals, xyzo, w.cnt_dev, capacity, keys));
     if ((rc = check_launch("full_keys_kernel"))) return rc;
   }
   return SPLAT_OK;

@@ -67,6 +67,27 @@ __device__ __forceinline__ void raise_status(int32_t* status, int32_t code) {
 void set_error(const char* fmt, ...);
 int fail(int code, const char* fmt, ...);
 int check_launch(const char* what);
+// Launch accounting: construct a LaunchScope right before a kernel launch and
+// let it end right after; it counts the launch and, while per-kernel timing is
+// enabled, brackets it with CUDA events on `s`.
+void count_launch(int n = 1);
+class LaunchScope {
+ public:
+  LaunchScope(const char* name, cudaStream_t s);
+  ~LaunchScope();
+  LaunchScope(const LaunchScope&) = delete;
+  LaunchScope& operator=(const LaunchScope&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t a_;
+};
+#define SPLAT_LAUNCH(name, stream, ...)         \
+  do {                                          \
+    ::splat::LaunchScope splat_scope_(name, stream); \
+    __VA_ARGS__;                                \
+  } while (0)
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }

@@ -310,14 +310,14 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(GaussiansK g, CamK cam
 int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, const ProjectedK& out,
                        cudaStream_t s) {
   if (g.n == 0) return SPLAT_OK;
-  project_fwd_kernel<<<ceil_div(g.n, 256), 256, 0, s>>>(g, cam, w2c, out);
+  SPLAT_LAUNCH("project_fwd_kernel", s, project_fwd_kernel<<<ceil_div(g.n, 256), 256, 0, s>>>(g, cam, w2c, out));
   return check_launch("project_fwd_kernel");
 }
 
 int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
                        const float* d2d, const GradK& out, float* d_pose, cudaStream_t s) {
   if (g.n == 0) return SPLAT_OK;
-  project_bwd_kernel<<<ceil_div(g.n, 256), 256, 0, s>>>(g, cam, w2c, conic, d2d, out, d_pose);
+  SPLAT_LAUNCH("project_bwd_kernel", s, project_bwd_kernel<<<ceil_div(g.n, 256), 256, 0, s>>>(g, cam, w2c, conic, d2d, out, d_pose));
   return check_launch("project_bwd_kernel");
 }
 

@@ -36,6 +36,7 @@ struct ImageK {
   float* t_final;
   int32_t* n_contrib;
   int32_t* max_id;
+  int32_t* n_used;
 };
 
 __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(const float4* __restrict__ xyzo,
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(const float4* _
   const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
   const uint2 rg = ranges[tile];
   float T = 1.0f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, S = 0.f, wmax = 0.f;
-  int32_t id = -1, last = 0;
+  int32_t id = -1, last = 0, used = 0;
   bool done = !inside;
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
     if (__syncthreads_count(done) == kTilePixels) break;
@@ -103,6 +104,7 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(const float4* _
         }
         T = test_T;
         last = (int32_t)(start - rg.x) + j + 1;
+        ++used;
       }
     }
   }
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(const float4* _
   out.t_final[p] = T;
   out.n_contrib[p] = last;
   out.max_id[p] = id;
+  if (out.n_used) out.n_used[p] = used;
 }
 
 __device__ __forceinline__ float warp_sum(float x) {
@@ -265,11 +268,11 @@ extern "C" int splat_render_fwd(const splat_projected* proj, const float* rgb, i
     return fail(SPLAT_EINVAL, "splat_render_fwd: null argument");
   if (n < 0 || cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "splat_render_fwd: bad sizes");
   const CamK ck = make_camk(*cam);
-  ImageK im{out->rgb, out->depth, out->sil, out->t_final, out->n_contrib, out->max_id};
+  ImageK im{out->rgb, out->depth, out->sil, out->t_final, out->n_contrib, out->max_id, out->n_used};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  render_fwd_kernel<<<ck.tiles_x * ck.tiles_y, kTilePixels, 0, s>>>(
+  SPLAT_LAUNCH("render_fwd_kernel", s, render_fwd_kernel<<<ck.tiles_x * ck.tiles_y, kTilePixels, 0, s>>>(
       reinterpret_cast<const float4*>(proj->xyzo), reinterpret_cast<const float4*>(proj->conic), rgb, vals,
-      reinterpret_cast<const uint2*>(ranges), ck, bg[0], bg[1], bg[2], im);
+      reinterpret_cast<const uint2*>(ranges), ck, bg[0], bg[1], bg[2], im));
   return check_launch("render_fwd_kernel");
 }
 
@@ -301,10 +304,10 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
   if (g->n > 0 && cudaMemsetAsync(grad2d, 0, sizeof(float) * 10 * (size_t)g->n, s) != cudaSuccess)
     return fail(SPLAT_ECUDA, "splat_render_bwd: memset failed");
   const CamK ck = make_camk(*cam);
-  render_bwd_kernel<<<ck.tiles_x * ck.tiles_y, kTilePixels, 0, s>>>(
+  SPLAT_LAUNCH("render_bwd_kernel", s, render_bwd_kernel<<<ck.tiles_x * ck.tiles_y, kTilePixels, 0, s>>>(
       reinterpret_cast<const float4*>(proj->xyzo), reinterpret_cast<const float4*>(proj->conic), g->rgb, vals,
       reinterpret_cast<const uint2*>(ranges), ck, bg[0], bg[1], bg[2], fwd->t_final, fwd->n_contrib, d_rgb, d_depth,
-      d_sil, grad2d);
+      d_sil, grad2d));
   if ((rc = check_launch("render_bwd_kernel"))) return rc;
   GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
   GradK gr{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};

@@ -27,7 +27,8 @@ def _f32(x, device):
 class FrameBuffers:
     """Device buffers of one view: projection, sorted lists, image, workspaces."""
 
-    def __init__(self, n: int, cam: Camera, device, capacity: int | None = None, want_keys: bool = False):
+    def __init__(self, n: int, cam: Camera, device, capacity: int | None = None, want_keys: bool = False,
+                 want_used: bool = False):
         self.n, self.cam, self.device = n, cam, device
         H, W = cam.height, cam.width
         f, i = dict(dtype=torch.float32, device=device), dict(dtype=torch.int32, device=device)
@@ -36,6 +37,8 @@ class FrameBuffers:
         self.image = dict(rgb=torch.zeros(H, W, 3, **f), depth=torch.zeros(H, W, **f), sil=torch.zeros(H, W, **f),
                           t_final=torch.zeros(H, W, **f), n_contrib=torch.zeros(H, W, **i),
                           max_id=torch.zeros(H, W, **i))
+        if want_used:
+            self.image["n_used"] = torch.zeros(H, W, **i)
         self.ranges = torch.zeros(cam.n_tiles, 2, dtype=torch.int32, device=device)
         self.k_dev = torch.zeros(1, dtype=torch.int64, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
@@ -65,8 +68,11 @@ def project(g: B.CGaussians, w2c, fb: FrameBuffers, stream=None):
 
 
 def bin_sort(fb: FrameBuffers, stream=None, sync_check: bool = True):
-    """Bin and sort; when `sync_check`, read K back and retry on overflow."""
-    fb.status.zero_()
+    """Bin and sort.  With `sync_check`, clear the status, read K back and
+    retry on overflow; without it the call stays asynchronous and the sticky
+    status word reports an overflow later."""
+    if sync_check:
+        fb.status.zero_()
     B.splat_bin_sort(fb.cproj, fb.n, fb.ccam, fb.keys, fb.vals, fb.capacity, fb.k_dev, fb.ranges, fb.status,
                      fb.bin_ws, stream)
     if sync_check:

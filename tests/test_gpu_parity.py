@@ -270,7 +270,7 @@ def test_adam(dev):
     p, g, m, v = (rng.normal(size=n).astype(np.float32) for _ in range(4))
     v = np.abs(v)
     tp, tg, tm, tv = (torch.as_tensor(x.copy(), device=dev) for x in (p, g, m, v))
-    B.splat_adam(tp, tg, tm, tv, 3, 1e-3)
+    B.splat_adam(tp, tg, tm, tv, torch.tensor([3], dtype=torch.int32, device=dev), 1e-3)
     rp, rm, rv = oracle.adam(p, g, m, v, 3, 1e-3)
     np.testing.assert_allclose(tp.cpu().numpy(), rp, rtol=1e-6, atol=1e-7)
     np.testing.assert_allclose(tm.cpu().numpy(), rm, rtol=1e-6, atol=1e-7)
@@ -285,7 +285,7 @@ def test_pose_step_matches_host_retraction(dev):
     w = _w(w0, dev)
     g = torch.tensor([0.3, -0.2, 0.1, 0.05, -0.4, 0.2], device=dev)
     m, v = torch.zeros(6, device=dev), torch.zeros(6, device=dev)
-    B.splat_pose_step(w, g, m, v, 1, 0.01, 0.002)
+    B.splat_pose_step(w, g, m, v, torch.tensor([1], dtype=torch.int32, device=dev), 0.01, 0.002)
     # first Adam step = -lr sign(g)
     d = -np.sign(g.cpu().numpy()) * np.array([0.01] * 3 + [0.002] * 3)
     ref = se3_exp(torch.tensor(d)).numpy() @ w0.astype(np.float64)

@@ -309,3 +309,21 @@ def test_assoc_self_is_diagonal(orc):
     vis = (out["max_id"] >= 0) & (out["t_final"] <= 0.5)
     assert counts.sum() == vis.sum()
     assert set(pairs[:, 0]) == set(np.unique(out["max_id"][vis]))
+
+
+def test_row_band_equals_full_frame_rows(orc):
+    """Rendering / differentiating only a band of rows gives exactly the rows
+    of the full-frame result (the band is a restriction, not a new computation)."""
+    sc, w2c, cam, bg = scenes.workload_small_forward(seed=5)
+    full = orc.render_fwd(sc, w2c, cam, bg)
+    band = orc.render_fwd(sc, w2c, cam, bg, rows=(32, 64))
+    for k in ("rgb", "depth", "sil", "t_final", "n_contrib", "max_id"):
+        assert np.array_equal(band[k][32:64], full[k][32:64])
+    rng = np.random.default_rng(0)
+    g = rng.normal(size=(cam.height, cam.width, 3)).astype(np.float32)
+    g[:32] = 0
+    g[64:] = 0
+    a = orc.render_bwd(sc, w2c, cam, bg, g)
+    b = orc.render_bwd(sc, w2c, cam, bg, g, rows=(32, 64))
+    for k in ("mean", "opacity_logit", "rgb", "pose"):
+        np.testing.assert_allclose(a[k], b[k], rtol=1e-5, atol=1e-7)
