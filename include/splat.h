@@ -184,6 +184,30 @@ int splat_bin_sort(const splat_projected *proj, int64_t n, const splat_camera *c
                    splat_stream_t stream);
 
 /*
+ * splat_bin_sort_static -- splat_bin_sort without a caller workspace.  (The
+ * paper has no counterpart: this is a convenience of this library.)
+ * For callers that cannot allocate device memory when they render -- a
+ * real-time loop that reserved its memory once at start-up and must not enter
+ * an allocator afterwards, or a host framework that owns the allocator and
+ * cannot lend scratch space to the code issuing the render.  The scratch comes
+ * from one device array of splat_bin_sort_static_scratch_bytes() bytes
+ * (64 MiB) that is part of this library's module: every GPU that loads the
+ * library holds it until the process exits.  The call allocates nothing.
+ *   Arguments, results and errors as splat_bin_sort (minus ws / ws_bytes).
+ *   Sizes whose scratch need exceeds the array (about 27 MiB for n = 300k
+ *   and capacity = 1.6M) are rejected with SPLAT_EINVAL and a message.
+ *   The first call on a device looks up the array's device address (with
+ *   that device current): make that first call before any stream capture.
+ *   All calls share the one array and leave their data in it; calls that
+ *   may overlap on the GPU (several streams or threads) race and must be
+ *   serialised by the caller.
+ */
+size_t splat_bin_sort_static_scratch_bytes(void);
+int splat_bin_sort_static(const splat_projected *proj, int64_t n, const splat_camera *cam,
+                          uint64_t *keys, uint32_t *vals, int64_t capacity, int64_t *k_dev,
+                          uint32_t *ranges, int32_t *status, splat_stream_t stream);
+
+/*
  * splat_render_fwd -- per-pixel front-to-back alpha compositing of colour,
  * depth and silhouette over the pixel's tile list (rendering equation of
  * Sec. 3.3; rendered depth of Sec. 3.5), recording the final transmittance

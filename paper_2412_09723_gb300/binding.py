@@ -58,6 +58,8 @@ _SIGS = {
     "splat_project": ([_c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_bin_sort_workspace_size": ([_c_i64, _c_i64, _c_i32], _c_sz),
     "splat_bin_sort": ([_c_p, _c_i64, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
+    "splat_bin_sort_static_scratch_bytes": ([], _c_sz),
+    "splat_bin_sort_static": ([_c_p, _c_i64, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_render_fwd": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_render_bwd_workspace_size": ([_c_i64], _c_sz),
     "splat_render_bwd": ([_c_p] * 15 + [_c_sz, _c_p], ctypes.c_int),
@@ -179,6 +181,18 @@ def splat_bin_sort(proj: CProjected, n, cam: CCamera, keys, vals, capacity, k_de
     _check("splat_bin_sort", load().splat_bin_sort(
         ctypes.byref(proj), n, ctypes.byref(cam), _p(keys), _p(vals), capacity, _p(k_dev), _p(ranges), _p(status),
         _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def splat_bin_sort_static_scratch_bytes() -> int:
+    return int(load().splat_bin_sort_static_scratch_bytes())
+
+
+def splat_bin_sort_static(proj: CProjected, n, cam: CCamera, keys, vals, capacity, k_dev, ranges, status,
+                          stream=None):
+    """splat_bin_sort with the library's static scratch array instead of a workspace."""
+    _check("splat_bin_sort_static", load().splat_bin_sort_static(
+        ctypes.byref(proj), n, ctypes.byref(cam), _p(keys), _p(vals), capacity, _p(k_dev), _p(ranges), _p(status),
+        _stream(stream)))
 
 
 def splat_render_fwd(proj: CProjected, rgb, n, vals, ranges, cam: CCamera, bg, image: CImage, stream=None):
