@@ -235,8 +235,8 @@ int splat_render_fwd(const splat_projected *proj, const float *rgb, int64_t n,
  *     of the left perturbation w2c <- exp(delta^) w2c.
  *   d2d: device float[n,10] or NULL: receives the screen-space gradients
  *     (du, dv, d conic a, b, c, d opacity, d rgb[3], d depth) (overwritten).
- *   ws: workspace of splat_render_bwd_workspace_size(n) bytes (used for the
- *     screen-space gradients when d2d is NULL).
+ *   ws: workspace of splat_render_bwd_workspace_size(n) bytes, 16-byte
+ *     aligned (always required: the screen-space gradients accumulate there).
  * Atomics make the summation order, and so the last bits, vary between runs.
  * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
  */

@@ -48,7 +48,10 @@ inline CamK make_camk(const splat_camera& c) {
 
 int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, const ProjectedK& out,
                        cudaStream_t s);
+// g2: screen-space gradients, rows of `stride` floats (du, dv, d conic a, b, c,
+// d opacity, d rgb[3], d depth, padding); d2d_out (optional): copy [n,10].
 int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
-                       const float* d2d, const GradK& out, float* d_pose, cudaStream_t s);
+                       const float* g2, int stride, const GradK& out, float* d_pose, float* d2d_out,
+                       cudaStream_t s);
 
 }  // namespace splat

@@ -161,10 +161,14 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(GaussiansK g, CamK cam
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) project_bwd_kernel(GaussiansK g, CamK cam, const float* __restrict__ w2c,
                                                           const float* __restrict__ conic,
-                                                          const float* __restrict__ d2d, GradK out,
-                                                          float* __restrict__ d_pose) {
+                                                          const float* __restrict__ g2, int stride, GradK out,
+                                                          float* __restrict__ d_pose, float* __restrict__ d2d_out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (i < g.n && d2d_out) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) d2d_out[10 * i + k] = g2[(size_t)stride * i + k];
+  }
   if (i < g.n) {
     float W[12];
 #pragma unroll
@@ -172,7 +176,7 @@ __global__ void __launch_bounds__(256) project_bwd_kernel(GaussiansK g, CamK cam
     ProjMath m;
     project_math(g.mean + 3 * i, g.log_scale + 3 * i, g.quat + 4 * i, g.opacity_logit[i], W, cam, m);
     if (m.visible) {
-      const float* d = d2d + 10 * i;
+      const float* d = g2 + (size_t)stride * i;
       const float du = d[0], dv = d[1], dqa = d[2], dqb = d[3], dqc = d[4], dlam = d[5], dz = d[9];
       out.rgb[3 * i + 0] += d[6];
       out.rgb[3 * i + 1] += d[7];
@@ -315,9 +319,11 @@ int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, c
 }
 
 int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
-                       const float* d2d, const GradK& out, float* d_pose, cudaStream_t s) {
+                       const float* g2, int stride, const GradK& out, float* d_pose, float* d2d_out,
+                       cudaStream_t s) {
   if (g.n == 0) return SPLAT_OK;
-  SPLAT_LAUNCH("project_bwd_kernel", s, project_bwd_kernel<<<ceil_div(g.n, 256), 256, 0, s>>>(g, cam, w2c, conic, d2d, out, d_pose));
+  SPLAT_LAUNCH("project_bwd_kernel", s, project_bwd_kernel<<<ceil_div(g.n, 256), 256, 0, s>>>(g, cam, w2c, conic, g2, stride, out, d_pose,
+                                                                                    d2d_out));
   return check_launch("project_bwd_kernel");
 }
 

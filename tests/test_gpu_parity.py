@@ -144,7 +144,7 @@ def _bwd_gpu(p, fb, w2c, cam, bg, g, dev):
     d2d = torch.zeros(sc_n(p), 10, dtype=torch.float32, device=dev)
     gr, gd, gs = (torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev) for a in g)
     B.splat_render_bwd(B.gaussians_struct(*p), fb.cproj, fb.ccam, _w(w2c, dev), fb.vals, fb.ranges, fb.cimg, bg,
-                       gr, gd, gs, B.CGaussiansGrad(*(B._p(t) for t in grads)), d_pose, d2d, None)
+                       gr, gd, gs, B.CGaussiansGrad(*(B._p(t) for t in grads)), d_pose, d2d, fb.bwd_ws)
     torch.cuda.synchronize()
     return [t.cpu().numpy() for t in grads], d_pose.cpu().numpy(), d2d.cpu().numpy()
 
