@@ -194,8 +194,8 @@ int splat_bin_sort(const splat_projected *proj, int64_t n, const splat_camera *c
  * (64 MiB) that is part of this library's module: every GPU that loads the
  * library holds it until the process exits.  The call allocates nothing.
  *   Arguments, results and errors as splat_bin_sort (minus ws / ws_bytes).
- *   Sizes whose scratch need exceeds the array (about 27 MiB for n = 300k
- *   and capacity = 1.6M) are rejected with SPLAT_EINVAL and a message.
+ *   Sizes whose scratch need exceeds the array (about 25 MiB for capacity =
+ *   1.6M duplicate slots) are rejected with SPLAT_EINVAL and a message.
  *   The first call on a device looks up the array's device address (with
  *   that device current): make that first call before any stream capture.
  *   All calls share the one array and leave their data in it; calls that
@@ -269,6 +269,19 @@ int splat_loss_l1(const float *rgb, const float *depth, const float *target_rgb,
  */
 int splat_adam(float *param, const float *grad, float *m, float *v, int64_t n, const int32_t *step,
                float lr, float beta1, float beta2, float eps, splat_stream_t stream);
+
+/*
+ * splat_adam_groups -- splat_adam over up to 8 parameter groups in one launch
+ * (e.g. mean, log_scale, quat, opacity_logit, rgb of a map), each with its
+ * own learning rate, sharing one device step count.  params[g], grads[g],
+ * m[g], v[g] are device arrays of sizes[g] floats (host arrays of pointers);
+ * lr: host float[n_groups].  With zero_grad != 0 every gradient element is set
+ * to 0 after it is consumed, so the next backward can accumulate into it.
+ * Errors: SPLAT_EINVAL (n_groups not in 1..8, null pointer), SPLAT_ECUDA.
+ */
+int splat_adam_groups(int32_t n_groups, float *const *params, float *const *grads, float *const *m,
+                      float *const *v, const int64_t *sizes, const float *lr, const int32_t *step,
+                      float beta1, float beta2, float eps, int32_t zero_grad, splat_stream_t stream);
 
 /*
  * splat_pose_step -- Adam on the 6-vector pose gradient followed by the

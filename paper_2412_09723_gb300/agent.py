@@ -81,6 +81,8 @@ class Agent:
         self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads))
         self.steps_done = 0
         self.t_dev = torch.zeros(1, dtype=torch.int32, device=device)  # Adam step, advanced on the device
+        names = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
+        self.adam = B.AdamGroups(self.params, self.grads, self.m, self.v, [self.cfg.lr[k] for k in names])
 
     # -- observation ---------------------------------------------------------
     def set_observation(self, rgb, depth, ids=None, t_final=None, stream=None):
@@ -129,9 +131,10 @@ class Agent:
         self.forward(s, sync_check)
         with torch.cuda.stream(s):
             self.loss.zero_()
-            for g in self.grads:
-                g.zero_()
             self.d_pose.zero_()
+            if not cfg.map:  # the fused Adam step clears the gradients when mapping
+                for g in self.grads:
+                    g.zero_()
         B.splat_loss_l1(fb.image["rgb"], fb.image["depth"], self.obs_rgb, self.obs_depth, cfg.w_rgb, cfg.w_depth,
                         self.g_rgb, self.g_depth, self.loss, s)
         B.splat_render_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.vals, fb.ranges, fb.cimg, cfg.bg, self.g_rgb,
@@ -141,9 +144,7 @@ class Agent:
             self.t_dev.add_(1)
         t = self.t_dev
         if cfg.map:
-            for name, p, g, m, v in zip(("mean", "log_scale", "quat", "opacity_logit", "rgb"), self.params, self.grads,
-                                        self.m, self.v):
-                B.splat_adam(p, g, m, v, t, cfg.lr[name], stream=s)
+            B.splat_adam_groups(self.adam, t, zero_grad=True, stream=s)
         if cfg.track:
             B.splat_pose_step(self.w2c, self.d_pose, self.pose_m, self.pose_v, t, cfg.pose_lr[0], cfg.pose_lr[1],
                               stream=s)

@@ -65,6 +65,8 @@ _SIGS = {
     "splat_render_bwd": ([_c_p] * 15 + [_c_sz, _c_p], ctypes.c_int),
     "splat_loss_l1": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_f, _c_f, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_adam": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_f, _c_f, _c_f, _c_f, _c_p], ctypes.c_int),
+    "splat_adam_groups": ([_c_i32, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_f, _c_f, _c_f, _c_i32, _c_p],
+                          ctypes.c_int),
     "splat_pose_step": ([_c_p, _c_p, _c_p, _c_p, _c_p, _c_f, _c_f, _c_f, _c_f, _c_f, _c_p], ctypes.c_int),
     "splat_assoc_workspace_size": ([_c_i64], _c_sz),
     "splat_assoc": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_i64, _c_i64, _c_f, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p,
@@ -226,6 +228,28 @@ def splat_adam(param, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-15, s
     """`step`: device int32[1] tensor holding the Adam step t >= 1."""
     _check("splat_adam", load().splat_adam(_p(param), _p(grad), _p(m), _p(v), param.numel(), _p(step), lr, beta1,
                                            beta2, eps, _stream(stream)))
+
+
+class AdamGroups:
+    """Host-side argument block of splat_adam_groups for fixed tensors."""
+
+    def __init__(self, params, grads, m, v, lr):
+        n = len(params)
+        P = ctypes.c_void_p * n
+        self.n = n
+        self.params = P(*(_p(t) for t in params))
+        self.grads = P(*(_p(t) for t in grads))
+        self.m = P(*(_p(t) for t in m))
+        self.v = P(*(_p(t) for t in v))
+        self.sizes = (ctypes.c_int64 * n)(*(t.numel() for t in params))
+        self.lr = (ctypes.c_float * n)(*lr)
+
+
+def splat_adam_groups(groups: AdamGroups, step, beta1=0.9, beta2=0.999, eps=1e-15, zero_grad=True, stream=None):
+    """One Adam step over all groups (`step`: device int32[1] holding t >= 1)."""
+    _check("splat_adam_groups", load().splat_adam_groups(
+        groups.n, groups.params, groups.grads, groups.m, groups.v, groups.sizes, groups.lr, _p(step), beta1, beta2,
+        eps, 1 if zero_grad else 0, _stream(stream)))
 
 
 def splat_pose_step(w2c, d_pose, m, v, step, lr_t, lr_r, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):

@@ -2,8 +2,7 @@
 // per-element kernels of the hot path: L1 loss (L1 terms of Eq. optim,
 // Sec. 3.5), Adam on resident parameters (map optimisation, Sec. 3.4 step 4),
 // the pose step (Adam + SE(3) retraction for render-driven tracking and the
-// inter-agent relative transform), render-based association (Sec. 3.5 step 2)
-// and the exponential.
+// inter-agent relative transform) and the exponential.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -95,6 +94,60 @@ __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, const 
   }
 }
 
+struct AdamGroups {
+  float* p[8];
+  float* g[8];
+  float* m[8];
+  float* v[8];
+  int64_t size[8];
+  int64_t end[8];  // inclusive prefix of the group sizes in units of 4 elements
+  float lr[8];
+  int vec[8];      // all four arrays 16-byte aligned
+  int n;
+};
+
+__device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v, float lr, float b1, float b2,
+                                         float bc1, float bc2, float eps, int zero_grad) {
+  m = b1 * m + (1.0f - b1) * g;
+  v = b2 * v + (1.0f - b2) * g * g;
+  p = p - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+  if (zero_grad) g = 0.0f;
+}
+
+// Grid-stride over the concatenation of the groups in units of 4 elements
+// (float4 loads where the 4 elements lie inside one 16-byte-aligned group).
+__global__ void __launch_bounds__(256) adam_groups_kernel(AdamGroups G, int64_t total4, float b1, float b2,
+                                                          const int32_t* __restrict__ step, float eps, int zero_grad) {
+  const float bc1 = bias_correction(b1, step);
+  const float bc2 = bias_correction(b2, step);
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total4; u += (int64_t)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < G.n && u >= G.end[k]) ++k;
+    const int64_t j = 4 * (u - (k ? G.end[k - 1] : 0));
+    const int64_t size = G.size[k];
+    float* P = G.p[k] + j;
+    float* Gr = G.g[k] + j;
+    float* M = G.m[k] + j;
+    float* V = G.v[k] + j;
+    const float lr = G.lr[k];
+    if (j + 4 <= size && G.vec[k]) {
+      float4 p4 = *reinterpret_cast<float4*>(P), g4 = *reinterpret_cast<float4*>(Gr);
+      float4 m4 = *reinterpret_cast<float4*>(M), v4 = *reinterpret_cast<float4*>(V);
+      adam_one(p4.x, g4.x, m4.x, v4.x, lr, b1, b2, bc1, bc2, eps, zero_grad);
+      adam_one(p4.y, g4.y, m4.y, v4.y, lr, b1, b2, bc1, bc2, eps, zero_grad);
+      adam_one(p4.z, g4.z, m4.z, v4.z, lr, b1, b2, bc1, bc2, eps, zero_grad);
+      adam_one(p4.w, g4.w, m4.w, v4.w, lr, b1, b2, bc1, bc2, eps, zero_grad);
+      *reinterpret_cast<float4*>(P) = p4;
+      *reinterpret_cast<float4*>(M) = m4;
+      *reinterpret_cast<float4*>(V) = v4;
+      if (zero_grad) *reinterpret_cast<float4*>(Gr) = g4;
+    } else {
+      for (int e = 0; e < 4 && j + e < size; ++e)
+        adam_one(P[e], Gr[e], M[e], V[e], lr, b1, b2, bc1, bc2, eps, zero_grad);
+    }
+  }
+}
+
 // Adam on the 6-vector pose gradient, then w2c <- exp(delta^) w2c.
 __global__ void pose_step_kernel(float* __restrict__ w2c, const float* __restrict__ g, float* __restrict__ m,
                                  float* __restrict__ v, float lr_t, float lr_r, float b1, float b2,
@@ -143,100 +196,6 @@ __global__ void pose_step_kernel(float* __restrict__ w2c, const float* __restric
     out[4 * i + 3] += t[i];
   }
   for (int k = 0; k < 12; ++k) w2c[k] = out[k];
-}
-
-// ----------------------------------------------------------------------------
-// Association
-// ----------------------------------------------------------------------------
-__global__ void assoc_flag_kernel(const int32_t* __restrict__ ia, const float* __restrict__ ta,
-                                  const int32_t* __restrict__ ib, const float* __restrict__ tb, int64_t npix,
-                                  float tmax, uint32_t* __restrict__ flag) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npix) return;
-  flag[i] = (ia[i] >= 0 && ib[i] >= 0 && ta[i] <= tmax && tb[i] <= tmax) ? 1u : 0u;
-}
-
-__global__ void assoc_compact_kernel(const int32_t* __restrict__ ia, const int32_t* __restrict__ ib,
-                                     const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
-                                     int64_t npix, int bits_b, uint64_t* __restrict__ keys,
-                                     int64_t* __restrict__ count) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npix) return;
-  if (flag[i]) keys[pos[i]] = ((uint64_t)(uint32_t)ia[i] << bits_b) | (uint64_t)(uint32_t)ib[i];
-  if (i == npix - 1) *count = (int64_t)pos[i] + flag[i];
-}
-
-__global__ void assoc_head_kernel(const uint64_t* __restrict__ keys, const int64_t* __restrict__ count, int64_t npix,
-                                  uint32_t* __restrict__ head) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npix) return;
-  const int64_t c = *count;
-  head[i] = (i < c && (i == 0 || keys[i] != keys[i - 1])) ? 1u : 0u;
-}
-
-__global__ void assoc_starts_kernel(const uint32_t* __restrict__ head, const uint32_t* __restrict__ uidx,
-                                    const int64_t* __restrict__ count, int64_t npix, int64_t capacity,
-                                    uint32_t* __restrict__ starts, int64_t* __restrict__ m_dev,
-                                    int32_t* __restrict__ status) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npix) return;
-  const int64_t c = *count;
-  if (head[i]) starts[uidx[i]] = (uint32_t)i;
-  if (i == npix - 1) {
-    const int64_t m = (int64_t)uidx[i] + head[i];
-    *m_dev = m;
-    starts[m] = (uint32_t)c;
-    if (m > capacity) raise_status(status, SPLAT_ECAPACITY);
-  }
-}
-
-__global__ void assoc_write_kernel(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ starts,
-                                   const int64_t* __restrict__ m_dev, int64_t capacity, int bits_b,
-                                   int32_t* __restrict__ pairs, int32_t* __restrict__ counts) {
-  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t m = *m_dev;
-  if (u >= m || u >= capacity) return;
-  const uint64_t k = keys[starts[u]];
-  pairs[2 * u] = (int32_t)(k >> bits_b);
-  pairs[2 * u + 1] = (int32_t)(k & ((1ull << bits_b) - 1ull));
-  counts[u] = (int32_t)(starts[u + 1] - starts[u]);
-}
-
-struct AssocWs {
-  uint32_t *flag, *pos, *head, *uidx, *starts;
-  uint64_t *k0, *k1;
-  int64_t* count;
-  void* scan;
-  void* radix;
-};
-
-static size_t carve_assoc(int64_t npix, char* base, AssocWs* w) {
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    char* p = base ? base + off : nullptr;
-    off += align_up(bytes);
-    return p;
-  };
-  const size_t n = (size_t)(npix > 0 ? npix : 1);
-  AssocWs t;
-  t.flag = (uint32_t*)take(4 * n);
-  t.pos = (uint32_t*)take(4 * n);
-  t.head = (uint32_t*)take(4 * n);
-  t.uidx = (uint32_t*)take(4 * n);
-  t.starts = (uint32_t*)take(4 * (n + 1));
-  t.k0 = (uint64_t*)take(8 * n);
-  t.k1 = (uint64_t*)take(8 * n);
-  t.count = (int64_t*)take(8);
-  t.scan = take(scan_workspace_size((int64_t)n));
-  t.radix = take(radix_workspace_size((int64_t)n));
-  if (w) *w = t;
-  return off;
-}
-
-static int bits_for(int64_t n) {
-  int b = 1;
-  while (b < 31 && ((int64_t)1 << b) < n) ++b;
-  return b;
 }
 
 __global__ void exp_kernel(const float* __restrict__ x, float* __restrict__ y, int64_t n) {
@@ -290,49 +249,41 @@ extern "C" int splat_adam(float* param, const float* grad, float* m, float* v, i
   return check_launch("adam_kernel");
 }
 
+extern "C" int splat_adam_groups(int32_t n_groups, float* const* params, float* const* grads, float* const* m,
+                                 float* const* v, const int64_t* sizes, const float* lr, const int32_t* step,
+                                 float beta1, float beta2, float eps, int32_t zero_grad, splat_stream_t stream) {
+  if (n_groups < 1 || n_groups > 8 || !params || !grads || !m || !v || !sizes || !lr || !step)
+    return fail(SPLAT_EINVAL, "splat_adam_groups: bad argument");
+  AdamGroups G;
+  int64_t total4 = 0;
+  for (int k = 0; k < n_groups; ++k) {
+    if (sizes[k] < 0 || (sizes[k] > 0 && (!params[k] || !grads[k] || !m[k] || !v[k])))
+      return fail(SPLAT_EINVAL, "splat_adam_groups: bad group %d", k);
+    G.p[k] = params[k];
+    G.g[k] = grads[k];
+    G.m[k] = m[k];
+    G.v[k] = v[k];
+    G.lr[k] = lr[k];
+    G.size[k] = sizes[k];
+    G.vec[k] = aligned16(params[k]) && aligned16(grads[k]) && aligned16(m[k]) && aligned16(v[k]);
+    total4 += (sizes[k] + 3) / 4;
+    G.end[k] = total4;
+  }
+  G.n = n_groups;
+  if (total4 == 0) return SPLAT_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int blocks = (int)std::min<int64_t>((total4 + 255) / 256, 152 * 16);
+  SPLAT_LAUNCH("adam_groups_kernel", s,
+               adam_groups_kernel<<<blocks, 256, 0, s>>>(G, total4, beta1, beta2, step, eps, zero_grad));
+  return check_launch("adam_groups_kernel");
+}
+
 extern "C" int splat_pose_step(float* w2c, const float* d_pose, float* m, float* v, const int32_t* step, float lr_t,
                                float lr_r, float beta1, float beta2, float eps, splat_stream_t stream) {
   if (!w2c || !d_pose || !m || !v || !step) return fail(SPLAT_EINVAL, "splat_pose_step: bad argument");
   SPLAT_LAUNCH("pose_step_kernel", reinterpret_cast<cudaStream_t>(stream), pose_step_kernel<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(w2c, d_pose, m, v, lr_t, lr_r, beta1, beta2,
                                                                           step, eps));
   return check_launch("pose_step_kernel");
-}
-
-extern "C" size_t splat_assoc_workspace_size(int64_t npix) { return npix < 0 ? 0 : carve_assoc(npix, nullptr, nullptr); }
-
-extern "C" int splat_assoc(const int32_t* id_a, const float* t_a, const int32_t* id_b, const float* t_b, int64_t npix,
-                           int64_t n_a, int64_t n_b, float t_max, int32_t* pairs, int32_t* counts, int64_t capacity,
-                           int64_t* m_dev, int32_t* status, void* ws, size_t ws_bytes, splat_stream_t stream) {
-  if (!id_a || !t_a || !id_b || !t_b || !m_dev || !status || !ws || npix < 0 || capacity < 0 || n_a < 1 || n_b < 1 ||
-      n_a > 0x7fffffff || n_b > 0x7fffffff || npix > 0x7fffffff)
-    return fail(SPLAT_EINVAL, "splat_assoc: bad argument");
-  if (capacity > 0 && (!pairs || !counts)) return fail(SPLAT_EINVAL, "splat_assoc: null output");
-  if (ws_bytes < carve_assoc(npix, nullptr, nullptr)) return fail(SPLAT_EINVAL, "splat_assoc: workspace too small");
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (npix == 0) {
-    if (cudaMemsetAsync(m_dev, 0, sizeof(int64_t), s) != cudaSuccess) return fail(SPLAT_ECUDA, "splat_assoc: memset");
-    return SPLAT_OK;
-  }
-  AssocWs w;
-  carve_assoc(npix, static_cast<char*>(ws), &w);
-  const int ba = bits_for(n_a), bb = bits_for(n_b);
-  const int nb = ceil_div(npix, 256);
-  SPLAT_LAUNCH("assoc_flag_kernel", s, assoc_flag_kernel<<<nb, 256, 0, s>>>(id_a, t_a, id_b, t_b, npix, t_max, w.flag));
-  int rc = exclusive_scan_u32(w.flag, w.pos, npix, w.scan, s);
-  if (rc) return rc;
-  SPLAT_LAUNCH("assoc_compact_kernel", s, assoc_compact_kernel<<<nb, 256, 0, s>>>(id_a, id_b, w.flag, w.pos, npix, bb, w.k0, w.count));
-  if ((rc = check_launch("assoc_compact_kernel"))) return rc;
-  int which = 0;
-  if ((rc = radix_sort<uint64_t>(w.k0, nullptr, w.k1, nullptr, npix, w.count, 0, ba + bb, w.radix, s, &which)))
-    return rc;
-  const uint64_t* keys = which ? w.k1 : w.k0;
-  SPLAT_LAUNCH("assoc_head_kernel", s, assoc_head_kernel<<<nb, 256, 0, s>>>(keys, w.count, npix, w.head));
-  if ((rc = exclusive_scan_u32(w.head, w.uidx, npix, w.scan, s))) return rc;
-  SPLAT_LAUNCH("assoc_starts_kernel", s, assoc_starts_kernel<<<nb, 256, 0, s>>>(w.head, w.uidx, w.count, npix, capacity, w.starts, m_dev, status));
-  if ((rc = check_launch("assoc_starts_kernel"))) return rc;
-  if (capacity == 0) return SPLAT_OK;
-  SPLAT_LAUNCH("assoc_write_kernel", s, assoc_write_kernel<<<nb, 256, 0, s>>>(keys, w.starts, m_dev, capacity, bb, pairs, counts));
-  return check_launch("assoc_write_kernel");
 }
 
 extern "C" int splat_exp_f32(const float* x, float* y, int64_t n, splat_stream_t stream) {

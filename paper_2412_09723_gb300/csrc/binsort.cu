@@ -3,26 +3,27 @@
 // composites in, per 16x16 tile), plus the device-wide scan and radix sort
 // primitives the library uses.
 //
-// Design.  Sorting K (tile, depth, id) duplicates with 64-bit keys would need
-// ~6 radix passes over 12 B items.  Instead:
-//   1. the N Gaussians are radix-sorted once by the bit pattern of their depth
-//      (4 passes over N, stable, so equal depths keep ascending id);
-//   2. duplicates are emitted in that depth order, each carrying only its tile
-//      id and Gaussian id;
-//   3. a stable radix sort on the tile id alone (ceil(log2 n_tiles) bits: 2
-//      passes for up to 65536 tiles) then leaves every tile's list in
-//      ascending (depth, id) order -- the same order as a sort of the full
-//      (tile, depth bits, id) key, bit for bit;
-//   4. tile ranges are the boundaries of equal tile ids.
-// The radix sort is LSD, reduce-then-scan: a per-block digit histogram, one
-// exclusive scan of the digit-major histogram matrix, and a stable scatter in
-// which each warp ranks its 32 items per round with __match_any_sync.  No
-// kernel waits on another block, so nothing can hang on scheduling order.
+// Design.  Binning is a two-level (MSD) radix sort of the (tile, depth, id)
+// duplicates: the top digit is the tile id, sorted by counting -- per-tile
+// counts with atomics, one exclusive scan whose result is directly the tile
+// ranges, and an atomic scatter of 64-bit (depth bits << 32 | id) keys into the
+// tile buckets; the remaining digits are sorted inside each tile's bucket by
+// one CTA in shared memory (bitonic; chunked + merged for buckets deeper than
+// the shared-memory capacity).  The keys are unique, so the result is the
+// ascending (tile, depth bits, id) order bit for bit, whatever order the
+// atomics gave.  Four kernels per view, K x 24 B of traffic.
+// The file also holds a general LSD radix sort (reduce-then-scan: per-block
+// digit histograms, one exclusive scan of the digit-major histogram matrix, a
+// stable scatter ranking each warp's 32 items per round with
+// __match_any_sync) used by the association.  No kernel waits on another
+// block, so nothing can hang on scheduling order.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "segsort.cuh"
 
 namespace splat {
 
@@ -34,35 +35,6 @@ constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 size_t scan_workspace_size(int64_t n) { return align_up(sizeof(uint32_t) * (size_t)std::max<int64_t>(1, (n + kScanTile - 1) / kScanTile)); }
-
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  return x;
-}
-
-// Block-wide exclusive scan of one value per thread; returns the block total.
-template <int NT>
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t& excl, uint32_t* sh /*[32]*/) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t inc = warp_incl_scan(x, lane);
-  if (lane == 31) sh[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    uint32_t w = lane < NT / 32 ? sh[lane] : 0u;
-    const uint32_t wi = warp_incl_scan(w, lane);
-    sh[lane] = wi - w;
-    if (lane == 31) sh[32] = wi;
-  }
-  __syncthreads();
-  excl = sh[warp] + inc - x;
-  const uint32_t total = sh[32];
-  __syncthreads();
-  return total;
-}
 
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n,
                                                                    uint32_t* __restrict__ partials) {
@@ -284,90 +256,213 @@ template int radix_sort<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, in
                                   cudaStream_t, int*);
 
 // ----------------------------------------------------------------------------
-// Binning kernels.
+// Binning: per-tile buckets, then one shared-memory sort per tile.
 // ----------------------------------------------------------------------------
-__global__ void depth_keys_kernel(const float4* __restrict__ xyzo, const int32_t* __restrict__ tiles, int64_t n,
-                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                  unsigned long long* __restrict__ k_total) {
+constexpr int kSegCap = 4096;        // keys a CTA sorts in shared memory (32 KB)
+constexpr int kSortThreads = 256;
+constexpr int kCursorStride = 32;    // one 128-byte line per bucket cursor
+constexpr int kSmemTiles = 8192;     // tiles whose local counters fit the scatter CTA
+constexpr int kScatterThreads = 256;
+constexpr int kScatterLanes = 4;     // threads sharing one Gaussian's rect (rows interleaved)
+constexpr int kScanGridSmem = 10240; // count-grid cells staged in shared memory (40 KB)
+
+// Visible Gaussians (tiles_touched > 0) appended to vis[] with one atomic per
+// CTA; the 64-bit duplicate total K is summed on the way.
+__global__ void __launch_bounds__(256) compact_visible_kernel(const int32_t* __restrict__ tiles, int64_t n,
+                                                              uint32_t* __restrict__ vis,
+                                                              unsigned int* __restrict__ n_vis,
+                                                              unsigned long long* __restrict__ k_total) {
+  __shared__ unsigned int s_warp[8];
+  __shared__ unsigned int s_base;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long t = 0;
-  if (i < n) {
-    const int tt = tiles[i];
-    keys[i] = tt > 0 ? __float_as_uint(xyzo[i].z) : 0xffffffffu;
-    vals[i] = (uint32_t)i;
-    t = (unsigned long long)(tt > 0 ? tt : 0);
-  }
-  // 64-bit duplicate total
+  const int tt = i < n ? tiles[i] : 0;
+  const bool v = tt > 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned ball = __ballot_sync(0xffffffffu, v);
+  unsigned long long t = (unsigned long long)(v ? tt : 0);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  if ((threadIdx.x & 31) == 0 && t) atomicAdd(k_total, t);
+  if (lane == 0) {
+    s_warp[warp] = __popc(ball);
+    if (t) atomicAdd(k_total, t);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int tot = 0;
+    for (int w = 0; w < 8; ++w) {
+      const unsigned int c = s_warp[w];
+      s_warp[w] = tot;
+      tot += c;
+    }
+    s_base = tot ? atomicAdd(n_vis, tot) : 0u;
+  }
+  __syncthreads();
+  if (v) vis[s_base + s_warp[warp] + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
 }
 
-__global__ void gather_counts_kernel(const uint32_t* __restrict__ order, const int32_t* __restrict__ tiles, int64_t n,
-                                     uint32_t* __restrict__ cnt) {
+// Tile counts by a 2D difference array: +1 at (x0, y0) and (x1, y1), -1 at
+// (x1, y0) and (x0, y1); the prefix sums in tile_scan_kernel turn it into the
+// number of rects holding each tile.  Grid: ceil(n / 256) CTAs; CTAs past the
+// visible count return.
+__global__ void __launch_bounds__(256) tile_count_kernel(const uint32_t* __restrict__ vis,
+                                                         const unsigned int* __restrict__ n_vis,
+                                                         const int4* __restrict__ rect, int gw,
+                                                         int* __restrict__ diff) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) cnt[i] = (uint32_t)tiles[order[i]];
+  if (i >= (int64_t)*n_vis) return;
+  const int4 r = rect[vis[i]];
+  atomicAdd(&diff[r.y * gw + r.x], 1);
+  atomicAdd(&diff[r.y * gw + r.z], -1);
+  atomicAdd(&diff[r.w * gw + r.x], -1);
+  atomicAdd(&diff[r.w * gw + r.z], 1);
 }
 
-__global__ void finalize_count_kernel(const unsigned long long* __restrict__ k_total, int64_t capacity,
-                                      int64_t* __restrict__ k_dev, int64_t* __restrict__ cnt_dev,
-                                      int32_t* __restrict__ status) {
-  const int64_t k = (int64_t)*k_total;
-  *k_dev = k;
-  *cnt_dev = k < capacity ? k : capacity;
-  if (k > capacity) raise_status(status, SPLAT_ECAPACITY);
+// One CTA: 2D prefix sums of the difference grid (tiles_y + 1 rows of
+// gw = tiles_x + 1 cells) -> per-tile counts; exclusive scan over tiles ->
+// ranges (clamped to the capacity) and bucket cursors; K and the status.
+__global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff, int tiles_x, int tiles_y,
+                                                         const unsigned long long* __restrict__ k_total,
+                                                         int64_t capacity, uint2* __restrict__ ranges,
+                                                         uint32_t* __restrict__ cursor, int64_t* __restrict__ k_dev,
+                                                         int32_t* __restrict__ status) {
+  __shared__ uint32_t sh[33];
+  __shared__ int s_grid[kScanGridSmem];
+  const int gw = tiles_x + 1;
+  const int cells = gw * tiles_y;
+  int* grid = cells <= kScanGridSmem ? s_grid : diff;  // prefix sums in shared memory when they fit
+  if (grid == s_grid)
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) s_grid[i] = diff[i];
+  __syncthreads();
+  for (int y = threadIdx.x; y < tiles_y; y += blockDim.x) {
+    int run = 0;
+    for (int x = 0; x < tiles_x; ++x) {
+      run += grid[y * gw + x];
+      grid[y * gw + x] = run;
+    }
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < tiles_x; x += blockDim.x) {
+    int run = 0;
+    for (int y = 0; y < tiles_y; ++y) {
+      run += grid[y * gw + x];
+      grid[y * gw + x] = run;
+    }
+  }
+  __syncthreads();
+  const int n_tiles = tiles_x * tiles_y;
+  const uint64_t cap = (uint64_t)capacity;
+  uint32_t carry = 0;
+  for (int base = 0; base < n_tiles; base += 1024) {
+    const int t = base + threadIdx.x;
+    const uint32_t c = t < n_tiles ? (uint32_t)grid[(t / tiles_x) * gw + (t % tiles_x)] : 0u;
+    uint32_t excl;
+    const uint32_t tot = block_excl_scan<1024>(c, excl, sh);
+    if (t < n_tiles) {
+      const uint64_t st = (uint64_t)carry + excl;
+      const uint64_t en = st + c;
+      ranges[t] = c ? make_uint2((uint32_t)(st < cap ? st : cap), (uint32_t)(en < cap ? en : cap)) : make_uint2(0u, 0u);
+      cursor[(size_t)t * kCursorStride] = (uint32_t)st;
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    const int64_t k = (int64_t)*k_total;
+    *k_dev = k;
+    if (k > capacity) raise_status(status, SPLAT_ECAPACITY);
+  }
 }
 
-// One thread per Gaussian in depth order writes (tile id, Gaussian id) for
-// every tile of its rect, row-major.
-__global__ void emit_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ cnt,
-                            const uint32_t* __restrict__ offs, const int4* __restrict__ rect, int64_t n,
-                            int tiles_x, int64_t capacity, uint32_t* __restrict__ tkey,
-                            uint32_t* __restrict__ tval) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || cnt[i] == 0) return;
-  const uint32_t g = order[i];
-  const int4 r = rect[g];
-  int64_t o = offs[i];
-  for (int ty = r.y; ty < r.w; ++ty)
-    for (int tx = r.x; tx < r.z; ++tx, ++o)
-      if (o < capacity) {
-        tkey[o] = (uint32_t)(ty * tiles_x + tx);
-        tval[o] = g;
+// Every visible Gaussian drops key (depth bits << 32 | id) into the bucket of
+// each tile of its rect.  A CTA takes a chunk of visible Gaussians, counts its
+// duplicates per tile in shared memory, reserves space in each touched bucket
+// with one global atomic, then places its keys with shared-memory atomics.  The
+// order inside a bucket is arbitrary; the keys are unique, so the per-tile
+// sort below makes the result deterministic.
+__global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(
+    const uint32_t* __restrict__ vis, const unsigned int* __restrict__ n_vis, const float4* __restrict__ xyzo,
+    const int4* __restrict__ rect, int tiles_x, int n_tiles, uint32_t* __restrict__ cursor, int64_t capacity,
+    uint64_t* __restrict__ skeys) {
+  extern __shared__ uint32_t s_cnt[];  // [n_tiles] local counts, then local cursors
+  uint32_t* s_base = s_cnt + n_tiles;  // [n_tiles] reserved bucket positions
+  constexpr int kChunk = kScatterThreads / kScatterLanes;  // Gaussians per chunk
+  const unsigned int nv = *n_vis;
+  const bool local = n_tiles <= kSmemTiles;
+  const int sub = threadIdx.x % kScatterLanes;  // this thread takes rect rows ty = y0 + sub (mod kScatterLanes)
+  for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < nv; c0 += (int64_t)gridDim.x * kChunk) {
+    const int64_t i = c0 + threadIdx.x / kScatterLanes;
+    const bool has = i < nv;
+    const uint32_t g = has ? vis[i] : 0u;
+    const int4 r = has ? rect[g] : make_int4(0, 0, 0, 0);
+    const uint64_t key = has ? (((uint64_t)__float_as_uint(xyzo[g].z) << 32) | (uint64_t)g) : 0ull;
+    if (!local) {  // too many tiles for shared memory: one global atomic per duplicate
+      for (int ty = r.y + sub; ty < r.w; ty += kScatterLanes)
+        for (int tx = r.x; tx < r.z; ++tx) {
+          const uint32_t pos = atomicAdd(&cursor[(size_t)(ty * tiles_x + tx) * kCursorStride], 1u);
+          if (pos < capacity) skeys[pos] = key;
+        }
+      continue;
+    }
+    for (int t = threadIdx.x; t < n_tiles; t += kScatterThreads) s_cnt[t] = 0u;
+    __syncthreads();
+    for (int ty = r.y + sub; ty < r.w; ty += kScatterLanes)
+      for (int tx = r.x; tx < r.z; ++tx) atomicAdd(&s_cnt[ty * tiles_x + tx], 1u);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += kScatterThreads) {
+      const uint32_t c = s_cnt[t];
+      s_base[t] = c ? atomicAdd(&cursor[(size_t)t * kCursorStride], c) : 0u;
+      s_cnt[t] = 0u;
+    }
+    __syncthreads();
+    for (int ty = r.y + sub; ty < r.w; ty += kScatterLanes)
+      for (int tx = r.x; tx < r.z; ++tx) {
+        const int t = ty * tiles_x + tx;
+        const uint32_t pos = s_base[t] + atomicAdd(&s_cnt[t], 1u);
+        if (pos < capacity) skeys[pos] = key;
       }
+    __syncthreads();
+  }
 }
 
-__global__ void ranges_kernel(const uint32_t* __restrict__ tkey, const int64_t* __restrict__ cnt_dev,
-                              int64_t capacity, uint32_t* __restrict__ ranges) {
-  const int64_t n = valid_count(cnt_dev, capacity);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t t = tkey[i];
-  if (i == 0 || tkey[i - 1] != t) ranges[2 * (int64_t)t] = (uint32_t)i;
-  if (i == n - 1 || tkey[i + 1] != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(i + 1);
-}
-
-__global__ void full_keys_kernel(const uint32_t* __restrict__ tkey, const uint32_t* __restrict__ vals,
-                                 const float4* __restrict__ xyzo, const int64_t* __restrict__ cnt_dev,
-                                 int64_t capacity, uint64_t* __restrict__ keys) {
-  const int64_t n = valid_count(cnt_dev, capacity);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  keys[i] = ((uint64_t)tkey[i] << 32) | (uint64_t)__float_as_uint(xyzo[vals[i]].z);
+// One CTA per tile: sort its bucket ascending by (depth bits, id) and write
+// the ids (and optionally the (tile, depth) keys).
+__global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint2* __restrict__ ranges,
+                                                                 uint64_t* __restrict__ skeys,
+                                                                 uint64_t* __restrict__ skeys2,
+                                                                 uint32_t* __restrict__ vals,
+                                                                 uint64_t* __restrict__ keys_out) {
+  __shared__ uint64_t smem[kSegCap];
+  const int tile = blockIdx.x;
+  const uint2 rg = ranges[tile];
+  const int n = (int)(rg.y - rg.x);
+  if (n <= 0) return;
+  const uint64_t* sorted;
+  if (n <= kSegCap) {
+    cta_sort_small(skeys + rg.x, n, smem);
+    sorted = smem;
+  } else {
+    cta_sort_segment(skeys + rg.x, skeys2 + rg.x, skeys + rg.x, n, smem, kSegCap);
+    sorted = skeys2 + rg.x;
+  }
+  const uint64_t thi = (uint64_t)tile << 32;
+  for (int i = threadIdx.x; i < n; i += kSortThreads) {
+    const uint64_t k = sorted[i];
+    vals[rg.x + i] = (uint32_t)k;
+    if (keys_out) keys_out[rg.x + i] = thi | (k >> 32);
+  }
 }
 
 // ----------------------------------------------------------------------------
 // Workspace layout and the entry point.
 // ----------------------------------------------------------------------------
 struct BinWs {
-  uint32_t *dk0, *dv0, *dk1, *dv1, *cnt, *offs, *tk0, *tk1, *valt;
-  int64_t* cnt_dev;
+  uint32_t *vis, *cursor;
+  int* diff;
+  uint64_t *skeys, *skeys2;
   unsigned long long* k_total;
-  void* radix;
-  void* scan;
+  unsigned int* n_vis;
 };
 
-static size_t carve_bin_ws(int64_t n, int64_t capacity, char* base, BinWs* w) {
+static size_t carve_bin_ws(int64_t n, int64_t tiles_x, int64_t tiles_y, int64_t capacity, char* base, BinWs* w) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char* p = base ? base + off : nullptr;
@@ -375,38 +470,29 @@ static size_t carve_bin_ws(int64_t n, int64_t capacity, char* base, BinWs* w) {
     return p;
   };
   const size_t nn = (size_t)std::max<int64_t>(n, 1), cc = (size_t)std::max<int64_t>(capacity, 1);
+  const size_t nt = (size_t)std::max<int64_t>(tiles_x * tiles_y, 1);
   BinWs t;
-  t.dk0 = (uint32_t*)take(4 * nn);
-  t.dv0 = (uint32_t*)take(4 * nn);
-  t.dk1 = (uint32_t*)take(4 * nn);
-  t.dv1 = (uint32_t*)take(4 * nn);
-  t.cnt = (uint32_t*)take(4 * nn);
-  t.offs = (uint32_t*)take(4 * nn);
-  t.tk0 = (uint32_t*)take(4 * cc);
-  t.tk1 = (uint32_t*)take(4 * cc);
-  t.valt = (uint32_t*)take(4 * cc);
-  t.cnt_dev = (int64_t*)take(8);
+  t.vis = (uint32_t*)take(4 * nn);
+  t.cursor = (uint32_t*)take(4 * kCursorStride * nt);
+  t.diff = (int*)take(4 * (size_t)(tiles_x + 1) * (tiles_y + 1));
+  t.skeys = (uint64_t*)take(8 * cc);
+  t.skeys2 = (uint64_t*)take(8 * cc);
   t.k_total = (unsigned long long*)take(8);
-  t.scan = take(scan_workspace_size((int64_t)nn));
-  t.radix = take(radix_workspace_size(std::max<int64_t>(n, capacity)));
+  t.n_vis = (unsigned int*)take(8);
   if (w) *w = t;
   return off;
-}
-
-static int tile_bits(int64_t n_tiles) {
-  int b = 0;
-  while (((int64_t)1 << b) < n_tiles) ++b;
-  return b;
 }
 
 }  // namespace splat
 
 using namespace splat;
 
+// The workspace depends on the tile grid (w + 1)(h + 1) cells of the count
+// grid); with only the tile count known, size it for a 1 x n_tiles grid, which
+// bounds (w + 1)(h + 1) = n_tiles + w + h + 1 <= 2 n_tiles + 2 for any w h = n_tiles.
 extern "C" size_t splat_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t n_tiles) {
-  (void)n_tiles;
-  if (n < 0 || capacity < 0) return 0;
-  return carve_bin_ws(n, capacity, nullptr, nullptr);
+  if (n < 0 || capacity < 0 || n_tiles < 1) return 0;
+  return carve_bin_ws(n, n_tiles, 1, capacity, nullptr, nullptr);
 }
 
 extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const splat_camera* cam, uint64_t* keys,
@@ -419,49 +505,59 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
   if (cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "splat_bin_sort: bad image size");
   if (n > 0 && (!proj->xyzo || !proj->rect || !proj->tiles_touched || !aligned16(proj->xyzo) || !aligned16(proj->rect)))
     return fail(SPLAT_EINVAL, "splat_bin_sort: projected arrays null or not 16-byte aligned");
-  const size_t need = carve_bin_ws(n, capacity, nullptr, nullptr);
-  if (ws_bytes < need) return fail(SPLAT_EINVAL, "splat_bin_sort: workspace %zu < %zu bytes", ws_bytes, need);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const CamK ck = make_camk(*cam);
   const int64_t n_tiles = (int64_t)ck.tiles_x * ck.tiles_y;
+  const size_t need = carve_bin_ws(n, ck.tiles_x, ck.tiles_y, capacity, nullptr, nullptr);
+  if (ws_bytes < need || !aligned16(ws) || !aligned16(ranges))
+    return fail(SPLAT_EINVAL, "splat_bin_sort: workspace %zu < %zu bytes, or ws/ranges misaligned", ws_bytes, need);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   BinWs w;
-  carve_bin_ws(n, capacity, static_cast<char*>(ws), &w);
-  if (cudaMemsetAsync(ranges, 0, sizeof(uint32_t) * 2 * n_tiles, s) != cudaSuccess ||
-      cudaMemsetAsync(w.k_total, 0, sizeof(unsigned long long), s) != cudaSuccess)
+  carve_bin_ws(n, ck.tiles_x, ck.tiles_y, capacity, static_cast<char*>(ws), &w);
+  const bool local = n_tiles <= kSmemTiles;
+  const size_t scatter_smem = local ? 2 * sizeof(uint32_t) * (size_t)n_tiles : 0;
+  if (scatter_smem > 48 * 1024) {  // more than the default: opt in once per device
+    static std::atomic<unsigned long long> attr_done{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(SPLAT_ECUDA, "splat_bin_sort: no current device");
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(attr_done.load() & bit)) {
+      if (cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(2 * sizeof(uint32_t) * kSmemTiles)) != cudaSuccess)
+        return fail(SPLAT_ECUDA, "splat_bin_sort: cannot enable shared memory for the scatter");
+      attr_done.fetch_or(bit);
+    }
+  }
+  const size_t diff_bytes = sizeof(int) * (size_t)(ck.tiles_x + 1) * (ck.tiles_y + 1);
+  if (cudaMemsetAsync(w.diff, 0, diff_bytes, s) != cudaSuccess ||
+      cudaMemsetAsync(w.k_total, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+      cudaMemsetAsync(w.n_vis, 0, sizeof(unsigned int), s) != cudaSuccess)
     return fail(SPLAT_ECUDA, "splat_bin_sort: memset failed");
   const float4* xyzo = reinterpret_cast<const float4*>(proj->xyzo);
+  const int4* rect = reinterpret_cast<const int4*>(proj->rect);
   const int nb = std::max(1, ceil_div(n, 256));
-  // 1. depth keys of the visible Gaussians (culled ones sort last), K total
-  if (n > 0) SPLAT_LAUNCH("depth_keys_kernel", s, depth_keys_kernel<<<nb, 256, 0, s>>>(xyzo, proj->tiles_touched, n, w.dk0, w.dv0, w.k_total));
-  int rc = check_launch("depth_keys_kernel");
-  if (rc) return rc;
-  SPLAT_LAUNCH("finalize_count_kernel", s, finalize_count_kernel<<<1, 1, 0, s>>>(w.k_total, capacity, k_dev, w.cnt_dev, status));
-  if ((rc = check_launch("finalize_count_kernel"))) return rc;
-  if (n == 0) return SPLAT_OK;
-  int which = 0;
-  if ((rc = radix_sort<uint32_t>(w.dk0, w.dv0, w.dk1, w.dv1, n, nullptr, 0, 32, w.radix, s, &which))) return rc;
-  const uint32_t* order = which ? w.dv1 : w.dv0;
-  // 2. duplicate offsets in depth order, emission
-  SPLAT_LAUNCH("gather_counts_kernel", s, gather_counts_kernel<<<nb, 256, 0, s>>>(order, proj->tiles_touched, n, w.cnt));
-  if ((rc = exclusive_scan_u32(w.cnt, w.offs, n, w.scan, s))) return rc;
-  if (capacity == 0) return SPLAT_OK;
-  const int tb = tile_bits(n_tiles);
-  const int passes = radix_passes(0, tb);
-  uint32_t* v0 = (passes & 1) ? w.valt : vals;
-  uint32_t* v1 = (passes & 1) ? vals : w.valt;
-  SPLAT_LAUNCH("emit_kernel", s, emit_kernel<<<nb, 256, 0, s>>>(order, w.cnt, w.offs, reinterpret_cast<const int4*>(proj->rect), n, ck.tiles_x,
-                                 capacity, w.tk0, v0));
-  if ((rc = check_launch("emit_kernel"))) return rc;
-  // 3. stable sort by tile id
-  if ((rc = radix_sort<uint32_t>(w.tk0, v0, w.tk1, v1, capacity, w.cnt_dev, 0, tb, w.radix, s, &which))) return rc;
-  const uint32_t* tk = which ? w.tk1 : w.tk0;
-  // 4. ranges, optional full keys
-  const int kb = std::max(1, ceil_div(capacity, 256));
-  SPLAT_LAUNCH("ranges_kernel", s, ranges_kernel<<<kb, 256, 0, s>>>(tk, w.cnt_dev, capacity, ranges));
-  if ((rc = check_launch("ranges_kernel"))) return rc;
-  if (keys) {
-    SPLAT_LAUNCH("full_keys_kernel", s, full_keys_kernel<<<kb, 256, 0, s>>>(tk, vals, xyzo, w.cnt_dev, capacity, keys));
-    if ((rc = check_launch("full_keys_kernel"))) return rc;
+  if (n > 0) {
+    SPLAT_LAUNCH("compact_visible_kernel", s,
+                 compact_visible_kernel<<<nb, 256, 0, s>>>(proj->tiles_touched, n, w.vis, w.n_vis, w.k_total));
+    SPLAT_LAUNCH("tile_count_kernel", s,
+                 tile_count_kernel<<<nb, 256, 0, s>>>(w.vis, w.n_vis, rect, ck.tiles_x + 1, w.diff));
   }
-  return SPLAT_OK;
+  SPLAT_LAUNCH("tile_scan_kernel", s,
+               tile_scan_kernel<<<1, 1024, 0, s>>>(w.diff, ck.tiles_x, ck.tiles_y, w.k_total, capacity,
+                                                   reinterpret_cast<uint2*>(ranges), w.cursor, k_dev, status));
+  int rc = check_launch("tile_scan_kernel");
+  if (rc || n == 0 || capacity == 0) return rc;
+  int sms = 152;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int sgrid = std::max(1, std::min(ceil_div(n, kScatterThreads / kScatterLanes), 4 * sms));
+  SPLAT_LAUNCH("bucket_scatter_kernel", s,
+               bucket_scatter_kernel<<<sgrid, kScatterThreads, scatter_smem, s>>>(
+                   w.vis, w.n_vis, xyzo, rect, ck.tiles_x, (int)n_tiles, w.cursor, capacity, w.skeys));
+  if ((rc = check_launch("bucket_scatter_kernel"))) return rc;
+  SPLAT_LAUNCH("tile_sort_kernel", s,
+               tile_sort_kernel<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(reinterpret_cast<const uint2*>(ranges),
+                                                                          w.skeys, w.skeys2, vals, keys));
+  return check_launch("tile_sort_kernel");
 }

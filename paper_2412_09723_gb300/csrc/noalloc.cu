@@ -55,7 +55,9 @@ extern "C" int splat_bin_sort_static(const splat_projected* proj, int64_t n, con
                                      int32_t* status, splat_stream_t stream) {
   if (!cam) return fail(SPLAT_EINVAL, "splat_bin_sort_static: null camera");
   if (n < 0 || capacity < 0) return fail(SPLAT_EINVAL, "splat_bin_sort_static: negative size");
-  const size_t need = splat_bin_sort_workspace_size(n, capacity, 0);
+  if (cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "splat_bin_sort_static: bad image size");
+  const int64_t n_tiles = (int64_t)((cam->width + 15) / 16) * ((cam->height + 15) / 16);
+  const size_t need = splat_bin_sort_workspace_size(n, capacity, (int32_t)n_tiles);
   if (need == 0 || need > kStaticScratchBytes)
     return fail(SPLAT_EINVAL,
                 "splat_bin_sort_static: n=%lld, capacity=%lld need %zu bytes of scratch, more than the %zu-byte "

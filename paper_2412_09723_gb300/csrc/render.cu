@@ -28,7 +28,7 @@
 namespace splat {
 
 constexpr int kBatch = 256;
-constexpr int kThreads = 128;  // 2 pixels per thread: (x, y) and (x, y + 2)
+constexpr int kThreads = 128;  // backward: 2 pixels per thread, (x, y) and (x, y + 2)
 constexpr int kGradStride = 12;  // internal screen-space gradient row (3 float4)
 constexpr int kAccStride = 11;   // shared accumulator row (10 sums, padded against bank conflicts)
 
@@ -88,74 +88,53 @@ __device__ __forceinline__ void composite_step(FwdPix& q, const float4 xo, const
   ++q.used;
 }
 
-__global__ void __launch_bounds__(kThreads) render_fwd_kernel(const float4* __restrict__ xyzo,
-                                                              const float4* __restrict__ conic,
-                                                              const float* __restrict__ rgb,
-                                                              const uint32_t* __restrict__ vals,
-                                                              const uint2* __restrict__ ranges, CamK cam,
-                                                              float bg0, float bg1, float bg2, ImageK out) {
+__global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(const float4* __restrict__ xyzo,
+                                                                 const float4* __restrict__ conic,
+                                                                 const float* __restrict__ rgb,
+                                                                 const uint32_t* __restrict__ vals,
+                                                                 const uint2* __restrict__ ranges, CamK cam,
+                                                                 float bg0, float bg1, float bg2, ImageK out) {
   __shared__ float4 s_xyzo[kBatch];
   __shared__ float4 s_con[kBatch];
   __shared__ float s_rgb[3 * kBatch];
   __shared__ int32_t s_id[kBatch];
   const int tile = blockIdx.x;
   const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-  int px[2], py[2];
-  bool inside[2];
-  float fxp[2], fyp[2];
-  FwdPix q[2];
-#pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    int lx, ly;
-    pixel_of(threadIdx.x, p, lx, ly);
-    px[p] = tx * kTile + lx;
-    py[p] = ty * kTile + ly;
-    inside[p] = px[p] < cam.width && py[p] < cam.height;
-    fxp[p] = (float)px[p] + 0.5f;
-    fyp[p] = (float)py[p] + 0.5f;
-    q[p] = FwdPix{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, 0, 0, !inside[p]};
-  }
+  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
+  const int py = ty * kTile + (threadIdx.x >> 4);
+  const bool inside = px < cam.width && py < cam.height;
+  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+  FwdPix q{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, 0, 0, !inside};
   const uint2 rg = ranges[tile];
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
-    if (__syncthreads_count(q[0].done && q[1].done) == kThreads) break;
-    for (int i = threadIdx.x; i < kBatch; i += kThreads) {
-      const uint32_t idx = start + i;
-      if (idx < rg.y) {
-        const uint32_t g = vals[idx];
-        s_id[i] = (int32_t)g;
-        s_xyzo[i] = xyzo[g];
-        s_con[i] = conic[g];
-        s_rgb[3 * i + 0] = rgb[3 * (size_t)g + 0];
-        s_rgb[3 * i + 1] = rgb[3 * (size_t)g + 1];
-        s_rgb[3 * i + 2] = rgb[3 * (size_t)g + 2];
-      }
+    if (__syncthreads_count(q.done) == kTilePixels) break;
+    const uint32_t idx = start + threadIdx.x;
+    if (idx < rg.y) {
+      const uint32_t g = vals[idx];
+      s_id[threadIdx.x] = (int32_t)g;
+      s_xyzo[threadIdx.x] = xyzo[g];
+      s_con[threadIdx.x] = conic[g];
+      s_rgb[3 * threadIdx.x + 0] = rgb[3 * (size_t)g + 0];
+      s_rgb[3 * threadIdx.x + 1] = rgb[3 * (size_t)g + 1];
+      s_rgb[3 * threadIdx.x + 2] = rgb[3 * (size_t)g + 2];
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
     const int32_t base = (int32_t)(start - rg.x);
-    for (int j = 0; j < cnt; ++j) {
-      if (q[0].done && q[1].done) break;
-      const float4 xo = s_xyzo[j];
-      const float4 co = s_con[j];
-#pragma unroll
-      for (int p = 0; p < 2; ++p)
-        if (!q[p].done) composite_step(q[p], xo, co, fxp[p], fyp[p], &s_rgb[3 * j], s_id[j], base + j);
-    }
+    for (int j = 0; j < cnt && !q.done; ++j)
+      composite_step(q, s_xyzo[j], s_con[j], fx, fy, &s_rgb[3 * j], s_id[j], base + j);
   }
-#pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    if (!inside[p]) continue;
-    const size_t i = (size_t)py[p] * cam.width + px[p];
-    out.rgb[3 * i + 0] = __fmaf_rn(q[p].T, bg0, q[p].C0);
-    out.rgb[3 * i + 1] = __fmaf_rn(q[p].T, bg1, q[p].C1);
-    out.rgb[3 * i + 2] = __fmaf_rn(q[p].T, bg2, q[p].C2);
-    out.depth[i] = q[p].D;
-    out.sil[i] = q[p].S;
-    out.t_final[i] = q[p].T;
-    out.n_contrib[i] = q[p].last;
-    out.max_id[i] = q[p].id;
-    if (out.n_used) out.n_used[i] = q[p].used;
-  }
+  if (!inside) return;
+  const size_t i = (size_t)py * cam.width + px;
+  out.rgb[3 * i + 0] = __fmaf_rn(q.T, bg0, q.C0);
+  out.rgb[3 * i + 1] = __fmaf_rn(q.T, bg1, q.C1);
+  out.rgb[3 * i + 2] = __fmaf_rn(q.T, bg2, q.C2);
+  out.depth[i] = q.D;
+  out.sil[i] = q.S;
+  out.t_final[i] = q.T;
+  out.n_contrib[i] = q.last;
+  out.max_id[i] = q.id;
+  if (out.n_used) out.n_used[i] = q.used;
 }
 
 // ----------------------------------------------------------------------------
@@ -368,7 +347,7 @@ extern "C" int splat_render_fwd(const splat_projected* proj, const float* rgb, i
   const CamK ck = make_camk(*cam);
   ImageK im{out->rgb, out->depth, out->sil, out->t_final, out->n_contrib, out->max_id, out->n_used};
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  SPLAT_LAUNCH("render_fwd_kernel", s, render_fwd_kernel<<<ck.tiles_x * ck.tiles_y, kThreads, 0, s>>>(
+  SPLAT_LAUNCH("render_fwd_kernel", s, render_fwd_kernel<<<ck.tiles_x * ck.tiles_y, kTilePixels, 0, s>>>(
       reinterpret_cast<const float4*>(proj->xyzo), reinterpret_cast<const float4*>(proj->conic), rgb, vals,
       reinterpret_cast<const uint2*>(ranges), ck, bg[0], bg[1], bg[2], im));
   return check_launch("render_fwd_kernel");

@@ -1,0 +1,229 @@
+// segsort.cuh -- CTA-level primitives: block scan, and one CTA sorting one
+// segment of 64-bit keys ascending.
+//
+// Segments up to the shared-memory capacity are loaded, padded to a power of
+// two with all-ones keys and bitonic-sorted in shared memory.  Longer segments
+// are sorted in capacity-sized chunks (same routine), then merged pairwise
+// with a merge-path rank per element (a binary search into the other run;
+// equal keys of the left run go first, so duplicates are allowed),
+// ping-ponging between the caller's output and temporary arrays.
+#pragma once
+
+#include "common.cuh"
+
+namespace splat {
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+template <int NT>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t& excl, uint32_t* sh /*[32]*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t inc = warp_incl_scan(x, lane);
+  if (lane == 31) sh[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < NT / 32 ? sh[lane] : 0u;
+    const uint32_t wi = warp_incl_scan(w, lane);
+    sh[lane] = wi - w;
+    if (lane == 31) sh[32] = wi;
+  }
+  __syncthreads();
+  excl = sh[warp] + inc - x;
+  const uint32_t total = sh[32];
+  __syncthreads();
+  return total;
+}
+
+// Bitonic sort of s[0, n2) ascending; n2 a power of two; all threads of the CTA.
+__device__ __forceinline__ void cta_bitonic_u64(uint64_t* s, int n2) {
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < (n2 >> 1); i += blockDim.x) {
+        const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+        const int hi = lo + j;
+        const bool up = (lo & k) == 0;
+        const uint64_t a = s[lo], b = s[hi];
+        if ((a > b) == up) {
+          s[lo] = b;
+          s[hi] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ int next_pow2(int n) {
+  int p = 1;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// Register-blocked bitonic sort: thread t holds elements [t E, t E + E) of the
+// n2 = E * blockDim.x keys.  Compare-exchange partners at distance j < E are in
+// the same thread, at E <= j < 32 E in another lane of the same warp (shuffle),
+// and only the stages with j >= 32 E go through shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t x, int m) {
+  const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)x, m);
+  const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(x >> 32), m);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+template <int E, int J>
+__device__ __forceinline__ void bitonic_inreg(uint64_t (&v)[E], int t, int k) {
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    if (i & J) continue;
+    const bool up = ((t * E + i) & k) == 0;
+    const uint64_t a = v[i], b = v[i + J];
+    const bool sw = (a > b) == up;
+    v[i] = sw ? b : a;
+    v[i + J] = sw ? a : b;
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void bitonic_inreg_any(uint64_t (&v)[E], int t, int k, int j) {
+  if constexpr (E > 8) {
+    if (j == 8) { bitonic_inreg<E, 8>(v, t, k); return; }
+  }
+  if constexpr (E > 4) {
+    if (j == 4) { bitonic_inreg<E, 4>(v, t, k); return; }
+  }
+  if constexpr (E > 2) {
+    if (j == 2) { bitonic_inreg<E, 2>(v, t, k); return; }
+  }
+  if constexpr (E > 1) {
+    if (j == 1) { bitonic_inreg<E, 1>(v, t, k); return; }
+  }
+}
+
+template <int E>
+__device__ void cta_bitonic_reg(uint64_t* s, int n2) {
+  const int t = threadIdx.x;
+  uint64_t v[E];
+#pragma unroll
+  for (int i = 0; i < E; ++i) v[i] = s[t * E + i];
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j < E) {
+        bitonic_inreg_any<E>(v, t, k, j);
+      } else if (j < 32 * E) {
+        const int m = j / E;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int g = t * E + i;
+          const bool keep_min = (((g & k) == 0) == ((g & j) == 0));
+          const uint64_t o = shfl_xor_u64(v[i], m);
+          v[i] = keep_min ? (o < v[i] ? o : v[i]) : (o > v[i] ? o : v[i]);
+        }
+      } else {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; ++i) s[t * E + i] = v[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+          const int g = t * E + i;
+          const bool keep_min = (((g & k) == 0) == ((g & j) == 0));
+          const uint64_t o = s[g ^ j];
+          v[i] = keep_min ? (o < v[i] ? o : v[i]) : (o > v[i] ? o : v[i]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < E; ++i) s[t * E + i] = v[i];
+  __syncthreads();
+}
+
+// Sort in[0, n) into smem (n <= cap) and leave the result in smem[0, n).
+// blockDim.x must be 256 when n can exceed 256 (register-blocked stages).
+__device__ __forceinline__ void cta_sort_small(const uint64_t* in, int n, uint64_t* smem) {
+  const int n2 = next_pow2(n < 1 ? 1 : n);
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) smem[i] = i < n ? in[i] : ~0ull;
+  __syncthreads();
+  if (blockDim.x != 256 || n2 <= 256) {
+    cta_bitonic_u64(smem, n2);
+    return;
+  }
+  switch (n2 >> 8) {
+    case 2: cta_bitonic_reg<2>(smem, n2); break;
+    case 4: cta_bitonic_reg<4>(smem, n2); break;
+    case 8: cta_bitonic_reg<8>(smem, n2); break;
+    default: cta_bitonic_u64(smem, n2); break;  // 4096: shared-memory stages only
+  }
+}
+
+// Number of elements of the sorted run r[0, m) that are < key (or <= key).
+__device__ __forceinline__ int rank_lt(const uint64_t* r, int m, uint64_t key) {
+  int lo = 0, hi = m;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (r[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int rank_le(const uint64_t* r, int m, uint64_t key) {
+  int lo = 0, hi = m;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (r[mid] <= key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Sort the segment in[0, n) (global) into out[0, n) (global).  tmp: global
+// scratch of n keys.  smem: cap keys of shared memory (cap a power of two).
+// `in` may alias `tmp` but not `out`.
+static __device__ void cta_sort_segment(const uint64_t* in, uint64_t* out, uint64_t* tmp, int n, uint64_t* smem, int cap) {
+  if (n <= cap) {
+    cta_sort_small(in, n, smem);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = smem[i];
+    __syncthreads();
+    return;
+  }
+  // 1. sorted chunks of `cap` keys; choose the chunk destination so that the
+  //    last merge level writes into `out`.
+  int levels = 0;
+  for (int L = cap; L < n; L <<= 1) ++levels;
+  uint64_t* a = (levels & 1) ? tmp : out;
+  uint64_t* b = (levels & 1) ? out : tmp;
+  for (int c0 = 0; c0 < n; c0 += cap) {
+    const int m = min(cap, n - c0);
+    __syncthreads();
+    cta_sort_small(in + c0, m, smem);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) a[c0 + i] = smem[i];
+  }
+  __syncthreads();
+  // 2. merge runs of length L into runs of 2L
+  for (int L = cap; L < n; L <<= 1) {
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int r0 = (e / (2 * L)) * (2 * L);
+      const int mid = min(r0 + L, n);
+      const int r1 = min(r0 + 2 * L, n);
+      const uint64_t key = a[e];
+      int pos;
+      if (e < mid) pos = (e - r0) + rank_lt(a + mid, r1 - mid, key);   // ties: left run first
+      else pos = (e - mid) + rank_le(a + r0, mid - r0, key);
+      b[r0 + pos] = key;
+    }
+    __syncthreads();
+    uint64_t* t = a;
+    a = b;
+    b = t;
+  }
+}
+
+}  // namespace splat

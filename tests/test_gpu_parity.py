@@ -341,3 +341,71 @@ def test_autograd_matches_oracle(dev):
     for name, t in zip(("mean", "log_scale", "quat", "opacity_logit", "rgb"), p):
         _assert_grad_close(t.grad.cpu().numpy(), ref[name], name)
     _assert_grad_close(delta.grad.cpu().numpy(), ref["pose"], "pose")
+
+
+def test_deep_tiles_use_the_merge_path(dev):
+    """More than 8192 duplicates in one tile: the per-tile sort falls back to
+    chunked shared-memory sorts plus global merges; the order must not change."""
+    rng = np.random.default_rng(3)
+    n = 30000
+    sc = scenes.Scene(
+        mean=np.stack([rng.uniform(-0.05, 0.05, n), rng.uniform(-0.05, 0.05, n), rng.uniform(1.0, 3.0, n)],
+                      axis=1).astype(np.float32),
+        log_scale=np.full((n, 3), -4.0, np.float32), quat=np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+        opacity_logit=rng.normal(-3.0, 0.5, n).astype(np.float32), rgb=rng.uniform(0, 1, (n, 3)).astype(np.float32))
+    cam = scenes.Camera(40, 40, 60.0, 60.0, 20.0, 20.0)
+    p, fb = _render_gpu(sc, np.eye(4, dtype=np.float32), cam, (0, 0, 0), dev)
+    ranges = fb.ranges.cpu().numpy().view(np.uint32)
+    assert (ranges[:, 1] - ranges[:, 0]).max() > 8192 * 2
+    _check_bins(fb, sc, np.eye(4, dtype=np.float32), cam)
+    _check_image(fb, oracle.render_fwd(sc, np.eye(4, dtype=np.float32), cam, np.zeros(3, np.float32)))
+
+
+def test_adam_groups_matches_per_group_adam(dev):
+    from paper_2412_09723_gb300 import binding as B
+
+    rng = np.random.default_rng(2)
+    sizes = [3001, 17, 4096, 1, 999]
+    lrs = [1e-3, 5e-2, 1e-4, 2e-3, 7e-3]
+    host = [[rng.normal(size=n).astype(np.float32) for _ in range(4)] for n in sizes]
+    for h in host:
+        h[3] = np.abs(h[3])
+    dev_t = [[torch.as_tensor(a.copy(), device=dev) for a in h] for h in host]
+    groups = B.AdamGroups([d[0] for d in dev_t], [d[1] for d in dev_t], [d[2] for d in dev_t], [d[3] for d in dev_t],
+                          lrs)
+    step = torch.tensor([4], dtype=torch.int32, device=dev)
+    B.splat_adam_groups(groups, step, zero_grad=True)
+    torch.cuda.synchronize()
+    for h, d, lr in zip(host, dev_t, lrs):
+        rp, rm, rv = oracle.adam(h[0], h[1], h[2], h[3], 4, lr)
+        np.testing.assert_allclose(d[0].cpu().numpy(), rp, rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(d[2].cpu().numpy(), rm, rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(d[3].cpu().numpy(), rv, rtol=1e-6, atol=1e-7)
+        assert not d[1].any()  # gradients cleared
+
+
+def test_assoc_deep_buckets_and_duplicates(dev):
+    """Few distinct ids over many pixels (deep buckets -> merge path) and many
+    repeated pairs; pairs and counts must equal the oracle's."""
+    from paper_2412_09723_gb300 import binding as B
+
+    rng = np.random.default_rng(5)
+    H, W = 300, 400
+    ia = rng.integers(0, 40, size=(H, W)).astype(np.int32)
+    ib = rng.integers(0, 7, size=(H, W)).astype(np.int32)
+    ia[:5] = -1
+    ta = rng.uniform(0, 1, (H, W)).astype(np.float32)
+    tb = rng.uniform(0, 1, (H, W)).astype(np.float32)
+    ref_pairs, ref_counts = oracle.assoc(ia, ta, ib, tb, 0.7)
+    t = [torch.as_tensor(x, device=dev) for x in (ia, ta, ib, tb)]
+    npix = H * W
+    pairs = torch.zeros(npix, 2, dtype=torch.int32, device=dev)
+    counts = torch.zeros(npix, dtype=torch.int32, device=dev)
+    m_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(B.splat_assoc_workspace_size(npix), dtype=torch.uint8, device=dev)
+    B.splat_assoc(t[0], t[1], t[2], t[3], 40, 7, 0.7, pairs, counts, npix, m_dev, status, ws)
+    m = int(m_dev.item())
+    assert m == len(ref_pairs)
+    assert np.array_equal(pairs[:m].cpu().numpy(), ref_pairs)
+    assert np.array_equal(counts[:m].cpu().numpy(), ref_counts)
