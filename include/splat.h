@@ -128,6 +128,12 @@ uint64_t splat_kernel_launches(void);
  * while a stream is being captured into a graph.  Returns SPLAT_OK. */
 int splat_profile_enable(int on);
 
+/* Restricts the timing to launches of the kernel named `kernel` (host string,
+ * copied; NULL or "" = every kernel).  Timing a single kernel keeps the host
+ * cost of the event records small enough not to leave the GPU waiting between
+ * launches.  Returns SPLAT_OK. */
+int splat_profile_select(const char *kernel);
+
 /* Waits for the recorded events, then returns, per kernel name, the number of
  * timed launches and their summed duration in milliseconds, and forgets the
  * records.  names (host, names_bytes) receives the kernel names separated by

@@ -155,6 +155,47 @@ class Agent:
                           cfg.t_max, self.pairs, self.counts, self.assoc_cap, self.m_dev, self.assoc_status,
                           self.assoc_ws, s)
 
+    # -- episodes ---------------------------------------------------------------
+    def _state(self):
+        return [*self.params, *self.m, *self.v, self.w2c, self.pose_m, self.pose_v, self.t_dev]
+
+    def snapshot(self):
+        """Keep a device copy of the map, optimiser state and pose."""
+        self._snap = [t.clone() for t in self._state()]
+
+    def restore(self, stream=None):
+        """Return the map, optimiser state and pose to the last snapshot
+        (device-to-device copies into the same buffers, so captured graphs
+        stay valid)."""
+        s = torch.cuda.current_stream() if stream is None else stream
+        with torch.cuda.stream(s):
+            for dst, src in zip(self._state(), self._snap):
+                dst.copy_(src, non_blocking=True)
+
+    # -- CUDA graph -------------------------------------------------------------
+    def capture(self):
+        """Capture one step into a CUDA graph.  All buffers are fixed (size the
+        duplicate capacity first); replaying the graph performs exactly the
+        kernels of `step()` with no host work.  Returns the number of library
+        kernel launches one replay performs."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):  # warm-up on the capture stream's side
+            self.step(stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        n0 = B.splat_kernel_launches()
+        with torch.cuda.graph(g):
+            self.step()
+        self.launches_per_step = B.splat_kernel_launches() - n0
+        self.graph = g
+        return self.launches_per_step
+
+    def replay(self):
+        self.graph.replay()
+        self.steps_done += 1
+
     def status(self) -> int:
         """Sticky device status of the last steps (host read)."""
         return int(self.fb.status.item()) | int(self.assoc_status.item())

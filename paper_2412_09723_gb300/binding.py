@@ -54,6 +54,7 @@ _SIGS = {
     "splat_last_error": ([], ctypes.c_char_p),
     "splat_kernel_launches": ([], ctypes.c_uint64),
     "splat_profile_enable": ([ctypes.c_int], ctypes.c_int),
+    "splat_profile_select": ([ctypes.c_char_p], ctypes.c_int),
     "splat_profile_read": ([_c_p, _c_sz, _c_p, _c_p, _c_i32, _c_p], ctypes.c_int),
     "splat_project": ([_c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_bin_sort_workspace_size": ([_c_i64, _c_i64, _c_i32], _c_sz),
@@ -157,6 +158,10 @@ def splat_kernel_launches() -> int:
 
 def splat_profile_enable(on: bool):
     _check("splat_profile_enable", load().splat_profile_enable(1 if on else 0))
+
+
+def splat_profile_select(kernel: str | None):
+    _check("splat_profile_select", load().splat_profile_select(None if kernel is None else kernel.encode()))
 
 
 def splat_profile_read(max_kernels: int = 64) -> dict:

@@ -26,6 +26,8 @@ struct Rec {
 };
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
+std::string g_only;  // time only this kernel ("" = all)
+std::atomic<int> g_has_only{0};
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {
@@ -45,6 +47,7 @@ LaunchScope::LaunchScope(const char* name, cudaStream_t s) : name_(name), s_(s),
   count_launch(1);
   if (g_timing.load(std::memory_order_relaxed)) {
     std::lock_guard<std::mutex> lk(g_mu);
+    if (g_has_only.load(std::memory_order_relaxed) && g_only != name_) return;
     a_ = take_event();
     if (a_ && cudaEventRecord(a_, s_) != cudaSuccess) {
       g_pool.push_back(a_);
@@ -73,6 +76,13 @@ extern "C" uint64_t splat_kernel_launches(void) { return (uint64_t)g_launches.lo
 
 extern "C" int splat_profile_enable(int on) {
   g_timing.store(on ? 1 : 0, std::memory_order_relaxed);
+  return SPLAT_OK;
+}
+
+extern "C" int splat_profile_select(const char* kernel) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_only = kernel ? kernel : "";
+  g_has_only.store(g_only.empty() ? 0 : 1);
   return SPLAT_OK;
 }
 
