@@ -11,15 +11,18 @@
 // changes no result.  Blocks leave as soon as every pixel has reached the
 // transmittance stop.  No atomics: the output is deterministic.
 //
-// Backward: same tiling; every thread starts from its pixel's final
+// Backward: same tiling, 128 threads with 2 pixels each ((x, y) and
+// (x, y + 2); a warp covers 16 x 4 pixels).  Every pixel starts from its final
 // transmittance and last contributor, walks the list back to front, recovers
 // T_i = T_{i+1} / (1 - alpha_i), and keeps the suffix sums
-// R_X <- X_i alpha_i + (1 - alpha_i) R_X of colour, depth and silhouette so that
+// R_X <- X_i alpha_i + (1 - alpha_i) R_X of colour, depth and silhouette, so
 // dL/dalpha_i = T_i [gC.(c_i - R_C) + gD (z_i - R_D) + gS (1 - R_S)]
 //             - (gC.bg) T_final / (1 - alpha_i).
-// The 10 screen-space gradients of a Gaussian are summed over the 32 pixels of
-// a warp with shuffles, over the warps of the CTA in shared memory, and added
-// to global memory with one atomic per value per CTA.
+// Per Gaussian and warp, ten sums are reduced with a recursive-halving
+// reduce-scatter (five moments of dL/dpower -- sum dp dx, dp dy, dp dx^2,
+// dp dx dy, dp dy^2 -- whose conic terms are applied once per Gaussian, plus
+// d opacity, d rgb, d depth), collected per CTA in shared memory and added to
+// global memory with three float4 atomics per Gaussian per CTA.
 #include <algorithm>
 
 #include "common.cuh"
