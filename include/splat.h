@@ -255,6 +255,64 @@ int splat_render_bwd(const splat_gaussians *g, const splat_projected *proj,
                      size_t ws_bytes, splat_stream_t stream);
 
 /*
+ * splat_project_bwd -- the projection adjoint alone (the second half of
+ * splat_render_bwd): chains screen-space gradients grad2d (device float
+ * [n,12], 16-byte aligned rows: du, dv, d conic a, b, c, d opacity,
+ * d rgb[3], d depth, 2 unused) to the Gaussian parameters (accumulated into
+ * `out`) and, if d_pose is not NULL, to the pose 6-vector (accumulated).
+ * d2d (optional) receives the [n,10] screen-space gradients.  Used after
+ * splat_render_bwd_batch.  Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_project_bwd(const splat_gaussians *g, const splat_projected *proj, const splat_camera *cam,
+                      const float *w2c, const float *grad2d, const splat_gaussians_grad *out,
+                      float *d_pose, float *d2d, splat_stream_t stream);
+
+/*
+ * Several views in one launch (batched differentiable rendering across
+ * agents, Sec. 3.6).  A view bundles one agent's projected map and sorted
+ * lists with its camera and image; views may have different Gaussian counts
+ * and image sizes.  The forward (backward) renders every tile of every view in
+ * ONE persistent launch: (CTAs per SM) x (SMs) CTAs take (view, tile) items
+ * from an atomic ticket counter; no CTA waits on another.  Results equal the
+ * single-view calls (the forward bit for bit).
+ */
+#define SPLAT_MAX_VIEWS 16
+
+typedef struct {
+  splat_projected proj;  /* output of splat_project (device) */
+  const float *rgb;      /* [n,3] Gaussian colours (device) */
+  int64_t n;
+  const uint32_t *vals;  /* sorted ids and tile ranges of splat_bin_sort */
+  const uint32_t *ranges;
+  splat_camera cam;
+  float bg[3];           /* background colour */
+  splat_image image;     /* forward outputs; t_final, n_contrib read back by the backward */
+  const float *d_rgb;    /* backward only: upstream per-pixel gradients (d_depth, d_sil may be NULL) */
+  const float *d_depth;
+  const float *d_sil;
+  float *grad2d;         /* backward only: [n,12] screen-space gradients, 16-byte aligned;
+                            zeroed and filled by splat_render_bwd_batch */
+} splat_view;
+
+/* Execution shape (does not change any result): shared-memory batch of
+ * Gaussians staged per round (64, 128 or 256) and resident CTAs per SM of the
+ * persistent grids. */
+typedef struct {
+  int32_t fwd_batch, fwd_ctas_per_sm;  /* fwd_ctas_per_sm in 1..8  */
+  int32_t bwd_batch, bwd_ctas_per_sm;  /* bwd_ctas_per_sm in 1..16 */
+} splat_batch_shape;
+
+/* Workspace (device, bytes) of the batched calls: the ticket counters. */
+size_t splat_batch_workspace_size(void);
+
+/* Host array `views` of n_views (1..SPLAT_MAX_VIEWS) views; shape may be NULL
+ * (default shape).  Errors: SPLAT_EINVAL, SPLAT_ECUDA. */
+int splat_render_fwd_batch(const splat_view *views, int32_t n_views, const splat_batch_shape *shape,
+                           void *ws, size_t ws_bytes, splat_stream_t stream);
+int splat_render_bwd_batch(const splat_view *views, int32_t n_views, const splat_batch_shape *shape,
+                           void *ws, size_t ws_bytes, splat_stream_t stream);
+
+/*
  * splat_loss_l1 -- the L1 colour and depth terms of Eq. (optim) (Sec. 3.5):
  *   L = w_rgb mean|C - C*| + w_depth mean|D - D*|, sign(0) = 0.
  * Writes dL/dC [npix,3] and dL/dD [npix] (overwritten) and ADDS L to

@@ -124,11 +124,18 @@ class Agent:
         bin_sort(fb, stream, sync_check=sync_check)
         B.splat_render_fwd(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg, stream)
 
-    def step(self, stream=None, sync_check: bool = False):
-        cfg = self.cfg
+    # The step in phases, so that a multi-agent batch can interleave them.
+    def phase_pre(self, s, sync_check: bool = False):
+        """Projection and binning."""
+        project(self.cg, self.w2c, self.fb, s)
+        bin_sort(self.fb, s, sync_check=sync_check)
+
+    def phase_render(self, s):
         fb = self.fb
-        s = torch.cuda.current_stream() if stream is None else stream
-        self.forward(s, sync_check)
+        B.splat_render_fwd(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg, s)
+
+    def phase_loss(self, s):
+        cfg, fb = self.cfg, self.fb
         with torch.cuda.stream(s):
             self.loss.zero_()
             self.d_pose.zero_()
@@ -137,8 +144,19 @@ class Agent:
                     g.zero_()
         B.splat_loss_l1(fb.image["rgb"], fb.image["depth"], self.obs_rgb, self.obs_depth, cfg.w_rgb, cfg.w_depth,
                         self.g_rgb, self.g_depth, self.loss, s)
-        B.splat_render_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.vals, fb.ranges, fb.cimg, cfg.bg, self.g_rgb,
-                           self.g_depth, None, self.cgr, self.d_pose, None, fb.bwd_ws, s)
+
+    def phase_backward(self, s):
+        fb = self.fb
+        B.splat_render_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.vals, fb.ranges, fb.cimg, self.cfg.bg,
+                           self.g_rgb, self.g_depth, None, self.cgr, self.d_pose, None, fb.bwd_ws, s)
+
+    def phase_project_backward(self, s):
+        """Projection adjoint of screen-space gradients already in bwd_ws."""
+        fb = self.fb
+        B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cgr, self.d_pose, None, s)
+
+    def phase_update(self, s):
+        cfg, fb = self.cfg, self.fb
         self.steps_done += 1
         with torch.cuda.stream(s):
             self.t_dev.add_(1)
@@ -154,6 +172,32 @@ class Agent:
             B.splat_assoc(fb.image["max_id"], fb.image["t_final"], self.obs_id, self.obs_tfinal, self.n, self.n,
                           cfg.t_max, self.pairs, self.counts, self.assoc_cap, self.m_dev, self.assoc_status,
                           self.assoc_ws, s)
+
+    def step(self, stream=None, sync_check: bool = False):
+        s = torch.cuda.current_stream() if stream is None else stream
+        self.phase_pre(s, sync_check)
+        self.phase_render(s)
+        self.phase_loss(s)
+        self.phase_backward(s)
+        self.phase_update(s)
+
+    def view(self):
+        """C descriptor of this agent's view for the batched render calls."""
+        fb = self.fb
+        v = B.CView()
+        v.proj = fb.cproj
+        v.rgb = B._p(self.params[4])
+        v.n = self.n
+        v.vals = B._p(fb.vals)
+        v.ranges = B._p(fb.ranges)
+        v.cam = fb.ccam
+        v.bg[0], v.bg[1], v.bg[2] = self.cfg.bg
+        v.image = fb.cimg
+        v.d_rgb = B._p(self.g_rgb)
+        v.d_depth = B._p(self.g_depth)
+        v.d_sil = None
+        v.grad2d = B._p(fb.bwd_ws)
+        return v
 
     # -- episodes ---------------------------------------------------------------
     def _state(self):

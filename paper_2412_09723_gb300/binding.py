@@ -49,6 +49,19 @@ class CImage(ctypes.Structure):
                 ("max_id", _c_p), ("n_used", _c_p)]
 
 
+class CView(ctypes.Structure):
+    _fields_ = [("proj", CProjected), ("rgb", _c_p), ("n", _c_i64), ("vals", _c_p), ("ranges", _c_p),
+                ("cam", CCamera), ("bg", ctypes.c_float * 3), ("image", CImage), ("d_rgb", _c_p), ("d_depth", _c_p),
+                ("d_sil", _c_p), ("grad2d", _c_p)]
+
+
+class CBatchShape(ctypes.Structure):
+    _fields_ = [("fwd_batch", _c_i32), ("fwd_ctas_per_sm", _c_i32), ("bwd_batch", _c_i32),
+                ("bwd_ctas_per_sm", _c_i32)]
+
+
+SPLAT_MAX_VIEWS = 16
+
 _SIGS = {
     "splat_abi_version": ([], _c_i32),
     "splat_last_error": ([], ctypes.c_char_p),
@@ -64,6 +77,10 @@ _SIGS = {
     "splat_render_fwd": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_render_bwd_workspace_size": ([_c_i64], _c_sz),
     "splat_render_bwd": ([_c_p] * 15 + [_c_sz, _c_p], ctypes.c_int),
+    "splat_project_bwd": ([_c_p] * 8 + [_c_p], ctypes.c_int),
+    "splat_batch_workspace_size": ([], _c_sz),
+    "splat_render_fwd_batch": ([_c_p, _c_i32, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
+    "splat_render_bwd_batch": ([_c_p, _c_i32, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
     "splat_loss_l1": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_f, _c_f, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_adam": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_f, _c_f, _c_f, _c_f, _c_p], ctypes.c_int),
     "splat_adam_groups": ([_c_i32, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_f, _c_f, _c_f, _c_i32, _c_p],
@@ -221,6 +238,30 @@ def splat_render_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c,
         ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(vals), _p(ranges),
         ctypes.byref(image), bgc, _p(d_rgb), _p(d_depth), _p(d_sil), ctypes.byref(grads), _p(d_pose), _p(d2d),
         _p(ws), wsb, _stream(stream)))
+
+
+def splat_project_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, grad2d, grads: CGaussiansGrad,
+                      d_pose, d2d=None, stream=None):
+    _check("splat_project_bwd", load().splat_project_bwd(
+        ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(grad2d), ctypes.byref(grads),
+        _p(d_pose), _p(d2d), _stream(stream)))
+
+
+def splat_batch_workspace_size() -> int:
+    return int(load().splat_batch_workspace_size())
+
+
+def splat_render_fwd_batch(views, shape: CBatchShape | None, ws, stream=None):
+    """`views`: ctypes array of CView."""
+    _check("splat_render_fwd_batch", load().splat_render_fwd_batch(
+        views, len(views), None if shape is None else ctypes.byref(shape), _p(ws), ws.numel() * ws.element_size(),
+        _stream(stream)))
+
+
+def splat_render_bwd_batch(views, shape: CBatchShape | None, ws, stream=None):
+    _check("splat_render_bwd_batch", load().splat_render_bwd_batch(
+        views, len(views), None if shape is None else ctypes.byref(shape), _p(ws), ws.numel() * ws.element_size(),
+        _stream(stream)))
 
 
 def splat_loss_l1(rgb, depth, target_rgb, target_depth, w_rgb, w_depth, d_rgb, d_depth, loss, stream=None):

@@ -1,19 +1,20 @@
 // render.cu -- per-tile front-to-back compositing of colour, depth and
 // silhouette (rendering equation of Sec. 3.3; rendered depth of Sec. 3.5) and
-// its back-to-front adjoint.
+// its back-to-front adjoint, for one view per launch or for several views
+// (agents of uneven map sizes, Sec. 3.6) in one persistent launch.
 //
-// Forward: one CTA per 16x16 tile, one thread per pixel.  The tile's list is
-// staged through shared memory in batches of 256 Gaussians (16 B position /
-// depth / opacity, 16 B conic + exponent cut, 12 B colour, 4 B id each) and
-// every thread walks the batch in order.  A pair whose exponent lies below the
-// Gaussian's cut (precomputed by the projection so that opacity * exp(power) <
-// 1/255 is certain) is skipped before the exponential is evaluated; this
-// changes no result.  Blocks leave as soon as every pixel has reached the
-// transmittance stop.  No atomics: the output is deterministic.
+// Forward: 256 threads, one per pixel of a 16x16 tile.  The tile's list is
+// staged through shared memory in batches of BATCH Gaussians (position /
+// depth / opacity, the quadratic form's coefficients A = -a/2, B = -b,
+// C = -c/2 with the exponent cut, colour, id) and every thread walks the batch
+// in order.  A pair whose exponent lies below the Gaussian's cut (set by the
+// projection so that opacity * exp(power) < 1/255 is certain) is skipped before
+// the exponential is evaluated; this changes no result.  A tile ends as soon as
+// all of its pixels have reached the transmittance stop.  No atomics.
 //
-// Backward: same tiling, 128 threads with 2 pixels each ((x, y) and
-// (x, y + 2); a warp covers 16 x 4 pixels).  Every pixel starts from its final
-// transmittance and last contributor, walks the list back to front, recovers
+// Backward: 128 threads with 2 pixels each ((x, y) and (x, y + 2); a warp
+// covers 16 x 4 pixels).  Every pixel starts from its final transmittance and
+// last contributor, walks the list back to front, recovers
 // T_i = T_{i+1} / (1 - alpha_i), and keeps the suffix sums
 // R_X <- X_i alpha_i + (1 - alpha_i) R_X of colour, depth and silhouette, so
 // dL/dalpha_i = T_i [gC.(c_i - R_C) + gD (z_i - R_D) + gS (1 - R_S)]
@@ -23,6 +24,10 @@
 // dp dx dy, dp dy^2 -- whose conic terms are applied once per Gaussian, plus
 // d opacity, d rgb, d depth), collected per CTA in shared memory and added to
 // global memory with three float4 atomics per Gaussian per CTA.
+//
+// Persistent launches: a grid of (CTAs per SM) x (SMs) CTAs takes (view, tile)
+// work items from one atomic ticket counter until the items run out; no CTA
+// ever waits on another.
 #include <algorithm>
 
 #include "common.cuh"
@@ -30,10 +35,11 @@
 
 namespace splat {
 
-constexpr int kBatch = 256;
-constexpr int kThreads = 128;  // backward: 2 pixels per thread, (x, y) and (x, y + 2)
-constexpr int kGradStride = 12;  // internal screen-space gradient row (3 float4)
-constexpr int kAccStride = 11;   // shared accumulator row (10 sums, padded against bank conflicts)
+constexpr int kFwdThreads = kTilePixels;  // forward: one pixel per thread
+constexpr int kBwdThreads = 128;          // backward: two pixels per thread
+constexpr int kGradStride = 12;           // screen-space gradient row (3 float4)
+constexpr int kAccStride = 11;            // shared accumulator row (10 sums, padded)
+constexpr int kMaxViews = SPLAT_MAX_VIEWS;
 
 struct ImageK {
   float* rgb;
@@ -45,13 +51,50 @@ struct ImageK {
   int32_t* n_used;
 };
 
-// Pixel coordinates of thread t's two pixels: warp w covers rows 4w .. 4w+3.
-__device__ __forceinline__ void pixel_of(int t, int p, int& lx, int& ly) {
-  const int lane = t & 31, warp = t >> 5;
-  lx = lane & 15;
-  ly = 4 * warp + (lane >> 4) + 2 * p;
+struct ViewK {
+  const float4* xyzo;
+  const float4* conic;
+  const float* rgb;
+  const uint32_t* vals;
+  const uint2* ranges;
+  CamK cam;
+  float bg0, bg1, bg2;
+  ImageK img;
+  const float* d_rgb;
+  const float* d_depth;
+  const float* d_sil;
+  float* g2;
+};
+
+struct ViewTable {
+  ViewK v[kMaxViews];
+  int tile_end[kMaxViews];  // inclusive prefix of the views' tile counts
+  int n;
+};
+
+// Shared-memory staging of one batch of Gaussians.
+template <int BATCH>
+struct Stage {
+  float4 xyzo[BATCH];
+  float4 quad[BATCH];  // A = -a/2, B = -b, C = -c/2, exponent cut
+  float rgb[3 * BATCH];
+  int32_t id[BATCH];
+};
+
+__device__ __forceinline__ void stage_one(const ViewK& V, uint32_t g, int i, float4* xyzo, float4* quad, float* rgb,
+                                          int32_t* id) {
+  const float4 co = V.conic[g];
+  id[i] = (int32_t)g;
+  xyzo[i] = V.xyzo[g];
+  quad[i] = make_float4(-0.5f * co.x, -co.y, -0.5f * co.z, co.w);
+  rgb[3 * i + 0] = V.rgb[3 * (size_t)g + 0];
+  rgb[3 * i + 1] = V.rgb[3 * (size_t)g + 1];
+  rgb[3 * i + 2] = V.rgb[3 * (size_t)g + 2];
 }
 
+// ----------------------------------------------------------------------------
+// Forward
+// ----------------------------------------------------------------------------
 struct FwdPix {
   float T, C0, C1, C2, D, S, wmax;
   int32_t id, last, used;
@@ -59,15 +102,12 @@ struct FwdPix {
 };
 
 // One front-to-back compositing step of one pixel (the specified order).
-__device__ __forceinline__ void composite_step(FwdPix& q, const float4 xo, const float4 co, float fx, float fy,
+__device__ __forceinline__ void composite_step(FwdPix& q, const float4 xo, const float4 qd, float fx, float fy,
                                                const float* c, int32_t gid, int32_t pos) {
   const float dx = xo.x - fx;
   const float dy = xo.y - fy;
-  const float A = -0.5f * co.x;
-  const float B = -co.y;
-  const float Cc = -0.5f * co.z;
-  const float power = __fmaf_rn(Cc * dy, dy, dx * __fmaf_rn(A, dx, B * dy));
-  if (power > 0.0f || power < co.w) return;
+  const float power = __fmaf_rn(qd.z * dy, dy, dx * __fmaf_rn(qd.x, dx, qd.y * dy));
+  if (power > 0.0f || power < qd.w) return;
   const float G = exp_core(power);
   const float alpha = fminf(kAlphaCap, xo.w * G);
   if (alpha < kAlphaMin) return;
@@ -91,53 +131,69 @@ __device__ __forceinline__ void composite_step(FwdPix& q, const float4 xo, const
   ++q.used;
 }
 
-__global__ void __launch_bounds__(kTilePixels) render_fwd_kernel(const float4* __restrict__ xyzo,
-                                                                 const float4* __restrict__ conic,
-                                                                 const float* __restrict__ rgb,
-                                                                 const uint32_t* __restrict__ vals,
-                                                                 const uint2* __restrict__ ranges, CamK cam,
-                                                                 float bg0, float bg1, float bg2, ImageK out) {
-  __shared__ float4 s_xyzo[kBatch];
-  __shared__ float4 s_con[kBatch];
-  __shared__ float s_rgb[3 * kBatch];
-  __shared__ int32_t s_id[kBatch];
-  const int tile = blockIdx.x;
+template <int BATCH>
+__device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>& sm) {
+  const CamK& cam = V.cam;
   const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
   const int px = tx * kTile + (threadIdx.x & (kTile - 1));
   const int py = ty * kTile + (threadIdx.x >> 4);
   const bool inside = px < cam.width && py < cam.height;
   const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
   FwdPix q{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, 0, 0, !inside};
-  const uint2 rg = ranges[tile];
-  for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
-    if (__syncthreads_count(q.done) == kTilePixels) break;
-    const uint32_t idx = start + threadIdx.x;
-    if (idx < rg.y) {
-      const uint32_t g = vals[idx];
-      s_id[threadIdx.x] = (int32_t)g;
-      s_xyzo[threadIdx.x] = xyzo[g];
-      s_con[threadIdx.x] = conic[g];
-      s_rgb[3 * threadIdx.x + 0] = rgb[3 * (size_t)g + 0];
-      s_rgb[3 * threadIdx.x + 1] = rgb[3 * (size_t)g + 1];
-      s_rgb[3 * threadIdx.x + 2] = rgb[3 * (size_t)g + 2];
-    }
+  const uint2 rg = V.ranges[tile];
+  for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
+    if (__syncthreads_count(q.done) == kFwdThreads) break;
+    if (threadIdx.x < BATCH && start + threadIdx.x < rg.y)
+      stage_one(V, V.vals[start + threadIdx.x], threadIdx.x, sm.xyzo, sm.quad, sm.rgb, sm.id);
     __syncthreads();
-    const int cnt = (int)min((uint32_t)kBatch, rg.y - start);
+    const int cnt = (int)min((uint32_t)BATCH, rg.y - start);
     const int32_t base = (int32_t)(start - rg.x);
     for (int j = 0; j < cnt && !q.done; ++j)
-      composite_step(q, s_xyzo[j], s_con[j], fx, fy, &s_rgb[3 * j], s_id[j], base + j);
+      composite_step(q, sm.xyzo[j], sm.quad[j], fx, fy, &sm.rgb[3 * j], sm.id[j], base + j);
   }
   if (!inside) return;
   const size_t i = (size_t)py * cam.width + px;
-  out.rgb[3 * i + 0] = __fmaf_rn(q.T, bg0, q.C0);
-  out.rgb[3 * i + 1] = __fmaf_rn(q.T, bg1, q.C1);
-  out.rgb[3 * i + 2] = __fmaf_rn(q.T, bg2, q.C2);
-  out.depth[i] = q.D;
-  out.sil[i] = q.S;
-  out.t_final[i] = q.T;
-  out.n_contrib[i] = q.last;
-  out.max_id[i] = q.id;
-  if (out.n_used) out.n_used[i] = q.used;
+  V.img.rgb[3 * i + 0] = __fmaf_rn(q.T, V.bg0, q.C0);
+  V.img.rgb[3 * i + 1] = __fmaf_rn(q.T, V.bg1, q.C1);
+  V.img.rgb[3 * i + 2] = __fmaf_rn(q.T, V.bg2, q.C2);
+  V.img.depth[i] = q.D;
+  V.img.sil[i] = q.S;
+  V.img.t_final[i] = q.T;
+  V.img.n_contrib[i] = q.last;
+  V.img.max_id[i] = q.id;
+  if (V.img.n_used) V.img.n_used[i] = q.used;
+}
+
+template <int BATCH>
+__global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(ViewK V) {
+  __shared__ Stage<BATCH> sm;
+  fwd_tile<BATCH>(V, blockIdx.x, sm);
+}
+
+// Work item -> (view, tile).
+__device__ __forceinline__ int view_of(const ViewTable& T, int item, int& tile) {
+  int v = 0;
+  while (v + 1 < T.n && item >= T.tile_end[v]) ++v;
+  tile = item - (v ? T.tile_end[v - 1] : 0);
+  return v;
+}
+
+__device__ __forceinline__ int next_item(int* counter, int* s_item) {
+  __syncthreads();  // every thread is done with the previous item's shared memory
+  if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+  __syncthreads();
+  return *s_item;
+}
+
+template <int BATCH>
+__global__ void __launch_bounds__(kFwdThreads) render_fwd_persistent(ViewTable T, int total, int* counter) {
+  __shared__ Stage<BATCH> sm;
+  __shared__ int s_item;
+  for (int item = next_item(counter, &s_item); item < total; item = next_item(counter, &s_item)) {
+    int tile;
+    const int v = view_of(T, item, tile);
+    fwd_tile<BATCH>(T.v[v], tile, sm);
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -184,28 +240,25 @@ __device__ __forceinline__ int warp_reduce_scatter10(const float (&v)[10], float
 }
 
 struct BwdPix {
-  float fx, fy, T, Tfin, gC0, gC1, gC2, gD, gS, gbgT, R0, R1, R2, RD, RS;
+  float fx, fy, T, gC0, gC1, gC2, gD, gS, gbgT, R0, R1, R2, RD, RS;
   int last;
 };
 
 // Per-pixel adjoint of one list position (back to front).  Accumulates the
 // pixel's share of (sum dp dx, sum dp dy, sum dp dx^2, sum dp dx dy, sum dp
 // dy^2, d opacity, d rgb[3], d depth) into v, dp = dL/d(power).
-__device__ __forceinline__ bool adjoint_step(BwdPix& q, const float4 xo, const float4 co, float c0, float c1,
+__device__ __forceinline__ bool adjoint_step(BwdPix& q, const float4 xo, const float4 qd, float c0, float c1,
                                              float c2, float (&v)[10]) {
   const float dx = xo.x - q.fx;
   const float dy = xo.y - q.fy;
-  const float A = -0.5f * co.x;
-  const float B = -co.y;
-  const float Cc = -0.5f * co.z;
-  const float power = __fmaf_rn(Cc * dy, dy, dx * __fmaf_rn(A, dx, B * dy));
-  if (power > 0.0f || power < co.w) return false;
+  const float power = __fmaf_rn(qd.z * dy, dy, dx * __fmaf_rn(qd.x, dx, qd.y * dy));
+  if (power > 0.0f || power < qd.w) return false;
   const float G = exp_core(power);
   const float raw = xo.w * G;
   const float alpha = fminf(kAlphaCap, raw);
   if (alpha < kAlphaMin) return false;
   const float om = 1.0f - alpha;
-  const float r = __frcp_rn(om);
+  const float r = __fdividef(1.0f, om);
   q.T = q.T * r;  // T_i
   const float w = alpha * q.T;
   v[6] = __fmaf_rn(q.gC0, w, v[6]);
@@ -236,91 +289,90 @@ __device__ __forceinline__ bool adjoint_step(BwdPix& q, const float4 xo, const f
   return true;
 }
 
-__global__ void __launch_bounds__(kThreads) render_bwd_kernel(
-    const float4* __restrict__ xyzo, const float4* __restrict__ conic, const float* __restrict__ rgb,
-    const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges, CamK cam, float bg0, float bg1, float bg2,
-    const float* __restrict__ t_final, const int32_t* __restrict__ n_contrib, const float* __restrict__ d_rgb,
-    const float* __restrict__ d_depth, const float* __restrict__ d_sil, float* __restrict__ g2) {
-  __shared__ float4 s_xyzo[kBatch];
-  __shared__ float4 s_con[kBatch];
-  __shared__ float s_rgb[3 * kBatch];
-  __shared__ int32_t s_id[kBatch];
-  __shared__ float s_acc[kBatch * kAccStride];
-  __shared__ int s_maxlast;
-  const int tile = blockIdx.x;
+template <int BATCH>
+struct BwdShared {
+  Stage<BATCH> st;
+  float acc[BATCH * kAccStride];
+  int maxlast;
+};
+
+// Pixel p (0 or 1) of thread t: warp w covers rows 4w .. 4w+3.
+__device__ __forceinline__ void bwd_pixel(int t, int p, int& lx, int& ly) {
+  const int lane = t & 31, warp = t >> 5;
+  lx = lane & 15;
+  ly = 4 * warp + (lane >> 4) + 2 * p;
+}
+
+template <int BATCH>
+__device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BATCH>& sm) {
+  const CamK& cam = V.cam;
   const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-  const uint2 rg = ranges[tile];
+  const uint2 rg = V.ranges[tile];
   BwdPix q[2];
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     int lx, ly;
-    pixel_of(threadIdx.x, p, lx, ly);
+    bwd_pixel(threadIdx.x, p, lx, ly);
     const int x = tx * kTile + lx, y = ty * kTile + ly;
     const bool inside = x < cam.width && y < cam.height;
     const size_t i = inside ? (size_t)y * cam.width + x : 0;
     BwdPix& b = q[p];
     b.fx = (float)x + 0.5f;
     b.fy = (float)y + 0.5f;
-    b.Tfin = inside ? t_final[i] : 1.0f;
-    b.T = b.Tfin;
-    b.last = inside ? n_contrib[i] : 0;
-    b.gC0 = inside ? d_rgb[3 * i + 0] : 0.f;
-    b.gC1 = inside ? d_rgb[3 * i + 1] : 0.f;
-    b.gC2 = inside ? d_rgb[3 * i + 2] : 0.f;
-    b.gD = (inside && d_depth) ? d_depth[i] : 0.f;
-    b.gS = (inside && d_sil) ? d_sil[i] : 0.f;
-    b.gbgT = (b.gC0 * bg0 + b.gC1 * bg1 + b.gC2 * bg2) * b.Tfin;
+    const float Tfin = inside ? V.img.t_final[i] : 1.0f;
+    b.T = Tfin;
+    b.last = inside ? V.img.n_contrib[i] : 0;
+    b.gC0 = inside ? V.d_rgb[3 * i + 0] : 0.f;
+    b.gC1 = inside ? V.d_rgb[3 * i + 1] : 0.f;
+    b.gC2 = inside ? V.d_rgb[3 * i + 2] : 0.f;
+    b.gD = (inside && V.d_depth) ? V.d_depth[i] : 0.f;
+    b.gS = (inside && V.d_sil) ? V.d_sil[i] : 0.f;
+    b.gbgT = (b.gC0 * V.bg0 + b.gC1 * V.bg1 + b.gC2 * V.bg2) * Tfin;
     b.R0 = b.R1 = b.R2 = b.RD = b.RS = 0.f;
   }
   const int lane = threadIdx.x & 31;
   const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(q[0].last, q[1].last));
-  if (threadIdx.x == 0) s_maxlast = 0;
+  if (threadIdx.x == 0) sm.maxlast = 0;
   __syncthreads();
-  if (lane == 0 && wlast > 0) atomicMax(&s_maxlast, wlast);
+  if (lane == 0 && wlast > 0) atomicMax(&sm.maxlast, wlast);
   __syncthreads();
-  const int maxlast = s_maxlast;
-  for (int end = maxlast; end > 0; end -= kBatch) {
-    const int start = max(0, end - kBatch);
+  const int maxlast = sm.maxlast;
+  for (int end = maxlast; end > 0; end -= BATCH) {
+    const int start = max(0, end - BATCH);
     const int cnt = end - start;
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += kThreads) {
-      const uint32_t g = vals[rg.x + start + i];
-      s_id[i] = (int32_t)g;
-      s_xyzo[i] = xyzo[g];
-      s_con[i] = conic[g];
-      s_rgb[3 * i + 0] = rgb[3 * (size_t)g + 0];
-      s_rgb[3 * i + 1] = rgb[3 * (size_t)g + 1];
-      s_rgb[3 * i + 2] = rgb[3 * (size_t)g + 2];
-    }
-    for (int i = threadIdx.x; i < kBatch * kAccStride; i += kThreads) s_acc[i] = 0.f;
+    for (int i = threadIdx.x; i < cnt; i += kBwdThreads)
+      stage_one(V, V.vals[rg.x + start + i], i, sm.st.xyzo, sm.st.quad, sm.st.rgb, sm.st.id);
+    for (int i = threadIdx.x; i < BATCH * kAccStride; i += kBwdThreads) sm.acc[i] = 0.f;
     __syncthreads();
     for (int j = cnt - 1; j >= 0; --j) {
       const int pos = start + j;
       if (pos >= wlast) continue;  // warp-uniform: no pixel of this warp reaches pos
-      const float4 xo = s_xyzo[j];
-      const float4 co = s_con[j];
-      const float c0 = s_rgb[3 * j + 0], c1 = s_rgb[3 * j + 1], c2 = s_rgb[3 * j + 2];
+      const float4 xo = sm.st.xyzo[j];
+      const float4 qd = sm.st.quad[j];
+      const float c0 = sm.st.rgb[3 * j + 0], c1 = sm.st.rgb[3 * j + 1], c2 = sm.st.rgb[3 * j + 2];
       float v[10];
 #pragma unroll
       for (int k = 0; k < 10; ++k) v[k] = 0.f;
       bool any = false;
 #pragma unroll
       for (int p = 0; p < 2; ++p)
-        if (pos < q[p].last) any |= adjoint_step(q[p], xo, co, c0, c1, c2, v);
+        if (pos < q[p].last) any |= adjoint_step(q[p], xo, qd, c0, c1, c2, v);
       if (__any_sync(0xffffffffu, any)) {
         float tot;
         const int k = warp_reduce_scatter10(v, tot);
-        if (k >= 0 && tot != 0.f) atomicAdd(&s_acc[j * kAccStride + k], tot);
+        if (k >= 0 && tot != 0.f) atomicAdd(&sm.acc[j * kAccStride + k], tot);
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += kThreads) {
-      const float* a = &s_acc[i * kAccStride];
-      const float4 co = s_con[i];
-      const float4 u0 = make_float4(-(co.x * a[0] + co.y * a[1]), -(co.y * a[0] + co.z * a[1]), -0.5f * a[2], -a[3]);
+    for (int i = threadIdx.x; i < cnt; i += kBwdThreads) {
+      const float* a = &sm.acc[i * kAccStride];
+      const float4 qd = sm.st.quad[i];
+      const float ca = -2.0f * qd.x, cb = -qd.y, cc = -2.0f * qd.z;  // the conic a, b, c (exact)
+      const float4 u0 = make_float4(-(ca * a[0] + cb * a[1]), -(cb * a[0] + cc * a[1]), -0.5f * a[2], -a[3]);
       const float4 u1 = make_float4(-0.5f * a[4], a[5], a[6], a[7]);
       const float4 u2 = make_float4(a[8], a[9], 0.f, 0.f);
-      float4* dst = reinterpret_cast<float4*>(g2 + kGradStride * (size_t)s_id[i]);
+      float4* dst = reinterpret_cast<float4*>(V.g2 + kGradStride * (size_t)sm.st.id[i]);
       if (u0.x != 0.f || u0.y != 0.f || u0.z != 0.f || u0.w != 0.f) atomicAdd(dst, u0);
       if (u1.x != 0.f || u1.y != 0.f || u1.z != 0.f || u1.w != 0.f) atomicAdd(dst + 1, u1);
       if (u2.x != 0.f || u2.y != 0.f) atomicAdd(dst + 2, u2);
@@ -328,31 +380,76 @@ __global__ void __launch_bounds__(kThreads) render_bwd_kernel(
   }
 }
 
-}  // namespace splat
+template <int BATCH>
+__global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(ViewK V) {
+  __shared__ BwdShared<BATCH> sm;
+  bwd_tile<BATCH>(V, blockIdx.x, sm);
+}
 
-using namespace splat;
+template <int BATCH>
+__global__ void __launch_bounds__(kBwdThreads) render_bwd_persistent(ViewTable T, int total, int* counter) {
+  __shared__ BwdShared<BATCH> sm;
+  __shared__ int s_item;
+  for (int item = next_item(counter, &s_item); item < total; item = next_item(counter, &s_item)) {
+    int tile;
+    const int v = view_of(T, item, tile);
+    bwd_tile<BATCH>(T.v[v], tile, sm);
+  }
+}
 
+// ----------------------------------------------------------------------------
+// Host side
+// ----------------------------------------------------------------------------
 static int check_proj(const splat_projected* proj, int64_t n, const char* who) {
   if (!proj || (n > 0 && (!proj->xyzo || !proj->conic)) || !aligned16(proj->xyzo) || !aligned16(proj->conic))
     return fail(SPLAT_EINVAL, "%s: projected arrays null or not 16-byte aligned", who);
   return SPLAT_OK;
 }
 
+static bool image_ok(const splat_image& im) {
+  return im.rgb && im.depth && im.sil && im.t_final && im.n_contrib && im.max_id;
+}
+
+static ViewK make_view(const splat_projected& proj, const float* rgb, const uint32_t* vals, const uint32_t* ranges,
+                       const splat_camera& cam, const float* bg, const splat_image& im) {
+  ViewK v;
+  v.xyzo = reinterpret_cast<const float4*>(proj.xyzo);
+  v.conic = reinterpret_cast<const float4*>(proj.conic);
+  v.rgb = rgb;
+  v.vals = vals;
+  v.ranges = reinterpret_cast<const uint2*>(ranges);
+  v.cam = make_camk(cam);
+  v.bg0 = bg[0];
+  v.bg1 = bg[1];
+  v.bg2 = bg[2];
+  v.img = ImageK{im.rgb, im.depth, im.sil, im.t_final, im.n_contrib, im.max_id, im.n_used};
+  v.d_rgb = v.d_depth = v.d_sil = nullptr;
+  v.g2 = nullptr;
+  return v;
+}
+
+static int sm_count() {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+}  // namespace splat
+
+using namespace splat;
+
 extern "C" int splat_render_fwd(const splat_projected* proj, const float* rgb, int64_t n, const uint32_t* vals,
                                 const uint32_t* ranges, const splat_camera* cam, const float* bg,
                                 const splat_image* out, splat_stream_t stream) {
   int rc = check_proj(proj, n, "splat_render_fwd");
   if (rc) return rc;
-  if ((n > 0 && !rgb) || !vals || !ranges || !cam || !bg || !out || !out->rgb || !out->depth || !out->sil || !out->t_final ||
-      !out->n_contrib || !out->max_id)
+  if ((n > 0 && !rgb) || !vals || !ranges || !cam || !bg || !out || !image_ok(*out))
     return fail(SPLAT_EINVAL, "splat_render_fwd: null argument");
   if (n < 0 || cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "splat_render_fwd: bad sizes");
-  const CamK ck = make_camk(*cam);
-  ImageK im{out->rgb, out->depth, out->sil, out->t_final, out->n_contrib, out->max_id, out->n_used};
+  const ViewK v = make_view(*proj, rgb, vals, ranges, *cam, bg, *out);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  SPLAT_LAUNCH("render_fwd_kernel", s, render_fwd_kernel<<<ck.tiles_x * ck.tiles_y, kTilePixels, 0, s>>>(
-      reinterpret_cast<const float4*>(proj->xyzo), reinterpret_cast<const float4*>(proj->conic), rgb, vals,
-      reinterpret_cast<const uint2*>(ranges), ck, bg[0], bg[1], bg[2], im));
+  SPLAT_LAUNCH("render_fwd_kernel", s,
+               render_fwd_kernel<256><<<v.cam.tiles_x * v.cam.tiles_y, kFwdThreads, 0, s>>>(v));
   return check_launch("render_fwd_kernel");
 }
 
@@ -380,13 +477,136 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (g->n > 0 && cudaMemsetAsync(g2, 0, sizeof(float) * kGradStride * (size_t)g->n, s) != cudaSuccess)
     return fail(SPLAT_ECUDA, "splat_render_bwd: memset failed");
-  const CamK ck = make_camk(*cam);
-  SPLAT_LAUNCH("render_bwd_kernel", s, render_bwd_kernel<<<ck.tiles_x * ck.tiles_y, kThreads, 0, s>>>(
-      reinterpret_cast<const float4*>(proj->xyzo), reinterpret_cast<const float4*>(proj->conic), g->rgb, vals,
-      reinterpret_cast<const uint2*>(ranges), ck, bg[0], bg[1], bg[2], fwd->t_final, fwd->n_contrib, d_rgb, d_depth,
-      d_sil, g2));
+  ViewK v = make_view(*proj, g->rgb, vals, ranges, *cam, bg, *fwd);
+  v.d_rgb = d_rgb;
+  v.d_depth = d_depth;
+  v.d_sil = d_sil;
+  v.g2 = g2;
+  SPLAT_LAUNCH("render_bwd_kernel", s,
+               render_bwd_kernel<256><<<v.cam.tiles_x * v.cam.tiles_y, kBwdThreads, 0, s>>>(v));
   if ((rc = check_launch("render_bwd_kernel"))) return rc;
   GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
   GradK gr{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};
-  return launch_project_bwd(gk, ck, w2c, proj->conic, g2, kGradStride, gr, d_pose, d2d, s);
+  return launch_project_bwd(gk, v.cam, w2c, proj->conic, g2, kGradStride, gr, d_pose, d2d, s);
+}
+
+extern "C" int splat_project_bwd(const splat_gaussians* g, const splat_projected* proj, const splat_camera* cam,
+                                 const float* w2c, const float* grad2d, const splat_gaussians_grad* out,
+                                 float* d_pose, float* d2d, splat_stream_t stream) {
+  if (!g || !cam || !w2c || !grad2d || !out) return fail(SPLAT_EINVAL, "splat_project_bwd: null argument");
+  int rc = check_proj(proj, g->n, "splat_project_bwd");
+  if (rc) return rc;
+  if (g->n < 0 || (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !out->mean ||
+                                !out->log_scale || !out->quat || !out->opacity_logit || !out->rgb)) ||
+      !aligned16(g->quat) || !aligned16(grad2d))
+    return fail(SPLAT_EINVAL, "splat_project_bwd: bad gaussian or gradient arrays");
+  GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
+  GradK gr{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};
+  return launch_project_bwd(gk, make_camk(*cam), w2c, proj->conic, grad2d, kGradStride, gr, d_pose, d2d,
+                            reinterpret_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// Several views in one persistent launch
+// ---------------------------------------------------------------------------
+static int build_table(const splat_view* views, int32_t n_views, bool bwd, ViewTable* T, int* total,
+                       const char* who) {
+  if (!views || n_views < 1 || n_views > kMaxViews)
+    return fail(SPLAT_EINVAL, "%s: n_views must be in 1..%d", who, kMaxViews);
+  int acc = 0;
+  for (int i = 0; i < n_views; ++i) {
+    const splat_view& w = views[i];
+    if (check_proj(&w.proj, w.n, who) || w.n < 0 || (w.n > 0 && !w.rgb) || !w.vals || !w.ranges ||
+        w.cam.width <= 0 || w.cam.height <= 0 || !image_ok(w.image))
+      return fail(SPLAT_EINVAL, "%s: view %d is incomplete", who, i);
+    if (bwd && (!w.d_rgb || !w.grad2d || !aligned16(w.grad2d)))
+      return fail(SPLAT_EINVAL, "%s: view %d lacks d_rgb or a 16-byte aligned grad2d", who, i);
+    ViewK v = make_view(w.proj, w.rgb, w.vals, w.ranges, w.cam, w.bg, w.image);
+    v.d_rgb = w.d_rgb;
+    v.d_depth = w.d_depth;
+    v.d_sil = w.d_sil;
+    v.g2 = w.grad2d;
+    T->v[i] = v;
+    acc += v.cam.tiles_x * v.cam.tiles_y;
+    T->tile_end[i] = acc;
+  }
+  T->n = n_views;
+  *total = acc;
+  return SPLAT_OK;
+}
+
+static splat_batch_shape default_shape() { return splat_batch_shape{256, 4, 256, 7}; }
+
+static bool shape_ok(const splat_batch_shape& sh) {
+  auto b = [](int x) { return x == 64 || x == 128 || x == 256; };
+  return b(sh.fwd_batch) && b(sh.bwd_batch) && sh.fwd_ctas_per_sm >= 1 && sh.fwd_ctas_per_sm <= 8 &&
+         sh.bwd_ctas_per_sm >= 1 && sh.bwd_ctas_per_sm <= 16;
+}
+
+extern "C" size_t splat_batch_workspace_size(void) { return 256; }
+
+extern "C" int splat_render_fwd_batch(const splat_view* views, int32_t n_views, const splat_batch_shape* shape,
+                                      void* ws, size_t ws_bytes, splat_stream_t stream) {
+  ViewTable T;
+  int total = 0;
+  int rc = build_table(views, n_views, false, &T, &total, "splat_render_fwd_batch");
+  if (rc) return rc;
+  const splat_batch_shape sh = shape ? *shape : default_shape();
+  if (!shape_ok(sh)) return fail(SPLAT_EINVAL, "splat_render_fwd_batch: unsupported shape");
+  if (!ws || ws_bytes < splat_batch_workspace_size()) return fail(SPLAT_EINVAL, "splat_render_fwd_batch: workspace");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int* counter = static_cast<int*>(ws);
+  if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess)
+    return fail(SPLAT_ECUDA, "splat_render_fwd_batch: memset failed");
+  const int grid = std::min(total, sh.fwd_ctas_per_sm * sm_count());
+  if (grid <= 0) return SPLAT_OK;
+  switch (sh.fwd_batch) {
+    case 64:
+      SPLAT_LAUNCH("render_fwd_persistent", s,
+                   render_fwd_persistent<64><<<grid, kFwdThreads, 0, s>>>(T, total, counter));
+      break;
+    case 128:
+      SPLAT_LAUNCH("render_fwd_persistent", s,
+                   render_fwd_persistent<128><<<grid, kFwdThreads, 0, s>>>(T, total, counter));
+      break;
+    default:
+      SPLAT_LAUNCH("render_fwd_persistent", s,
+                   render_fwd_persistent<256><<<grid, kFwdThreads, 0, s>>>(T, total, counter));
+  }
+  return check_launch("render_fwd_persistent");
+}
+
+extern "C" int splat_render_bwd_batch(const splat_view* views, int32_t n_views, const splat_batch_shape* shape,
+                                      void* ws, size_t ws_bytes, splat_stream_t stream) {
+  ViewTable T;
+  int total = 0;
+  int rc = build_table(views, n_views, true, &T, &total, "splat_render_bwd_batch");
+  if (rc) return rc;
+  const splat_batch_shape sh = shape ? *shape : default_shape();
+  if (!shape_ok(sh)) return fail(SPLAT_EINVAL, "splat_render_bwd_batch: unsupported shape");
+  if (!ws || ws_bytes < splat_batch_workspace_size()) return fail(SPLAT_EINVAL, "splat_render_bwd_batch: workspace");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int* counter = static_cast<int*>(ws) + 1;
+  if (cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess)
+    return fail(SPLAT_ECUDA, "splat_render_bwd_batch: memset failed");
+  for (int i = 0; i < n_views; ++i)
+    if (views[i].n > 0 &&
+        cudaMemsetAsync(views[i].grad2d, 0, sizeof(float) * kGradStride * (size_t)views[i].n, s) != cudaSuccess)
+      return fail(SPLAT_ECUDA, "splat_render_bwd_batch: memset failed");
+  const int grid = std::min(total, sh.bwd_ctas_per_sm * sm_count());
+  if (grid <= 0) return SPLAT_OK;
+  switch (sh.bwd_batch) {
+    case 64:
+      SPLAT_LAUNCH("render_bwd_persistent", s,
+                   render_bwd_persistent<64><<<grid, kBwdThreads, 0, s>>>(T, total, counter));
+      break;
+    case 128:
+      SPLAT_LAUNCH("render_bwd_persistent", s,
+                   render_bwd_persistent<128><<<grid, kBwdThreads, 0, s>>>(T, total, counter));
+      break;
+    default:
+      SPLAT_LAUNCH("render_bwd_persistent", s,
+                   render_bwd_persistent<256><<<grid, kBwdThreads, 0, s>>>(T, total, counter));
+  }
+  return check_launch("render_bwd_persistent");
 }

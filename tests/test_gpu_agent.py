@@ -65,3 +65,61 @@ def test_tracking_reduces_pose_error(dev):
     assert a.status() == 0
     assert l1 < 0.7 * l0
     assert e1 < e0
+
+
+def _agents(dev, sizes, cams, **cfg):
+    from paper_2412_09723_gb300.agent import Agent, StepConfig
+
+    out = []
+    for i, (n, cam) in enumerate(zip(sizes, cams)):
+        sc = scenes.scene_room(n, 30 + i)
+        w2c = scenes.perturbed_w2c(40 + i, 0.05, 3.0)
+        a = Agent(sc, w2c, cam, dev, cfg=StepConfig(**cfg))
+        a.render_observation_from(scenes.perturbed_w2c(50 + i, 0.01, 0.5, base=w2c))
+        a.size_capacity(1.5)
+        out.append(a)
+    return out
+
+
+SIZES = (15000, 40000, 90000)
+CAMS = (scenes.Camera(320, 240, 262.5, 262.5, 160.0, 120.0), scenes.Camera(400, 300, 300.0, 300.0, 200.0, 150.0),
+        scenes.Camera(600, 340, 300.0, 300.0, 300.0, 170.0))
+
+
+def test_batched_step_equals_single_agent_steps(dev):
+    from paper_2412_09723_gb300.batch import MultiAgentBatch
+
+    solo = _agents(dev, SIZES, CAMS, map=False, track=False)
+    mine = _agents(dev, SIZES, CAMS, map=False, track=False)
+    for a in solo:
+        a.step()
+    batch = MultiAgentBatch(mine, shape=(128, 4, 128, 7))
+    batch.step()
+    torch.cuda.synchronize()
+    for a, b in zip(solo, mine):
+        for k in ("rgb", "depth", "sil", "t_final", "n_contrib", "max_id"):
+            assert torch.equal(a.fb.image[k], b.fb.image[k]), k
+        for ga, gb in zip(a.grads, b.grads):
+            ref = ga.double()
+            tol = 1e-3 * float(ref.pow(2).mean().sqrt()) + 1e-3 * ref.abs()
+            assert bool(((ga.double() - gb.double()).abs() <= tol).all())
+        assert torch.allclose(a.d_pose, b.d_pose, rtol=1e-3, atol=1e-3 * float(a.d_pose.abs().max()))
+    # the captured graph of the batch replays the same forward
+    batch.capture()
+    batch.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(solo, mine):
+        assert torch.equal(a.fb.image["max_id"], b.fb.image["max_id"])
+    assert batch.status() == 0
+
+
+def test_autotune_picks_a_candidate(dev, tmp_path):
+    from paper_2412_09723_gb300.batch import MultiAgentBatch
+
+    agents = _agents(dev, SIZES[:2], CAMS[:2])
+    batch = MultiAgentBatch(agents)
+    cands = [(128, 4, 128, 7), (256, 2, 256, 4)]
+    entry = batch.autotune(candidates=cands, reps=2, cache_path=str(tmp_path / "tune.json"))
+    assert tuple(entry["shape"]) in cands and len(entry["tried"]) == 2
+    again = batch.autotune(candidates=cands, reps=2, cache_path=str(tmp_path / "tune.json"))
+    assert again["shape"] == entry["shape"]
