@@ -60,6 +60,7 @@ def _parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel timing pass (no roofline)")
     ap.add_argument("--eager", action="store_true", help="time eager launches instead of CUDA-graph replays")
+    ap.add_argument("--no-multi", action="store_true", help="skip the batched multi-agent comparison")
     return ap.parse_args()
 
 
@@ -254,6 +255,69 @@ def _traffic_for(kernel):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def multi_agent_section(dev, steps, flush, seed_base=2):
+    """Three agents with 150k / 400k / 900k-Gaussian room maps at 1200x680
+    (fx = fy = 600): the batched step (one persistent forward and one
+    persistent backward launch over all agents, autotuned shape, one CUDA graph)
+    against the plain per-request path (each agent's own single-view graph,
+    replayed one after another).  Frames/s counts one fwd+bwd render per agent."""
+    import torch
+
+    from paper_2412_09723_gb300 import scenes
+    from paper_2412_09723_gb300.agent import Agent
+    from paper_2412_09723_gb300.batch import MultiAgentBatch
+
+    agents = []
+    for i, (sc, w2c, cam) in enumerate(scenes.workload_multi_agent(seed=seed_base)):
+        a = Agent(sc, w2c, cam, dev)
+        a.render_observation_from(scenes.perturbed_w2c(700 + i, 0.01, 0.5, base=w2c))
+        a.size_capacity(1.5)
+        agents.append(a)
+    batch = MultiAgentBatch(agents)
+    batch.snapshot()
+    tune = batch.autotune(reps=3)
+    batch.restore()
+
+    def timed(run, k_steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_steps)]
+        for k in range(k_steps):
+            if k % EPISODE == 0:
+                batch.restore()
+            flush.fill_(float(k))
+            evs[k][0].record()
+            run()
+            evs[k][1].record()
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    kb = max(4, min(steps, 200))
+    per_batch = batch.capture()
+    for _ in range(3):
+        batch.replay()
+    t_batch = timed(batch.replay, kb)
+    if batch.status() != 0:
+        raise SystemExit("device status set in the batched multi-agent steps")
+    batch.restore()
+    per_plain = sum(a.capture() for a in agents)
+
+    def plain():
+        for a in agents:
+            a.replay()
+
+    for _ in range(3):
+        plain()
+    t_plain = timed(plain, kb)
+    n = len(agents)
+    return {"workload": "multi_agent_150k_400k_900k_1200x680", "agents": n,
+            "value": n * kb / (sum(t_batch) / 1e3), "unit": UNIT, "ms_per_step": sum(t_batch) / kb,
+            "p50_ms": statistics.median(t_batch), "p99_ms": _pct(t_batch, 99),
+            "plain_value": n * kb / (sum(t_plain) / 1e3), "plain_ms_per_step": sum(t_plain) / kb,
+            "plain_p50_ms": statistics.median(t_plain), "plain_p99_ms": _pct(t_plain, 99),
+            "speedup_vs_plain": sum(t_plain) / sum(t_batch), "steps": kb, "shape": list(tune["shape"]),
+            "gpu_launches_per_step": per_batch, "plain_gpu_launches_per_step": per_plain,
+            "plain": "each agent's own captured single-view step, replayed one after another"}
+
+
 def main():
     args = _parse()
     rank, world, local = _dist()
@@ -421,6 +485,10 @@ def main():
                "d2h_bytes_per_step": 4 + 64, "steps": Ke, "p50_ms": 1e3 * statistics.median(t_e2e),
                "p99_ms": 1e3 * _pct(t_e2e, 99)}
 
+    multi = None
+    if not args.no_multi:
+        multi = multi_agent_section(dev, K, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
@@ -437,7 +505,7 @@ def main():
                 "p50_ms": statistics.median(step_ms), "p99_ms": _pct(step_ms, 99),
                 "tracked_frames_per_s": value / EPISODE,
                 "wall_s_timed": t_wall, "gpu_launches": launches, "roofline": roofline, "kernels": breakdown,
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "batched_multi_agent": multi}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
