@@ -61,6 +61,8 @@ def _parse():
     ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel timing pass (no roofline)")
     ap.add_argument("--eager", action="store_true", help="time eager launches instead of CUDA-graph replays")
     ap.add_argument("--no-multi", action="store_true", help="skip the batched multi-agent comparison")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop comparison")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson request trace")
     return ap.parse_args()
 
 
@@ -255,6 +257,48 @@ def _traffic_for(kernel):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def serving_section(dev, seconds, seed=4):
+    """Eight agents (maps log-uniform in 100k..2M Gaussians; four at 640x480,
+    four at 1200x680), Poisson tracking requests at 30 Hz each and a mapping
+    request with every 5th frame.  The continuous-batching server (150 GB HBM
+    budget, and a reduced 2 GB budget that forces swapping) against the plain
+    per-request path, on the same trace in real time and all at once."""
+    from paper_2412_09723_gb300 import scenes
+    from paper_2412_09723_gb300.serve import Server, latency_stats, make_agents_workload, poisson_trace
+
+    spec = scenes.serving_agents(seed=seed)
+    srv = Server(dev, 150 << 30, max_batch=8, n_streams=2)
+    make_agents_workload(srv, spec, frames_per_agent=8)
+    out = {"workload": "serve_8_agents_100k_2M_poisson_30hz", "agents": len(spec),
+           "map_sizes": [s["n"] for s in spec], "trace_seconds": seconds}
+
+    def run(kind, realtime, budget, rate=30.0):
+        srv.reset(budget)
+        srv.prepare()
+        reqs = poisson_trace(len(spec), rate, seconds, 8, map_every=5, seed=seed)
+        span = srv.serve(reqs, realtime=realtime) if kind == "served" else srv.serve_plain(reqs, realtime=realtime)
+        st = latency_stats(reqs, span)
+        st["swaps"] = srv.swaps
+        return st
+
+    from paper_2412_09723_gb300.serve import _agent_bytes
+
+    out["served"] = run("served", True, 150 << 30)
+    out["plain"] = run("plain", True, 150 << 30)
+    footprint = sum(_agent_bytes(s.agent) for s in srv.slots if s.agent is not None)
+    out["served_90hz"] = run("served", True, 150 << 30, rate=90.0)
+    out["plain_90hz"] = run("plain", True, 150 << 30, rate=90.0)
+    out["served_saturated"] = run("served", False, 150 << 30)
+    out["plain_saturated"] = run("plain", False, 150 << 30)
+    half = footprint // 2
+    out["resident_footprint_bytes"] = footprint
+    out["reduced_budget_bytes"] = half
+    out["served_half_budget"] = run("served", True, half)
+    out["served_saturated_half_budget"] = run("served", False, half)
+    srv.reset()
+    return out
+
+
 def multi_agent_section(dev, steps, flush, seed_base=2):
     """Three agents with 150k / 400k / 900k-Gaussian room maps at 1200x680
     (fx = fy = 600): the batched step (one persistent forward and one
@@ -488,6 +532,9 @@ def main():
     multi = None
     if not args.no_multi:
         multi = multi_agent_section(dev, K, flush)
+    served = None
+    if not args.no_serve:
+        served = serving_section(dev, args.serve_seconds)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -505,7 +552,8 @@ def main():
                 "p50_ms": statistics.median(step_ms), "p99_ms": _pct(step_ms, 99),
                 "tracked_frames_per_s": value / EPISODE,
                 "wall_s_timed": t_wall, "gpu_launches": launches, "roofline": roofline, "kernels": breakdown,
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "batched_multi_agent": multi}
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "batched_multi_agent": multi,
+                "serving": served}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -81,6 +81,7 @@ class Agent:
         self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads))
         self.steps_done = 0
         self.t_dev = torch.zeros(1, dtype=torch.int32, device=device)  # Adam step, advanced on the device
+        self.grads_clean = True  # host-side: the gradient buffers hold zeros
         names = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
         self.adam = B.AdamGroups(self.params, self.grads, self.m, self.v, [self.cfg.lr[k] for k in names])
 
@@ -139,19 +140,22 @@ class Agent:
         with torch.cuda.stream(s):
             self.loss.zero_()
             self.d_pose.zero_()
-            if not cfg.map:  # the fused Adam step clears the gradients when mapping
+            if not self.grads_clean:  # the fused Adam step leaves them cleared when mapping
                 for g in self.grads:
                     g.zero_()
+        self.grads_clean = True
         B.splat_loss_l1(fb.image["rgb"], fb.image["depth"], self.obs_rgb, self.obs_depth, cfg.w_rgb, cfg.w_depth,
                         self.g_rgb, self.g_depth, self.loss, s)
 
     def phase_backward(self, s):
+        self.grads_clean = False
         fb = self.fb
         B.splat_render_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.vals, fb.ranges, fb.cimg, self.cfg.bg,
                            self.g_rgb, self.g_depth, None, self.cgr, self.d_pose, None, fb.bwd_ws, s)
 
     def phase_project_backward(self, s):
         """Projection adjoint of screen-space gradients already in bwd_ws."""
+        self.grads_clean = False
         fb = self.fb
         B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cgr, self.d_pose, None, s)
 
@@ -163,6 +167,7 @@ class Agent:
         t = self.t_dev
         if cfg.map:
             B.splat_adam_groups(self.adam, t, zero_grad=True, stream=s)
+            self.grads_clean = True
         if cfg.track:
             B.splat_pose_step(self.w2c, self.d_pose, self.pose_m, self.pose_v, t, cfg.pose_lr[0], cfg.pose_lr[1],
                               stream=s)

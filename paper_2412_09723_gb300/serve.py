@@ -1,0 +1,414 @@
+"""Serving loop: asynchronous per-agent tracking and mapping requests over
+resident agents, with continuous batching (the asynchronous, parallel intra-
+and inter-agent processing of Sec. 3.2 / 3.6, on one GPU).
+
+* Residency.  Every admitted agent's map, Adam state, pose and work buffers
+  live on the device and are charged against an HBM budget.  When a request
+  arrives for an agent that is not resident and the budget is full, idle
+  agents are swapped out to pinned host memory, least recently used first.
+* Continuous batching.  At every tick the loop admits the requests that have
+  arrived, takes up to `max_batch` ready requests of distinct agents (oldest
+  first; an agent has at most one request in flight, so its state advances in
+  order) and launches them as ONE batched step on a free stream: the frames are
+  copied in from pinned host memory, every agent is projected and binned on its
+  own stream, all of them are rendered forward and backward in one persistent
+  launch each, and the loss, pose and Adam updates follow per agent.  Up to
+  `n_streams` batches are in flight at once, so requests that arrive while
+  others run are admitted as stream slots and memory free up, and their work
+  overlaps on the device.  Completion is detected with CUDA events.
+* Plain mode serves the same requests one at a time in arrival order with the
+  single-agent launches and a synchronisation per request.
+
+A request is one fwd + bwd + update step: "track" updates the pose, "map"
+updates the Gaussian map.  Its result is the loss of the step and the pose
+after it.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import statistics
+import time
+
+import numpy as np
+import torch
+
+from . import binding as B
+from .agent import Agent, StepConfig
+
+
+@dataclasses.dataclass
+class Request:
+    agent: int
+    kind: str  # "track" or "map"
+    frame: int  # index of the agent's observation frame
+    arrival: float  # seconds (trace time)
+    rid: int = 0
+    start: float = 0.0
+    done: float = 0.0
+    loss: float = float("nan")
+    w2c: np.ndarray | None = None
+
+
+class _AgentSlot:
+    """Host-side record of an agent: its map when swapped out, its frames."""
+
+    def __init__(self, aid, scene, w2c, cam, frames, cfg):
+        self.aid = aid
+        self.scene = scene
+        self.w2c = np.asarray(w2c, np.float32)
+        self.cam = cam
+        self.frames = frames  # list of (rgb pinned [H,W,3], depth pinned [H,W])
+        self.cfg = cfg
+        self.agent: Agent | None = None
+        self.host_state = None  # swapped-out device state
+        self.capacity = None
+        self.bytes = 0
+        self.footprint = 0  # device bytes when resident (last measured)
+        self.last_used = 0.0
+        self.busy = False
+
+
+def _agent_bytes(a: Agent) -> int:
+    seen = set()
+    total = 0
+
+    def add(t):
+        nonlocal total
+        if isinstance(t, torch.Tensor) and t.is_cuda and t.data_ptr() not in seen:
+            seen.add(t.data_ptr())
+            total += t.numel() * t.element_size()
+
+    for v in vars(a).values():
+        if isinstance(v, torch.Tensor):
+            add(v)
+        elif isinstance(v, (list, tuple)):
+            for t in v:
+                add(t)
+    fb = a.fb
+    for d in (fb.proj, fb.image):
+        for t in d.values():
+            add(t)
+    for t in (fb.ranges, fb.k_dev, fb.status, fb.vals, fb.keys, fb.bin_ws, fb.bwd_ws):
+        add(t)
+    return total
+
+
+class Server:
+    def __init__(self, device, hbm_budget_bytes: int, max_batch: int = 8, n_streams: int = 2,
+                 shape=(256, 4, 256, 7)):
+        self.device = device
+        self.budget = int(hbm_budget_bytes)
+        self.max_batch = min(max_batch, B.SPLAT_MAX_VIEWS)
+        self.n_streams = n_streams
+        self.shape = B.CBatchShape(*shape)
+        self.slots: list[_AgentSlot] = []
+        self.used = 0
+        self.swaps = 0
+        self.batch_ws = [torch.zeros(256, dtype=torch.uint8, device=device) for _ in range(n_streams)]
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
+        self.agent_streams = [[torch.cuda.Stream(device=device) for _ in range(self.max_batch)]
+                              for _ in range(n_streams)]
+
+    def reset(self, budget: int | None = None):
+        """Drop every agent's device state (they restart from their initial
+        maps and poses at the next prepare())."""
+        for slot in self.slots:
+            slot.agent = None
+            slot.host_state = None
+            slot.bytes = 0
+            slot.busy = False
+            slot.last_used = 0.0
+        self.used = 0
+        self.swaps = 0
+        if budget is not None:
+            self.budget = int(budget)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+    # -- agents and residency -------------------------------------------------
+    def add_agent(self, scene, w2c, cam, frames, cfg: StepConfig | None = None) -> int:
+        slot = _AgentSlot(len(self.slots), scene, w2c, cam, frames, cfg or StepConfig())
+        self.slots.append(slot)
+        return slot.aid
+
+    def _can_fit(self, slot: _AgentSlot) -> bool:
+        """Whether the agent fits once every idle resident is swapped out
+        (known footprint only; an agent never resident is always tried)."""
+        if slot.footprint == 0:
+            return True
+        idle = sum(s.bytes for s in self.slots if s.agent is not None and not s.busy)
+        return self.used - idle + slot.footprint <= self.budget
+
+    def _make_resident(self, slot: _AgentSlot, now: float) -> bool:
+        if slot.agent is not None:
+            return True
+        if not self._can_fit(slot):
+            return False
+        if slot.host_state is not None:
+            # swap in: the map comes from the saved state, not from the initial scene
+            from .scenes import Scene
+
+            p = slot.host_state[:5]
+            a = Agent(Scene(*p), slot.w2c, slot.cam, self.device, cfg=dataclasses.replace(slot.cfg),
+                      capacity=slot.capacity)
+            for dst, src in zip(a._state()[5:], slot.host_state[5:]):
+                dst.copy_(src, non_blocking=True)
+        else:
+            a = Agent(slot.scene, slot.w2c, slot.cam, self.device, cfg=dataclasses.replace(slot.cfg),
+                      capacity=slot.capacity)
+            if slot.capacity is None:
+                slot.capacity = a.fb.capacity
+        need = _agent_bytes(a)
+        if self.used + need > self.budget:
+            # swap out idle residents, least recently used first
+            for other in sorted((s for s in self.slots if s.agent is not None and not s.busy),
+                                key=lambda s: s.last_used):
+                if self.used + need <= self.budget:
+                    break
+                self._swap_out(other)
+        if self.used + need > self.budget:
+            del a
+            return False
+        slot.agent = a
+        slot.bytes = need
+        slot.footprint = need
+        self.used += need
+        slot.last_used = now
+        return True
+
+    def _swap_out(self, slot: _AgentSlot):
+        a = slot.agent
+        state = a._state()
+        if slot.host_state is None:  # pinned host copies, allocated once per agent and reused
+            slot.host_state = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in state]
+        s = torch.cuda.current_stream()
+        for dst, src in zip(slot.host_state, state):
+            dst.copy_(src, non_blocking=True)
+        s.synchronize()
+        slot.w2c = slot.host_state[-4].numpy().copy()
+        slot.capacity = a.fb.capacity
+        slot.agent = None
+        self.used -= slot.bytes
+        slot.bytes = 0
+        self.swaps += 1
+
+    def prepare(self, size_capacity: bool = True):
+        """Size every agent's duplicate buffers (one host read each, before
+        serving), bringing agents in one after another and swapping earlier
+        ones out when the budget requires; the agents resident at the end are
+        the last ones that fit."""
+        for slot in self.slots:
+            if not self._make_resident(slot, 0.0):
+                raise RuntimeError(f"agent {slot.aid} alone exceeds the HBM budget")
+            if size_capacity:
+                slot.agent.size_capacity(1.5)
+                slot.capacity = slot.agent.fb.capacity
+                self.used -= slot.bytes
+                slot.bytes = slot.footprint = _agent_bytes(slot.agent)
+                self.used += slot.bytes
+            torch.cuda.synchronize()
+
+    # -- one batched step ---------------------------------------------------------
+    def _launch(self, reqs, si):
+        s = self.streams[si]
+        agents = [self.slots[r.agent].agent for r in reqs]
+        views = (B.CView * len(agents))(*[a.view() for a in agents])
+        ast = self.agent_streams[si]
+        with torch.cuda.stream(s):
+            for r, a in zip(reqs, agents):
+                rgb, depth = self.slots[r.agent].frames[r.frame]
+                a.obs_rgb.copy_(rgb, non_blocking=True)
+                a.obs_depth.copy_(depth, non_blocking=True)
+        for a, st in zip(agents, ast):
+            st.wait_stream(s)
+            a.phase_pre(st)
+        for st in ast[:len(agents)]:
+            s.wait_stream(st)
+        B.splat_render_fwd_batch(views, self.shape, self.batch_ws[si], s)
+        for a, st in zip(agents, ast):
+            st.wait_stream(s)
+            a.phase_loss(st)
+        for st in ast[:len(agents)]:
+            s.wait_stream(st)
+        B.splat_render_bwd_batch(views, self.shape, self.batch_ws[si], s)
+        for r, a, st in zip(reqs, agents, ast):
+            st.wait_stream(s)
+            a.phase_project_backward(st)
+            a.cfg.track = r.kind == "track"
+            a.cfg.map = r.kind == "map"
+            a.phase_update(st)
+        for st in ast[:len(agents)]:
+            s.wait_stream(st)
+        outs = []
+        with torch.cuda.stream(s):
+            for a in agents:
+                loss = torch.empty(1, dtype=torch.float32, pin_memory=True)
+                w2c = torch.empty(4, 4, dtype=torch.float32, pin_memory=True)
+                loss.copy_(a.loss, non_blocking=True)
+                w2c.copy_(a.w2c, non_blocking=True)
+                outs.append((loss, w2c))
+        ev = torch.cuda.Event()
+        ev.record(s)
+        return ev, outs
+
+    def _finish(self, reqs, outs, now):
+        for r, (loss, w2c) in zip(reqs, outs):
+            r.done = now
+            r.loss = float(loss.item())
+            r.w2c = w2c.numpy().copy()
+            slot = self.slots[r.agent]
+            slot.busy = False
+            slot.last_used = now
+
+    # -- the loop -------------------------------------------------------------------
+    def serve(self, requests, realtime: bool = True):
+        """Serve `requests` (arrival times in seconds from the start).  With
+        `realtime`, a request becomes visible at its arrival time on the host
+        clock; otherwise all are submitted at time 0 (saturation), and their
+        arrival is set to 0."""
+        if not realtime:
+            for r in requests:
+                r.arrival = 0.0
+        pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
+        ready = collections.deque()
+        in_flight = {}  # stream index -> (event, reqs, outs)
+        t0 = time.perf_counter()
+        n_done = 0
+        total = len(pending)
+        while n_done < total:
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0].arrival <= now):
+                ready.append(pending.popleft())
+            # completions
+            for si in list(in_flight):
+                ev, reqs, outs = in_flight[si]
+                if ev.query():
+                    self._finish(reqs, outs, time.perf_counter() - t0)
+                    n_done += len(reqs)
+                    del in_flight[si]
+            # admissions: free stream slots take the oldest ready requests of idle, resident agents
+            free = [si for si in range(self.n_streams) if si not in in_flight]
+            while free and ready:
+                batch, seen, keep = [], set(), collections.deque()
+                # requests of resident agents first; swap agents in only when none is left
+                failed = set()
+                for resident_only in (True, False):
+                    if batch:
+                        break
+                    while ready and len(batch) < self.max_batch:
+                        r = ready.popleft()
+                        slot = self.slots[r.agent]
+                        if (r.agent in seen or r.agent in failed or slot.busy
+                                or (resident_only and slot.agent is None)):
+                            keep.append(r)
+                            continue
+                        if not self._make_resident(slot, now):
+                            failed.add(r.agent)
+                            keep.append(r)
+                            continue
+                        seen.add(r.agent)
+                        slot.busy = True  # from here on it cannot be swapped out for another batch member
+                        batch.append(r)
+                    ready.extendleft(reversed(keep))
+                    keep = collections.deque()
+                if not batch:
+                    break
+                si = free.pop(0)
+                for r in batch:
+                    r.start = now
+                ev, outs = self._launch(batch, si)
+                in_flight[si] = (ev, batch, outs)
+            if not in_flight and not ready and pending and realtime:
+                time.sleep(max(0.0, min(0.0005, pending[0].arrival - (time.perf_counter() - t0))))
+        torch.cuda.synchronize()
+        status = 0
+        for slot in self.slots:
+            if slot.agent is not None:
+                status |= slot.agent.status()
+        if status:
+            raise RuntimeError(f"device status {status} while serving")
+        return time.perf_counter() - t0
+
+    def serve_plain(self, requests, realtime: bool = True):
+        """The per-request path: one request at a time in arrival order
+        (without `realtime`, all are submitted at time 0)."""
+        order = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        if not realtime:
+            for r in order:
+                r.arrival = 0.0
+        t0 = time.perf_counter()
+        s = torch.cuda.current_stream()
+        for r in order:
+            now = time.perf_counter() - t0
+            if realtime and r.arrival > now:
+                time.sleep(r.arrival - now)
+            slot = self.slots[r.agent]
+            if not self._make_resident(slot, time.perf_counter() - t0):
+                raise RuntimeError("agent does not fit the HBM budget alone")
+            a = slot.agent
+            r.start = time.perf_counter() - t0
+            rgb, depth = slot.frames[r.frame]
+            a.obs_rgb.copy_(rgb, non_blocking=True)
+            a.obs_depth.copy_(depth, non_blocking=True)
+            a.cfg.track = r.kind == "track"
+            a.cfg.map = r.kind == "map"
+            a.step(stream=s)
+            r.loss = float(a.loss.item())  # synchronises
+            r.w2c = a.w2c.cpu().numpy()
+            r.done = time.perf_counter() - t0
+            slot.last_used = r.done
+        return time.perf_counter() - t0
+
+
+def latency_stats(requests, makespan):
+    lat = [1e3 * (r.done - r.arrival) for r in requests]
+    lat.sort()
+    k = max(0, int(np.ceil(0.99 * len(lat))) - 1)
+    return {"requests": len(requests), "frames_per_s": len(requests) / makespan, "p50_ms": statistics.median(lat),
+            "p99_ms": lat[k], "mean_ms": float(np.mean(lat)), "makespan_s": makespan}
+
+
+def poisson_trace(n_agents, rate_hz, duration_s, frames_per_agent, map_every=5, seed=0):
+    """Poisson tracking requests per agent; every `map_every`-th frame of an
+    agent also carries a mapping request."""
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for a in range(n_agents):
+        t, k = 0.0, 0
+        while True:
+            t += rng.exponential(1.0 / rate_hz)
+            if t > duration_s:
+                break
+            f = k % frames_per_agent
+            reqs.append(Request(a, "track", f, t))
+            if (k + 1) % map_every == 0:
+                reqs.append(Request(a, "map", f, t))
+            k += 1
+    reqs.sort(key=lambda r: r.arrival)
+    for i, r in enumerate(reqs):
+        r.rid = i
+    return reqs
+
+
+def make_agents_workload(server: Server, agents_spec, frames_per_agent=8, seed=0, device=None):
+    """Register agents (dicts with n, seed, cam) on `server`: each gets a room
+    map, a start pose near the room centre and `frames_per_agent` observation
+    frames rendered from a trajectory of poses 1 cm / 0.5 degree apart (on the
+    GPU, then kept in pinned host memory)."""
+    from . import scenes
+
+    device = device or server.device
+    for spec in agents_spec:
+        sc = scenes.scene_room(spec["n"], spec["seed"])
+        w2c0 = scenes.perturbed_w2c(spec["seed"] + 7, 0.05, 5.0)
+        tmp = Agent(sc, w2c0, spec["cam"], device)
+        frames = []
+        pose = w2c0
+        for f in range(frames_per_agent):
+            pose = scenes.perturbed_w2c(spec["seed"] * 100 + f, 0.01, 0.5, base=pose)
+            fb = tmp.render_observation_from(pose)
+            frames.append((fb.image["rgb"].cpu().pin_memory(), fb.image["depth"].cpu().pin_memory()))
+        del tmp
+        server.add_agent(sc, w2c0, spec["cam"], frames)
+    torch.cuda.synchronize()
