@@ -221,6 +221,19 @@ def run_reference(args, rank, world):
     return 0
 
 
+def whole_job_rate(units_per_rank: int, local_ms: float, world: int, dist=None, device=None):
+    """Units per second of the whole job: every rank processed
+    `units_per_rank` units; the job's time is the slowest rank's (MAX over
+    ranks).  Returns (rate, max_ms)."""
+    import torch
+
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    if world > 1 and dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    return world * units_per_rank / (max_ms / 1e3), max_ms
+
+
 def _pct(xs, q):
     s = sorted(xs)
     if not s:
@@ -436,11 +449,7 @@ def main():
     status = agent.status()
     if status != 0:
         raise SystemExit(f"device status {status} (capacity overflow) during the timed steps")
-    mx = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-    total_ms_max = float(mx.item())
-    value = world * K / (total_ms_max / 1e3)
+    value, total_ms_max = whole_job_rate(K, total_ms, world, dist if world > 1 else None, dev)
 
     # per-kernel timing pass: the same steps launched eagerly, each kernel
     # bracketed by CUDA events on its launching stream
