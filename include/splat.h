@@ -360,6 +360,25 @@ int splat_pose_step(float *w2c, const float *d_pose, float *m, float *v, const i
                     splat_stream_t stream);
 
 /*
+ * splat_pose_compose -- out[k] = a[k] b for n row-major 4x4 poses (device
+ * float[n,16], float[16], float[n,16]): the cameras through which a map
+ * aligned by a relative transform is seen, w2c_eff = w2c_A T_rel (inter-agent
+ * alignment, Sec. 3.5 step 3).  Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_pose_compose(int32_t n, const float *a, const float *b, float *out, splat_stream_t stream);
+
+/*
+ * splat_pose_rel_grad -- gradient with respect to the left perturbation of a
+ * relative transform T_rel when view k is rendered with w2c[k] T_rel and
+ * d_cam[k] is that view's camera-pose gradient (both 6-vectors (rho, phi)):
+ * w2c exp(d^) T_rel = exp((Ad_w2c d)^) w2c T_rel, so
+ * d_rel = sum_k Ad(w2c[k])^T d_cam[k], i.e. rho: R^T g_rho, phi: R^T (g_phi - t x g_rho).
+ * w2c: device float[n,16]; d_cam: device float[n,6]; d_rel: device float[6]
+ * (overwritten).  Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_pose_rel_grad(int32_t n, const float *w2c, const float *d_cam, float *d_rel, splat_stream_t stream);
+
+/*
  * splat_assoc -- render-based Gaussian association between two maps
  * (Sec. 3.5 step 2): at every pixel where both renders have a maximum-weight
  * Gaussian (id >= 0) and both final transmittances are <= t_max, the pair

@@ -89,6 +89,8 @@ _SIGS = {
     "splat_assoc_workspace_size": ([_c_i64], _c_sz),
     "splat_assoc": ([_c_p, _c_p, _c_p, _c_p, _c_i64, _c_i64, _c_i64, _c_f, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p,
                      _c_sz, _c_p], ctypes.c_int),
+    "splat_pose_compose": ([_c_i32, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_pose_rel_grad": ([_c_i32, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_exp_f32": ([_c_p, _c_p, _c_i64, _c_p], ctypes.c_int),
 }
 
@@ -312,6 +314,17 @@ def splat_assoc(id_a, t_a, id_b, t_b, n_a, n_b, t_max, pairs, counts, capacity, 
     _check("splat_assoc", load().splat_assoc(
         _p(id_a), _p(t_a), _p(id_b), _p(t_b), id_a.numel(), n_a, n_b, t_max, _p(pairs), _p(counts), capacity,
         _p(m_dev), _p(status), _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def splat_pose_compose(a, b, out, stream=None):
+    """out[k] = a[k] @ b for a [n,4,4], b [4,4] (device float32)."""
+    _check("splat_pose_compose", load().splat_pose_compose(a.shape[0], _p(a), _p(b), _p(out), _stream(stream)))
+
+
+def splat_pose_rel_grad(w2c, d_cam, d_rel, stream=None):
+    """d_rel = sum_k Ad(w2c[k])^T d_cam[k]."""
+    _check("splat_pose_rel_grad", load().splat_pose_rel_grad(w2c.shape[0], _p(w2c), _p(d_cam), _p(d_rel),
+                                                             _stream(stream)))
 
 
 def splat_exp_f32(x, y, stream=None):

@@ -198,6 +198,37 @@ __global__ void pose_step_kernel(float* __restrict__ w2c, const float* __restric
   for (int k = 0; k < 12; ++k) w2c[k] = out[k];
 }
 
+__global__ void pose_compose_kernel(int n, const float* __restrict__ a, const float* __restrict__ b,
+                                    float* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float* A = a + 16 * k;
+  float* O = out + 16 * k;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      O[4 * i + j] = A[4 * i] * b[j] + A[4 * i + 1] * b[4 + j] + A[4 * i + 2] * b[8 + j] + A[4 * i + 3] * b[12 + j];
+}
+
+__global__ void pose_rel_grad_kernel(int n, const float* __restrict__ w2c, const float* __restrict__ d_cam,
+                                     float* __restrict__ d_rel) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int k = 0; k < n; ++k) {
+    const float* T = w2c + 16 * k;
+    const float* g = d_cam + 6 * k;
+    const float t0 = T[3], t1 = T[7], t2 = T[11];
+    // h = g_phi - t x g_rho
+    const float h0 = g[3] - (t1 * g[2] - t2 * g[1]);
+    const float h1 = g[4] - (t2 * g[0] - t0 * g[2]);
+    const float h2 = g[5] - (t0 * g[1] - t1 * g[0]);
+    for (int j = 0; j < 3; ++j) {  // R^T v: column j of R dotted with v
+      acc[j] += T[j] * g[0] + T[4 + j] * g[1] + T[8 + j] * g[2];
+      acc[3 + j] += T[j] * h0 + T[4 + j] * h1 + T[8 + j] * h2;
+    }
+  }
+  for (int j = 0; j < 6; ++j) d_rel[j] = acc[j];
+}
+
 __global__ void exp_kernel(const float* __restrict__ x, float* __restrict__ y, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = exp_full(x[i]);
@@ -284,6 +315,22 @@ extern "C" int splat_pose_step(float* w2c, const float* d_pose, float* m, float*
   SPLAT_LAUNCH("pose_step_kernel", reinterpret_cast<cudaStream_t>(stream), pose_step_kernel<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(w2c, d_pose, m, v, lr_t, lr_r, beta1, beta2,
                                                                           step, eps));
   return check_launch("pose_step_kernel");
+}
+
+extern "C" int splat_pose_compose(int32_t n, const float* a, const float* b, float* out, splat_stream_t stream) {
+  if (n < 0 || (n > 0 && (!a || !b || !out))) return fail(SPLAT_EINVAL, "splat_pose_compose: bad argument");
+  if (n == 0) return SPLAT_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SPLAT_LAUNCH("pose_compose_kernel", s, pose_compose_kernel<<<ceil_div(n, 64), 64, 0, s>>>(n, a, b, out));
+  return check_launch("pose_compose_kernel");
+}
+
+extern "C" int splat_pose_rel_grad(int32_t n, const float* w2c, const float* d_cam, float* d_rel,
+                                   splat_stream_t stream) {
+  if (n < 0 || !d_rel || (n > 0 && (!w2c || !d_cam))) return fail(SPLAT_EINVAL, "splat_pose_rel_grad: bad argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SPLAT_LAUNCH("pose_rel_grad_kernel", s, pose_rel_grad_kernel<<<1, 32, 0, s>>>(n, w2c, d_cam, d_rel));
+  return check_launch("pose_rel_grad_kernel");
 }
 
 extern "C" int splat_exp_f32(const float* x, float* y, int64_t n, splat_stream_t stream) {

@@ -141,3 +141,31 @@ def test_planted_mistake_is_caught_by_fd(orc):
             fd.append(v)
     with pytest.raises(AssertionError):
         _check(an, fd, 1e-5)
+
+
+def ad_transpose_apply(w2c, g):
+    """Ad(w2c)^T g for a 6-vector g = (rho, phi): (R^T g_rho, R^T (g_phi - t x g_rho))."""
+    R, t = np.asarray(w2c)[:3, :3], np.asarray(w2c)[:3, 3]
+    g = np.asarray(g, float)
+    return np.concatenate([R.T @ g[:3], R.T @ (g[3:] - np.cross(t, g[:3]))])
+
+
+def test_relative_transform_gradient_is_adjoint_transpose(orc):
+    """A map aligned by T_rel and seen through w2c_A is rendered with
+    w2c_A exp(delta^) T_rel; its gradient w.r.t. delta equals
+    Ad(w2c_A)^T applied to the camera-pose gradient at w2c_A T_rel."""
+    sc, _, g = _setup(104)
+    w2c_a = scenes.perturbed_w2c(20, 0.05, 4.0).astype(np.float64)
+    T_rel = scenes.perturbed_w2c(21, 0.03, 2.0).astype(np.float64)
+    w_eff = w2c_a @ T_rel
+    L0, sig0 = _loss(orc, sc, w_eff, g)
+    d_cam = orc.render_bwd(sc, w_eff, CAM, BG, *g, dtype=np.float64)["pose"]
+    want = ad_transpose_apply(w2c_a, d_cam)
+    fd = []
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = 1.0
+        v = _fd(orc, lambda h: _loss(orc, sc, w2c_a @ se3_exp(h * e) @ T_rel, g), sig0)
+        assert v is not None
+        fd.append(v)
+    _check(want, fd, 1e-5)
