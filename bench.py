@@ -62,6 +62,7 @@ def _parse():
     ap.add_argument("--eager", action="store_true", help="time eager launches instead of CUDA-graph replays")
     ap.add_argument("--no-multi", action="store_true", help="skip the batched multi-agent comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop comparison")
+    ap.add_argument("--no-align", action="store_true", help="skip the two-agent association/alignment section")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson request trace")
     return ap.parse_args()
 
@@ -375,6 +376,57 @@ def multi_agent_section(dev, steps, flush, seed_base=2):
             "plain": "each agent's own captured single-view step, replayed one after another"}
 
 
+def alignment_section(dev, flush, iters=40):
+    """Two agents with 1M-Gaussian maps of the same room in frames 20 cm /
+    10 degrees apart; B's map rendered from 8 of A's keyframes at 1200x680
+    (one persistent forward and one backward launch over the 8 views, one CUDA
+    graph per iteration), `iters` alignment iterations of T_rel from 1 cm /
+    0.5 degrees off, then the association of every keyframe.  Frames/s counts
+    one fwd+bwd view render."""
+    import torch
+
+    from paper_2412_09723_gb300 import align, scenes
+
+    a, b, perm, T_true, kfs, T0, cam = scenes.workload_alignment()
+    targets = align.render_targets(a, kfs, cam, dev)
+    al = align.Alignment(b, kfs, targets, cam, T0, dev)
+    al.size_capacity()
+    e0 = al.error(T_true)
+    per_step = al.capture()
+    for _ in range(3):
+        al.replay()
+    al.reset(T0)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
+    for k in range(iters):
+        flush.fill_(float(k))
+        evs[k][0].record()
+        al.replay()
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    t = [x.elapsed_time(y) for x, y in evs]
+    e1 = al.error(T_true)
+    loss = float(al.loss.item())
+    flush.fill_(0.0)
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for k in range(len(kfs)):
+        ea.record()
+        al.associate(k)
+        eb.record()
+        torch.cuda.synchronize()
+        ms.append(ea.elapsed_time(eb))
+        m_last = int(al.m_dev.item())
+    if al.status() != 0:
+        raise SystemExit("device status set in the alignment steps")
+    nv = len(kfs)
+    return {"workload": "align_2x1M_8views_1200x680", "views": nv, "value": nv * iters / (sum(t) / 1e3),
+            "unit": UNIT, "ms_per_iteration": sum(t) / iters, "p50_ms": statistics.median(t),
+            "p99_ms": _pct(t, 99), "iterations": iters, "gpu_launches_per_iteration": per_step,
+            "error_start": {"trans_m": e0[0], "rot_deg": e0[1]}, "error_end": {"trans_m": e1[0], "rot_deg": e1[1]},
+            "loss_end": loss, "assoc_ms_per_view": statistics.median(ms), "assoc_pairs_last_view": m_last,
+            "duplicates_K_view0": int(al.fbs[0].k_dev.item())}
+
+
 def main():
     args = _parse()
     rank, world, local = _dist()
@@ -545,6 +597,10 @@ def main():
     if not args.no_serve:
         served = serving_section(dev, args.serve_seconds)
 
+    aligned = None
+    if not args.no_align:
+        aligned = alignment_section(dev, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample()
@@ -562,7 +618,7 @@ def main():
                 "tracked_frames_per_s": value / EPISODE,
                 "wall_s_timed": t_wall, "gpu_launches": launches, "roofline": roofline, "kernels": breakdown,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "batched_multi_agent": multi,
-                "serving": served}
+                "serving": served, "alignment": aligned}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -221,3 +221,56 @@ def serving_agents(seed: int = 4, n_agents: int = 8, lo: int = 100_000, hi: int 
         cam = CAM_VGA if a < n_agents // 2 else CAM_WIDE
         agents.append(dict(n=int(sizes[a]), seed=1000 + a, cam=cam))
     return agents
+
+
+def _quat_of_rotation(R):
+    """(w, x, y, z) unit quaternion of a rotation matrix (Shepperd's method)."""
+    R = np.asarray(R, dtype=np.float64)
+    tr = np.trace(R)
+    if tr > 0:
+        s = 2.0 * math.sqrt(1.0 + tr)
+        return np.array([0.25 * s, (R[2, 1] - R[1, 2]) / s, (R[0, 2] - R[2, 0]) / s, (R[1, 0] - R[0, 1]) / s])
+    i = int(np.argmax(np.diag(R)))
+    j, k = (i + 1) % 3, (i + 2) % 3
+    s = 2.0 * math.sqrt(1.0 + R[i, i] - R[j, j] - R[k, k])
+    q = np.zeros(4)
+    q[0] = (R[k, j] - R[j, k]) / s
+    q[1 + i] = 0.25 * s
+    q[1 + j] = (R[j, i] + R[i, j]) / s
+    q[1 + k] = (R[k, i] + R[i, k]) / s
+    return q
+
+
+def transform_scene(scene: Scene, T) -> Scene:
+    """The scene moved rigidly by T (4x4): means x -> R x + t, rotations
+    q -> q_R * q (Hamilton product); scales, opacities and colours unchanged."""
+    T = np.asarray(T, dtype=np.float64)
+    R, t = T[:3, :3], T[:3, 3]
+    mean = scene.mean.astype(np.float64) @ R.T + t
+    a = _quat_of_rotation(R)
+    q = scene.quat.astype(np.float64)
+    w = a[0] * q[:, 0] - a[1] * q[:, 1] - a[2] * q[:, 2] - a[3] * q[:, 3]
+    x = a[0] * q[:, 1] + a[1] * q[:, 0] + a[2] * q[:, 3] - a[3] * q[:, 2]
+    y = a[0] * q[:, 2] - a[1] * q[:, 3] + a[2] * q[:, 0] + a[3] * q[:, 1]
+    z = a[0] * q[:, 3] + a[1] * q[:, 2] - a[2] * q[:, 1] + a[3] * q[:, 0]
+    return Scene(_f32(mean), scene.log_scale.copy(), _f32(np.stack([w, x, y, z], 1)), scene.opacity_logit.copy(),
+                 scene.rgb.copy())
+
+
+def workload_alignment(seed: int = 3, n: int = 1_000_000, n_views: int = 8, cam: Camera = CAM_WIDE):
+    """Two agents that mapped the same room: A's map, and B's map of the same
+    surfaces (A's Gaussians in a shuffled order, means jittered by 2 mm and
+    colours by 0.02) held in B's own world frame, which differs from A's by
+    T_true (B world -> A world: 20 cm and 10 degrees).  Returns A's map, B's
+    map, T_true, A's keyframe poses and the alignment's starting transform,
+    T_true perturbed by 1 cm / 0.5 degrees."""
+    a = scene_room(n, seed)
+    rng = np.random.default_rng(seed + 77)
+    perm = rng.permutation(n)
+    b = a.subset(perm)
+    b.mean = _f32(b.mean + rng.normal(0.0, 0.002, b.mean.shape))
+    b.rgb = _f32(np.clip(b.rgb + rng.normal(0.0, 0.02, b.rgb.shape), 0.0, 1.0))
+    T_true = perturbed_w2c(seed + 200, 0.2, 10.0).astype(np.float64)
+    b = transform_scene(b, np.linalg.inv(T_true))
+    T0 = perturbed_w2c(seed + 300, 0.01, 0.5, base=T_true)
+    return a, b, perm, T_true.astype(np.float32), keyframe_poses(n_views, seed), T0, cam

@@ -1,0 +1,182 @@
+"""Inter-agent association and render-based alignment (two agents' maps
+related by a rigid transform, B rendered from A's keyframes through T_rel).
+
+- pose composition on the device equals the float32 product written out on
+  the host, bit for bit; the relative-transform gradient equals
+  sum_k Ad(w2c_k)^T d_cam_k in float64;
+- at full size (2 x 1M Gaussians, 8 keyframes at 1200x680) every keyframe's
+  sort keys, Gaussian ids and tile ranges of B's batched render equal the
+  oracle's, and row bands (including the ragged last tile row) match the
+  oracle's image (ids and contributor counts exactly) and association;
+- 40 alignment iterations from 1 cm / 0.5 degrees off reduce the error."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_09723_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_09723_gb300 import binding
+
+    binding.load()
+    return torch.device("cuda:0")
+
+
+def compose_host_f32(a, b):
+    """out[k] = a[k] b in float32, each entry ((p0 + p1) + p2) + p3 with the
+    products rounded separately (no fused multiply-add)."""
+    a, b = np.asarray(a, np.float32), np.asarray(b, np.float32)
+    out = np.zeros_like(a)
+    for i in range(4):
+        for j in range(4):
+            acc = a[:, i, 0] * b[0, j]
+            for l in range(1, 4):
+                acc = (acc + a[:, i, l] * b[l, j]).astype(np.float32)
+            out[:, i, j] = acc
+    return out
+
+
+def ad_transpose_sum(w2c, d_cam):
+    out = np.zeros(6)
+    for T, g in zip(np.asarray(w2c, np.float64), np.asarray(d_cam, np.float64)):
+        R, t = T[:3, :3], T[:3, 3]
+        out += np.concatenate([R.T @ g[:3], R.T @ (g[3:] - np.cross(t, g[:3]))])
+    return out
+
+
+def test_pose_compose_bit_exact(dev):
+    from paper_2412_09723_gb300 import binding as B
+
+    kfs = np.stack(scenes.keyframe_poses(13, 9))
+    T = scenes.perturbed_w2c(4, 0.3, 20.0)
+    a, b = torch.as_tensor(kfs, device=dev), torch.as_tensor(T, device=dev)
+    out = torch.zeros_like(a)
+    B.splat_pose_compose(a, b, out)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), compose_host_f32(kfs, T).view(np.uint32))
+
+
+def test_pose_rel_grad_formula(dev):
+    from paper_2412_09723_gb300 import binding as B
+
+    kfs = np.stack(scenes.keyframe_poses(8, 5))
+    d_cam = np.random.default_rng(0).normal(size=(8, 6)).astype(np.float32)
+    out = torch.zeros(6, device=dev)
+    B.splat_pose_rel_grad(torch.as_tensor(kfs, device=dev), torch.as_tensor(d_cam, device=dev), out)
+    ref = ad_transpose_sum(kfs, d_cam)
+    np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+
+
+def _alignment(dev, n, cam, want_keys=False):
+    from paper_2412_09723_gb300 import align
+
+    a, b, perm, T_true, kfs, T0, _ = scenes.workload_alignment(n=n, cam=cam)
+    targets = align.render_targets(a, kfs, cam, dev)
+    al = align.Alignment(b, kfs, targets, cam, T0, dev, want_keys=want_keys)
+    al.size_capacity()
+    return al, (a, b, perm, T_true, kfs, T0)
+
+
+BANDS = ((320, 336), (672, 680))  # a middle tile row; the ragged last tile row of a 680-row frame
+
+
+def test_full_size_views_bit_exact(dev):
+    """2 x 1M Gaussians, 8 keyframes of 1200x680 in one batched launch."""
+    cam = scenes.CAM_WIDE
+    al, (a, b, perm, T_true, kfs, T0) = _alignment(dev, 1_000_000, cam, want_keys=True)
+    al.render()
+    torch.cuda.synchronize()
+    assert al.status() == 0
+    w_eff = compose_host_f32(np.stack(kfs), T0)
+    assert np.array_equal(al.w2c_eff.cpu().numpy().view(np.uint32), w_eff.view(np.uint32))
+    bg = np.zeros(3, np.float32)
+    for k in (0, 7):
+        fb = al.fbs[k]
+        keys, vals, ranges = oracle.bin_sort(b, w_eff[k], cam)
+        kdup = int(fb.k_dev.item())
+        assert kdup == len(vals) > 1_000_000
+        assert np.array_equal(fb.keys[:kdup].cpu().numpy().view(np.uint64), keys)
+        assert np.array_equal(fb.vals[:kdup].cpu().numpy().view(np.uint32), vals)
+        assert np.array_equal(fb.ranges.cpu().numpy().view(np.uint32), ranges)
+        got = {key: v.cpu().numpy() for key, v in fb.image.items()}
+        tgt = {key: (v.cpu().numpy() if hasattr(v, "cpu") else v) for key, v in al.targets[k].items()}
+        for r0, r1 in BANDS:
+            ref = oracle.render_fwd(b, w_eff[k], cam, bg, rows=(r0, r1))
+            for key in ("rgb", "depth", "sil", "t_final"):
+                assert np.abs(got[key][r0:r1].astype(np.float64) - ref[key][r0:r1]).max() <= 1e-4, key
+            for key in ("n_contrib", "max_id"):
+                assert np.array_equal(got[key][r0:r1], ref[key][r0:r1]), key
+            # association of the band: A's render of the keyframe from the oracle as well
+            ref_a = oracle.render_fwd(a, kfs[k], cam, bg, rows=(r0, r1))
+            assert np.array_equal(tgt["max_id"][r0:r1], ref_a["max_id"][r0:r1])
+            pr, cr = oracle.assoc(ref_a["max_id"][r0:r1], ref_a["t_final"][r0:r1], ref["max_id"][r0:r1],
+                                  ref["t_final"][r0:r1], 0.5)
+            _assoc_band(dev, tgt, got, r0, r1, a.n, b.n, pr, cr)
+        # the pairs are mostly the same surface element: B's id maps to A's through the shuffle
+        al.associate(k)
+        torch.cuda.synchronize()
+        m = int(al.m_dev.item())
+        assert int(al.assoc_status.item()) == 0 and m > 2000
+        pairs = al.pairs[:m].cpu().numpy()
+        counts = al.counts[:m].cpu().numpy()
+        same = perm[pairs[:, 1]] == pairs[:, 0]
+        assert counts[same].sum() > 0.5 * counts.sum()
+
+
+def _assoc_band(dev, tgt, got, r0, r1, n_a, n_b, ref_pairs, ref_counts):
+    from paper_2412_09723_gb300 import binding as B
+
+    t = [torch.as_tensor(np.ascontiguousarray(x[r0:r1]), device=dev)
+         for x in (tgt["max_id"], tgt["t_final"], got["max_id"], got["t_final"])]
+    npix = t[0].numel()
+    pairs = torch.zeros(npix, 2, dtype=torch.int32, device=dev)
+    counts = torch.zeros(npix, dtype=torch.int32, device=dev)
+    m_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(B.splat_assoc_workspace_size(npix), dtype=torch.uint8, device=dev)
+    B.splat_assoc(t[0], t[1], t[2], t[3], n_a, n_b, 0.5, pairs, counts, npix, m_dev, status, ws)
+    m = int(m_dev.item())
+    assert int(status.item()) == 0 and m == len(ref_pairs)
+    assert np.array_equal(pairs[:m].cpu().numpy(), ref_pairs)
+    assert np.array_equal(counts[:m].cpu().numpy(), ref_counts)
+
+
+def test_alignment_converges(dev):
+    """40 iterations (graph replays) from 1 cm / 0.5 degrees off T_true."""
+    cam = scenes.Camera(600, 340, 300.0, 300.0, 300.0, 170.0)
+    al, (a, b, perm, T_true, kfs, T0) = _alignment(dev, 200_000, cam)
+    e0 = al.error(T_true)
+    al.capture()
+    al.replay()
+    torch.cuda.synchronize()
+    l0 = float(al.loss.item())
+    for _ in range(39):
+        al.replay()
+    torch.cuda.synchronize()
+    l1 = float(al.loss.item())
+    e1 = al.error(T_true)
+    assert al.status() == 0
+    assert l1 < l0
+    assert e1[0] < 0.3 * e0[0] and e1[1] < 0.4 * e0[1], (e0, e1)
+
+
+def test_alignment_graph_equals_eager(dev):
+    """Graph replays and eager steps give the same T_rel."""
+    cam = scenes.Camera(320, 180, 160.0, 160.0, 160.0, 90.0)
+    al, (a, b, perm, T_true, kfs, T0) = _alignment(dev, 40_000, cam)
+    for _ in range(5):
+        al.step()
+    torch.cuda.synchronize()
+    T_eager = al.T.cpu().numpy().copy()
+    al.reset(T0)
+    al.capture()
+    for _ in range(5):
+        al.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(al.T.cpu().numpy(), T_eager, atol=1e-6)
