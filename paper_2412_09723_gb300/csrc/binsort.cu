@@ -424,23 +424,42 @@ __global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(
 }
 
 // One CTA per tile: sort its bucket ascending by (depth bits, id) and write
-// the ids (and optionally the (tile, depth) keys).
+// the ids (and optionally the (tile, depth) keys).  Buckets of up to 256 keys
+// are bitonic-sorted; longer ones go through the shared-memory radix sort
+// (chunks of kSegCap keys, merged in global memory above that).  Dynamic
+// shared memory: two key buffers of kSegCap, 8 x 256 digit counters, scan
+// scratch.
+constexpr size_t kSortSmem = 2 * sizeof(uint64_t) * kSegCap + sizeof(uint32_t) * (kSegRadixWarps * 256 + 64);
+constexpr int kSortBitonicMax = 256;
+
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint2* __restrict__ ranges,
                                                                  uint64_t* __restrict__ skeys,
                                                                  uint64_t* __restrict__ skeys2,
                                                                  uint32_t* __restrict__ vals,
                                                                  uint64_t* __restrict__ keys_out) {
-  __shared__ uint64_t smem[kSegCap];
+  extern __shared__ __align__(16) unsigned char sort_smem[];
+  uint64_t* bufa = reinterpret_cast<uint64_t*>(sort_smem);
+  uint64_t* bufb = bufa + kSegCap;
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(bufb + kSegCap);
+  uint32_t* sh = cnt + kSegRadixWarps * 256;
   const int tile = blockIdx.x;
   const uint2 rg = ranges[tile];
   const int n = (int)(rg.y - rg.x);
   if (n <= 0) return;
+  auto sort_chunk = [&](const uint64_t* src, int m) -> const uint64_t* {
+    if (m <= kSortBitonicMax) {
+      cta_sort_small(src, m, bufa);
+      return bufa;
+    }
+    for (int i = threadIdx.x; i < m; i += kSortThreads) bufa[i] = src[i];
+    __syncthreads();
+    return cta_radix_sort_hi32(bufa, bufb, m, cnt, sh);
+  };
   const uint64_t* sorted;
   if (n <= kSegCap) {
-    cta_sort_small(skeys + rg.x, n, smem);
-    sorted = smem;
+    sorted = sort_chunk(skeys + rg.x, n);
   } else {
-    cta_sort_segment(skeys + rg.x, skeys2 + rg.x, skeys + rg.x, n, smem, kSegCap);
+    cta_sort_segment_with(skeys + rg.x, skeys2 + rg.x, skeys + rg.x, n, kSegCap, sort_chunk);
     sorted = skeys2 + rg.x;
   }
   const uint64_t thi = (uint64_t)tile << 32;
@@ -556,8 +575,20 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
                bucket_scatter_kernel<<<sgrid, kScatterThreads, scatter_smem, s>>>(
                    w.vis, w.n_vis, xyzo, rect, ck.tiles_x, (int)n_tiles, w.cursor, capacity, w.skeys));
   if ((rc = check_launch("bucket_scatter_kernel"))) return rc;
+  {
+    static std::atomic<unsigned long long> sort_attr_done{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(SPLAT_ECUDA, "splat_bin_sort: no current device");
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(sort_attr_done.load() & bit)) {
+      if (cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem) !=
+          cudaSuccess)
+        return fail(SPLAT_ECUDA, "splat_bin_sort: cannot enable shared memory for the tile sort");
+      sort_attr_done.fetch_or(bit);
+    }
+  }
   SPLAT_LAUNCH("tile_sort_kernel", s,
-               tile_sort_kernel<<<(unsigned)n_tiles, kSortThreads, 0, s>>>(reinterpret_cast<const uint2*>(ranges),
-                                                                          w.skeys, w.skeys2, vals, keys));
+               tile_sort_kernel<<<(unsigned)n_tiles, kSortThreads, kSortSmem, s>>>(
+                   reinterpret_cast<const uint2*>(ranges), w.skeys, w.skeys2, vals, keys));
   return check_launch("tile_sort_kernel");
 }

@@ -14,11 +14,12 @@
 //
 // Backward: 128 threads with 2 pixels each ((x, y) and (x, y + 2); a warp
 // covers 16 x 4 pixels).  Every pixel starts from its final transmittance and
-// last contributor, walks the list back to front, recovers
-// T_i = T_{i+1} / (1 - alpha_i), and keeps the suffix sums
-// R_X <- X_i alpha_i + (1 - alpha_i) R_X of colour, depth and silhouette, so
-// dL/dalpha_i = T_i [gC.(c_i - R_C) + gD (z_i - R_D) + gS (1 - R_S)]
-//             - (gC.bg) T_final / (1 - alpha_i).
+// last contributor, walks the list back to front and recovers
+// T_i = T_{i+1} / (1 - alpha_i).  With the pixel's upstream gradients folded
+// into one scalar per Gaussian, P_i = gC.c_i + gD z_i + gS, and the weights
+// w_j = alpha_j T_j, every later weight carries a factor (1 - alpha_i), so
+// dL/dalpha_i = T_i P_i - [sum_{j>i} w_j P_j + (gC.bg) T_final] / (1 - alpha_i);
+// the bracket is one running sum per pixel (started at (gC.bg) T_final).
 // Per Gaussian and warp, ten sums are reduced with a recursive-halving
 // reduce-scatter (five moments of dL/dpower -- sum dp dx, dp dy, dp dx^2,
 // dp dx dy, dp dy^2 -- whose conic terms are applied once per Gaussian, plus
@@ -240,7 +241,7 @@ __device__ __forceinline__ int warp_reduce_scatter10(const float (&v)[10], float
 }
 
 struct BwdPix {
-  float fx, fy, T, gC0, gC1, gC2, gD, gS, gbgT, R0, R1, R2, RD, RS;
+  float fx, fy, T, gC0, gC1, gC2, gD, gS, Q;  // Q = sum_{j>i} w_j P_j + (gC.bg) T_final
   int last;
 };
 
@@ -265,17 +266,12 @@ __device__ __forceinline__ bool adjoint_step(BwdPix& q, const float4 xo, const f
   v[7] = __fmaf_rn(q.gC1, w, v[7]);
   v[8] = __fmaf_rn(q.gC2, w, v[8]);
   v[9] = __fmaf_rn(q.gD, w, v[9]);
-  float dA = q.gC0 * (c0 - q.R0);
-  dA = __fmaf_rn(q.gC1, c1 - q.R1, dA);
-  dA = __fmaf_rn(q.gC2, c2 - q.R2, dA);
-  dA = __fmaf_rn(q.gD, xo.z - q.RD, dA);
-  dA = __fmaf_rn(q.gS, 1.0f - q.RS, dA);
-  dA = __fmaf_rn(dA, q.T, -q.gbgT * r);
-  q.R0 = __fmaf_rn(c0, alpha, om * q.R0);
-  q.R1 = __fmaf_rn(c1, alpha, om * q.R1);
-  q.R2 = __fmaf_rn(c2, alpha, om * q.R2);
-  q.RD = __fmaf_rn(xo.z, alpha, om * q.RD);
-  q.RS = __fmaf_rn(1.0f, alpha, om * q.RS);
+  float P = __fmaf_rn(q.gC0, c0, q.gS);
+  P = __fmaf_rn(q.gC1, c1, P);
+  P = __fmaf_rn(q.gC2, c2, P);
+  P = __fmaf_rn(q.gD, xo.z, P);
+  const float dA = __fmaf_rn(q.T, P, -(r * q.Q));
+  q.Q = __fmaf_rn(w, P, q.Q);
   if (!(raw > kAlphaCap)) {
     v[5] = __fmaf_rn(G, dA, v[5]);
     const float dp = raw * dA;
@@ -327,8 +323,7 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
     b.gC2 = inside ? V.d_rgb[3 * i + 2] : 0.f;
     b.gD = (inside && V.d_depth) ? V.d_depth[i] : 0.f;
     b.gS = (inside && V.d_sil) ? V.d_sil[i] : 0.f;
-    b.gbgT = (b.gC0 * V.bg0 + b.gC1 * V.bg1 + b.gC2 * V.bg2) * Tfin;
-    b.R0 = b.R1 = b.R2 = b.RD = b.RS = 0.f;
+    b.Q = (b.gC0 * V.bg0 + b.gC1 * V.bg1 + b.gC2 * V.bg2) * Tfin;
   }
   const int lane = threadIdx.x & 31;
   const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(q[0].last, q[1].last));

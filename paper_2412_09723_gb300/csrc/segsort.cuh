@@ -148,12 +148,9 @@ __device__ void cta_bitonic_reg(uint64_t* s, int n2) {
   __syncthreads();
 }
 
-// Sort in[0, n) into smem (n <= cap) and leave the result in smem[0, n).
-// blockDim.x must be 256 when n can exceed 256 (register-blocked stages).
-__device__ __forceinline__ void cta_sort_small(const uint64_t* in, int n, uint64_t* smem) {
-  const int n2 = next_pow2(n < 1 ? 1 : n);
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) smem[i] = i < n ? in[i] : ~0ull;
-  __syncthreads();
+// Bitonic sort of smem[0, n2) (n2 a power of two, already padded).
+// blockDim.x must be 256 when n2 can exceed 256 (register-blocked stages).
+__device__ __forceinline__ void cta_bitonic_any(uint64_t* smem, int n2) {
   if (blockDim.x != 256 || n2 <= 256) {
     cta_bitonic_u64(smem, n2);
     return;
@@ -164,6 +161,158 @@ __device__ __forceinline__ void cta_sort_small(const uint64_t* in, int n, uint64
     case 8: cta_bitonic_reg<8>(smem, n2); break;
     default: cta_bitonic_u64(smem, n2); break;  // 4096: shared-memory stages only
   }
+}
+
+// Sort in[0, n) into smem (n <= cap) and leave the result in smem[0, n).
+__device__ __forceinline__ void cta_sort_small(const uint64_t* in, int n, uint64_t* smem) {
+  const int n2 = next_pow2(n < 1 ? 1 : n);
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) smem[i] = i < n ? in[i] : ~0ull;
+  __syncthreads();
+  cta_bitonic_any(smem, n2);
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort in shared memory of 64-bit keys whose high word is the
+// primary key and whose low word breaks ties (depth bits | id).  Only the
+// high-word bits that differ within the segment are sorted, 8 per pass, each
+// pass a stable counting sort: every warp owns a contiguous slice and counts
+// its digits in its own 256 counters (shared-memory atomics), the (digit,
+// warp) counters are turned into exclusive offsets, and every key goes to its
+// counter's offset plus the number of lower lanes with the same digit (lanes
+// with equal digits found with ballots, the lowest one advancing the counter).  Keys
+// with equal high words then still sit in input order, so each run of equal
+// high words is re-sorted by the full key (runs longer than 32 make the CTA
+// bitonic-sort the whole segment instead).  256 threads; a and b hold cap
+// keys each (cap a power of two >= n); cnt: 8 x 256 counters; sh: 34 words.
+// Returns the buffer (a or b) holding the sorted keys.
+// ---------------------------------------------------------------------------
+constexpr int kSegRadixThreads = 256;
+constexpr int kSegRadixWarps = kSegRadixThreads / 32;
+constexpr int kRadixBatch = 4;  // rounds of 32 keys a warp loads and ranks before placing them
+
+// Active lanes of the warp whose 8-bit digit equals this lane's (eight ballots).
+__device__ __forceinline__ unsigned same_digit_lanes(uint32_t d, bool act) {
+  unsigned m = __ballot_sync(0xffffffffu, act);
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const unsigned v = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? v : ~v;
+  }
+  return m;
+}
+
+__device__ __forceinline__ uint64_t* cta_radix_sort_hi32(uint64_t* a, uint64_t* b, int n, uint32_t* cnt,
+                                                         uint32_t* sh) {
+  const unsigned full = 0xffffffffu;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  // 1. the high-word bits that differ
+  uint32_t mn = 0xffffffffu, mx = 0u;
+  for (int i = t; i < n; i += kSegRadixThreads) {
+    const uint32_t h = (uint32_t)(a[i] >> 32);
+    mn = min(mn, h);
+    mx = max(mx, h);
+  }
+  mn = __reduce_min_sync(full, mn);
+  mx = __reduce_max_sync(full, mx);
+  if (lane == 0) {
+    sh[warp] = mn;
+    sh[kSegRadixWarps + warp] = mx;
+  }
+  __syncthreads();
+  for (int w = 0; w < kSegRadixWarps; ++w) {
+    mn = min(mn, sh[w]);
+    mx = max(mx, sh[kSegRadixWarps + w]);
+  }
+  __syncthreads();  // sh is reused by the scans below
+  const uint32_t diff = mn ^ mx;
+  const int top = diff ? 64 - __clz(diff) : 32;  // sort bits [32, top)
+  // 2. counting-sort passes over 8-bit digits
+  const int per = (n + kSegRadixWarps - 1) / kSegRadixWarps;
+  const int w0 = min(n, warp * per), w1 = min(n, w0 + per);
+  const unsigned lower = (1u << lane) - 1u;
+  uint32_t* wc = cnt + warp * 256;
+  uint64_t* src = a;
+  uint64_t* dst = b;
+  for (int shift = 32; shift < top; shift += 8) {
+    for (int i = t; i < kSegRadixWarps * 256; i += kSegRadixThreads) cnt[i] = 0u;
+    __syncthreads();
+    for (int i = w0 + lane; i < w1; i += 32) atomicAdd(&wc[(uint32_t)(src[i] >> shift) & 0xffu], 1u);
+    __syncthreads();
+    {
+      const int d = t;  // one digit per thread
+      uint32_t tot = 0u;
+      for (int w = 0; w < kSegRadixWarps; ++w) tot += cnt[w * 256 + d];
+      uint32_t off;
+      block_excl_scan<kSegRadixThreads>(tot, off, sh);
+      for (int w = 0; w < kSegRadixWarps; ++w) {
+        const uint32_t c = cnt[w * 256 + d];
+        cnt[w * 256 + d] = off;
+        off += c;
+      }
+    }
+    __syncthreads();
+    for (int base = w0; base < w1; base += 32 * kRadixBatch) {
+      uint64_t key[kRadixBatch];
+      uint32_t dg[kRadixBatch];
+      unsigned peers[kRadixBatch];
+#pragma unroll
+      for (int r = 0; r < kRadixBatch; ++r) {
+        const int i = base + 32 * r + lane;
+        const bool act = i < w1;
+        key[r] = act ? src[i] : 0ull;
+        dg[r] = (uint32_t)(key[r] >> shift) & 0xffu;
+        peers[r] = same_digit_lanes(dg[r], act);
+      }
+#pragma unroll
+      for (int r = 0; r < kRadixBatch; ++r) {
+        if (base + 32 * r >= w1) break;  // warp-uniform
+        const bool act = base + 32 * r + lane < w1;
+        const unsigned before = peers[r] & lower;
+        const uint32_t pos = act ? wc[dg[r]] + (uint32_t)__popc(before) : 0u;
+        __syncwarp();
+        if (act) {
+          dst[pos] = key[r];
+          if (before == 0u) wc[dg[r]] += (uint32_t)__popc(peers[r]);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    uint64_t* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  // 3. runs of equal high words, ordered by the full key
+  bool long_run = false;
+  for (int i = t + 1; i < n; i += kSegRadixThreads) {
+    const uint32_t h = (uint32_t)(src[i] >> 32);
+    if (h != (uint32_t)(src[i - 1] >> 32)) continue;
+    if (i >= 2 && (uint32_t)(src[i - 2] >> 32) == h) continue;  // only the run's second key acts
+    const int r0 = i - 1;
+    int r1 = i + 1;
+    while (r1 < n && (uint32_t)(src[r1] >> 32) == h && r1 - r0 <= 32) ++r1;
+    if (r1 - r0 > 32) {
+      long_run = true;
+      continue;
+    }
+    for (int x = r0 + 1; x < r1; ++x) {  // insertion sort of a short run
+      const uint64_t k = src[x];
+      int y = x - 1;
+      while (y >= r0 && src[y] > k) {
+        src[y + 1] = src[y];
+        --y;
+      }
+      src[y + 1] = k;
+    }
+  }
+  if (__syncthreads_or(long_run)) {
+    const int n2 = next_pow2(n);
+    for (int i = n + t; i < n2; i += kSegRadixThreads) src[i] = ~0ull;
+    __syncthreads();
+    cta_bitonic_any(src, n2);
+  }
+  return src;
 }
 
 // Number of elements of the sorted run r[0, m) that are < key (or <= key).
@@ -185,12 +334,15 @@ __device__ __forceinline__ int rank_le(const uint64_t* r, int m, uint64_t key) {
 }
 
 // Sort the segment in[0, n) (global) into out[0, n) (global).  tmp: global
-// scratch of n keys.  smem: cap keys of shared memory (cap a power of two).
-// `in` may alias `tmp` but not `out`.
-static __device__ void cta_sort_segment(const uint64_t* in, uint64_t* out, uint64_t* tmp, int n, uint64_t* smem, int cap) {
+// scratch of n keys.  sort_chunk(src, m) sorts the m <= cap keys src[0, m)
+// (global) into shared memory and returns where they are; cap is a power of
+// two.  `in` may alias `tmp` but not `out`.
+template <class SortChunk>
+__device__ void cta_sort_segment_with(const uint64_t* in, uint64_t* out, uint64_t* tmp, int n, int cap,
+                                      SortChunk sort_chunk) {
   if (n <= cap) {
-    cta_sort_small(in, n, smem);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = smem[i];
+    const uint64_t* r = sort_chunk(in, n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) out[i] = r[i];
     __syncthreads();
     return;
   }
@@ -203,8 +355,8 @@ static __device__ void cta_sort_segment(const uint64_t* in, uint64_t* out, uint6
   for (int c0 = 0; c0 < n; c0 += cap) {
     const int m = min(cap, n - c0);
     __syncthreads();
-    cta_sort_small(in + c0, m, smem);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) a[c0 + i] = smem[i];
+    const uint64_t* r = sort_chunk(in + c0, m);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) a[c0 + i] = r[i];
   }
   __syncthreads();
   // 2. merge runs of length L into runs of 2L
@@ -224,6 +376,15 @@ static __device__ void cta_sort_segment(const uint64_t* in, uint64_t* out, uint6
     a = b;
     b = t;
   }
+}
+
+// The same with bitonic chunk sorts in smem[0, cap).
+__device__ __forceinline__ void cta_sort_segment(const uint64_t* in, uint64_t* out, uint64_t* tmp, int n,
+                                                 uint64_t* smem, int cap) {
+  cta_sort_segment_with(in, out, tmp, n, cap, [smem](const uint64_t* src, int m) -> const uint64_t* {
+    cta_sort_small(src, m, smem);
+    return smem;
+  });
 }
 
 }  // namespace splat

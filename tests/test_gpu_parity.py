@@ -361,6 +361,27 @@ def test_deep_tiles_use_the_merge_path(dev):
     _check_image(fb, oracle.render_fwd(sc, np.eye(4, dtype=np.float32), cam, np.zeros(3, np.float32)))
 
 
+@pytest.mark.parametrize("levels", [1, 40, 1500])
+def test_depth_ties_break_by_id(dev, levels):
+    """Depths drawn from `levels` exact values (1: one fronto-parallel plane,
+    every tile one long run of equal depths; 40: runs of tens; 1500: short
+    runs): equal depths must come in ascending id order in every tile."""
+    rng = np.random.default_rng(levels)
+    n = 6000
+    z = (2.0 + 1e-3 * rng.integers(0, levels, n)).astype(np.float32)
+    sc = scenes.Scene(
+        mean=np.stack([rng.uniform(-0.3, 0.3, n), rng.uniform(-0.2, 0.2, n), z], axis=1).astype(np.float32),
+        log_scale=np.full((n, 3), -3.5, np.float32), quat=np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+        opacity_logit=rng.normal(-2.0, 0.5, n).astype(np.float32), rgb=rng.uniform(0, 1, (n, 3)).astype(np.float32))
+    cam = scenes.Camera(160, 112, 200.0, 200.0, 80.0, 56.0)
+    w2c = np.eye(4, dtype=np.float32)
+    p, fb = _render_gpu(sc, w2c, cam, (0, 0, 0), dev)
+    ranges = fb.ranges.cpu().numpy().view(np.uint32)
+    assert (ranges[:, 1] - ranges[:, 0]).max() > 256  # the radix path, not only the small bitonic one
+    _check_bins(fb, sc, w2c, cam)
+    _check_image(fb, oracle.render_fwd(sc, w2c, cam, np.zeros(3, np.float32)))
+
+
 def test_adam_groups_matches_per_group_adam(dev):
     from paper_2412_09723_gb300 import binding as B
 
