@@ -17,7 +17,8 @@ operations are spelled out one by one.
   sum_(k,l) r^T M r with r = T x_k - x_l over associated pairs, the combined
   covariance M^-1 = R Sigma_k R^T + Sigma_l evaluated at the current T and
   held fixed in the step (with R = I this is the printed Sigma_k + Sigma_l),
-  and T <- exp(delta^) T.
+  and T <- exp(delta^) T; optionally only pairs within a correspondence
+  distance (the G-ICP point-selection threshold of Sec. 4.1, 0.02).
 - Pruning, Algorithm 1: opacity below tau_o, or largest scale above tau_s, or
   largest scale above tau_e times the sum of the other two.
 """
@@ -148,9 +149,12 @@ def se3_exp(d):
     return T
 
 
-def mahalanobis_system(T, x_k, cov_k, x_l, cov_l, weights=None):
+def mahalanobis_system(T, x_k, cov_k, x_l, cov_l, weights=None, max_dist=None):
     """Cost, gradient g (6) and Gauss-Newton matrix H (6 x 6) of
-    sum_(k,l) w r^T M r at T (left perturbation delta = (rho, phi))."""
+    sum_(k,l) w r^T M r at T (left perturbation delta = (rho, phi)).  With
+    max_dist, pairs whose Euclidean residual |r| at T exceeds it are left out
+    (the correspondence distance threshold of the G-ICP point selection,
+    0.02 in Sec. 4.1)."""
     T = np.asarray(T, np.float64)
     R, t = T[:3, :3], T[:3, 3]
     cost, g, H = 0.0, np.zeros(6), np.zeros((6, 6))
@@ -158,6 +162,8 @@ def mahalanobis_system(T, x_k, cov_k, x_l, cov_l, weights=None):
         wi = 1.0 if weights is None else float(weights[i])
         p = R @ x_k[i] + t
         r = p - x_l[i]
+        if max_dist is not None and float(r @ r) > max_dist * max_dist:
+            continue
         M = np.linalg.inv(R @ cov_k[i] @ R.T + cov_l[i])
         J = np.hstack([np.eye(3), -skew(p)])  # d(exp(delta^) p)/d delta at 0
         cost += wi * float(r @ M @ r)
@@ -166,9 +172,9 @@ def mahalanobis_system(T, x_k, cov_k, x_l, cov_l, weights=None):
     return cost, g, H
 
 
-def mahalanobis_step(T, x_k, cov_k, x_l, cov_l, weights=None):
+def mahalanobis_step(T, x_k, cov_k, x_l, cov_l, weights=None, max_dist=None):
     """One Gauss-Newton step: delta = -H^-1 g, T <- exp(delta^) T."""
-    cost, g, H = mahalanobis_system(T, x_k, cov_k, x_l, cov_l, weights)
+    cost, g, H = mahalanobis_system(T, x_k, cov_k, x_l, cov_l, weights, max_dist)
     delta = -np.linalg.solve(H, g)
     return se3_exp(delta) @ np.asarray(T, np.float64), delta, cost
 

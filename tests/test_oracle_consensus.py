@@ -259,3 +259,25 @@ def test_prune_keeps_order_and_moves_rows_together():
     a2, b2 = C.prune([a, b], mask)
     assert b2.tolist() == [0, 2, 3, 6, 7, 8]
     np.testing.assert_array_equal(a2, a[b2])
+
+
+def test_mahalanobis_distance_threshold_drops_far_pairs():
+    """Pairs beyond max_dist contribute nothing: the system equals the one
+    built from the near pairs alone, and outliers beyond it cannot bias the
+    exact recovery."""
+    x_k, x_l, cov_k, cov_l, T_true = _pairs(16)
+    T = C.se3_exp([0.004, -0.003, 0.002, 0.002, -0.001, 0.002]) @ T_true
+    rng = np.random.default_rng(17)
+    out = rng.choice(len(x_k), 15, replace=False)
+    x_bad = x_l.copy()
+    x_bad[out] += rng.normal(0, 0.3, (15, 3)) + 0.2  # gross outliers, far beyond 2 cm
+    r = np.linalg.norm(x_k @ T[:3, :3].T + T[:3, 3] - x_bad, axis=1)
+    near = r <= 0.02
+    assert near.sum() == len(x_k) - 15
+    full = C.mahalanobis_system(T, x_k, cov_k, x_bad, cov_l, max_dist=0.02)
+    ref = C.mahalanobis_system(T, x_k[near], cov_k[near], x_bad[near], cov_l[near])
+    for a, b in zip(full, ref):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12)
+    for _ in range(5):
+        T, _, _ = C.mahalanobis_step(T, x_k, cov_k, x_bad, cov_l, max_dist=0.02)
+    np.testing.assert_allclose(T, T_true, atol=1e-10)
