@@ -376,26 +376,42 @@ def multi_agent_section(dev, steps, flush, seed_base=2):
             "plain": "each agent's own captured single-view step, replayed one after another"}
 
 
-def alignment_section(dev, flush, iters=40):
+def alignment_section(dev, flush, iters=40, maha_iters=3):
     """Two agents with 1M-Gaussian maps of the same room in frames 20 cm /
-    10 degrees apart; B's map rendered from 8 of A's keyframes at 1200x680
-    (one persistent forward and one backward launch over the 8 views, one CUDA
-    graph per iteration), `iters` alignment iterations of T_rel from 1 cm /
-    0.5 degrees off, then the association of every keyframe.  Frames/s counts
-    one fwd+bwd view render."""
+    10 degrees apart; B's map seen from 8 of A's keyframes at 1200x680.
+    Starting 1 cm / 0.5 degrees off T_true: `maha_iters` Gauss-Newton
+    iterations of the Mahalanobis alignment over the associated pairs (each:
+    one persistent forward launch over the 8 views, 8 associations, the
+    system, the solve), then `iters` render-based iterations of the Eq. (optim)
+    loss (L1 + SSIM + depth; one persistent forward and one backward launch
+    over the 8 views, one CUDA graph per iteration).  Frames/s counts one
+    fwd+bwd view of the render-based iterations."""
     import torch
 
     from paper_2412_09723_gb300 import align, scenes
 
     a, b, perm, T_true, kfs, T0, cam = scenes.workload_alignment()
     targets = align.render_targets(a, kfs, cam, dev)
-    al = align.Alignment(b, kfs, targets, cam, T0, dev)
+    al = align.Alignment(b, kfs, targets, cam, T0, dev, map_a=a)
     al.size_capacity()
     e0 = al.error(T_true)
+    al.mahalanobis(iters=1)  # warm-up
+    al.reset(T0)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(maha_iters)]
+    for k in range(maha_iters):
+        flush.fill_(float(k))
+        ev[k][0].record()
+        al.mahalanobis(iters=1)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    t_maha = [x.elapsed_time(y) for x, y in ev]
+    e_maha = al.error(T_true)
+    T_maha = al.T.clone()
     per_step = al.capture()
     for _ in range(3):
         al.replay()
-    al.reset(T0)
+    al.reset(T_maha)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
     for k in range(iters):
         flush.fill_(float(k))
@@ -405,8 +421,13 @@ def alignment_section(dev, flush, iters=40):
     torch.cuda.synchronize()
     t = [x.elapsed_time(y) for x, y in evs]
     e1 = al.error(T_true)
-    loss = float(al.loss.item())
-    flush.fill_(0.0)
+    loss, ssim_sum = (float(v) for v in al.loss.cpu())
+    # render-only refinement from the original start, for comparison
+    al.reset(T0)
+    for _ in range(iters):
+        al.replay()
+    torch.cuda.synchronize()
+    e_render_only = al.error(T_true)
     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ms = []
     for k in range(len(kfs)):
@@ -419,12 +440,16 @@ def alignment_section(dev, flush, iters=40):
     if al.status() != 0:
         raise SystemExit("device status set in the alignment steps")
     nv = len(kfs)
+    err = lambda e: {"trans_m": e[0], "rot_deg": e[1]}
     return {"workload": "align_2x1M_8views_1200x680", "views": nv, "value": nv * iters / (sum(t) / 1e3),
             "unit": UNIT, "ms_per_iteration": sum(t) / iters, "p50_ms": statistics.median(t),
             "p99_ms": _pct(t, 99), "iterations": iters, "gpu_launches_per_iteration": per_step,
-            "error_start": {"trans_m": e0[0], "rot_deg": e0[1]}, "error_end": {"trans_m": e1[0], "rot_deg": e1[1]},
-            "loss_end": loss, "assoc_ms_per_view": statistics.median(ms), "assoc_pairs_last_view": m_last,
-            "duplicates_K_view0": int(al.fbs[0].k_dev.item())}
+            "loss": "Eq. (optim): 0.8 L1 + 0.2 (1 - SSIM) + 0.1 L1 depth",
+            "error_start": err(e0), "mahalanobis_iterations": maha_iters,
+            "mahalanobis_ms_per_iteration": sum(t_maha) / maha_iters, "error_after_mahalanobis": err(e_maha),
+            "error_end": err(e1), "error_end_render_only_from_start": err(e_render_only),
+            "loss_end": loss, "ssim_end": ssim_sum / nv, "assoc_ms_per_view": statistics.median(ms),
+            "assoc_pairs_last_view": m_last, "duplicates_K_view0": int(al.fbs[0].k_dev.item())}
 
 
 def main():

@@ -57,7 +57,8 @@ enum {
   SPLAT_EINVAL = 1,    /* null pointer, bad size or misaligned buffer */
   SPLAT_ECAPACITY = 2, /* (device status) an output buffer was too small */
   SPLAT_ECUDA = 3,     /* a kernel launch or CUDA runtime call failed */
-  SPLAT_ETIMEOUT = 4   /* (device status) a bounded wait gave up */
+  SPLAT_ETIMEOUT = 4,  /* (device status) a bounded wait gave up */
+  SPLAT_ENUMERIC = 8   /* (device status) a linear system was not positive definite */
 };
 
 /* Pinhole camera.  tan(fov_x / 2) = width / (2 fx). */
@@ -397,6 +398,99 @@ int splat_assoc(const int32_t *id_a, const float *t_a, const int32_t *id_b, cons
                 int64_t npix, int64_t n_a, int64_t n_b, float t_max, int32_t *pairs,
                 int32_t *counts, int64_t capacity, int64_t *m_dev, int32_t *status, void *ws,
                 size_t ws_bytes, splat_stream_t stream);
+
+/*
+ * splat_loss_consensus -- the inter-agent optimisation loss of Eq. (optim)
+ * (Sec. 3.5 step 4) between a rendered image (C, D) and another agent's
+ * (C*, D*), with its SSIM term read as w_ssim (1 - SSIM) since the loss is
+ * minimised:
+ *   L = w_l1 mean|C - C*| + w_ssim (1 - SSIM(C, C*)) + w_geom mean|D - D*|,
+ * the paper's weights being 0.8, 0.2, 0.1 (Sec. 4.1).  SSIM is the mean over
+ * pixels and channels of the windowed statistic (11 x 11 Gaussian window,
+ * sigma 1.5, normalised; the image is zero outside its border;
+ * C1 = 0.01^2, C2 = 0.03^2).  Gradients with respect to C and D are written
+ * (overwritten) to d_rgb and d_depth (sign(0) = 0); C* and D* get none.
+ *   rgb, target_rgb: device float[H,W,3]; depth, target_depth: device float[H,W];
+ *   loss: device float[2], ADDED to: loss[0] += L, loss[1] += SSIM (the
+ *   caller zeroes it);
+ *   ws: splat_loss_consensus_workspace_size(H, W) bytes, 16-byte aligned.
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+size_t splat_loss_consensus_workspace_size(int32_t height, int32_t width);
+int splat_loss_consensus(const float *rgb, const float *depth, const float *target_rgb,
+                         const float *target_depth, int32_t height, int32_t width, float w_l1,
+                         float w_ssim, float w_geom, float *d_rgb, float *d_depth, float *loss,
+                         void *ws, size_t ws_bytes, splat_stream_t stream);
+
+/*
+ * splat_mahalanobis_system -- the Gauss-Newton system of the inter-agent
+ * alignment objective of Sec. 3.5 step 3,
+ *   sum_(k,l) w_kl r^T M r,  r = T x_l - x_k,  M^-1 = R Sigma_l R^T + Sigma_k,
+ * over associated pairs (k in map A, l in map B; T = (R, t) maps B's world
+ * into A's), for the left perturbation T <- exp(delta^) T, delta = (rho, phi).
+ * The combined covariance is taken at the current T and held fixed in the
+ * step (with R = I it is the printed Sigma_k + Sigma_l).  Sigma = R(q)
+ * diag(exp(2 log_scale)) R(q)^T of each Gaussian.
+ *   map_a, map_b: the two maps (mean, log_scale, quat are read);
+ *   pairs: device int32[capacity,2] of (id in A, id in B), as splat_assoc
+ *   writes them; weights: device int32[capacity] pair weights (e.g. the pixel
+ *   counts of splat_assoc) or NULL for weight 1; m_dev: device int64[1], the
+ *   number of valid pairs (min(M, capacity) are used);
+ *   T: device float[16] row-major;
+ *   max_dist: pairs whose residual |r| at T exceeds it are left out (the
+ *   correspondence distance of the G-ICP point selection, 0.02 in Sec. 4.1);
+ *   <= 0 keeps every pair;
+ *   sys: device double[28], ADDED to (the caller zeroes it): H's upper
+ *   triangle row by row (21, H = 2 sum w J^T M J), g (6, g = 2 sum w J^T M r),
+ *   cost (1), with J = [I | -[T x_l]x].
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_mahalanobis_system(const splat_gaussians *map_a, const splat_gaussians *map_b,
+                             const int32_t *pairs, const int32_t *weights, const int64_t *m_dev,
+                             int64_t capacity, const float *T, float max_dist, double *sys,
+                             splat_stream_t stream);
+
+/*
+ * splat_mahalanobis_step -- solves H delta = -g of a system written by
+ * splat_mahalanobis_system (Cholesky, double precision) and applies
+ * T <- exp(delta^) T.  delta_out: device double[6] or NULL.  If H is not
+ * positive definite T is left unchanged and SPLAT_ENUMERIC is raised in
+ * status (device int32[1]).  Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_mahalanobis_step(const double *sys, float *T, double *delta_out, int32_t *status,
+                           splat_stream_t stream);
+
+/*
+ * splat_prune -- Gaussian splat pruning (Algorithm 1, Suppl. "Gaussian Splat
+ * Pruning for Mapping"): a Gaussian is removed when its opacity
+ * 1 / (1 + exp(-logit)) < tau_o, or, when tau_s > 0, when its largest scale
+ * exp(log_scale) exceeds tau_s or exceeds tau_e times the sum of the other two
+ * (the paper's defaults are 0.005, 0.25, 10).  Every decision is taken in
+ * float32 with the exponential of splat_exp_f32 in this order: opacity =
+ * 1 / (1 + e), largest = max(max(s0, s1), s2), sum = (s0 + s1) + s2,
+ * elongated = largest > tau_e * (sum - largest).
+ * The kept rows of every column are written, in their original order, to the
+ * column's destination (a column is a float[n, width] array: a parameter, its
+ * gradient or an Adam moment), so the map and its optimiser state stay
+ * aligned.
+ *   g: the map (opacity_logit and log_scale are read);
+ *   cols: host array of n_cols (<= 16) descriptors; src and dst must not
+ *   overlap; width 1..16;
+ *   mask: device uint8[n] (1 = removed) or NULL;
+ *   n_keep_dev: device int64[1] receives the number of kept Gaussians;
+ *   ws: splat_prune_workspace_size(n) bytes.
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+typedef struct splat_column {
+  const float *src;
+  float *dst;
+  int32_t width;
+} splat_column;
+
+size_t splat_prune_workspace_size(int64_t n);
+int splat_prune(const splat_gaussians *g, float tau_o, float tau_s, float tau_e,
+                const splat_column *cols, int32_t n_cols, uint8_t *mask, int64_t *n_keep_dev,
+                void *ws, size_t ws_bytes, splat_stream_t stream);
 
 /*
  * splat_exp_f32 -- the exponential every kernel above uses, over n device

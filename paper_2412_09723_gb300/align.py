@@ -1,14 +1,21 @@
-"""Inter-agent association and render-based alignment (Sec. 3.5 steps 2-3).
+"""Inter-agent association and alignment (Sec. 3.5 steps 2-4).
 
 Agent B's map is brought into agent A's frame by a relative transform T_rel
 (B world -> A world).  B is rendered from A's keyframe poses w2c_k composed
-with T_rel, w2c_eff = w2c_k T_rel; the L1 colour + depth loss against A's own
-renders of the same keyframes is differentiated to every view's camera pose,
-and since w2c_k exp(d^) T_rel = exp((Ad_{w2c_k} d)^) w2c_k T_rel the gradient
-with respect to T_rel is sum_k Ad(w2c_k)^T d_cam_k; an Adam step with the
-retraction T_rel <- exp(delta^) T_rel follows.  All views are rendered forward
-and backward in one persistent launch each.  The association pairs the
-per-pixel maximum-weight Gaussians of A's and B's renders of each keyframe.
+with T_rel, w2c_eff = w2c_k T_rel, all views forward and backward in one
+persistent launch each.
+
+* Association (step 2): the per-pixel maximum-weight Gaussians of A's and B's
+  renders of each keyframe are paired (`associate`).
+* Alignment (step 3): Gauss-Newton on the Mahalanobis objective over the
+  associated pairs of all keyframes, T_rel <- exp(delta^) T_rel
+  (`mahalanobis`).
+* Optimisation (step 4): the loss of Eq. (optim) (L1 colour, SSIM and L1
+  depth with the paper's weights 0.8 / 0.2 / 0.1) between B's and A's renders
+  is differentiated to every view's camera pose; since
+  w2c_k exp(d^) T_rel = exp((Ad_{w2c_k} d)^) w2c_k T_rel, the gradient with
+  respect to T_rel is sum_k Ad(w2c_k)^T d_cam_k, and an Adam step with the
+  retraction T_rel <- exp(delta^) T_rel follows (`step`).
 """
 from __future__ import annotations
 
@@ -20,11 +27,15 @@ from .scenes import Camera
 
 
 class Alignment:
-    def __init__(self, map_b, keyframes, targets, cam: Camera, T_rel0, device, w_rgb=1.0, w_depth=1.0,
-                 lr=(1e-3, 4e-4), shape=(256, 4, 256, 7), capacity=None, want_keys=False):
+    def __init__(self, map_b, keyframes, targets, cam: Camera, T_rel0, device, loss="paper",
+                 weights=(0.8, 0.2, 0.1), lr=(1e-3, 4e-4), shape=(256, 4, 256, 7), capacity=None, want_keys=False,
+                 map_a=None):
         """map_b: Scene of B's map (B's world); keyframes: list of A's w2c
         (4x4); targets: list of dicts with A's renders ("rgb", "depth",
-        "max_id", "t_final") of the keyframes (device tensors)."""
+        "max_id", "t_final") of the keyframes (device tensors); loss: "paper"
+        (Eq. (optim) with `weights` = (L1, SSIM, geometry)) or "l1" (L1 colour
+        and depth with weights[0], weights[2]); map_a: A's map (Scene or
+        device tensors), needed by `mahalanobis`."""
         n_views = len(keyframes)
         if not 1 <= n_views <= B.SPLAT_MAX_VIEWS:
             raise ValueError(f"1..{B.SPLAT_MAX_VIEWS} keyframes")
@@ -44,9 +55,22 @@ class Alignment:
         self.m6 = torch.zeros(6, dtype=torch.float32, device=device)
         self.v6 = torch.zeros(6, dtype=torch.float32, device=device)
         self.t_dev = torch.zeros(1, dtype=torch.int32, device=device)
-        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.loss = torch.zeros(2, dtype=torch.float32, device=device)  # loss, SSIM
         self.lr = lr
-        self.w = (w_rgb, w_depth)
+        if loss not in ("paper", "l1"):
+            raise ValueError("loss must be 'paper' or 'l1'")
+        self.loss_kind = loss
+        self.w = tuple(weights)
+        self.loss_ws = torch.empty(max(16, B.splat_loss_consensus_workspace_size(cam.height, cam.width)),
+                                   dtype=torch.uint8, device=device)
+        self.map_a = None
+        if map_a is not None:
+            arrs = map_a.arrays() if hasattr(map_a, "arrays") else map_a
+            self.map_a = [torch.as_tensor(a, dtype=torch.float32, device=device).contiguous() for a in arrs]
+            self.cga = B.gaussians_struct(*self.map_a)
+        self.sys = torch.zeros(28, dtype=torch.float64, device=device)
+        self.delta = torch.zeros(6, dtype=torch.float64, device=device)
+        self.maha_status = torch.zeros(1, dtype=torch.int32, device=device)
         self.targets = targets
         self.fbs = [FrameBuffers(self.n, cam, device, capacity=capacity, want_keys=want_keys) for _ in range(n_views)]
         H, W = cam.height, cam.width
@@ -113,8 +137,12 @@ class Alignment:
                 g.zero_()
         for k, fb in enumerate(self.fbs):
             t = self.targets[k]
-            B.splat_loss_l1(fb.image["rgb"], fb.image["depth"], t["rgb"], t["depth"], self.w[0], self.w[1],
-                            self.g_rgb[k], self.g_depth[k], self.loss, s)
+            if self.loss_kind == "paper":
+                B.splat_loss_consensus(fb.image["rgb"], fb.image["depth"], t["rgb"], t["depth"], self.w[0], self.w[1],
+                                       self.w[2], self.g_rgb[k], self.g_depth[k], self.loss, self.loss_ws, s)
+            else:
+                B.splat_loss_l1(fb.image["rgb"], fb.image["depth"], t["rgb"], t["depth"], self.w[0], self.w[2],
+                                self.g_rgb[k], self.g_depth[k], self.loss, s)
         B.splat_render_bwd_batch(self.views, self.shape, self.ws, s)
         for k, fb in enumerate(self.fbs):
             B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c_eff[k], fb.bwd_ws, self.cgr, self.d_cam[k],
@@ -151,6 +179,7 @@ class Alignment:
     def reset(self, T_rel0):
         """Restart the optimisation from T_rel0."""
         self.T.copy_(torch.as_tensor(T_rel0, dtype=torch.float32))
+        self.maha_status.zero_()
         self.m6.zero_()
         self.v6.zero_()
         self.t_dev.zero_()
@@ -158,6 +187,26 @@ class Alignment:
     def error(self, T_true):
         """(translation metres, rotation degrees) of T_rel T_true^-1."""
         return pose_error(self.T.double().cpu().numpy(), T_true)
+
+    def mahalanobis(self, iters=3, views=None, t_max=0.5, weighted=True, max_dist=0.02, s=None):
+        """Gauss-Newton iterations of the Mahalanobis alignment over the pairs
+        associated in every keyframe (re-rendered and re-associated at each
+        iteration).  Pairs are weighted by their pixel counts unless
+        `weighted` is False; pairs farther apart than `max_dist` (the G-ICP
+        correspondence distance of Sec. 4.1) are left out."""
+        if self.map_a is None:
+            raise ValueError("the Mahalanobis alignment needs map_a")
+        s = torch.cuda.current_stream() if s is None else s
+        views = range(len(self.fbs)) if views is None else views
+        for _ in range(iters):
+            self.render(s)
+            with torch.cuda.stream(s):
+                self.sys.zero_()
+            for k in views:
+                self.associate(k, t_max, s)
+                B.splat_mahalanobis_system(self.cga, self.cg, self.pairs, self.counts if weighted else None,
+                                           self.m_dev, self.T, self.sys, max_dist, s)
+            B.splat_mahalanobis_step(self.sys, self.T, self.delta, self.maha_status, s)
 
     def associate(self, k, t_max=0.5, s=None):
         """Distinct (A id, B id) pairs of keyframe k with pixel counts (device
@@ -172,7 +221,7 @@ class Alignment:
                       self.assoc_ws, s)
 
     def status(self) -> int:
-        st = int(self.assoc_status.item())
+        st = int(self.assoc_status.item()) | int(self.maha_status.item())
         for fb in self.fbs:
             st |= int(fb.status.item())
         return st

@@ -17,7 +17,7 @@ from . import build as _build
 
 _c_i32, _c_i64, _c_f, _c_p, _c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
 
-SPLAT_OK, SPLAT_EINVAL, SPLAT_ECAPACITY, SPLAT_ECUDA, SPLAT_ETIMEOUT = 0, 1, 2, 3, 4
+SPLAT_OK, SPLAT_EINVAL, SPLAT_ECAPACITY, SPLAT_ECUDA, SPLAT_ETIMEOUT, SPLAT_ENUMERIC = 0, 1, 2, 3, 4, 8
 
 
 class SplatError(RuntimeError):
@@ -53,6 +53,10 @@ class CView(ctypes.Structure):
     _fields_ = [("proj", CProjected), ("rgb", _c_p), ("n", _c_i64), ("vals", _c_p), ("ranges", _c_p),
                 ("cam", CCamera), ("bg", ctypes.c_float * 3), ("image", CImage), ("d_rgb", _c_p), ("d_depth", _c_p),
                 ("d_sil", _c_p), ("grad2d", _c_p)]
+
+
+class CColumn(ctypes.Structure):
+    _fields_ = [("src", _c_p), ("dst", _c_p), ("width", _c_i32)]
 
 
 class CBatchShape(ctypes.Structure):
@@ -91,6 +95,13 @@ _SIGS = {
                      _c_sz, _c_p], ctypes.c_int),
     "splat_pose_compose": ([_c_i32, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_pose_rel_grad": ([_c_i32, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_loss_consensus_workspace_size": ([_c_i32, _c_i32], _c_sz),
+    "splat_loss_consensus": ([_c_p, _c_p, _c_p, _c_p, _c_i32, _c_i32, _c_f, _c_f, _c_f, _c_p, _c_p, _c_p, _c_p,
+                              _c_sz, _c_p], ctypes.c_int),
+    "splat_mahalanobis_system": ([_c_p, _c_p, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_f, _c_p, _c_p], ctypes.c_int),
+    "splat_mahalanobis_step": ([_c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_prune_workspace_size": ([_c_i64], _c_sz),
+    "splat_prune": ([_c_p, _c_f, _c_f, _c_f, _c_p, _c_i32, _c_p, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
     "splat_exp_f32": ([_c_p, _c_p, _c_i64, _c_p], ctypes.c_int),
 }
 
@@ -325,6 +336,48 @@ def splat_pose_rel_grad(w2c, d_cam, d_rel, stream=None):
     """d_rel = sum_k Ad(w2c[k])^T d_cam[k]."""
     _check("splat_pose_rel_grad", load().splat_pose_rel_grad(w2c.shape[0], _p(w2c), _p(d_cam), _p(d_rel),
                                                              _stream(stream)))
+
+
+def splat_loss_consensus_workspace_size(height, width) -> int:
+    return int(load().splat_loss_consensus_workspace_size(height, width))
+
+
+def splat_loss_consensus(rgb, depth, target_rgb, target_depth, w_l1, w_ssim, w_geom, d_rgb, d_depth, loss, ws,
+                         stream=None):
+    """`loss`: device float32[2] (loss, SSIM), added to."""
+    H, W = depth.shape
+    _check("splat_loss_consensus", load().splat_loss_consensus(
+        _p(rgb), _p(depth), _p(target_rgb), _p(target_depth), H, W, w_l1, w_ssim, w_geom, _p(d_rgb), _p(d_depth),
+        _p(loss), _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def splat_mahalanobis_system(map_a: CGaussians, map_b: CGaussians, pairs, weights, m_dev, T, sys, max_dist=0.0,
+                             stream=None):
+    """`pairs`: device int32[capacity, 2]; `sys`: device float64[28], added to."""
+    _check("splat_mahalanobis_system", load().splat_mahalanobis_system(
+        ctypes.byref(map_a), ctypes.byref(map_b), _p(pairs), _p(weights), _p(m_dev), pairs.shape[0], _p(T),
+        max_dist, _p(sys), _stream(stream)))
+
+
+def splat_mahalanobis_step(sys, T, delta, status, stream=None):
+    _check("splat_mahalanobis_step", load().splat_mahalanobis_step(_p(sys), _p(T), _p(delta), _p(status),
+                                                                    _stream(stream)))
+
+
+def splat_prune_workspace_size(n) -> int:
+    return int(load().splat_prune_workspace_size(n))
+
+
+def splat_prune(g: CGaussians, tau_o, tau_s, tau_e, columns, mask, n_keep_dev, ws, stream=None):
+    """`columns`: list of (src, dst) float32 device tensors of shape [n, width]
+    (or [n])."""
+    cols = (CColumn * max(1, len(columns)))()
+    for i, (src, dst) in enumerate(columns):
+        width = 1 if src.dim() == 1 else src.shape[1]
+        cols[i] = CColumn(_p(src), _p(dst), width)
+    _check("splat_prune", load().splat_prune(
+        ctypes.byref(g), tau_o, tau_s, tau_e, cols, len(columns), _p(mask), _p(n_keep_dev), _p(ws),
+        ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def splat_exp_f32(x, y, stream=None):

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsplat_gb300.so")
-SOURCES = ["api.cu", "project.cu", "binsort.cu", "render.cu", "assoc.cu", "profile.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "project.cu", "binsort.cu", "render.cu", "assoc.cu", "profile.cu", "noalloc.cu", "consensus.cu"]
 HEADERS = ["common.cuh", "internal.cuh", "segsort.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -69,6 +69,15 @@ __global__ void __launch_bounds__(256) loss_l1_kernel(const float* __restrict__ 
   }
 }
 
+int launch_loss_l1(const float* rgb, const float* depth, const float* trgb, const float* tdepth, int64_t npix,
+                   float sc, float sd, float* grgb, float* gdepth, float* loss, cudaStream_t s) {
+  if (npix == 0) return SPLAT_OK;
+  const int grid = (int)std::min<int64_t>((npix + 255) / 256, 152 * 8);
+  SPLAT_LAUNCH("loss_l1_kernel", s,
+               loss_l1_kernel<<<grid, 256, 0, s>>>(rgb, depth, trgb, tdepth, npix, sc, sd, grgb, gdepth, loss));
+  return check_launch("loss_l1_kernel");
+}
+
 // ----------------------------------------------------------------------------
 // Adam
 // ----------------------------------------------------------------------------
@@ -262,12 +271,8 @@ extern "C" int splat_loss_l1(const float* rgb, const float* depth, const float* 
   if (!rgb || !depth || !target_rgb || !target_depth || !d_rgb || !d_depth || npix < 0)
     return fail(SPLAT_EINVAL, "splat_loss_l1: bad argument");
   if (npix == 0) return SPLAT_OK;
-  const float sc = w_rgb / (float)(3 * npix);
-  const float sd = w_depth / (float)npix;
-  const int blocks = (int)std::min<int64_t>((npix + 255) / 256, 152 * 8);
-  SPLAT_LAUNCH("loss_l1_kernel", reinterpret_cast<cudaStream_t>(stream), loss_l1_kernel<<<blocks, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(rgb, depth, target_rgb, target_depth,
-                                                                              npix, sc, sd, d_rgb, d_depth, loss));
-  return check_launch("loss_l1_kernel");
+  return launch_loss_l1(rgb, depth, target_rgb, target_depth, npix, w_rgb / (float)(3 * npix), w_depth / (float)npix,
+                        d_rgb, d_depth, loss, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int splat_adam(float* param, const float* grad, float* m, float* v, int64_t n, const int32_t* step,

@@ -1,0 +1,599 @@
+// consensus.cu -- the inter-agent consensus terms and map pruning.
+//
+// * Loss of Eq. (optim) (Sec. 3.5 step 4): L1 colour, SSIM and L1 depth
+//   terms with their image gradients.  SSIM uses an 11 x 11 Gaussian window
+//   (sigma 1.5) over a zero-padded image; one CTA computes a 16 x 16 block of
+//   one channel: the 26 x 26 patch of both images is staged in shared memory,
+//   the window is applied separably (rows, then columns) to the five products
+//   x, y, x^2, y^2, xy, and each pixel's SSIM and its partial derivatives with
+//   respect to the three window sums that involve x (A = dS/dmu_x,
+//   B = dS/dE[x^2], C = dS/dE[xy]) are written out.  A second kernel applies
+//   the same window to A, B, C and forms
+//   dS/dx(q) = (W*A)(q) + 2 x(q) (W*B)(q) + y(q) (W*C)(q).
+// * Mahalanobis alignment (Sec. 3.5 step 3): one thread per associated pair
+//   builds its Gauss-Newton contribution (21 + 6 + 1 numbers) in float,
+//   accumulated in double per thread, reduced per CTA, and added to the
+//   system with double atomics; one thread solves the 6 x 6 system by
+//   Cholesky and retracts T.
+// * Pruning (Algorithm 1): a flag kernel (the three criteria, block counts),
+//   a one-CTA scan of the block counts, and a scatter kernel that re-ranks
+//   the kept Gaussians inside each block and copies every column's row.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.cuh"
+#include "segsort.cuh"
+
+namespace splat {
+
+// ----------------------------------------------------------------------------
+// SSIM
+// ----------------------------------------------------------------------------
+constexpr int kSsT = 16;                  // output block side
+constexpr int kSsR = 5;                   // window radius
+constexpr int kSsP = kSsT + 2 * kSsR;     // staged patch side (26)
+constexpr int kSsTaps = 2 * kSsR + 1;     // 11
+constexpr float kSsC1 = 0.01f * 0.01f;
+constexpr float kSsC2 = 0.03f * 0.03f;
+
+struct SsimWin {
+  float w[kSsTaps];  // 1-D Gaussian taps; the 2-D window is their outer product
+};
+
+static SsimWin ssim_window() {
+  double g[kSsTaps], tot = 0.0;
+  for (int i = 0; i < kSsTaps; ++i) {
+    const double r = i - kSsR;
+    g[i] = std::exp(-r * r / (2.0 * 1.5 * 1.5));
+    tot += g[i];
+  }
+  SsimWin w;
+  for (int i = 0; i < kSsTaps; ++i) w.w[i] = (float)(g[i] / tot);
+  return w;
+}
+
+__device__ __forceinline__ float block_sum_256(float v, float* red /*[8]*/) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < 8 ? red[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+// Stage the 26 x 26 patch of channel ch of an interleaved [H, W, 3] image
+// (zero outside the image).
+__device__ __forceinline__ void stage_patch(const float* __restrict__ img, int H, int W, int ch, int x0, int y0,
+                                            float (*dst)[kSsP]) {
+  for (int i = threadIdx.x; i < kSsP * kSsP; i += 256) {
+    const int r = i / kSsP, c = i - r * kSsP;
+    const int gy = y0 + r, gx = x0 + c;
+    const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+    dst[r][c] = in ? img[((size_t)gy * W + gx) * 3 + ch] : 0.f;
+  }
+}
+
+__global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
+                                                       int H, int W, SsimWin win, float loss_scale, float ssim_scale,
+                                                       float* __restrict__ abc, float* __restrict__ loss) {
+  __shared__ float sx[kSsP][kSsP], sy[kSsP][kSsP];
+  __shared__ float hs[5][kSsP][kSsT + 1];
+  __shared__ float red[8];
+  const int ch = blockIdx.z;
+  const int bx = blockIdx.x * kSsT, by = blockIdx.y * kSsT;
+  stage_patch(x, H, W, ch, bx - kSsR, by - kSsR, sx);
+  stage_patch(y, H, W, ch, bx - kSsR, by - kSsR, sy);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kSsP * kSsT; i += 256) {  // horizontal pass over all 26 rows
+    const int r = i / kSsT, c = i - r * kSsT;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSsTaps; ++k) {
+      const float u = sx[r][c + k], v = sy[r][c + k], w = win.w[k];
+      const float wu = w * u, wv = w * v;
+      a0 += wu;
+      a1 += wv;
+      a2 = fmaf(wu, u, a2);
+      a3 = fmaf(wv, v, a3);
+      a4 = fmaf(wu, v, a4);
+    }
+    hs[0][r][c] = a0;
+    hs[1][r][c] = a1;
+    hs[2][r][c] = a2;
+    hs[3][r][c] = a3;
+    hs[4][r][c] = a4;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & (kSsT - 1), ty = threadIdx.x / kSsT;
+  float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < kSsTaps; ++k) {
+    const float w = win.w[k];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) m[q] = fmaf(w, hs[q][ty + k][tx], m[q]);
+  }
+  const int gx = bx + tx, gy = by + ty;
+  float one_minus_s = 0.f, s = 0.f;
+  if (gx < W && gy < H) {
+    const float mx = m[0], my = m[1];
+    const float vx = m[2] - mx * mx, vy = m[3] - my * my, cxy = m[4] - mx * my;
+    const float a = 2.f * mx * my + kSsC1, b = 2.f * cxy + kSsC2;
+    const float c = mx * mx + my * my + kSsC1, d = vx + vy + kSsC2;
+    const float cd = c * d;
+    s = a * b / cd;
+    const float A = (2.f * my * (b - a)) / cd - s * (2.f * mx / c - 2.f * mx / d);
+    const float Bm = -s / d;
+    const float Cm = 2.f * a / cd;
+    const size_t i = ((size_t)gy * W + gx) * 3 + ch;
+    const size_t plane = (size_t)H * W * 3;
+    abc[i] = A;
+    abc[plane + i] = Bm;
+    abc[2 * plane + i] = Cm;
+    one_minus_s = 1.f - s;
+  }
+  const float t0 = block_sum_256(one_minus_s, red);
+  __syncthreads();
+  const float t1 = block_sum_256(s, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&loss[0], t0 * loss_scale);
+    atomicAdd(&loss[1], t1 * ssim_scale);
+  }
+}
+
+__global__ void __launch_bounds__(256) ssim_bwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
+                                                       int H, int W, SsimWin win, float grad_scale,
+                                                       const float* __restrict__ abc, float* __restrict__ d_rgb) {
+  __shared__ float sp[3][kSsP][kSsP];
+  __shared__ float hs[3][kSsP][kSsT + 1];
+  const int ch = blockIdx.z;
+  const int bx = blockIdx.x * kSsT, by = blockIdx.y * kSsT;
+  const size_t plane = (size_t)H * W * 3;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) stage_patch(abc + q * plane, H, W, ch, bx - kSsR, by - kSsR, sp[q]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kSsP * kSsT; i += 256) {
+    const int r = i / kSsT, c = i - r * kSsT;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSsTaps; ++k) {
+      const float w = win.w[k];
+      a0 = fmaf(w, sp[0][r][c + k], a0);
+      a1 = fmaf(w, sp[1][r][c + k], a1);
+      a2 = fmaf(w, sp[2][r][c + k], a2);
+    }
+    hs[0][r][c] = a0;
+    hs[1][r][c] = a1;
+    hs[2][r][c] = a2;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & (kSsT - 1), ty = threadIdx.x / kSsT;
+  const int gx = bx + tx, gy = by + ty;
+  if (gx >= W || gy >= H) return;
+  float ga = 0.f, gb = 0.f, gc = 0.f;
+#pragma unroll
+  for (int k = 0; k < kSsTaps; ++k) {
+    const float w = win.w[k];
+    ga = fmaf(w, hs[0][ty + k][tx], ga);
+    gb = fmaf(w, hs[1][ty + k][tx], gb);
+    gc = fmaf(w, hs[2][ty + k][tx], gc);
+  }
+  const size_t i = ((size_t)gy * W + gx) * 3 + ch;
+  d_rgb[i] = fmaf(grad_scale, ga + 2.f * x[i] * gb + y[i] * gc, d_rgb[i]);
+}
+
+// ----------------------------------------------------------------------------
+// Mahalanobis alignment
+// ----------------------------------------------------------------------------
+struct MapK {
+  const float* mean;
+  const float* log_scale;
+  const float* quat;
+};
+
+// Sigma = R(q) diag(exp(2 log_scale)) R(q)^T as (xx, xy, xz, yy, yz, zz).
+__device__ __forceinline__ void gaussian_cov(const MapK& g, int i, float S[6]) {
+  float qw = g.quat[4 * (size_t)i], qx = g.quat[4 * (size_t)i + 1], qy = g.quat[4 * (size_t)i + 2],
+        qz = g.quat[4 * (size_t)i + 3];
+  const float nn = qw * qw + qx * qx + qy * qy + qz * qz;
+  if (nn > 0.f) {
+    const float inv = rsqrtf(nn);
+    qw *= inv; qx *= inv; qy *= inv; qz *= inv;
+  } else {
+    qw = 1.f; qx = qy = qz = 0.f;
+  }
+  const float R[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                      2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                      2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+  float s2[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) s2[k] = expf(2.f * g.log_scale[3 * (size_t)i + k]);
+  int e = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b, ++e)
+      S[e] = R[3 * a] * s2[0] * R[3 * b] + R[3 * a + 1] * s2[1] * R[3 * b + 1] + R[3 * a + 2] * s2[2] * R[3 * b + 2];
+}
+
+constexpr int kSysN = 28;  // 21 (H upper) + 6 (g) + 1 (cost)
+
+__global__ void __launch_bounds__(256) mahalanobis_kernel(MapK A, MapK Bm, const int32_t* __restrict__ pairs,
+                                                          const int32_t* __restrict__ weights,
+                                                          const int64_t* __restrict__ m_dev, int64_t capacity,
+                                                          const float* __restrict__ T, float max_d2,
+                                                          double* __restrict__ sys) {
+  __shared__ double red[8][kSysN];
+  const int64_t M = min(*m_dev, capacity);
+  float R[9], t[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) R[3 * a + b] = T[4 * a + b];
+    t[a] = T[4 * a + 3];
+  }
+  double acc[kSysN];
+#pragma unroll
+  for (int k = 0; k < kSysN; ++k) acc[k] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+    const int ka = pairs[2 * i], lb = pairs[2 * i + 1];
+    const float w = weights ? (float)weights[i] : 1.f;
+    const float xb0 = Bm.mean[3 * (size_t)lb], xb1 = Bm.mean[3 * (size_t)lb + 1], xb2 = Bm.mean[3 * (size_t)lb + 2];
+    float p[3], r[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      p[a] = R[3 * a] * xb0 + R[3 * a + 1] * xb1 + R[3 * a + 2] * xb2 + t[a];
+      r[a] = p[a] - A.mean[3 * (size_t)ka + a];
+    }
+    if (max_d2 > 0.f && r[0] * r[0] + r[1] * r[1] + r[2] * r[2] > max_d2) continue;
+    float Sa[6], Sb[6];
+    gaussian_cov(A, ka, Sa);
+    gaussian_cov(Bm, lb, Sb);
+    // R Sb R^T + Sa
+    const float Sbf[9] = {Sb[0], Sb[1], Sb[2], Sb[1], Sb[3], Sb[4], Sb[2], Sb[4], Sb[5]};
+    float RS[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) RS[3 * a + b] = R[3 * a] * Sbf[b] + R[3 * a + 1] * Sbf[3 + b] + R[3 * a + 2] * Sbf[6 + b];
+    float S[6];
+    int e = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b, ++e)
+        S[e] = RS[3 * a] * R[3 * b] + RS[3 * a + 1] * R[3 * b + 1] + RS[3 * a + 2] * R[3 * b + 2] + Sa[e];
+    // inverse of the symmetric S (adjugate / determinant)
+    const float c00 = S[3] * S[5] - S[4] * S[4], c01 = S[2] * S[4] - S[1] * S[5], c02 = S[1] * S[4] - S[2] * S[3];
+    const float c11 = S[0] * S[5] - S[2] * S[2], c12 = S[1] * S[2] - S[0] * S[4], c22 = S[0] * S[3] - S[1] * S[1];
+    const float det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+    if (!(det > 0.f)) continue;
+    const float id = 1.f / det;
+    const float Mi[9] = {c00 * id, c01 * id, c02 * id, c01 * id, c11 * id, c12 * id, c02 * id, c12 * id, c22 * id};
+    // J = [I | -[p]x]; columns 3..5 of J are -[p]x = [[0, p2, -p1], [-p2, 0, p0], [p1, -p0, 0]]
+    float J[3][6] = {{1.f, 0.f, 0.f, 0.f, p[2], -p[1]}, {0.f, 1.f, 0.f, -p[2], 0.f, p[0]},
+                     {0.f, 0.f, 1.f, p[1], -p[0], 0.f}};
+    float MJ[3][6], Mr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Mr[a] = Mi[3 * a] * r[0] + Mi[3 * a + 1] * r[1] + Mi[3 * a + 2] * r[2];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) MJ[a][c] = Mi[3 * a] * J[0][c] + Mi[3 * a + 1] * J[1][c] + Mi[3 * a + 2] * J[2][c];
+    }
+    const float w2 = 2.f * w;
+    e = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int b = a; b < 6; ++b, ++e)
+        acc[e] += (double)(w2 * (J[0][a] * MJ[0][b] + J[1][a] * MJ[1][b] + J[2][a] * MJ[2][b]));
+#pragma unroll
+    for (int a = 0; a < 6; ++a) acc[21 + a] += (double)(w2 * (J[0][a] * Mr[0] + J[1][a] * Mr[1] + J[2][a] * Mr[2]));
+    acc[27] += (double)(w * (r[0] * Mr[0] + r[1] * Mr[1] + r[2] * Mr[2]));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kSysN; ++k) {
+    double v = acc[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kSysN) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+    if (v != 0.0) atomicAdd(&sys[threadIdx.x], v);
+  }
+}
+
+__global__ void mahalanobis_step_kernel(const double* __restrict__ sys, float* __restrict__ T,
+                                        double* __restrict__ delta_out, int32_t* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double H[6][6], L[6][6] = {}, g[6], d[6];
+  int o = 0;
+  for (int a = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b) H[a][b] = H[b][a] = sys[o++];
+  for (int a = 0; a < 6; ++a) g[a] = sys[21 + a];
+  for (int j = 0; j < 6; ++j) {  // Cholesky H = L L^T
+    double s = H[j][j];
+    for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+    if (!(s > 0.0)) {
+      raise_status(status, SPLAT_ENUMERIC);
+      if (delta_out)
+        for (int a = 0; a < 6; ++a) delta_out[a] = 0.0;
+      return;
+    }
+    L[j][j] = sqrt(s);
+    for (int i = j + 1; i < 6; ++i) {
+      double v = H[i][j];
+      for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+      L[i][j] = v / L[j][j];
+    }
+  }
+  double z[6];
+  for (int i = 0; i < 6; ++i) {  // L z = -g
+    double v = -g[i];
+    for (int k = 0; k < i; ++k) v -= L[i][k] * z[k];
+    z[i] = v / L[i][i];
+  }
+  for (int i = 5; i >= 0; --i) {  // L^T d = z
+    double v = z[i];
+    for (int k = i + 1; k < 6; ++k) v -= L[k][i] * d[k];
+    d[i] = v / L[i][i];
+  }
+  if (delta_out)
+    for (int a = 0; a < 6; ++a) delta_out[a] = d[a];
+  // exp(d^): R by Rodrigues, t = V rho
+  const double px = d[3], py = d[4], pz = d[5];
+  const double th2 = px * px + py * py + pz * pz, th = sqrt(th2);
+  double a1, b1, c1;  // sin(th)/th, (1 - cos)/th^2, (th - sin)/th^3
+  if (th < 1e-6) {
+    a1 = 1.0 - th2 / 6.0;
+    b1 = 0.5 - th2 / 24.0;
+    c1 = 1.0 / 6.0 - th2 / 120.0;
+  } else {
+    a1 = sin(th) / th;
+    b1 = (1.0 - cos(th)) / th2;
+    c1 = (th - sin(th)) / (th2 * th);
+  }
+  const double K[9] = {0.0, -pz, py, pz, 0.0, -px, -py, px, 0.0};
+  double K2[9], E[16];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) {
+      const double I = i == j ? 1.0 : 0.0;
+      E[4 * i + j] = I + a1 * K[3 * i + j] + b1 * K2[3 * i + j];
+    }
+    double tv = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      const double I = i == j ? 1.0 : 0.0;
+      tv += (I + b1 * K[3 * i + j] + c1 * K2[3 * i + j]) * d[j];
+    }
+    E[4 * i + 3] = tv;
+  }
+  E[12] = E[13] = E[14] = 0.0;
+  E[15] = 1.0;
+  double out[16];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < 4; ++k) v += E[4 * i + k] * (double)T[4 * k + j];
+      out[4 * i + j] = v;
+    }
+  for (int k = 0; k < 16; ++k) T[k] = (float)out[k];
+}
+
+// ----------------------------------------------------------------------------
+// Pruning
+// ----------------------------------------------------------------------------
+constexpr int kPrThreads = 256;
+constexpr int kPrMaxCols = 16;
+
+struct PruneCols {
+  const float* src[kPrMaxCols];
+  float* dst[kPrMaxCols];
+  int width[kPrMaxCols];
+  int n;
+};
+
+__device__ __forceinline__ bool prune_decision(const float* __restrict__ logit, const float* __restrict__ ls,
+                                               int64_t i, float tau_o, float tau_s, float tau_e) {
+  const float lam = __fdiv_rn(1.0f, __fadd_rn(1.0f, exp_full(-logit[i])));
+  bool pr = lam < tau_o;
+  if (tau_s > 0.f) {
+    const float s0 = exp_full(ls[3 * i]), s1 = exp_full(ls[3 * i + 1]), s2 = exp_full(ls[3 * i + 2]);
+    const float largest = fmaxf(fmaxf(s0, s1), s2);
+    const float total = __fadd_rn(__fadd_rn(s0, s1), s2);
+    pr |= largest > tau_s;
+    pr |= largest > __fmul_rn(tau_e, __fsub_rn(total, largest));
+  }
+  return pr;
+}
+
+__global__ void __launch_bounds__(kPrThreads) prune_flags_kernel(const float* __restrict__ logit,
+                                                                 const float* __restrict__ ls, int64_t n, float tau_o,
+                                                                 float tau_s, float tau_e, uint8_t* __restrict__ flag,
+                                                                 uint32_t* __restrict__ block_keep) {
+  const int64_t i = (int64_t)blockIdx.x * kPrThreads + threadIdx.x;
+  bool keep = false;
+  if (i < n) {
+    const bool pr = prune_decision(logit, ls, i, tau_o, tau_s, tau_e);
+    flag[i] = pr ? 1 : 0;
+    keep = !pr;
+  }
+  const int c = __syncthreads_count(keep);
+  if (threadIdx.x == 0) block_keep[blockIdx.x] = (uint32_t)c;
+}
+
+__global__ void __launch_bounds__(1024) prune_scan_kernel(const uint32_t* __restrict__ block_keep, int nb,
+                                                          uint32_t* __restrict__ block_off,
+                                                          int64_t* __restrict__ n_keep) {
+  __shared__ uint32_t sh[33];
+  uint32_t carry = 0;
+  for (int base = 0; base < nb; base += 1024) {
+    const int b = base + threadIdx.x;
+    const uint32_t c = b < nb ? block_keep[b] : 0u;
+    uint32_t excl;
+    const uint32_t tot = block_excl_scan<1024>(c, excl, sh);
+    if (b < nb) block_off[b] = carry + excl;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *n_keep = (int64_t)carry;
+}
+
+__global__ void __launch_bounds__(kPrThreads) prune_scatter_kernel(const uint8_t* __restrict__ flag, int64_t n,
+                                                                   const uint32_t* __restrict__ block_off,
+                                                                   PruneCols cols) {
+  __shared__ uint32_t sh[33];
+  const int64_t i = (int64_t)blockIdx.x * kPrThreads + threadIdx.x;
+  const bool keep = i < n && flag[i] == 0;
+  uint32_t excl;
+  block_excl_scan<kPrThreads>(keep ? 1u : 0u, excl, sh);
+  if (!keep) return;
+  const int64_t dst = (int64_t)block_off[blockIdx.x] + excl;
+  for (int c = 0; c < cols.n; ++c) {
+    const int w = cols.width[c];
+    const float* s = cols.src[c] + i * w;
+    float* d = cols.dst[c] + dst * w;
+    for (int k = 0; k < w; ++k) d[k] = s[k];
+  }
+}
+
+struct PruneWs {
+  uint8_t* flag;
+  uint32_t *block_keep, *block_off;
+};
+
+static size_t carve_prune(int64_t n, char* base, PruneWs* w) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  const size_t nb = (nn + kPrThreads - 1) / kPrThreads;
+  PruneWs t;
+  t.flag = (uint8_t*)take(nn);
+  t.block_keep = (uint32_t*)take(4 * nb);
+  t.block_off = (uint32_t*)take(4 * nb);
+  if (w) *w = t;
+  return off;
+}
+
+}  // namespace splat
+
+using namespace splat;
+
+// ----------------------------------------------------------------------------
+// Entry points
+// ----------------------------------------------------------------------------
+extern "C" size_t splat_loss_consensus_workspace_size(int32_t height, int32_t width) {
+  if (height < 0 || width < 0) return 0;
+  return align_up(sizeof(float) * 3 * 3 * (size_t)std::max(1, height) * (size_t)std::max(1, width));
+}
+
+extern "C" int splat_loss_consensus(const float* rgb, const float* depth, const float* target_rgb,
+                                    const float* target_depth, int32_t height, int32_t width, float w_l1,
+                                    float w_ssim, float w_geom, float* d_rgb, float* d_depth, float* loss, void* ws,
+                                    size_t ws_bytes, splat_stream_t stream) {
+  if (!rgb || !depth || !target_rgb || !target_depth || !d_rgb || !d_depth || !loss || height < 0 || width < 0)
+    return fail(SPLAT_EINVAL, "splat_loss_consensus: bad argument");
+  const int64_t npix = (int64_t)height * width;
+  if (npix == 0) return SPLAT_OK;
+  if (!ws || !aligned16(ws) || ws_bytes < splat_loss_consensus_workspace_size(height, width))
+    return fail(SPLAT_EINVAL, "splat_loss_consensus: workspace missing, too small or misaligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int rc = launch_loss_l1(rgb, depth, target_rgb, target_depth, npix, w_l1 / (float)(3 * npix),
+                          w_geom / (float)npix, d_rgb, d_depth, loss, s);
+  if (rc) return rc;
+  if (w_ssim == 0.f) return SPLAT_OK;
+  const SsimWin win = ssim_window();
+  const dim3 grid((unsigned)((width + kSsT - 1) / kSsT), (unsigned)((height + kSsT - 1) / kSsT), 3);
+  float* abc = static_cast<float*>(ws);
+  const float inv = 1.0f / (float)(3 * npix);
+  SPLAT_LAUNCH("ssim_fwd_kernel", s,
+               ssim_fwd_kernel<<<grid, 256, 0, s>>>(rgb, target_rgb, height, width, win, w_ssim * inv, inv, abc,
+                                                    loss));
+  if ((rc = check_launch("ssim_fwd_kernel"))) return rc;
+  SPLAT_LAUNCH("ssim_bwd_kernel", s,
+               ssim_bwd_kernel<<<grid, 256, 0, s>>>(rgb, target_rgb, height, width, win, -w_ssim * inv, abc, d_rgb));
+  return check_launch("ssim_bwd_kernel");
+}
+
+extern "C" int splat_mahalanobis_system(const splat_gaussians* map_a, const splat_gaussians* map_b,
+                                        const int32_t* pairs, const int32_t* weights, const int64_t* m_dev,
+                                        int64_t capacity, const float* T, float max_dist, double* sys,
+                                        splat_stream_t stream) {
+  if (!map_a || !map_b || !m_dev || !T || !sys || capacity < 0 || (capacity > 0 && !pairs))
+    return fail(SPLAT_EINVAL, "splat_mahalanobis_system: bad argument");
+  if ((map_a->n > 0 && (!map_a->mean || !map_a->log_scale || !map_a->quat)) ||
+      (map_b->n > 0 && (!map_b->mean || !map_b->log_scale || !map_b->quat)))
+    return fail(SPLAT_EINVAL, "splat_mahalanobis_system: null map array");
+  if (capacity == 0) return SPLAT_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const MapK A{map_a->mean, map_a->log_scale, map_a->quat}, Bm{map_b->mean, map_b->log_scale, map_b->quat};
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((capacity + 255) / 256, 2 * 152));
+  SPLAT_LAUNCH("mahalanobis_kernel", s,
+               mahalanobis_kernel<<<grid, 256, 0, s>>>(A, Bm, pairs, weights, m_dev, capacity, T,
+                                                       max_dist > 0.f ? max_dist * max_dist : 0.f, sys));
+  return check_launch("mahalanobis_kernel");
+}
+
+extern "C" int splat_mahalanobis_step(const double* sys, float* T, double* delta_out, int32_t* status,
+                                      splat_stream_t stream) {
+  if (!sys || !T || !status) return fail(SPLAT_EINVAL, "splat_mahalanobis_step: bad argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SPLAT_LAUNCH("mahalanobis_step_kernel", s, mahalanobis_step_kernel<<<1, 32, 0, s>>>(sys, T, delta_out, status));
+  return check_launch("mahalanobis_step_kernel");
+}
+
+extern "C" size_t splat_prune_workspace_size(int64_t n) { return n < 0 ? 0 : carve_prune(n, nullptr, nullptr); }
+
+extern "C" int splat_prune(const splat_gaussians* g, float tau_o, float tau_s, float tau_e, const splat_column* cols,
+                           int32_t n_cols, uint8_t* mask, int64_t* n_keep_dev, void* ws, size_t ws_bytes,
+                           splat_stream_t stream) {
+  if (!g || !n_keep_dev || !ws || n_cols < 0 || n_cols > kPrMaxCols || (n_cols > 0 && !cols) || g->n < 0 ||
+      g->n > 0x7fffffffLL)
+    return fail(SPLAT_EINVAL, "splat_prune: bad argument");
+  if (g->n > 0 && (!g->opacity_logit || !g->log_scale))
+    return fail(SPLAT_EINVAL, "splat_prune: opacity_logit / log_scale missing");
+  if (ws_bytes < carve_prune(g->n, nullptr, nullptr)) return fail(SPLAT_EINVAL, "splat_prune: workspace too small");
+  PruneCols pc;
+  pc.n = n_cols;
+  for (int c = 0; c < n_cols; ++c) {
+    if (!cols[c].src || !cols[c].dst || cols[c].width < 1 || cols[c].width > 16)
+      return fail(SPLAT_EINVAL, "splat_prune: column %d invalid", c);
+    pc.src[c] = cols[c].src;
+    pc.dst[c] = cols[c].dst;
+    pc.width[c] = cols[c].width;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (g->n == 0) {
+    if (cudaMemsetAsync(n_keep_dev, 0, sizeof(int64_t), s) != cudaSuccess)
+      return fail(SPLAT_ECUDA, "splat_prune: memset failed");
+    return SPLAT_OK;
+  }
+  PruneWs w;
+  carve_prune(g->n, static_cast<char*>(ws), &w);
+  uint8_t* flag = mask ? mask : w.flag;
+  const int nb = (int)((g->n + kPrThreads - 1) / kPrThreads);
+  SPLAT_LAUNCH("prune_flags_kernel", s,
+               prune_flags_kernel<<<nb, kPrThreads, 0, s>>>(g->opacity_logit, g->log_scale, g->n, tau_o, tau_s, tau_e,
+                                                            flag, w.block_keep));
+  int rc = check_launch("prune_flags_kernel");
+  if (rc) return rc;
+  SPLAT_LAUNCH("prune_scan_kernel", s, prune_scan_kernel<<<1, 1024, 0, s>>>(w.block_keep, nb, w.block_off, n_keep_dev));
+  if ((rc = check_launch("prune_scan_kernel"))) return rc;
+  if (n_cols == 0) return SPLAT_OK;
+  SPLAT_LAUNCH("prune_scatter_kernel", s,
+               prune_scatter_kernel<<<nb, kPrThreads, 0, s>>>(flag, g->n, w.block_off, pc));
+  return check_launch("prune_scatter_kernel");
+}

@@ -54,4 +54,9 @@ int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, c
                        const float* g2, int stride, const GradK& out, float* d_pose, float* d2d_out,
                        cudaStream_t s);
 
+// L1 terms: grgb = sc sign(rgb - trgb), gdepth = sd sign(depth - tdepth) (overwritten),
+// loss += sc sum|rgb - trgb| + sd sum|depth - tdepth|.
+int launch_loss_l1(const float* rgb, const float* depth, const float* trgb, const float* tdepth, int64_t npix,
+                   float sc, float sd, float* grgb, float* gdepth, float* loss, cudaStream_t s);
+
 }  // namespace splat
