@@ -6,7 +6,8 @@ package never imports it and shares no code with it.
 
 Inputs are plain numpy arrays (a `scenes.Scene`-like object with .mean,
 .log_scale, .quat, .opacity_logit, .rgb, and a camera with .width, .height,
-.fx, .fy, .cx, .cy, .z_near); outputs are numpy arrays.  `dtype` selects the
+.fx, .fy, .cx, .cy, .z_near and optionally .max_dist, the distance beyond
+which Gaussians are not candidates); outputs are numpy arrays.  `dtype` selects the
 float32 instantiation (bit-level parity; project exp) or the float64 one
 (std::exp; finite-difference checks).
 """
@@ -98,7 +99,7 @@ def _scene_args(scene, dtype):
 
 def _cam_args(cam, dtype):
     ci = np.array([cam.width, cam.height], dtype=np.int32)
-    cf = np.array([cam.fx, cam.fy, cam.cx, cam.cy, cam.z_near], dtype=dtype)
+    cf = np.array([cam.fx, cam.fy, cam.cx, cam.cy, cam.z_near, getattr(cam, "max_dist", 0.0)], dtype=dtype)
     return ci, cf
 
 

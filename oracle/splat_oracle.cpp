@@ -117,6 +117,7 @@ template <> struct K<float> {
 template <typename T> struct Cam {
   int width, height;
   T fx, fy, cx, cy, znear;
+  T maxdist;  // > 0: candidate selection by distance from the camera (Sec. 3.4 step 1)
   int tiles_x() const { return (width + TILE - 1) / TILE; }
   int tiles_y() const { return (height + TILE - 1) / TILE; }
 };
@@ -195,6 +196,13 @@ Proj<T> project_one(const T* x, const T* ls, const T* q, T logit, const T* w2c,
   if (!(z > cam.znear)) {  // near-plane cull (also rejects NaN)
     if (keep) *keep = f;
     return P;
+  }
+  if (cam.maxdist > T(0)) {  // distance selection: |p|^2 = (p0 p0 + p1 p1) + p2 p2 against maxdist^2
+    const T d2 = (f.p[0] * f.p[0] + f.p[1] * f.p[1]) + f.p[2] * f.p[2];
+    if (d2 > cam.maxdist * cam.maxdist) {
+      if (keep) *keep = f;
+      return P;
+    }
   }
   // EWA Jacobian with the guard-band clamp of x/z and y/z
   const T tan_x = T(cam.width) / (T(2) * cam.fx);
@@ -377,7 +385,7 @@ template <typename T>
 Cam<T> make_cam(const int32_t* ci, const T* cf) {
   Cam<T> c;
   c.width = ci[0]; c.height = ci[1];
-  c.fx = cf[0]; c.fy = cf[1]; c.cx = cf[2]; c.cy = cf[3]; c.znear = cf[4];
+  c.fx = cf[0]; c.fy = cf[1]; c.cx = cf[2]; c.cy = cf[3]; c.znear = cf[4]; c.maxdist = cf[5];
   return c;
 }
 
@@ -620,7 +628,7 @@ int render_bwd(const Scene<T>& S, const T* w2c, const Cam<T>& cam, const T* bg, 
 
 // ============================================================================
 // C ABI (host pointers; caller owns every buffer).
-// cam_i = {width, height}; cam_f = {fx, fy, cx, cy, z_near}; w2c = 4x4 row-major.
+// cam_i = {width, height}; cam_f = {fx, fy, cx, cy, z_near, max_dist}; w2c = 4x4 row-major.
 // ============================================================================
 extern "C" {
 

@@ -30,6 +30,7 @@ class Camera:
     cx: float
     cy: float
     z_near: float = 0.2
+    max_dist: float = 0.0  # > 0: only Gaussians within this distance of the camera are candidates
 
     @property
     def npix(self) -> int:

@@ -1,6 +1,7 @@
 """Pins of the CPU oracle against facts that do not come from the oracle itself:
 closed forms, hand-computed composites of the rendering equation (Sec. 3.3),
 invariants, brute force and an independent rotation library."""
+import dataclasses
 import json
 import math
 import os
@@ -327,3 +328,39 @@ def test_row_band_equals_full_frame_rows(orc):
     b = orc.render_bwd(sc, w2c, cam, bg, g, rows=(32, 64))
     for k in ("mean", "opacity_logit", "rgb", "pose"):
         np.testing.assert_allclose(a[k], b[k], rtol=1e-5, atol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# candidate selection by distance (Sec. 3.4 step 1)
+# ---------------------------------------------------------------------------
+def test_distance_selection_single_gaussian(orc):
+    cam = scenes.Camera(64, 48, 60.0, 60.0, 32.0, 24.0)
+    sc = scenes.Scene(np.float32([[0.1, -0.05, 2.0]]), np.full((1, 3), -3.0, np.float32),
+                      np.float32([[1, 0, 0, 0]]), np.float32([2.0]), np.float32([[1, 0, 0]]))
+    d = float(np.sqrt(0.1 ** 2 + 0.05 ** 2 + 2.0 ** 2))
+    near = dataclasses.replace(cam, max_dist=d * (1 - 1e-4))
+    far = dataclasses.replace(cam, max_dist=d * (1 + 1e-4))
+    assert orc.project(sc, np.eye(4, dtype=np.float32), near)["radius"][0] == 0
+    assert orc.project(sc, np.eye(4, dtype=np.float32), far)["radius"][0] > 0
+
+
+def test_distance_selection_equals_rendering_the_selected_subset(orc):
+    """Rendering with a distance limit equals rendering, without the limit,
+    only the Gaussians whose camera-space distance is within it."""
+    sc = scenes.scene_room(4000, 21)
+    w2c = scenes.perturbed_w2c(22, 0.3, 20.0)
+    cam = scenes.Camera(96, 72, 80.0, 80.0, 48.0, 36.0)
+    W = w2c.astype(np.float64)
+    dist = np.linalg.norm(sc.mean.astype(np.float64) @ W[:3, :3].T + W[:3, 3], axis=1)
+    r = np.sort(dist)
+    lo, hi = int(0.3 * len(r)), int(0.7 * len(r))
+    j = lo + int(np.argmax(np.diff(r[lo:hi])))
+    d = 0.5 * (r[j] + r[j + 1])
+    assert r[j + 1] - r[j] > 1e-5
+    keep = np.nonzero(dist <= d)[0]
+    assert 0.1 < len(keep) / sc.n < 0.9
+    a = orc.render_fwd(sc, w2c, dataclasses.replace(cam, max_dist=d), np.zeros(3, np.float32))
+    b = orc.render_fwd(sc.subset(keep), w2c, cam, np.zeros(3, np.float32))
+    for k in ("rgb", "depth", "sil", "t_final", "n_contrib"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(a["max_id"], np.where(b["max_id"] >= 0, keep[np.maximum(b["max_id"], 0)], -1))
