@@ -63,6 +63,7 @@ def _parse():
     ap.add_argument("--no-multi", action="store_true", help="skip the batched multi-agent comparison")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop comparison")
     ap.add_argument("--no-align", action="store_true", help="skip the two-agent association/alignment section")
+    ap.add_argument("--no-next", action="store_true", help="skip the consensus-loss / Mahalanobis / pruning timings")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson request trace")
     return ap.parse_args()
 
@@ -376,6 +377,137 @@ def multi_agent_section(dev, steps, flush, seed_base=2):
             "plain": "each agent's own captured single-view step, replayed one after another"}
 
 
+SSIM_OPS_PER_PX_CH = 211  # separable 11-tap window: 5 sums x 22 FMA + ~30 (fwd), 3 x 22 + ~5 (adjoint)
+MAHA_OPS_PER_PAIR = 420   # two covariances (~2 x 60), rotation of one (~54), 3x3 inverse (~30), J^T M J etc. (~210)
+
+
+def _time_calls(fn, reps, flush):
+    import torch
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for k in range(reps):
+        flush.fill_(float(k))
+        ev[k][0].record()
+        fn()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
+def next_rows_section(dev, flush, reps=20):
+    """The rows beyond the render path, each timed on its own at a size of the
+    workloads above (CUDA events, median of `reps`, L2 flushed between), with
+    algorithmic work and the fraction of the measured HBM or FP32 issue peak:
+    the Eq. (optim) loss with SSIM at 1200x680, the Mahalanobis system + step
+    over 100k associated pairs of two 1M maps, Algorithm 1 pruning of a 2M map
+    with its Adam state (15 columns), and the distance selection inside the
+    projection of the 300k room."""
+    import dataclasses
+
+    import numpy as np
+    import torch
+
+    from paper_2412_09723_gb300 import binding as B
+    from paper_2412_09723_gb300 import scenes
+    from paper_2412_09723_gb300.rasterizer import FrameBuffers
+
+    peaks, peak_kind = _peaks()
+    hbm = float(peaks["hbm_gbs"])
+    alu = SMS * FP32_LANES * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    out = {"peaks": {"hbm_gbs": hbm, "alu_tops": alu, "source": peak_kind}}
+    rng = np.random.default_rng(0)
+
+    # 1. Eq. (optim) loss with SSIM, 1200 x 680
+    H, W = 680, 1200
+    x = torch.rand(H, W, 3, device=dev)
+    y = (x + 0.05 * torch.randn(H, W, 3, device=dev)).clamp(0, 1)
+    d = 1 + torch.rand(H, W, device=dev)
+    dt = d + 0.01 * torch.randn(H, W, device=dev)
+    g_rgb, g_d, loss = torch.zeros_like(x), torch.zeros_like(d), torch.zeros(2, device=dev)
+    ws = torch.empty(B.splat_loss_consensus_workspace_size(H, W), dtype=torch.uint8, device=dev)
+    run = lambda: B.splat_loss_consensus(x, d, y, dt, 0.8, 0.2, 0.1, g_rgb, g_d, loss, ws)
+    run()
+    ms = _time_calls(run, reps, flush)
+    ms_l1 = _time_calls(lambda: B.splat_loss_l1(x, d, y, dt, 0.8, 0.1, g_rgb, g_d, loss), reps, flush)
+    npx = H * W
+    ops = SSIM_OPS_PER_PX_CH * 3 * npx
+    byt = 48 * npx  # C, D, C*, D* read, dC, dD written
+    out["consensus_loss_1200x680"] = {
+        "ms": ms, "ms_l1_terms": ms_l1, "ms_ssim_terms": ms - ms_l1,
+        "achieved_gbs": byt / (ms * 1e-3) / 1e9, "hbm_frac": byt / (ms * 1e-3) / 1e9 / hbm,
+        "ssim_tops": ops / ((ms - ms_l1) * 1e-3) / 1e12, "ssim_alu_frac": ops / ((ms - ms_l1) * 1e-3) / 1e12 / alu,
+        "work": f"{byt} algorithmic bytes (48 per pixel); {ops} SSIM ops ({SSIM_OPS_PER_PX_CH} per pixel-channel)"}
+
+    # 2. Mahalanobis system + step over 100k pairs of two 1M maps
+    a, b, perm, T_true, _, T0, _ = scenes.workload_alignment(n=1_000_000, n_views=1)
+    m = 100_000
+    lb = rng.choice(a.n, m, replace=False).astype(np.int32)
+    pairs = torch.as_tensor(np.stack([perm[lb].astype(np.int32), lb], 1), device=dev)
+    wts = torch.as_tensor(rng.integers(1, 40, m).astype(np.int32), device=dev)
+    pa = [torch.as_tensor(t, device=dev) for t in a.arrays()]
+    pb = [torch.as_tensor(t, device=dev) for t in b.arrays()]
+    ga, gb = B.gaussians_struct(*pa), B.gaussians_struct(*pb)
+    m_dev = torch.tensor([m], dtype=torch.int64, device=dev)
+    T = torch.as_tensor(T0, device=dev)
+    sys_ = torch.zeros(28, dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    T_keep = T.clone()
+
+    def maha():
+        sys_.zero_()
+        B.splat_mahalanobis_system(ga, gb, pairs, wts, m_dev, T, sys_, 0.02)
+        B.splat_mahalanobis_step(sys_, T, None, st)
+        T.copy_(T_keep)
+
+    maha()
+    ms = _time_calls(maha, reps, flush)
+    ops = MAHA_OPS_PER_PAIR * m
+    out["mahalanobis_100k_pairs"] = {
+        "ms": ms, "tops": ops / (ms * 1e-3) / 1e12, "alu_frac": ops / (ms * 1e-3) / 1e12 / alu,
+        "achieved_gbs": 92 * m / (ms * 1e-3) / 1e9,
+        "work": f"{MAHA_OPS_PER_PAIR} ops and 92 bytes (two Gaussians' mean, log-scale, quaternion; pair; weight) "
+                "per pair; includes the zeroing of the system and the one-thread 6x6 solve"}
+    del pa, pb, a, b
+
+    # 3. Algorithm 1 pruning of a 2M map with its Adam moments (15 columns)
+    n = 2_000_000
+    sc = scenes.scene_room(n, 5)
+    sc.opacity_logit = rng.normal(-1.0, 2.5, n).astype(np.float32)
+    src = [torch.as_tensor(t, device=dev) for t in sc.arrays()]
+    src += [torch.randn_like(t) for t in src] + [torch.rand_like(t) for t in src]
+    dst = [torch.empty_like(t) for t in src]
+    gg = B.gaussians_struct(*src[:5])
+    n_keep = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = torch.empty(B.splat_prune_workspace_size(n), dtype=torch.uint8, device=dev)
+    cols = list(zip(src, dst))
+    run = lambda: B.splat_prune(gg, 0.005, 0.25, 10.0, cols, None, n_keep, ws)
+    run()
+    ms = _time_calls(run, reps, flush)
+    kept = int(n_keep.item())
+    byt = 16 * n + 2 * 3 * 56 * kept + n  # logit + log-scale read; 42 floats read + written per kept; flags
+    out["prune_2M_15_columns"] = {
+        "ms": ms, "kept": kept, "n": n, "achieved_gbs": byt / (ms * 1e-3) / 1e9,
+        "hbm_frac": byt / (ms * 1e-3) / 1e9 / hbm,
+        "work": "16 B per Gaussian read for the decision, 336 B per kept Gaussian copied (parameters + 2 moments)"}
+    del src, dst, cols
+
+    # 4. distance selection inside the projection (300k room, 640x480)
+    sc, w2c, _, cam, _ = scenes.workload_track_map()
+    p = [torch.as_tensor(t, device=dev) for t in sc.arrays()]
+    g = B.gaussians_struct(*p)
+    w = torch.as_tensor(w2c, device=dev)
+    res = {}
+    for name, c in (("no_limit", cam), ("max_dist_2m", dataclasses.replace(cam, max_dist=2.0))):
+        fb = FrameBuffers(sc.n, c, dev)
+        run = lambda: B.splat_project(g, fb.ccam, w, fb.cproj)
+        run()
+        ms = _time_calls(run, reps, flush)
+        vis = float((fb.proj["radius"] > 0).float().mean())
+        res[name] = {"ms": ms, "visible_fraction": vis, "achieved_gbs": 112 * sc.n / (ms * 1e-3) / 1e9}
+    out["project_distance_selection_300k"] = res
+    return out
+
+
 def alignment_section(dev, flush, iters=40, maha_iters=3):
     """Two agents with 1M-Gaussian maps of the same room in frames 20 cm /
     10 degrees apart; B's map seen from 8 of A's keyframes at 1200x680.
@@ -625,6 +757,9 @@ def main():
     aligned = None
     if not args.no_align:
         aligned = alignment_section(dev, flush)
+    nxt = None
+    if not args.no_next:
+        nxt = next_rows_section(dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -643,7 +778,7 @@ def main():
                 "tracked_frames_per_s": value / EPISODE,
                 "wall_s_timed": t_wall, "gpu_launches": launches, "roofline": roofline, "kernels": breakdown,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "batched_multi_agent": multi,
-                "serving": served, "alignment": aligned}
+                "serving": served, "alignment": aligned, "next_rows": nxt}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -61,11 +61,14 @@ enum {
   SPLAT_ENUMERIC = 8   /* (device status) a linear system was not positive definite */
 };
 
-/* Pinhole camera.  tan(fov_x / 2) = width / (2 fx). */
+/* Pinhole camera.  tan(fov_x / 2) = width / (2 fx).  max_dist > 0 limits the
+ * candidates to Gaussians within that distance of the camera centre (the
+ * distance part of the candidate selection of Sec. 3.4 step 1); 0 = no limit. */
 typedef struct {
   int32_t width, height;
   float fx, fy, cx, cy;
   float z_near;
+  float max_dist;
 } splat_camera;
 
 /* Gaussian map, structure of arrays (Sec. 3.3: mean x, covariance from
@@ -147,11 +150,13 @@ int splat_profile_read(char *names, size_t names_bytes, int64_t *launches, doubl
 
 /*
  * splat_project -- per-Gaussian activation and EWA projection (Sec. 3.3, the
- * f_i^proj of the rendering equation; frustum part of the candidate
+ * f_i^proj of the rendering equation; the frustum and distance candidate
  * selection of Sec. 3.4 step 1).
  *   s = exp(log_scale), R = R(q/|q|) (identity if |q| = 0),
  *   Sigma = R diag(s^2) R^T, opacity = sigmoid(logit), p = W x + t;
- *   culled if p_z <= z_near;  Sigma2 = J W Sigma W^T J^T + 0.3 I;
+ *   culled if p_z <= z_near, or if max_dist > 0 and
+ *   (p_x p_x + p_y p_y) + p_z p_z > max_dist max_dist (float32, in this order);
+ *   Sigma2 = J W Sigma W^T J^T + 0.3 I;
  *   culled if det(Sigma2) <= 0; conic = Sigma2^-1; (u, v) = (fx p_x/p_z + cx,
  *   fy p_y/p_z + cy); radius r = ceil(3 sqrt(lambda_max(Sigma2)));
  *   rect = [floor((u-r)/16), floor((u+r)/16)+1) x (same in v), clamped to

@@ -204,6 +204,42 @@ class Agent:
         v.grad2d = B._p(fb.bwd_ws)
         return v
 
+    # -- pruning -----------------------------------------------------------------
+    def prune(self, tau_o: float = 0.005, tau_s: float = 0.25, tau_e: float = 10.0, stream=None) -> int:
+        """Gaussian splat pruning (Algorithm 1) of the resident map: Gaussians
+        with opacity below tau_o, or (tau_s > 0) largest scale above tau_s or
+        above tau_e times the sum of the other two, are removed from the map
+        and from both Adam moments, keeping the order of the rest.  The map
+        shrinks to the kept Gaussians (one host read of the count); gradient
+        and frame buffers are re-made at the new size and a captured graph or
+        snapshot is dropped.  Returns the number kept."""
+        s = torch.cuda.current_stream() if stream is None else stream
+        n = self.n
+        ws = torch.empty(max(16, B.splat_prune_workspace_size(n)), dtype=torch.uint8, device=self.device)
+        n_keep = torch.zeros(1, dtype=torch.int64, device=self.device)
+        B.splat_prune(self.cg, tau_o, tau_s, tau_e, [], None, n_keep, ws, s)  # count only
+        s.synchronize()
+        k = int(n_keep.item())
+        if k == n:
+            return k
+        src = [*self.params, *self.m, *self.v]
+        dst = [torch.empty((k,) + tuple(t.shape[1:]), dtype=t.dtype, device=self.device) for t in src]
+        B.splat_prune(self.cg, tau_o, tau_s, tau_e, list(zip(src, dst)), None, n_keep, ws, s)
+        s.synchronize()
+        self.params, self.m, self.v = dst[:5], dst[5:10], dst[10:]
+        self.n = k
+        self.grads = [torch.zeros_like(t) for t in self.params]
+        self.cg = B.gaussians_struct(*self.params)
+        self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads))
+        self.grads_clean = True
+        self.fb = FrameBuffers(k, self.cam, self.device, capacity=self.fb.capacity, want_keys=self.fb.want_keys,
+                               want_used="n_used" in self.fb.image)
+        names = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
+        self.adam = B.AdamGroups(self.params, self.grads, self.m, self.v, [self.cfg.lr[k2] for k2 in names])
+        self.graph = None
+        self._snap = None
+        return k
+
     # -- episodes ---------------------------------------------------------------
     def _state(self):
         return [*self.params, *self.m, *self.v, self.w2c, self.pose_m, self.pose_v, self.t_dev]

@@ -28,7 +28,7 @@ class SplatError(RuntimeError):
 
 class CCamera(ctypes.Structure):
     _fields_ = [("width", _c_i32), ("height", _c_i32), ("fx", _c_f), ("fy", _c_f), ("cx", _c_f), ("cy", _c_f),
-                ("z_near", _c_f)]
+                ("z_near", _c_f), ("max_dist", _c_f)]
 
 
 class CGaussians(ctypes.Structure):
@@ -158,7 +158,7 @@ def _check(name, rc):
 
 
 def camera_struct(cam) -> CCamera:
-    return CCamera(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, cam.z_near)
+    return CCamera(cam.width, cam.height, cam.fx, cam.fy, cam.cx, cam.cy, cam.z_near, getattr(cam, "max_dist", 0.0))
 
 
 def gaussians_struct(mean, log_scale, quat, opacity_logit, rgb) -> CGaussians:

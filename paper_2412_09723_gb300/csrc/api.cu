@@ -247,7 +247,7 @@ __global__ void exp_kernel(const float* __restrict__ x, float* __restrict__ y, i
 
 using namespace splat;
 
-extern "C" int32_t splat_abi_version(void) { return 1; }
+extern "C" int32_t splat_abi_version(void) { return 2; }
 
 extern "C" const char* splat_last_error(void) { return g_last_error; }
 

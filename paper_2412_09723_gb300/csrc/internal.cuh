@@ -9,6 +9,7 @@ namespace splat {
 struct CamK {
   int width, height, tiles_x, tiles_y;
   float fx, fy, cx, cy, znear;
+  float maxd2;  // squared distance limit, 0 = none
 };
 
 struct GaussiansK {
@@ -43,6 +44,7 @@ inline CamK make_camk(const splat_camera& c) {
   k.tiles_x = (c.width + kTile - 1) / kTile;
   k.tiles_y = (c.height + kTile - 1) / kTile;
   k.fx = c.fx; k.fy = c.fy; k.cx = c.cx; k.cy = c.cy; k.znear = c.z_near;
+  k.maxd2 = c.max_dist > 0.f ? c.max_dist * c.max_dist : 0.f;
   return k;
 }
 

@@ -75,6 +75,9 @@ __device__ __forceinline__ void project_math(const float* __restrict__ mean,
     m.p[i] = ((W[4 * i] * mean[0] + W[4 * i + 1] * mean[1]) + W[4 * i + 2] * mean[2]) + W[4 * i + 3];
   const float z = m.p[2];
   if (!(z > cam.znear)) return;
+  if (cam.maxd2 > 0.f &&
+      __fadd_rn(__fadd_rn(__fmul_rn(m.p[0], m.p[0]), __fmul_rn(m.p[1], m.p[1])), __fmul_rn(z, z)) > cam.maxd2)
+    return;  // outside the selection distance
   const float lim_x = kClip * ((float)cam.width / (2.0f * cam.fx));
   const float lim_y = kClip * ((float)cam.height / (2.0f * cam.fy));
   const float txz = m.p[0] / z;

@@ -123,3 +123,43 @@ def test_autotune_picks_a_candidate(dev, tmp_path):
     assert tuple(entry["shape"]) in cands and len(entry["tried"]) == 2
     again = batch.autotune(candidates=cands, reps=2, cache_path=str(tmp_path / "tune.json"))
     assert again["shape"] == entry["shape"]
+
+
+def test_agent_prune_matches_oracle_and_keeps_stepping(dev):
+    """Algorithm 1 on a resident map after some mapping steps: the kept map
+    and Adam moments are the oracle's compaction of the device state, the
+    pruned map renders exactly as the oracle renders the same Gaussians, and
+    the agent keeps stepping (and capturing) at the new size."""
+    import oracle
+    from oracle import consensus as C
+
+    a = _agent(dev)
+    rng = np.random.default_rng(4)
+    with torch.no_grad():  # make every criterion bite on some Gaussians
+        idx = torch.as_tensor(rng.choice(a.n, 3000, replace=False), device=dev)
+        a.params[3][idx[:1000]] = -7.0                   # transparent
+        a.params[1][idx[1000:2000], 0] = float(np.log(0.3))  # large
+        a.params[1][idx[2000:], 1] = a.params[1][idx[2000:], 0] + 4.0  # elongated
+    for _ in range(3):
+        a.step()
+    torch.cuda.synchronize()
+    state = [t.cpu().numpy() for t in (*a.params, *a.m, *a.v)]
+    mask = C.prune_mask(state[3], state[1], oracle.exp_f32)
+    ref = C.prune(state, mask)
+    k = a.prune()
+    assert k == int((~mask).sum()) and k == a.n
+    assert a.n < 60000 - 2500
+    for got, want in zip((*a.params, *a.m, *a.v), ref):
+        assert np.array_equal(got.cpu().numpy(), want)
+    a.forward()
+    torch.cuda.synchronize()
+    scene = scenes.Scene(*(t.cpu().numpy() for t in a.params))
+    refimg = oracle.render_fwd(scene, a.w2c.cpu().numpy(), a.cam, np.zeros(3, np.float32))
+    for key in ("n_contrib", "max_id"):
+        assert np.array_equal(a.fb.image[key].cpu().numpy(), refimg[key]), key
+    a.size_capacity(1.5)
+    a.capture()
+    for _ in range(3):
+        a.replay()
+    torch.cuda.synchronize()
+    assert a.status() == 0 and np.isfinite(float(a.loss.item()))

@@ -430,3 +430,32 @@ def test_assoc_deep_buckets_and_duplicates(dev):
     assert m == len(ref_pairs)
     assert np.array_equal(pairs[:m].cpu().numpy(), ref_pairs)
     assert np.array_equal(counts[:m].cpu().numpy(), ref_counts)
+
+
+def test_distance_selection_parity(dev):
+    """Candidate selection by distance (Sec. 3.4 step 1) inside the projection:
+    projection, bins and image bit-exact, gradients within tolerance."""
+    import dataclasses
+
+    sc = scenes.scene_room(20000, 23)
+    w2c = scenes.perturbed_w2c(24, 0.2, 15.0)
+    W = w2c.astype(np.float64)
+    r = np.sort(np.linalg.norm(sc.mean.astype(np.float64) @ W[:3, :3].T + W[:3, 3], axis=1))
+    lo, hi = int(0.3 * len(r)), int(0.7 * len(r))
+    j = lo + int(np.argmax(np.diff(r[lo:hi])))
+    cam = dataclasses.replace(scenes.Camera(200, 150, 120.0, 120.0, 100.0, 75.0), max_dist=float(0.5 * (r[j] + r[j + 1])))
+    bg = np.float32([0.1, 0.2, 0.3])
+    p, fb = _render_gpu(sc, w2c, cam, bg, dev)
+    ref = oracle.project(sc, w2c, cam)
+    got = {k: v.cpu().numpy() for k, v in fb.proj.items()}
+    for k in ("radius", "rect", "tiles_touched"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert 0 < (ref["radius"] == 0).mean() < 1
+    _check_bins(fb, sc, w2c, cam)
+    _check_image(fb, oracle.render_fwd(sc, w2c, cam, bg))
+    g = _upstream(cam, 12)
+    grads, d_pose, d2d = _bwd_gpu(p, fb, w2c, cam, bg, g, dev)
+    refg = oracle.render_bwd(sc, w2c, cam, bg, *g)
+    for name, gg in zip(("mean", "log_scale", "quat", "opacity_logit", "rgb"), grads):
+        _assert_grad_close(gg, refg[name], name)
+    _assert_grad_close(d_pose, refg["pose"], "pose")
