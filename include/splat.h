@@ -240,6 +240,8 @@ int splat_render_fwd(const splat_projected *proj, const float *rgb, int64_t n,
  * per-pixel upstream gradients (map optimisation by differentiable rendering,
  * Sec. 3.4 step 4; gradients through renders for alignment and joint
  * optimisation, Sec. 3.5 steps 3-4).
+ *   proj: the splat_project output for this map, camera and pose (its radius
+ *     is read: Gaussians it culled get no gradient and are skipped).
  *   d_rgb [H,W,3], d_depth [H,W], d_sil [H,W] (d_depth, d_sil may be NULL).
  *   fwd: the image of the forward call (t_final, n_contrib are read).
  *   out: Gaussian-parameter gradients, ACCUMULATED (+=); the caller zeroes.
@@ -266,8 +268,10 @@ int splat_render_bwd(const splat_gaussians *g, const splat_projected *proj,
  * [n,12], 16-byte aligned rows: du, dv, d conic a, b, c, d opacity,
  * d rgb[3], d depth, 2 unused) to the Gaussian parameters (accumulated into
  * `out`) and, if d_pose is not NULL, to the pose 6-vector (accumulated).
- * d2d (optional) receives the [n,10] screen-space gradients.  Used after
- * splat_render_bwd_batch.  Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ * d2d (optional) receives the [n,10] screen-space gradients.  proj must be
+ * the splat_project output for the same map, camera and pose (Gaussians with
+ * radius 0 are skipped).  Used after splat_render_bwd_batch.
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
  */
 int splat_project_bwd(const splat_gaussians *g, const splat_projected *proj, const splat_camera *cam,
                       const float *w2c, const float *grad2d, const splat_gaussians_grad *out,

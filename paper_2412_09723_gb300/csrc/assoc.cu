@@ -5,13 +5,17 @@
 // (id_a, id_b) is formed; the output is the sorted set of distinct pairs with
 // the number of pixels of each.
 //
-// Design: the 64-bit pair keys (id_a << 32 | id_b) are bucketed by ranges of
-// id_a (monotone buckets, so bucket order is key order), with per-CTA counts in
-// shared memory and one global atomic per (CTA, bucket) to reserve space; each
-// bucket's distinct keys are then counted by one CTA in a shared-memory hash
-// table and only the distinct keys are sorted (a bucket with too many distinct
-// keys is sorted whole and run-length encoded); the distinct pairs are written
-// at the offsets of an exclusive scan over the buckets.  Six kernels.
+// Design: a maximum-weight Gaussian covers runs of neighbouring pixels, so
+// every thread reads kAsRun consecutive pixels and merges runs of the same
+// pair into one weighted entry (key = id_a << 32 | id_b, weight = pixels).
+// Entries are bucketed by ranges of id_a (monotone buckets, so bucket order
+// is key order), with per-CTA counts in shared memory and one global atomic
+// per (CTA, bucket) to reserve space; each bucket's distinct keys are then
+// summed by one CTA in a shared-memory hash table (weights added) and only
+// the distinct keys are sorted; a bucket with more distinct keys than the
+// table holds uses a hash table in global memory instead.  The distinct pairs
+// are written at the offsets of an exclusive scan over the buckets.  Six
+// kernels.
 #include <algorithm>
 
 #include "common.cuh"
@@ -20,15 +24,11 @@
 namespace splat {
 
 constexpr int kAsThreads = 256;
+constexpr int kAsRun = 8;             // consecutive pixels a thread merges into runs
 constexpr int kAsBucketKeys = 1024;   // expected keys per bucket
 constexpr int kAsMaxBuckets = 4096;   // shared-memory counters per CTA
 constexpr int kAsSegCap = 4096;       // keys a CTA sorts in shared memory
 constexpr int kAsStride = 32;         // one 128-byte line per global counter
-
-__device__ __forceinline__ bool assoc_valid(const int32_t* ia, const float* ta, const int32_t* ib, const float* tb,
-                                            int64_t p, float tmax) {
-  return ia[p] >= 0 && ib[p] >= 0 && ta[p] <= tmax && tb[p] <= tmax;
-}
 
 __device__ __forceinline__ int assoc_bucket(int32_t a, int64_t n_a, int nb) {
   const int64_t b = ((int64_t)a * nb) / n_a;
@@ -36,26 +36,80 @@ __device__ __forceinline__ int assoc_bucket(int32_t a, int64_t n_a, int nb) {
 }
 
 // Pixel range of CTA `blk` out of `grid` (contiguous, so neighbouring pixels,
-// which tend to share ids, land in the same CTA).
+// which tend to share ids, land in the same CTA; a multiple of kAsRun long, so
+// that every thread's chunk starts on a 32-byte boundary).
 __device__ __forceinline__ void cta_range(int64_t npix, int64_t& p0, int64_t& p1) {
-  const int64_t per = (npix + gridDim.x - 1) / gridDim.x;
+  int64_t per = (npix + gridDim.x - 1) / gridDim.x;
+  per = (per + kAsRun - 1) / kAsRun * kAsRun;
   p0 = (int64_t)blockIdx.x * per;
   p1 = p0 + per < npix ? p0 + per : npix;
+}
+
+// Walks the kAsRun-pixel chunks of this CTA's range; calls emit(key, weight)
+// once per run of equal valid pairs (in pixel order).
+// vec: all four images 16-byte aligned, so a full chunk is read with 128-bit loads.
+template <class Emit>
+__device__ __forceinline__ void for_each_run(const int32_t* __restrict__ ia, const float* __restrict__ ta,
+                                             const int32_t* __restrict__ ib, const float* __restrict__ tb,
+                                             int64_t p0, int64_t p1, float tmax, bool vec, Emit emit) {
+  for (int64_t c = p0 + (int64_t)threadIdx.x * kAsRun; c < p1; c += (int64_t)kAsThreads * kAsRun) {
+    int32_t a[kAsRun], b[kAsRun];
+    float u[kAsRun], v[kAsRun];
+    const int len = c + kAsRun <= p1 ? kAsRun : (int)(p1 - c);
+    if (vec && len == kAsRun) {
+#pragma unroll
+      for (int h = 0; h < kAsRun; h += 4) {
+        const int4 x = *reinterpret_cast<const int4*>(ia + c + h);
+        const int4 y = *reinterpret_cast<const int4*>(ib + c + h);
+        const float4 tx = *reinterpret_cast<const float4*>(ta + c + h);
+        const float4 ty = *reinterpret_cast<const float4*>(tb + c + h);
+        a[h] = x.x; a[h + 1] = x.y; a[h + 2] = x.z; a[h + 3] = x.w;
+        b[h] = y.x; b[h + 1] = y.y; b[h + 2] = y.z; b[h + 3] = y.w;
+        u[h] = tx.x; u[h + 1] = tx.y; u[h + 2] = tx.z; u[h + 3] = tx.w;
+        v[h] = ty.x; v[h + 1] = ty.y; v[h + 2] = ty.z; v[h + 3] = ty.w;
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < kAsRun; ++h) {
+        const bool in = h < len;
+        a[h] = in ? ia[c + h] : -1;
+        b[h] = in ? ib[c + h] : -1;
+        u[h] = in ? ta[c + h] : 0.f;
+        v[h] = in ? tb[c + h] : 0.f;
+      }
+    }
+    uint64_t cur = 0;
+    uint32_t w = 0;
+#pragma unroll
+    for (int h = 0; h < kAsRun; ++h) {
+      if (!(a[h] >= 0 && b[h] >= 0 && u[h] <= tmax && v[h] <= tmax)) continue;
+      const uint64_t key = ((uint64_t)(uint32_t)a[h] << 32) | (uint64_t)(uint32_t)b[h];
+      if (w && key == cur) {
+        ++w;
+      } else {
+        if (w) emit(cur, w);
+        cur = key;
+        w = 1;
+      }
+    }
+    if (w) emit(cur, w);
+  }
 }
 
 __global__ void __launch_bounds__(kAsThreads) assoc_count_kernel(const int32_t* __restrict__ ia,
                                                                  const float* __restrict__ ta,
                                                                  const int32_t* __restrict__ ib,
                                                                  const float* __restrict__ tb, int64_t npix,
-                                                                 float tmax, int64_t n_a, int nb,
+                                                                 float tmax, int64_t n_a, int nb, bool vec,
                                                                  uint32_t* __restrict__ bcnt) {
   __shared__ uint32_t s_cnt[kAsMaxBuckets];
   for (int b = threadIdx.x; b < nb; b += kAsThreads) s_cnt[b] = 0u;
   __syncthreads();
   int64_t p0, p1;
   cta_range(npix, p0, p1);
-  for (int64_t p = p0 + threadIdx.x; p < p1; p += kAsThreads)
-    if (assoc_valid(ia, ta, ib, tb, p, tmax)) atomicAdd(&s_cnt[assoc_bucket(ia[p], n_a, nb)], 1u);
+  for_each_run(ia, ta, ib, tb, p0, p1, tmax, vec, [&](uint64_t key, uint32_t) {
+    atomicAdd(&s_cnt[assoc_bucket((int32_t)(key >> 32), n_a, nb)], 1u);
+  });
   __syncthreads();
   for (int b = threadIdx.x; b < nb; b += kAsThreads)
     if (s_cnt[b]) atomicAdd(&bcnt[(size_t)b * kAsStride], s_cnt[b]);
@@ -83,16 +137,17 @@ __global__ void __launch_bounds__(1024) assoc_scan_kernel(const uint32_t* __rest
 
 __global__ void __launch_bounds__(kAsThreads) assoc_scatter_kernel(
     const int32_t* __restrict__ ia, const float* __restrict__ ta, const int32_t* __restrict__ ib,
-    const float* __restrict__ tb, int64_t npix, float tmax, int64_t n_a, int nb, uint32_t* __restrict__ cursor,
-    uint64_t* __restrict__ skeys) {
+    const float* __restrict__ tb, int64_t npix, float tmax, int64_t n_a, int nb, bool vec,
+    uint32_t* __restrict__ cursor, uint64_t* __restrict__ skeys, uint32_t* __restrict__ sw) {
   __shared__ uint32_t s_cnt[kAsMaxBuckets];
   __shared__ uint32_t s_base[kAsMaxBuckets];
   for (int b = threadIdx.x; b < nb; b += kAsThreads) s_cnt[b] = 0u;
   __syncthreads();
   int64_t p0, p1;
   cta_range(npix, p0, p1);
-  for (int64_t p = p0 + threadIdx.x; p < p1; p += kAsThreads)
-    if (assoc_valid(ia, ta, ib, tb, p, tmax)) atomicAdd(&s_cnt[assoc_bucket(ia[p], n_a, nb)], 1u);
+  for_each_run(ia, ta, ib, tb, p0, p1, tmax, vec, [&](uint64_t key, uint32_t) {
+    atomicAdd(&s_cnt[assoc_bucket((int32_t)(key >> 32), n_a, nb)], 1u);
+  });
   __syncthreads();
   for (int b = threadIdx.x; b < nb; b += kAsThreads) {
     const uint32_t c = s_cnt[b];
@@ -100,31 +155,40 @@ __global__ void __launch_bounds__(kAsThreads) assoc_scatter_kernel(
     s_cnt[b] = 0u;
   }
   __syncthreads();
-  for (int64_t p = p0 + threadIdx.x; p < p1; p += kAsThreads)
-    if (assoc_valid(ia, ta, ib, tb, p, tmax)) {
-      const int b = assoc_bucket(ia[p], n_a, nb);
-      const uint32_t pos = s_base[b] + atomicAdd(&s_cnt[b], 1u);
-      skeys[pos] = ((uint64_t)(uint32_t)ia[p] << 32) | (uint64_t)(uint32_t)ib[p];
-    }
+  for_each_run(ia, ta, ib, tb, p0, p1, tmax, vec, [&](uint64_t key, uint32_t w) {
+    const int b = assoc_bucket((int32_t)(key >> 32), n_a, nb);
+    const uint32_t pos = s_base[b] + atomicAdd(&s_cnt[b], 1u);
+    skeys[pos] = key;
+    sw[pos] = w;
+  });
 }
 
-constexpr int kAsHash = 2048;          // shared-memory hash slots per bucket
-constexpr int kAsHashMaxDistinct = 1536;  // at most 75% load, else the sort path
+constexpr int kAsHash = 2048;             // shared-memory hash slots per bucket
+constexpr int kAsHashMaxDistinct = 1536;  // at most 75% load, else the global-memory table
 constexpr uint64_t kAsEmpty = ~0ull;
 
-// One CTA per bucket.  Distinct keys and their multiplicities are collected in
-// a shared-memory hash table (linear probing, bounded by the table size); the
-// distinct keys are then bitonic-sorted and written with their counts at the
-// bucket's own start of ukeys / ucnt; nuniq[b] = number of distinct keys.  If
-// a bucket holds more distinct keys than the table takes, the CTA sorts the
-// whole bucket and run-length encodes it instead.
+__device__ __forceinline__ uint32_t assoc_hash(uint64_t key) {
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 32);
+}
+
+// One CTA per bucket.  The weights of equal keys are summed in a hash table
+// (linear probing, bounded by the table size): in shared memory when the
+// bucket has at most kAsHashMaxDistinct distinct keys, else in the bucket's
+// own global region of 2n slots (gkey/gcnt at 2 * start).  The distinct keys
+// are then sorted (bitonic in shared memory, or the segment sort through
+// global memory) and written with their summed weights at the bucket's start
+// of ukeys / ucnt; nuniq[b] = number of distinct keys.
 __global__ void __launch_bounds__(kAsThreads) assoc_sort_rle_kernel(const uint32_t* __restrict__ bstart,
-                                                                    uint64_t* __restrict__ skeys,
+                                                                    const uint64_t* __restrict__ skeys,
+                                                                    const uint32_t* __restrict__ sw,
                                                                     uint64_t* __restrict__ skeys2,
+                                                                    uint64_t* __restrict__ skeys3,
+                                                                    uint64_t* __restrict__ gkey,
+                                                                    uint32_t* __restrict__ gcnt,
                                                                     uint64_t* __restrict__ ukeys,
                                                                     uint32_t* __restrict__ ucnt,
                                                                     uint32_t* __restrict__ nuniq) {
-  __shared__ uint64_t smem[kAsSegCap];  // hash keys (first kAsHash), later the sort buffer
+  __shared__ uint64_t smem[kAsSegCap];  // hash keys (first kAsHash), then the distinct keys
   __shared__ uint32_t s_hcnt[kAsHash];
   __shared__ uint32_t sh[33];
   __shared__ int s_overflow;
@@ -136,7 +200,7 @@ __global__ void __launch_bounds__(kAsThreads) assoc_sort_rle_kernel(const uint32
     if (threadIdx.x == 0) nuniq[b] = 0u;
     return;
   }
-  // 1. hash count
+  // 1. shared-memory table
   uint64_t* hkey = smem;
   for (int i = threadIdx.x; i < kAsHash; i += kAsThreads) {
     hkey[i] = kAsEmpty;
@@ -147,9 +211,9 @@ __global__ void __launch_bounds__(kAsThreads) assoc_sort_rle_kernel(const uint32
     s_ndist = 0u;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += kAsThreads) {
+  for (int i = threadIdx.x; i < n && !s_overflow; i += kAsThreads) {
     const uint64_t key = skeys[s0 + i];
-    uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 53);  // 11 bits
+    uint32_t h = assoc_hash(key) & (kAsHash - 1);
     int probes = 0;
     for (; probes < kAsHash; ++probes, h = (h + 1) & (kAsHash - 1)) {
       const uint64_t prev = atomicCAS(reinterpret_cast<unsigned long long*>(&hkey[h]), kAsEmpty, key);
@@ -160,18 +224,17 @@ __global__ void __launch_bounds__(kAsThreads) assoc_sort_rle_kernel(const uint32
       if (prev == key) break;
     }
     if (probes == kAsHash) s_overflow = 1;
-    else atomicAdd(&s_hcnt[h], 1u);
+    else atomicAdd(&s_hcnt[h], sw[s0 + i]);
   }
   __syncthreads();
   if (!s_overflow) {
-    // 2. compact the occupied slots (slot order), then sort the distinct keys
-    //    together with their counts (count in a parallel array, moved by rank)
+    // compact the occupied slots, sort the distinct keys, look their sums up
     uint32_t mine = 0;
     const int per = kAsHash / kAsThreads;
     for (int i = threadIdx.x * per; i < (threadIdx.x + 1) * per; ++i) mine += hkey[i] != kAsEmpty ? 1u : 0u;
     uint32_t off;
     const uint32_t nd = block_excl_scan<kAsThreads>(mine, off, sh);
-    uint64_t* dk = smem + kAsHash;  // distinct keys (nd <= 1536 <= kAsSegCap - kAsHash)
+    uint64_t* dk = smem + kAsHash;  // nd <= 1536 <= kAsSegCap - kAsHash
     for (int i = threadIdx.x * per; i < (threadIdx.x + 1) * per; ++i)
       if (hkey[i] != kAsEmpty) dk[off++] = hkey[i];
     __syncthreads();
@@ -181,7 +244,7 @@ __global__ void __launch_bounds__(kAsThreads) assoc_sort_rle_kernel(const uint32
     cta_bitonic_u64(dk, n2);
     for (int u = threadIdx.x; u < (int)nd; u += kAsThreads) {
       const uint64_t key = dk[u];
-      uint32_t h = (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 53);
+      uint32_t h = assoc_hash(key) & (kAsHash - 1);
       for (int probes = 0; probes < kAsHash && hkey[h] != key; ++probes) h = (h + 1) & (kAsHash - 1);
       ukeys[s0 + u] = key;
       ucnt[s0 + u] = s_hcnt[h];
@@ -189,32 +252,48 @@ __global__ void __launch_bounds__(kAsThreads) assoc_sort_rle_kernel(const uint32
     if (threadIdx.x == 0) nuniq[b] = nd;
     return;
   }
+  // 2. global-memory table of 2n slots (never more than half full)
+  const uint32_t T = 2u * (uint32_t)n;
+  uint64_t* tk = gkey + 2 * (size_t)s0;
+  uint32_t* tc = gcnt + 2 * (size_t)s0;
+  for (uint32_t i = threadIdx.x; i < T; i += kAsThreads) {
+    tk[i] = kAsEmpty;
+    tc[i] = 0u;
+  }
   __syncthreads();
-  // 3. too many distinct keys: sort the bucket and run-length encode it
-  const uint64_t* k;
-  if (n <= kAsSegCap) {
-    cta_sort_small(skeys + s0, n, smem);
-    k = smem;
-  } else {
-    cta_sort_segment(skeys + s0, skeys2 + s0, skeys + s0, n, smem, kAsSegCap);
-    k = skeys2 + s0;
+  for (int i = threadIdx.x; i < n; i += kAsThreads) {
+    const uint64_t key = skeys[s0 + i];
+    uint32_t h = assoc_hash(key) % T;
+    for (uint32_t probes = 0; probes < T; ++probes, h = h + 1 == T ? 0u : h + 1) {
+      const uint64_t prev = atomicCAS(reinterpret_cast<unsigned long long*>(&tk[h]), kAsEmpty, key);
+      if (prev == kAsEmpty || prev == key) {
+        atomicAdd(&tc[h], sw[s0 + i]);
+        break;
+      }
+    }
   }
-  const int per = (n + kAsThreads - 1) / kAsThreads;
-  const int i0 = threadIdx.x * per;
-  const int i1 = min(n, i0 + per);
-  uint32_t heads = 0;
-  for (int i = i0; i < i1; ++i) heads += (i == 0 || k[i] != k[i - 1]) ? 1u : 0u;
-  uint32_t u;
-  const uint32_t total = block_excl_scan<kAsThreads>(heads, u, sh);
-  for (int i = i0; i < i1; ++i) {
-    if (!(i == 0 || k[i] != k[i - 1])) continue;
-    int j = i + 1;
-    while (j < n && k[j] == k[i]) ++j;
-    ukeys[s0 + u] = k[i];
-    ucnt[s0 + u] = (uint32_t)(j - i);
-    ++u;
+  __syncthreads();
+  // distinct keys -> skeys2[s0, s0 + nd) in slot order, then sorted into ukeys
+  uint32_t carry = 0;
+  for (uint32_t base = 0; base < T; base += kAsThreads) {
+    const uint32_t i = base + threadIdx.x;
+    const bool occ = i < T && tk[i] != kAsEmpty;
+    uint32_t off;
+    const uint32_t tot = block_excl_scan<kAsThreads>(occ ? 1u : 0u, off, sh);
+    if (occ) skeys2[s0 + carry + off] = tk[i];
+    carry += tot;
   }
-  if (threadIdx.x == 0) nuniq[b] = total;
+  __syncthreads();
+  const int nd = (int)carry;
+  cta_sort_segment(skeys2 + s0, ukeys + s0, skeys3 + s0, nd, smem, kAsSegCap);
+  __syncthreads();
+  for (int u = threadIdx.x; u < nd; u += kAsThreads) {
+    const uint64_t key = ukeys[s0 + u];
+    uint32_t h = assoc_hash(key) % T;
+    for (uint32_t probes = 0; probes < T && tk[h] != key; ++probes) h = h + 1 == T ? 0u : h + 1;
+    ucnt[s0 + u] = tc[h];
+  }
+  if (threadIdx.x == 0) nuniq[b] = (uint32_t)nd;
 }
 
 __global__ void __launch_bounds__(1024) assoc_offsets_kernel(const uint32_t* __restrict__ nuniq, int nb,
@@ -257,8 +336,8 @@ __global__ void __launch_bounds__(kAsThreads) assoc_write_kernel(const uint32_t*
 }
 
 struct AssocWs {
-  uint32_t *bcnt, *cursor, *bstart, *nuniq, *uoff, *ucnt;
-  uint64_t *skeys, *skeys2, *ukeys;
+  uint32_t *bcnt, *cursor, *bstart, *nuniq, *uoff, *ucnt, *sw, *gcnt;
+  uint64_t *skeys, *skeys2, *skeys3, *ukeys, *gkey;
 };
 
 static int assoc_buckets(int64_t npix) {
@@ -282,9 +361,13 @@ static size_t carve_assoc(int64_t npix, char* base, AssocWs* w) {
   t.nuniq = (uint32_t*)take(4 * nb);
   t.uoff = (uint32_t*)take(4 * nb);
   t.ucnt = (uint32_t*)take(4 * n);
+  t.sw = (uint32_t*)take(4 * n);
+  t.gcnt = (uint32_t*)take(4 * 2 * n);
   t.skeys = (uint64_t*)take(8 * n);
   t.skeys2 = (uint64_t*)take(8 * n);
+  t.skeys3 = (uint64_t*)take(8 * n);
   t.ukeys = (uint64_t*)take(8 * n);
+  t.gkey = (uint64_t*)take(8 * 2 * n);
   if (w) *w = t;
   return off;
 }
@@ -317,15 +400,17 @@ extern "C" int splat_assoc(const int32_t* id_a, const float* t_a, const int32_t*
   int sms = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((npix + 1023) / 1024, 2 * sms));
+  const bool vec = aligned16(id_a) && aligned16(t_a) && aligned16(id_b) && aligned16(t_b);
   SPLAT_LAUNCH("assoc_count_kernel", s,
-               assoc_count_kernel<<<grid, kAsThreads, 0, s>>>(id_a, t_a, id_b, t_b, npix, t_max, n_a, nb, w.bcnt));
+               assoc_count_kernel<<<grid, kAsThreads, 0, s>>>(id_a, t_a, id_b, t_b, npix, t_max, n_a, nb, vec,
+                                                              w.bcnt));
   SPLAT_LAUNCH("assoc_scan_kernel", s, assoc_scan_kernel<<<1, 1024, 0, s>>>(w.bcnt, nb, w.bstart, w.cursor));
   SPLAT_LAUNCH("assoc_scatter_kernel", s,
-               assoc_scatter_kernel<<<grid, kAsThreads, 0, s>>>(id_a, t_a, id_b, t_b, npix, t_max, n_a, nb, w.cursor,
-                                                                w.skeys));
+               assoc_scatter_kernel<<<grid, kAsThreads, 0, s>>>(id_a, t_a, id_b, t_b, npix, t_max, n_a, nb, vec,
+                                                                w.cursor, w.skeys, w.sw));
   SPLAT_LAUNCH("assoc_sort_rle_kernel", s,
-               assoc_sort_rle_kernel<<<nb, kAsThreads, 0, s>>>(w.bstart, w.skeys, w.skeys2, w.ukeys, w.ucnt,
-                                                                w.nuniq));
+               assoc_sort_rle_kernel<<<nb, kAsThreads, 0, s>>>(w.bstart, w.skeys, w.sw, w.skeys2, w.skeys3, w.gkey,
+                                                                w.gcnt, w.ukeys, w.ucnt, w.nuniq));
   SPLAT_LAUNCH("assoc_offsets_kernel", s,
                assoc_offsets_kernel<<<1, 1024, 0, s>>>(w.nuniq, nb, w.uoff, capacity, m_dev, status));
   int rc = check_launch("assoc_offsets_kernel");

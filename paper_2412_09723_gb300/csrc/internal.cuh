@@ -52,9 +52,10 @@ int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, c
                        cudaStream_t s);
 // g2: screen-space gradients, rows of `stride` floats (du, dv, d conic a, b, c,
 // d opacity, d rgb[3], d depth, padding); d2d_out (optional): copy [n,10].
+// radius: the forward projection's radii (0 = culled: no gradient, skipped).
 int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
-                       const float* g2, int stride, const GradK& out, float* d_pose, float* d2d_out,
-                       cudaStream_t s);
+                       const int32_t* radius, const float* g2, int stride, const GradK& out, float* d_pose,
+                       float* d2d_out, cudaStream_t s);
 
 // L1 terms: grgb = sc sign(rgb - trgb), gdepth = sd sign(depth - tdepth) (overwritten),
 // loss += sc sum|rgb - trgb| + sd sum|depth - tdepth|.

@@ -14,6 +14,8 @@
 // (du, dv, d conic, d opacity, d depth) back to mean, log-scale, quaternion and
 // opacity logit, and the pose 6-vector is reduced per block before one atomic
 // per component.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.cuh"
 
@@ -162,138 +164,172 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(GaussiansK g, CamK cam
 // ----------------------------------------------------------------------------
 // Adjoint.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) project_bwd_kernel(GaussiansK g, CamK cam, const float* __restrict__ w2c,
-                                                          const float* __restrict__ conic,
-                                                          const float* __restrict__ g2, int stride, GradK out,
-                                                          float* __restrict__ d_pose, float* __restrict__ d2d_out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (i < g.n && d2d_out) {
+// Adjoint of one Gaussian's projection (its screen-space gradients in g2),
+// accumulated into `out` and, for the pose, into `pose`.
+__device__ __forceinline__ void project_adjoint_one(const GaussiansK& g, const CamK& cam, const float* W,
+                                                    const float* __restrict__ conic, const float* __restrict__ g2,
+                                                    int stride, const GradK& out, int64_t i, float (&pose)[6]) {
+  ProjMath m;
+  project_math(g.mean + 3 * i, g.log_scale + 3 * i, g.quat + 4 * i, g.opacity_logit[i], W, cam, m);
+  if (m.visible) {
+    const float* d = g2 + (size_t)stride * i;
+    const float du = d[0], dv = d[1], dqa = d[2], dqb = d[3], dqc = d[4], dlam = d[5], dz = d[9];
+    out.rgb[3 * i + 0] += d[6];
+    out.rgb[3 * i + 1] += d[7];
+    out.rgb[3 * i + 2] += d[8];
+    out.opacity_logit[i] += dlam * m.lam * (1.0f - m.lam);
+    // conic Q = cov^-1 with cov = [[ca, cb], [cb, cc]]; the off-diagonal conic
+    // entry is one scalar used twice, so the full-matrix gradient of Q is
+    // [[dqa, dqb/2], [dqb/2, dqc]] and d cov = -Q dQ Q.
+    const float4 Q = reinterpret_cast<const float4*>(conic)[i];
+    const float qa = Q.x, qb = Q.y, qc = Q.z;
+    const float h = 0.5f * dqb;
+    const float t00 = qa * dqa + qb * h, t01 = qa * h + qb * dqc;
+    const float t10 = qb * dqa + qc * h, t11 = qb * h + qc * dqc;
+    const float g00 = -(t00 * qa + t01 * qb);
+    const float g01 = -(t00 * qb + t01 * qc);
+    const float g11 = -(t10 * qb + t11 * qc);
+    // cov = Tm Sig Tm^T: dTm = 2 G Tm Sig, dSig = Tm^T G Tm  (G symmetric 2x2)
+    float TS[6];
 #pragma unroll
-    for (int k = 0; k < 10; ++k) d2d_out[10 * i + k] = g2[(size_t)stride * i + k];
+    for (int a2 = 0; a2 < 2; ++a2)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        TS[3 * a2 + j] = m.Tm[3 * a2] * m.Sig[j] + m.Tm[3 * a2 + 1] * m.Sig[3 + j] + m.Tm[3 * a2 + 2] * m.Sig[6 + j];
+    float dTm[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      dTm[j] = 2.0f * (g00 * TS[j] + g01 * TS[3 + j]);
+      dTm[3 + j] = 2.0f * (g01 * TS[j] + g11 * TS[3 + j]);
+    }
+    float dSig[9];
+#pragma unroll
+    for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+      for (int b3 = 0; b3 < 3; ++b3) {
+        const float x0 = m.Tm[a3], x1 = m.Tm[3 + a3];
+        const float y0 = m.Tm[b3], y1 = m.Tm[3 + b3];
+        dSig[3 * a3 + b3] = x0 * (g00 * y0 + g01 * y1) + x1 * (g01 * y0 + g11 * y1);
+      }
+    // Tm rows: (J00 W0 + J02 W2), (J11 W1 + J12 W2)
+    const float dJ00 = dTm[0] * W[0] + dTm[1] * W[1] + dTm[2] * W[2];
+    const float dJ02 = dTm[0] * W[8] + dTm[1] * W[9] + dTm[2] * W[10];
+    const float dJ11 = dTm[3] * W[4] + dTm[4] * W[5] + dTm[5] * W[6];
+    const float dJ12 = dTm[3] * W[8] + dTm[4] * W[9] + dTm[5] * W[10];
+    // gradient of the rotation block through Tm: dW_ij = sum_a J_ai dTm_aj
+    float dWr[9];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      dWr[j] = m.J00 * dTm[j];
+      dWr[3 + j] = m.J11 * dTm[3 + j];
+      dWr[6 + j] = m.J02 * dTm[j] + m.J12 * dTm[3 + j];
+    }
+    const float z = m.p[2];
+    const float iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
+    float gz = -cam.fx * iz2 * dJ00 - cam.fy * iz2 * dJ11 + 2.0f * cam.fx * m.tx * iz3 * dJ02 +
+               2.0f * cam.fy * m.ty * iz3 * dJ12;
+    const float gtx = -cam.fx * iz2 * dJ02;
+    const float gty = -cam.fy * iz2 * dJ12;
+    float gp0 = 0.f, gp1 = 0.f;
+    if (m.clamp_x) gz += gtx * (m.tx * iz); else gp0 += gtx;
+    if (m.clamp_y) gz += gty * (m.ty * iz); else gp1 += gty;
+    gp0 += du * cam.fx * iz;
+    gp1 += dv * cam.fy * iz;
+    gz -= (du * cam.fx * m.p[0] + dv * cam.fy * m.p[1]) * iz2;
+    gz += dz;
+    const float gp[3] = {gp0, gp1, gz};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) out.mean[3 * i + j] += W[j] * gp[0] + W[4 + j] * gp[1] + W[8 + j] * gp[2];
+    // Sig = M M^T, M = R diag(s)
+    float dM[9];
+#pragma unroll
+    for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        dM[3 * a3 + j] = 2.0f * (dSig[3 * a3] * m.M[j] + dSig[3 * a3 + 1] * m.M[3 + j] + dSig[3 * a3 + 2] * m.M[6 + j]);
+    float dR[9];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float gs = dM[j] * m.R[j] + dM[3 + j] * m.R[3 + j] + dM[6 + j] * m.R[6 + j];
+      out.log_scale[3 * i + j] += gs * m.s[j];
+      dR[j] = dM[j] * m.s[j];
+      dR[3 + j] = dM[3 + j] * m.s[j];
+      dR[6 + j] = dM[6 + j] * m.s[j];
+    }
+    if (m.qnorm > 0.0f) {
+      const float r = m.qn[0], a = m.qn[1], b = m.qn[2], c = m.qn[3];
+      float gq[4];
+      gq[0] = 2.0f * (c * (dR[3] - dR[1]) + b * (dR[2] - dR[6]) + a * (dR[7] - dR[5]));
+      gq[1] = 2.0f * (b * (dR[1] + dR[3]) + c * (dR[2] + dR[6]) + r * (dR[7] - dR[5])) - 4.0f * a * (dR[4] + dR[8]);
+      gq[2] = 2.0f * (a * (dR[1] + dR[3]) + r * (dR[2] - dR[6]) + c * (dR[5] + dR[7])) - 4.0f * b * (dR[0] + dR[8]);
+      gq[3] = 2.0f * (r * (dR[3] - dR[1]) + a * (dR[2] + dR[6]) + b * (dR[5] + dR[7])) - 4.0f * c * (dR[0] + dR[4]);
+      const float dot = r * gq[0] + a * gq[1] + b * gq[2] + c * gq[3];
+      const float inv = 1.0f / m.qnorm;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) out.quat[4 * i + k] += (gq[k] - m.qn[k] * dot) * inv;
+    }
+    // pose: rho = dL/dp ; phi = p x dL/dp + vee(dW W^T)
+    float A[9];
+#pragma unroll
+    for (int a3 = 0; a3 < 3; ++a3)
+#pragma unroll
+      for (int b3 = 0; b3 < 3; ++b3)
+        A[3 * a3 + b3] = dWr[3 * a3] * W[4 * b3] + dWr[3 * a3 + 1] * W[4 * b3 + 1] + dWr[3 * a3 + 2] * W[4 * b3 + 2];
+    pose[0] += gp[0];
+    pose[1] += gp[1];
+    pose[2] += gp[2];
+    pose[3] += m.p[1] * gp[2] - m.p[2] * gp[1] + (A[7] - A[5]);
+    pose[4] += m.p[2] * gp[0] - m.p[0] * gp[2] + (A[2] - A[6]);
+    pose[5] += m.p[0] * gp[1] - m.p[1] * gp[0] + (A[3] - A[1]);
   }
-  if (i < g.n) {
-    float W[12];
+}
+
+// Gaussians the forward projection culled (radius 0) have no gradient.  Each
+// warp scans its share of the map 32 at a time and queues the visible ones in
+// shared memory; the adjoint runs whenever 32 are queued (and once more for
+// the rest), so that no warp runs it for one or two visible lanes only.
+constexpr int kPbThreads = 256;
+constexpr int kPbWarps = kPbThreads / 32;
+
+__global__ void __launch_bounds__(kPbThreads) project_bwd_kernel(GaussiansK g, CamK cam, const float* __restrict__ w2c,
+                                                                 const float* __restrict__ conic,
+                                                                 const int32_t* __restrict__ radius,
+                                                                 const float* __restrict__ g2, int stride, GradK out,
+                                                                 float* __restrict__ d_pose,
+                                                                 float* __restrict__ d2d_out) {
+  __shared__ int32_t queue[kPbWarps][64];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lower = (1u << lane) - 1u;
+  float W[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) W[k] = __ldg(w2c + k);
-    ProjMath m;
-    project_math(g.mean + 3 * i, g.log_scale + 3 * i, g.quat + 4 * i, g.opacity_logit[i], W, cam, m);
-    if (m.visible) {
-      const float* d = g2 + (size_t)stride * i;
-      const float du = d[0], dv = d[1], dqa = d[2], dqb = d[3], dqc = d[4], dlam = d[5], dz = d[9];
-      out.rgb[3 * i + 0] += d[6];
-      out.rgb[3 * i + 1] += d[7];
-      out.rgb[3 * i + 2] += d[8];
-      out.opacity_logit[i] += dlam * m.lam * (1.0f - m.lam);
-      // conic Q = cov^-1 with cov = [[ca, cb], [cb, cc]]; the off-diagonal conic
-      // entry is one scalar used twice, so the full-matrix gradient of Q is
-      // [[dqa, dqb/2], [dqb/2, dqc]] and d cov = -Q dQ Q.
-      const float4 Q = reinterpret_cast<const float4*>(conic)[i];
-      const float qa = Q.x, qb = Q.y, qc = Q.z;
-      const float h = 0.5f * dqb;
-      const float t00 = qa * dqa + qb * h, t01 = qa * h + qb * dqc;
-      const float t10 = qb * dqa + qc * h, t11 = qb * h + qc * dqc;
-      const float g00 = -(t00 * qa + t01 * qb);
-      const float g01 = -(t00 * qb + t01 * qc);
-      const float g11 = -(t10 * qb + t11 * qc);
-      // cov = Tm Sig Tm^T: dTm = 2 G Tm Sig, dSig = Tm^T G Tm  (G symmetric 2x2)
-      float TS[6];
+  for (int k = 0; k < 12; ++k) W[k] = __ldg(w2c + k);
+  float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int qn = 0;  // warp-uniform
+  const int64_t stride_all = (int64_t)gridDim.x * kPbThreads;
+  for (int64_t base = ((int64_t)blockIdx.x * kPbWarps + warp) * 32; base < g.n; base += stride_all) {
+    const int64_t i = base + lane;
+    if (i < g.n && d2d_out) {
 #pragma unroll
-      for (int a2 = 0; a2 < 2; ++a2)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-          TS[3 * a2 + j] = m.Tm[3 * a2] * m.Sig[j] + m.Tm[3 * a2 + 1] * m.Sig[3 + j] + m.Tm[3 * a2 + 2] * m.Sig[6 + j];
-      float dTm[6];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        dTm[j] = 2.0f * (g00 * TS[j] + g01 * TS[3 + j]);
-        dTm[3 + j] = 2.0f * (g01 * TS[j] + g11 * TS[3 + j]);
-      }
-      float dSig[9];
-#pragma unroll
-      for (int a3 = 0; a3 < 3; ++a3)
-#pragma unroll
-        for (int b3 = 0; b3 < 3; ++b3) {
-          const float x0 = m.Tm[a3], x1 = m.Tm[3 + a3];
-          const float y0 = m.Tm[b3], y1 = m.Tm[3 + b3];
-          dSig[3 * a3 + b3] = x0 * (g00 * y0 + g01 * y1) + x1 * (g01 * y0 + g11 * y1);
-        }
-      // Tm rows: (J00 W0 + J02 W2), (J11 W1 + J12 W2)
-      const float dJ00 = dTm[0] * W[0] + dTm[1] * W[1] + dTm[2] * W[2];
-      const float dJ02 = dTm[0] * W[8] + dTm[1] * W[9] + dTm[2] * W[10];
-      const float dJ11 = dTm[3] * W[4] + dTm[4] * W[5] + dTm[5] * W[6];
-      const float dJ12 = dTm[3] * W[8] + dTm[4] * W[9] + dTm[5] * W[10];
-      // gradient of the rotation block through Tm: dW_ij = sum_a J_ai dTm_aj
-      float dWr[9];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        dWr[j] = m.J00 * dTm[j];
-        dWr[3 + j] = m.J11 * dTm[3 + j];
-        dWr[6 + j] = m.J02 * dTm[j] + m.J12 * dTm[3 + j];
-      }
-      const float z = m.p[2];
-      const float iz = 1.0f / z, iz2 = iz * iz, iz3 = iz2 * iz;
-      float gz = -cam.fx * iz2 * dJ00 - cam.fy * iz2 * dJ11 + 2.0f * cam.fx * m.tx * iz3 * dJ02 +
-                 2.0f * cam.fy * m.ty * iz3 * dJ12;
-      const float gtx = -cam.fx * iz2 * dJ02;
-      const float gty = -cam.fy * iz2 * dJ12;
-      float gp0 = 0.f, gp1 = 0.f;
-      if (m.clamp_x) gz += gtx * (m.tx * iz); else gp0 += gtx;
-      if (m.clamp_y) gz += gty * (m.ty * iz); else gp1 += gty;
-      gp0 += du * cam.fx * iz;
-      gp1 += dv * cam.fy * iz;
-      gz -= (du * cam.fx * m.p[0] + dv * cam.fy * m.p[1]) * iz2;
-      gz += dz;
-      const float gp[3] = {gp0, gp1, gz};
-#pragma unroll
-      for (int j = 0; j < 3; ++j) out.mean[3 * i + j] += W[j] * gp[0] + W[4 + j] * gp[1] + W[8 + j] * gp[2];
-      // Sig = M M^T, M = R diag(s)
-      float dM[9];
-#pragma unroll
-      for (int a3 = 0; a3 < 3; ++a3)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-          dM[3 * a3 + j] = 2.0f * (dSig[3 * a3] * m.M[j] + dSig[3 * a3 + 1] * m.M[3 + j] + dSig[3 * a3 + 2] * m.M[6 + j]);
-      float dR[9];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const float gs = dM[j] * m.R[j] + dM[3 + j] * m.R[3 + j] + dM[6 + j] * m.R[6 + j];
-        out.log_scale[3 * i + j] += gs * m.s[j];
-        dR[j] = dM[j] * m.s[j];
-        dR[3 + j] = dM[3 + j] * m.s[j];
-        dR[6 + j] = dM[6 + j] * m.s[j];
-      }
-      if (m.qnorm > 0.0f) {
-        const float r = m.qn[0], a = m.qn[1], b = m.qn[2], c = m.qn[3];
-        float gq[4];
-        gq[0] = 2.0f * (c * (dR[3] - dR[1]) + b * (dR[2] - dR[6]) + a * (dR[7] - dR[5]));
-        gq[1] = 2.0f * (b * (dR[1] + dR[3]) + c * (dR[2] + dR[6]) + r * (dR[7] - dR[5])) - 4.0f * a * (dR[4] + dR[8]);
-        gq[2] = 2.0f * (a * (dR[1] + dR[3]) + r * (dR[2] - dR[6]) + c * (dR[5] + dR[7])) - 4.0f * b * (dR[0] + dR[8]);
-        gq[3] = 2.0f * (r * (dR[3] - dR[1]) + a * (dR[2] + dR[6]) + b * (dR[5] + dR[7])) - 4.0f * c * (dR[0] + dR[4]);
-        const float dot = r * gq[0] + a * gq[1] + b * gq[2] + c * gq[3];
-        const float inv = 1.0f / m.qnorm;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) out.quat[4 * i + k] += (gq[k] - m.qn[k] * dot) * inv;
-      }
-      // pose: rho = dL/dp ; phi = p x dL/dp + vee(dW W^T)
-      float A[9];
-#pragma unroll
-      for (int a3 = 0; a3 < 3; ++a3)
-#pragma unroll
-        for (int b3 = 0; b3 < 3; ++b3)
-          A[3 * a3 + b3] = dWr[3 * a3] * W[4 * b3] + dWr[3 * a3 + 1] * W[4 * b3 + 1] + dWr[3 * a3 + 2] * W[4 * b3 + 2];
-      pose[0] = gp[0];
-      pose[1] = gp[1];
-      pose[2] = gp[2];
-      pose[3] = m.p[1] * gp[2] - m.p[2] * gp[1] + (A[7] - A[5]);
-      pose[4] = m.p[2] * gp[0] - m.p[0] * gp[2] + (A[2] - A[6]);
-      pose[5] = m.p[0] * gp[1] - m.p[1] * gp[0] + (A[3] - A[1]);
+      for (int k = 0; k < 10; ++k) d2d_out[10 * i + k] = g2[(size_t)stride * i + k];
+    }
+    const bool vis = i < g.n && radius[i] != 0;
+    const unsigned m = __ballot_sync(full, vis);
+    if (vis) queue[warp][qn + __popc(m & lower)] = (int32_t)i;
+    qn += __popc(m);
+    __syncwarp();
+    if (qn >= 32) {
+      project_adjoint_one(g, cam, W, conic, g2, stride, out, queue[warp][lane], pose);
+      __syncwarp();
+      if (lane < qn - 32) queue[warp][lane] = queue[warp][32 + lane];
+      __syncwarp();
+      qn -= 32;
     }
   }
+  if (lane < qn) project_adjoint_one(g, cam, W, conic, g2, stride, out, queue[warp][lane], pose);
   if (d_pose == nullptr) return;
   // block reduction of the pose gradient: warp shuffles, then one warp
   __shared__ float red[6][8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     float x = pose[k];
@@ -322,11 +358,15 @@ int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, c
 }
 
 int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
-                       const float* g2, int stride, const GradK& out, float* d_pose, float* d2d_out,
-                       cudaStream_t s) {
+                       const int32_t* radius, const float* g2, int stride, const GradK& out, float* d_pose,
+                       float* d2d_out, cudaStream_t s) {
   if (g.n == 0) return SPLAT_OK;
-  SPLAT_LAUNCH("project_bwd_kernel", s, project_bwd_kernel<<<ceil_div(g.n, 256), 256, 0, s>>>(g, cam, w2c, conic, g2, stride, out, d_pose,
-                                                                                    d2d_out));
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(ceil_div(g.n, kPbThreads), 2 * (int64_t)sms);
+  SPLAT_LAUNCH("project_bwd_kernel", s,
+               project_bwd_kernel<<<grid, kPbThreads, 0, s>>>(g, cam, w2c, conic, radius, g2, stride, out, d_pose,
+                                                             d2d_out));
   return check_launch("project_bwd_kernel");
 }
 

@@ -74,23 +74,77 @@ struct ViewTable {
 };
 
 // Shared-memory staging of one batch of Gaussians.
+constexpr int kMaxWarps = 8;  // warps of a tile CTA (forward 8 of 2 rows, backward 4 of 4 rows)
+
+struct StagePtrs {
+  float4* xyzo;
+  float4* quad;
+  float* rgb;
+  int32_t* id;
+  uint8_t* wmask;
+};
+
 template <int BATCH>
 struct Stage {
   float4 xyzo[BATCH];
   float4 quad[BATCH];  // A = -a/2, B = -b, C = -c/2, exponent cut
   float rgb[3 * BATCH];
   int32_t id[BATCH];
+  uint8_t wmask[BATCH];              // warps whose pixel rows the Gaussian can reach
+  uint8_t wlist[kMaxWarps][BATCH];   // per warp: the staged positions it visits, ascending
 };
 
-__device__ __forceinline__ void stage_one(const ViewK& V, uint32_t g, int i, float4* xyzo, float4* quad, float* rgb,
-                                          int32_t* id) {
+// Bit w set when the pixel rows of warp w (rows_per_warp consecutive rows of
+// the tile) and the tile's columns meet the box around the ellipse on which
+// the exponent reaches the Gaussian's cut: outside it every pixel would skip
+// the Gaussian, so a warp whose bit is clear need not look at it.  The box
+// half-widths sqrt(K c / det), sqrt(K a / det) (K = -2 cut, det = ac - b^2)
+// are widened by 0.1% + 0.01 px, far beyond the rounding of the per-pixel test.
+__device__ __forceinline__ uint8_t warp_mask(const float4 xo, const float4 co, int tx0, int ty0, int rows_per_warp) {
+  const float K = -2.0f * co.w;
+  if (!(K > 0.0f)) return 0;  // the cut is above 1: no pixel passes
+  const float det = co.x * co.z - co.y * co.y;
+  if (!(det > 0.0f)) return 0xff;
+  const float sk = K / det;
+  const float ex = sqrtf(sk * co.z) * 1.001f + 0.01f;
+  const float ey = sqrtf(sk * co.x) * 1.001f + 0.01f;
+  if (!(ex < 1e30f && ey < 1e30f)) return 0xff;
+  if (xo.x + ex < (float)tx0 + 0.5f || xo.x - ex > (float)tx0 + 15.5f) return 0;
+  const float lo = fmaxf(0.0f, ceilf(xo.y - ey - (float)ty0 - 0.5f));
+  const float hi = fminf(15.0f, floorf(xo.y + ey - (float)ty0 - 0.5f));
+  if (lo > hi) return 0;
+  const int w0 = (int)lo / rows_per_warp, w1 = (int)hi / rows_per_warp;
+  return (uint8_t)(((2u << w1) - 1u) & ~((1u << w0) - 1u));
+}
+
+__device__ __forceinline__ void stage_one(const ViewK& V, uint32_t g, int i, StagePtrs p, int tx0, int ty0,
+                                          int rows_per_warp) {
   const float4 co = V.conic[g];
-  id[i] = (int32_t)g;
-  xyzo[i] = V.xyzo[g];
-  quad[i] = make_float4(-0.5f * co.x, -co.y, -0.5f * co.z, co.w);
-  rgb[3 * i + 0] = V.rgb[3 * (size_t)g + 0];
-  rgb[3 * i + 1] = V.rgb[3 * (size_t)g + 1];
-  rgb[3 * i + 2] = V.rgb[3 * (size_t)g + 2];
+  const float4 xo = V.xyzo[g];
+  p.id[i] = (int32_t)g;
+  p.xyzo[i] = xo;
+  p.quad[i] = make_float4(-0.5f * co.x, -co.y, -0.5f * co.z, co.w);
+  p.rgb[3 * i + 0] = V.rgb[3 * (size_t)g + 0];
+  p.rgb[3 * i + 1] = V.rgb[3 * (size_t)g + 1];
+  p.rgb[3 * i + 2] = V.rgb[3 * (size_t)g + 2];
+  p.wmask[i] = warp_mask(xo, co, tx0, ty0, rows_per_warp);
+}
+
+// The positions (ascending) of the cnt staged Gaussians whose mask has this
+// warp's bit; returns their number.  All lanes of the warp take part.
+__device__ __forceinline__ int build_warp_list(const uint8_t* wmask, uint8_t* list, int cnt, int warp) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lower = (1u << lane) - 1u;
+  int n = 0;
+  for (int k0 = 0; k0 < cnt; k0 += 32) {
+    const int k = k0 + lane;
+    const bool in = k < cnt && ((wmask[k] >> warp) & 1u);
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if (in) list[n + __popc(m & lower)] = (uint8_t)k;
+    n += __popc(m);
+  }
+  __syncwarp();
+  return n;
 }
 
 // ----------------------------------------------------------------------------
@@ -142,15 +196,20 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
   const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
   FwdPix q{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, 0, 0, !inside};
   const uint2 rg = V.ranges[tile];
+  const int warp = threadIdx.x >> 5;
+  const StagePtrs sp{sm.xyzo, sm.quad, sm.rgb, sm.id, sm.wmask};
   for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
     if (__syncthreads_count(q.done) == kFwdThreads) break;
     if (threadIdx.x < BATCH && start + threadIdx.x < rg.y)
-      stage_one(V, V.vals[start + threadIdx.x], threadIdx.x, sm.xyzo, sm.quad, sm.rgb, sm.id);
+      stage_one(V, V.vals[start + threadIdx.x], threadIdx.x, sp, tx * kTile, ty * kTile, 2);
     __syncthreads();
     const int cnt = (int)min((uint32_t)BATCH, rg.y - start);
     const int32_t base = (int32_t)(start - rg.x);
-    for (int j = 0; j < cnt && !q.done; ++j)
+    const int nl = build_warp_list(sm.wmask, sm.wlist[warp], cnt, warp);
+    for (int e = 0; e < nl && !q.done; ++e) {
+      const int j = sm.wlist[warp][e];
       composite_step(q, sm.xyzo[j], sm.quad[j], fx, fy, &sm.rgb[3 * j], sm.id[j], base + j);
+    }
   }
   if (!inside) return;
   const size_t i = (size_t)py * cam.width + px;
@@ -325,7 +384,8 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
     b.gS = (inside && V.d_sil) ? V.d_sil[i] : 0.f;
     b.Q = (b.gC0 * V.bg0 + b.gC1 * V.bg1 + b.gC2 * V.bg2) * Tfin;
   }
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const StagePtrs sp{sm.st.xyzo, sm.st.quad, sm.st.rgb, sm.st.id, sm.st.wmask};
   const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(q[0].last, q[1].last));
   if (threadIdx.x == 0) sm.maxlast = 0;
   __syncthreads();
@@ -337,10 +397,12 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
     const int cnt = end - start;
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += kBwdThreads)
-      stage_one(V, V.vals[rg.x + start + i], i, sm.st.xyzo, sm.st.quad, sm.st.rgb, sm.st.id);
+      stage_one(V, V.vals[rg.x + start + i], i, sp, tx * kTile, ty * kTile, 4);
     for (int i = threadIdx.x; i < BATCH * kAccStride; i += kBwdThreads) sm.acc[i] = 0.f;
     __syncthreads();
-    for (int j = cnt - 1; j >= 0; --j) {
+    const int nl = build_warp_list(sm.st.wmask, sm.st.wlist[warp], cnt, warp);
+    for (int e = nl - 1; e >= 0; --e) {
+      const int j = sm.st.wlist[warp][e];
       const int pos = start + j;
       if (pos >= wlast) continue;  // warp-uniform: no pixel of this warp reaches pos
       const float4 xo = sm.st.xyzo[j];
@@ -466,6 +528,7 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
   if ((g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->rgb)) || !aligned16(g->quat))
     return fail(SPLAT_EINVAL, "splat_render_bwd: gaussian arrays null or quat not 16-byte aligned");
   if (g->n < 0 || cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "splat_render_bwd: bad sizes");
+  if (g->n > 0 && !proj->radius) return fail(SPLAT_EINVAL, "splat_render_bwd: proj->radius is null");
   if (!ws || !aligned16(ws) || ws_bytes < splat_render_bwd_workspace_size(g->n))
     return fail(SPLAT_EINVAL, "splat_render_bwd: workspace missing, too small or not 16-byte aligned");
   float* g2 = static_cast<float*>(ws);
@@ -482,7 +545,7 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
   if ((rc = check_launch("render_bwd_kernel"))) return rc;
   GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
   GradK gr{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};
-  return launch_project_bwd(gk, v.cam, w2c, proj->conic, g2, kGradStride, gr, d_pose, d2d, s);
+  return launch_project_bwd(gk, v.cam, w2c, proj->conic, proj->radius, g2, kGradStride, gr, d_pose, d2d, s);
 }
 
 extern "C" int splat_project_bwd(const splat_gaussians* g, const splat_projected* proj, const splat_camera* cam,
@@ -495,9 +558,10 @@ extern "C" int splat_project_bwd(const splat_gaussians* g, const splat_projected
                                 !out->log_scale || !out->quat || !out->opacity_logit || !out->rgb)) ||
       !aligned16(g->quat) || !aligned16(grad2d))
     return fail(SPLAT_EINVAL, "splat_project_bwd: bad gaussian or gradient arrays");
+  if (g->n > 0 && !proj->radius) return fail(SPLAT_EINVAL, "splat_project_bwd: proj->radius is null");
   GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
   GradK gr{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};
-  return launch_project_bwd(gk, make_camk(*cam), w2c, proj->conic, grad2d, kGradStride, gr, d_pose, d2d,
+  return launch_project_bwd(gk, make_camk(*cam), w2c, proj->conic, proj->radius, grad2d, kGradStride, gr, d_pose, d2d,
                             reinterpret_cast<cudaStream_t>(stream));
 }
 

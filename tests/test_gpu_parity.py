@@ -459,3 +459,44 @@ def test_distance_selection_parity(dev):
     for name, gg in zip(("mean", "log_scale", "quat", "opacity_logit", "rgb"), grads):
         _assert_grad_close(gg, refg[name], name)
     _assert_grad_close(d_pose, refg["pose"], "pose")
+
+
+def _assoc_gpu(dev, ia, ta, ib, tb, n_a, n_b, t_max):
+    from paper_2412_09723_gb300 import binding as B
+
+    t = [torch.as_tensor(np.ascontiguousarray(x), device=dev) for x in (ia, ta, ib, tb)]
+    npix = ia.size
+    pairs = torch.zeros(npix, 2, dtype=torch.int32, device=dev)
+    counts = torch.zeros(npix, dtype=torch.int32, device=dev)
+    m_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(B.splat_assoc_workspace_size(npix), dtype=torch.uint8, device=dev)
+    B.splat_assoc(t[0], t[1], t[2], t[3], n_a, n_b, t_max, pairs, counts, npix, m_dev, status, ws)
+    torch.cuda.synchronize()
+    m = int(m_dev.item())
+    assert int(status.item()) == 0
+    return pairs[:m].cpu().numpy(), counts[:m].cpu().numpy()
+
+
+def test_assoc_runs_and_global_table(dev):
+    """Long horizontal runs of one pair (merged per thread, split at chunk and
+    CTA boundaries), and buckets with tens of thousands of distinct pairs (the
+    global-memory hash table): pairs and pixel counts equal the oracle's."""
+    rng = np.random.default_rng(9)
+    H, W = 333, 517
+    yy, xx = np.mgrid[0:H, 0:W]
+    ia = ((yy // 3) * 1000 + xx // 13).astype(np.int32)   # runs of 13 along rows
+    ib = ((yy // 5) * 700 + xx // 11).astype(np.int32)
+    ia[rng.uniform(size=ia.shape) < 0.02] = -1
+    ta = rng.uniform(0, 1, (H, W)).astype(np.float32)
+    tb = rng.uniform(0, 0.6, (H, W)).astype(np.float32)
+    ref = oracle.assoc(ia, ta, ib, tb, 0.8)
+    got = _assoc_gpu(dev, ia, ta, ib, tb, int(ia.max()) + 1, int(ib.max()) + 1, 0.8)
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    # three ids of map A, each paired with ~40k distinct ids of map B
+    ia2 = rng.integers(0, 3, (H, W)).astype(np.int32)
+    ib2 = rng.integers(0, 60000, (H, W)).astype(np.int32)
+    ref2 = oracle.assoc(ia2, ta, ib2, tb, 0.8)
+    assert len(ref2[0]) > 3 * 2000
+    got2 = _assoc_gpu(dev, ia2, ta, ib2, tb, 3, 60000, 0.8)
+    assert np.array_equal(got2[0], ref2[0]) and np.array_equal(got2[1], ref2[1])
