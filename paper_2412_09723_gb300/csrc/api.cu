@@ -86,20 +86,27 @@ __device__ __forceinline__ float bias_correction(float beta, const int32_t* step
   return 1.0f - powf(beta, (float)(*step));
 }
 
+// One Adam update.  The bias corrections enter as reciprocals (computed once
+// per thread) and the step's division is the fast one: the update differs
+// from the textbook expression by a few ulp of the step, not of the parameter.
+__device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, float lr, float b1, float b2,
+                                            float ibc1, float ibc2, float eps) {
+  m = b1 * m + (1.0f - b1) * g;
+  v = b2 * v + (1.0f - b2) * g * g;
+  p = p - __fdividef(lr * (m * ibc1), sqrtf(v * ibc2) + eps);
+}
+
 __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, const float* __restrict__ g,
                                                    float* __restrict__ m, float* __restrict__ v, int64_t n, float lr,
                                                    float b1, float b2, const int32_t* __restrict__ step, float eps) {
-  const float bc1 = bias_correction(b1, step);
-  const float bc2 = bias_correction(b2, step);
+  const float ibc1 = 1.0f / bias_correction(b1, step);
+  const float ibc2 = 1.0f / bias_correction(b2, step);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    float pi = p[i], mi = m[i], vi = v[i];
+    adam_update(pi, g[i], mi, vi, lr, b1, b2, ibc1, ibc2, eps);
     m[i] = mi;
     v[i] = vi;
-    const float mh = mi / bc1;
-    const float vh = vi / bc2;
-    p[i] = p[i] - lr * mh / (sqrtf(vh) + eps);
+    p[i] = pi;
   }
 }
 
@@ -116,10 +123,8 @@ struct AdamGroups {
 };
 
 __device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v, float lr, float b1, float b2,
-                                         float bc1, float bc2, float eps, int zero_grad) {
-  m = b1 * m + (1.0f - b1) * g;
-  v = b2 * v + (1.0f - b2) * g * g;
-  p = p - lr * (m / bc1) / (sqrtf(v / bc2) + eps);
+                                         float ibc1, float ibc2, float eps, int zero_grad) {
+  adam_update(p, g, m, v, lr, b1, b2, ibc1, ibc2, eps);
   if (zero_grad) g = 0.0f;
 }
 
@@ -127,8 +132,8 @@ __device__ __forceinline__ void adam_one(float& p, float& g, float& m, float& v,
 // (float4 loads where the 4 elements lie inside one 16-byte-aligned group).
 __global__ void __launch_bounds__(256) adam_groups_kernel(AdamGroups G, int64_t total4, float b1, float b2,
                                                           const int32_t* __restrict__ step, float eps, int zero_grad) {
-  const float bc1 = bias_correction(b1, step);
-  const float bc2 = bias_correction(b2, step);
+  const float bc1 = 1.0f / bias_correction(b1, step);  // reciprocals
+  const float bc2 = 1.0f / bias_correction(b2, step);
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total4; u += (int64_t)gridDim.x * blockDim.x) {
     int k = 0;
     while (k + 1 < G.n && u >= G.end[k]) ++k;

@@ -94,29 +94,70 @@ struct Stage {
   uint8_t wlist[kMaxWarps][BATCH];   // per warp: the staged positions it visits, ascending
 };
 
-// Bit w set when the pixel rows of warp w (rows_per_warp consecutive rows of
-// the tile) and the tile's columns meet the box around the ellipse on which
-// the exponent reaches the Gaussian's cut: outside it every pixel would skip
-// the Gaussian, so a warp whose bit is clear need not look at it.  The box
-// half-widths sqrt(K c / det), sqrt(K a / det) (K = -2 cut, det = ac - b^2)
-// are widened by 0.1% + 0.01 px, far beyond the rounding of the per-pixel test.
+// Whether the ellipse a dx^2 + 2 b dx dy + c dy^2 <= K (centred at the
+// origin) meets the rectangle [dxa, dxb] x [dya, dyb]: the quadratic form is
+// convex, so its minimum over the rectangle is 0 with the centre inside, else
+// on an edge, where it is a 1-D quadratic minimised in closed form.
+__device__ __forceinline__ bool ellipse_meets_rect(float dxa, float dxb, float dya, float dyb, float a, float b,
+                                                   float c, float ba, float bc, float K) {
+  if (dxa <= 0.0f && 0.0f <= dxb && dya <= 0.0f && 0.0f <= dyb) return true;
+  float m = 3.0e38f;
+#pragma unroll 1
+  for (int e = 0; e < 2; ++e) {
+    const float dy = e ? dyb : dya;  // horizontal edge, minimiser dx = -(b/a) dy
+    const float dx = fminf(dxb, fmaxf(dxa, -ba * dy));
+    m = fminf(m, (a * dx + 2.0f * b * dy) * dx + c * dy * dy);
+    const float ex = e ? dxb : dxa;  // vertical edge, minimiser dy = -(b/c) dx
+    const float ey = fminf(dyb, fmaxf(dya, -bc * ex));
+    m = fminf(m, a * ex * ex + (2.0f * b * ex + c * ey) * ey);
+  }
+  return m <= K;
+}
+
+// Bit w set when the pixel centres of warp w (rows_per_warp consecutive rows
+// of the tile, all 16 columns) can lie on the ellipse where the exponent
+// reaches the Gaussian's cut (a dx^2 + 2 b dx dy + c dy^2 <= K, K = -2 cut):
+// outside it every pixel skips the Gaussian, so a warp whose bit is clear need
+// not look at it.  The bounding box of the ellipse (half-widths
+// sqrt(K c / det), sqrt(K a / det), det = ac - b^2) limits the candidate rows;
+// with EXACT (the backward pass, where a visit costs most) each candidate
+// warp's rectangle of pixel centres is then tested against the ellipse itself.
+// K is widened by 0.2% + 1e-3 and the box by 0.1% + 0.01 px, far beyond the
+// rounding of the per-pixel test, so no pixel that would take the Gaussian is
+// ever left out.
+template <bool EXACT>
 __device__ __forceinline__ uint8_t warp_mask(const float4 xo, const float4 co, int tx0, int ty0, int rows_per_warp) {
   const float K = -2.0f * co.w;
   if (!(K > 0.0f)) return 0;  // the cut is above 1: no pixel passes
-  const float det = co.x * co.z - co.y * co.y;
-  if (!(det > 0.0f)) return 0xff;
+  const float a = co.x, b = co.y, c = co.z;
+  const float det = a * c - b * b;
+  if (!(det > 0.0f && a > 0.0f && c > 0.0f)) return 0xff;
   const float sk = K / det;
-  const float ex = sqrtf(sk * co.z) * 1.001f + 0.01f;
-  const float ey = sqrtf(sk * co.x) * 1.001f + 0.01f;
+  const float ex = sqrtf(sk * c) * 1.001f + 0.01f;
+  const float ey = sqrtf(sk * a) * 1.001f + 0.01f;
   if (!(ex < 1e30f && ey < 1e30f)) return 0xff;
-  if (xo.x + ex < (float)tx0 + 0.5f || xo.x - ex > (float)tx0 + 15.5f) return 0;
+  const float xa = fmaxf((float)tx0 + 0.5f, xo.x - ex), xb = fminf((float)tx0 + 15.5f, xo.x + ex);
+  if (xa > xb) return 0;
   const float lo = fmaxf(0.0f, ceilf(xo.y - ey - (float)ty0 - 0.5f));
   const float hi = fminf(15.0f, floorf(xo.y + ey - (float)ty0 - 0.5f));
   if (lo > hi) return 0;
-  const int w0 = (int)lo / rows_per_warp, w1 = (int)hi / rows_per_warp;
-  return (uint8_t)(((2u << w1) - 1u) & ~((1u << w0) - 1u));
+  const int r0 = (int)lo, r1 = (int)hi;
+  const int w0 = r0 / rows_per_warp, w1 = r1 / rows_per_warp;
+  if (!EXACT) return (uint8_t)(((2u << w1) - 1u) & ~((1u << w0) - 1u));
+  const float Kt = K * 1.002f + 1e-3f;
+  const float ba = __fdividef(b, a), bc = __fdividef(b, c);
+  uint8_t mask = 0;
+#pragma unroll 1
+  for (int w = w0; w <= w1; ++w) {
+    const int ra = max(r0, w * rows_per_warp), rb = min(r1, w * rows_per_warp + rows_per_warp - 1);
+    const float ya = (float)(ty0 + ra) + 0.5f, yb = (float)(ty0 + rb) + 0.5f;
+    if (ellipse_meets_rect(xa - xo.x, xb - xo.x, ya - xo.y, yb - xo.y, a, b, c, ba, bc, Kt))
+      mask |= (uint8_t)(1u << w);
+  }
+  return mask;
 }
 
+template <bool EXACT>
 __device__ __forceinline__ void stage_one(const ViewK& V, uint32_t g, int i, StagePtrs p, int tx0, int ty0,
                                           int rows_per_warp) {
   const float4 co = V.conic[g];
@@ -127,7 +168,7 @@ __device__ __forceinline__ void stage_one(const ViewK& V, uint32_t g, int i, Sta
   p.rgb[3 * i + 0] = V.rgb[3 * (size_t)g + 0];
   p.rgb[3 * i + 1] = V.rgb[3 * (size_t)g + 1];
   p.rgb[3 * i + 2] = V.rgb[3 * (size_t)g + 2];
-  p.wmask[i] = warp_mask(xo, co, tx0, ty0, rows_per_warp);
+  p.wmask[i] = warp_mask<EXACT>(xo, co, tx0, ty0, rows_per_warp);
 }
 
 // The positions (ascending) of the cnt staged Gaussians whose mask has this
@@ -201,7 +242,7 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
   for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
     if (__syncthreads_count(q.done) == kFwdThreads) break;
     if (threadIdx.x < BATCH && start + threadIdx.x < rg.y)
-      stage_one(V, V.vals[start + threadIdx.x], threadIdx.x, sp, tx * kTile, ty * kTile, 2);
+      stage_one<false>(V, V.vals[start + threadIdx.x], threadIdx.x, sp, tx * kTile, ty * kTile, 2);
     __syncthreads();
     const int cnt = (int)min((uint32_t)BATCH, rg.y - start);
     const int32_t base = (int32_t)(start - rg.x);
@@ -225,7 +266,7 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
 }
 
 template <int BATCH>
-__global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(ViewK V) {
+__global__ void __launch_bounds__(kFwdThreads, 6) render_fwd_kernel(ViewK V) {
   __shared__ Stage<BATCH> sm;
   fwd_tile<BATCH>(V, blockIdx.x, sm);
 }
@@ -246,7 +287,7 @@ __device__ __forceinline__ int next_item(int* counter, int* s_item) {
 }
 
 template <int BATCH>
-__global__ void __launch_bounds__(kFwdThreads) render_fwd_persistent(ViewTable T, int total, int* counter) {
+__global__ void __launch_bounds__(kFwdThreads, 6) render_fwd_persistent(ViewTable T, int total, int* counter) {
   __shared__ Stage<BATCH> sm;
   __shared__ int s_item;
   for (int item = next_item(counter, &s_item); item < total; item = next_item(counter, &s_item)) {
@@ -397,7 +438,7 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
     const int cnt = end - start;
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += kBwdThreads)
-      stage_one(V, V.vals[rg.x + start + i], i, sp, tx * kTile, ty * kTile, 4);
+      stage_one<true>(V, V.vals[rg.x + start + i], i, sp, tx * kTile, ty * kTile, 4);
     for (int i = threadIdx.x; i < BATCH * kAccStride; i += kBwdThreads) sm.acc[i] = 0.f;
     __syncthreads();
     const int nl = build_warp_list(sm.st.wmask, sm.st.wlist[warp], cnt, warp);
