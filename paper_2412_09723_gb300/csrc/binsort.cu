@@ -266,13 +266,20 @@ constexpr int kScatterThreads = 256;
 constexpr int kScatterLanes = 4;     // threads sharing one Gaussian's rect (rows interleaved)
 constexpr int kScanGridSmem = 10240; // count-grid cells staged in shared memory (40 KB)
 
-// Visible Gaussians (tiles_touched > 0) appended to vis[] with one atomic per
-// CTA; the 64-bit duplicate total K is summed on the way.
-__global__ void __launch_bounds__(256) compact_visible_kernel(const int32_t* __restrict__ tiles, int64_t n,
-                                                              uint32_t* __restrict__ vis,
-                                                              unsigned int* __restrict__ n_vis,
-                                                              unsigned long long* __restrict__ k_total) {
+// Visible Gaussians (tiles_touched > 0) are appended to vis[] with one atomic
+// per CTA, the duplicate total K is summed per CTA (one 64-bit atomic per CTA),
+// and every visible Gaussian's rect enters the tile counts through a 2D
+// difference array: +1 at (x0, y0) and (x1, y1), -1 at (x1, y0) and (x0, y1);
+// the prefix sums in tile_scan_kernel turn it into the number of rects
+// holding each tile.
+__global__ void __launch_bounds__(256) compact_count_kernel(const int32_t* __restrict__ tiles,
+                                                            const int4* __restrict__ rect, int64_t n, int gw,
+                                                            uint32_t* __restrict__ vis,
+                                                            unsigned int* __restrict__ n_vis,
+                                                            unsigned long long* __restrict__ k_total,
+                                                            int* __restrict__ diff) {
   __shared__ unsigned int s_warp[8];
+  __shared__ unsigned long long s_k[8];
   __shared__ unsigned int s_base;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int tt = i < n ? tiles[i] : 0;
@@ -284,37 +291,30 @@ __global__ void __launch_bounds__(256) compact_visible_kernel(const int32_t* __r
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   if (lane == 0) {
     s_warp[warp] = __popc(ball);
-    if (t) atomicAdd(k_total, t);
+    s_k[warp] = t;
+  }
+  if (v) {
+    const int4 r = rect[i];
+    atomicAdd(&diff[r.y * gw + r.x], 1);
+    atomicAdd(&diff[r.y * gw + r.z], -1);
+    atomicAdd(&diff[r.w * gw + r.x], -1);
+    atomicAdd(&diff[r.w * gw + r.z], 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int tot = 0;
+    unsigned long long k = 0;
     for (int w = 0; w < 8; ++w) {
       const unsigned int c = s_warp[w];
       s_warp[w] = tot;
       tot += c;
+      k += s_k[w];
     }
     s_base = tot ? atomicAdd(n_vis, tot) : 0u;
+    if (k) atomicAdd(k_total, k);
   }
   __syncthreads();
   if (v) vis[s_base + s_warp[warp] + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
-}
-
-// Tile counts by a 2D difference array: +1 at (x0, y0) and (x1, y1), -1 at
-// (x1, y0) and (x0, y1); the prefix sums in tile_scan_kernel turn it into the
-// number of rects holding each tile.  Grid: ceil(n / 256) CTAs; CTAs past the
-// visible count return.
-__global__ void __launch_bounds__(256) tile_count_kernel(const uint32_t* __restrict__ vis,
-                                                         const unsigned int* __restrict__ n_vis,
-                                                         const int4* __restrict__ rect, int gw,
-                                                         int* __restrict__ diff) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)*n_vis) return;
-  const int4 r = rect[vis[i]];
-  atomicAdd(&diff[r.y * gw + r.x], 1);
-  atomicAdd(&diff[r.y * gw + r.z], -1);
-  atomicAdd(&diff[r.w * gw + r.x], -1);
-  atomicAdd(&diff[r.w * gw + r.z], 1);
 }
 
 // One CTA: 2D prefix sums of the difference grid (tiles_y + 1 rows of
@@ -333,19 +333,27 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
   if (grid == s_grid)
     for (int i = threadIdx.x; i < cells; i += blockDim.x) s_grid[i] = diff[i];
   __syncthreads();
-  for (int y = threadIdx.x; y < tiles_y; y += blockDim.x) {
-    int run = 0;
-    for (int x = 0; x < tiles_x; ++x) {
-      run += grid[y * gw + x];
-      grid[y * gw + x] = run;
+  // row prefix sums, one warp per row, then column prefix sums, one warp per
+  // column (32 cells per warp scan; two's-complement sums, so the negative
+  // entries of the difference array need no special care)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int y = wid; y < tiles_y; y += nw) {
+    uint32_t carry = 0;
+    for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+      const int x = x0 + lane;
+      const uint32_t v = warp_incl_scan(x < tiles_x ? (uint32_t)grid[y * gw + x] : 0u, lane) + carry;
+      if (x < tiles_x) grid[y * gw + x] = (int)v;
+      carry = __shfl_sync(0xffffffffu, v, 31);
     }
   }
   __syncthreads();
-  for (int x = threadIdx.x; x < tiles_x; x += blockDim.x) {
-    int run = 0;
-    for (int y = 0; y < tiles_y; ++y) {
-      run += grid[y * gw + x];
-      grid[y * gw + x] = run;
+  for (int x = wid; x < tiles_x; x += nw) {
+    uint32_t carry = 0;
+    for (int y0 = 0; y0 < tiles_y; y0 += 32) {
+      const int y = y0 + lane;
+      const uint32_t v = warp_incl_scan(y < tiles_y ? (uint32_t)grid[y * gw + x] : 0u, lane) + carry;
+      if (y < tiles_y) grid[y * gw + x] = (int)v;
+      carry = __shfl_sync(0xffffffffu, v, 31);
     }
   }
   __syncthreads();
@@ -429,9 +437,16 @@ __global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(
 // (chunks of kSegCap keys, merged in global memory above that).  Dynamic
 // shared memory: two key buffers of kSegCap, 8 x 256 digit counters, scan
 // scratch.
-constexpr size_t kSortSmem = 2 * sizeof(uint64_t) * kSegCap + sizeof(uint32_t) * (kSegRadixWarps * 256 + 64);
+// CAP keys per shared-memory sort: kSegCap, or half of it when the average
+// bucket is small (so that more CTAs fit on an SM; longer buckets still sort
+// correctly through the merge path).
+template <int CAP>
+constexpr size_t sort_smem_bytes() {
+  return 2 * sizeof(uint64_t) * CAP + sizeof(uint32_t) * (kSegRadixWarps * 256 + 64);
+}
 constexpr int kSortBitonicMax = 256;
 
+template <int CAP>
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint2* __restrict__ ranges,
                                                                  uint64_t* __restrict__ skeys,
                                                                  uint64_t* __restrict__ skeys2,
@@ -439,8 +454,8 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint2* __
                                                                  uint64_t* __restrict__ keys_out) {
   extern __shared__ __align__(16) unsigned char sort_smem[];
   uint64_t* bufa = reinterpret_cast<uint64_t*>(sort_smem);
-  uint64_t* bufb = bufa + kSegCap;
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(bufb + kSegCap);
+  uint64_t* bufb = bufa + CAP;
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(bufb + CAP);
   uint32_t* sh = cnt + kSegRadixWarps * 256;
   const int tile = blockIdx.x;
   const uint2 rg = ranges[tile];
@@ -456,10 +471,10 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint2* __
     return cta_radix_sort_hi32(bufa, bufb, m, cnt, sh);
   };
   const uint64_t* sorted;
-  if (n <= kSegCap) {
+  if (n <= CAP) {
     sorted = sort_chunk(skeys + rg.x, n);
   } else {
-    cta_sort_segment_with(skeys + rg.x, skeys2 + rg.x, skeys + rg.x, n, kSegCap, sort_chunk);
+    cta_sort_segment_with(skeys + rg.x, skeys2 + rg.x, skeys + rg.x, n, CAP, sort_chunk);
     sorted = skeys2 + rg.x;
   }
   const uint64_t thi = (uint64_t)tile << 32;
@@ -554,12 +569,10 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
   const float4* xyzo = reinterpret_cast<const float4*>(proj->xyzo);
   const int4* rect = reinterpret_cast<const int4*>(proj->rect);
   const int nb = std::max(1, ceil_div(n, 256));
-  if (n > 0) {
-    SPLAT_LAUNCH("compact_visible_kernel", s,
-                 compact_visible_kernel<<<nb, 256, 0, s>>>(proj->tiles_touched, n, w.vis, w.n_vis, w.k_total));
-    SPLAT_LAUNCH("tile_count_kernel", s,
-                 tile_count_kernel<<<nb, 256, 0, s>>>(w.vis, w.n_vis, rect, ck.tiles_x + 1, w.diff));
-  }
+  if (n > 0)
+    SPLAT_LAUNCH("compact_count_kernel", s,
+                 compact_count_kernel<<<nb, 256, 0, s>>>(proj->tiles_touched, rect, n, ck.tiles_x + 1, w.vis, w.n_vis,
+                                                         w.k_total, w.diff));
   SPLAT_LAUNCH("tile_scan_kernel", s,
                tile_scan_kernel<<<1, 1024, 0, s>>>(w.diff, ck.tiles_x, ck.tiles_y, w.k_total, capacity,
                                                    reinterpret_cast<uint2*>(ranges), w.cursor, k_dev, status));
@@ -581,14 +594,23 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(SPLAT_ECUDA, "splat_bin_sort: no current device");
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(sort_attr_done.load() & bit)) {
-      if (cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmem) !=
-          cudaSuccess)
+      if (cudaFuncSetAttribute(tile_sort_kernel<kSegCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sort_smem_bytes<kSegCap>()) != cudaSuccess ||
+          cudaFuncSetAttribute(tile_sort_kernel<kSegCap / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sort_smem_bytes<kSegCap / 2>()) != cudaSuccess)
         return fail(SPLAT_ECUDA, "splat_bin_sort: cannot enable shared memory for the tile sort");
       sort_attr_done.fetch_or(bit);
     }
   }
-  SPLAT_LAUNCH("tile_sort_kernel", s,
-               tile_sort_kernel<<<(unsigned)n_tiles, kSortThreads, kSortSmem, s>>>(
-                   reinterpret_cast<const uint2*>(ranges), w.skeys, w.skeys2, vals, keys));
+  // the duplicate capacity bounds K, so capacity / n_tiles bounds the average bucket
+  if (capacity <= (int64_t)n_tiles * (kSegCap / 2)) {
+    SPLAT_LAUNCH("tile_sort_kernel", s,
+                 tile_sort_kernel<kSegCap / 2><<<(unsigned)n_tiles, kSortThreads, sort_smem_bytes<kSegCap / 2>(), s>>>(
+                     reinterpret_cast<const uint2*>(ranges), w.skeys, w.skeys2, vals, keys));
+  } else {
+    SPLAT_LAUNCH("tile_sort_kernel", s,
+                 tile_sort_kernel<kSegCap><<<(unsigned)n_tiles, kSortThreads, sort_smem_bytes<kSegCap>(), s>>>(
+                     reinterpret_cast<const uint2*>(ranges), w.skeys, w.skeys2, vals, keys));
+  }
   return check_launch("tile_sort_kernel");
 }

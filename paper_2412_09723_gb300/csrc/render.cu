@@ -37,7 +37,8 @@
 namespace splat {
 
 constexpr int kFwdThreads = kTilePixels;  // forward: one pixel per thread
-constexpr int kBwdThreads = 128;          // backward: two pixels per thread
+constexpr int kBwdThreads = 128;          // backward (batched launch): two pixels per thread
+constexpr int kBwdSinglePPT = 2;          // backward (one view): pixels per thread (4 measured slower)
 constexpr int kGradStride = 12;           // screen-space gradient row (3 float4)
 constexpr int kAccStride = 11;            // shared accumulator row (10 sums, padded)
 constexpr int kMaxViews = SPLAT_MAX_VIEWS;
@@ -392,23 +393,26 @@ struct BwdShared {
   int maxlast;
 };
 
-// Pixel p (0 or 1) of thread t: warp w covers rows 4w .. 4w+3.
+// Pixel p (0 .. PPT-1) of thread t: warp w covers rows 2 PPT w .. 2 PPT w +
+// 2 PPT - 1 (lanes 0-15 the even rows, lanes 16-31 the odd ones).
+template <int PPT>
 __device__ __forceinline__ void bwd_pixel(int t, int p, int& lx, int& ly) {
   const int lane = t & 31, warp = t >> 5;
   lx = lane & 15;
-  ly = 4 * warp + (lane >> 4) + 2 * p;
+  ly = 2 * PPT * warp + (lane >> 4) + 2 * p;
 }
 
-template <int BATCH>
+template <int BATCH, int PPT>
 __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BATCH>& sm) {
+  constexpr int NT = kTilePixels / PPT;
   const CamK& cam = V.cam;
   const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
   const uint2 rg = V.ranges[tile];
-  BwdPix q[2];
+  BwdPix q[PPT];
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < PPT; ++p) {
     int lx, ly;
-    bwd_pixel(threadIdx.x, p, lx, ly);
+    bwd_pixel<PPT>(threadIdx.x, p, lx, ly);
     const int x = tx * kTile + lx, y = ty * kTile + ly;
     const bool inside = x < cam.width && y < cam.height;
     const size_t i = inside ? (size_t)y * cam.width + x : 0;
@@ -427,7 +431,10 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const StagePtrs sp{sm.st.xyzo, sm.st.quad, sm.st.rgb, sm.st.id, sm.st.wmask};
-  const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(q[0].last, q[1].last));
+  int mylast = 0;
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) mylast = max(mylast, q[p].last);
+  const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)mylast);
   if (threadIdx.x == 0) sm.maxlast = 0;
   __syncthreads();
   if (lane == 0 && wlast > 0) atomicMax(&sm.maxlast, wlast);
@@ -437,9 +444,9 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
     const int start = max(0, end - BATCH);
     const int cnt = end - start;
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += kBwdThreads)
-      stage_one<true>(V, V.vals[rg.x + start + i], i, sp, tx * kTile, ty * kTile, 4);
-    for (int i = threadIdx.x; i < BATCH * kAccStride; i += kBwdThreads) sm.acc[i] = 0.f;
+    for (int i = threadIdx.x; i < cnt; i += NT)
+      stage_one<true>(V, V.vals[rg.x + start + i], i, sp, tx * kTile, ty * kTile, 2 * PPT);
+    for (int i = threadIdx.x; i < BATCH * kAccStride; i += NT) sm.acc[i] = 0.f;
     __syncthreads();
     const int nl = build_warp_list(sm.st.wmask, sm.st.wlist[warp], cnt, warp);
     for (int e = nl - 1; e >= 0; --e) {
@@ -454,7 +461,7 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
       for (int k = 0; k < 10; ++k) v[k] = 0.f;
       bool any = false;
 #pragma unroll
-      for (int p = 0; p < 2; ++p)
+      for (int p = 0; p < PPT; ++p)
         if (pos < q[p].last) any |= adjoint_step(q[p], xo, qd, c0, c1, c2, v);
       if (__any_sync(0xffffffffu, any)) {
         float tot;
@@ -463,7 +470,7 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += kBwdThreads) {
+    for (int i = threadIdx.x; i < cnt; i += NT) {
       const float* a = &sm.acc[i * kAccStride];
       const float4 qd = sm.st.quad[i];
       const float ca = -2.0f * qd.x, cb = -qd.y, cc = -2.0f * qd.z;  // the conic a, b, c (exact)
@@ -478,10 +485,10 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
   }
 }
 
-template <int BATCH>
-__global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(ViewK V) {
+template <int BATCH, int PPT>
+__global__ void __launch_bounds__(kTilePixels / PPT) render_bwd_kernel(ViewK V) {
   __shared__ BwdShared<BATCH> sm;
-  bwd_tile<BATCH>(V, blockIdx.x, sm);
+  bwd_tile<BATCH, PPT>(V, blockIdx.x, sm);
 }
 
 template <int BATCH>
@@ -491,7 +498,7 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_persistent(ViewTable T
   for (int item = next_item(counter, &s_item); item < total; item = next_item(counter, &s_item)) {
     int tile;
     const int v = view_of(T, item, tile);
-    bwd_tile<BATCH>(T.v[v], tile, sm);
+    bwd_tile<BATCH, kTilePixels / kBwdThreads>(T.v[v], tile, sm);
   }
 }
 
@@ -582,7 +589,7 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
   v.d_sil = d_sil;
   v.g2 = g2;
   SPLAT_LAUNCH("render_bwd_kernel", s,
-               render_bwd_kernel<256><<<v.cam.tiles_x * v.cam.tiles_y, kBwdThreads, 0, s>>>(v));
+               render_bwd_kernel<256, kBwdSinglePPT><<<v.cam.tiles_x * v.cam.tiles_y, kTilePixels / kBwdSinglePPT, 0, s>>>(v));
   if ((rc = check_launch("render_bwd_kernel"))) return rc;
   GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
   GradK gr{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};
