@@ -14,8 +14,8 @@
 // summed by one CTA in a shared-memory hash table (weights added) and only
 // the distinct keys are sorted; a bucket with more distinct keys than the
 // table holds uses a hash table in global memory instead.  The distinct pairs
-// are written at the offsets of an exclusive scan over the buckets.  Six
-// kernels.
+// are written at the offsets of an exclusive scan over the buckets.  Four
+// kernels (the scans are folded into the kernels that need them).
 #include <algorithm>
 
 #include "common.cuh"
@@ -115,32 +115,30 @@ __global__ void __launch_bounds__(kAsThreads) assoc_count_kernel(const int32_t* 
     if (s_cnt[b]) atomicAdd(&bcnt[(size_t)b * kAsStride], s_cnt[b]);
 }
 
-// One CTA: bucket starts (exclusive scan) and cursors.
-__global__ void __launch_bounds__(1024) assoc_scan_kernel(const uint32_t* __restrict__ bcnt, int nb,
-                                                          uint32_t* __restrict__ bstart,
-                                                          uint32_t* __restrict__ cursor) {
-  __shared__ uint32_t sh[33];
-  uint32_t carry = 0;
-  for (int base = 0; base < nb; base += 1024) {
-    const int b = base + threadIdx.x;
-    const uint32_t c = b < nb ? bcnt[(size_t)b * kAsStride] : 0u;
-    uint32_t excl;
-    const uint32_t tot = block_excl_scan<1024>(c, excl, sh);
-    if (b < nb) {
-      bstart[b] = carry + excl;
-      cursor[(size_t)b * kAsStride] = carry + excl;
-    }
-    carry += tot;
-  }
-  if (threadIdx.x == 0) bstart[nb] = carry;
-}
-
 __global__ void __launch_bounds__(kAsThreads) assoc_scatter_kernel(
     const int32_t* __restrict__ ia, const float* __restrict__ ta, const int32_t* __restrict__ ib,
     const float* __restrict__ tb, int64_t npix, float tmax, int64_t n_a, int nb, bool vec,
-    uint32_t* __restrict__ cursor, uint64_t* __restrict__ skeys, uint32_t* __restrict__ sw) {
+    const uint32_t* __restrict__ bcnt, uint32_t* __restrict__ cursor, uint32_t* __restrict__ bstart,
+    uint64_t* __restrict__ skeys, uint32_t* __restrict__ sw) {
   __shared__ uint32_t s_cnt[kAsMaxBuckets];
-  __shared__ uint32_t s_base[kAsMaxBuckets];
+  __shared__ uint32_t s_base[kAsMaxBuckets];  // bucket starts, then this CTA's reserved positions
+  __shared__ uint32_t sh[33];
+  // bucket starts: exclusive scan of the bucket counts (every CTA computes it;
+  // CTA 0 also publishes it, with the total, for the per-bucket kernel)
+  {
+    const int per = (nb + kAsThreads - 1) / kAsThreads;
+    const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
+    uint32_t loc = 0;
+    for (int b = b0; b < b1; ++b) loc += bcnt[(size_t)b * kAsStride];
+    uint32_t excl;
+    const uint32_t tot = block_excl_scan<kAsThreads>(loc, excl, sh);
+    for (int b = b0; b < b1; ++b) {
+      s_base[b] = excl;
+      if (blockIdx.x == 0) bstart[b] = excl;
+      excl += bcnt[(size_t)b * kAsStride];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) bstart[nb] = tot;
+  }
   for (int b = threadIdx.x; b < nb; b += kAsThreads) s_cnt[b] = 0u;
   __syncthreads();
   int64_t p0, p1;
@@ -149,9 +147,9 @@ __global__ void __launch_bounds__(kAsThreads) assoc_scatter_kernel(
     atomicAdd(&s_cnt[assoc_bucket((int32_t)(key >> 32), n_a, nb)], 1u);
   });
   __syncthreads();
-  for (int b = threadIdx.x; b < nb; b += kAsThreads) {
+  for (int b = threadIdx.x; b < nb; b += kAsThreads) {  // cursors count from 0 within each bucket
     const uint32_t c = s_cnt[b];
-    s_base[b] = c ? atomicAdd(&cursor[(size_t)b * kAsStride], c) : 0u;
+    if (c) s_base[b] += atomicAdd(&cursor[(size_t)b * kAsStride], c);
     s_cnt[b] = 0u;
   }
   __syncthreads();
@@ -296,35 +294,32 @@ __global__ void __launch_bounds__(kAsThreads) assoc_sort_rle_kernel(const uint32
   if (threadIdx.x == 0) nuniq[b] = (uint32_t)nd;
 }
 
-__global__ void __launch_bounds__(1024) assoc_offsets_kernel(const uint32_t* __restrict__ nuniq, int nb,
-                                                             uint32_t* __restrict__ uoff, int64_t capacity,
-                                                             int64_t* __restrict__ m_dev,
-                                                             int32_t* __restrict__ status) {
-  __shared__ uint32_t sh[33];
-  uint32_t carry = 0;
-  for (int base = 0; base < nb; base += 1024) {
-    const int b = base + threadIdx.x;
-    const uint32_t c = b < nb ? nuniq[b] : 0u;
-    uint32_t excl;
-    const uint32_t tot = block_excl_scan<1024>(c, excl, sh);
-    if (b < nb) uoff[b] = carry + excl;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) {
-    *m_dev = (int64_t)carry;
-    if ((int64_t)carry > capacity) raise_status(status, SPLAT_ECAPACITY);
-  }
-}
-
+// One CTA per bucket: its distinct pairs go to the output at the sum of the
+// distinct counts of the buckets before it; the last bucket's CTA writes M
+// and raises SPLAT_ECAPACITY when M exceeds the capacity.
 __global__ void __launch_bounds__(kAsThreads) assoc_write_kernel(const uint32_t* __restrict__ bstart,
-                                                                 const uint32_t* __restrict__ nuniq,
-                                                                 const uint32_t* __restrict__ uoff,
+                                                                 const uint32_t* __restrict__ nuniq, int nb,
                                                                  const uint64_t* __restrict__ ukeys,
                                                                  const uint32_t* __restrict__ ucnt, int64_t capacity,
                                                                  int32_t* __restrict__ pairs,
-                                                                 int32_t* __restrict__ counts) {
+                                                                 int32_t* __restrict__ counts,
+                                                                 int64_t* __restrict__ m_dev,
+                                                                 int32_t* __restrict__ status) {
+  __shared__ unsigned long long red[kAsThreads / 32];
   const int b = blockIdx.x;
-  const uint32_t s0 = bstart[b], nu = nuniq[b], o0 = uoff[b];
+  unsigned long long part = 0;
+  for (int k = threadIdx.x; k < b; k += kAsThreads) part += nuniq[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+  __syncthreads();
+  unsigned long long o0 = 0;
+  for (int w = 0; w < kAsThreads / 32; ++w) o0 += red[w];
+  const uint32_t s0 = bstart[b], nu = nuniq[b];
+  if (b == nb - 1 && threadIdx.x == 0) {
+    *m_dev = (int64_t)(o0 + nu);
+    if ((int64_t)(o0 + nu) > capacity) raise_status(status, SPLAT_ECAPACITY);
+  }
   for (uint32_t u = threadIdx.x; u < nu; u += kAsThreads) {
     const int64_t o = (int64_t)o0 + u;
     if (o >= capacity) break;
@@ -336,7 +331,7 @@ __global__ void __launch_bounds__(kAsThreads) assoc_write_kernel(const uint32_t*
 }
 
 struct AssocWs {
-  uint32_t *bcnt, *cursor, *bstart, *nuniq, *uoff, *ucnt, *sw, *gcnt;
+  uint32_t *bcnt, *cursor, *bstart, *nuniq, *ucnt, *sw, *gcnt;
   uint64_t *skeys, *skeys2, *skeys3, *ukeys, *gkey;
 };
 
@@ -359,7 +354,6 @@ static size_t carve_assoc(int64_t npix, char* base, AssocWs* w) {
   t.cursor = (uint32_t*)take(4 * kAsStride * nb);
   t.bstart = (uint32_t*)take(4 * (nb + 1));
   t.nuniq = (uint32_t*)take(4 * nb);
-  t.uoff = (uint32_t*)take(4 * nb);
   t.ucnt = (uint32_t*)take(4 * n);
   t.sw = (uint32_t*)take(4 * n);
   t.gcnt = (uint32_t*)take(4 * 2 * n);
@@ -395,8 +389,9 @@ extern "C" int splat_assoc(const int32_t* id_a, const float* t_a, const int32_t*
   AssocWs w;
   carve_assoc(npix, static_cast<char*>(ws), &w);
   const int nb = assoc_buckets(npix);
-  if (cudaMemsetAsync(w.bcnt, 0, sizeof(uint32_t) * kAsStride * nb, s) != cudaSuccess)
-    return fail(SPLAT_ECUDA, "splat_assoc: memset failed");
+  // bucket counts and cursors are adjacent in the workspace: one memset
+  const size_t zero_bytes = (size_t)((char*)(w.cursor + (size_t)kAsStride * nb) - (char*)w.bcnt);
+  if (cudaMemsetAsync(w.bcnt, 0, zero_bytes, s) != cudaSuccess) return fail(SPLAT_ECUDA, "splat_assoc: memset failed");
   int sms = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((npix + 1023) / 1024, 2 * sms));
@@ -404,19 +399,14 @@ extern "C" int splat_assoc(const int32_t* id_a, const float* t_a, const int32_t*
   SPLAT_LAUNCH("assoc_count_kernel", s,
                assoc_count_kernel<<<grid, kAsThreads, 0, s>>>(id_a, t_a, id_b, t_b, npix, t_max, n_a, nb, vec,
                                                               w.bcnt));
-  SPLAT_LAUNCH("assoc_scan_kernel", s, assoc_scan_kernel<<<1, 1024, 0, s>>>(w.bcnt, nb, w.bstart, w.cursor));
   SPLAT_LAUNCH("assoc_scatter_kernel", s,
                assoc_scatter_kernel<<<grid, kAsThreads, 0, s>>>(id_a, t_a, id_b, t_b, npix, t_max, n_a, nb, vec,
-                                                                w.cursor, w.skeys, w.sw));
+                                                                w.bcnt, w.cursor, w.bstart, w.skeys, w.sw));
   SPLAT_LAUNCH("assoc_sort_rle_kernel", s,
                assoc_sort_rle_kernel<<<nb, kAsThreads, 0, s>>>(w.bstart, w.skeys, w.sw, w.skeys2, w.skeys3, w.gkey,
                                                                 w.gcnt, w.ukeys, w.ucnt, w.nuniq));
-  SPLAT_LAUNCH("assoc_offsets_kernel", s,
-               assoc_offsets_kernel<<<1, 1024, 0, s>>>(w.nuniq, nb, w.uoff, capacity, m_dev, status));
-  int rc = check_launch("assoc_offsets_kernel");
-  if (rc || capacity == 0) return rc;
   SPLAT_LAUNCH("assoc_write_kernel", s,
-               assoc_write_kernel<<<nb, kAsThreads, 0, s>>>(w.bstart, w.nuniq, w.uoff, w.ukeys, w.ucnt, capacity,
-                                                            pairs, counts));
+               assoc_write_kernel<<<nb, kAsThreads, 0, s>>>(w.bstart, w.nuniq, nb, w.ukeys, w.ucnt, capacity, pairs,
+                                                            counts, m_dev, status));
   return check_launch("assoc_write_kernel");
 }
