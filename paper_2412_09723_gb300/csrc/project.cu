@@ -41,6 +41,16 @@ __device__ __forceinline__ void project_math(const float* __restrict__ mean,
                                              const float* W, const CamK& cam, ProjMath& m) {
   m.visible = false;
   m.tiles = 0;
+  // camera transform and the near / distance culls first: a culled Gaussian
+  // needs none of the activation below (the results are the same either way)
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    m.p[i] = ((W[4 * i] * mean[0] + W[4 * i + 1] * mean[1]) + W[4 * i + 2] * mean[2]) + W[4 * i + 3];
+  if (!(m.p[2] > cam.znear)) return;
+  if (cam.maxd2 > 0.f &&
+      __fadd_rn(__fadd_rn(__fmul_rn(m.p[0], m.p[0]), __fmul_rn(m.p[1], m.p[1])), __fmul_rn(m.p[2], m.p[2])) >
+          cam.maxd2)
+    return;  // outside the selection distance
   for (int k = 0; k < 3; ++k) m.s[k] = exp_full(log_scale[k]);
   const float4 q = *reinterpret_cast<const float4*>(quat);
   const float n2 = ((q.x * q.x + q.y * q.y) + q.z * q.z) + q.w * q.w;
@@ -72,14 +82,7 @@ __device__ __forceinline__ void project_math(const float* __restrict__ mean,
     for (int j = 0; j < 3; ++j)
       m.Sig[3 * i + j] = (m.M[3 * i] * m.M[3 * j] + m.M[3 * i + 1] * m.M[3 * j + 1]) +
                          m.M[3 * i + 2] * m.M[3 * j + 2];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-    m.p[i] = ((W[4 * i] * mean[0] + W[4 * i + 1] * mean[1]) + W[4 * i + 2] * mean[2]) + W[4 * i + 3];
   const float z = m.p[2];
-  if (!(z > cam.znear)) return;
-  if (cam.maxd2 > 0.f &&
-      __fadd_rn(__fadd_rn(__fmul_rn(m.p[0], m.p[0]), __fmul_rn(m.p[1], m.p[1])), __fmul_rn(z, z)) > cam.maxd2)
-    return;  // outside the selection distance
   const float lim_x = kClip * ((float)cam.width / (2.0f * cam.fx));
   const float lim_y = kClip * ((float)cam.height / (2.0f * cam.fy));
   const float txz = m.p[0] / z;
