@@ -437,9 +437,7 @@ __global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(
 // (chunks of kSegCap keys, merged in global memory above that).  Dynamic
 // shared memory: two key buffers of kSegCap, 8 x 256 digit counters, scan
 // scratch.
-// CAP keys per shared-memory sort: kSegCap, or half of it when the average
-// bucket is small (so that more CTAs fit on an SM; longer buckets still sort
-// correctly through the merge path).
+// Shared memory of a tile sort with CAP keys per shared-memory pass.
 template <int CAP>
 constexpr size_t sort_smem_bytes() {
   return 2 * sizeof(uint64_t) * CAP + sizeof(uint32_t) * (kSegRadixWarps * 256 + 64);
@@ -595,22 +593,13 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(sort_attr_done.load() & bit)) {
       if (cudaFuncSetAttribute(tile_sort_kernel<kSegCap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sort_smem_bytes<kSegCap>()) != cudaSuccess ||
-          cudaFuncSetAttribute(tile_sort_kernel<kSegCap / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sort_smem_bytes<kSegCap / 2>()) != cudaSuccess)
+                               (int)sort_smem_bytes<kSegCap>()) != cudaSuccess)
         return fail(SPLAT_ECUDA, "splat_bin_sort: cannot enable shared memory for the tile sort");
       sort_attr_done.fetch_or(bit);
     }
   }
-  // the duplicate capacity bounds K, so capacity / n_tiles bounds the average bucket
-  if (capacity <= (int64_t)n_tiles * (kSegCap / 2)) {
-    SPLAT_LAUNCH("tile_sort_kernel", s,
-                 tile_sort_kernel<kSegCap / 2><<<(unsigned)n_tiles, kSortThreads, sort_smem_bytes<kSegCap / 2>(), s>>>(
-                     reinterpret_cast<const uint2*>(ranges), w.skeys, w.skeys2, vals, keys));
-  } else {
-    SPLAT_LAUNCH("tile_sort_kernel", s,
-                 tile_sort_kernel<kSegCap><<<(unsigned)n_tiles, kSortThreads, sort_smem_bytes<kSegCap>(), s>>>(
-                     reinterpret_cast<const uint2*>(ranges), w.skeys, w.skeys2, vals, keys));
-  }
+  SPLAT_LAUNCH("tile_sort_kernel", s,
+               tile_sort_kernel<kSegCap><<<(unsigned)n_tiles, kSortThreads, sort_smem_bytes<kSegCap>(), s>>>(
+                   reinterpret_cast<const uint2*>(ranges), w.skeys, w.skeys2, vals, keys));
   return check_launch("tile_sort_kernel");
 }

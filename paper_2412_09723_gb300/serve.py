@@ -67,6 +67,9 @@ class _AgentSlot:
         self.footprint = 0  # device bytes when resident (last measured)
         self.last_used = 0.0
         self.busy = False
+        # pinned result buffers (an agent has at most one request in flight)
+        self.out_loss = torch.empty(1, dtype=torch.float32, pin_memory=True)
+        self.out_w2c = torch.empty(4, 4, dtype=torch.float32, pin_memory=True)
 
 
 def _agent_bytes(a: Agent) -> int:
@@ -242,12 +245,11 @@ class Server:
             s.wait_stream(st)
         outs = []
         with torch.cuda.stream(s):
-            for a in agents:
-                loss = torch.empty(1, dtype=torch.float32, pin_memory=True)
-                w2c = torch.empty(4, 4, dtype=torch.float32, pin_memory=True)
-                loss.copy_(a.loss, non_blocking=True)
-                w2c.copy_(a.w2c, non_blocking=True)
-                outs.append((loss, w2c))
+            for r, a in zip(reqs, agents):
+                slot = self.slots[r.agent]
+                slot.out_loss.copy_(a.loss, non_blocking=True)
+                slot.out_w2c.copy_(a.w2c, non_blocking=True)
+                outs.append((slot.out_loss, slot.out_w2c))
         ev = torch.cuda.Event()
         ev.record(s)
         return ev, outs
