@@ -34,6 +34,7 @@ constexpr int kSsT = 16;                  // output block side
 constexpr int kSsR = 5;                   // window radius
 constexpr int kSsP = kSsT + 2 * kSsR;     // staged patch side (26)
 constexpr int kSsTaps = 2 * kSsR + 1;     // 11
+constexpr int kSsLd = 48;                 // shared row stride: two rows of a warp fall in different banks
 constexpr float kSsC1 = 0.01f * 0.01f;
 constexpr float kSsC2 = 0.03f * 0.03f;
 
@@ -67,47 +68,55 @@ __device__ __forceinline__ float block_sum_256(float v, float* red /*[8]*/) {
   return t;  // valid in thread 0
 }
 
-// Stage the 26 x 26 patch of channel ch of an interleaved [H, W, 3] image
-// (zero outside the image).
-__device__ __forceinline__ void stage_patch(const float* __restrict__ img, int H, int W, int ch, int x0, int y0,
-                                            float (*dst)[kSsP]) {
+// Stage the 26 x 26 patch at (x0, y0) of an image with pixel stride `ps`
+// (3 for channel ch of an interleaved [H, W, 3] image, 1 for a plane), zero
+// outside the image.
+__device__ __forceinline__ void stage_patch(const float* __restrict__ img, int H, int W, int ps, int x0, int y0,
+                                            float (*dst)[kSsLd]) {
   for (int i = threadIdx.x; i < kSsP * kSsP; i += 256) {
     const int r = i / kSsP, c = i - r * kSsP;
     const int gy = y0 + r, gx = x0 + c;
     const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-    dst[r][c] = in ? img[((size_t)gy * W + gx) * 3 + ch] : 0.f;
+    dst[r][c] = in ? img[((size_t)gy * W + gx) * ps] : 0.f;
   }
 }
 
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                                        int H, int W, SsimWin win, float loss_scale, float ssim_scale,
                                                        float* __restrict__ abc, float* __restrict__ loss) {
-  __shared__ float sx[kSsP][kSsP], sy[kSsP][kSsP];
-  __shared__ float hs[5][kSsP][kSsT + 1];
+  __shared__ float sx[kSsP][kSsLd], sy[kSsP][kSsLd];
+  __shared__ float hs[5][kSsP][kSsLd];
   __shared__ float red[8];
   const int ch = blockIdx.z;
   const int bx = blockIdx.x * kSsT, by = blockIdx.y * kSsT;
-  stage_patch(x, H, W, ch, bx - kSsR, by - kSsR, sx);
-  stage_patch(y, H, W, ch, bx - kSsR, by - kSsR, sy);
+  stage_patch(x + ch, H, W, 3, bx - kSsR, by - kSsR, sx);
+  stage_patch(y + ch, H, W, 3, bx - kSsR, by - kSsR, sy);
   __syncthreads();
-  for (int i = threadIdx.x; i < kSsP * kSsT; i += 256) {  // horizontal pass over all 26 rows
-    const int r = i / kSsT, c = i - r * kSsT;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+  if (threadIdx.x < kSsP * kSsT / 2) {  // horizontal pass over all 26 rows, two columns per thread
+    const int r = threadIdx.x / (kSsT / 2), c = 2 * (threadIdx.x % (kSsT / 2));
+    float a[2][5] = {};
+    float u = sx[r][c], v = sy[r][c];
 #pragma unroll
     for (int k = 0; k < kSsTaps; ++k) {
-      const float u = sx[r][c + k], v = sy[r][c + k], w = win.w[k];
-      const float wu = w * u, wv = w * v;
-      a0 += wu;
-      a1 += wv;
-      a2 = fmaf(wu, u, a2);
-      a3 = fmaf(wv, v, a3);
-      a4 = fmaf(wu, v, a4);
+      const float u1 = sx[r][c + k + 1], v1 = sy[r][c + k + 1], w = win.w[k];
+#pragma unroll
+      for (int o = 0; o < 2; ++o) {
+        const float uu = o ? u1 : u, vv = o ? v1 : v;
+        const float wu = w * uu, wv = w * vv;
+        a[o][0] += wu;
+        a[o][1] += wv;
+        a[o][2] = fmaf(wu, uu, a[o][2]);
+        a[o][3] = fmaf(wv, vv, a[o][3]);
+        a[o][4] = fmaf(wu, vv, a[o][4]);
+      }
+      u = u1;
+      v = v1;
     }
-    hs[0][r][c] = a0;
-    hs[1][r][c] = a1;
-    hs[2][r][c] = a2;
-    hs[3][r][c] = a3;
-    hs[4][r][c] = a4;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      hs[q][r][c] = a[0][q];
+      hs[q][r][c + 1] = a[1][q];
+    }
   }
   __syncthreads();
   const int tx = threadIdx.x & (kSsT - 1), ty = threadIdx.x / kSsT;
@@ -130,11 +139,12 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
     const float A = (2.f * my * (b - a)) / cd - s * (2.f * mx / c - 2.f * mx / d);
     const float Bm = -s / d;
     const float Cm = 2.f * a / cd;
-    const size_t i = ((size_t)gy * W + gx) * 3 + ch;
-    const size_t plane = (size_t)H * W * 3;
+    // planar layout [map][channel][H][W], so the adjoint stages contiguous rows
+    const size_t plane = (size_t)H * W;
+    const size_t i = (size_t)ch * plane + (size_t)gy * W + gx;
     abc[i] = A;
-    abc[plane + i] = Bm;
-    abc[2 * plane + i] = Cm;
+    abc[3 * plane + i] = Bm;
+    abc[6 * plane + i] = Cm;
     one_minus_s = 1.f - s;
   }
   const float t0 = block_sum_256(one_minus_s, red);
@@ -149,27 +159,30 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                                        int H, int W, SsimWin win, float grad_scale,
                                                        const float* __restrict__ abc, float* __restrict__ d_rgb) {
-  __shared__ float sp[3][kSsP][kSsP];
-  __shared__ float hs[3][kSsP][kSsT + 1];
+  __shared__ float sp[3][kSsP][kSsLd];
+  __shared__ float hs[3][kSsP][kSsLd];
   const int ch = blockIdx.z;
   const int bx = blockIdx.x * kSsT, by = blockIdx.y * kSsT;
-  const size_t plane = (size_t)H * W * 3;
+  const size_t plane = (size_t)H * W;
 #pragma unroll
-  for (int q = 0; q < 3; ++q) stage_patch(abc + q * plane, H, W, ch, bx - kSsR, by - kSsR, sp[q]);
+  for (int q = 0; q < 3; ++q) stage_patch(abc + (3 * q + ch) * plane, H, W, 1, bx - kSsR, by - kSsR, sp[q]);
   __syncthreads();
-  for (int i = threadIdx.x; i < kSsP * kSsT; i += 256) {
-    const int r = i / kSsT, c = i - r * kSsT;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+  if (threadIdx.x < kSsP * kSsT / 2) {  // two columns per thread
+    const int r = threadIdx.x / (kSsT / 2), c = 2 * (threadIdx.x % (kSsT / 2));
 #pragma unroll
-    for (int k = 0; k < kSsTaps; ++k) {
-      const float w = win.w[k];
-      a0 = fmaf(w, sp[0][r][c + k], a0);
-      a1 = fmaf(w, sp[1][r][c + k], a1);
-      a2 = fmaf(w, sp[2][r][c + k], a2);
+    for (int q = 0; q < 3; ++q) {
+      float a0 = 0.f, a1 = 0.f;
+      float prev = sp[q][r][c];
+#pragma unroll
+      for (int k = 0; k < kSsTaps; ++k) {
+        const float w = win.w[k], next = sp[q][r][c + k + 1];
+        a0 = fmaf(w, prev, a0);
+        a1 = fmaf(w, next, a1);
+        prev = next;
+      }
+      hs[q][r][c] = a0;
+      hs[q][r][c + 1] = a1;
     }
-    hs[0][r][c] = a0;
-    hs[1][r][c] = a1;
-    hs[2][r][c] = a2;
   }
   __syncthreads();
   const int tx = threadIdx.x & (kSsT - 1), ty = threadIdx.x / kSsT;
