@@ -34,7 +34,10 @@ constexpr float kPowerCutMargin = 1e-3f;
 // polynomial in Horner form with fused multiply-adds, 2^k from exponent bits.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ float exp_core(float x) {  // x in [-87, 88]
-  const float k = rintf(__fmul_rn(x, 1.44269502f));
+  // k = rint(x log2 e): adding 1.5 * 2^23 rounds to an integer (to nearest,
+  // ties to even) and leaves k in the low mantissa bits
+  const float t = __fadd_rn(__fmul_rn(x, 1.44269502f), 12582912.0f);
+  const float k = __fsub_rn(t, 12582912.0f);
   float r = __fmaf_rn(-k, 0.693145751953125f, x);
   r = __fmaf_rn(-k, 1.42860677e-06f, r);
   float p = 1.98412701e-04f;
@@ -45,7 +48,7 @@ __device__ __forceinline__ float exp_core(float x) {  // x in [-87, 88]
   p = __fmaf_rn(p, r, 0.5f);
   p = __fmaf_rn(p, r, 1.0f);
   p = __fmaf_rn(p, r, 1.0f);
-  const int ki = __float2int_rz(k);
+  const int ki = __float_as_int(t) - 0x4B400000;
   return __fmul_rn(p, __int_as_float((ki + 127) << 23));
 }
 

@@ -80,8 +80,7 @@ constexpr int kMaxWarps = 8;  // warps of a tile CTA (forward 8 of 2 rows, backw
 struct StagePtrs {
   float4* xyzo;
   float4* quad;
-  float* rgb;
-  int32_t* id;
+  float4* cid;
   uint8_t* wmask;
 };
 
@@ -89,8 +88,7 @@ template <int BATCH>
 struct Stage {
   float4 xyzo[BATCH];
   float4 quad[BATCH];  // A = -a/2, B = -b, C = -c/2, exponent cut
-  float rgb[3 * BATCH];
-  int32_t id[BATCH];
+  float4 cid[BATCH];   // colour r, g, b and the Gaussian's id (bits of .w)
   uint8_t wmask[BATCH];              // warps whose pixel rows the Gaussian can reach
   uint8_t wlist[kMaxWarps][BATCH];   // per warp: the staged positions it visits, ascending
 };
@@ -163,12 +161,10 @@ __device__ __forceinline__ void stage_one(const ViewK& V, uint32_t g, int i, Sta
                                           int rows_per_warp) {
   const float4 co = V.conic[g];
   const float4 xo = V.xyzo[g];
-  p.id[i] = (int32_t)g;
   p.xyzo[i] = xo;
   p.quad[i] = make_float4(-0.5f * co.x, -co.y, -0.5f * co.z, co.w);
-  p.rgb[3 * i + 0] = V.rgb[3 * (size_t)g + 0];
-  p.rgb[3 * i + 1] = V.rgb[3 * (size_t)g + 1];
-  p.rgb[3 * i + 2] = V.rgb[3 * (size_t)g + 2];
+  p.cid[i] = make_float4(V.rgb[3 * (size_t)g + 0], V.rgb[3 * (size_t)g + 1], V.rgb[3 * (size_t)g + 2],
+                         __int_as_float((int32_t)g));
   p.wmask[i] = warp_mask<EXACT>(xo, co, tx0, ty0, rows_per_warp);
 }
 
@@ -200,7 +196,7 @@ struct FwdPix {
 
 // One front-to-back compositing step of one pixel (the specified order).
 __device__ __forceinline__ void composite_step(FwdPix& q, const float4 xo, const float4 qd, float fx, float fy,
-                                               const float* c, int32_t gid, int32_t pos) {
+                                               const float4* cidp, int32_t pos) {
   const float dx = xo.x - fx;
   const float dy = xo.y - fy;
   const float power = __fmaf_rn(qd.z * dy, dy, dx * __fmaf_rn(qd.x, dx, qd.y * dy));
@@ -214,14 +210,15 @@ __device__ __forceinline__ void composite_step(FwdPix& q, const float4 xo, const
     return;
   }
   const float w = alpha * q.T;
-  q.C0 = __fmaf_rn(c[0], w, q.C0);
-  q.C1 = __fmaf_rn(c[1], w, q.C1);
-  q.C2 = __fmaf_rn(c[2], w, q.C2);
+  const float4 c = *cidp;
+  q.C0 = __fmaf_rn(c.x, w, q.C0);
+  q.C1 = __fmaf_rn(c.y, w, q.C1);
+  q.C2 = __fmaf_rn(c.z, w, q.C2);
   q.D = __fmaf_rn(xo.z, w, q.D);
   q.S = q.S + w;
   if (w > q.wmax) {
     q.wmax = w;
-    q.id = gid;
+    q.id = __float_as_int(c.w);
   }
   q.T = test_T;
   q.last = pos + 1;
@@ -239,7 +236,7 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
   FwdPix q{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, 0, 0, !inside};
   const uint2 rg = V.ranges[tile];
   const int warp = threadIdx.x >> 5;
-  const StagePtrs sp{sm.xyzo, sm.quad, sm.rgb, sm.id, sm.wmask};
+  const StagePtrs sp{sm.xyzo, sm.quad, sm.cid, sm.wmask};
   for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
     if (__syncthreads_count(q.done) == kFwdThreads) break;
     if (threadIdx.x < BATCH && start + threadIdx.x < rg.y)
@@ -250,7 +247,7 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
     const int nl = build_warp_list(sm.wmask, sm.wlist[warp], cnt, warp);
     for (int e = 0; e < nl && !q.done; ++e) {
       const int j = sm.wlist[warp][e];
-      composite_step(q, sm.xyzo[j], sm.quad[j], fx, fy, &sm.rgb[3 * j], sm.id[j], base + j);
+      composite_step(q, sm.xyzo[j], sm.quad[j], fx, fy, &sm.cid[j], base + j);
     }
   }
   if (!inside) return;
@@ -430,7 +427,7 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
     b.Q = (b.gC0 * V.bg0 + b.gC1 * V.bg1 + b.gC2 * V.bg2) * Tfin;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const StagePtrs sp{sm.st.xyzo, sm.st.quad, sm.st.rgb, sm.st.id, sm.st.wmask};
+  const StagePtrs sp{sm.st.xyzo, sm.st.quad, sm.st.cid, sm.st.wmask};
   int mylast = 0;
 #pragma unroll
   for (int p = 0; p < PPT; ++p) mylast = max(mylast, q[p].last);
@@ -455,7 +452,8 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
       if (pos >= wlast) continue;  // warp-uniform: no pixel of this warp reaches pos
       const float4 xo = sm.st.xyzo[j];
       const float4 qd = sm.st.quad[j];
-      const float c0 = sm.st.rgb[3 * j + 0], c1 = sm.st.rgb[3 * j + 1], c2 = sm.st.rgb[3 * j + 2];
+      const float4 cd = sm.st.cid[j];
+      const float c0 = cd.x, c1 = cd.y, c2 = cd.z;
       float v[10];
 #pragma unroll
       for (int k = 0; k < 10; ++k) v[k] = 0.f;
@@ -477,7 +475,7 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
       const float4 u0 = make_float4(-(ca * a[0] + cb * a[1]), -(cb * a[0] + cc * a[1]), -0.5f * a[2], -a[3]);
       const float4 u1 = make_float4(-0.5f * a[4], a[5], a[6], a[7]);
       const float4 u2 = make_float4(a[8], a[9], 0.f, 0.f);
-      float4* dst = reinterpret_cast<float4*>(V.g2 + kGradStride * (size_t)sm.st.id[i]);
+      float4* dst = reinterpret_cast<float4*>(V.g2 + kGradStride * (size_t)__float_as_int(sm.st.cid[i].w));
       if (u0.x != 0.f || u0.y != 0.f || u0.z != 0.f || u0.w != 0.f) atomicAdd(dst, u0);
       if (u1.x != 0.f || u1.y != 0.f || u1.z != 0.f || u1.w != 0.f) atomicAdd(dst + 1, u1);
       if (u2.x != 0.f || u2.y != 0.f) atomicAdd(dst + 2, u2);
