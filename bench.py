@@ -737,7 +737,7 @@ def main():
             between_steps(k)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            agent.set_observation(h_rgb.to(dev, non_blocking=True), h_depth.to(dev, non_blocking=True))
+            agent.set_observation(h_rgb, h_depth)  # pinned host -> resident observation buffers
             run_step()
             h_loss.copy_(agent.loss, non_blocking=True)
             h_pose.copy_(agent.w2c, non_blocking=True)

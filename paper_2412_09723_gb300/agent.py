@@ -58,7 +58,9 @@ class Agent:
         self.m = [torch.zeros_like(p) for p in self.params]
         self.v = [torch.zeros_like(p) for p in self.params]
         self.w2c = torch.as_tensor(w2c, dtype=torch.float32, device=device).contiguous().clone()
-        self.d_pose = torch.zeros(6, dtype=torch.float32, device=device)
+        # per-step accumulators in one block, cleared by one launch: d_pose [6], loss [1], association status [1]
+        self._acc = torch.zeros(8, dtype=torch.float32, device=device)
+        self.d_pose = self._acc[0:6]
         self.pose_m = torch.zeros(6, dtype=torch.float32, device=device)
         self.pose_v = torch.zeros(6, dtype=torch.float32, device=device)
         self.fb = FrameBuffers(self.n, cam, device, capacity=capacity, want_used=want_used)
@@ -69,13 +71,13 @@ class Agent:
         self.obs_tfinal = torch.ones(H, W, dtype=torch.float32, device=device)
         self.g_rgb = torch.zeros(H, W, 3, dtype=torch.float32, device=device)
         self.g_depth = torch.zeros(H, W, dtype=torch.float32, device=device)
-        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.loss = self._acc[6:7]
         npix = cam.npix
         self.assoc_cap = npix
         self.pairs = torch.zeros(npix, 2, dtype=torch.int32, device=device)
         self.counts = torch.zeros(npix, dtype=torch.int32, device=device)
         self.m_dev = torch.zeros(1, dtype=torch.int64, device=device)
-        self.assoc_status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.assoc_status = self._acc[7:8].view(torch.int32)
         self.assoc_ws = torch.empty(max(1, B.splat_assoc_workspace_size(npix)), dtype=torch.uint8, device=device)
         self.cg = B.gaussians_struct(*self.params)
         self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads))
@@ -138,8 +140,7 @@ class Agent:
     def phase_loss(self, s):
         cfg, fb = self.cfg, self.fb
         with torch.cuda.stream(s):
-            self.loss.zero_()
-            self.d_pose.zero_()
+            self._acc.zero_()  # d_pose, loss and the association status
             if not self.grads_clean:  # the fused Adam step leaves them cleared when mapping
                 for g in self.grads:
                     g.zero_()
@@ -171,9 +172,7 @@ class Agent:
         if cfg.track:
             B.splat_pose_step(self.w2c, self.d_pose, self.pose_m, self.pose_v, t, cfg.pose_lr[0], cfg.pose_lr[1],
                               stream=s)
-        if cfg.assoc:
-            with torch.cuda.stream(s):
-                self.assoc_status.zero_()
+        if cfg.assoc:  # the status word was cleared with the other accumulators in phase_loss
             B.splat_assoc(fb.image["max_id"], fb.image["t_final"], self.obs_id, self.obs_tfinal, self.n, self.n,
                           cfg.t_max, self.pairs, self.counts, self.assoc_cap, self.m_dev, self.assoc_status,
                           self.assoc_ws, s)
