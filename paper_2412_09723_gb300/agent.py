@@ -257,23 +257,41 @@ class Agent:
                 dst.copy_(src, non_blocking=True)
 
     # -- CUDA graph -------------------------------------------------------------
-    def capture(self):
+    def capture(self, keep_state: bool = False):
         """Capture one step into a CUDA graph.  All buffers are fixed (size the
         duplicate capacity first); replaying the graph performs exactly the
-        kernels of `step()` with no host work.  Returns the number of library
-        kernel launches one replay performs."""
+        kernels of `step()` with no host work.  The capture is preceded by one
+        eager warm-up step; with `keep_state` the map, optimiser state and pose
+        are put back after it, so that capturing changes nothing.  Returns the
+        number of library kernel launches one replay performs."""
+        saved = [t.clone() for t in self._state()] if keep_state else None
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):  # warm-up on the capture stream's side
             self.step(stream=s)
         torch.cuda.current_stream().wait_stream(s)
         torch.cuda.synchronize()
+        if saved is not None:
+            for dst, src in zip(self._state(), saved):
+                dst.copy_(src)
+            torch.cuda.synchronize()
+            del saved
+            self.steps_done -= 1
+            self.grads_clean = False  # the graph clears the gradients itself, whatever ran before it
         g = torch.cuda.CUDAGraph()
         n0 = B.splat_kernel_launches()
         with torch.cuda.graph(g):
             self.step()
         self.launches_per_step = B.splat_kernel_launches() - n0
         self.graph = g
+        if keep_state:  # one replay (the first launch of a graph is the slow one), then the state put back
+            saved = [t.clone() for t in self._state()]
+            g.replay()
+            torch.cuda.synchronize()
+            for dst, src in zip(self._state(), saved):
+                dst.copy_(src)
+            torch.cuda.synchronize()
+            del saved
         return self.launches_per_step
 
     def replay(self):

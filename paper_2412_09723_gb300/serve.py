@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import statistics
 import time
 
@@ -70,6 +71,7 @@ class _AgentSlot:
         # pinned result buffers (an agent has at most one request in flight)
         self.out_loss = torch.empty(1, dtype=torch.float32, pin_memory=True)
         self.out_w2c = torch.empty(4, 4, dtype=torch.float32, pin_memory=True)
+        self.graphs = {}  # request kind -> captured single-agent step of the resident agent
 
 
 def _agent_bytes(a: Agent) -> int:
@@ -99,8 +101,9 @@ def _agent_bytes(a: Agent) -> int:
 
 class Server:
     def __init__(self, device, hbm_budget_bytes: int, max_batch: int = 8, n_streams: int = 2,
-                 shape=(256, 4, 256, 7)):
+                 shape=(256, 4, 256, 7), single_graphs: bool = True):
         self.device = device
+        self.single_graphs = single_graphs  # a lone request replays its agent's captured step
         self.budget = int(hbm_budget_bytes)
         self.max_batch = min(max_batch, B.SPLAT_MAX_VIEWS)
         self.n_streams = n_streams
@@ -118,6 +121,7 @@ class Server:
         maps and poses at the next prepare())."""
         for slot in self.slots:
             slot.agent = None
+            slot.graphs = {}
             slot.host_state = None
             slot.bytes = 0
             slot.busy = False
@@ -192,6 +196,7 @@ class Server:
         slot.w2c = slot.host_state[-4].numpy().copy()
         slot.capacity = a.fb.capacity
         slot.agent = None
+        slot.graphs = {}
         self.used -= slot.bytes
         slot.bytes = 0
         self.swaps += 1
@@ -211,10 +216,27 @@ class Server:
                 slot.bytes = slot.footprint = _agent_bytes(slot.agent)
                 self.used += slot.bytes
             torch.cuda.synchronize()
+        if self.single_graphs:  # the agents resident now get their single-request graphs
+            for slot in self.slots:
+                if slot.agent is not None:
+                    self._capture(slot)
+
+    def _capture(self, slot: _AgentSlot):
+        """One captured step per request kind, taken without changing the
+        agent's state."""
+        a = slot.agent
+        for kind in ("track", "map"):
+            a.cfg.track = kind == "track"
+            a.cfg.map = kind == "map"
+            a.capture(keep_state=True)
+            slot.graphs[kind] = a.graph
+        a.graph = None
 
     # -- one batched step ---------------------------------------------------------
     def _launch(self, reqs, si):
         s = self.streams[si]
+        if len(reqs) == 1 and self.slots[reqs[0].agent].graphs:
+            return self._launch_graph(reqs[0], s)
         agents = [self.slots[r.agent].agent for r in reqs]
         views = (B.CView * len(agents))(*[a.view() for a in agents])
         ast = self.agent_streams[si]
@@ -254,6 +276,24 @@ class Server:
         ev.record(s)
         return ev, outs
 
+    def _launch_graph(self, r, s):
+        """A lone request: its frame is copied in and the agent's captured step
+        for the request kind is replayed on stream s."""
+        slot = self.slots[r.agent]
+        a = slot.agent
+        rgb, depth = slot.frames[r.frame]
+        with torch.cuda.stream(s):
+            a.obs_rgb.copy_(rgb, non_blocking=True)
+            a.obs_depth.copy_(depth, non_blocking=True)
+            slot.graphs[r.kind].replay()
+            slot.out_loss.copy_(a.loss, non_blocking=True)
+            slot.out_w2c.copy_(a.w2c, non_blocking=True)
+        a.steps_done += 1
+        a.grads_clean = False
+        ev = torch.cuda.Event()
+        ev.record(s)
+        return ev, [(slot.out_loss, slot.out_w2c)]
+
     def _finish(self, reqs, outs, now):
         for r, (loss, w2c) in zip(reqs, outs):
             r.done = now
@@ -272,6 +312,10 @@ class Server:
         if not realtime:
             for r in requests:
                 r.arrival = 0.0
+        with _no_gc():
+            return self._serve(requests, realtime)
+
+    def _serve(self, requests, realtime):
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         ready = collections.deque()
         in_flight = {}  # stream index -> (event, reqs, outs)
@@ -339,6 +383,10 @@ class Server:
         if not realtime:
             for r in order:
                 r.arrival = 0.0
+        with _no_gc():
+            return self._serve_plain(order, realtime)
+
+    def _serve_plain(self, order, realtime):
         t0 = time.perf_counter()
         s = torch.cuda.current_stream()
         for r in order:
@@ -361,6 +409,20 @@ class Server:
             r.done = time.perf_counter() - t0
             slot.last_used = r.done
         return time.perf_counter() - t0
+
+
+class _no_gc:
+    """The Python collector stays off while requests are served (a collection
+    of the host's object graph can take tens of milliseconds)."""
+
+    def __enter__(self):
+        gc.collect()
+        self.was = gc.isenabled()
+        gc.disable()
+
+    def __exit__(self, *exc):
+        if self.was:
+            gc.enable()
 
 
 def latency_stats(requests, makespan):
