@@ -103,6 +103,15 @@ def _cam_args(cam, dtype):
     return ci, cf
 
 
+def set_exact_tiles(on: bool):
+    """Test switch: with False, every tile of a Gaussian's rect is a member
+    (the images must be the same either way)."""
+    L = lib()
+    L.oracle_set_exact_tiles.argtypes = [ctypes.c_int]
+    L.oracle_set_exact_tiles.restype = None
+    L.oracle_set_exact_tiles(1 if on else 0)
+
+
 def exp_f32(x):
     x = _c(x, np.float32)
     y = np.empty_like(x)

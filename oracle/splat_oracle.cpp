@@ -101,6 +101,7 @@ constexpr int TILE = 16;
 template <typename T> struct K {
   static T alpha_cap() { return T(0.99); }
   static T alpha_min() { return T(1.0) / T(255.0); }
+  static T tile_alpha() { return T(0.99) / T(255.0); }
   static T t_stop() { return T(1e-4); }
   static T lowpass() { return T(0.3); }
   static T clip() { return T(1.3); }
@@ -109,6 +110,7 @@ template <typename T> struct K {
 template <> struct K<float> {
   static float alpha_cap() { return 0.99f; }
   static float alpha_min() { return 1.0f / 255.0f; }
+  static float tile_alpha() { return 0.99f / 255.0f; }
   static float t_stop() { return 1e-4f; }
   static float lowpass() { return 0.3f; }
   static float clip() { return 1.3f; }
@@ -290,6 +292,58 @@ std::vector<Proj<T>> project_all(const Scene<T>& S, const T* w2c, const Cam<T>& 
 // O2 + O3: per-tile candidate lists ordered by (depth, gid).  The depth order
 // in float is the order of the float bit patterns (depth > 0).
 // Only tile rows [ty0, ty1) are filled (all rows by default).
+// Tile membership.  A tile of the Gaussian's rect can hold a contributor only
+// if some point of its 16 x 16 rectangle of pixel centres reaches
+// opacity * exp(-Q/2) >= 0.99/255, Q = a dx^2 + 2 b dx dy + c dy^2 (the conic
+// of the projection): below 1/255 every pixel skips the Gaussian.  Q is convex,
+// so its minimum over the rectangle is 0 with the centre inside, else on an
+// edge, where it is a 1-D quadratic minimised in closed form.  The operation
+// order is part of the specification (the decision must be the same in float
+// on every implementation).
+bool g_exact_tiles = true;  // test switch: false keeps whole rects
+
+template <typename T>
+bool tile_reaches(const Proj<T>& p, int tx, int ty) {
+  const T xa = (T(TILE * tx) + T(0.5)) - p.u;
+  const T xb = xa + T(15);
+  const T ya = (T(TILE * ty) + T(0.5)) - p.v;
+  const T yb = ya + T(15);
+  if (xa <= T(0) && T(0) <= xb && ya <= T(0) && T(0) <= yb) return true;
+  const T a = p.con_a, b = p.con_b, c = p.con_c;
+  const T b2 = T(2) * b;
+  T m = std::numeric_limits<T>::infinity();
+  for (int e = 0; e < 2; ++e) {
+    const T dy = e ? yb : ya;  // horizontal edge: minimiser dx = -(b dy) / a
+    const T dx = std::fmin(xb, std::fmax(xa, -((b * dy) / a)));
+    const T qh = ((a * dx) + (b2 * dy)) * dx + (c * dy) * dy;
+    m = std::fmin(m, qh);
+    const T ex = e ? xb : xa;  // vertical edge: minimiser dy = -(b dx) / c
+    const T ey = std::fmin(yb, std::fmax(ya, -((b * ex) / c)));
+    const T qv = (a * ex) * ex + ((b2 * ex) + (c * ey)) * ey;
+    m = std::fmin(m, qv);
+  }
+  return p.lam * act_exp<T>(T(-0.5) * m) >= K<T>::tile_alpha();
+}
+
+// The member tiles of row ty: from the first to the last tile of the rect row
+// that passes tile_reaches (the set of tiles meeting the ellipse within a
+// band is contiguous; holes from rounding are filled by definition).  Returns
+// false for an empty row.
+template <typename T>
+bool row_members(const Proj<T>& p, int ty, int& x0, int& x1) {
+  if (!g_exact_tiles) {
+    x0 = p.rect[0];
+    x1 = p.rect[2] - 1;
+    return x0 <= x1;
+  }
+  x0 = p.rect[0];
+  while (x0 < p.rect[2] && !tile_reaches(p, x0, ty)) ++x0;
+  if (x0 >= p.rect[2]) return false;
+  x1 = p.rect[2] - 1;
+  while (x1 > x0 && !tile_reaches(p, x1, ty)) --x1;
+  return true;
+}
+
 template <typename T>
 std::vector<std::vector<int32_t>> bin_all(const std::vector<Proj<T>>& P, const Cam<T>& cam, int ty0 = 0,
                                           int ty1 = 1 << 30) {
@@ -298,8 +352,11 @@ std::vector<std::vector<int32_t>> bin_all(const std::vector<Proj<T>>& P, const C
   for (size_t g = 0; g < P.size(); ++g) {
     const Proj<T>& p = P[g];
     if (p.tiles == 0) continue;
-    for (int ty = std::max(p.rect[1], ty0); ty < std::min(p.rect[3], ty1); ++ty)
-      for (int tx = p.rect[0]; tx < p.rect[2]; ++tx) bins[(size_t)ty * ntx + tx].push_back((int32_t)g);
+    for (int ty = std::max(p.rect[1], ty0); ty < std::min(p.rect[3], ty1); ++ty) {
+      int x0, x1;
+      if (!row_members(p, ty, x0, x1)) continue;
+      for (int tx = x0; tx <= x1; ++tx) bins[(size_t)ty * ntx + tx].push_back((int32_t)g);
+    }
   }
   for (auto& b : bins)
     std::sort(b.begin(), b.end(), [&](int32_t i, int32_t j) {
@@ -628,6 +685,9 @@ int render_bwd(const Scene<T>& S, const T* w2c, const Cam<T>& cam, const T* bg, 
 
 // ============================================================================
 // C ABI (host pointers; caller owns every buffer).
+// Test switch: 0 keeps whole rects as tile members (the images must not change).
+extern "C" void oracle_set_exact_tiles(int on) { g_exact_tiles = on != 0; }
+
 // cam_i = {width, height}; cam_f = {fx, fy, cx, cy, z_near, max_dist}; w2c = 4x4 row-major.
 // ============================================================================
 extern "C" {

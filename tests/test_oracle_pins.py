@@ -222,13 +222,26 @@ def test_near_plane_cull(orc):
 # ---------------------------------------------------------------------------
 # tile membership and order: brute force
 # ---------------------------------------------------------------------------
+def _tile_min_q(u, v, a, b, c, tx, ty):
+    """Minimum of a dx^2 + 2 b dx dy + c dy^2 over the tile's rectangle of
+    pixel centres, by dense sampling (65 x 65 points, float64) refined with
+    the exact value at the centre when it lies inside."""
+    xs = np.linspace(16 * tx + 0.5, 16 * tx + 15.5, 65) - u
+    ys = np.linspace(16 * ty + 0.5, 16 * ty + 15.5, 65) - v
+    dx, dy = np.meshgrid(xs, ys)
+    q = a * dx * dx + 2 * b * dx * dy + c * dy * dy
+    if xs[0] <= 0 <= xs[-1] and ys[0] <= 0 <= ys[-1]:
+        return 0.0
+    return float(q.min())
+
+
 @pytest.mark.parametrize("seed,w,h", [(0, 40, 35), (1, 64, 48), (2, 17, 90)])
 def test_bins_match_brute_force(orc, seed, w, h):
     cam = scenes.Camera(w, h, 60.0, 60.0, w / 2, h / 2)
     sc = scenes.scene_uniform(150, seed)
     pr = orc.project(sc, np.eye(4), cam)
     keys, vals, ranges = orc.bin_sort(sc, np.eye(4), cam)
-    xyzo, rad, rect = pr["xyzo"], pr["radius"], pr["rect"]
+    xyzo, rad, rect, con = pr["xyzo"], pr["radius"], pr["rect"], pr["conic"]
     # the rectangle covers every tile that holds a pixel centre within the radius box
     for g in np.nonzero(rad > 0)[0]:
         u, v, r = float(xyzo[g, 0]), float(xyzo[g, 1]), int(rad[g])
@@ -242,13 +255,36 @@ def test_bins_match_brute_force(orc, seed, w, h):
             assert rect[g, 1] <= t < rect[g, 3]
         if tx.size:
             assert rect[g, 2] - rect[g, 0] <= tx.size + 1
-    # per tile: all candidates in ascending (depth bits, gid), flattened in tile order
+    members = {}  # tile -> Gaussians holding it
+    for t in range(cam.n_tiles):
+        s0, s1 = ranges[t]
+        members[t] = set(int(x) for x in vals[s0:s1])
+    gx = np.arange(16) + 0.5
+    for g in np.nonzero(rad > 0)[0]:
+        u, v, lam = float(xyzo[g, 0]), float(xyzo[g, 1]), float(xyzo[g, 3])
+        a, b, c = (float(x) for x in con[g, :3])
+        for ty_ in range(rect[g, 1], rect[g, 3]):
+            row = []
+            for tx_ in range(rect[g, 0], rect[g, 2]):
+                t = ty_ * cam.tiles_x + tx_
+                # soundness: a tile with a pixel centre at alpha >= 1/255 holds the Gaussian
+                dx, dy = np.meshgrid(16 * tx_ + gx - u, 16 * ty_ + gx - v)
+                alpha = lam * np.exp(-0.5 * (a * dx * dx + 2 * b * dx * dy + c * dy * dy))
+                if alpha.max() >= 1 / 255:
+                    assert g in members[t], (g, t)
+                if g in members[t]:
+                    row.append(tx_)
+                    reach = lam * np.exp(-0.5 * _tile_min_q(u, v, a, b, c, tx_, ty_)) >= 0.99 / 255 * (1 - 1e-3)
+                    row[-1] = (tx_, reach)
+            # members of a row are contiguous, and the ones at its ends reach the threshold
+            if row:
+                xs_ = [x for x, _ in row]
+                assert xs_ == list(range(xs_[0], xs_[-1] + 1))
+                assert row[0][1] and row[-1][1]
+    # per tile: members in ascending (depth bits, gid), flattened in tile order
     k = 0
     for t in range(cam.n_tiles):
-        ty_, tx_ = divmod(t, cam.tiles_x)
-        cand = [g for g in range(sc.n) if rad[g] > 0 and rect[g, 0] <= tx_ < rect[g, 2]
-                and rect[g, 1] <= ty_ < rect[g, 3]]
-        cand.sort(key=lambda g: (int(xyzo[g, 2:3].view(np.uint32)[0]), g))
+        cand = sorted(members[t], key=lambda g: (int(xyzo[g, 2:3].view(np.uint32)[0]), g))
         assert list(vals[k:k + len(cand)]) == cand
         for j, g in enumerate(cand):
             assert int(keys[k + j]) == (t << 32) | int(xyzo[g, 2:3].view(np.uint32)[0])
@@ -257,7 +293,29 @@ def test_bins_match_brute_force(orc, seed, w, h):
         else:
             assert tuple(ranges[t]) == (0, 0)
         k += len(cand)
-    assert k == len(vals) == int(pr["tiles_touched"].sum())
+    assert k == len(vals) <= int(pr["tiles_touched"].sum())
+
+
+def test_tile_membership_leaves_the_images_unchanged(orc):
+    """Dropping the rect tiles that no pixel can take a Gaussian in changes
+    nothing rendered: images, ids and transmittance equal the whole-rect ones,
+    and fewer (Gaussian, tile) pairs are walked."""
+    sc = scenes.scene_room(6000, 6)
+    w2c = scenes.perturbed_w2c(7, 0.2, 10.0)
+    cam = scenes.Camera(96, 72, 80.0, 80.0, 48.0, 36.0)
+    bg = np.float32([0.1, 0.2, 0.3])
+    a = orc.render_fwd(sc, w2c, cam, bg)
+    try:
+        orc.set_exact_tiles(False)
+        b = orc.render_fwd(sc, w2c, cam, bg)
+        kb = len(orc.bin_sort(sc, w2c, cam)[1])
+    finally:
+        orc.set_exact_tiles(True)
+    ka = len(orc.bin_sort(sc, w2c, cam)[1])
+    for key in ("rgb", "depth", "sil", "t_final", "max_id"):
+        assert np.array_equal(a[key], b[key]), key
+    assert ka < 0.8 * kb
+    assert a["n_pairs"] < b["n_pairs"]
 
 
 # ---------------------------------------------------------------------------
