@@ -98,7 +98,7 @@ typedef struct {
                              alpha can still reach 1/255 (minus a margin)  */
   int32_t *radius;        /* [n] ceil(3 sqrt(lambda_max)); 0 = culled      */
   int32_t *rect;          /* [n,4] tile xmin, ymin, xmax, ymax (half open) */
-  int32_t *tiles_touched; /* [n] (xmax - xmin) * (ymax - ymin)             */
+  int32_t *tiles_touched; /* [n] (xmax - xmin) * (ymax - ymin): rect area, an upper bound of the member tiles */
 } splat_projected;
 
 /* Per-pixel render outputs, row-major [H,W] (rgb [H,W,3]). */
@@ -169,14 +169,27 @@ int splat_project(const splat_gaussians *g, const splat_camera *cam, const float
                   const splat_projected *out, splat_stream_t stream);
 
 /*
- * splat_bin_sort -- duplicate every visible Gaussian into each tile of its
- * rect and sort the (tile, depth) keys (the tile binning and front-to-back
+ * splat_bin_sort -- duplicate every visible Gaussian into each of its member
+ * tiles and sort the (tile, depth) keys (the tile binning and front-to-back
  * order the rendering equation of Sec. 3.3 composites in).
+ * Members: the tiles of the rect whose 16 x 16 rectangle of pixel centres can
+ * reach opacity * exp(-Q/2) >= 0.99/255 (Q = a dx^2 + 2 b dx dy + c dy^2 with
+ * the conic; minimum of Q over the rectangle: 0 with the centre inside, else
+ * the closed-form minimum over each edge, each operation rounded in the
+ * order written: xa = ((16 tx) + 0.5) - u, xb = xa + 15, same in y; on the
+ * edge y = dy, dx = min(xb, max(xa, -((b / a) dy))) and
+ * Q = ((a dx) + ((2 b) dy)) dx + (c dy) dy; on the edge x = dx,
+ * dy = min(yb, max(ya, -((b / c) dx))) and Q = (a dx) dx + (((2 b) dx) + (c dy)) dy;
+ * the test is opacity * exp(-0.5 Q_min) >= 0.99f / 255 with splat_exp_f32's
+ * exponential); in each rect row the members run from the first to the last
+ * tile that passes.  No pixel can take a Gaussian in a tile left out, so the
+ * images are those of whole rects.
  * Result: for every tile t, vals[ranges[2t] .. ranges[2t+1]) are the ids of
- * the Gaussians whose rect holds t, in ascending (depth, id) order; tiles
- * follow each other in tile-id order; an empty tile has range (0, 0).
+ * the Gaussians holding t, in ascending (depth, id) order; tiles follow each
+ * other in tile-id order; an empty tile has range (0, 0).
  * keys (optional, may be NULL) receives (uint64)tile << 32 | bits(depth).
- *   proj:     output of splat_project for n Gaussians (device)
+ *   proj:     output of splat_project for n Gaussians (device; xyzo, conic,
+ *             rect and tiles_touched are read)
  *   cam:      host; only width/height are used
  *   keys:     device uint64[capacity] or NULL
  *   vals:     device uint32[capacity]
@@ -206,8 +219,9 @@ int splat_bin_sort(const splat_projected *proj, int64_t n, const splat_camera *c
  * (64 MiB) that is part of this library's module: every GPU that loads the
  * library holds it until the process exits.  The call allocates nothing.
  *   Arguments, results and errors as splat_bin_sort (minus ws / ws_bytes).
- *   Sizes whose scratch need exceeds the array (about 25 MiB for capacity =
- *   1.6M duplicate slots) are rejected with SPLAT_EINVAL and a message.
+ *   Sizes whose scratch need exceeds the array (16 bytes per duplicate slot
+ *   and 8 per Gaussian: about 27 MiB for 300k Gaussians with 1.6M slots) are
+ *   rejected with SPLAT_EINVAL and a message.
  *   The first call on a device looks up the array's device address (with
  *   that device current): make that first call before any stream capture.
  *   All calls share the one array and leave their data in it; calls that

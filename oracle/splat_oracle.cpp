@@ -311,14 +311,15 @@ bool tile_reaches(const Proj<T>& p, int tx, int ty) {
   if (xa <= T(0) && T(0) <= xb && ya <= T(0) && T(0) <= yb) return true;
   const T a = p.con_a, b = p.con_b, c = p.con_c;
   const T b2 = T(2) * b;
+  const T ra = b / a, rc = b / c;
   T m = std::numeric_limits<T>::infinity();
   for (int e = 0; e < 2; ++e) {
-    const T dy = e ? yb : ya;  // horizontal edge: minimiser dx = -(b dy) / a
-    const T dx = std::fmin(xb, std::fmax(xa, -((b * dy) / a)));
+    const T dy = e ? yb : ya;  // horizontal edge: minimiser dx = -(b/a) dy
+    const T dx = std::fmin(xb, std::fmax(xa, -(ra * dy)));
     const T qh = ((a * dx) + (b2 * dy)) * dx + (c * dy) * dy;
     m = std::fmin(m, qh);
-    const T ex = e ? xb : xa;  // vertical edge: minimiser dy = -(b dx) / c
-    const T ey = std::fmin(yb, std::fmax(ya, -((b * ex) / c)));
+    const T ex = e ? xb : xa;  // vertical edge: minimiser dy = -(b/c) dx
+    const T ey = std::fmin(yb, std::fmax(ya, -(rc * ex)));
     const T qv = (a * ex) * ex + ((b2 * ex) + (c * ey)) * ey;
     m = std::fmin(m, qv);
   }

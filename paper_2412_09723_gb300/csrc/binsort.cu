@@ -266,18 +266,138 @@ constexpr int kScatterThreads = 256;
 constexpr int kScatterLanes = 4;     // threads sharing one Gaussian's rect (rows interleaved)
 constexpr int kScanGridSmem = 10240; // count-grid cells staged in shared memory (40 KB)
 
-// Visible Gaussians (tiles_touched > 0) are appended to vis[] with one atomic
-// per CTA, the duplicate total K is summed per CTA (one 64-bit atomic per CTA),
-// and every visible Gaussian's rect enters the tile counts through a 2D
-// difference array: +1 at (x0, y0) and (x1, y1), -1 at (x1, y0) and (x0, y1);
-// the prefix sums in tile_scan_kernel turn it into the number of rects
-// holding each tile.
+// Tile membership: a tile of the Gaussian's rect holds it only if some point
+// of its 16 x 16 rectangle of pixel centres reaches
+// opacity * exp(-Q/2) >= 0.99/255, Q = a dx^2 + 2 b dx dy + c dy^2 (below
+// 1/255 every pixel skips the Gaussian, so dropping the other tiles changes
+// no image).  Q is convex: its minimum over the rectangle is 0 with the centre
+// inside, else on an edge, a 1-D quadratic minimised in closed form.  Every
+// operation is rounded as written, in the written order (the CPU oracle takes
+// the same decision bit for bit).  In each tile row the members run from the
+// first to the last tile of the rect row that passes.
+constexpr float kTileAlpha = 0.99f / 255.0f;
+
+// Per-Gaussian data of the membership test.  qlo / qhi bracket the Q at which
+// opacity * exp(-Q/2) crosses 0.99/255 (from logf, widened by 1e-4 relative +
+// 1e-4): below qlo the test certainly passes and above qhi it certainly fails
+// (the exponential's error is a few 1e-7), so the exponential is evaluated
+// only in between -- the decision is the specified one either way.
+struct TileTest {
+  float u, v, a, b, c, b2, ra, rc, lam, qlo, qhi;
+  float det, ey, dyl;  // a c - b^2; y half-extent and leftmost point's dy of {Q <= qhi}
+};
+
+__device__ __forceinline__ TileTest tile_test(const float4 xo, const float4 co) {
+  TileTest t;
+  t.u = xo.x;
+  t.v = xo.y;
+  t.lam = xo.w;
+  t.a = co.x;
+  t.b = co.y;
+  t.c = co.z;
+  t.b2 = __fmul_rn(2.0f, co.y);
+  t.ra = __fdiv_rn(co.y, co.x);
+  t.rc = __fdiv_rn(co.y, co.z);
+  const float qt = 2.0f * (logf(xo.w) - logf(kTileAlpha));
+  const float w = 1e-4f * fabsf(qt) + 1e-4f;
+  t.qlo = qt - w;
+  t.qhi = qt + w;
+  t.det = co.x * co.z - co.y * co.y;
+  const float K = fmaxf(t.qhi, 0.0f);
+  t.ey = sqrtf(K * co.x / t.det);
+  t.dyl = co.y * sqrtf(K / (co.z * t.det));
+  return t;
+}
+
+// A range of tiles of rect row ty outside which the test certainly fails:
+// the tiles whose pixel-centre columns meet the x-extent of {Q <= qhi} within
+// the row's band (its leftmost and rightmost points over the band, from the
+// closed-form boundary of the ellipse), widened by 1 px + 0.1%.  Scanning from
+// its ends finds the same first and last passing tiles as scanning the whole
+// rect row.  False when the band certainly misses the ellipse.
+__device__ __forceinline__ bool row_candidates(const TileTest& t, const int4 r, int ty, int& xs, int& xe) {
+  if (!(t.det > 0.0f) || !(t.ey < 3e38f)) {  // degenerate: scan the whole rect row
+    xs = r.x;
+    xe = r.z - 1;
+    return true;
+  }
+  const float ya = (float)(kTile * ty) + 0.5f - t.v, yb = ya + 15.0f;
+  const float eyw = t.ey * 1.001f + 1.0f;
+  if (yb < -eyw || ya > eyw) return false;
+  const float lo = fmaxf(ya, -t.ey), hi = fminf(yb, t.ey);
+  const float K = fmaxf(t.qhi, 0.0f);
+  auto half = [&](float dy) { return sqrtf(fmaxf(0.0f, K * t.a - t.det * dy * dy)) / t.a; };
+  const float dl = fminf(hi, fmaxf(lo, t.dyl)), dr = fminf(hi, fmaxf(lo, -t.dyl));
+  const float X0 = -t.ra * dl - half(dl), X1 = -t.ra * dr + half(dr);
+  const float m = 1.0f + 1e-3f * (fabsf(X0) + fabsf(X1));
+  xs = max(r.x, (int)ceilf((t.u + X0 - m - 15.5f) * (1.0f / kTile)));
+  xe = min(r.z - 1, (int)floorf((t.u + X1 + m - 0.5f) * (1.0f / kTile)));
+  return xs <= xe;
+}
+
+__device__ __forceinline__ bool tile_reaches(const TileTest& t, int tx, int ty) {
+  const float xa = __fsub_rn(__fadd_rn((float)(kTile * tx), 0.5f), t.u);
+  const float xb = __fadd_rn(xa, 15.0f);
+  const float ya = __fsub_rn(__fadd_rn((float)(kTile * ty), 0.5f), t.v);
+  const float yb = __fadd_rn(ya, 15.0f);
+  if (xa <= 0.0f && 0.0f <= xb && ya <= 0.0f && 0.0f <= yb) return true;
+  float m = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float dy = e ? yb : ya;
+    const float dx = fminf(xb, fmaxf(xa, -__fmul_rn(t.ra, dy)));
+    const float qh = __fadd_rn(__fmul_rn(__fadd_rn(__fmul_rn(t.a, dx), __fmul_rn(t.b2, dy)), dx),
+                               __fmul_rn(__fmul_rn(t.c, dy), dy));
+    m = fminf(m, qh);
+    const float ex = e ? xb : xa;
+    const float ey = fminf(yb, fmaxf(ya, -__fmul_rn(t.rc, ex)));
+    const float qv = __fadd_rn(__fmul_rn(__fmul_rn(t.a, ex), ex),
+                               __fmul_rn(__fadd_rn(__fmul_rn(t.b2, ex), __fmul_rn(t.c, ey)), ey));
+    m = fminf(m, qv);
+  }
+  if (m < t.qlo) return true;
+  if (m > t.qhi) return false;
+  return __fmul_rn(t.lam, exp_full(__fmul_rn(-0.5f, m))) >= kTileAlpha;
+}
+
+// Member tiles [x0, x1] of rect row ty (the first and last passing tiles);
+// false for an empty row.
+__device__ __forceinline__ bool row_members(const TileTest& t, const int4 r, int ty, int& x0, int& x1) {
+  int xs, xe;
+  if (!row_candidates(t, r, ty, xs, xe)) return false;
+  x0 = xs;
+  while (x0 <= xe && !tile_reaches(t, x0, ty)) ++x0;
+  if (x0 > xe) return false;
+  x1 = xe;
+  while (x1 > x0 && !tile_reaches(t, x1, ty)) --x1;
+  return true;
+}
+
+// Visible Gaussians (tiles_touched > 0, a non-empty rect) are appended to
+// vis[] with one atomic per CTA.  Each warp then takes its visible Gaussians
+// one after another, a rect row per lane: the row's member tiles enter the
+// tile counts as +1 / -1 at its ends in a per-row difference array (prefix
+// sums along the rows in tile_scan_kernel give the counts), the duplicate
+// total K is summed (one 64-bit atomic per CTA), and the row's span is kept
+// for the scatter: one 16-bit word per rect row (first and last member as
+// offsets from the rect's left column; 0x00ff for an empty row) in a region
+// reserved with one atomic per warp.  A Gaussian whose rect is wider than 255
+// tiles, or whose rows do not fit the span buffer, gets no spans (vspan =
+// ~0) and the scatter tests its tiles again.
+constexpr uint32_t kNoSpan = 0xffffffffu;
+constexpr uint16_t kEmptySpan = 0x00ff;
+
 __global__ void __launch_bounds__(256) compact_count_kernel(const int32_t* __restrict__ tiles,
-                                                            const int4* __restrict__ rect, int64_t n, int gw,
+                                                            const int4* __restrict__ rect,
+                                                            const float4* __restrict__ xyzo,
+                                                            const float4* __restrict__ conic, int64_t n, int gw,
                                                             uint32_t* __restrict__ vis,
                                                             unsigned int* __restrict__ n_vis,
                                                             unsigned long long* __restrict__ k_total,
-                                                            int* __restrict__ diff) {
+                                                            int* __restrict__ diff, uint16_t* __restrict__ spans,
+                                                            uint64_t span_cap,
+                                                            unsigned long long* __restrict__ span_top,
+                                                            uint32_t* __restrict__ vspan) {
   __shared__ unsigned int s_warp[8];
   __shared__ unsigned long long s_k[8];
   __shared__ unsigned int s_base;
@@ -285,41 +405,110 @@ __global__ void __launch_bounds__(256) compact_count_kernel(const int32_t* __res
   const int tt = i < n ? tiles[i] : 0;
   const bool v = tt > 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lower = (1u << lane) - 1u;
   const unsigned ball = __ballot_sync(0xffffffffu, v);
-  unsigned long long t = (unsigned long long)(v ? tt : 0);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-  if (lane == 0) {
-    s_warp[warp] = __popc(ball);
-    s_k[warp] = t;
-  }
-  if (v) {
-    const int4 r = rect[i];
-    atomicAdd(&diff[r.y * gw + r.x], 1);
-    atomicAdd(&diff[r.y * gw + r.z], -1);
-    atomicAdd(&diff[r.w * gw + r.x], -1);
-    atomicAdd(&diff[r.w * gw + r.z], 1);
-  }
+  if (lane == 0) s_warp[warp] = __popc(ball);
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int tot = 0;
-    unsigned long long k = 0;
     for (int w = 0; w < 8; ++w) {
       const unsigned int c = s_warp[w];
       s_warp[w] = tot;
       tot += c;
-      k += s_k[w];
     }
     s_base = tot ? atomicAdd(n_vis, tot) : 0u;
-    if (k) atomicAdd(k_total, k);
   }
   __syncthreads();
-  if (v) vis[s_base + s_warp[warp] + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
+  const unsigned int wbase = s_base + s_warp[warp];
+  if (v) vis[wbase + __popc(ball & lower)] = (uint32_t)i;
+  // span region of the warp: its visible Gaussians' rect heights, one atomic
+  int4 rr = make_int4(0, 0, 0, 0);
+  uint32_t h = 0;
+  if (v) {
+    rr = rect[i];
+    h = rr.z - rr.x <= 255 ? (uint32_t)(rr.w - rr.y) : 0u;
+  }
+  uint32_t hx = h;  // exclusive prefix of h over the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, hx, o);
+    if (lane >= o) hx += y;
+  }
+  const uint32_t htot = __shfl_sync(0xffffffffu, hx, 31);
+  hx -= h;
+  unsigned long long sbase = 0;
+  if (lane == 0 && htot) sbase = atomicAdd(span_top, (unsigned long long)htot);
+  sbase = __shfl_sync(0xffffffffu, sbase, 0);
+  const bool fits = sbase + htot <= span_cap;
+  if (v) vspan[wbase + __popc(ball & lower)] = (h && fits) ? (uint32_t)(sbase + hx) : kNoSpan;
+  // the rows of the warp's visible Gaussians, flattened over its lanes: each
+  // lane's Gaussian's test data goes to shared memory, then lane q takes rows
+  // q, q + 32, ... of the concatenation (owner found by binary search)
+  __shared__ TileTest s_tt[8][32];
+  __shared__ int4 s_rect[8][32];
+  __shared__ uint32_t s_row0[8][33];  // exclusive prefix of the visible lanes' rect heights
+  __shared__ uint32_t s_sb[8][32];
+  const uint32_t hr = v ? (uint32_t)(rr.w - rr.y) : 0u;
+  uint32_t rx = hr;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, rx, o);
+    if (lane >= o) rx += y;
+  }
+  const uint32_t rows = __shfl_sync(0xffffffffu, rx, 31);
+  s_row0[warp][lane] = rx - hr;
+  if (lane == 31) s_row0[warp][32] = rows;
+  if (v) {
+    s_tt[warp][lane] = tile_test(xyzo[i], conic[i]);
+    s_rect[warp][lane] = rr;
+    s_sb[warp][lane] = (h && fits) ? (uint32_t)(sbase + hx) : kNoSpan;
+  }
+  __syncwarp();
+  unsigned long long t = 0;
+  for (uint32_t q = lane; q < rows; q += 32) {
+    int lo = 0, hi = 31;  // owner: the last lane whose first row is <= q (lanes without rows share it)
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_row0[warp][mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    while (s_row0[warp][lo + 1] <= q) ++lo;  // skip empty lanes sharing the prefix
+    const int4 r = s_rect[warp][lo];
+    const int ty = r.y + (int)(q - s_row0[warp][lo]);
+    const uint32_t sb = s_sb[warp][lo];
+    int x0, x1;
+    const bool any = row_members(s_tt[warp][lo], r, ty, x0, x1);
+    if (sb != kNoSpan) spans[(size_t)sb + (ty - r.y)] = any ? (uint16_t)((x0 - r.x) | ((x1 - r.x) << 8)) : kEmptySpan;
+    if (!any) continue;
+    atomicAdd(&diff[ty * gw + x0], 1);
+    atomicAdd(&diff[ty * gw + x1 + 1], -1);
+    t += (unsigned long long)(x1 - x0 + 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) s_k[warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long k = 0;
+    for (int w = 0; w < 8; ++w) k += s_k[w];
+    if (k) atomicAdd(k_total, k);
+  }
 }
 
-// One CTA: 2D prefix sums of the difference grid (tiles_y + 1 rows of
-// gw = tiles_x + 1 cells) -> per-tile counts; exclusive scan over tiles ->
-// ranges (clamped to the capacity) and bucket cursors; K and the status.
+// Member tiles of rect row ty from the kept span, or by testing again.
+__device__ __forceinline__ bool row_span(const uint16_t* __restrict__ spans, uint32_t sb, const float4 xo,
+                                         const float4 co, const int4 r, int ty, int& x0, int& x1) {
+  if (sb != kNoSpan) {
+    const uint16_t w = spans[(size_t)sb + (ty - r.y)];
+    x0 = r.x + (w & 0xff);
+    x1 = r.x + (w >> 8);
+    return x0 <= x1;
+  }
+  return row_members(tile_test(xo, co), r, ty, x0, x1);
+}
+
+// One CTA: prefix sums along the rows of the difference grid (gw = tiles_x + 1
+// cells per row) -> per-tile counts; exclusive scan over tiles -> ranges
+// (clamped to the capacity) and bucket cursors; K and the status.
 __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff, int tiles_x, int tiles_y,
                                                          const unsigned long long* __restrict__ k_total,
                                                          int64_t capacity, uint2* __restrict__ ranges,
@@ -333,9 +522,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
   if (grid == s_grid)
     for (int i = threadIdx.x; i < cells; i += blockDim.x) s_grid[i] = diff[i];
   __syncthreads();
-  // row prefix sums, one warp per row, then column prefix sums, one warp per
-  // column (32 cells per warp scan; two's-complement sums, so the negative
-  // entries of the difference array need no special care)
+  // prefix sums along each row (one warp per row, 32 cells per warp scan;
+  // two's-complement sums, so the negative entries need no special care)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int y = wid; y < tiles_y; y += nw) {
     uint32_t carry = 0;
@@ -343,16 +531,6 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
       const int x = x0 + lane;
       const uint32_t v = warp_incl_scan(x < tiles_x ? (uint32_t)grid[y * gw + x] : 0u, lane) + carry;
       if (x < tiles_x) grid[y * gw + x] = (int)v;
-      carry = __shfl_sync(0xffffffffu, v, 31);
-    }
-  }
-  __syncthreads();
-  for (int x = wid; x < tiles_x; x += nw) {
-    uint32_t carry = 0;
-    for (int y0 = 0; y0 < tiles_y; y0 += 32) {
-      const int y = y0 + lane;
-      const uint32_t v = warp_incl_scan(y < tiles_y ? (uint32_t)grid[y * gw + x] : 0u, lane) + carry;
-      if (y < tiles_y) grid[y * gw + x] = (int)v;
       carry = __shfl_sync(0xffffffffu, v, 31);
     }
   }
@@ -381,53 +559,85 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
 }
 
 // Every visible Gaussian drops key (depth bits << 32 | id) into the bucket of
-// each tile of its rect.  A CTA takes a chunk of visible Gaussians, counts its
-// duplicates per tile in shared memory, reserves space in each touched bucket
-// with one global atomic, then places its keys with shared-memory atomics.  The
-// order inside a bucket is arbitrary; the keys are unique, so the per-tile
-// sort below makes the result deterministic.
+// each of its member tiles.  A CTA takes a contiguous slice of the visible list,
+// counts its duplicates per tile in shared memory (kScatterLanes threads per
+// rect, rows interleaved), reserves space in each touched bucket with one
+// global atomic for the whole slice, then places its keys with shared-memory
+// atomics.  The order inside a bucket is arbitrary; the keys are unique, so
+// the per-tile sort below makes the result deterministic.
 __global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(
     const uint32_t* __restrict__ vis, const unsigned int* __restrict__ n_vis, const float4* __restrict__ xyzo,
-    const int4* __restrict__ rect, int tiles_x, int n_tiles, uint32_t* __restrict__ cursor, int64_t capacity,
+    const float4* __restrict__ conic, const int4* __restrict__ rect, const uint16_t* __restrict__ spans,
+    const uint32_t* __restrict__ vspan, int tiles_x, int n_tiles, uint32_t* __restrict__ cursor, int64_t capacity,
     uint64_t* __restrict__ skeys) {
   extern __shared__ uint32_t s_cnt[];  // [n_tiles] local counts, then local cursors
   uint32_t* s_base = s_cnt + n_tiles;  // [n_tiles] reserved bucket positions
-  constexpr int kChunk = kScatterThreads / kScatterLanes;  // Gaussians per chunk
+  constexpr int kChunk = kScatterThreads / kScatterLanes;  // Gaussians per round
   const unsigned int nv = *n_vis;
-  const bool local = n_tiles <= kSmemTiles;
   const int sub = threadIdx.x % kScatterLanes;  // this thread takes rect rows ty = y0 + sub (mod kScatterLanes)
-  for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < nv; c0 += (int64_t)gridDim.x * kChunk) {
-    const int64_t i = c0 + threadIdx.x / kScatterLanes;
-    const bool has = i < nv;
-    const uint32_t g = has ? vis[i] : 0u;
-    const int4 r = has ? rect[g] : make_int4(0, 0, 0, 0);
-    const uint64_t key = has ? (((uint64_t)__float_as_uint(xyzo[g].z) << 32) | (uint64_t)g) : 0ull;
-    if (!local) {  // too many tiles for shared memory: one global atomic per duplicate
-      for (int ty = r.y + sub; ty < r.w; ty += kScatterLanes)
-        for (int tx = r.x; tx < r.z; ++tx) {
+  if (n_tiles > kSmemTiles) {  // too many tiles for shared memory: one global atomic per duplicate
+    for (int64_t c0 = (int64_t)blockIdx.x * kChunk; c0 < nv; c0 += (int64_t)gridDim.x * kChunk) {
+      const int64_t i = c0 + threadIdx.x / kScatterLanes;
+      if (i >= nv) continue;
+      const uint32_t g = vis[i];
+      const int4 r = rect[g];
+      const float4 xo = xyzo[g], co = conic[g];
+      const uint32_t sb = vspan[i];
+      const uint64_t key = ((uint64_t)__float_as_uint(xo.z) << 32) | (uint64_t)g;
+      for (int ty = r.y + sub; ty < r.w; ty += kScatterLanes) {
+        int x0, x1;
+        if (!row_span(spans, sb, xo, co, r, ty, x0, x1)) continue;
+        for (int tx = x0; tx <= x1; ++tx) {
           const uint32_t pos = atomicAdd(&cursor[(size_t)(ty * tiles_x + tx) * kCursorStride], 1u);
           if (pos < capacity) skeys[pos] = key;
         }
-      continue;
+      }
     }
-    for (int t = threadIdx.x; t < n_tiles; t += kScatterThreads) s_cnt[t] = 0u;
-    __syncthreads();
-    for (int ty = r.y + sub; ty < r.w; ty += kScatterLanes)
-      for (int tx = r.x; tx < r.z; ++tx) atomicAdd(&s_cnt[ty * tiles_x + tx], 1u);
-    __syncthreads();
-    for (int t = threadIdx.x; t < n_tiles; t += kScatterThreads) {
-      const uint32_t c = s_cnt[t];
-      s_base[t] = c ? atomicAdd(&cursor[(size_t)t * kCursorStride], c) : 0u;
-      s_cnt[t] = 0u;
+    return;
+  }
+  const int64_t per = ((int64_t)nv + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < (int64_t)nv ? lo + per : (int64_t)nv;
+  for (int t = threadIdx.x; t < n_tiles; t += kScatterThreads) s_cnt[t] = 0u;
+  __syncthreads();
+  for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {  // count
+    const int64_t i = c0 + threadIdx.x / kScatterLanes;
+    if (i >= hi) continue;
+    const uint32_t g = vis[i];
+    const int4 r = rect[g];
+    const uint32_t sb = vspan[i];
+    const float4 xo = sb == kNoSpan ? xyzo[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 co = sb == kNoSpan ? conic[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int ty = r.y + sub; ty < r.w; ty += kScatterLanes) {
+      int x0, x1;
+      if (!row_span(spans, sb, xo, co, r, ty, x0, x1)) continue;
+      for (int tx = x0; tx <= x1; ++tx) atomicAdd(&s_cnt[ty * tiles_x + tx], 1u);
     }
-    __syncthreads();
-    for (int ty = r.y + sub; ty < r.w; ty += kScatterLanes)
-      for (int tx = r.x; tx < r.z; ++tx) {
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_tiles; t += kScatterThreads) {  // reserve
+    const uint32_t c = s_cnt[t];
+    s_base[t] = c ? atomicAdd(&cursor[(size_t)t * kCursorStride], c) : 0u;
+    s_cnt[t] = 0u;
+  }
+  __syncthreads();
+  for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {  // place
+    const int64_t i = c0 + threadIdx.x / kScatterLanes;
+    if (i >= hi) continue;
+    const uint32_t g = vis[i];
+    const int4 r = rect[g];
+    const float4 xo = xyzo[g];
+    const uint32_t sb = vspan[i];
+    const float4 co = sb == kNoSpan ? conic[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint64_t key = ((uint64_t)__float_as_uint(xo.z) << 32) | (uint64_t)g;
+    for (int ty = r.y + sub; ty < r.w; ty += kScatterLanes) {
+      int x0, x1;
+      if (!row_span(spans, sb, xo, co, r, ty, x0, x1)) continue;
+      for (int tx = x0; tx <= x1; ++tx) {
         const int t = ty * tiles_x + tx;
         const uint32_t pos = s_base[t] + atomicAdd(&s_cnt[t], 1u);
         if (pos < capacity) skeys[pos] = key;
       }
-    __syncthreads();
+    }
   }
 }
 
@@ -487,10 +697,10 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint2* __
 // Workspace layout and the entry point.
 // ----------------------------------------------------------------------------
 struct BinWs {
-  uint32_t *vis, *cursor;
+  uint32_t *vis, *vspan, *cursor;
   int* diff;
-  uint64_t *skeys, *skeys2;
-  unsigned long long* k_total;
+  uint64_t *skeys, *skeys2;  // skeys2 also holds the row spans until the tile sort
+  unsigned long long *k_total, *span_top;
   unsigned int* n_vis;
 };
 
@@ -505,11 +715,13 @@ static size_t carve_bin_ws(int64_t n, int64_t tiles_x, int64_t tiles_y, int64_t 
   const size_t nt = (size_t)std::max<int64_t>(tiles_x * tiles_y, 1);
   BinWs t;
   t.vis = (uint32_t*)take(4 * nn);
+  t.vspan = (uint32_t*)take(4 * nn);
   t.cursor = (uint32_t*)take(4 * kCursorStride * nt);
   t.diff = (int*)take(4 * (size_t)(tiles_x + 1) * (tiles_y + 1));
   t.skeys = (uint64_t*)take(8 * cc);
   t.skeys2 = (uint64_t*)take(8 * cc);
   t.k_total = (unsigned long long*)take(8);
+  t.span_top = (unsigned long long*)take(8);
   t.n_vis = (unsigned int*)take(8);
   if (w) *w = t;
   return off;
@@ -535,7 +747,8 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
   if (n < 0 || n > 0x7fffffff || capacity < 0 || capacity > 0x7fffffff)
     return fail(SPLAT_EINVAL, "splat_bin_sort: n=%lld capacity=%lld out of range", (long long)n, (long long)capacity);
   if (cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "splat_bin_sort: bad image size");
-  if (n > 0 && (!proj->xyzo || !proj->rect || !proj->tiles_touched || !aligned16(proj->xyzo) || !aligned16(proj->rect)))
+  if (n > 0 && (!proj->xyzo || !proj->conic || !proj->rect || !proj->tiles_touched || !aligned16(proj->xyzo) ||
+                !aligned16(proj->conic) || !aligned16(proj->rect)))
     return fail(SPLAT_EINVAL, "splat_bin_sort: projected arrays null or not 16-byte aligned");
   const CamK ck = make_camk(*cam);
   const int64_t n_tiles = (int64_t)ck.tiles_x * ck.tiles_y;
@@ -562,15 +775,20 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
   const size_t diff_bytes = sizeof(int) * (size_t)(ck.tiles_x + 1) * (ck.tiles_y + 1);
   if (cudaMemsetAsync(w.diff, 0, diff_bytes, s) != cudaSuccess ||
       cudaMemsetAsync(w.k_total, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+      cudaMemsetAsync(w.span_top, 0, sizeof(unsigned long long), s) != cudaSuccess ||
       cudaMemsetAsync(w.n_vis, 0, sizeof(unsigned int), s) != cudaSuccess)
     return fail(SPLAT_ECUDA, "splat_bin_sort: memset failed");
   const float4* xyzo = reinterpret_cast<const float4*>(proj->xyzo);
   const int4* rect = reinterpret_cast<const int4*>(proj->rect);
+  const float4* conic = reinterpret_cast<const float4*>(proj->conic);
   const int nb = std::max(1, ceil_div(n, 256));
   if (n > 0)
     SPLAT_LAUNCH("compact_count_kernel", s,
-                 compact_count_kernel<<<nb, 256, 0, s>>>(proj->tiles_touched, rect, n, ck.tiles_x + 1, w.vis, w.n_vis,
-                                                         w.k_total, w.diff));
+                 compact_count_kernel<<<nb, 256, 0, s>>>(proj->tiles_touched, rect, xyzo, conic, n, ck.tiles_x + 1,
+                                                         w.vis, w.n_vis, w.k_total, w.diff,
+                                                         reinterpret_cast<uint16_t*>(w.skeys2),
+                                                         4 * (uint64_t)std::max<int64_t>(capacity, 1), w.span_top,
+                                                         w.vspan));
   SPLAT_LAUNCH("tile_scan_kernel", s,
                tile_scan_kernel<<<1, 1024, 0, s>>>(w.diff, ck.tiles_x, ck.tiles_y, w.k_total, capacity,
                                                    reinterpret_cast<uint2*>(ranges), w.cursor, k_dev, status));
@@ -581,10 +799,11 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  const int sgrid = std::max(1, std::min(ceil_div(n, kScatterThreads / kScatterLanes), 4 * sms));
+  const int sgrid = std::max(1, std::min(ceil_div(n, kScatterThreads / kScatterLanes), 2 * sms));
   SPLAT_LAUNCH("bucket_scatter_kernel", s,
                bucket_scatter_kernel<<<sgrid, kScatterThreads, scatter_smem, s>>>(
-                   w.vis, w.n_vis, xyzo, rect, ck.tiles_x, (int)n_tiles, w.cursor, capacity, w.skeys));
+                   w.vis, w.n_vis, xyzo, conic, rect, reinterpret_cast<const uint16_t*>(w.skeys2), w.vspan,
+                   ck.tiles_x, (int)n_tiles, w.cursor, capacity, w.skeys));
   if ((rc = check_launch("bucket_scatter_kernel"))) return rc;
   {
     static std::atomic<unsigned long long> sort_attr_done{0};
