@@ -15,7 +15,11 @@ and inter-agent processing of Sec. 3.2 / 3.6, on one GPU).
   launch each, and the loss, pose and Adam updates follow per agent.  Up to
   `n_streams` batches are in flight at once, so requests that arrive while
   others run are admitted as stream slots and memory free up, and their work
-  overlaps on the device.  Completion is detected with CUDA events.
+  overlaps on the device.  Completion is detected with CUDA events.  A batch
+  of one request replays the agent's own captured single-agent step (one
+  graph launch, captured and warmed when the agent becomes resident, without
+  changing its state).  Python's cyclic garbage collector is off while the
+  loop serves, so no collection pause lands inside a request.
 * Plain mode serves the same requests one at a time in arrival order with the
   single-agent launches and a synchronisation per request.
 
