@@ -79,6 +79,7 @@ class Agent:
         self.m_dev = torch.zeros(1, dtype=torch.int64, device=device)
         self.assoc_status = self._acc[7:8].view(torch.int32)
         self.assoc_ws = torch.empty(max(1, B.splat_assoc_workspace_size(npix)), dtype=torch.uint8, device=device)
+        self.side = torch.cuda.Stream(device=device)  # the association runs here, beside the backward chain
         self.cg = B.gaussians_struct(*self.params)
         self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads))
         self.steps_done = 0
@@ -160,8 +161,8 @@ class Agent:
         fb = self.fb
         B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cgr, self.d_pose, None, s)
 
-    def phase_update(self, s):
-        cfg, fb = self.cfg, self.fb
+    def phase_update(self, s, assoc: bool = True):
+        cfg = self.cfg
         self.steps_done += 1
         with torch.cuda.stream(s):
             self.t_dev.add_(1)
@@ -172,18 +173,34 @@ class Agent:
         if cfg.track:
             B.splat_pose_step(self.w2c, self.d_pose, self.pose_m, self.pose_v, t, cfg.pose_lr[0], cfg.pose_lr[1],
                               stream=s)
+        if assoc:
+            self.phase_assoc(s)
+
+    def phase_assoc(self, s):
+        """Association of the rendered ids with the observation's (needs the
+        forward render and the accumulators cleared in phase_loss)."""
+        cfg, fb = self.cfg, self.fb
         if cfg.assoc:  # the status word was cleared with the other accumulators in phase_loss
             B.splat_assoc(fb.image["max_id"], fb.image["t_final"], self.obs_id, self.obs_tfinal, self.n, self.n,
                           cfg.t_max, self.pairs, self.counts, self.assoc_cap, self.m_dev, self.assoc_status,
                           self.assoc_ws, s)
 
     def step(self, stream=None, sync_check: bool = False):
+        """One step.  The association depends only on the forward render, so it
+        runs on a side stream forked after the loss and joined at the end,
+        overlapping the backward render, the projection adjoint and the
+        updates."""
         s = torch.cuda.current_stream() if stream is None else stream
         self.phase_pre(s, sync_check)
         self.phase_render(s)
         self.phase_loss(s)
+        if self.cfg.assoc:
+            self.side.wait_stream(s)
+            self.phase_assoc(self.side)
         self.phase_backward(s)
-        self.phase_update(s)
+        self.phase_update(s, assoc=False)
+        if self.cfg.assoc:
+            s.wait_stream(self.side)
 
     def view(self):
         """C descriptor of this agent's view for the batched render calls."""
