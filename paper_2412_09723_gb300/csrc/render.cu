@@ -3,11 +3,12 @@
 // its back-to-front adjoint, for one view per launch or for several views
 // (agents of uneven map sizes, Sec. 3.6) in one persistent launch.
 //
-// Forward: 256 threads, one per pixel of a 16x16 tile.  The tile's list is
-// staged through shared memory in batches of BATCH Gaussians (position /
-// depth / opacity, the quadratic form's coefficients A = -a/2, B = -b,
-// C = -c/2 with the exponent cut, colour, id) and every thread walks the batch
-// in order.  A pair whose exponent lies below the Gaussian's cut (set by the
+// Forward: 128 threads with 2 pixels each ((x, y) and (x, y + 2); a warp
+// covers 16 x 4 pixels), the pair's arithmetic in packed single-precision
+// pairs.  The tile's list is staged through shared memory in batches of BATCH
+// Gaussians (position / depth / opacity, the quadratic form's coefficients
+// A = -a/2, B = -b, C = -c/2 with the exponent cut, colour, id) and every
+// thread walks the batch in order.  A pair whose exponent lies below the Gaussian's cut (set by the
 // projection so that opacity * exp(power) < 1/255 is certain) is skipped before
 // the exponential is evaluated; this changes no result.  A tile ends as soon as
 // all of its pixels have reached the transmittance stop.  No atomics.
@@ -36,7 +37,7 @@
 
 namespace splat {
 
-constexpr int kFwdThreads = kTilePixels;  // forward: one pixel per thread
+constexpr int kFwdThreads = 128;         // forward: two pixels per thread
 constexpr int kBwdThreads = 128;          // backward (batched launch): two pixels per thread
 constexpr int kBwdSinglePPT = 2;          // backward (one view): pixels per thread (4 measured slower)
 constexpr int kGradStride = 12;           // screen-space gradient row (3 float4)
@@ -75,7 +76,7 @@ struct ViewTable {
 };
 
 // Shared-memory staging of one batch of Gaussians.
-constexpr int kMaxWarps = 8;  // warps of a tile CTA (forward 8 of 2 rows, backward 4 of 4 rows)
+constexpr int kMaxWarps = 8;  // warps of a tile CTA (forward and backward: 4 of 4 rows)
 
 struct StagePtrs {
   float4* xyzo;
@@ -188,83 +189,152 @@ __device__ __forceinline__ int build_warp_list(const uint8_t* wmask, uint8_t* li
 // ----------------------------------------------------------------------------
 // Forward
 // ----------------------------------------------------------------------------
+// Two pixels per thread, (x, y) and (x, y + 2), so one staged Gaussian's loads
+// and the shared dx serve both, and their arithmetic runs as packed pairs
+// (__fadd2_rn, __fmul2_rn, __ffma2_rn: two IEEE single-precision operations
+// each, rounded exactly as the scalar ones, so every value is bit for bit the
+// specified one).  A pixel that skips a Gaussian keeps its state by masking:
+// its weight is set to 0 (fma(c, 0, C) = C, S + 0 = S) and T, the last
+// contributor and the counters are selected.
 struct FwdPix {
-  float T, C0, C1, C2, D, S, wmax;
-  int32_t id, last, used;
-  bool done;
+  float2 T, C0, C1, C2, D, S, wmax;
+  int32_t id[2], last[2], used[2];
+  bool done[2];
 };
 
-// One front-to-back compositing step of one pixel (the specified order).
-__device__ __forceinline__ void composite_step(FwdPix& q, const float4 xo, const float4 qd, float fx, float fy,
-                                               const float4* cidp, int32_t pos) {
+__device__ __forceinline__ float2 bcast(float v) { return make_float2(v, v); }
+
+// exp_core of both lanes (same operations as the scalar one).
+__device__ __forceinline__ float2 exp_core2(float2 x) {
+  const float2 t = __fadd2_rn(__fmul2_rn(x, bcast(1.44269502f)), bcast(12582912.0f));
+  const float2 k = __fadd2_rn(t, bcast(-12582912.0f));
+  float2 r = __ffma2_rn(k, bcast(-0.693145751953125f), x);
+  r = __ffma2_rn(k, bcast(-1.42860677e-06f), r);
+  float2 q = bcast(1.98412701e-04f);
+  q = __ffma2_rn(q, r, bcast(1.38888892e-03f));
+  q = __ffma2_rn(q, r, bcast(8.33333377e-03f));
+  q = __ffma2_rn(q, r, bcast(4.16666679e-02f));
+  q = __ffma2_rn(q, r, bcast(1.66666672e-01f));
+  q = __ffma2_rn(q, r, bcast(0.5f));
+  q = __ffma2_rn(q, r, bcast(1.0f));
+  q = __ffma2_rn(q, r, bcast(1.0f));
+  const float2 sc = make_float2(__int_as_float((__float_as_int(t.x) - 0x4B400000 + 127) << 23),
+                                __int_as_float((__float_as_int(t.y) - 0x4B400000 + 127) << 23));
+  return __fmul2_rn(q, sc);
+}
+
+// One front-to-back compositing step of the thread's two pixels (the
+// specified order).  nfy = (-fy0, -fy1).
+__device__ __forceinline__ void composite_step2(FwdPix& q, const float4 xo, const float4 qd, float fx, float2 nfy,
+                                                const float4* cidp, int32_t pos) {
   const float dx = xo.x - fx;
-  const float dy = xo.y - fy;
-  const float power = __fmaf_rn(qd.z * dy, dy, dx * __fmaf_rn(qd.x, dx, qd.y * dy));
-  if (power > 0.0f || power < qd.w) return;
-  const float G = exp_core(power);
-  const float alpha = fminf(kAlphaCap, xo.w * G);
-  if (alpha < kAlphaMin) return;
-  const float test_T = q.T * (1.0f - alpha);
-  if (test_T < kTStop) {
-    q.done = true;
-    return;
+  const float2 dy = __fadd2_rn(bcast(xo.y), nfy);
+  const float2 inner = __ffma2_rn(bcast(qd.x), bcast(dx), __fmul2_rn(bcast(qd.y), dy));
+  const float2 power = __ffma2_rn(__fmul2_rn(bcast(qd.z), dy), dy, __fmul2_rn(bcast(dx), inner));
+  bool in0 = !q.done[0] && !(power.x > 0.0f || power.x < qd.w);
+  bool in1 = !q.done[1] && !(power.y > 0.0f || power.y < qd.w);
+  if (!(in0 || in1)) return;
+  const float2 G = exp_core2(power);
+  const float2 raw = __fmul2_rn(bcast(xo.w), G);
+  const float2 alpha = make_float2(fminf(kAlphaCap, raw.x), fminf(kAlphaCap, raw.y));
+  in0 = in0 && !(alpha.x < kAlphaMin);
+  in1 = in1 && !(alpha.y < kAlphaMin);
+  const float2 test_T = __fmul2_rn(q.T, __ffma2_rn(alpha, bcast(-1.0f), bcast(1.0f)));
+  if (in0 && test_T.x < kTStop) {
+    q.done[0] = true;
+    in0 = false;
   }
-  const float w = alpha * q.T;
+  if (in1 && test_T.y < kTStop) {
+    q.done[1] = true;
+    in1 = false;
+  }
+  if (!(in0 || in1)) return;
+  float2 w = __fmul2_rn(alpha, q.T);
+  w.x = in0 ? w.x : 0.0f;
+  w.y = in1 ? w.y : 0.0f;
   const float4 c = *cidp;
-  q.C0 = __fmaf_rn(c.x, w, q.C0);
-  q.C1 = __fmaf_rn(c.y, w, q.C1);
-  q.C2 = __fmaf_rn(c.z, w, q.C2);
-  q.D = __fmaf_rn(xo.z, w, q.D);
-  q.S = q.S + w;
-  if (w > q.wmax) {
-    q.wmax = w;
-    q.id = __float_as_int(c.w);
+  q.C0 = __ffma2_rn(bcast(c.x), w, q.C0);
+  q.C1 = __ffma2_rn(bcast(c.y), w, q.C1);
+  q.C2 = __ffma2_rn(bcast(c.z), w, q.C2);
+  q.D = __ffma2_rn(bcast(xo.z), w, q.D);
+  q.S = __fadd2_rn(q.S, w);
+  if (w.x > q.wmax.x) {
+    q.wmax.x = w.x;
+    q.id[0] = __float_as_int(c.w);
   }
-  q.T = test_T;
-  q.last = pos + 1;
-  ++q.used;
+  if (w.y > q.wmax.y) {
+    q.wmax.y = w.y;
+    q.id[1] = __float_as_int(c.w);
+  }
+  q.T.x = in0 ? test_T.x : q.T.x;
+  q.T.y = in1 ? test_T.y : q.T.y;
+  q.last[0] = in0 ? pos + 1 : q.last[0];
+  q.last[1] = in1 ? pos + 1 : q.last[1];
+  q.used[0] += in0;
+  q.used[1] += in1;
+}
+
+// Pixel p (0 or 1) of forward thread t: warp w covers rows 4w .. 4w + 3
+// (lanes 0-15 rows 4w and 4w + 2, lanes 16-31 rows 4w + 1 and 4w + 3).
+__device__ __forceinline__ void fwd_pixel(int t, int p, int& lx, int& ly) {
+  const int lane = t & 31, warp = t >> 5;
+  lx = lane & 15;
+  ly = 4 * warp + (lane >> 4) + 2 * p;
 }
 
 template <int BATCH>
 __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>& sm) {
   const CamK& cam = V.cam;
   const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
-  const int px = tx * kTile + (threadIdx.x & (kTile - 1));
-  const int py = ty * kTile + (threadIdx.x >> 4);
-  const bool inside = px < cam.width && py < cam.height;
-  const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
-  FwdPix q{1.0f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, -1, 0, 0, !inside};
+  int lx, ly0, ly1;
+  fwd_pixel(threadIdx.x, 0, lx, ly0);
+  fwd_pixel(threadIdx.x, 1, lx, ly1);
+  const int px = tx * kTile + lx, py0 = ty * kTile + ly0, py1 = ty * kTile + ly1;
+  const bool in0 = px < cam.width && py0 < cam.height, in1 = px < cam.width && py1 < cam.height;
+  const float fx = (float)px + 0.5f;
+  const float2 nfy = make_float2(-((float)py0 + 0.5f), -((float)py1 + 0.5f));
+  FwdPix q;
+  q.T = bcast(1.0f);
+  q.C0 = q.C1 = q.C2 = q.D = q.S = q.wmax = bcast(0.0f);
+  q.id[0] = q.id[1] = -1;
+  q.last[0] = q.last[1] = q.used[0] = q.used[1] = 0;
+  q.done[0] = !in0;
+  q.done[1] = !in1;
   const uint2 rg = V.ranges[tile];
   const int warp = threadIdx.x >> 5;
   const StagePtrs sp{sm.xyzo, sm.quad, sm.cid, sm.wmask};
   for (uint32_t start = rg.x; start < rg.y; start += BATCH) {
-    if (__syncthreads_count(q.done) == kFwdThreads) break;
-    if (threadIdx.x < BATCH && start + threadIdx.x < rg.y)
-      stage_one<false>(V, V.vals[start + threadIdx.x], threadIdx.x, sp, tx * kTile, ty * kTile, 2);
-    __syncthreads();
+    if (__syncthreads_count(q.done[0] && q.done[1]) == kFwdThreads) break;
     const int cnt = (int)min((uint32_t)BATCH, rg.y - start);
+    for (int i = threadIdx.x; i < cnt; i += kFwdThreads)
+      stage_one<false>(V, V.vals[start + i], i, sp, tx * kTile, ty * kTile, 4);
+    __syncthreads();
     const int32_t base = (int32_t)(start - rg.x);
     const int nl = build_warp_list(sm.wmask, sm.wlist[warp], cnt, warp);
-    for (int e = 0; e < nl && !q.done; ++e) {
+    for (int e = 0; e < nl && !(q.done[0] && q.done[1]); ++e) {
       const int j = sm.wlist[warp][e];
-      composite_step(q, sm.xyzo[j], sm.quad[j], fx, fy, &sm.cid[j], base + j);
+      composite_step2(q, sm.xyzo[j], sm.quad[j], fx, nfy, &sm.cid[j], base + j);
     }
   }
-  if (!inside) return;
-  const size_t i = (size_t)py * cam.width + px;
-  V.img.rgb[3 * i + 0] = __fmaf_rn(q.T, V.bg0, q.C0);
-  V.img.rgb[3 * i + 1] = __fmaf_rn(q.T, V.bg1, q.C1);
-  V.img.rgb[3 * i + 2] = __fmaf_rn(q.T, V.bg2, q.C2);
-  V.img.depth[i] = q.D;
-  V.img.sil[i] = q.S;
-  V.img.t_final[i] = q.T;
-  V.img.n_contrib[i] = q.last;
-  V.img.max_id[i] = q.id;
-  if (V.img.n_used) V.img.n_used[i] = q.used;
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    if (!(p ? in1 : in0)) continue;
+    const size_t i = (size_t)(p ? py1 : py0) * cam.width + px;
+    const float T = p ? q.T.y : q.T.x;
+    V.img.rgb[3 * i + 0] = __fmaf_rn(T, V.bg0, p ? q.C0.y : q.C0.x);
+    V.img.rgb[3 * i + 1] = __fmaf_rn(T, V.bg1, p ? q.C1.y : q.C1.x);
+    V.img.rgb[3 * i + 2] = __fmaf_rn(T, V.bg2, p ? q.C2.y : q.C2.x);
+    V.img.depth[i] = p ? q.D.y : q.D.x;
+    V.img.sil[i] = p ? q.S.y : q.S.x;
+    V.img.t_final[i] = T;
+    V.img.n_contrib[i] = q.last[p];
+    V.img.max_id[i] = q.id[p];
+    if (V.img.n_used) V.img.n_used[i] = q.used[p];
+  }
 }
 
 template <int BATCH>
-__global__ void __launch_bounds__(kFwdThreads, 6) render_fwd_kernel(ViewK V) {
+__global__ void __launch_bounds__(kFwdThreads, 8) render_fwd_kernel(ViewK V) {
   __shared__ Stage<BATCH> sm;
   fwd_tile<BATCH>(V, blockIdx.x, sm);
 }
@@ -285,7 +355,7 @@ __device__ __forceinline__ int next_item(int* counter, int* s_item) {
 }
 
 template <int BATCH>
-__global__ void __launch_bounds__(kFwdThreads, 6) render_fwd_persistent(ViewTable T, int total, int* counter) {
+__global__ void __launch_bounds__(kFwdThreads, 8) render_fwd_persistent(ViewTable T, int total, int* counter) {
   __shared__ Stage<BATCH> sm;
   __shared__ int s_item;
   for (int item = next_item(counter, &s_item); item < total; item = next_item(counter, &s_item)) {
