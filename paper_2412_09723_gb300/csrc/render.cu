@@ -14,7 +14,7 @@
 // all of its pixels have reached the transmittance stop.  No atomics.
 //
 // Backward: 128 threads with 2 pixels each ((x, y) and (x, y + 2); a warp
-// covers 16 x 4 pixels).  Every pixel starts from its final transmittance and
+// covers 16 x 4 pixels), again in packed pairs.  Every pixel starts from its final transmittance and
 // last contributor, walks the list back to front and recovers
 // T_i = T_{i+1} / (1 - alpha_i).  With the pixel's upstream gradients folded
 // into one scalar per Gaussian, P_i = gC.c_i + gD z_i + gS, and the weights
@@ -38,8 +38,7 @@
 namespace splat {
 
 constexpr int kFwdThreads = 128;         // forward: two pixels per thread
-constexpr int kBwdThreads = 128;          // backward (batched launch): two pixels per thread
-constexpr int kBwdSinglePPT = 2;          // backward (one view): pixels per thread (4 measured slower)
+constexpr int kBwdThreads = 128;          // backward: two pixels per thread
 constexpr int kGradStride = 12;           // screen-space gradient row (3 float4)
 constexpr int kAccStride = 11;            // shared accumulator row (10 sums, padded)
 constexpr int kMaxViews = SPLAT_MAX_VIEWS;
@@ -274,9 +273,9 @@ __device__ __forceinline__ void composite_step2(FwdPix& q, const float4 xo, cons
   q.used[1] += in1;
 }
 
-// Pixel p (0 or 1) of forward thread t: warp w covers rows 4w .. 4w + 3
+// Pixel p (0 or 1) of thread t (forward and backward): warp w covers rows 4w .. 4w + 3
 // (lanes 0-15 rows 4w and 4w + 2, lanes 16-31 rows 4w + 1 and 4w + 3).
-__device__ __forceinline__ void fwd_pixel(int t, int p, int& lx, int& ly) {
+__device__ __forceinline__ void pair_pixel(int t, int p, int& lx, int& ly) {
   const int lane = t & 31, warp = t >> 5;
   lx = lane & 15;
   ly = 4 * warp + (lane >> 4) + 2 * p;
@@ -287,8 +286,8 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
   const CamK& cam = V.cam;
   const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
   int lx, ly0, ly1;
-  fwd_pixel(threadIdx.x, 0, lx, ly0);
-  fwd_pixel(threadIdx.x, 1, lx, ly1);
+  pair_pixel(threadIdx.x, 0, lx, ly0);
+  pair_pixel(threadIdx.x, 1, lx, ly1);
   const int px = tx * kTile + lx, py0 = ty * kTile + ly0, py1 = ty * kTile + ly1;
   const bool in0 = px < cam.width && py0 < cam.height, in1 = px < cam.width && py1 < cam.height;
   const float fx = (float)px + 0.5f;
@@ -408,48 +407,71 @@ __device__ __forceinline__ int warp_reduce_scatter10(const float (&v)[10], float
   return (!(lane & 1) && i2 < 3 && i1 < 5) ? (b4 ? 5 : 0) + i1 : -1;
 }
 
-struct BwdPix {
-  float fx, fy, T, gC0, gC1, gC2, gD, gS, Q;  // Q = sum_{j>i} w_j P_j + (gC.bg) T_final
-  int last;
+// The thread's two pixels (x, y) and (x, y + 2): they share x, and their
+// arithmetic runs in packed single-precision pairs.  Q = sum_{j>i} w_j P_j +
+// (gC.bg) T_final.
+struct BwdPair {
+  float fx;
+  float2 nfy, T, gC0, gC1, gC2, gD, gS, Q;
+  int last[2];
 };
 
-// Per-pixel adjoint of one list position (back to front).  Accumulates the
-// pixel's share of (sum dp dx, sum dp dy, sum dp dx^2, sum dp dx dy, sum dp
-// dy^2, d opacity, d rgb[3], d depth) into v, dp = dL/d(power).
-__device__ __forceinline__ bool adjoint_step(BwdPix& q, const float4 xo, const float4 qd, float c0, float c1,
-                                             float c2, float (&v)[10]) {
+// Per-pixel adjoint of one list position (back to front) for both pixels of
+// the pair; pixel p takes part when pos < last[p] and the Gaussian passes its
+// exponent, alpha-floor tests (the forward's decisions, same operations).
+// Adds the pair's share of (sum dp dx, sum dp dy, sum dp dx^2, sum dp dx dy,
+// sum dp dy^2, d opacity, d rgb[3], d depth) to v, dp = dL/d(power); returns
+// whether either pixel took part.  A pixel that does not take part keeps T and
+// Q (its weight is 0) and adds nothing (its G and raw opacity are set to 0).
+__device__ __forceinline__ bool adjoint_step2(BwdPair& q, int pos, const float4 xo, const float4 qd, float c0,
+                                              float c1, float c2, float (&v)[10]) {
   const float dx = xo.x - q.fx;
-  const float dy = xo.y - q.fy;
-  const float power = __fmaf_rn(qd.z * dy, dy, dx * __fmaf_rn(qd.x, dx, qd.y * dy));
-  if (power > 0.0f || power < qd.w) return false;
-  const float G = exp_core(power);
-  const float raw = xo.w * G;
-  const float alpha = fminf(kAlphaCap, raw);
-  if (alpha < kAlphaMin) return false;
-  const float om = 1.0f - alpha;
-  const float r = __fdividef(1.0f, om);
-  q.T = q.T * r;  // T_i
-  const float w = alpha * q.T;
-  v[6] = __fmaf_rn(q.gC0, w, v[6]);
-  v[7] = __fmaf_rn(q.gC1, w, v[7]);
-  v[8] = __fmaf_rn(q.gC2, w, v[8]);
-  v[9] = __fmaf_rn(q.gD, w, v[9]);
-  float P = __fmaf_rn(q.gC0, c0, q.gS);
-  P = __fmaf_rn(q.gC1, c1, P);
-  P = __fmaf_rn(q.gC2, c2, P);
-  P = __fmaf_rn(q.gD, xo.z, P);
-  const float dA = __fmaf_rn(q.T, P, -(r * q.Q));
-  q.Q = __fmaf_rn(w, P, q.Q);
-  if (!(raw > kAlphaCap)) {
-    v[5] = __fmaf_rn(G, dA, v[5]);
-    const float dp = raw * dA;
-    const float m1 = dp * dx, m2 = dp * dy;
-    v[0] += m1;
-    v[1] += m2;
-    v[2] = __fmaf_rn(m1, dx, v[2]);
-    v[3] = __fmaf_rn(m1, dy, v[3]);
-    v[4] = __fmaf_rn(m2, dy, v[4]);
-  }
+  const float2 dy = __fadd2_rn(bcast(xo.y), q.nfy);
+  const float2 inner = __ffma2_rn(bcast(qd.x), bcast(dx), __fmul2_rn(bcast(qd.y), dy));
+  const float2 power = __ffma2_rn(__fmul2_rn(bcast(qd.z), dy), dy, __fmul2_rn(bcast(dx), inner));
+  bool in0 = pos < q.last[0] && !(power.x > 0.0f || power.x < qd.w);
+  bool in1 = pos < q.last[1] && !(power.y > 0.0f || power.y < qd.w);
+  if (!(in0 || in1)) return false;
+  const float2 G = exp_core2(power);
+  const float2 raw = __fmul2_rn(bcast(xo.w), G);
+  float2 alpha = make_float2(fminf(kAlphaCap, raw.x), fminf(kAlphaCap, raw.y));
+  in0 = in0 && !(alpha.x < kAlphaMin);
+  in1 = in1 && !(alpha.y < kAlphaMin);
+  if (!(in0 || in1)) return false;
+  alpha.x = in0 ? alpha.x : 0.0f;
+  alpha.y = in1 ? alpha.y : 0.0f;
+  const float2 om = __ffma2_rn(alpha, bcast(-1.0f), bcast(1.0f));
+  const float2 r = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
+  const float2 Tn = __fmul2_rn(q.T, r);  // T_i
+  q.T.x = in0 ? Tn.x : q.T.x;
+  q.T.y = in1 ? Tn.y : q.T.y;
+  const float2 w = __fmul2_rn(alpha, Tn);  // 0 for a pixel that does not take part
+  const float2 t6 = __fmul2_rn(q.gC0, w), t7 = __fmul2_rn(q.gC1, w), t8 = __fmul2_rn(q.gC2, w);
+  const float2 t9 = __fmul2_rn(q.gD, w);
+  v[6] += t6.x + t6.y;
+  v[7] += t7.x + t7.y;
+  v[8] += t8.x + t8.y;
+  v[9] += t9.x + t9.y;
+  float2 P = __ffma2_rn(q.gC0, bcast(c0), q.gS);
+  P = __ffma2_rn(q.gC1, bcast(c1), P);
+  P = __ffma2_rn(q.gC2, bcast(c2), P);
+  P = __ffma2_rn(q.gD, bcast(xo.z), P);
+  const float2 rq = __fmul2_rn(r, q.Q);
+  const float2 dA = __ffma2_rn(Tn, P, make_float2(-rq.x, -rq.y));
+  q.Q = __ffma2_rn(w, P, q.Q);
+  const bool l0 = in0 && !(raw.x > kAlphaCap), l1 = in1 && !(raw.y > kAlphaCap);
+  const float2 Ge = make_float2(l0 ? G.x : 0.0f, l1 ? G.y : 0.0f);
+  const float2 re = make_float2(l0 ? raw.x : 0.0f, l1 ? raw.y : 0.0f);
+  const float2 t5 = __fmul2_rn(Ge, dA);
+  v[5] += t5.x + t5.y;
+  const float2 dp = __fmul2_rn(re, dA);
+  const float2 m1 = __fmul2_rn(dp, bcast(dx)), m2 = __fmul2_rn(dp, dy);
+  const float2 s2 = __fmul2_rn(m1, bcast(dx)), s3 = __fmul2_rn(m1, dy), s4 = __fmul2_rn(m2, dy);
+  v[0] += m1.x + m1.y;
+  v[1] += m2.x + m2.y;
+  v[2] += s2.x + s2.y;
+  v[3] += s3.x + s3.y;
+  v[4] += s4.x + s4.y;
   return true;
 }
 
@@ -460,48 +482,51 @@ struct BwdShared {
   int maxlast;
 };
 
-// Pixel p (0 .. PPT-1) of thread t: warp w covers rows 2 PPT w .. 2 PPT w +
-// 2 PPT - 1 (lanes 0-15 the even rows, lanes 16-31 the odd ones).
-template <int PPT>
-__device__ __forceinline__ void bwd_pixel(int t, int p, int& lx, int& ly) {
-  const int lane = t & 31, warp = t >> 5;
-  lx = lane & 15;
-  ly = 2 * PPT * warp + (lane >> 4) + 2 * p;
-}
-
-template <int BATCH, int PPT>
+template <int BATCH>
 __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BATCH>& sm) {
-  constexpr int NT = kTilePixels / PPT;
+  constexpr int NT = kBwdThreads;
   const CamK& cam = V.cam;
   const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
   const uint2 rg = V.ranges[tile];
-  BwdPix q[PPT];
+  BwdPair q;
+  int lx, ly0, ly1;
+  pair_pixel(threadIdx.x, 0, lx, ly0);
+  pair_pixel(threadIdx.x, 1, lx, ly1);
+  const int x = tx * kTile + lx;
+  q.fx = (float)x + 0.5f;
+  {
+    float f[2][8];
 #pragma unroll
-  for (int p = 0; p < PPT; ++p) {
-    int lx, ly;
-    bwd_pixel<PPT>(threadIdx.x, p, lx, ly);
-    const int x = tx * kTile + lx, y = ty * kTile + ly;
-    const bool inside = x < cam.width && y < cam.height;
-    const size_t i = inside ? (size_t)y * cam.width + x : 0;
-    BwdPix& b = q[p];
-    b.fx = (float)x + 0.5f;
-    b.fy = (float)y + 0.5f;
-    const float Tfin = inside ? V.img.t_final[i] : 1.0f;
-    b.T = Tfin;
-    b.last = inside ? V.img.n_contrib[i] : 0;
-    b.gC0 = inside ? V.d_rgb[3 * i + 0] : 0.f;
-    b.gC1 = inside ? V.d_rgb[3 * i + 1] : 0.f;
-    b.gC2 = inside ? V.d_rgb[3 * i + 2] : 0.f;
-    b.gD = (inside && V.d_depth) ? V.d_depth[i] : 0.f;
-    b.gS = (inside && V.d_sil) ? V.d_sil[i] : 0.f;
-    b.Q = (b.gC0 * V.bg0 + b.gC1 * V.bg1 + b.gC2 * V.bg2) * Tfin;
+    for (int p = 0; p < 2; ++p) {
+      const int y = ty * kTile + (p ? ly1 : ly0);
+      const bool inside = x < cam.width && y < cam.height;
+      const size_t i = inside ? (size_t)y * cam.width + x : 0;
+      const float Tfin = inside ? V.img.t_final[i] : 1.0f;
+      const float g0 = inside ? V.d_rgb[3 * i + 0] : 0.f;
+      const float g1 = inside ? V.d_rgb[3 * i + 1] : 0.f;
+      const float g2 = inside ? V.d_rgb[3 * i + 2] : 0.f;
+      f[p][0] = -((float)y + 0.5f);
+      f[p][1] = Tfin;
+      f[p][2] = g0;
+      f[p][3] = g1;
+      f[p][4] = g2;
+      f[p][5] = (inside && V.d_depth) ? V.d_depth[i] : 0.f;
+      f[p][6] = (inside && V.d_sil) ? V.d_sil[i] : 0.f;
+      f[p][7] = (g0 * V.bg0 + g1 * V.bg1 + g2 * V.bg2) * Tfin;
+      q.last[p] = inside ? V.img.n_contrib[i] : 0;
+    }
+    q.nfy = make_float2(f[0][0], f[1][0]);
+    q.T = make_float2(f[0][1], f[1][1]);
+    q.gC0 = make_float2(f[0][2], f[1][2]);
+    q.gC1 = make_float2(f[0][3], f[1][3]);
+    q.gC2 = make_float2(f[0][4], f[1][4]);
+    q.gD = make_float2(f[0][5], f[1][5]);
+    q.gS = make_float2(f[0][6], f[1][6]);
+    q.Q = make_float2(f[0][7], f[1][7]);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const StagePtrs sp{sm.st.xyzo, sm.st.quad, sm.st.cid, sm.st.wmask};
-  int mylast = 0;
-#pragma unroll
-  for (int p = 0; p < PPT; ++p) mylast = max(mylast, q[p].last);
-  const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)mylast);
+  const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(q.last[0], q.last[1]));
   if (threadIdx.x == 0) sm.maxlast = 0;
   __syncthreads();
   if (lane == 0 && wlast > 0) atomicMax(&sm.maxlast, wlast);
@@ -512,7 +537,7 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
     const int cnt = end - start;
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += NT)
-      stage_one<true>(V, V.vals[rg.x + start + i], i, sp, tx * kTile, ty * kTile, 2 * PPT);
+      stage_one<true>(V, V.vals[rg.x + start + i], i, sp, tx * kTile, ty * kTile, 4);
     for (int i = threadIdx.x; i < BATCH * kAccStride; i += NT) sm.acc[i] = 0.f;
     __syncthreads();
     const int nl = build_warp_list(sm.st.wmask, sm.st.wlist[warp], cnt, warp);
@@ -523,14 +548,10 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
       const float4 xo = sm.st.xyzo[j];
       const float4 qd = sm.st.quad[j];
       const float4 cd = sm.st.cid[j];
-      const float c0 = cd.x, c1 = cd.y, c2 = cd.z;
       float v[10];
 #pragma unroll
       for (int k = 0; k < 10; ++k) v[k] = 0.f;
-      bool any = false;
-#pragma unroll
-      for (int p = 0; p < PPT; ++p)
-        if (pos < q[p].last) any |= adjoint_step(q[p], xo, qd, c0, c1, c2, v);
+      const bool any = adjoint_step2(q, pos, xo, qd, cd.x, cd.y, cd.z, v);
       if (__any_sync(0xffffffffu, any)) {
         float tot;
         const int k = warp_reduce_scatter10(v, tot);
@@ -553,10 +574,10 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
   }
 }
 
-template <int BATCH, int PPT>
-__global__ void __launch_bounds__(kTilePixels / PPT) render_bwd_kernel(ViewK V) {
+template <int BATCH>
+__global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(ViewK V) {
   __shared__ BwdShared<BATCH> sm;
-  bwd_tile<BATCH, PPT>(V, blockIdx.x, sm);
+  bwd_tile<BATCH>(V, blockIdx.x, sm);
 }
 
 template <int BATCH>
@@ -566,7 +587,7 @@ __global__ void __launch_bounds__(kBwdThreads) render_bwd_persistent(ViewTable T
   for (int item = next_item(counter, &s_item); item < total; item = next_item(counter, &s_item)) {
     int tile;
     const int v = view_of(T, item, tile);
-    bwd_tile<BATCH, kTilePixels / kBwdThreads>(T.v[v], tile, sm);
+    bwd_tile<BATCH>(T.v[v], tile, sm);
   }
 }
 
@@ -657,7 +678,7 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
   v.d_sil = d_sil;
   v.g2 = g2;
   SPLAT_LAUNCH("render_bwd_kernel", s,
-               render_bwd_kernel<256, kBwdSinglePPT><<<v.cam.tiles_x * v.cam.tiles_y, kTilePixels / kBwdSinglePPT, 0, s>>>(v));
+               render_bwd_kernel<256><<<v.cam.tiles_x * v.cam.tiles_y, kBwdThreads, 0, s>>>(v));
   if ((rc = check_launch("render_bwd_kernel"))) return rc;
   GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
   GradK gr{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};
