@@ -465,12 +465,13 @@ __device__ __forceinline__ bool adjoint_step2(BwdPair& q, int pos, const float4 
   const float2 t5 = __fmul2_rn(Ge, dA);
   v[5] += t5.x + t5.y;
   const float2 dp = __fmul2_rn(re, dA);
-  const float2 m1 = __fmul2_rn(dp, bcast(dx)), m2 = __fmul2_rn(dp, dy);
-  const float2 s2 = __fmul2_rn(m1, bcast(dx)), s3 = __fmul2_rn(m1, dy), s4 = __fmul2_rn(m2, dy);
-  v[0] += m1.x + m1.y;
-  v[1] += m2.x + m2.y;
-  v[2] += s2.x + s2.y;
-  v[3] += s3.x + s3.y;
+  const float2 m2 = __fmul2_rn(dp, dy);
+  const float2 s4 = __fmul2_rn(m2, dy);
+  const float sx = dx * (dp.x + dp.y), sy = m2.x + m2.y;  // the pair shares dx
+  v[0] += sx;
+  v[1] += sy;
+  v[2] += dx * sx;
+  v[3] += dx * sy;
   v[4] += s4.x + s4.y;
   return true;
 }
