@@ -365,6 +365,11 @@ int splat_adam(float *param, const float *grad, float *m, float *v, int64_t n, c
  * m[g], v[g] are device arrays of sizes[g] floats (host arrays of pointers);
  * lr: host float[n_groups].  With zero_grad != 0 every gradient element is set
  * to 0 after it is consumed, so the next backward can accumulate into it.
+ * Aligned runs of 4 elements whose gradient and both moments are all +0.0
+ * (bit pattern 0) are skipped: their update is exactly nothing (m and v stay
+ * +0, p - 0 = p), so the result is bit for bit that of the full update while
+ * the parameters of Gaussians unseen since their moments were zero are
+ * neither read nor written.
  * Errors: SPLAT_EINVAL (n_groups not in 1..8, null pointer), SPLAT_ECUDA.
  */
 int splat_adam_groups(int32_t n_groups, float *const *params, float *const *grads, float *const *m,

@@ -171,8 +171,17 @@ __global__ void __launch_bounds__(256) adam_groups_kernel(AdamGroups G, int64_t 
     float* V = G.v[k] + j;
     const float lr = G.lr[k];
     if (j + 4 <= size && G.vec[k]) {
-      float4 p4 = *reinterpret_cast<float4*>(P), g4 = *reinterpret_cast<float4*>(Gr);
+      float4 g4 = *reinterpret_cast<float4*>(Gr);
       float4 m4 = *reinterpret_cast<float4*>(M), v4 = *reinterpret_cast<float4*>(V);
+      // Elements whose gradient and moments are all +0 (a Gaussian never seen
+      // since its moments were last zero) have an update of exactly 0: m and v
+      // stay +0, p - 0 = p; their parameters are neither read nor written.
+      const uint32_t any_bits = __float_as_uint(g4.x) | __float_as_uint(g4.y) | __float_as_uint(g4.z) |
+                                __float_as_uint(g4.w) | __float_as_uint(m4.x) | __float_as_uint(m4.y) |
+                                __float_as_uint(m4.z) | __float_as_uint(m4.w) | __float_as_uint(v4.x) |
+                                __float_as_uint(v4.y) | __float_as_uint(v4.z) | __float_as_uint(v4.w);
+      if (any_bits == 0u) continue;
+      float4 p4 = *reinterpret_cast<float4*>(P);
       adam_one(p4.x, g4.x, m4.x, v4.x, lr, b1, b2, bc1, bc2, eps, zero_grad);
       adam_one(p4.y, g4.y, m4.y, v4.y, lr, b1, b2, bc1, bc2, eps, zero_grad);
       adam_one(p4.z, g4.z, m4.z, v4.z, lr, b1, b2, bc1, bc2, eps, zero_grad);

@@ -405,6 +405,43 @@ def test_adam_groups_matches_per_group_adam(dev):
         assert not d[1].any()  # gradients cleared
 
 
+def test_adam_groups_sparse_state(dev):
+    """Most aligned runs of 4 elements have gradient and moments +0 (Gaussians
+    never seen): their parameters stay bit for bit unchanged; runs with a -0,
+    with only moments, or with only a gradient get the full update."""
+    from paper_2412_09723_gb300 import binding as B
+
+    rng = np.random.default_rng(9)
+    n = 4096 + 3
+    h = [rng.normal(size=n).astype(np.float32) for _ in range(4)]
+    h[3] = np.abs(h[3])
+    quiet = rng.random((n + 3) // 4) < 0.7
+    mask = np.repeat(quiet, 4)[:n]
+    for a in (h[1], h[2], h[3]):
+        a[mask] = 0.0
+    live = np.nonzero(~mask)[0]
+    h[1][live[:40]] = 0.0  # moments only
+    h[2][live[40:80]] = 0.0
+    h[3][live[40:80]] = 0.0  # gradient only
+    q = np.nonzero(quiet)[0][:5] * 4  # a -0 gradient in five otherwise quiet runs
+    h[1][q] = np.float32(-0.0)
+    d = [torch.as_tensor(a.copy(), device=dev) for a in h]
+    groups = B.AdamGroups([d[0]], [d[1]], [d[2]], [d[3]], [3e-3])
+    step = torch.tensor([7], dtype=torch.int32, device=dev)
+    B.splat_adam_groups(groups, step, zero_grad=True)
+    torch.cuda.synchronize()
+    rp, rm, rv = oracle.adam(h[0], h[1], h[2], h[3], 7, 3e-3)
+    got = [x.cpu().numpy() for x in d]
+    np.testing.assert_allclose(got[0], rp, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(got[2], rm, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(got[3], rv, rtol=1e-6, atol=1e-7)
+    skipped = mask.copy()
+    skipped[q] = False
+    assert np.array_equal(got[0][skipped].view(np.uint32), h[0][skipped].view(np.uint32))
+    assert not got[1].any()
+    assert not np.signbit(got[1]).any()  # the -0 gradients were consumed and cleared to +0
+
+
 def test_assoc_deep_buckets_and_duplicates(dev):
     """Few distinct ids over many pixels (deep buckets -> merge path) and many
     repeated pairs; pairs and counts must equal the oracle's."""
