@@ -374,123 +374,136 @@ __device__ __forceinline__ bool row_members(const TileTest& t, const int4 r, int
 }
 
 // Visible Gaussians (tiles_touched > 0, a non-empty rect) are appended to
-// vis[] with one atomic per CTA.  Each warp then takes its visible Gaussians
-// one after another, a rect row per lane: the row's member tiles enter the
-// tile counts as +1 / -1 at its ends in a per-row difference array (prefix
-// sums along the rows in tile_scan_kernel give the counts), the duplicate
-// total K is summed (one 64-bit atomic per CTA), and the row's span is kept
-// for the scatter: one 16-bit word per rect row (first and last member as
-// offsets from the rect's left column; 0x00ff for an empty row) in a region
-// reserved with one atomic per warp.  A Gaussian whose rect is wider than 255
-// tiles, or whose rows do not fit the span buffer, gets no spans (vspan =
-// ~0) and the scatter tests its tiles again.
+// vis[] with one atomic per CTA.  A warp takes 128 consecutive Gaussians (4
+// per lane, coalesced), packs its visible ones into slots in shared memory
+// (their rect and membership-test data), and then takes the rect rows of all
+// its slots, one row per lane: the row's member tiles enter the tile counts as
+// +1 / -1 at its ends in a per-row difference array (prefix sums along the
+// rows in tile_scan_kernel give the counts), the duplicate total K is summed
+// (one 64-bit atomic per CTA), and the row's span is kept for the scatter: one
+// 16-bit word per rect row (first and last member as offsets from the rect's
+// left column; 0x00ff for an empty row) in a region reserved with one atomic
+// per warp.  A Gaussian whose rect is wider than 255 tiles, or whose rows do
+// not fit the span buffer, gets no spans (vspan = ~0) and the scatter tests its
+// tiles again.
 constexpr uint32_t kNoSpan = 0xffffffffu;
 constexpr uint16_t kEmptySpan = 0x00ff;
+constexpr int kCcWarps = 4;                // warps per CTA
+constexpr int kCcPer = 4;                  // Gaussians per lane
+constexpr int kCcSlots = 32 * kCcPer;      // Gaussians per warp
+constexpr int kCcThreads = 32 * kCcWarps;
 
-__global__ void __launch_bounds__(256) compact_count_kernel(const int32_t* __restrict__ tiles,
-                                                            const int4* __restrict__ rect,
-                                                            const float4* __restrict__ xyzo,
-                                                            const float4* __restrict__ conic, int64_t n, int gw,
-                                                            uint32_t* __restrict__ vis,
-                                                            unsigned int* __restrict__ n_vis,
-                                                            unsigned long long* __restrict__ k_total,
-                                                            int* __restrict__ diff, uint16_t* __restrict__ spans,
-                                                            uint64_t span_cap,
-                                                            unsigned long long* __restrict__ span_top,
-                                                            uint32_t* __restrict__ vspan) {
-  __shared__ unsigned int s_warp[8];
-  __shared__ unsigned long long s_k[8];
+__global__ void __launch_bounds__(kCcThreads) compact_count_kernel(
+    const int32_t* __restrict__ tiles, const int4* __restrict__ rect, const float4* __restrict__ xyzo,
+    const float4* __restrict__ conic, int64_t n, int gw, uint32_t* __restrict__ vis, unsigned int* __restrict__ n_vis,
+    unsigned long long* __restrict__ k_total, int* __restrict__ diff, uint16_t* __restrict__ spans, uint64_t span_cap,
+    unsigned long long* __restrict__ span_top, uint32_t* __restrict__ vspan) {
+  __shared__ TileTest s_tt[kCcWarps][kCcSlots];
+  __shared__ int4 s_rect[kCcWarps][kCcSlots];
+  __shared__ uint32_t s_row0[kCcWarps][kCcSlots + 1];  // exclusive prefix of the slots' rect heights
+  __shared__ uint32_t s_hx[kCcWarps][kCcSlots];        // exclusive prefix of the span heights, or kNoSpan
+  __shared__ uint32_t s_gid[kCcWarps][kCcSlots];
+  __shared__ unsigned int s_warp[kCcWarps];
+  __shared__ unsigned long long s_k[kCcWarps];
   __shared__ unsigned int s_base;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int tt = i < n ? tiles[i] : 0;
-  const bool v = tt > 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lower = (1u << lane) - 1u;
-  const unsigned ball = __ballot_sync(0xffffffffu, v);
-  if (lane == 0) s_warp[warp] = __popc(ball);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int tot = 0;
-    for (int w = 0; w < 8; ++w) {
-      const unsigned int c = s_warp[w];
-      s_warp[w] = tot;
-      tot += c;
+  const unsigned full = 0xffffffffu, lower = (1u << lane) - 1u;
+  const int64_t w0 = ((int64_t)blockIdx.x * kCcWarps + warp) * kCcSlots;
+  int tt[kCcPer];
+#pragma unroll
+  for (int k = 0; k < kCcPer; ++k) {
+    const int64_t i = w0 + 32 * k + lane;
+    tt[k] = i < n ? tiles[i] : 0;
+  }
+  int nvw = 0;
+#pragma unroll
+  for (int k = 0; k < kCcPer; ++k) {
+    const unsigned b = __ballot_sync(full, tt[k] > 0);
+    if (tt[k] > 0) {
+      const int sl = nvw + __popc(b & lower);
+      const int64_t i = w0 + 32 * k + lane;
+      s_rect[warp][sl] = rect[i];
+      s_tt[warp][sl] = tile_test(xyzo[i], conic[i]);
+      s_gid[warp][sl] = (uint32_t)i;
     }
-    s_base = tot ? atomicAdd(n_vis, tot) : 0u;
-  }
-  __syncthreads();
-  const unsigned int wbase = s_base + s_warp[warp];
-  if (v) vis[wbase + __popc(ball & lower)] = (uint32_t)i;
-  // span region of the warp: its visible Gaussians' rect heights, one atomic
-  int4 rr = make_int4(0, 0, 0, 0);
-  uint32_t h = 0;
-  if (v) {
-    rr = rect[i];
-    h = rr.z - rr.x <= 255 ? (uint32_t)(rr.w - rr.y) : 0u;
-  }
-  uint32_t hx = h;  // exclusive prefix of h over the warp
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, hx, o);
-    if (lane >= o) hx += y;
-  }
-  const uint32_t htot = __shfl_sync(0xffffffffu, hx, 31);
-  hx -= h;
-  unsigned long long sbase = 0;
-  if (lane == 0 && htot) sbase = atomicAdd(span_top, (unsigned long long)htot);
-  sbase = __shfl_sync(0xffffffffu, sbase, 0);
-  const bool fits = sbase + htot <= span_cap;
-  if (v) vspan[wbase + __popc(ball & lower)] = (h && fits) ? (uint32_t)(sbase + hx) : kNoSpan;
-  // the rows of the warp's visible Gaussians, flattened over its lanes: each
-  // lane's Gaussian's test data goes to shared memory, then lane q takes rows
-  // q, q + 32, ... of the concatenation (owner found by binary search)
-  __shared__ TileTest s_tt[8][32];
-  __shared__ int4 s_rect[8][32];
-  __shared__ uint32_t s_row0[8][33];  // exclusive prefix of the visible lanes' rect heights
-  __shared__ uint32_t s_sb[8][32];
-  const uint32_t hr = v ? (uint32_t)(rr.w - rr.y) : 0u;
-  uint32_t rx = hr;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, rx, o);
-    if (lane >= o) rx += y;
-  }
-  const uint32_t rows = __shfl_sync(0xffffffffu, rx, 31);
-  s_row0[warp][lane] = rx - hr;
-  if (lane == 31) s_row0[warp][32] = rows;
-  if (v) {
-    s_tt[warp][lane] = tile_test(xyzo[i], conic[i]);
-    s_rect[warp][lane] = rr;
-    s_sb[warp][lane] = (h && fits) ? (uint32_t)(sbase + hx) : kNoSpan;
+    nvw += __popc(b);
   }
   __syncwarp();
+  // exclusive prefixes over the slots of the rect heights (rows) and of the
+  // span heights (0 for a rect wider than 255 tiles)
+  uint32_t cr = 0, ch = 0;
+  for (int c = 0; c < nvw; c += 32) {
+    const int sl = c + lane;
+    const int4 r = sl < nvw ? s_rect[warp][sl] : make_int4(0, 0, 0, 0);
+    const uint32_t hr = (uint32_t)(r.w - r.y);
+    const uint32_t h = r.z - r.x <= 255 ? hr : 0u;
+    uint32_t xr = hr, xh = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t yr = __shfl_up_sync(full, xr, o), yh = __shfl_up_sync(full, xh, o);
+      if (lane >= o) {
+        xr += yr;
+        xh += yh;
+      }
+    }
+    if (sl < nvw) {
+      s_row0[warp][sl] = cr + xr - hr;
+      s_hx[warp][sl] = h ? ch + xh - h : kNoSpan;
+    }
+    cr += __shfl_sync(full, xr, 31);
+    ch += __shfl_sync(full, xh, 31);
+  }
+  if (lane == 0) {
+    s_row0[warp][nvw] = cr;
+    s_warp[warp] = (unsigned)nvw;
+  }
+  unsigned long long sbase = 0;
+  if (lane == 0 && ch) sbase = atomicAdd(span_top, (unsigned long long)ch);
+  sbase = __shfl_sync(full, sbase, 0);
+  const bool fits = sbase + ch <= span_cap && sbase + ch < (unsigned long long)kNoSpan;
+  __syncwarp();
   unsigned long long t = 0;
-  for (uint32_t q = lane; q < rows; q += 32) {
-    int lo = 0, hi = 31;  // owner: the last lane whose first row is <= q (lanes without rows share it)
+  for (uint32_t q = lane; q < cr; q += 32) {
+    int lo = 0, hi = nvw - 1;  // the last slot whose first row is <= q
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (s_row0[warp][mid] <= q) lo = mid; else hi = mid - 1;
     }
-    while (s_row0[warp][lo + 1] <= q) ++lo;  // skip empty lanes sharing the prefix
+    while (s_row0[warp][lo + 1] <= q) ++lo;  // slots without rows share a prefix (sentinel at nvw)
     const int4 r = s_rect[warp][lo];
     const int ty = r.y + (int)(q - s_row0[warp][lo]);
-    const uint32_t sb = s_sb[warp][lo];
+    const uint32_t hx = s_hx[warp][lo];
     int x0, x1;
     const bool any = row_members(s_tt[warp][lo], r, ty, x0, x1);
-    if (sb != kNoSpan) spans[(size_t)sb + (ty - r.y)] = any ? (uint16_t)((x0 - r.x) | ((x1 - r.x) << 8)) : kEmptySpan;
+    if (hx != kNoSpan && fits)
+      spans[(size_t)(sbase + hx) + (ty - r.y)] = any ? (uint16_t)((x0 - r.x) | ((x1 - r.x) << 8)) : kEmptySpan;
     if (!any) continue;
     atomicAdd(&diff[ty * gw + x0], 1);
     atomicAdd(&diff[ty * gw + x1 + 1], -1);
     t += (unsigned long long)(x1 - x0 + 1);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
   if (lane == 0) s_k[warp] = t;
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned long long k = 0;
-    for (int w = 0; w < 8; ++w) k += s_k[w];
-    if (k) atomicAdd(k_total, k);
+    unsigned int tot = 0;
+    unsigned long long kk = 0;
+    for (int w = 0; w < kCcWarps; ++w) {
+      const unsigned int c = s_warp[w];
+      s_warp[w] = tot;
+      tot += c;
+      kk += s_k[w];
+    }
+    s_base = tot ? atomicAdd(n_vis, tot) : 0u;
+    if (kk) atomicAdd(k_total, kk);
+  }
+  __syncthreads();
+  const unsigned int base = s_base + s_warp[warp];
+  for (int sl = lane; sl < nvw; sl += 32) {
+    vis[base + sl] = s_gid[warp][sl];
+    const uint32_t hx = s_hx[warp][sl];
+    vspan[base + sl] = (hx != kNoSpan && fits) ? (uint32_t)(sbase + hx) : kNoSpan;
   }
 }
 
@@ -781,10 +794,10 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
   const float4* xyzo = reinterpret_cast<const float4*>(proj->xyzo);
   const int4* rect = reinterpret_cast<const int4*>(proj->rect);
   const float4* conic = reinterpret_cast<const float4*>(proj->conic);
-  const int nb = std::max(1, ceil_div(n, 256));
+  const int nb = std::max(1, ceil_div(n, kCcWarps * kCcSlots));
   if (n > 0)
     SPLAT_LAUNCH("compact_count_kernel", s,
-                 compact_count_kernel<<<nb, 256, 0, s>>>(proj->tiles_touched, rect, xyzo, conic, n, ck.tiles_x + 1,
+                 compact_count_kernel<<<nb, kCcThreads, 0, s>>>(proj->tiles_touched, rect, xyzo, conic, n, ck.tiles_x + 1,
                                                          w.vis, w.n_vis, w.k_total, w.diff,
                                                          reinterpret_cast<uint16_t*>(w.skeys2),
                                                          4 * (uint64_t)std::max<int64_t>(capacity, 1), w.span_top,
