@@ -261,6 +261,8 @@ template int radix_sort<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, in
 constexpr int kSegCap = 4096;        // keys a CTA sorts in shared memory (32 KB)
 constexpr int kSortThreads = 256;
 constexpr int kCursorStride = 32;    // one 128-byte line per bucket cursor
+constexpr int kDiffStride = 32;      // one 128-byte line per difference-grid cell: the row-end atomics of all
+                                     // visible Gaussians spread over the L2 slices instead of a few lines
 constexpr int kSmemTiles = 8192;     // tiles whose local counters fit the scatter CTA
 constexpr int kScatterThreads = 256;
 constexpr int kScatterLanes = 4;     // threads sharing one Gaussian's rect (rows interleaved)
@@ -374,13 +376,13 @@ __device__ __forceinline__ bool row_members(const TileTest& t, const int4 r, int
 }
 
 // Visible Gaussians (tiles_touched > 0, a non-empty rect) are appended to
-// vis[] with one atomic per CTA.  A warp takes 128 consecutive Gaussians (4
+// vis[] with one atomic per warp.  A warp takes 128 consecutive Gaussians (4
 // per lane, coalesced), packs its visible ones into slots in shared memory
-// (their rect and membership-test data), and then takes the rect rows of all
-// its slots, one row per lane: the row's member tiles enter the tile counts as
+// (one lane per slot then loads the rect and prepares the membership test),
+// and then takes the rect rows of all its slots, one row per lane: the row's member tiles enter the tile counts as
 // +1 / -1 at its ends in a per-row difference array (prefix sums along the
 // rows in tile_scan_kernel give the counts), the duplicate total K is summed
-// (one 64-bit atomic per CTA), and the row's span is kept for the scatter: one
+// (one 64-bit atomic per warp), and the row's span is kept for the scatter: one
 // 16-bit word per rect row (first and last member as offsets from the rect's
 // left column; 0x00ff for an empty row) in a region reserved with one atomic
 // per warp.  A Gaussian whose rect is wider than 255 tiles, or whose rows do
@@ -403,9 +405,6 @@ __global__ void __launch_bounds__(kCcThreads) compact_count_kernel(
   __shared__ uint32_t s_row0[kCcWarps][kCcSlots + 1];  // exclusive prefix of the slots' rect heights
   __shared__ uint32_t s_hx[kCcWarps][kCcSlots];        // exclusive prefix of the span heights, or kNoSpan
   __shared__ uint32_t s_gid[kCcWarps][kCcSlots];
-  __shared__ unsigned int s_warp[kCcWarps];
-  __shared__ unsigned long long s_k[kCcWarps];
-  __shared__ unsigned int s_base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned full = 0xffffffffu, lower = (1u << lane) - 1u;
   const int64_t w0 = ((int64_t)blockIdx.x * kCcWarps + warp) * kCcSlots;
@@ -419,14 +418,14 @@ __global__ void __launch_bounds__(kCcThreads) compact_count_kernel(
 #pragma unroll
   for (int k = 0; k < kCcPer; ++k) {
     const unsigned b = __ballot_sync(full, tt[k] > 0);
-    if (tt[k] > 0) {
-      const int sl = nvw + __popc(b & lower);
-      const int64_t i = w0 + 32 * k + lane;
-      s_rect[warp][sl] = rect[i];
-      s_tt[warp][sl] = tile_test(xyzo[i], conic[i]);
-      s_gid[warp][sl] = (uint32_t)i;
-    }
+    if (tt[k] > 0) s_gid[warp][nvw + __popc(b & lower)] = (uint32_t)(w0 + 32 * k + lane);
     nvw += __popc(b);
+  }
+  __syncwarp();
+  for (int sl = lane; sl < nvw; sl += 32) {
+    const uint32_t i = s_gid[warp][sl];
+    s_rect[warp][sl] = rect[i];
+    s_tt[warp][sl] = tile_test(xyzo[i], conic[i]);
   }
   __syncwarp();
   // exclusive prefixes over the slots of the rect heights (rows) and of the
@@ -453,13 +452,13 @@ __global__ void __launch_bounds__(kCcThreads) compact_count_kernel(
     cr += __shfl_sync(full, xr, 31);
     ch += __shfl_sync(full, xh, 31);
   }
-  if (lane == 0) {
-    s_row0[warp][nvw] = cr;
-    s_warp[warp] = (unsigned)nvw;
-  }
+  if (lane == 0) s_row0[warp][nvw] = cr;
   unsigned long long sbase = 0;
+  unsigned int base = 0;
   if (lane == 0 && ch) sbase = atomicAdd(span_top, (unsigned long long)ch);
+  if (lane == 0 && nvw) base = atomicAdd(n_vis, (unsigned)nvw);
   sbase = __shfl_sync(full, sbase, 0);
+  base = __shfl_sync(full, base, 0);
   const bool fits = sbase + ch <= span_cap && sbase + ch < (unsigned long long)kNoSpan;
   __syncwarp();
   unsigned long long t = 0;
@@ -478,28 +477,13 @@ __global__ void __launch_bounds__(kCcThreads) compact_count_kernel(
     if (hx != kNoSpan && fits)
       spans[(size_t)(sbase + hx) + (ty - r.y)] = any ? (uint16_t)((x0 - r.x) | ((x1 - r.x) << 8)) : kEmptySpan;
     if (!any) continue;
-    atomicAdd(&diff[ty * gw + x0], 1);
-    atomicAdd(&diff[ty * gw + x1 + 1], -1);
+    atomicAdd(&diff[(size_t)(ty * gw + x0) * kDiffStride], 1);
+    atomicAdd(&diff[(size_t)(ty * gw + x1 + 1) * kDiffStride], -1);
     t += (unsigned long long)(x1 - x0 + 1);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
-  if (lane == 0) s_k[warp] = t;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned int tot = 0;
-    unsigned long long kk = 0;
-    for (int w = 0; w < kCcWarps; ++w) {
-      const unsigned int c = s_warp[w];
-      s_warp[w] = tot;
-      tot += c;
-      kk += s_k[w];
-    }
-    s_base = tot ? atomicAdd(n_vis, tot) : 0u;
-    if (kk) atomicAdd(k_total, kk);
-  }
-  __syncthreads();
-  const unsigned int base = s_base + s_warp[warp];
+  if (lane == 0 && t) atomicAdd(k_total, t);
   for (int sl = lane; sl < nvw; sl += 32) {
     vis[base + sl] = s_gid[warp][sl];
     const uint32_t hx = s_hx[warp][sl];
@@ -520,7 +504,7 @@ __device__ __forceinline__ bool row_span(const uint16_t* __restrict__ spans, uin
 }
 
 // One CTA: prefix sums along the rows of the difference grid (gw = tiles_x + 1
-// cells per row) -> per-tile counts; exclusive scan over tiles -> ranges
+// cells per row, kDiffStride ints apart) -> per-tile counts; exclusive scan over tiles -> ranges
 // (clamped to the capacity) and bucket cursors; K and the status.
 __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff, int tiles_x, int tiles_y,
                                                          const unsigned long long* __restrict__ k_total,
@@ -531,9 +515,12 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
   __shared__ int s_grid[kScanGridSmem];
   const int gw = tiles_x + 1;
   const int cells = gw * tiles_y;
-  int* grid = cells <= kScanGridSmem ? s_grid : diff;  // prefix sums in shared memory when they fit
-  if (grid == s_grid)
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) s_grid[i] = diff[i];
+  // prefix sums in shared memory when they fit, else in place (strided)
+  const bool in_smem = cells <= kScanGridSmem;
+  int* grid = in_smem ? s_grid : diff;
+  const int gs = in_smem ? 1 : kDiffStride;
+  if (in_smem)
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) s_grid[i] = diff[(size_t)i * kDiffStride];
   __syncthreads();
   // prefix sums along each row (one warp per row, 32 cells per warp scan;
   // two's-complement sums, so the negative entries need no special care)
@@ -542,8 +529,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
     uint32_t carry = 0;
     for (int x0 = 0; x0 < tiles_x; x0 += 32) {
       const int x = x0 + lane;
-      const uint32_t v = warp_incl_scan(x < tiles_x ? (uint32_t)grid[y * gw + x] : 0u, lane) + carry;
-      if (x < tiles_x) grid[y * gw + x] = (int)v;
+      const uint32_t v = warp_incl_scan(x < tiles_x ? (uint32_t)grid[(size_t)(y * gw + x) * gs] : 0u, lane) + carry;
+      if (x < tiles_x) grid[(size_t)(y * gw + x) * gs] = (int)v;
       carry = __shfl_sync(0xffffffffu, v, 31);
     }
   }
@@ -553,7 +540,7 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
   uint32_t carry = 0;
   for (int base = 0; base < n_tiles; base += 1024) {
     const int t = base + threadIdx.x;
-    const uint32_t c = t < n_tiles ? (uint32_t)grid[(t / tiles_x) * gw + (t % tiles_x)] : 0u;
+    const uint32_t c = t < n_tiles ? (uint32_t)grid[(size_t)((t / tiles_x) * gw + (t % tiles_x)) * gs] : 0u;
     uint32_t excl;
     const uint32_t tot = block_excl_scan<1024>(c, excl, sh);
     if (t < n_tiles) {
@@ -730,7 +717,7 @@ static size_t carve_bin_ws(int64_t n, int64_t tiles_x, int64_t tiles_y, int64_t 
   t.vis = (uint32_t*)take(4 * nn);
   t.vspan = (uint32_t*)take(4 * nn);
   t.cursor = (uint32_t*)take(4 * kCursorStride * nt);
-  t.diff = (int*)take(4 * (size_t)(tiles_x + 1) * (tiles_y + 1));
+  t.diff = (int*)take(4 * (size_t)kDiffStride * (tiles_x + 1) * (tiles_y + 1));
   t.skeys = (uint64_t*)take(8 * cc);
   t.skeys2 = (uint64_t*)take(8 * cc);
   t.k_total = (unsigned long long*)take(8);
@@ -785,7 +772,7 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
       attr_done.fetch_or(bit);
     }
   }
-  const size_t diff_bytes = sizeof(int) * (size_t)(ck.tiles_x + 1) * (ck.tiles_y + 1);
+  const size_t diff_bytes = sizeof(int) * (size_t)kDiffStride * (ck.tiles_x + 1) * (ck.tiles_y + 1);
   if (cudaMemsetAsync(w.diff, 0, diff_bytes, s) != cudaSuccess ||
       cudaMemsetAsync(w.k_total, 0, sizeof(unsigned long long), s) != cudaSuccess ||
       cudaMemsetAsync(w.span_top, 0, sizeof(unsigned long long), s) != cudaSuccess ||
