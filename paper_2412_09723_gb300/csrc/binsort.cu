@@ -642,9 +642,10 @@ __global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(
 }
 
 // One CTA per tile: sort its bucket ascending by (depth bits, id) and write
-// the ids (and optionally the (tile, depth) keys).  Buckets of up to 256 keys
-// are bitonic-sorted; longer ones go through the shared-memory radix sort
-// (chunks of kSegCap keys, merged in global memory above that).  Dynamic
+// the ids (and optionally the (tile, depth) keys).  Buckets of up to 32 keys
+// are bitonic-sorted; longer ones are bucket-sorted on the depth range in
+// shared memory, or radix-sorted when the depths cluster (chunks of kSegCap
+// keys, merged in global memory above that).  Dynamic
 // shared memory: two key buffers of kSegCap, 8 x 256 digit counters, scan
 // scratch.
 // Shared memory of a tile sort with CAP keys per shared-memory pass.
@@ -652,7 +653,7 @@ template <int CAP>
 constexpr size_t sort_smem_bytes() {
   return 2 * sizeof(uint64_t) * CAP + sizeof(uint32_t) * (kSegRadixWarps * 256 + 64);
 }
-constexpr int kSortBitonicMax = 256;
+constexpr int kSortBitonicMax = 32;
 
 template <int CAP>
 __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint2* __restrict__ ranges,
@@ -676,6 +677,7 @@ __global__ void __launch_bounds__(kSortThreads) tile_sort_kernel(const uint2* __
     }
     for (int i = threadIdx.x; i < m; i += kSortThreads) bufa[i] = src[i];
     __syncthreads();
+    if (uint64_t* r = cta_bucket_sort_hi32(bufa, bufb, m, cnt, sh)) return r;
     return cta_radix_sort_hi32(bufa, bufb, m, cnt, sh);
   };
   const uint64_t* sorted;

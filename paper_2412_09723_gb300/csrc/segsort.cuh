@@ -315,6 +315,92 @@ __device__ __forceinline__ uint64_t* cta_radix_sort_hi32(uint64_t* a, uint64_t* 
   return src;
 }
 
+// Bucket sort by the high word's value range: the high words h are mapped
+// linearly onto `bins` buckets, d = (h - min h) >> s (bins a power of two
+// between 2n and kBucketBins, s the smallest shift that fits the range), a
+// counting pass places every key of a[0, n) in its bucket of b (the order
+// inside a bucket comes from shared atomics), and one thread per bucket
+// insertion-sorts it by the full key.  The keys are distinct, so the result is
+// the ascending order whatever the atomics did.  Returns b, or nullptr
+// (uniformly over the CTA, a untouched) when a bucket would hold more than
+// kBucketMax keys -- clustered depths, which the radix sort handles.
+// cnt: kBucketBins counters; sh: 64 words.  All threads of the CTA.
+constexpr int kBucketMax = 16;
+constexpr int kBucketBins = kSegRadixWarps * 256;
+
+__device__ __forceinline__ uint64_t* cta_bucket_sort_hi32(const uint64_t* a, uint64_t* b, int n, uint32_t* cnt,
+                                                          uint32_t* sh) {
+  const unsigned full = 0xffffffffu;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint32_t mn = 0xffffffffu, mx = 0u;
+  for (int i = t; i < n; i += kSegRadixThreads) {
+    const uint32_t h = (uint32_t)(a[i] >> 32);
+    mn = min(mn, h);
+    mx = max(mx, h);
+  }
+  mn = __reduce_min_sync(full, mn);
+  mx = __reduce_max_sync(full, mx);
+  if (lane == 0) {
+    sh[warp] = mn;
+    sh[kSegRadixWarps + warp] = mx;
+  }
+  const int bins = min(kBucketBins, max(32, next_pow2(2 * n)));
+  const int lb = 31 - __clz(bins);
+  for (int i = t; i < bins; i += kSegRadixThreads) cnt[i] = 0u;
+  __syncthreads();
+  for (int w = 0; w < kSegRadixWarps; ++w) {
+    mn = min(mn, sh[w]);
+    mx = max(mx, sh[kSegRadixWarps + w]);
+  }
+  const uint32_t rng = mx - mn;
+  const int width = rng ? 32 - __clz(rng) : 0;
+  const int sft = max(0, width - lb);
+  for (int i = t; i < n; i += kSegRadixThreads) atomicAdd(&cnt[((uint32_t)(a[i] >> 32) - mn) >> sft], 1u);
+  __syncthreads();
+  const int per = max(1, bins / kSegRadixThreads);  // consecutive buckets per thread
+  const int b0 = t * per;
+  uint32_t loc = 0u, bmax = 0u;
+  for (int k = 0; k < per; ++k)
+    if (b0 + k < bins) {
+      const uint32_t c = cnt[b0 + k];
+      loc += c;
+      bmax = max(bmax, c);
+    }
+  bmax = __reduce_max_sync(full, bmax);
+  if (lane == 0) sh[40 + warp] = bmax;
+  uint32_t ex;
+  block_excl_scan<kSegRadixThreads>(loc, ex, sh);  // its barriers also publish sh[40 ..]
+  uint32_t gmax = 0u;
+  for (int w = 0; w < kSegRadixWarps; ++w) gmax = max(gmax, sh[40 + w]);
+  if (gmax > (uint32_t)kBucketMax) return nullptr;
+  for (int k = 0; k < per; ++k)
+    if (b0 + k < bins) {
+      const uint32_t c = cnt[b0 + k];
+      cnt[b0 + k] = ex;
+      ex += c;
+    }
+  __syncthreads();
+  for (int i = t; i < n; i += kSegRadixThreads) {
+    const uint64_t key = a[i];
+    b[atomicAdd(&cnt[((uint32_t)(key >> 32) - mn) >> sft], 1u)] = key;
+  }
+  __syncthreads();
+  for (int d = t; d < bins; d += kSegRadixThreads) {  // bucket d now spans [end of d - 1, end of d)
+    const int lo = d ? (int)cnt[d - 1] : 0, hi = (int)cnt[d];
+    for (int x = lo + 1; x < hi; ++x) {
+      const uint64_t k = b[x];
+      int y = x - 1;
+      while (y >= lo && b[y] > k) {
+        b[y + 1] = b[y];
+        --y;
+      }
+      b[y + 1] = k;
+    }
+  }
+  __syncthreads();
+  return b;
+}
+
 // Number of elements of the sorted run r[0, m) that are < key (or <= key).
 __device__ __forceinline__ int rank_lt(const uint64_t* r, int m, uint64_t key) {
   int lo = 0, hi = m;
