@@ -80,6 +80,8 @@ class Agent:
         self.assoc_status = self._acc[7:8].view(torch.int32)
         self.assoc_ws = torch.empty(max(1, B.splat_assoc_workspace_size(npix)), dtype=torch.uint8, device=device)
         self.side = torch.cuda.Stream(device=device)  # the association runs here, beside the backward chain
+        self.host_in = None  # pinned (rgb, depth) the step copies its observation from, or None
+        self.host_out = None  # pinned (loss, w2c) the step writes its results to, or None
         self.cg = B.gaussians_struct(*self.params)
         self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads))
         self.steps_done = 0
@@ -100,6 +102,28 @@ class Agent:
                 self.obs_id.copy_(ids, non_blocking=True)
             if t_final is not None:
                 self.obs_tfinal.copy_(t_final, non_blocking=True)
+
+    def attach_host_io(self, rgb=None, depth=None, loss=None, w2c=None):
+        """Pinned host buffers that the step itself reads its observation from
+        (rgb [H, W, 3], depth [H, W]) and writes its loss [1] and pose [4, 4]
+        to, every step and also inside a captured graph: put the next frame in
+        `rgb` / `depth` before a step, read `loss` / `w2c` after synchronising.
+        The frame's copy runs on the side stream and overlaps the projection,
+        binning and forward render; only the loss waits for it.  Calling it
+        with no arguments detaches the buffers.  A graph captured before must
+        be captured again."""
+        H, W = self.cam.height, self.cam.width
+        want = ((rgb, (H, W, 3)), (depth, (H, W)), (loss, (1,)), (w2c, (4, 4)))
+        for t, shape in want:
+            if t is None:
+                continue
+            if t.device.type != "cpu" or not t.is_pinned() or t.dtype != torch.float32 or tuple(t.shape) != shape:
+                raise ValueError(f"host buffers must be pinned float32 CPU tensors of shape {shape}")
+        if (rgb is None) != (depth is None) or (loss is None) != (w2c is None):
+            raise ValueError("attach rgb with depth, and loss with w2c")
+        self.host_in = (rgb, depth) if rgb is not None else None
+        self.host_out = (loss, w2c) if loss is not None else None
+        self.graph = None
 
     def render_observation_from(self, w2c_obs, stream=None):
         """Render the map from `w2c_obs` into the observation buffers (used to
@@ -161,18 +185,25 @@ class Agent:
         fb = self.fb
         B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cgr, self.d_pose, None, s)
 
-    def phase_update(self, s, assoc: bool = True):
+    def phase_update(self, s, assoc: bool = True, pose_stream=None):
+        """Adam on the map and the pose step (on `pose_stream` when given: the
+        two are independent once the projection adjoint is done), then the
+        association when `assoc`."""
         cfg = self.cfg
         self.steps_done += 1
         with torch.cuda.stream(s):
             self.t_dev.add_(1)
         t = self.t_dev
+        if cfg.track:
+            ps = s
+            if pose_stream is not None:
+                pose_stream.wait_stream(s)
+                ps = pose_stream
+            B.splat_pose_step(self.w2c, self.d_pose, self.pose_m, self.pose_v, t, cfg.pose_lr[0], cfg.pose_lr[1],
+                              stream=ps)
         if cfg.map:
             B.splat_adam_groups(self.adam, t, zero_grad=True, stream=s)
             self.grads_clean = True
-        if cfg.track:
-            B.splat_pose_step(self.w2c, self.d_pose, self.pose_m, self.pose_v, t, cfg.pose_lr[0], cfg.pose_lr[1],
-                              stream=s)
         if assoc:
             self.phase_assoc(s)
 
@@ -187,20 +218,30 @@ class Agent:
 
     def step(self, stream=None, sync_check: bool = False):
         """One step.  The association depends only on the forward render, so it
-        runs on a side stream forked after the loss and joined at the end,
-        overlapping the backward render, the projection adjoint and the
-        updates."""
+        runs on a side stream forked after the loss, overlapping the backward
+        render and the projection adjoint; the pose step follows it there,
+        beside the map's Adam; the side stream is joined at the end."""
         s = torch.cuda.current_stream() if stream is None else stream
+        if self.host_in is not None:  # the frame arrives while the map is projected, binned and rendered
+            self.side.wait_stream(s)
+            with torch.cuda.stream(self.side):
+                self.obs_rgb.copy_(self.host_in[0], non_blocking=True)
+                self.obs_depth.copy_(self.host_in[1], non_blocking=True)
         self.phase_pre(s, sync_check)
         self.phase_render(s)
+        if self.host_in is not None:
+            s.wait_stream(self.side)
         self.phase_loss(s)
         if self.cfg.assoc:
             self.side.wait_stream(s)
             self.phase_assoc(self.side)
         self.phase_backward(s)
-        self.phase_update(s, assoc=False)
-        if self.cfg.assoc:
-            s.wait_stream(self.side)
+        self.phase_update(s, assoc=False, pose_stream=self.side)
+        s.wait_stream(self.side)
+        if self.host_out is not None:
+            with torch.cuda.stream(s):
+                self.host_out[0].copy_(self.loss, non_blocking=True)
+                self.host_out[1].copy_(self.w2c, non_blocking=True)
 
     def view(self):
         """C descriptor of this agent's view for the batched render calls."""

@@ -6,9 +6,9 @@ One batched step:
   all agents, ONE persistent launch:  forward render   (splat_render_fwd_batch)
   per agent, on its own stream:  L1 loss
   all agents, ONE persistent launch:  backward render  (splat_render_bwd_batch)
-  per agent, on its own stream:  projection adjoint, Adam, pose step
+  per agent, on its own stream:  projection adjoint, Adam
   per agent, on a side stream forked after the loss:  association (overlaps
-  the backward launch and the updates, joined at the end)
+  the backward launch), then the pose step beside Adam; joined at the end
 The whole step is captured into one CUDA graph (the per-agent streams are
 forked from and joined back into the capture stream), so a replay is a single
 host call.  The persistent launches' execution shape (shared-memory batch of
@@ -64,7 +64,7 @@ class MultiAgentBatch:
             a.side.wait_stream(s)
             a.phase_assoc(a.side)
         B.splat_render_bwd_batch(self.views, self.shape, self.ws, s)
-        self._fork(s, lambda a, st: (a.phase_project_backward(st), a.phase_update(st, assoc=False)))
+        self._fork(s, lambda a, st: (a.phase_project_backward(st), a.phase_update(st, assoc=False, pose_stream=a.side)))
         for a in self.agents:
             s.wait_stream(a.side)
 

@@ -45,6 +45,41 @@ def test_graph_replay_equals_eager_step(dev):
     assert torch.equal(a.pairs[: int(a.m_dev.item())], b.pairs[: int(b.m_dev.item())])
 
 
+def test_host_io_inside_the_captured_step(dev):
+    """With pinned host buffers attached, the captured step copies its frame in
+    and its loss and pose out: the same results as set_observation + step, and
+    a new frame placed in the buffer is the one the next replay uses (no map
+    or pose update, so that every frame renders the same map bit for bit)."""
+    a = _agent(dev, map=False, track=False)
+    b = _agent(dev, map=False, track=False)
+    H, W = a.cam.height, a.cam.width
+    rng = np.random.default_rng(4)
+    frames = [(torch.as_tensor(rng.uniform(0, 1, (H, W, 3)).astype(np.float32)).pin_memory(),
+               torch.as_tensor(rng.uniform(1, 3, (H, W)).astype(np.float32)).pin_memory()) for _ in range(2)]
+    h_rgb = torch.empty(H, W, 3).pin_memory()
+    h_depth = torch.empty(H, W).pin_memory()
+    h_loss = torch.empty(1).pin_memory()
+    h_pose = torch.empty(4, 4).pin_memory()
+    b.attach_host_io(h_rgb, h_depth, h_loss, h_pose)
+    h_rgb.copy_(frames[0][0])
+    h_depth.copy_(frames[0][1])
+    b.capture(keep_state=True)
+    for rgb, depth in frames:
+        a.set_observation(rgb.to(dev), depth.to(dev))
+        a.step()
+        h_rgb.copy_(rgb)
+        h_depth.copy_(depth)
+        b.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(a.obs_rgb, b.obs_rgb) and torch.equal(a.obs_depth, b.obs_depth)
+        for k in ("rgb", "depth", "t_final", "max_id"):
+            assert torch.equal(a.fb.image[k], b.fb.image[k]), k
+        assert float(h_loss[0]) == pytest.approx(float(a.loss.item()), rel=1e-5)
+        np.testing.assert_allclose(h_pose.numpy(), a.w2c.cpu().numpy(), atol=1e-6)
+    with pytest.raises(ValueError):
+        b.attach_host_io(torch.empty(H, W, 3), h_depth)  # not pinned
+
+
 def test_tracking_reduces_pose_error(dev):
     """40 tracking + mapping steps from a pose 1 cm / 0.5 degree off the pose
     that rendered the target: the loss falls and the pose moves toward it."""
