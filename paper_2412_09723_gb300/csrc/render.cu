@@ -21,11 +21,12 @@
 // w_j = alpha_j T_j, every later weight carries a factor (1 - alpha_i), so
 // dL/dalpha_i = T_i P_i - [sum_{j>i} w_j P_j + (gC.bg) T_final] / (1 - alpha_i);
 // the bracket is one running sum per pixel (started at (gC.bg) T_final).
-// Per Gaussian and warp, ten sums are reduced with a recursive-halving
-// reduce-scatter (five moments of dL/dpower -- sum dp dx, dp dy, dp dx^2,
-// dp dx dy, dp dy^2 -- whose conic terms are applied once per Gaussian, plus
-// d opacity, d rgb, d depth), collected per CTA in shared memory and added to
-// global memory with three float4 atomics per Gaussian per CTA.
+// Per Gaussian and warp, ten sums (five moments of dL/dpower -- sum dp dx,
+// dp dy, dp dx^2, dp dx dy, dp dy^2 -- whose conic terms are applied once per
+// Gaussian, plus d opacity, d rgb, d depth) are reduced through a per-warp
+// shared-memory transpose (each lane writes its column, two lanes add one row
+// with 16-byte loads and packed adds), collected per CTA in shared memory and
+// added to global memory with three float4 atomics per Gaussian per CTA.
 //
 // Persistent launches: a grid of (CTAs per SM) x (SMs) CTAs takes (view, tile)
 // work items from one atomic ticket counter until the items run out; no CTA
@@ -41,6 +42,7 @@ constexpr int kFwdThreads = 128;         // forward: two pixels per thread
 constexpr int kBwdThreads = 128;          // backward: two pixels per thread
 constexpr int kGradStride = 12;           // screen-space gradient row (3 float4)
 constexpr int kAccStride = 11;            // shared accumulator row (10 sums, padded)
+constexpr int kRedRow = 36;               // transposed-reduction row: 32 lanes + 4 (rows start in different banks)
 constexpr int kMaxViews = SPLAT_MAX_VIEWS;
 
 struct ImageK {
@@ -367,46 +369,6 @@ __global__ void __launch_bounds__(kFwdThreads, 8) render_fwd_persistent(ViewTabl
 // ----------------------------------------------------------------------------
 // Backward
 // ----------------------------------------------------------------------------
-// Sums v[0..9] over the 32 lanes of a warp by recursive halving: at each of
-// the first four levels a lane keeps half of its values and sends the other
-// half to its partner, so every lane ends up with one total.  Returns the
-// index of the value whose warp total `out` holds, or -1 for lanes that hold
-// a duplicate or a padding slot.
-__device__ __forceinline__ int warp_reduce_scatter10(const float (&v)[10], float& out) {
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-  float w[6];
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const float send = b4 ? v[k] : v[5 + k];
-    const float keep = b4 ? v[5 + k] : v[k];
-    w[k] = keep + __shfl_xor_sync(full, send, 16);
-  }
-  w[5] = 0.f;
-  float x[4];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float send = b3 ? w[k] : w[3 + k];
-    const float keep = b3 ? w[3 + k] : w[k];
-    x[k] = keep + __shfl_xor_sync(full, send, 8);
-  }
-  x[3] = 0.f;
-  float y[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float send = b2 ? x[k] : x[2 + k];
-    const float keep = b2 ? x[2 + k] : x[k];
-    y[k] = keep + __shfl_xor_sync(full, send, 4);
-  }
-  float z = (b1 ? y[1] : y[0]) + __shfl_xor_sync(full, b1 ? y[0] : y[1], 2);
-  z += __shfl_xor_sync(full, z, 1);
-  out = z;
-  const int i2 = (b2 ? 2 : 0) + (b1 ? 1 : 0);
-  const int i1 = (b3 ? 3 : 0) + i2;
-  return (!(lane & 1) && i2 < 3 && i1 < 5) ? (b4 ? 5 : 0) + i1 : -1;
-}
-
 // The thread's two pixels (x, y) and (x, y + 2): they share x, and their
 // arithmetic runs in packed single-precision pairs.  Q = sum_{j>i} w_j P_j +
 // (gC.bg) T_final.
@@ -480,6 +442,7 @@ template <int BATCH>
 struct BwdShared {
   Stage<BATCH> st;
   float acc[BATCH * kAccStride];
+  __align__(16) float red[kBwdThreads / 32][10 * kRedRow];  // per warp: the lanes' 10 sums, transposed
   int maxlast;
 };
 
@@ -554,9 +517,25 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
       for (int k = 0; k < 10; ++k) v[k] = 0.f;
       const bool any = adjoint_step2(q, pos, xo, qd, cd.x, cd.y, cd.z, v);
       if (__any_sync(0xffffffffu, any)) {
-        float tot;
-        const int k = warp_reduce_scatter10(v, tot);
-        if (k >= 0 && tot != 0.f) atomicAdd(&sm.acc[j * kAccStride + k], tot);
+        // warp sums of the 10 values through shared memory: lane writes its
+        // column, lanes 2k and 2k + 1 each add one half of row k (four
+        // 16-byte loads, a packed-pair tree) and combine by one shuffle
+        float* rb = sm.red[warp];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) rb[k * kRedRow + lane] = v[k];
+        __syncwarp();
+        const int k = min(lane >> 1, 9);
+        const float4* src = reinterpret_cast<const float4*>(rb + k * kRedRow + 16 * (lane & 1));
+        const float4 a0 = src[0], a1 = src[1], a2 = src[2], a3 = src[3];
+        const float2 s0 = __fadd2_rn(make_float2(a0.x, a0.y), make_float2(a0.z, a0.w));
+        const float2 s1 = __fadd2_rn(make_float2(a1.x, a1.y), make_float2(a1.z, a1.w));
+        const float2 s2 = __fadd2_rn(make_float2(a2.x, a2.y), make_float2(a2.z, a2.w));
+        const float2 s3 = __fadd2_rn(make_float2(a3.x, a3.y), make_float2(a3.z, a3.w));
+        const float2 s4 = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
+        float tot = s4.x + s4.y;
+        tot += __shfl_xor_sync(0xffffffffu, tot, 1);
+        __syncwarp();  // the buffer is rewritten at the next visit
+        if (lane < 20 && !(lane & 1) && tot != 0.f) atomicAdd(&sm.acc[j * kAccStride + k], tot);
       }
     }
     __syncthreads();
@@ -679,7 +658,7 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
   v.d_sil = d_sil;
   v.g2 = g2;
   SPLAT_LAUNCH("render_bwd_kernel", s,
-               render_bwd_kernel<256><<<v.cam.tiles_x * v.cam.tiles_y, kBwdThreads, 0, s>>>(v));
+               render_bwd_kernel<128><<<v.cam.tiles_x * v.cam.tiles_y, kBwdThreads, 0, s>>>(v));
   if ((rc = check_launch("render_bwd_kernel"))) return rc;
   GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
   GradK gr{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};
