@@ -719,12 +719,13 @@ static size_t carve_bin_ws(int64_t n, int64_t tiles_x, int64_t tiles_y, int64_t 
   t.vis = (uint32_t*)take(4 * nn);
   t.vspan = (uint32_t*)take(4 * nn);
   t.cursor = (uint32_t*)take(4 * kCursorStride * nt);
+  // the difference grid and the three counters are contiguous: one memset clears them
   t.diff = (int*)take(4 * (size_t)kDiffStride * (tiles_x + 1) * (tiles_y + 1));
-  t.skeys = (uint64_t*)take(8 * cc);
-  t.skeys2 = (uint64_t*)take(8 * cc);
   t.k_total = (unsigned long long*)take(8);
   t.span_top = (unsigned long long*)take(8);
   t.n_vis = (unsigned int*)take(8);
+  t.skeys = (uint64_t*)take(8 * cc);
+  t.skeys2 = (uint64_t*)take(8 * cc);
   if (w) *w = t;
   return off;
 }
@@ -774,11 +775,8 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
       attr_done.fetch_or(bit);
     }
   }
-  const size_t diff_bytes = sizeof(int) * (size_t)kDiffStride * (ck.tiles_x + 1) * (ck.tiles_y + 1);
-  if (cudaMemsetAsync(w.diff, 0, diff_bytes, s) != cudaSuccess ||
-      cudaMemsetAsync(w.k_total, 0, sizeof(unsigned long long), s) != cudaSuccess ||
-      cudaMemsetAsync(w.span_top, 0, sizeof(unsigned long long), s) != cudaSuccess ||
-      cudaMemsetAsync(w.n_vis, 0, sizeof(unsigned int), s) != cudaSuccess)
+  const size_t clear_bytes = (size_t)(reinterpret_cast<char*>(w.n_vis) - reinterpret_cast<char*>(w.diff)) + 8;
+  if (cudaMemsetAsync(w.diff, 0, clear_bytes, s) != cudaSuccess)
     return fail(SPLAT_ECUDA, "splat_bin_sort: memset failed");
   const float4* xyzo = reinterpret_cast<const float4*>(proj->xyzo);
   const int4* rect = reinterpret_cast<const int4*>(proj->rect);

@@ -52,6 +52,42 @@ __device__ __forceinline__ void project_math(const float* __restrict__ mean,
           cam.maxd2)
     return;  // outside the selection distance
   for (int k = 0; k < 3; ++k) m.s[k] = exp_full(log_scale[k]);
+  const float z = m.p[2];
+  const float lim_x = kClip * ((float)cam.width / (2.0f * cam.fx));
+  const float lim_y = kClip * ((float)cam.height / (2.0f * cam.fy));
+  const float txz = m.p[0] / z;
+  const float tyz = m.p[1] / z;
+  m.clamp_x = !(txz >= -lim_x && txz <= lim_x);
+  m.clamp_y = !(tyz >= -lim_y && tyz <= lim_y);
+  m.tx = fminf(lim_x, fmaxf(-lim_x, txz)) * z;
+  m.ty = fminf(lim_y, fmaxf(-lim_y, tyz)) * z;
+  const float zz = z * z;
+  m.J00 = cam.fx / z;
+  m.J02 = -(cam.fx * m.tx) / zz;
+  m.J11 = cam.fy / z;
+  m.J12 = -(cam.fy * m.ty) / zz;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    m.Tm[j] = m.J00 * W[j] + m.J02 * W[8 + j];
+    m.Tm[3 + j] = m.J11 * W[4 + j] + m.J12 * W[8 + j];
+  }
+  m.u = cam.fx * txz + cam.cx;
+  m.v = cam.fy * tyz + cam.cy;
+  {
+    // Centre cull, conservative: the largest eigenvalue of the screen
+    // covariance Tm Sigma Tm^T + 0.3 I is at most |Tm|_F^2 s_max^2 + 0.3, so
+    // the 3-sigma radius is at most rb (0.1% and 2 px above, far beyond the
+    // rounding of the exact radius); a centre more than rb outside the tile
+    // grid gives an empty rect, exactly what the full computation below would
+    // find.  The rest is skipped for such Gaussians.
+    float f2 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) f2 += m.Tm[j] * m.Tm[j];
+    const float smax = fmaxf(m.s[0], fmaxf(m.s[1], m.s[2]));
+    const float rb = 3.0f * sqrtf((f2 * (smax * smax) + kLowPass) * 1.001f) + 2.0f;
+    const float gxp = (float)(kTile * cam.tiles_x), gyp = (float)(kTile * cam.tiles_y);
+    if (m.u + rb < 0.0f || m.u - rb >= gxp || m.v + rb < 0.0f || m.v - rb >= gyp) return;
+  }
   const float4 q = *reinterpret_cast<const float4*>(quat);
   const float n2 = ((q.x * q.x + q.y * q.y) + q.z * q.z) + q.w * q.w;
   if (n2 == 0.0f) {
@@ -82,25 +118,6 @@ __device__ __forceinline__ void project_math(const float* __restrict__ mean,
     for (int j = 0; j < 3; ++j)
       m.Sig[3 * i + j] = (m.M[3 * i] * m.M[3 * j] + m.M[3 * i + 1] * m.M[3 * j + 1]) +
                          m.M[3 * i + 2] * m.M[3 * j + 2];
-  const float z = m.p[2];
-  const float lim_x = kClip * ((float)cam.width / (2.0f * cam.fx));
-  const float lim_y = kClip * ((float)cam.height / (2.0f * cam.fy));
-  const float txz = m.p[0] / z;
-  const float tyz = m.p[1] / z;
-  m.clamp_x = !(txz >= -lim_x && txz <= lim_x);
-  m.clamp_y = !(tyz >= -lim_y && tyz <= lim_y);
-  m.tx = fminf(lim_x, fmaxf(-lim_x, txz)) * z;
-  m.ty = fminf(lim_y, fmaxf(-lim_y, tyz)) * z;
-  const float zz = z * z;
-  m.J00 = cam.fx / z;
-  m.J02 = -(cam.fx * m.tx) / zz;
-  m.J11 = cam.fy / z;
-  m.J12 = -(cam.fy * m.ty) / zz;
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    m.Tm[j] = m.J00 * W[j] + m.J02 * W[8 + j];
-    m.Tm[3 + j] = m.J11 * W[4 + j] + m.J12 * W[8 + j];
-  }
   float U[6];
 #pragma unroll
   for (int a2 = 0; a2 < 2; ++a2)
@@ -116,8 +133,6 @@ __device__ __forceinline__ void project_math(const float* __restrict__ mean,
   m.cc = s11 + kLowPass;
   m.det = m.ca * m.cc - m.cb * m.cb;
   if (!(m.det > 0.0f)) return;
-  m.u = cam.fx * txz + cam.cx;
-  m.v = cam.fy * tyz + cam.cy;
   const float mid = 0.5f * (m.ca + m.cc);
   const float disc = mid * mid - m.det;
   const float lmax = mid + sqrtf(fmaxf(disc, 0.0f));
