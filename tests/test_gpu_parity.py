@@ -102,6 +102,35 @@ def test_project_bit_exact(dev, case):
         assert np.array_equal(got[k], ref[k]), k
 
 
+def test_project_off_screen_centres_bit_exact(dev):
+    """Centres in a band around the image border, large anisotropic splats:
+    many Gaussians reach into the image from outside (and many do not), so the
+    projection's conservative centre cull is exercised on both sides of its
+    bound; every field must equal the oracle's."""
+    rng = np.random.default_rng(17)
+    n = 20000
+    cam = scenes.Camera(200, 150, 120.0, 120.0, 100.0, 75.0)
+    z = rng.uniform(0.5, 4.0, n)
+    u = rng.uniform(-150.0, 350.0, n)
+    v = rng.uniform(-150.0, 300.0, n)
+    mean = np.stack([(u - cam.cx) * z / cam.fx, (v - cam.cy) * z / cam.fy, z], 1)
+    ls = rng.normal(-2.3, 0.8, (n, 3))
+    q = rng.normal(size=(n, 4))
+    sc = scenes.Scene(mean.astype(np.float32), ls.astype(np.float32), q.astype(np.float32),
+                      rng.normal(0, 1, n).astype(np.float32), rng.uniform(0, 1, (n, 3)).astype(np.float32))
+    w2c = np.eye(4, dtype=np.float32)
+    p, fb = _render_gpu(sc, w2c, cam, np.zeros(3, np.float32), dev)
+    ref = oracle.project(sc, w2c, cam)
+    got = {k: v.cpu().numpy() for k, v in fb.proj.items()}
+    outside = (u < 0) | (u >= 200) | (v < 0) | (v >= 150)
+    reaching = outside & (ref["radius"] > 0)
+    assert reaching.sum() > 1000 and (outside & (ref["radius"] == 0)).sum() > 1000
+    assert np.array_equal(_bits(got["xyzo"]), _bits(ref["xyzo"]))
+    assert np.array_equal(_bits(got["conic"][:, :3]), _bits(ref["conic"][:, :3]))
+    for k in ("radius", "rect", "tiles_touched"):
+        assert np.array_equal(got[k], ref[k]), k
+
+
 def _check_bins(fb, sc, w2c, cam):
     keys, vals, ranges = oracle.bin_sort(sc, w2c, cam)
     k = int(fb.k_dev.item())
@@ -359,6 +388,40 @@ def test_deep_tiles_use_the_merge_path(dev):
     assert (ranges[:, 1] - ranges[:, 0]).max() > 8192 * 2
     _check_bins(fb, sc, np.eye(4, dtype=np.float32), cam)
     _check_image(fb, oracle.render_fwd(sc, np.eye(4, dtype=np.float32), cam, np.zeros(3, np.float32)))
+
+
+def _render_gpu_cap(sc, w2c, cam, bg, dev, capacity):
+    from paper_2412_09723_gb300 import rasterizer as R
+
+    p = _params(sc, dev)
+    fb = R.FrameBuffers(sc.n, cam, dev, capacity=capacity, want_keys=True)
+    R.render_forward(p, _w(w2c, dev), cam, tuple(float(x) for x in bg), fb)
+    torch.cuda.synchronize()
+    return p, fb
+
+
+def test_bins_at_tight_capacity_and_one_deep_tile(dev):
+    """The full 300k / 640x480 workload with a duplicate capacity close to K
+    (as the agent sizes it), and a 640x480 frame whose centre tile holds about
+    20000 keys (chunked shared-memory sorts and global merges): bins equal the
+    oracle's."""
+    sc, w2c, cam, bg = _full_vga()
+    K = int(oracle.project(sc, w2c, cam)["tiles_touched"].sum())  # whole-rect count: an upper bound of K
+    p, fb = _render_gpu_cap(sc, w2c, cam, bg, dev, int(K * 1.1))
+    _check_bins(fb, sc, w2c, cam)
+    rng = np.random.default_rng(8)
+    n = 20000
+    c = np.array([(16 * 20 + 8 - 320) / 525.0, (16 * 15 + 8 - 240) / 525.0])  # a tile centre at depth 1
+    z = rng.uniform(1.0, 3.0, n)
+    deep = scenes.Scene(
+        mean=np.stack([c[0] * z + rng.normal(0, 1e-3, n), c[1] * z + rng.normal(0, 1e-3, n), z], 1).astype(np.float32),
+        log_scale=np.full((n, 3), -6.0, np.float32), quat=np.tile(np.float32([1, 0, 0, 0]), (n, 1)),
+        opacity_logit=rng.normal(0.0, 0.5, n).astype(np.float32), rgb=rng.uniform(0, 1, (n, 3)).astype(np.float32))
+    eye = np.eye(4, dtype=np.float32)
+    p, fb = _render_gpu_cap(deep, eye, cam, bg, dev, 4 * n)
+    ranges = fb.ranges.cpu().numpy().view(np.uint32)
+    assert (ranges[:, 1] - ranges[:, 0]).max() > 4 * 2048
+    _check_bins(fb, deep, eye, cam)
 
 
 @pytest.mark.parametrize("levels", [1, 40, 1500])
