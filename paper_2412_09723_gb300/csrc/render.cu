@@ -514,7 +514,7 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
       const float4 cd = sm.st.cid[j];
       float v[10];
 #pragma unroll
-      for (int k = 0; k < 10; ++k) v[k] = 0.f;
+      for (int k = 0; k < 10; ++k) v[k] = -0.0f;  // -0 + x = x exactly: the first sum folds away
       const bool any = adjoint_step2(q, pos, xo, qd, cd.x, cd.y, cd.z, v);
       if (__any_sync(0xffffffffu, any)) {
         // warp sums of the 10 values through shared memory: lane writes its
