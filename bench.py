@@ -722,6 +722,26 @@ def main():
     tot_prof = sum(v[1] for v in prof.values()) or 1.0
     breakdown = {k: {"launches": n, "ms_per_step": ms / Kp, "share": ms / tot_prof} for k, (n, ms) in kernels}
 
+    # whole-step roofline: algorithmic FP32 ops of both renders against the
+    # issue peak, algorithmic bytes of the step against the measured HBM copy
+    # rate; the larger time bounds the step
+    frame_roofline = None
+    if q_walk and q_used:
+        K_dup = int(agent.fb.k_dev.item())
+        n_pix = cam.width * cam.height
+        ops_alg = 2 * OPS_WALK * q_walk + (OPS_CONTRIB_FWD + OPS_CONTRIB_BWD) * q_used
+        bytes_alg = (2 * 56 * agent.n + 24 * K_dup + 8 * cam.n_tiles + 32 * n_pix + 40 * n_pix)
+        t_alu = ops_alg / (alu_peak_tops * 1e12)
+        t_hbm = bytes_alg / (float(peaks["hbm_gbs"]) * 1e9)
+        frame_roofline = {
+            "bound": "alu" if t_alu >= t_hbm else "hbm", "ops_alg": ops_alg, "bytes_alg": bytes_alg,
+            "t_alu_ms": 1e3 * t_alu, "t_hbm_ms": 1e3 * t_hbm, "t_bound_ms": 1e3 * max(t_alu, t_hbm),
+            "frac": None,  # filled in below from the measured step time
+            "work": "ops: 2 x 9 per walked pair + (25 + 63) per contributing pair (forward + backward renders); "
+                    "bytes: map in and gradients out (2 x 56 B per Gaussian), 24 B per duplicate (key and value "
+                    "written and read once), 8 B per tile, 32 B per pixel of render output, 40 B per pixel of "
+                    "targets and backward re-read"}
+
     # end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -780,6 +800,8 @@ def main():
                 "p50_ms": statistics.median(step_ms), "p99_ms": _pct(step_ms, 99),
                 "tracked_frames_per_s": value / EPISODE,
                 "wall_s_timed": t_wall, "gpu_launches": launches, "roofline": roofline, "kernels": breakdown,
+                "frame_roofline": (dict(frame_roofline, frac=frame_roofline["t_bound_ms"] / (total_ms_max / K))
+                                   if frame_roofline else None),
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "batched_multi_agent": multi,
                 "serving": served, "alignment": aligned, "next_rows": nxt}
         print(json.dumps(line))
