@@ -2,10 +2,10 @@
 //
 // * Loss of Eq. (optim) (Sec. 3.5 step 4): L1 colour, SSIM and L1 depth
 //   terms with their image gradients.  SSIM uses an 11 x 11 Gaussian window
-//   (sigma 1.5) over a zero-padded image; one CTA computes a 16 x 16 block of
-//   one channel: the 26 x 26 patch of both images is staged in shared memory,
-//   the window is applied separably (rows, then columns) to the five products
-//   x, y, x^2, y^2, xy, and each pixel's SSIM and its partial derivatives with
+//   (sigma 1.5) over a zero-padded image; one CTA computes a 32 x 16 block of
+//   all three channels: the 42 x 26 patch of both images is staged in shared
+//   memory, the window is applied separably (rows, then columns) to the five
+//   products x, y, x^2, y^2, xy, and each pixel's SSIM and its partial derivatives with
 //   respect to the three window sums that involve x (A = dS/dmu_x,
 //   B = dS/dE[x^2], C = dS/dE[xy]) are written out.  A second kernel applies
 //   the same window to A, B, C and forms
@@ -30,11 +30,8 @@ namespace splat {
 // ----------------------------------------------------------------------------
 // SSIM
 // ----------------------------------------------------------------------------
-constexpr int kSsT = 16;                  // output block side
 constexpr int kSsR = 5;                   // window radius
-constexpr int kSsP = kSsT + 2 * kSsR;     // staged patch side (26)
 constexpr int kSsTaps = 2 * kSsR + 1;     // 11
-constexpr int kSsLd = 48;                 // shared row stride: two rows of a warp fall in different banks
 constexpr float kSsC1 = 0.01f * 0.01f;
 constexpr float kSsC2 = 0.03f * 0.03f;
 
@@ -68,89 +65,126 @@ __device__ __forceinline__ float block_sum_256(float v, float* red /*[8]*/) {
   return t;  // valid in thread 0
 }
 
-// Stage the 26 x 26 patch at (x0, y0) of an image with pixel stride `ps`
-// (3 for channel ch of an interleaved [H, W, 3] image, 1 for a plane), zero
-// outside the image.
-__device__ __forceinline__ void stage_patch(const float* __restrict__ img, int H, int W, int ps, int x0, int y0,
-                                            float (*dst)[kSsLd]) {
-  for (int i = threadIdx.x; i < kSsP * kSsP; i += 256) {
-    const int r = i / kSsP, c = i - r * kSsP;
-    const int gy = y0 + r, gx = x0 + c;
-    const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-    dst[r][c] = in ? img[((size_t)gy * W + gx) * ps] : 0.f;
-  }
-}
+// The window sums run in two separable passes over a patch staged in shared
+// memory: a horizontal pass in which a thread takes a run of kSsRun outputs of
+// one patch row (each staged pixel is read once per run and added, with each
+// tap weight, into the outputs it reaches), and a vertical pass in which a
+// thread takes two outputs of one column.  Pairs of sums that share a weight
+// ((x, y), (x^2, y^2), (A, B)) are accumulated as packed single-precision
+// pairs.  One CTA covers a kSsTX x kSsTY block of all three channels.
+constexpr int kSsTX = 32, kSsTY = 16;     // output block
+constexpr int kSsPX = kSsTX + 2 * kSsR;   // staged patch, 42 x 26
+constexpr int kSsPY = kSsTY + 2 * kSsR;
+constexpr int kSsRun = 4;                 // horizontal outputs per thread
+constexpr int kSsHItems = kSsPY * (kSsTX / kSsRun);  // 208 horizontal runs per channel
+
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                                        int H, int W, SsimWin win, float loss_scale, float ssim_scale,
                                                        float* __restrict__ abc, float* __restrict__ loss) {
-  __shared__ float sx[kSsP][kSsLd], sy[kSsP][kSsLd];
-  __shared__ float hs[5][kSsP][kSsLd];
+  __shared__ float2 sxy[3][kSsPY][kSsPX];  // (x, y) of every channel
+  __shared__ float2 h1[kSsPY][kSsTX];      // horizontal sums of (x, y)
+  __shared__ float2 h2[kSsPY][kSsTX];      // ... of (x^2, y^2)
+  __shared__ float h3[kSsPY][kSsTX + 1];   // ... of x y
   __shared__ float red[8];
-  const int ch = blockIdx.z;
-  const int bx = blockIdx.x * kSsT, by = blockIdx.y * kSsT;
-  stage_patch(x + ch, H, W, 3, bx - kSsR, by - kSsR, sx);
-  stage_patch(y + ch, H, W, 3, bx - kSsR, by - kSsR, sy);
+  const int t = threadIdx.x;
+  const int bx = blockIdx.x * kSsTX, by = blockIdx.y * kSsTY;
+  for (int i = t; i < kSsPY * kSsPX * 3; i += 256) {  // a patch row is 126 consecutive floats of each image
+    const int r = i / (kSsPX * 3), rem = i - r * (kSsPX * 3);
+    const int c = rem / 3, ch = rem - 3 * c;
+    const int gy = by - kSsR + r, gx = bx - kSsR + c;
+    const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+    const size_t gi = ((size_t)gy * W + gx) * 3 + ch;
+    sxy[ch][r][c] = in ? make_float2(x[gi], y[gi]) : make_float2(0.f, 0.f);
+  }
   __syncthreads();
-  if (threadIdx.x < kSsP * kSsT / 2) {  // horizontal pass over all 26 rows, two columns per thread
-    const int r = threadIdx.x / (kSsT / 2), c = 2 * (threadIdx.x % (kSsT / 2));
-    float a[2][5] = {};
-    float u = sx[r][c], v = sy[r][c];
+  const size_t plane = (size_t)H * W;
+  float sum_1ms = 0.f, sum_s = 0.f;
+  for (int ch = 0; ch < 3; ++ch) {
+    if (t < kSsHItems) {
+      const int r = t / (kSsTX / kSsRun), c0 = kSsRun * (t % (kSsTX / kSsRun));
+      float2 a1[kSsRun], a2[kSsRun];
+      float a3[kSsRun];
 #pragma unroll
-    for (int k = 0; k < kSsTaps; ++k) {
-      const float u1 = sx[r][c + k + 1], v1 = sy[r][c + k + 1], w = win.w[k];
-#pragma unroll
-      for (int o = 0; o < 2; ++o) {
-        const float uu = o ? u1 : u, vv = o ? v1 : v;
-        const float wu = w * uu, wv = w * vv;
-        a[o][0] += wu;
-        a[o][1] += wv;
-        a[o][2] = fmaf(wu, uu, a[o][2]);
-        a[o][3] = fmaf(wv, vv, a[o][3]);
-        a[o][4] = fmaf(wu, vv, a[o][4]);
+      for (int j = 0; j < kSsRun; ++j) {
+        a1[j] = a2[j] = bc2(-0.0f);
+        a3[j] = -0.0f;
       }
-      u = u1;
-      v = v1;
+#pragma unroll
+      for (int p = 0; p < kSsRun + 2 * kSsR; ++p) {
+        const float2 v = sxy[ch][r][c0 + p];
+        const float2 sq = __fmul2_rn(v, v);
+        const float pr = v.x * v.y;
+#pragma unroll
+        for (int j = 0; j < kSsRun; ++j) {
+          const int k = p - j;
+          if (k >= 0 && k < kSsTaps) {
+            const float2 w = bc2(win.w[k]);
+            a1[j] = __ffma2_rn(w, v, a1[j]);
+            a2[j] = __ffma2_rn(w, sq, a2[j]);
+            a3[j] = fmaf(win.w[k], pr, a3[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kSsRun; ++j) {
+        h1[r][c0 + j] = a1[j];
+        h2[r][c0 + j] = a2[j];
+        h3[r][c0 + j] = a3[j];
+      }
+    }
+    __syncthreads();
+    const int tx = t & 31, ty0 = 2 * (t >> 5);
+    float2 m1[2], m2[2];
+    float m3[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      m1[j] = m2[j] = bc2(-0.0f);
+      m3[j] = -0.0f;
     }
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      hs[q][r][c] = a[0][q];
-      hs[q][r][c + 1] = a[1][q];
+    for (int p = 0; p < 2 + 2 * kSsR; ++p) {
+      const float2 v1 = h1[ty0 + p][tx], v2 = h2[ty0 + p][tx];
+      const float v3 = h3[ty0 + p][tx];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int k = p - j;
+        if (k >= 0 && k < kSsTaps) {
+          const float2 w = bc2(win.w[k]);
+          m1[j] = __ffma2_rn(w, v1, m1[j]);
+          m2[j] = __ffma2_rn(w, v2, m2[j]);
+          m3[j] = fmaf(win.w[k], v3, m3[j]);
+        }
+      }
     }
-  }
-  __syncthreads();
-  const int tx = threadIdx.x & (kSsT - 1), ty = threadIdx.x / kSsT;
-  float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < kSsTaps; ++k) {
-    const float w = win.w[k];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) m[q] = fmaf(w, hs[q][ty + k][tx], m[q]);
+    for (int j = 0; j < 2; ++j) {
+      const int gx = bx + tx, gy = by + ty0 + j;
+      if (gx >= W || gy >= H) continue;
+      const float mx = m1[j].x, my = m1[j].y;
+      const float vx = m2[j].x - mx * mx, vy = m2[j].y - my * my, cxy = m3[j] - mx * my;
+      const float a = 2.f * mx * my + kSsC1, b = 2.f * cxy + kSsC2;
+      const float c = mx * mx + my * my + kSsC1, d = vx + vy + kSsC2;
+      const float cd = c * d;
+      const float sv = a * b / cd;
+      const float A = (2.f * my * (b - a)) / cd - sv * (2.f * mx / c - 2.f * mx / d);
+      const float Bm = -sv / d;
+      const float Cm = 2.f * a / cd;
+      // planar layout [map][channel][H][W], so the adjoint stages contiguous rows
+      const size_t i = (size_t)ch * plane + (size_t)gy * W + gx;
+      abc[i] = A;
+      abc[3 * plane + i] = Bm;
+      abc[6 * plane + i] = Cm;
+      sum_1ms += 1.f - sv;
+      sum_s += sv;
+    }
+    __syncthreads();  // the horizontal sums are rewritten for the next channel
   }
-  const int gx = bx + tx, gy = by + ty;
-  float one_minus_s = 0.f, s = 0.f;
-  if (gx < W && gy < H) {
-    const float mx = m[0], my = m[1];
-    const float vx = m[2] - mx * mx, vy = m[3] - my * my, cxy = m[4] - mx * my;
-    const float a = 2.f * mx * my + kSsC1, b = 2.f * cxy + kSsC2;
-    const float c = mx * mx + my * my + kSsC1, d = vx + vy + kSsC2;
-    const float cd = c * d;
-    s = a * b / cd;
-    const float A = (2.f * my * (b - a)) / cd - s * (2.f * mx / c - 2.f * mx / d);
-    const float Bm = -s / d;
-    const float Cm = 2.f * a / cd;
-    // planar layout [map][channel][H][W], so the adjoint stages contiguous rows
-    const size_t plane = (size_t)H * W;
-    const size_t i = (size_t)ch * plane + (size_t)gy * W + gx;
-    abc[i] = A;
-    abc[3 * plane + i] = Bm;
-    abc[6 * plane + i] = Cm;
-    one_minus_s = 1.f - s;
-  }
-  const float t0 = block_sum_256(one_minus_s, red);
+  const float t0 = block_sum_256(sum_1ms, red);
   __syncthreads();
-  const float t1 = block_sum_256(s, red);
-  if (threadIdx.x == 0) {
+  const float t1 = block_sum_256(sum_s, red);
+  if (t == 0) {
     atomicAdd(&loss[0], t0 * loss_scale);
     atomicAdd(&loss[1], t1 * ssim_scale);
   }
@@ -159,45 +193,83 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                                        int H, int W, SsimWin win, float grad_scale,
                                                        const float* __restrict__ abc, float* __restrict__ d_rgb) {
-  __shared__ float sp[3][kSsP][kSsLd];
-  __shared__ float hs[3][kSsP][kSsLd];
-  const int ch = blockIdx.z;
-  const int bx = blockIdx.x * kSsT, by = blockIdx.y * kSsT;
+  __shared__ float2 sab[kSsPY][kSsPX];      // (A, B) of the channel
+  __shared__ float sc[kSsPY][kSsPX + 1];    // C
+  __shared__ float2 hab[kSsPY][kSsTX];
+  __shared__ float hc[kSsPY][kSsTX + 1];
+  const int t = threadIdx.x;
+  const int bx = blockIdx.x * kSsTX, by = blockIdx.y * kSsTY;
   const size_t plane = (size_t)H * W;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) stage_patch(abc + (3 * q + ch) * plane, H, W, 1, bx - kSsR, by - kSsR, sp[q]);
-  __syncthreads();
-  if (threadIdx.x < kSsP * kSsT / 2) {  // two columns per thread
-    const int r = threadIdx.x / (kSsT / 2), c = 2 * (threadIdx.x % (kSsT / 2));
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      float a0 = 0.f, a1 = 0.f;
-      float prev = sp[q][r][c];
-#pragma unroll
-      for (int k = 0; k < kSsTaps; ++k) {
-        const float w = win.w[k], next = sp[q][r][c + k + 1];
-        a0 = fmaf(w, prev, a0);
-        a1 = fmaf(w, next, a1);
-        prev = next;
-      }
-      hs[q][r][c] = a0;
-      hs[q][r][c + 1] = a1;
+  for (int ch = 0; ch < 3; ++ch) {
+    const float* pa = abc + (size_t)ch * plane;
+    for (int i = t; i < kSsPY * kSsPX; i += 256) {
+      const int r = i / kSsPX, c = i - r * kSsPX;
+      const int gy = by - kSsR + r, gx = bx - kSsR + c;
+      const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+      const size_t gi = (size_t)gy * W + gx;
+      sab[r][c] = in ? make_float2(pa[gi], pa[3 * plane + gi]) : make_float2(0.f, 0.f);
+      sc[r][c] = in ? pa[6 * plane + gi] : 0.f;
     }
-  }
-  __syncthreads();
-  const int tx = threadIdx.x & (kSsT - 1), ty = threadIdx.x / kSsT;
-  const int gx = bx + tx, gy = by + ty;
-  if (gx >= W || gy >= H) return;
-  float ga = 0.f, gb = 0.f, gc = 0.f;
+    __syncthreads();
+    if (t < kSsHItems) {
+      const int r = t / (kSsTX / kSsRun), c0 = kSsRun * (t % (kSsTX / kSsRun));
+      float2 a1[kSsRun];
+      float a2[kSsRun];
 #pragma unroll
-  for (int k = 0; k < kSsTaps; ++k) {
-    const float w = win.w[k];
-    ga = fmaf(w, hs[0][ty + k][tx], ga);
-    gb = fmaf(w, hs[1][ty + k][tx], gb);
-    gc = fmaf(w, hs[2][ty + k][tx], gc);
+      for (int j = 0; j < kSsRun; ++j) {
+        a1[j] = bc2(-0.0f);
+        a2[j] = -0.0f;
+      }
+#pragma unroll
+      for (int p = 0; p < kSsRun + 2 * kSsR; ++p) {
+        const float2 v = sab[r][c0 + p];
+        const float vc = sc[r][c0 + p];
+#pragma unroll
+        for (int j = 0; j < kSsRun; ++j) {
+          const int k = p - j;
+          if (k >= 0 && k < kSsTaps) {
+            a1[j] = __ffma2_rn(bc2(win.w[k]), v, a1[j]);
+            a2[j] = fmaf(win.w[k], vc, a2[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kSsRun; ++j) {
+        hab[r][c0 + j] = a1[j];
+        hc[r][c0 + j] = a2[j];
+      }
+    }
+    __syncthreads();
+    const int tx = t & 31, ty0 = 2 * (t >> 5);
+    float2 m1[2];
+    float m2[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      m1[j] = bc2(-0.0f);
+      m2[j] = -0.0f;
+    }
+#pragma unroll
+    for (int p = 0; p < 2 + 2 * kSsR; ++p) {
+      const float2 v1 = hab[ty0 + p][tx];
+      const float v2 = hc[ty0 + p][tx];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int k = p - j;
+        if (k >= 0 && k < kSsTaps) {
+          m1[j] = __ffma2_rn(bc2(win.w[k]), v1, m1[j]);
+          m2[j] = fmaf(win.w[k], v2, m2[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gx = bx + tx, gy = by + ty0 + j;
+      if (gx >= W || gy >= H) continue;
+      const size_t i = ((size_t)gy * W + gx) * 3 + ch;
+      d_rgb[i] = fmaf(grad_scale, m1[j].x + 2.f * x[i] * m1[j].y + y[i] * m2[j], d_rgb[i]);
+    }
+    __syncthreads();  // the staged planes are rewritten for the next channel
   }
-  const size_t i = ((size_t)gy * W + gx) * 3 + ch;
-  d_rgb[i] = fmaf(grad_scale, ga + 2.f * x[i] * gb + y[i] * gc, d_rgb[i]);
 }
 
 // ----------------------------------------------------------------------------
@@ -529,7 +601,7 @@ extern "C" int splat_loss_consensus(const float* rgb, const float* depth, const 
   if (rc) return rc;
   if (w_ssim == 0.f) return SPLAT_OK;
   const SsimWin win = ssim_window();
-  const dim3 grid((unsigned)((width + kSsT - 1) / kSsT), (unsigned)((height + kSsT - 1) / kSsT), 3);
+  const dim3 grid((unsigned)((width + kSsTX - 1) / kSsTX), (unsigned)((height + kSsTY - 1) / kSsTY));
   float* abc = static_cast<float*>(ws);
   const float inv = 1.0f / (float)(3 * npix);
   SPLAT_LAUNCH("ssim_fwd_kernel", s,
