@@ -166,11 +166,12 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
       const float vx = m2[j].x - mx * mx, vy = m2[j].y - my * my, cxy = m3[j] - mx * my;
       const float a = 2.f * mx * my + kSsC1, b = 2.f * cxy + kSsC2;
       const float c = mx * mx + my * my + kSsC1, d = vx + vy + kSsC2;
-      const float cd = c * d;
-      const float sv = a * b / cd;
-      const float A = (2.f * my * (b - a)) / cd - sv * (2.f * mx / c - 2.f * mx / d);
-      const float Bm = -sv / d;
-      const float Cm = 2.f * a / cd;
+      const float rc = __frcp_rn(c), rd = __frcp_rn(d);  // two reciprocals instead of six divisions
+      const float rcd = rc * rd;
+      const float sv = a * b * rcd;
+      const float A = 2.f * my * (b - a) * rcd - sv * (2.f * mx * rc - 2.f * mx * rd);
+      const float Bm = -sv * rd;
+      const float Cm = 2.f * a * rcd;
       // planar layout [map][channel][H][W], so the adjoint stages contiguous rows
       const size_t i = (size_t)ch * plane + (size_t)gy * W + gx;
       abc[i] = A;
