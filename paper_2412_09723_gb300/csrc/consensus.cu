@@ -90,13 +90,19 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
   __shared__ float red[8];
   const int t = threadIdx.x;
   const int bx = blockIdx.x * kSsTX, by = blockIdx.y * kSsTY;
-  for (int i = t; i < kSsPY * kSsPX * 3; i += 256) {  // a patch row is 126 consecutive floats of each image
-    const int r = i / (kSsPX * 3), rem = i - r * (kSsPX * 3);
-    const int c = rem / 3, ch = rem - 3 * c;
-    const int gy = by - kSsR + r, gx = bx - kSsR + c;
-    const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-    const size_t gi = ((size_t)gy * W + gx) * 3 + ch;
-    sxy[ch][r][c] = in ? make_float2(x[gi], y[gi]) : make_float2(0.f, 0.f);
+  {  // a patch row is 126 consecutive floats of each image: threads 0-125 take one row, 128-253 the next
+    const int j = t & 127, r0 = t >> 7;
+    const int c = j / 3, ch = j - 3 * c;
+    const int gx = bx - kSsR + c;
+    if (j < 3 * kSsPX) {
+      const bool inx = gx >= 0 && gx < W;
+      for (int r = r0; r < kSsPY; r += 2) {
+        const int gy = by - kSsR + r;
+        const bool in = inx && gy >= 0 && gy < H;
+        const size_t gi = ((size_t)gy * W + gx) * 3 + ch;
+        sxy[ch][r][c] = in ? make_float2(x[gi], y[gi]) : make_float2(0.f, 0.f);
+      }
+    }
   }
   __syncthreads();
   const size_t plane = (size_t)H * W;
@@ -203,13 +209,19 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float* __restrict__
   const size_t plane = (size_t)H * W;
   for (int ch = 0; ch < 3; ++ch) {
     const float* pa = abc + (size_t)ch * plane;
-    for (int i = t; i < kSsPY * kSsPX; i += 256) {
-      const int r = i / kSsPX, c = i - r * kSsPX;
-      const int gy = by - kSsR + r, gx = bx - kSsR + c;
-      const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-      const size_t gi = (size_t)gy * W + gx;
-      sab[r][c] = in ? make_float2(pa[gi], pa[3 * plane + gi]) : make_float2(0.f, 0.f);
-      sc[r][c] = in ? pa[6 * plane + gi] : 0.f;
+    {  // six patch rows per pass, one column per thread
+      const int c = t % kSsPX, r0 = t / kSsPX;
+      const int gx = bx - kSsR + c;
+      if (r0 < 6) {
+        const bool inx = gx >= 0 && gx < W;
+        for (int r = r0; r < kSsPY; r += 6) {
+          const int gy = by - kSsR + r;
+          const bool in = inx && gy >= 0 && gy < H;
+          const size_t gi = (size_t)gy * W + gx;
+          sab[r][c] = in ? make_float2(pa[gi], pa[3 * plane + gi]) : make_float2(0.f, 0.f);
+          sc[r][c] = in ? pa[6 * plane + gi] : 0.f;
+        }
+      }
     }
     __syncthreads();
     if (t < kSsHItems) {
