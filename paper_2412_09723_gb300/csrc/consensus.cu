@@ -12,8 +12,9 @@
 //   dS/dx(q) = (W*A)(q) + 2 x(q) (W*B)(q) + y(q) (W*C)(q).
 // * Mahalanobis alignment (Sec. 3.5 step 3): one thread per associated pair
 //   builds its Gauss-Newton contribution (21 + 6 + 1 numbers) in float,
-//   accumulated in double per thread, reduced per CTA, and added to the
-//   system with double atomics; one thread solves the 6 x 6 system by
+//   summed in float per thread and per warp (a few pairs and 32 partial sums:
+//   double precision is slow on this part), then in double per CTA and into
+//   the system with double atomics; one thread solves the 6 x 6 system by
 //   Cholesky and retracts T.
 // * Pruning (Algorithm 1): a flag kernel (the three criteria, block counts),
 //   a one-CTA scan of the block counts, and a scatter kernel that re-ranks
@@ -335,9 +336,11 @@ __global__ void __launch_bounds__(256) mahalanobis_kernel(MapK A, MapK Bm, const
     for (int b = 0; b < 3; ++b) R[3 * a + b] = T[4 * a + b];
     t[a] = T[4 * a + 3];
   }
-  double acc[kSysN];
+  // per-thread and per-warp sums in float (a thread takes a few pairs, a warp
+  // adds 32 partial sums); the per-CTA totals and the system in double
+  float acc[kSysN];
 #pragma unroll
-  for (int k = 0; k < kSysN; ++k) acc[k] = 0.0;
+  for (int k = 0; k < kSysN; ++k) acc[k] = 0.0f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
     const int ka = pairs[2 * i], lb = pairs[2 * i + 1];
     const float w = weights ? (float)weights[i] : 1.f;
@@ -389,18 +392,18 @@ __global__ void __launch_bounds__(256) mahalanobis_kernel(MapK A, MapK Bm, const
     for (int a = 0; a < 6; ++a)
 #pragma unroll
       for (int b = a; b < 6; ++b, ++e)
-        acc[e] += (double)(w2 * (J[0][a] * MJ[0][b] + J[1][a] * MJ[1][b] + J[2][a] * MJ[2][b]));
+        acc[e] += w2 * (J[0][a] * MJ[0][b] + J[1][a] * MJ[1][b] + J[2][a] * MJ[2][b]);
 #pragma unroll
-    for (int a = 0; a < 6; ++a) acc[21 + a] += (double)(w2 * (J[0][a] * Mr[0] + J[1][a] * Mr[1] + J[2][a] * Mr[2]));
-    acc[27] += (double)(w * (r[0] * Mr[0] + r[1] * Mr[1] + r[2] * Mr[2]));
+    for (int a = 0; a < 6; ++a) acc[21 + a] += w2 * (J[0][a] * Mr[0] + J[1][a] * Mr[1] + J[2][a] * Mr[2]);
+    acc[27] += w * (r[0] * Mr[0] + r[1] * Mr[1] + r[2] * Mr[2]);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kSysN; ++k) {
-    double v = acc[k];
+    float v = acc[k];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) red[warp][k] = v;
+    if (lane == 0) red[warp][k] = (double)v;
   }
   __syncthreads();
   if (threadIdx.x < kSysN) {
