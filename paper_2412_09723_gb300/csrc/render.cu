@@ -8,14 +8,16 @@
 // pairs.  The tile's list is staged through shared memory in batches of BATCH
 // Gaussians (position / depth / opacity, the quadratic form's coefficients
 // A = -a/2, B = -b, C = -c/2 with the exponent cut, colour, id) and every
-// thread walks the batch in order.  A pair whose exponent lies below the Gaussian's cut (set by the
-// projection so that opacity * exp(power) < 1/255 is certain) is skipped before
-// the exponential is evaluated; this changes no result.  A tile ends as soon as
-// all of its pixels have reached the transmittance stop.  No atomics.
+// thread walks the batch in order.  A pair whose exponent lies below the
+// Gaussian's cut (set by the projection so that opacity * exp(power) < 1/255
+// is certain) is skipped before the exponential is evaluated; this changes no
+// result.  A tile ends as soon as all of its pixels have reached the
+// transmittance stop.  No atomics.
 //
 // Backward: 128 threads with 2 pixels each ((x, y) and (x, y + 2); a warp
-// covers 16 x 4 pixels), again in packed pairs.  Every pixel starts from its final transmittance and
-// last contributor, walks the list back to front and recovers
+// covers 16 x 4 pixels), again in packed pairs.  Every pixel starts from its
+// final transmittance and last contributor, walks the list back to front and
+// recovers
 // T_i = T_{i+1} / (1 - alpha_i).  With the pixel's upstream gradients folded
 // into one scalar per Gaussian, P_i = gC.c_i + gD z_i + gS, and the weights
 // w_j = alpha_j T_j, every later weight carries a factor (1 - alpha_i), so
