@@ -78,16 +78,20 @@ constexpr int kSsPX = kSsTX + 2 * kSsR;   // staged patch, 42 x 26
 constexpr int kSsPY = kSsTY + 2 * kSsR;
 constexpr int kSsRun = 4;                 // horizontal outputs per thread
 constexpr int kSsHItems = kSsPY * (kSsTX / kSsRun);  // 208 horizontal runs per channel
+// Padded shared rows: the 8 runs of a patch row and the 4 rows a warp spans
+// fall in distinct banks (patch rows of 43 pairs, sum rows of 33).
+constexpr int kSsPXp = kSsPX + 1;
+constexpr int kSsTXp = kSsTX + 1;
 
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                                        int H, int W, SsimWin win, float loss_scale, float ssim_scale,
                                                        float* __restrict__ abc, float* __restrict__ loss) {
-  __shared__ float2 sxy[3][kSsPY][kSsPX];  // (x, y) of every channel
-  __shared__ float2 h1[kSsPY][kSsTX];      // horizontal sums of (x, y)
-  __shared__ float2 h2[kSsPY][kSsTX];      // ... of (x^2, y^2)
-  __shared__ float h3[kSsPY][kSsTX + 1];   // ... of x y
+  __shared__ float2 sxy[3][kSsPY][kSsPXp];  // (x, y) of every channel
+  __shared__ float2 h1[kSsPY][kSsTXp];      // horizontal sums of (x, y)
+  __shared__ float2 h2[kSsPY][kSsTXp];      // ... of (x^2, y^2)
+  __shared__ float h3[kSsPY][kSsTXp];       // ... of x y
   __shared__ float red[8];
   const int t = threadIdx.x;
   const int bx = blockIdx.x * kSsTX, by = blockIdx.y * kSsTY;
@@ -201,10 +205,10 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                                        int H, int W, SsimWin win, float grad_scale,
                                                        const float* __restrict__ abc, float* __restrict__ d_rgb) {
-  __shared__ float2 sab[kSsPY][kSsPX];      // (A, B) of the channel
-  __shared__ float sc[kSsPY][kSsPX + 1];    // C
-  __shared__ float2 hab[kSsPY][kSsTX];
-  __shared__ float hc[kSsPY][kSsTX + 1];
+  __shared__ float2 sab[kSsPY][kSsPXp];  // (A, B) of the channel
+  __shared__ float sc[kSsPY][kSsPXp];    // C
+  __shared__ float2 hab[kSsPY][kSsTXp];
+  __shared__ float hc[kSsPY][kSsTXp];
   const int t = threadIdx.x;
   const int bx = blockIdx.x * kSsTX, by = blockIdx.y * kSsTY;
   const size_t plane = (size_t)H * W;
