@@ -4,6 +4,13 @@ Every translation unit is compiled with --fmad=false (fused multiply-adds
 only where the source writes them) and IEEE division / square root (nvcc's
 defaults, never --use_fast_math), which the bit-exact parity of tile rects,
 sort keys and maximum-weight ids relies on.
+
+With SPLAT_FAST_EXP=1 in the environment a second library,
+libsplat_gb300_fastexp.so, is built (and loaded by the binding) in which the
+exponential is the hardware __expf instead of the project exponential: it
+measures what the bit-exact exponential costs.  Its results are not the
+oracle's bit for bit (only the image and gradient tolerances can hold), so it
+is a measurement build, never the default.
 """
 from __future__ import annotations
 
@@ -15,13 +22,14 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "libsplat_gb300.so")
+FAST_EXP = os.environ.get("SPLAT_FAST_EXP", "") == "1"
+BUILD = os.path.join(HERE, "_build_fastexp" if FAST_EXP else "_build")
+LIB = os.path.join(HERE, "libsplat_gb300_fastexp.so" if FAST_EXP else "libsplat_gb300.so")
 SOURCES = ["api.cu", "project.cu", "binsort.cu", "render.cu", "assoc.cu", "profile.cu", "noalloc.cu", "consensus.cu"]
 HEADERS = ["common.cuh", "internal.cuh", "segsort.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "--fmad=false", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr"]
+              "--expt-relaxed-constexpr"] + (["-DSPLAT_FAST_EXP=1"] if FAST_EXP else [])
 
 
 def nvcc() -> str:

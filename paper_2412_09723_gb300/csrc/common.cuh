@@ -33,6 +33,10 @@ constexpr float kPowerCutMargin = 1e-3f;
 // 15-significant-bit head and a tail), exp(r) by the degree-7 Taylor
 // polynomial in Horner form with fused multiply-adds, 2^k from exponent bits.
 // ----------------------------------------------------------------------------
+#if defined(SPLAT_FAST_EXP)
+// Measurement build: the hardware exponential (not bit-exact with the oracle).
+__device__ __forceinline__ float exp_core(float x) { return __expf(x); }
+#else
 __device__ __forceinline__ float exp_core(float x) {  // x in [-87, 88]
   // k = rint(x log2 e): adding 1.5 * 2^23 rounds to an integer (to nearest,
   // ties to even) and leaves k in the low mantissa bits
@@ -51,6 +55,7 @@ __device__ __forceinline__ float exp_core(float x) {  // x in [-87, 88]
   const int ki = __float_as_int(t) - 0x4B400000;
   return __fmul_rn(p, __int_as_float((ki + 127) << 23));
 }
+#endif
 
 __device__ __forceinline__ float exp_full(float x) {
   if (x != x) return x;

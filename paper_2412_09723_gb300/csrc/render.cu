@@ -208,6 +208,9 @@ struct FwdPix {
 __device__ __forceinline__ float2 bcast(float v) { return make_float2(v, v); }
 
 // exp_core of both lanes (same operations as the scalar one).
+#if defined(SPLAT_FAST_EXP)
+__device__ __forceinline__ float2 exp_core2(float2 x) { return make_float2(__expf(x.x), __expf(x.y)); }
+#else
 __device__ __forceinline__ float2 exp_core2(float2 x) {
   const float2 t = __fadd2_rn(__fmul2_rn(x, bcast(1.44269502f)), bcast(12582912.0f));
   const float2 k = __fadd2_rn(t, bcast(-12582912.0f));
@@ -225,6 +228,7 @@ __device__ __forceinline__ float2 exp_core2(float2 x) {
                                 __int_as_float((__float_as_int(t.y) - 0x4B400000 + 127) << 23));
   return __fmul2_rn(q, sc);
 }
+#endif
 
 // One front-to-back compositing step of the thread's two pixels (the
 // specified order).  nfy = (-fy0, -fy1).
