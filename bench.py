@@ -236,6 +236,23 @@ def whole_job_rate(units_per_rank: int, local_ms: float, world: int, dist=None, 
     return world * units_per_rank / (max_ms / 1e3), max_ms
 
 
+def step_roofline(walked: int, contributing: int, n_gaussians: int, duplicates: int, n_tiles: int, n_pix: int,
+                  alu_peak_tops: float, hbm_gbs: float) -> dict:
+    """Bound of one tracking + mapping step: the algorithmic FP32 ops of both
+    renders at the issue peak against the step's algorithmic bytes at the HBM
+    rate; `frac` is left for the caller to fill in from the measured step."""
+    ops_alg = 2 * OPS_WALK * walked + (OPS_CONTRIB_FWD + OPS_CONTRIB_BWD) * contributing
+    bytes_alg = 2 * 56 * n_gaussians + 24 * duplicates + 8 * n_tiles + (32 + 40) * n_pix
+    t_alu = ops_alg / (alu_peak_tops * 1e12)
+    t_hbm = bytes_alg / (hbm_gbs * 1e9)
+    return {"bound": "alu" if t_alu >= t_hbm else "hbm", "ops_alg": ops_alg, "bytes_alg": bytes_alg,
+            "t_alu_ms": 1e3 * t_alu, "t_hbm_ms": 1e3 * t_hbm, "t_bound_ms": 1e3 * max(t_alu, t_hbm), "frac": None,
+            "work": "ops: 2 x 9 per walked pair + (25 + 63) per contributing pair (forward + backward renders); "
+                    "bytes: map in and gradients out (2 x 56 B per Gaussian), 24 B per duplicate (key and value "
+                    "written and read once), 8 B per tile, 32 B per pixel of render output, 40 B per pixel of "
+                    "targets and backward re-read"}
+
+
 def _pct(xs, q):
     s = sorted(xs)
     if not s:
@@ -727,20 +744,8 @@ def main():
     # rate; the larger time bounds the step
     frame_roofline = None
     if q_walk and q_used:
-        K_dup = int(agent.fb.k_dev.item())
-        n_pix = cam.width * cam.height
-        ops_alg = 2 * OPS_WALK * q_walk + (OPS_CONTRIB_FWD + OPS_CONTRIB_BWD) * q_used
-        bytes_alg = (2 * 56 * agent.n + 24 * K_dup + 8 * cam.n_tiles + 32 * n_pix + 40 * n_pix)
-        t_alu = ops_alg / (alu_peak_tops * 1e12)
-        t_hbm = bytes_alg / (float(peaks["hbm_gbs"]) * 1e9)
-        frame_roofline = {
-            "bound": "alu" if t_alu >= t_hbm else "hbm", "ops_alg": ops_alg, "bytes_alg": bytes_alg,
-            "t_alu_ms": 1e3 * t_alu, "t_hbm_ms": 1e3 * t_hbm, "t_bound_ms": 1e3 * max(t_alu, t_hbm),
-            "frac": None,  # filled in below from the measured step time
-            "work": "ops: 2 x 9 per walked pair + (25 + 63) per contributing pair (forward + backward renders); "
-                    "bytes: map in and gradients out (2 x 56 B per Gaussian), 24 B per duplicate (key and value "
-                    "written and read once), 8 B per tile, 32 B per pixel of render output, 40 B per pixel of "
-                    "targets and backward re-read"}
+        frame_roofline = step_roofline(q_walk, q_used, agent.n, int(agent.fb.k_dev.item()), cam.n_tiles,
+                                       cam.width * cam.height, alu_peak_tops, float(peaks["hbm_gbs"]))
 
     # end to end through the public API with host buffers
     e2e = None
