@@ -348,7 +348,10 @@ extern "C" int splat_adam_groups(int32_t n_groups, float* const* params, float* 
   G.n = n_groups;
   if (total4 == 0) return SPLAT_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int blocks = (int)std::min<int64_t>((total4 + 255) / 256, 152 * 16);
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // one resident wave (6 CTAs of 256 threads per SM at this kernel's registers), grid-stride beyond
+  const int blocks = (int)std::min<int64_t>((total4 + 255) / 256, 6 * (int64_t)sms);
   SPLAT_LAUNCH("adam_groups_kernel", s,
                adam_groups_kernel<<<blocks, 256, 0, s>>>(G, total4, beta1, beta2, step, eps, zero_grad));
   return check_launch("adam_groups_kernel");
