@@ -317,7 +317,7 @@ __device__ __forceinline__ uint64_t* cta_radix_sort_hi32(uint64_t* a, uint64_t* 
 
 // Bucket sort by the high word's value range: the high words h are mapped
 // linearly onto `bins` buckets, d = (h - min h) >> s (bins a power of two
-// between 2n and kBucketBins, s the smallest shift that fits the range), a
+// between n and kBucketBins, s the smallest shift that fits the range), a
 // counting pass places every key of a[0, n) in its bucket of b (the order
 // inside a bucket comes from shared atomics), and one thread per bucket
 // insertion-sorts it by the full key.  The keys are distinct, so the result is
@@ -344,7 +344,7 @@ __device__ __forceinline__ uint64_t* cta_bucket_sort_hi32(const uint64_t* a, uin
     sh[warp] = mn;
     sh[kSegRadixWarps + warp] = mx;
   }
-  const int bins = min(kBucketBins, max(32, next_pow2(2 * n)));
+  const int bins = min(kBucketBins, max(32, next_pow2(n)));
   const int lb = 31 - __clz(bins);
   for (int i = t; i < bins; i += kSegRadixThreads) cnt[i] = 0u;
   __syncthreads();
