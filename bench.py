@@ -64,7 +64,8 @@ def _parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop comparison")
     ap.add_argument("--no-align", action="store_true", help="skip the two-agent association/alignment section")
     ap.add_argument("--no-next", action="store_true", help="skip the consensus-loss / Mahalanobis / pruning timings")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson request trace")
+    ap.add_argument("--serve-seconds", type=float, default=30.0,
+                    help="length of the 30 Hz Poisson request trace (served and plain)")
     return ap.parse_args()
 
 
@@ -140,7 +141,7 @@ def _oracle_step(oracle, sc, w2c, cam, bg, target, lr, rows=None):
     import numpy as np
 
     r0, r1 = rows or (0, cam.height)
-    out = oracle.render_fwd(sc, w2c, cam, bg, rows=(r0, r1))
+    out = oracle.render_fwd(sc, w2c, cam, bg, rows=(r0, r1), signature=False)
     L, g_rgb, g_depth = oracle.loss_l1(out["rgb"][r0:r1], out["depth"][r0:r1], target["rgb"][r0:r1],
                                        target["depth"][r0:r1], 1.0, 0.5)
     G_rgb = np.zeros_like(out["rgb"])
@@ -164,60 +165,85 @@ def _cpu_workload():
     return sc, w2c, w2c_target, cam, bg
 
 
-def cpu_baseline_sample():
-    """Time the oracle as it stands (single-threaded) on one full frame of the
-    workload: fwd + loss + bwd + Adam + association."""
-    import oracle
+def _oracle_frames(oracle, budget_s, min_frames, max_frames):
+    """Whole oracle frames of the workload (fwd + L1 loss + bwd + Adam + assoc,
+    one projection and one Adam per frame) until `budget_s` seconds have passed
+    (at least `min_frames`); returns the per-frame times."""
     from paper_2412_09723_gb300.agent import DEFAULT_LR
 
-    oracle.lib()
     sc, w2c, w2c_t, cam, bg = _cpu_workload()
-    target = oracle.render_fwd(sc, w2c_t, cam, bg)
-    t0 = time.perf_counter()
-    _oracle_step(oracle, sc, w2c, cam, bg, target, DEFAULT_LR)
-    dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full frame (fwd + L1 loss + bwd + Adam + assoc) of {WORKLOAD}, single-threaded, "
-                      f"{dt:.2f} s"}
+    target = oracle.render_fwd(sc, w2c_t, cam, bg, signature=False)
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max_frames and (len(times) < min_frames or time.perf_counter() - t_start < budget_s):
+        t0 = time.perf_counter()
+        _oracle_step(oracle, sc, w2c, cam, bg, target, DEFAULT_LR)
+        times.append(time.perf_counter() - t0)
+    return times
 
 
-REF_BAND_ROWS = 16
+def cpu_baseline_sample(budget_s=15.0):
+    """The oracle as it stands, built with its OpenMP loops (tiles of the
+    forward render, tiles with per-thread gradient buffers in the adjoint,
+    Gaussians in the projection) on every host core, timed on whole frames of
+    the workload for about `budget_s` seconds; plus one single-threaded frame
+    of the parity build for comparison."""
+    import oracle
+
+    nproc = os.cpu_count() or 1
+    flags = " ".join(oracle.CFLAGS_OMP)
+    try:
+        with oracle.parallel(nproc) as nth:
+            _oracle_frames(oracle, 0.0, 1, 1)  # warm-up (library load, page faults)
+            times = _oracle_frames(oracle, budget_s, 3, 200)
+        kind = f"oracle, g++ {flags}, OpenMP"
+    except (OSError, RuntimeError, subprocess.CalledProcessError) as e:  # no OpenMP runtime: the parity build
+        nth = 1
+        times = _oracle_frames(oracle, budget_s, 1, 200)
+        kind = f"oracle, single-threaded parity build (OpenMP build unavailable: {e})"
+    single = _oracle_frames(oracle, 0.0, 1, 1)
+    mean = sum(times) / len(times)
+    return {"value": 1.0 / mean, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "host_nproc": nproc, "build": kind,
+            "sample": f"{len(times)} whole frames (fwd + L1 loss + bwd + Adam + assoc) of {WORKLOAD} on {nth} "
+                      f"threads, {mean:.3f} s per frame",
+            "single_thread": {"value": 1.0 / single[0], "unit": UNIT, "cores": 1,
+                              "build": "g++ " + " ".join(oracle.CFLAGS), "sample": "one whole frame"}}
+
+
+def _config(cam, duplicates):
+    """The workload's description, the same dict in both arms."""
+    return {"workload": WORKLOAD, "n_gaussians": N_GAUSSIANS, "width": cam.width, "height": cam.height,
+            "duplicates_K": int(duplicates), "iterations_per_episode": EPISODE,
+            "l2": "GPU arm: flushed between steps (256 MiB write)",
+            "parallelism": "1 independent agent per GPU (replicas)"}
 
 
 def run_reference(args, rank, world):
-    """The CPU oracle as the reference arm.  Each step is a bounded sample of
-    the workload: one 16-row band of the frame (fwd + loss + bwd + Adam +
-    assoc, with the projection of the whole map), cycling down the frame; the
-    frame rate is the band's share of a frame divided by the step time."""
+    """The CPU oracle as the reference arm: each step is one whole frame of the
+    workload (projection, binning, forward render, L1 loss, adjoint, Adam on
+    the map, association), single-threaded (the parity build, as it stands).
+    Under torchrun only rank 0 runs and prints."""
     if rank != 0:
         return 0
     import oracle
-    from paper_2412_09723_gb300.agent import DEFAULT_LR
 
     oracle.lib()
     sc, w2c, w2c_t, cam, bg = _cpu_workload()
-    target = oracle.render_fwd(sc, w2c_t, cam, bg)
-    nb = cam.height // REF_BAND_ROWS
-    times = []
-    for k in range(args.warmup + args.steps):
-        b = k % nb
-        t0 = time.perf_counter()
-        _oracle_step(oracle, sc, w2c, cam, bg, target, DEFAULT_LR, rows=(b * REF_BAND_ROWS, (b + 1) * REF_BAND_ROWS))
-        dt = time.perf_counter() - t0
-        if k >= args.warmup:
-            times.append(dt)
+    k_dup = len(oracle.bin_sort(sc, w2c, cam)[1])
+    _oracle_frames(oracle, 0.0, args.warmup, args.warmup)
+    times = _oracle_frames(oracle, 0.0, args.steps, args.steps)
     total = sum(times)
-    frac = REF_BAND_ROWS / cam.height
-    value = frac * len(times) / total
+    value = len(times) / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSSIANS, "width": cam.width, "height": cam.height},
+            "config": _config(cam, k_dup),
             "p50_ms": 1e3 * statistics.median(times), "p99_ms": 1e3 * _pct(times, 99),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"per step one {REF_BAND_ROWS}-row band of {WORKLOAD} (fwd + L1 loss + bwd + "
-                                       "Adam + assoc; the whole map projected), single-threaded CPU oracle; "
-                                       "frames/s = band fraction / step time"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "build": "g++ " + " ".join(oracle.CFLAGS),
+                             "sample": f"per step one whole frame of {WORKLOAD} (projection, binning, fwd, L1 loss, "
+                                       "bwd, Adam, assoc), single-threaded parity build of the CPU oracle"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -289,46 +315,55 @@ def _traffic_for(kernel):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def serving_section(dev, seconds, seed=4):
+def serving_section(dev, seconds, seed=4, short_seconds=5.0):
     """Eight agents (maps log-uniform in 100k..2M Gaussians; four at 640x480,
     four at 1200x680), Poisson tracking requests at 30 Hz each and a mapping
-    request with every 5th frame.  The continuous-batching server (150 GB HBM
-    budget, and a reduced 2 GB budget that forces swapping) against the plain
-    per-request path, on the same trace in real time and all at once."""
+    request with every 5th frame.  The continuous-batching server against the
+    plain per-request path on the same trace: in real time at 30 Hz per agent
+    for `seconds` (the workload's 30 s), at 90 Hz and at half of the agents'
+    resident footprint as HBM budget (admission binds, agents are swapped to
+    pinned host memory) for `short_seconds`, and saturated (every request of
+    a 2 s trace submitted at t = 0)."""
     from paper_2412_09723_gb300 import scenes
-    from paper_2412_09723_gb300.serve import Server, latency_stats, make_agents_workload, poisson_trace
+    from paper_2412_09723_gb300.serve import Server, _agent_bytes, latency_stats, make_agents_workload, poisson_trace
 
     spec = scenes.serving_agents(seed=seed)
     srv = Server(dev, 150 << 30, max_batch=8, n_streams=2)
     make_agents_workload(srv, spec, frames_per_agent=8)
     out = {"workload": "serve_8_agents_100k_2M_poisson_30hz", "agents": len(spec),
-           "map_sizes": [s["n"] for s in spec], "trace_seconds": seconds}
+           "map_sizes": [s["n"] for s in spec]}
 
-    def run(kind, realtime, budget, rate=30.0):
+    def run(kind, realtime, budget, rate=30.0, secs=seconds):
         srv.reset(budget)
         srv.prepare()
-        reqs = poisson_trace(len(spec), rate, seconds, 8, map_every=5, seed=seed)
+        reqs = poisson_trace(len(spec), rate, secs, 8, map_every=5, seed=seed)
         span = srv.serve(reqs, realtime=realtime) if kind == "served" else srv.serve_plain(reqs, realtime=realtime)
         st = latency_stats(reqs, span)
         st["swaps"] = srv.swaps
+        st["trace_s"] = secs
         return st
 
-    from paper_2412_09723_gb300.serve import _agent_bytes
-
-    out["served"] = run("served", True, 150 << 30)
-    out["plain"] = run("plain", True, 150 << 30)
+    full = 150 << 30
+    rows = {}
+    rows["30hz"] = (run("served", True, full), run("plain", True, full))
     footprint = sum(_agent_bytes(s.agent) for s in srv.slots if s.agent is not None)
-    out["served_90hz"] = run("served", True, 150 << 30, rate=90.0)
-    out["plain_90hz"] = run("plain", True, 150 << 30, rate=90.0)
-    out["served_saturated"] = run("served", False, 150 << 30)
-    out["plain_saturated"] = run("plain", False, 150 << 30)
+    rows["90hz"] = (run("served", True, full, 90.0, short_seconds), run("plain", True, full, 90.0, short_seconds))
+    rows["saturated"] = (run("served", False, full, secs=2.0), run("plain", False, full, secs=2.0))
     half = footprint // 2
+    rows["30hz_half_budget"] = (run("served", True, half, secs=short_seconds),
+                                run("plain", True, half, secs=short_seconds))
+    rows["saturated_half_budget"] = (run("served", False, half, secs=2.0), run("plain", False, half, secs=2.0))
     out["resident_footprint_bytes"] = footprint
     out["reduced_budget_bytes"] = half
-    out["served_half_budget"] = run("served", True, half)
-    out["served_saturated_half_budget"] = run("served", False, half)
+    for k, (a, b) in rows.items():
+        out["served_" + k] = a
+        out["plain_" + k] = b
     srv.reset()
-    return out
+    keys = ("frames_per_s", "p50_ms", "p99_ms")
+    summary = {k: {"served": {x: round(a[x], 3) for x in keys}, "plain": {x: round(b[x], 3) for x in keys},
+                   "p99_ratio_plain_over_served": round(b["p99_ms"] / a["p99_ms"], 3)}
+               for k, (a, b) in rows.items()}
+    return out, summary
 
 
 def multi_agent_section(dev, steps, flush, seed_base=2):
@@ -778,9 +813,9 @@ def main():
     multi = None
     if not args.no_multi:
         multi = multi_agent_section(dev, K, flush)
-    served = None
+    served, served_summary = None, None
     if not args.no_serve:
-        served = serving_section(dev, args.serve_seconds)
+        served, served_summary = serving_section(dev, args.serve_seconds)
 
     aligned = None
     if not args.no_align:
@@ -797,18 +832,19 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
                 "ms_per_step": total_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSSIANS, "width": cam.width,
-                           "height": cam.height, "duplicates_K": int(agent.fb.k_dev.item()),
-                           "l2": "flushed between steps (256 MiB write)", "iterations_per_episode": EPISODE,
-                           "mode": "CUDA graph replay" if use_graph else "eager stream-ordered launches",
-                           "parallelism": f"{world} independent agent(s), one per GPU"},
+                "config": _config(cam, agent.fb.k_dev.item()),
+                "mode": "CUDA graph replay" if use_graph else "eager stream-ordered launches",
                 "p50_ms": statistics.median(step_ms), "p99_ms": _pct(step_ms, 99),
                 "tracked_frames_per_s": value / EPISODE,
                 "wall_s_timed": t_wall, "gpu_launches": launches, "roofline": roofline, "kernels": breakdown,
                 "frame_roofline": (dict(frame_roofline, frac=frame_roofline["t_bound_ms"] / (total_ms_max / K))
                                    if frame_roofline else None),
-                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "batched_multi_agent": multi,
-                "serving": served, "alignment": aligned, "next_rows": nxt}
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "next_rows": nxt, "alignment": aligned,
+                "serving": served, "batched_multi_agent": multi,
+                "batched_vs_plain": ({"batched_fps": round(multi["value"], 1), "plain_fps": round(multi["plain_value"], 1),
+                                      "batched_p99_ms": round(multi["p99_ms"], 3),
+                                      "plain_p99_ms": round(multi["plain_p99_ms"], 3)} if multi else None),
+                "served_vs_plain": served_summary}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

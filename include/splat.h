@@ -57,7 +57,7 @@ enum {
   SPLAT_EINVAL = 1,    /* null pointer, bad size or misaligned buffer */
   SPLAT_ECAPACITY = 2, /* (device status) an output buffer was too small */
   SPLAT_ECUDA = 3,     /* a kernel launch or CUDA runtime call failed */
-  SPLAT_ETIMEOUT = 4,  /* (device status) a bounded wait gave up */
+  SPLAT_ETIMEOUT = 4,  /* reserved: no call returns or raises it (no kernel of this library waits) */
   SPLAT_ENUMERIC = 8   /* (device status) a linear system was not positive definite */
 };
 
@@ -224,6 +224,8 @@ int splat_bin_sort(const splat_projected *proj, int64_t n, const splat_camera *c
  *   rejected with SPLAT_EINVAL and a message.
  *   The first call on a device looks up the array's device address (with
  *   that device current): make that first call before any stream capture.
+ *   Later calls look the address up again unless their stream is capturing,
+ *   so that a device reset (which reloads the module) is followed.
  *   All calls share the one array and leave their data in it; calls that
  *   may overlap on the GPU (several streams or threads) race and must be
  *   serialised by the caller.

@@ -13,6 +13,7 @@ float32 instantiation (bit-level parity; project exp) or the float64 one
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -23,23 +24,47 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "splat_oracle.cpp")
 _LIB = os.path.join(_HERE, "_build", "libsplat_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "libsplat_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
+_active = threading.local()
 
 CFLAGS = ["-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+# the timed CPU baseline: the same source with its OpenMP loops switched on
+CFLAGS_OMP = CFLAGS + ["-fopenmp"]
+
+
+def _build_one(path, flags, force):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", *flags, _SRC, "-o", tmp])
+        os.replace(tmp, path)
+    return path
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (float ops in source order, no contraction)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", *CFLAGS, _SRC, "-o", tmp])
-        os.replace(tmp, _LIB)
-    return _LIB
+    """Compile the oracle with g++ (float ops in source order, no contraction);
+    single-threaded: this is the build every parity check uses."""
+    return _build_one(_LIB, CFLAGS, force)
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile the multi-threaded build of the same source (the timed CPU
+    baseline; its forward results equal the parity build's, its adjoint sums
+    are grouped per thread)."""
+    return _build_one(_LIB_OMP, CFLAGS_OMP, force)
 
 
 def lib():
+    """The library the calls below use: the parity build, or the
+    multi-threaded build inside a `parallel()` block."""
+    L = getattr(_active, "lib", None)
+    return L if L is not None else _parity_lib()
+
+
+def _parity_lib():
     global _lib
     with _lock:
         if _lib is None:
@@ -49,6 +74,37 @@ def lib():
     return _lib
 
 
+def _omp_lib():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            L = ctypes.CDLL(build_omp())
+            _declare(L)
+            _lib_omp = L
+    return _lib_omp
+
+
+@contextlib.contextmanager
+def parallel(threads: int | None = None):
+    """Run the oracle calls of the block on the multi-threaded build (for
+    timing only; parity checks use the single-threaded build).  Yields the
+    number of threads."""
+    L = _omp_lib()
+    if threads:
+        L.oracle_set_threads(int(threads))
+    prev = getattr(_active, "lib", None)
+    _active.lib = L
+    try:
+        yield int(L.oracle_threads())
+    finally:
+        _active.lib = prev
+
+
+def threads() -> int:
+    """Threads of the library in use (1 for the parity build)."""
+    return int(lib().oracle_threads())
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -56,6 +112,10 @@ _F = ctypes.c_float
 
 
 def _declare(L):
+    L.oracle_threads.argtypes = []
+    L.oracle_threads.restype = ctypes.c_int
+    L.oracle_set_threads.argtypes = [ctypes.c_int]
+    L.oracle_set_threads.restype = None
     L.oracle_exp_f32.argtypes = [_I64, _P, _P]
     L.oracle_exp_f32.restype = None
     for suf in ("f32", "f64"):
@@ -150,10 +210,13 @@ def bin_sort(scene, w2c, cam):
     return keys[:k], vals[:k], ranges
 
 
-def render_fwd(scene, w2c, cam, bg, dtype=np.float32, rows=None):
+def render_fwd(scene, w2c, cam, bg, dtype=np.float32, rows=None, signature=None):
     """Forward render: rgb [H,W,3], depth, sil, t_final [H,W], n_contrib, max_id
-    [H,W] int32, the hash of all discrete decisions and the summed n_contrib.
+    [H,W] int32, the hash of all discrete decisions (`signature`: by default
+    in the parity build only; 0 when not taken) and the summed n_contrib.
     `rows` = (row0, row1) renders only that band (other pixels stay zero)."""
+    if signature is None:
+        signature = threads() == 1
     H, W = cam.height, cam.width
     args = _scene_args(scene, dtype) + [_c(scene.rgb, dtype)]
     w = _c(w2c, dtype)
@@ -167,7 +230,7 @@ def render_fwd(scene, w2c, cam, bg, dtype=np.float32, rows=None):
     getattr(lib(), f"oracle_render_fwd_{_suffix(dtype)}")(
         scene.n, *map(_ptr, args), _ptr(w), _ptr(ci), _ptr(cf), _ptr(b), _ptr(out["rgb"]),
         _ptr(out["depth"]), _ptr(out["sil"]), _ptr(out["t_final"]), _ptr(out["n_contrib"]),
-        _ptr(out["max_id"]), _ptr(sig), _ptr(npairs), *(rows or (0, H)))
+        _ptr(out["max_id"]), _ptr(sig) if signature else None, _ptr(npairs), *(rows or (0, H)))
     out["signature"] = int(sig[0])
     out["n_pairs"] = int(npairs[0])
     return out

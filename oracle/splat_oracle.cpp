@@ -46,6 +46,15 @@
 // depth order; central finite differences of the double adjoint for every
 // parameter and the pose; L1 loss and Adam closed forms; brute-force
 // association.  No function here is left unpinned.
+//
+// Threads.  The parity build is single-threaded (compiled without -fopenmp,
+// every loop below runs in source order).  Built with -fopenmp, the same
+// source is the timed CPU baseline: the projection runs over Gaussians and
+// the per-tile sorts over tiles in parallel (same results), the forward
+// render over tiles (same results), and the adjoint over tiles with one
+// screen-space gradient buffer per thread, summed in thread order afterwards
+// (the per-pixel arithmetic is unchanged; only the grouping of the sums over
+// pixels and Gaussians differs).
 
 #include <algorithm>
 #include <cmath>
@@ -53,6 +62,10 @@
 #include <cstring>
 #include <limits>
 #include <vector>
+
+#if defined(_OPENMP)
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -284,6 +297,9 @@ template <typename T> struct Scene {
 template <typename T>
 std::vector<Proj<T>> project_all(const Scene<T>& S, const T* w2c, const Cam<T>& cam) {
   std::vector<Proj<T>> P((size_t)S.n);
+#if defined(_OPENMP)
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t g = 0; g < S.n; ++g)
     P[g] = project_one<T>(S.mean + 3 * g, S.log_scale + 3 * g, S.quat + 4 * g, S.logit[g], w2c, cam);
   return P;
@@ -359,8 +375,11 @@ std::vector<std::vector<int32_t>> bin_all(const std::vector<Proj<T>>& P, const C
       for (int tx = x0; tx <= x1; ++tx) bins[(size_t)ty * ntx + tx].push_back((int32_t)g);
     }
   }
-  for (auto& b : bins)
-    std::sort(b.begin(), b.end(), [&](int32_t i, int32_t j) {
+#if defined(_OPENMP)
+#pragma omp parallel for schedule(dynamic, 8)
+#endif
+  for (int64_t t = 0; t < (int64_t)bins.size(); ++t)
+    std::sort(bins[t].begin(), bins[t].end(), [&](int32_t i, int32_t j) {
       if (P[i].z != P[j].z) return P[i].z < P[j].z;
       return i < j;
     });
@@ -472,19 +491,34 @@ int render_fwd(const Scene<T>& S, const T* w2c, const Cam<T>& cam, const T* bg,
     sig.add(P[g].radius);
     for (int k = 0; k < 4; ++k) sig.add(P[g].rect[k]);
   }
-  for (int y = row0; y < row1; ++y)
-    for (int x = 0; x < cam.width; ++x) {
-      const auto& list = bins[(size_t)(y / TILE) * ntx + (x / TILE)];
-      PixOut<T> o = composite_pixel<T>(x, y, list, P, S.rgb, bg, nullptr, signature ? &sig : nullptr);
-      const size_t i = (size_t)y * cam.width + x;
-      for (int k = 0; k < 3; ++k) out_rgb[3 * i + k] = o.rgb[k];
-      out_depth[i] = o.depth;
-      out_sil[i] = o.sil;
-      out_tfin[i] = o.tfin;
-      out_n[i] = o.ncontrib;
-      out_id[i] = o.maxid;
-      pairs += o.ncontrib;
+  auto pixel = [&](int x, int y, Sig* sg) -> int64_t {
+    const auto& list = bins[(size_t)(y / TILE) * ntx + (x / TILE)];
+    PixOut<T> o = composite_pixel<T>(x, y, list, P, S.rgb, bg, nullptr, sg);
+    const size_t i = (size_t)y * cam.width + x;
+    for (int k = 0; k < 3; ++k) out_rgb[3 * i + k] = o.rgb[k];
+    out_depth[i] = o.depth;
+    out_sil[i] = o.sil;
+    out_tfin[i] = o.tfin;
+    out_n[i] = o.ncontrib;
+    out_id[i] = o.maxid;
+    return o.ncontrib;
+  };
+#if defined(_OPENMP)
+  if (!signature) {  // timing build: tiles in parallel (every pixel computed as below)
+    const int ty0 = row0 / TILE, ty1 = (row1 + TILE - 1) / TILE;
+    const int64_t nt = (int64_t)(ty1 - ty0) * ntx;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : pairs)
+    for (int64_t t = 0; t < nt; ++t) {
+      const int ty = ty0 + (int)(t / ntx), tx = (int)(t % ntx);
+      for (int y = std::max(row0, ty * TILE); y < std::min(row1, ty * TILE + TILE); ++y)
+        for (int x = tx * TILE; x < std::min(cam.width, tx * TILE + TILE); ++x) pairs += pixel(x, y, nullptr);
     }
+    if (n_pairs) *n_pairs = pairs;
+    return 0;
+  }
+#endif
+  for (int y = row0; y < row1; ++y)
+    for (int x = 0; x < cam.width; ++x) pairs += pixel(x, y, signature ? &sig : nullptr);
   if (signature) *signature = sig.h;
   if (n_pairs) *n_pairs = pairs;
   return 0;
@@ -659,16 +693,65 @@ int render_bwd(const Scene<T>& S, const T* w2c, const Cam<T>& cam, const T* bg, 
   auto bins = bin_all(P, cam, row0 / TILE, (row1 + TILE - 1) / TILE);
   const int ntx = cam.tiles_x();
   std::vector<Grad2D<T>> G2((size_t)S.n);
+  auto pixel = [&](int x, int y, std::vector<Contrib<T>>& rec, std::vector<Grad2D<T>>& G) {
+    const auto& list = bins[(size_t)(y / TILE) * ntx + (x / TILE)];
+    rec.clear();
+    PixOut<T> o = composite_pixel<T>(x, y, list, P, S.rgb, bg, &rec, nullptr);
+    const size_t i = (size_t)y * cam.width + x;
+    const T gC[3] = {g_rgb[3 * i], g_rgb[3 * i + 1], g_rgb[3 * i + 2]};
+    pixel_adjoint<T>(rec, o, gC, g_depth ? g_depth[i] : T(0), g_sil ? g_sil[i] : T(0), P, S.rgb, bg, G);
+  };
+#if defined(_OPENMP)
+  // timing build: tiles in parallel, one screen-space gradient buffer per
+  // thread, the buffers summed in thread order; then the projection adjoint
+  // over Gaussians in parallel with one pose gradient per thread
+  const int nth = omp_get_max_threads();
+  std::vector<std::vector<Grad2D<T>>> G2t((size_t)nth);
+  std::vector<T> pose_t((size_t)nth * 6, T(0));
+  {
+    const int ty0 = row0 / TILE, ty1 = (row1 + TILE - 1) / TILE;
+    const int64_t nt = (int64_t)(ty1 - ty0) * ntx;
+#pragma omp parallel
+    {
+      const int th = omp_get_thread_num();
+      G2t[th].assign((size_t)S.n, Grad2D<T>());
+      std::vector<Contrib<T>> rec;
+#pragma omp for schedule(dynamic, 4)
+      for (int64_t t = 0; t < nt; ++t) {
+        const int ty = ty0 + (int)(t / ntx), tx = (int)(t % ntx);
+        for (int y = std::max(row0, ty * TILE); y < std::min(row1, ty * TILE + TILE); ++y)
+          for (int x = tx * TILE; x < std::min(cam.width, tx * TILE + TILE); ++x) pixel(x, y, rec, G2t[th]);
+      }
+#pragma omp for schedule(static)
+      for (int64_t g = 0; g < S.n; ++g) {
+        Grad2D<T>& d = G2[g];
+        for (int k = 0; k < nth; ++k) {
+          const Grad2D<T>& e = G2t[k][g];
+          d.du += e.du; d.dv += e.dv; d.dca += e.dca; d.dcb += e.dcb; d.dcc += e.dcc;
+          d.dlam += e.dlam; d.dz += e.dz;
+          for (int c = 0; c < 3; ++c) d.drgb[c] += e.drgb[c];
+        }
+      }
+#pragma omp for schedule(static)
+      for (int64_t g = 0; g < S.n; ++g) {
+        const Grad2D<T>& d = G2[g];
+        for (int k = 0; k < 3; ++k) d_rgb[3 * g + k] += d.drgb[k];
+        if (d2d) {
+          T* o = d2d + 10 * g;
+          o[0] = d.du; o[1] = d.dv; o[2] = d.dca; o[3] = d.dcb; o[4] = d.dcc;
+          o[5] = d.dlam; o[6] = d.drgb[0]; o[7] = d.drgb[1]; o[8] = d.drgb[2]; o[9] = d.dz;
+        }
+        project_adjoint<T>(g, S, w2c, cam, d, d_mean, d_ls, d_q, d_logit, &pose_t[6 * (size_t)th]);
+      }
+    }
+  }
+  for (int k = 0; k < nth; ++k)
+    for (int j = 0; j < 6; ++j) d_pose[j] += pose_t[6 * (size_t)k + j];
+  return 0;
+#endif
   std::vector<Contrib<T>> rec;
   for (int y = row0; y < row1; ++y)
-    for (int x = 0; x < cam.width; ++x) {
-      const auto& list = bins[(size_t)(y / TILE) * ntx + (x / TILE)];
-      rec.clear();
-      PixOut<T> o = composite_pixel<T>(x, y, list, P, S.rgb, bg, &rec, nullptr);
-      const size_t i = (size_t)y * cam.width + x;
-      const T gC[3] = {g_rgb[3 * i], g_rgb[3 * i + 1], g_rgb[3 * i + 2]};
-      pixel_adjoint<T>(rec, o, gC, g_depth ? g_depth[i] : T(0), g_sil ? g_sil[i] : T(0), P, S.rgb, bg, G2);
-    }
+    for (int x = 0; x < cam.width; ++x) pixel(x, y, rec, G2);
   for (int64_t g = 0; g < S.n; ++g) {
     const Grad2D<T>& d = G2[g];
     for (int k = 0; k < 3; ++k) d_rgb[3 * g + k] += d.drgb[k];
@@ -688,6 +771,23 @@ int render_bwd(const Scene<T>& S, const T* w2c, const Cam<T>& cam, const T* bg, 
 // C ABI (host pointers; caller owns every buffer).
 // Test switch: 0 keeps whole rects as tile members (the images must not change).
 extern "C" void oracle_set_exact_tiles(int on) { g_exact_tiles = on != 0; }
+
+// Threads the loops above use: 1 in the parity build; in the -fopenmp build
+// the OpenMP maximum (OMP_NUM_THREADS, else every core), or `n` once set.
+extern "C" int oracle_threads(void) {
+#if defined(_OPENMP)
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+extern "C" void oracle_set_threads(int n) {
+#if defined(_OPENMP)
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
 
 // cam_i = {width, height}; cam_f = {fx, fy, cx, cy, z_near, max_dist}; w2c = 4x4 row-major.
 // ============================================================================

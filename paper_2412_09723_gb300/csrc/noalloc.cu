@@ -11,11 +11,14 @@
 // every device that loads the library and stays there until the process
 // exits.  Host code cannot pass the array's symbol to a kernel (on the host
 // the name stands for a host-side shadow, not a device address), so the
-// device address is looked up with cudaGetSymbolAddress once per device, with
-// that device current, on the first call made on it.
+// device address is looked up with cudaGetSymbolAddress, with the device
+// current: on the first call made on it, and again on every later call whose
+// stream is not capturing (after a device reset the module, and with it the
+// array, may sit at a new address).
 #include <mutex>
 
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace splat {
 
@@ -27,12 +30,17 @@ static __device__ __align__(256) unsigned char g_bin_sort_scratch[kStaticScratch
 static std::mutex g_scratch_mu;
 static void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
-static int static_scratch(void** out) {
+static int static_scratch(cudaStream_t s, void** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(SPLAT_ECUDA, "splat_bin_sort_static: no current CUDA device");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess)
+    return fail(SPLAT_ECUDA, "splat_bin_sort_static: cudaStreamIsCapturing failed");
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] && cs != cudaStreamCaptureStatusNone)
+    return fail(SPLAT_EINVAL, "splat_bin_sort_static: first call on device %d made during stream capture", dev);
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_bin_sort_scratch);
     if (e != cudaSuccess || !p)
@@ -56,7 +64,8 @@ extern "C" int splat_bin_sort_static(const splat_projected* proj, int64_t n, con
   if (!cam) return fail(SPLAT_EINVAL, "splat_bin_sort_static: null camera");
   if (n < 0 || capacity < 0) return fail(SPLAT_EINVAL, "splat_bin_sort_static: negative size");
   if (cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "splat_bin_sort_static: bad image size");
-  const int64_t n_tiles = (int64_t)((cam->width + 15) / 16) * ((cam->height + 15) / 16);
+  const CamK ck = make_camk(*cam);
+  const int64_t n_tiles = (int64_t)ck.tiles_x * ck.tiles_y;
   const size_t need = splat_bin_sort_workspace_size(n, capacity, (int32_t)n_tiles);
   if (need == 0 || need > kStaticScratchBytes)
     return fail(SPLAT_EINVAL,
@@ -64,7 +73,7 @@ extern "C" int splat_bin_sort_static(const splat_projected* proj, int64_t n, con
                 "static array; use splat_bin_sort with a caller workspace",
                 (long long)n, (long long)capacity, need, kStaticScratchBytes);
   void* ws = nullptr;
-  const int rc = static_scratch(&ws);
+  const int rc = static_scratch(reinterpret_cast<cudaStream_t>(stream), &ws);
   if (rc) return rc;
   return splat_bin_sort(proj, n, cam, keys, vals, capacity, k_dev, ranges, status, ws, kStaticScratchBytes, stream);
 }

@@ -10,8 +10,6 @@ path; the batched / graph path keeps fixed capacities instead).
 """
 from __future__ import annotations
 
-import math
-
 import torch
 
 from . import binding as B
@@ -149,21 +147,3 @@ def render(mean, log_scale, quat, opacity_logit, rgb, w2c, cam: Camera, bg=(0.0,
     if delta is None:
         delta = torch.zeros(6, dtype=torch.float32, device=mean.device)
     return SplatRender.apply(mean, log_scale, quat, opacity_logit, rgb, delta, w2c, cam, tuple(bg))
-
-
-def se3_exp(delta: torch.Tensor) -> torch.Tensor:
-    """4x4 exp of a 6-vector (rho, phi), for host-side pose bookkeeping."""
-    d = delta.detach().double().cpu()
-    rho, phi = d[:3], d[3:]
-    th = float(torch.linalg.norm(phi))
-    K = torch.tensor([[0, -phi[2], phi[1]], [phi[2], 0, -phi[0]], [-phi[1], phi[0], 0]], dtype=torch.float64)
-    I = torch.eye(3, dtype=torch.float64)
-    if th < 1e-10:
-        R, V = I + K, I + 0.5 * K
-    else:
-        R = I + math.sin(th) / th * K + (1 - math.cos(th)) / th ** 2 * K @ K
-        V = I + (1 - math.cos(th)) / th ** 2 * K + (th - math.sin(th)) / th ** 3 * K @ K
-    T = torch.eye(4, dtype=torch.float64)
-    T[:3, :3] = R
-    T[:3, 3] = V @ rho
-    return T

@@ -2,8 +2,11 @@
 
 Integer and bit-level outputs (projection, tile rects, sort keys, Gaussian
 ids, tile ranges, contributor counts, maximum-weight ids, association pairs)
-must match exactly; rendered colour / depth / silhouette / transmittance to
-1e-4 absolute; gradients to |g - g_ref| <= 1e-3 |g_ref| + 1e-3 rms(g_ref)."""
+must match exactly; rendered colour / depth / silhouette / transmittance too
+(both sides take the same IEEE operations in the same order; the stated
+tolerance is 1e-4 absolute, and the check is bit for bit so that a change of
+operation order cannot hide under it); gradients to
+|g - g_ref| <= 1e-3 |g_ref| + 1e-3 rms(g_ref)."""
 import numpy as np
 import pytest
 
@@ -146,6 +149,7 @@ def _check_image(fb, ref):
     for k in ("rgb", "depth", "sil", "t_final"):
         d = np.abs(got[k].astype(np.float64) - ref[k])
         assert d.max() <= ATOL_IMG, (k, d.max())
+        assert np.array_equal(_bits(got[k]), _bits(ref[k])), (k, "not bit-exact", d.max())
     assert np.array_equal(got["n_contrib"], ref["n_contrib"])
     assert np.array_equal(got["max_id"], ref["max_id"])
 
@@ -306,19 +310,35 @@ def test_adam(dev):
     np.testing.assert_allclose(tv.cpu().numpy(), rv, rtol=1e-6, atol=1e-7)
 
 
-def test_pose_step_matches_host_retraction(dev):
+def test_pose_step_matches_oracle_adam_and_retraction(dev):
+    """Five pose steps with gradients that change size and sign from step to
+    step, so that the moments and bias corrections of steps t > 1 matter: the
+    device moments equal the oracle's Adam (run on the 6-vector, the update of
+    a zero parameter being the step delta itself), and the device pose the
+    oracle's chain w2c_t = exp(delta_t^) w2c_(t-1) in float64 from the same
+    start, within float32 rounding."""
+    from oracle import consensus as C
     from paper_2412_09723_gb300 import binding as B
-    from paper_2412_09723_gb300.rasterizer import se3_exp
 
     w0 = scenes.perturbed_w2c(3, 0.2, 15.0)
     w = _w(w0, dev)
-    g = torch.tensor([0.3, -0.2, 0.1, 0.05, -0.4, 0.2], device=dev)
     m, v = torch.zeros(6, device=dev), torch.zeros(6, device=dev)
-    B.splat_pose_step(w, g, m, v, torch.tensor([1], dtype=torch.int32, device=dev), 0.01, 0.002)
-    # first Adam step = -lr sign(g)
-    d = -np.sign(g.cpu().numpy()) * np.array([0.01] * 3 + [0.002] * 3)
-    ref = se3_exp(torch.tensor(d)).numpy() @ w0.astype(np.float64)
-    np.testing.assert_allclose(w.cpu().numpy(), ref, atol=2e-6)
+    lr_t, lr_r = 0.01, 0.002
+    rng = np.random.default_rng(21)
+    ref_w = w0.astype(np.float64)
+    rm, rv = np.zeros(6, np.float32), np.zeros(6, np.float32)
+    for t in range(1, 6):
+        g = (rng.normal(size=6) * 10.0 ** rng.uniform(-2, 1, 6)).astype(np.float32)
+        B.splat_pose_step(w, torch.as_tensor(g, device=dev), m, v, torch.tensor([t], dtype=torch.int32, device=dev),
+                          lr_t, lr_r)
+        d_t, rm[:3], rv[:3] = oracle.adam(np.zeros(3, np.float32), g[:3], rm[:3], rv[:3], t, lr_t)
+        d_r, rm[3:], rv[3:] = oracle.adam(np.zeros(3, np.float32), g[3:], rm[3:], rv[3:], t, lr_r)
+        ref_w = C.se3_exp(np.concatenate([d_t, d_r]).astype(np.float64)) @ ref_w
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(m.cpu().numpy(), rm, rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(v.cpu().numpy(), rv, rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(w.cpu().numpy(), ref_w, atol=2e-6 * t)
+    assert np.abs(ref_w - w0).max() > 1e-3  # the steps did move the pose
 
 
 def test_assoc_two_maps(dev):

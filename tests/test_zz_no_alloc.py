@@ -57,6 +57,32 @@ def test_static_scratch_matches_workspace_path_twice():
         assert torch.equal(ranges, fb.ranges)
 
 
+def test_static_scratch_call_allocates_nothing():
+    """After a first call, a call with preallocated outputs changes neither
+    torch's allocated bytes nor the device's free memory."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_09723_gb300 import binding as B
+
+    dev = torch.device("cuda:0")
+    sc, w2c, cam = scenes.workload_small_forward()[:3]
+    fb = _setup(sc, w2c, cam, dev)
+    keys = torch.zeros(fb.capacity, dtype=torch.int64, device=dev)
+    vals = torch.zeros(fb.capacity, dtype=torch.int32, device=dev)
+    ranges = torch.zeros_like(fb.ranges)
+    k_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    call = lambda: B.splat_bin_sort_static(fb.cproj, fb.n, fb.ccam, keys, vals, fb.capacity, k_dev, ranges, status)
+    call()
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(dev), torch.cuda.mem_get_info(dev)[0])
+    call()
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(dev), torch.cuda.mem_get_info(dev)[0])
+    assert after == before
+    assert int(status.item()) == 0 and torch.equal(vals[: int(k_dev.item())], fb.vals[: int(fb.k_dev.item())])
+
+
 def test_static_scratch_rejects_oversized_problems():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
