@@ -433,11 +433,13 @@ SSIM_OPS_PER_PX_CH = 211  # separable 11-tap window: 5 sums x 22 FMA + ~30 (fwd)
 MAHA_OPS_PER_PAIR = 420   # two covariances (~2 x 60), rotation of one (~54), 3x3 inverse (~30), J^T M J etc. (~210)
 
 
-def _time_calls(fn, reps, flush):
+def _time_calls(fn, reps, flush, reset=None):
     import torch
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
     for k in range(reps):
+        if reset is not None:  # outside the timed events, like the flush
+            reset()
         flush.fill_(float(k))
         ev[k][0].record()
         fn()
@@ -501,24 +503,21 @@ def next_rows_section(dev, flush, reps=20):
     ga, gb = B.gaussians_struct(*pa), B.gaussians_struct(*pb)
     m_dev = torch.tensor([m], dtype=torch.int64, device=dev)
     T = torch.as_tensor(T0, device=dev)
-    sys_ = torch.zeros(28, dtype=torch.float64, device=dev)
+    sys_ = torch.zeros(32, dtype=torch.float64, device=dev)  # left zero by every solve
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     T_keep = T.clone()
 
-    def maha():
-        sys_.zero_()
-        B.splat_mahalanobis_system(ga, gb, pairs, wts, m_dev, T, sys_, 0.02)
-        B.splat_mahalanobis_step(sys_, T, None, st)
-        T.copy_(T_keep)
+    def maha():  # one launch: the system, and the solve and step in its last CTA
+        B.splat_mahalanobis_system_step(ga, gb, pairs, wts, m_dev, T, sys_, None, st, 0.02)
 
     maha()
-    ms = _time_calls(maha, reps, flush)
+    ms = _time_calls(maha, reps, flush, reset=lambda: T.copy_(T_keep))
     ops = MAHA_OPS_PER_PAIR * m
     out["mahalanobis_100k_pairs"] = {
         "ms": ms, "tops": ops / (ms * 1e-3) / 1e12, "alu_frac": ops / (ms * 1e-3) / 1e12 / alu,
         "achieved_gbs": 92 * m / (ms * 1e-3) / 1e9,
         "work": f"{MAHA_OPS_PER_PAIR} ops and 92 bytes (two Gaussians' mean, log-scale, quaternion; pair; weight) "
-                "per pair; includes the zeroing of the system and the one-thread 6x6 solve"}
+                "per pair; one launch: the system, the 6x6 solve and the step in the last CTA"}
     del pa, pb, a, b
 
     # 3. Algorithm 1 pruning of a 2M map with its Adam moments (15 columns)
@@ -754,7 +753,7 @@ def main():
     peaks, peak_kind = _peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak_tops = SMS * FP32_LANES * sm_mhz * 1e6 / 1e12
-    if top == "render_bwd_kernel":
+    if top in ("render_bwd_kernel", "render_bwd_persistent"):
         ops = OPS_WALK * q_walk + OPS_CONTRIB_BWD * q_used
     elif top == "render_fwd_kernel":
         ops = OPS_WALK * q_walk + OPS_CONTRIB_FWD * q_used

@@ -196,6 +196,11 @@ int splat_project(const splat_gaussians *g, const splat_camera *cam, const float
  *   capacity: number of slots in keys/vals (< 2^31)
  *   k_dev:    device int64[1]: receives K, the number of duplicates
  *   ranges:   device uint32[2 * n_tiles]
+ *   tile_order: device uint32[n_tiles] or NULL: receives every tile id once,
+ *             the tiles with the longest lists first (descending in steps of
+ *             an eighth of an octave of the list length; ties in any order):
+ *             the order in which splat_render_bwd's persistent launch takes
+ *             the tiles, so that it ends on short lists
  *   status:   device int32[1]: set to SPLAT_ECAPACITY when K > capacity (the
  *             sorted lists are then incomplete; resize and call again);
  *             never cleared by the library
@@ -205,8 +210,8 @@ int splat_project(const splat_gaussians *g, const splat_camera *cam, const float
 size_t splat_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t n_tiles);
 int splat_bin_sort(const splat_projected *proj, int64_t n, const splat_camera *cam,
                    uint64_t *keys, uint32_t *vals, int64_t capacity, int64_t *k_dev,
-                   uint32_t *ranges, int32_t *status, void *ws, size_t ws_bytes,
-                   splat_stream_t stream);
+                   uint32_t *ranges, uint32_t *tile_order, int32_t *status, void *ws,
+                   size_t ws_bytes, splat_stream_t stream);
 
 /*
  * splat_bin_sort_static -- splat_bin_sort without a caller workspace.  (The
@@ -258,6 +263,8 @@ int splat_render_fwd(const splat_projected *proj, const float *rgb, int64_t n,
  * optimisation, Sec. 3.5 steps 3-4).
  *   proj: the splat_project output for this map, camera and pose (its radius
  *     is read: Gaussians it culled get no gradient and are skipped).
+ *   tile_order: splat_bin_sort's heavy-first tile order, or NULL for the
+ *     natural order (the result is the same either way).
  *   d_rgb [H,W,3], d_depth [H,W], d_sil [H,W] (d_depth, d_sil may be NULL).
  *   fwd: the image of the forward call (t_final, n_contrib are read).
  *   out: Gaussian-parameter gradients, ACCUMULATED (+=); the caller zeroes.
@@ -266,14 +273,21 @@ int splat_render_fwd(const splat_projected *proj, const float *rgb, int64_t n,
  *   d2d: device float[n,10] or NULL: receives the screen-space gradients
  *     (du, dv, d conic a, b, c, d opacity, d rgb[3], d depth) (overwritten).
  *   ws: workspace of splat_render_bwd_workspace_size(n) bytes, 16-byte
- *     aligned (always required: the screen-space gradients accumulate there).
- * Atomics make the summation order, and so the last bits, vary between runs.
+ *     aligned (always required: the screen-space gradients accumulate there,
+ *     [n,12] float rows as splat_project_bwd reads them).
+ *   out, d_pose and d2d all NULL: only the screen-space adjoint runs, and its
+ *     gradients are left in ws for splat_project_bwd or splat_project_bwd_adam.
+ * The tile lists are walked in two independent parts per tile (positions
+ * before and after a split point, front to back and back to front) by one
+ * persistent launch; atomics make the summation order, and so the last bits,
+ * vary between runs.
  * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
  */
 size_t splat_render_bwd_workspace_size(int64_t n);
 int splat_render_bwd(const splat_gaussians *g, const splat_projected *proj,
                      const splat_camera *cam, const float *w2c, const uint32_t *vals,
-                     const uint32_t *ranges, const splat_image *fwd, const float *bg,
+                     const uint32_t *ranges, const uint32_t *tile_order,
+                     const splat_image *fwd, const float *bg,
                      const float *d_rgb, const float *d_depth, const float *d_sil,
                      const splat_gaussians_grad *out, float *d_pose, float *d2d, void *ws,
                      size_t ws_bytes, splat_stream_t stream);
@@ -292,6 +306,59 @@ int splat_render_bwd(const splat_gaussians *g, const splat_projected *proj,
 int splat_project_bwd(const splat_gaussians *g, const splat_projected *proj, const splat_camera *cam,
                       const float *w2c, const float *grad2d, const splat_gaussians_grad *out,
                       float *d_pose, float *d2d, splat_stream_t stream);
+
+/*
+ * splat_project_bwd_adam -- splat_project_bwd with the map's Adam step taken
+ * in the same launch (map optimisation, Sec. 3.4 step 4, the SplaTAM-style
+ * optimiser): every Gaussian's 14 parameters move by one bias-corrected Adam
+ * step with the gradient the projection adjoint gives it -- the gradient
+ * splat_project_bwd would accumulate into zeroed arrays, 0 for a Gaussian the
+ * projection culled -- the same update as splat_adam_groups with those
+ * gradients, bit for bit.  No gradient array is read or written.  One part
+ * of the launch runs the adjoint and update of the kept Gaussians (radius >
+ * 0), the other the zero-gradient update of the culled ones, side by side;
+ * elements of culled Gaussians whose moments are both +0 are left exactly
+ * as they are (their update is nothing).  The pose gradient is accumulated
+ * into d_pose (if not NULL) as by splat_project_bwd.
+ *   g: the map; its arrays are UPDATED IN PLACE (the const of splat_gaussians
+ *     does not hold for this call).  m, v: device moments of the same shapes.
+ *   lr: HOST float[5], the step sizes of mean, log_scale, quat,
+ *     opacity_logit, rgb; step: DEVICE int32[1] holding t >= 1.
+ *   proj, cam, w2c, grad2d: as splat_project_bwd.
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_project_bwd_adam(const splat_gaussians *g, const splat_projected *proj,
+                           const splat_camera *cam, const float *w2c, const float *grad2d,
+                           const splat_gaussians_grad *m, const splat_gaussians_grad *v,
+                           const float *lr, float beta1, float beta2, float eps,
+                           const int32_t *step, float *d_pose, splat_stream_t stream);
+
+/*
+ * splat_render_fwd_l1 -- splat_render_fwd with the L1 terms of the loss of
+ * Eq. (optim) (Sec. 3.5) taken in the same pass, while each pixel's colour and
+ * depth are still in registers: for the rendered C, D and targets C*, D*,
+ *   loss    += w_rgb mean|C - C*| + w_depth mean|D - D*|
+ *              (means over the 3 H W colour and H W depth values),
+ *   d_rgb    = (w_rgb / 3HW) sign(C - C*),  d_depth = (w_depth / HW) sign(D - D*),
+ *   sign(0) = 0.  The gradients are written (not accumulated) and equal those of
+ *   splat_loss_l1 on the rendered images bit for bit; the loss is summed in a
+ *   different order (per tile, then one float atomic per tile).
+ *   l1: descriptor below (device arrays [H,W,3] / [H,W]; loss: device float,
+ *   accumulated, the caller zeroes it).  Errors: as splat_render_fwd.
+ */
+typedef struct {
+  const float *t_rgb;    /* target colour [H,W,3] */
+  const float *t_depth;  /* target depth [H,W] */
+  float w_rgb, w_depth;  /* weights of the two L1 terms */
+  float *d_rgb;          /* out: dL/dC [H,W,3] */
+  float *d_depth;        /* out: dL/dD [H,W] */
+  float *loss;           /* in/out: device float, += L (may be NULL) */
+} splat_l1;
+
+int splat_render_fwd_l1(const splat_projected *proj, const float *rgb, int64_t n,
+                        const uint32_t *vals, const uint32_t *ranges, const splat_camera *cam,
+                        const float *bg, const splat_image *out, const splat_l1 *l1,
+                        splat_stream_t stream);
 
 /*
  * Several views in one launch (batched differentiable rendering across
@@ -318,6 +385,10 @@ typedef struct {
   const float *d_sil;
   float *grad2d;         /* backward only: [n,12] screen-space gradients, 16-byte aligned;
                             zeroed and filled by splat_render_bwd_batch */
+  const splat_l1 *l1;    /* forward only, optional: the view's L1 loss terms taken in the
+                            forward's epilogue (as splat_render_fwd_l1); NULL = none */
+  const uint32_t *tile_order; /* backward only, optional: splat_bin_sort's heavy-first tile
+                                 order for this view; NULL = natural order */
 } splat_view;
 
 /* Execution shape (does not change any result): shared-memory batch of
@@ -489,6 +560,24 @@ int splat_mahalanobis_system(const splat_gaussians *map_a, const splat_gaussians
  */
 int splat_mahalanobis_step(const double *sys, float *T, double *delta_out, int32_t *status,
                            splat_stream_t stream);
+
+/*
+ * splat_mahalanobis_system_step -- splat_mahalanobis_system followed by
+ * splat_mahalanobis_step in one launch: the pairs' contributions are added to
+ * sys, and the CTA that finishes last solves the whole accumulated system
+ * (including what earlier splat_mahalanobis_system calls added, e.g. other
+ * keyframes' pairs), applies T <- exp(delta^) T and sets sys back to zero.
+ *   sys: device double[32], 8-byte aligned: the 28 sums as in
+ *   splat_mahalanobis_system, then a counter; zero-filled before the first
+ *   call, and left zero-filled by every call (no clearing between
+ *   iterations).  T: updated in place (read by the pairs' terms first).
+ *   delta_out (device double[6] or NULL), status: as splat_mahalanobis_step.
+ * Calls on the same sys must not overlap.  Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_mahalanobis_system_step(const splat_gaussians *map_a, const splat_gaussians *map_b,
+                                  const int32_t *pairs, const int32_t *weights, const int64_t *m_dev,
+                                  int64_t capacity, float *T, float max_dist, double *sys,
+                                  double *delta_out, int32_t *status, splat_stream_t stream);
 
 /*
  * splat_prune -- Gaussian splat pruning (Algorithm 1, Suppl. "Gaussian Splat

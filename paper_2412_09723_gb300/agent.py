@@ -6,9 +6,12 @@ RGB-D observation and every work buffer on the device.  One step is the whole
 hot path of the method for one frame:
 
   splat_project -> splat_bin_sort -> splat_render_fwd      (render, Sec. 3.3)
-  -> splat_loss_l1 (L1 colour + w_depth L1 depth, L1 terms of Eq. optim)
-  -> splat_render_bwd (gradients to every Gaussian parameter and the pose)
-  -> splat_adam per parameter group (mapping, Sec. 3.4 step 4)
+     with the L1 terms of Eq. optim (L1 colour + w_depth L1 depth) and their
+     image gradients taken in the same pass (splat_render_fwd_l1)
+  -> splat_render_bwd (screen-space adjoint of the render)
+  -> splat_project_bwd_adam (projection adjoint to every Gaussian parameter
+     and the pose, with the map's Adam step in the same launch: mapping,
+     Sec. 3.4 step 4; tracking-only steps use splat_project_bwd)
   -> splat_pose_step (render-driven tracking)
   -> splat_assoc of the rendered maximum-weight ids against the observation's
      ids (render-based association, Sec. 3.5 step 2).
@@ -18,6 +21,7 @@ asked for), so it can run back to back, be timed with events, or be captured.
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
 
 import torch
@@ -48,21 +52,41 @@ class Agent:
     """Resident map + optimiser state + buffers of one agent."""
 
     def __init__(self, scene, w2c, cam: Camera, device, cfg: StepConfig | None = None, capacity: int | None = None,
-                 want_used: bool = False):
+                 want_used: bool = False, state=None, side=None):
+        """`scene`: the map (numpy arrays, copied in synchronously), or None
+        with `state`: the pinned host tensors of a swapped-out agent's
+        _state() (map, moments, pose, pose moments, step), copied in
+        asynchronously on the current stream, like every allocation and fill
+        here, so that a swap-in needs no host synchronisation.  `side`: a
+        stream to reuse for the side work (a new one by default)."""
         self.cfg = cfg or StepConfig()
         self.cam = cam
         self.device = device
-        self.params = [torch.as_tensor(a, dtype=torch.float32, device=device).contiguous() for a in scene.arrays()]
+        if state is not None:
+            def dev(t):
+                d = torch.empty(t.shape, dtype=t.dtype, device=device)
+                d.copy_(t, non_blocking=True)
+                return d
+            self.params = [dev(t) for t in state[:5]]
+            self.m = [dev(t) for t in state[5:10]]
+            self.v = [dev(t) for t in state[10:15]]
+            self.w2c = dev(state[15])
+        else:
+            self.params = [torch.as_tensor(a, dtype=torch.float32, device=device).contiguous() for a in scene.arrays()]
+            self.m = [torch.zeros_like(p) for p in self.params]
+            self.v = [torch.zeros_like(p) for p in self.params]
+            self.w2c = torch.as_tensor(w2c, dtype=torch.float32, device=device).contiguous().clone()
         self.n = self.params[0].shape[0]
         self.grads = [torch.zeros_like(p) for p in self.params]
-        self.m = [torch.zeros_like(p) for p in self.params]
-        self.v = [torch.zeros_like(p) for p in self.params]
-        self.w2c = torch.as_tensor(w2c, dtype=torch.float32, device=device).contiguous().clone()
         # per-step accumulators in one block, cleared by one launch: d_pose [6], loss [1], association status [1]
         self._acc = torch.zeros(8, dtype=torch.float32, device=device)
         self.d_pose = self._acc[0:6]
         self.pose_m = torch.zeros(6, dtype=torch.float32, device=device)
         self.pose_v = torch.zeros(6, dtype=torch.float32, device=device)
+        self.t_dev = torch.zeros(1, dtype=torch.int32, device=device)  # Adam step, advanced on the device
+        if state is not None:
+            for dst, src in zip((self.pose_m, self.pose_v, self.t_dev), state[16:19]):
+                dst.copy_(src, non_blocking=True)
         self.fb = FrameBuffers(self.n, cam, device, capacity=capacity, want_used=want_used)
         H, W = cam.height, cam.width
         self.obs_rgb = torch.zeros(H, W, 3, dtype=torch.float32, device=device)
@@ -79,16 +103,28 @@ class Agent:
         self.m_dev = torch.zeros(1, dtype=torch.int64, device=device)
         self.assoc_status = self._acc[7:8].view(torch.int32)
         self.assoc_ws = torch.empty(max(1, B.splat_assoc_workspace_size(npix)), dtype=torch.uint8, device=device)
-        self.side = torch.cuda.Stream(device=device)  # the association runs here, beside the backward chain
+        self.side = side if side is not None else torch.cuda.Stream(device=device)  # association, beside the backward
         self.host_in = None  # pinned (rgb, depth) the step copies its observation from, or None
         self.host_out = None  # pinned (loss, w2c) the step writes its results to, or None
         self.cg = B.gaussians_struct(*self.params)
         self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads))
         self.steps_done = 0
-        self.t_dev = torch.zeros(1, dtype=torch.int32, device=device)  # Adam step, advanced on the device
         self.grads_clean = True  # host-side: the gradient buffers hold zeros
+        self._make_adam()
+        self._make_l1()
+
+    def _make_adam(self):
         names = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
-        self.adam = B.AdamGroups(self.params, self.grads, self.m, self.v, [self.cfg.lr[k] for k in names])
+        self.lrs = [self.cfg.lr[k] for k in names]
+        self.adam = B.AdamGroups(self.params, self.grads, self.m, self.v, self.lrs)
+        self.cm = B.CGaussiansGrad(*(B._p(t) for t in self.m))
+        self.cv = B.CGaussiansGrad(*(B._p(t) for t in self.v))
+
+    def _make_l1(self):
+        """The L1 loss descriptor the forward render fills (observation as
+        target, gradient images, loss accumulator)."""
+        self.cl1 = B.l1_struct(self.obs_rgb, self.obs_depth, self.cfg.w_rgb, self.cfg.w_depth, self.g_rgb,
+                               self.g_depth, self.loss)
 
     # -- observation ---------------------------------------------------------
     def set_observation(self, rgb, depth, ids=None, t_final=None, stream=None):
@@ -109,7 +145,7 @@ class Agent:
         to, every step and also inside a captured graph: put the next frame in
         `rgb` / `depth` before a step, read `loss` / `w2c` after synchronising.
         The frame's copy runs on the side stream and overlaps the projection,
-        binning and forward render; only the loss waits for it.  Calling it
+        binning; the forward render, which takes the loss, waits for it.  Calling it
         with no arguments detaches the buffers.  A graph captured before must
         be captured again."""
         H, W = self.cam.height, self.cam.width
@@ -153,89 +189,105 @@ class Agent:
         B.splat_render_fwd(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg, stream)
 
     # The step in phases, so that a multi-agent batch can interleave them.
+    def phase_clear(self, s):
+        """Start a step: zero its accumulators (d_pose, loss, association
+        status) and, when a previous step left them filled, the parameter
+        gradients; advance the device Adam step count."""
+        with torch.cuda.stream(s):
+            self._acc.zero_()
+            self.t_dev.add_(1)
+            if not self.grads_clean:  # the fused adjoint + Adam never fills them
+                for g in self.grads:
+                    g.zero_()
+        self.grads_clean = True
+        self.steps_done += 1
+
     def phase_pre(self, s, sync_check: bool = False):
         """Projection and binning."""
         project(self.cg, self.w2c, self.fb, s)
         bin_sort(self.fb, s, sync_check=sync_check)
 
     def phase_render(self, s):
+        """Forward render with the L1 loss terms and their image gradients
+        (needs phase_clear before it, and the observation in place)."""
         fb = self.fb
-        B.splat_render_fwd(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg, s)
+        B.splat_render_fwd_l1(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg,
+                              self.cl1, s)
 
     def phase_loss(self, s):
+        """Clear, then the L1 terms as a separate pass over a rendered image
+        (the unfused form of phase_clear + the loss part of phase_render)."""
         cfg, fb = self.cfg, self.fb
-        with torch.cuda.stream(s):
-            self._acc.zero_()  # d_pose, loss and the association status
-            if not self.grads_clean:  # the fused Adam step leaves them cleared when mapping
-                for g in self.grads:
-                    g.zero_()
-        self.grads_clean = True
+        self.phase_clear(s)
         B.splat_loss_l1(fb.image["rgb"], fb.image["depth"], self.obs_rgb, self.obs_depth, cfg.w_rgb, cfg.w_depth,
                         self.g_rgb, self.g_depth, self.loss, s)
 
     def phase_backward(self, s):
-        self.grads_clean = False
+        """Screen-space adjoint of the render (left in the backward workspace)."""
         fb = self.fb
         B.splat_render_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.vals, fb.ranges, fb.cimg, self.cfg.bg,
-                           self.g_rgb, self.g_depth, None, self.cgr, self.d_pose, None, fb.bwd_ws, s)
+                           self.g_rgb, self.g_depth, None, None, None, None, fb.bwd_ws, s, tile_order=fb.tile_order)
 
     def phase_project_backward(self, s):
-        """Projection adjoint of screen-space gradients already in bwd_ws."""
-        self.grads_clean = False
+        """Projection adjoint of the screen-space gradients in the backward
+        workspace: with mapping on, fused with the map's Adam step (the map
+        moves, no gradient array is written); otherwise into the gradient
+        arrays.  Either way the pose gradient goes to d_pose."""
         fb = self.fb
-        B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cgr, self.d_pose, None, s)
+        if self.cfg.map:
+            B.splat_project_bwd_adam(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cm, self.cv, self.lrs,
+                                     self.t_dev, self.d_pose, stream=s)
+        else:
+            self.grads_clean = False
+            B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cgr, self.d_pose, None, s)
 
     def phase_update(self, s, assoc: bool = True, pose_stream=None):
-        """Adam on the map and the pose step (on `pose_stream` when given: the
-        two are independent once the projection adjoint is done), then the
-        association when `assoc`."""
+        """The pose step (on `pose_stream` when given, after the projection
+        adjoint on s), then the association when `assoc`.  The map's Adam
+        step is part of phase_project_backward."""
         cfg = self.cfg
-        self.steps_done += 1
-        with torch.cuda.stream(s):
-            self.t_dev.add_(1)
-        t = self.t_dev
         if cfg.track:
             ps = s
             if pose_stream is not None:
                 pose_stream.wait_stream(s)
                 ps = pose_stream
-            B.splat_pose_step(self.w2c, self.d_pose, self.pose_m, self.pose_v, t, cfg.pose_lr[0], cfg.pose_lr[1],
-                              stream=ps)
-        if cfg.map:
-            B.splat_adam_groups(self.adam, t, zero_grad=True, stream=s)
-            self.grads_clean = True
+            B.splat_pose_step(self.w2c, self.d_pose, self.pose_m, self.pose_v, self.t_dev, cfg.pose_lr[0],
+                              cfg.pose_lr[1], stream=ps)
         if assoc:
             self.phase_assoc(s)
 
     def phase_assoc(self, s):
         """Association of the rendered ids with the observation's (needs the
-        forward render and the accumulators cleared in phase_loss)."""
+        forward render and the accumulators cleared in phase_clear)."""
         cfg, fb = self.cfg, self.fb
-        if cfg.assoc:  # the status word was cleared with the other accumulators in phase_loss
+        if cfg.assoc:  # the status word was cleared with the other accumulators in phase_clear
             B.splat_assoc(fb.image["max_id"], fb.image["t_final"], self.obs_id, self.obs_tfinal, self.n, self.n,
                           cfg.t_max, self.pairs, self.counts, self.assoc_cap, self.m_dev, self.assoc_status,
                           self.assoc_ws, s)
 
     def step(self, stream=None, sync_check: bool = False):
-        """One step.  The association depends only on the forward render, so it
-        runs on a side stream forked after the loss, overlapping the backward
-        render and the projection adjoint; the pose step follows it there,
-        beside the map's Adam; the side stream is joined at the end."""
+        """One step.  The accumulators are cleared (and the frame copied in,
+        with host buffers attached) on a side stream while the map is projected
+        and binned; the forward render takes the loss.  The association depends
+        only on the forward render, so it runs on the side stream forked after
+        it, overlapping the backward render and the projection adjoint; the
+        pose step follows it there, beside the map's Adam; the side stream is
+        joined at the end."""
         s = torch.cuda.current_stream() if stream is None else stream
-        if self.host_in is not None:  # the frame arrives while the map is projected, binned and rendered
-            self.side.wait_stream(s)
+        self.side.wait_stream(s)
+        self.phase_clear(self.side)
+        if self.host_in is not None:
             with torch.cuda.stream(self.side):
                 self.obs_rgb.copy_(self.host_in[0], non_blocking=True)
                 self.obs_depth.copy_(self.host_in[1], non_blocking=True)
         self.phase_pre(s, sync_check)
+        s.wait_stream(self.side)
         self.phase_render(s)
-        if self.host_in is not None:
-            s.wait_stream(self.side)
-        self.phase_loss(s)
         if self.cfg.assoc:
             self.side.wait_stream(s)
             self.phase_assoc(self.side)
         self.phase_backward(s)
+        self.phase_project_backward(s)
         self.phase_update(s, assoc=False, pose_stream=self.side)
         s.wait_stream(self.side)
         if self.host_out is not None:
@@ -259,6 +311,8 @@ class Agent:
         v.d_depth = B._p(self.g_depth)
         v.d_sil = None
         v.grad2d = B._p(fb.bwd_ws)
+        v.l1 = ctypes.pointer(self.cl1)
+        v.tile_order = B._p(fb.tile_order)
         return v
 
     # -- pruning -----------------------------------------------------------------
@@ -291,8 +345,7 @@ class Agent:
         self.grads_clean = True
         self.fb = FrameBuffers(k, self.cam, self.device, capacity=self.fb.capacity, want_keys=self.fb.want_keys,
                                want_used="n_used" in self.fb.image)
-        names = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
-        self.adam = B.AdamGroups(self.params, self.grads, self.m, self.v, [self.cfg.lr[k2] for k2 in names])
+        self._make_adam()
         self.graph = None
         self._snap = None
         return k

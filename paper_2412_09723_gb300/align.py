@@ -28,7 +28,7 @@ from .scenes import Camera
 
 class Alignment:
     def __init__(self, map_b, keyframes, targets, cam: Camera, T_rel0, device, loss="paper",
-                 weights=(0.8, 0.2, 0.1), lr=(1e-3, 4e-4), shape=(256, 4, 256, 7), capacity=None, want_keys=False,
+                 weights=(0.8, 0.2, 0.1), lr=(1e-3, 4e-4), shape=(256, 4, 64, 8), capacity=None, want_keys=False,
                  map_a=None):
         """map_b: Scene of B's map (B's world); keyframes: list of A's w2c
         (4x4); targets: list of dicts with A's renders ("rgb", "depth",
@@ -68,7 +68,7 @@ class Alignment:
             arrs = map_a.arrays() if hasattr(map_a, "arrays") else map_a
             self.map_a = [torch.as_tensor(a, dtype=torch.float32, device=device).contiguous() for a in arrs]
             self.cga = B.gaussians_struct(*self.map_a)
-        self.sys = torch.zeros(28, dtype=torch.float64, device=device)
+        self.sys = torch.zeros(32, dtype=torch.float64, device=device)  # 28 sums + a counter, left zero by every solve
         self.delta = torch.zeros(6, dtype=torch.float64, device=device)
         self.maha_status = torch.zeros(1, dtype=torch.int32, device=device)
         self.targets = targets
@@ -105,6 +105,7 @@ class Alignment:
         v.d_depth = B._p(self.g_depth[k])
         v.d_sil = None
         v.grad2d = B._p(fb.bwd_ws)
+        v.tile_order = B._p(fb.tile_order)
 
     def size_capacity(self, headroom=1.5):
         """One host read per view to size the duplicate buffers."""
@@ -198,15 +199,18 @@ class Alignment:
             raise ValueError("the Mahalanobis alignment needs map_a")
         s = torch.cuda.current_stream() if s is None else s
         views = range(len(self.fbs)) if views is None else views
+        views = list(views)
         for _ in range(iters):
             self.render(s)
-            with torch.cuda.stream(s):
-                self.sys.zero_()
-            for k in views:
+            for i, k in enumerate(views):
                 self.associate(k, t_max, s)
-                B.splat_mahalanobis_system(self.cga, self.cg, self.pairs, self.counts if weighted else None,
-                                           self.m_dev, self.T, self.sys, max_dist, s)
-            B.splat_mahalanobis_step(self.sys, self.T, self.delta, self.maha_status, s)
+                w = self.counts if weighted else None
+                if i + 1 < len(views):  # accumulate; the last view's call also solves, steps and clears sys
+                    B.splat_mahalanobis_system(self.cga, self.cg, self.pairs, w, self.m_dev, self.T, self.sys,
+                                               max_dist, s)
+                else:
+                    B.splat_mahalanobis_system_step(self.cga, self.cg, self.pairs, w, self.m_dev, self.T, self.sys,
+                                                    self.delta, self.maha_status, max_dist, s)
 
     def associate(self, k, t_max=0.5, s=None):
         """Distinct (A id, B id) pairs of keyframe k with pixel counts (device

@@ -2,13 +2,13 @@
 agents, Sec. 3.6 of the paper: intra-agent work is independent per agent).
 
 One batched step:
-  per agent, on its own stream:  projection, binning
-  all agents, ONE persistent launch:  forward render   (splat_render_fwd_batch)
-  per agent, on its own stream:  L1 loss
+  per agent, on its own stream:  accumulators cleared, projection, binning
+  all agents, ONE persistent launch:  forward render with each agent's L1 loss
+                                      terms (splat_render_fwd_batch)
   all agents, ONE persistent launch:  backward render  (splat_render_bwd_batch)
-  per agent, on its own stream:  projection adjoint, Adam
-  per agent, on a side stream forked after the loss:  association (overlaps
-  the backward launch), then the pose step beside Adam; joined at the end
+  per agent, on its own stream:  projection adjoint with the map's Adam step
+  per agent, on a side stream forked after the forward:  association
+  (overlapping the backward launch), then the pose step; joined at the end
 The whole step is captured into one CUDA graph (the per-agent streams are
 forked from and joined back into the capture stream), so a replay is a single
 host call.  The persistent launches' execution shape (shared-memory batch of
@@ -30,8 +30,8 @@ def shape_of(t):
     return B.CBatchShape(*t)
 
 
-DEFAULT_SHAPE = (256, 4, 256, 7)
-CANDIDATES = [(fb, fc, bb, bc) for fb in (128, 256) for fc in (2, 4, 8) for bb in (128, 256) for bc in (4, 7, 10)]
+DEFAULT_SHAPE = (256, 4, 64, 8)
+CANDIDATES = [(fb, fc, bb, bc) for fb in (128, 256) for fc in (4, 8) for bb in (64, 128) for bc in (6, 8, 10)]
 
 
 class MultiAgentBatch:
@@ -57,9 +57,8 @@ class MultiAgentBatch:
 
     def step(self, stream=None):
         s = torch.cuda.current_stream() if stream is None else stream
-        self._fork(s, lambda a, st: a.phase_pre(st))
+        self._fork(s, lambda a, st: (a.phase_clear(st), a.phase_pre(st)))
         B.splat_render_fwd_batch(self.views, self.shape, self.ws, s)
-        self._fork(s, lambda a, st: a.phase_loss(st))
         for a in self.agents:  # associations overlap the backward launch and the updates
             a.side.wait_stream(s)
             a.phase_assoc(a.side)

@@ -49,10 +49,15 @@ class CImage(ctypes.Structure):
                 ("max_id", _c_p), ("n_used", _c_p)]
 
 
+class CL1(ctypes.Structure):
+    _fields_ = [("t_rgb", _c_p), ("t_depth", _c_p), ("w_rgb", _c_f), ("w_depth", _c_f), ("d_rgb", _c_p),
+                ("d_depth", _c_p), ("loss", _c_p)]
+
+
 class CView(ctypes.Structure):
     _fields_ = [("proj", CProjected), ("rgb", _c_p), ("n", _c_i64), ("vals", _c_p), ("ranges", _c_p),
                 ("cam", CCamera), ("bg", ctypes.c_float * 3), ("image", CImage), ("d_rgb", _c_p), ("d_depth", _c_p),
-                ("d_sil", _c_p), ("grad2d", _c_p)]
+                ("d_sil", _c_p), ("grad2d", _c_p), ("l1", ctypes.POINTER(CL1)), ("tile_order", _c_p)]
 
 
 class CColumn(ctypes.Structure):
@@ -75,13 +80,15 @@ _SIGS = {
     "splat_profile_read": ([_c_p, _c_sz, _c_p, _c_p, _c_i32, _c_p], ctypes.c_int),
     "splat_project": ([_c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_bin_sort_workspace_size": ([_c_i64, _c_i64, _c_i32], _c_sz),
-    "splat_bin_sort": ([_c_p, _c_i64, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
+    "splat_bin_sort": ([_c_p, _c_i64, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
     "splat_bin_sort_static_scratch_bytes": ([], _c_sz),
     "splat_bin_sort_static": ([_c_p, _c_i64, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_render_fwd": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_render_fwd_l1": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_render_bwd_workspace_size": ([_c_i64], _c_sz),
-    "splat_render_bwd": ([_c_p] * 15 + [_c_sz, _c_p], ctypes.c_int),
+    "splat_render_bwd": ([_c_p] * 16 + [_c_sz, _c_p], ctypes.c_int),
     "splat_project_bwd": ([_c_p] * 8 + [_c_p], ctypes.c_int),
+    "splat_project_bwd_adam": ([_c_p] * 8 + [_c_f, _c_f, _c_f, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_batch_workspace_size": ([], _c_sz),
     "splat_render_fwd_batch": ([_c_p, _c_i32, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
     "splat_render_bwd_batch": ([_c_p, _c_i32, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
@@ -100,6 +107,8 @@ _SIGS = {
                               _c_sz, _c_p], ctypes.c_int),
     "splat_mahalanobis_system": ([_c_p, _c_p, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_f, _c_p, _c_p], ctypes.c_int),
     "splat_mahalanobis_step": ([_c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_mahalanobis_system_step": ([_c_p, _c_p, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_f, _c_p, _c_p, _c_p, _c_p],
+                                      ctypes.c_int),
     "splat_prune_workspace_size": ([_c_i64], _c_sz),
     "splat_prune": ([_c_p, _c_f, _c_f, _c_f, _c_p, _c_i32, _c_p, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
     "splat_exp_f32": ([_c_p, _c_p, _c_i64, _c_p], ctypes.c_int),
@@ -214,10 +223,11 @@ def splat_bin_sort_workspace_size(n, capacity, n_tiles) -> int:
     return int(load().splat_bin_sort_workspace_size(n, capacity, n_tiles))
 
 
-def splat_bin_sort(proj: CProjected, n, cam: CCamera, keys, vals, capacity, k_dev, ranges, status, ws, stream=None):
+def splat_bin_sort(proj: CProjected, n, cam: CCamera, keys, vals, capacity, k_dev, ranges, status, ws, stream=None,
+                   tile_order=None):
     _check("splat_bin_sort", load().splat_bin_sort(
-        ctypes.byref(proj), n, ctypes.byref(cam), _p(keys), _p(vals), capacity, _p(k_dev), _p(ranges), _p(status),
-        _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
+        ctypes.byref(proj), n, ctypes.byref(cam), _p(keys), _p(vals), capacity, _p(k_dev), _p(ranges),
+        _p(tile_order), _p(status), _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def splat_bin_sort_static_scratch_bytes() -> int:
@@ -239,18 +249,30 @@ def splat_render_fwd(proj: CProjected, rgb, n, vals, ranges, cam: CCamera, bg, i
         _stream(stream)))
 
 
+def l1_struct(t_rgb, t_depth, w_rgb, w_depth, d_rgb, d_depth, loss) -> CL1:
+    return CL1(_p(t_rgb), _p(t_depth), w_rgb, w_depth, _p(d_rgb), _p(d_depth), _p(loss))
+
+
+def splat_render_fwd_l1(proj: CProjected, rgb, n, vals, ranges, cam: CCamera, bg, image: CImage, l1: CL1,
+                        stream=None):
+    bgc = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    _check("splat_render_fwd_l1", load().splat_render_fwd_l1(
+        ctypes.byref(proj), _p(rgb), n, _p(vals), _p(ranges), ctypes.byref(cam), bgc, ctypes.byref(image),
+        ctypes.byref(l1), _stream(stream)))
+
+
 def splat_render_bwd_workspace_size(n) -> int:
     return int(load().splat_render_bwd_workspace_size(n))
 
 
 def splat_render_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, vals, ranges, image: CImage, bg,
-                     d_rgb, d_depth, d_sil, grads: CGaussiansGrad, d_pose, d2d, ws, stream=None):
+                     d_rgb, d_depth, d_sil, grads: CGaussiansGrad, d_pose, d2d, ws, stream=None, tile_order=None):
     bgc = (ctypes.c_float * 3)(*[float(x) for x in bg])
     wsb = 0 if ws is None else ws.numel() * ws.element_size()
     _check("splat_render_bwd", load().splat_render_bwd(
         ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(vals), _p(ranges),
-        ctypes.byref(image), bgc, _p(d_rgb), _p(d_depth), _p(d_sil), ctypes.byref(grads), _p(d_pose), _p(d2d),
-        _p(ws), wsb, _stream(stream)))
+        _p(tile_order), ctypes.byref(image), bgc, _p(d_rgb), _p(d_depth), _p(d_sil), None if grads is None else ctypes.byref(grads),
+        _p(d_pose), _p(d2d), _p(ws), wsb, _stream(stream)))
 
 
 def splat_project_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, grad2d, grads: CGaussiansGrad,
@@ -258,6 +280,16 @@ def splat_project_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c
     _check("splat_project_bwd", load().splat_project_bwd(
         ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(grad2d), ctypes.byref(grads),
         _p(d_pose), _p(d2d), _stream(stream)))
+
+
+def splat_project_bwd_adam(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, grad2d, m: CGaussiansGrad,
+                           v: CGaussiansGrad, lr, step, d_pose, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    """`gaussians`' arrays are updated in place; `lr`: 5 step sizes (mean,
+    log_scale, quat, opacity_logit, rgb); `step`: device int32[1] (t >= 1)."""
+    lrc = (ctypes.c_float * 5)(*[float(x) for x in lr])
+    _check("splat_project_bwd_adam", load().splat_project_bwd_adam(
+        ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(grad2d), ctypes.byref(m),
+        ctypes.byref(v), lrc, beta1, beta2, eps, _p(step), _p(d_pose), _stream(stream)))
 
 
 def splat_batch_workspace_size() -> int:
@@ -362,6 +394,15 @@ def splat_mahalanobis_system(map_a: CGaussians, map_b: CGaussians, pairs, weight
 def splat_mahalanobis_step(sys, T, delta, status, stream=None):
     _check("splat_mahalanobis_step", load().splat_mahalanobis_step(_p(sys), _p(T), _p(delta), _p(status),
                                                                     _stream(stream)))
+
+
+def splat_mahalanobis_system_step(map_a: CGaussians, map_b: CGaussians, pairs, weights, m_dev, T, sys, delta, status,
+                                  max_dist=0.0, stream=None):
+    """`sys`: device float64[32], zero before the first call and left zero by
+    every call; T updated in place."""
+    _check("splat_mahalanobis_system_step", load().splat_mahalanobis_system_step(
+        ctypes.byref(map_a), ctypes.byref(map_b), _p(pairs), _p(weights), _p(m_dev), pairs.shape[0], _p(T),
+        max_dist, _p(sys), _p(delta), _p(status), _stream(stream)))
 
 
 def splat_prune_workspace_size(n) -> int:

@@ -107,20 +107,7 @@ int launch_loss_l1(const float* rgb, const float* depth, const float* trgb, cons
 // ----------------------------------------------------------------------------
 // Adam
 // ----------------------------------------------------------------------------
-// 1 - beta^t in float, from a device-resident step count.
-__device__ __forceinline__ float bias_correction(float beta, const int32_t* step) {
-  return 1.0f - powf(beta, (float)(*step));
-}
-
-// One Adam update.  The bias corrections enter as reciprocals (computed once
-// per thread) and the step's division is the fast one: the update differs
-// from the textbook expression by a few ulp of the step, not of the parameter.
-__device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, float lr, float b1, float b2,
-                                            float ibc1, float ibc2, float eps) {
-  m = b1 * m + (1.0f - b1) * g;
-  v = b2 * v + (1.0f - b2) * g * g;
-  p = p - __fdividef(lr * (m * ibc1), sqrtf(v * ibc2) + eps);
-}
+// bias_correction and adam_update: internal.cuh.
 
 __global__ void __launch_bounds__(256) adam_kernel(float* __restrict__ p, const float* __restrict__ g,
                                                    float* __restrict__ m, float* __restrict__ v, int64_t n, float lr,
@@ -287,7 +274,7 @@ __global__ void exp_kernel(const float* __restrict__ x, float* __restrict__ y, i
 
 using namespace splat;
 
-extern "C" int32_t splat_abi_version(void) { return 2; }
+extern "C" int32_t splat_abi_version(void) { return 3; }
 
 extern "C" const char* splat_last_error(void) { return g_last_error; }
 

@@ -1,7 +1,8 @@
 // consensus.cu -- the inter-agent consensus terms and map pruning.
 //
 // * Loss of Eq. (optim) (Sec. 3.5 step 4): L1 colour, SSIM and L1 depth
-//   terms with their image gradients.  SSIM uses an 11 x 11 Gaussian window
+//   terms with their image gradients, in two passes (the L1 terms ride on
+//   the first, which has each pixel's colours staged).  SSIM uses an 11 x 11 Gaussian window
 //   (sigma 1.5) over a zero-padded image; one CTA computes a 32 x 16 block of
 //   all three channels: the 42 x 26 patch of both images is staged in shared
 //   memory, the window is applied separably (rows, then columns) to the five
@@ -85,9 +86,16 @@ constexpr int kSsTXp = kSsTX + 1;
 
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
+// The L1 terms of the loss ride along: each output pixel's colour residual
+// x - y (already staged) and depth residual give the L1 subgradients
+// (written to d_rgb / d_depth; the adjoint kernel adds the SSIM part) and
+// their share of the loss.
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
+                                                       const float* __restrict__ dep, const float* __restrict__ tdep,
                                                        int H, int W, SsimWin win, float loss_scale, float ssim_scale,
-                                                       float* __restrict__ abc, float* __restrict__ loss) {
+                                                       float sc, float sd, float* __restrict__ d_rgb,
+                                                       float* __restrict__ d_depth, float* __restrict__ abc,
+                                                       float* __restrict__ loss) {
   __shared__ float2 sxy[3][kSsPY][kSsPXp];  // (x, y) of every channel
   __shared__ float2 h1[kSsPY][kSsTXp];      // horizontal sums of (x, y)
   __shared__ float2 h2[kSsPY][kSsTXp];      // ... of (x^2, y^2)
@@ -111,7 +119,7 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
   }
   __syncthreads();
   const size_t plane = (size_t)H * W;
-  float sum_1ms = 0.f, sum_s = 0.f;
+  float sum_1ms = 0.f, sum_s = 0.f, sum_c = 0.f, sum_d = 0.f;
   for (int ch = 0; ch < 3; ++ch) {
     if (t < kSsHItems) {
       const int r = t / (kSsTX / kSsRun), c0 = kSsRun * (t % (kSsTX / kSsRun));
@@ -190,14 +198,27 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
       abc[6 * plane + i] = Cm;
       sum_1ms += 1.f - sv;
       sum_s += sv;
+      // L1 terms (sign(0) = 0), as splat_loss_l1
+      const size_t pix = (size_t)gy * W + gx;
+      const float2 xy = sxy[ch][ty0 + j + kSsR][tx + kSsR];
+      const float e = xy.x - xy.y;
+      d_rgb[3 * pix + ch] = e > 0.f ? sc : (e < 0.f ? -sc : 0.f);
+      sum_c += fabsf(e);
+      if (ch == 0) {
+        const float ed = dep[pix] - tdep[pix];
+        d_depth[pix] = ed > 0.f ? sd : (ed < 0.f ? -sd : 0.f);
+        sum_d += fabsf(ed);
+      }
     }
     __syncthreads();  // the horizontal sums are rewritten for the next channel
   }
   const float t0 = block_sum_256(sum_1ms, red);
   __syncthreads();
   const float t1 = block_sum_256(sum_s, red);
+  __syncthreads();
+  const float t2 = block_sum_256(sc * sum_c + sd * sum_d, red);
   if (t == 0) {
-    atomicAdd(&loss[0], t0 * loss_scale);
+    atomicAdd(&loss[0], t0 * loss_scale + t2);
     atomicAdd(&loss[1], t1 * ssim_scale);
   }
 }
@@ -326,11 +347,21 @@ __device__ __forceinline__ void gaussian_cov(const MapK& g, int i, float S[6]) {
 
 constexpr int kSysN = 28;  // 21 (H upper) + 6 (g) + 1 (cost)
 
+__device__ void maha_solve_apply(const double* __restrict__ sys, float* __restrict__ T,
+                                 double* __restrict__ delta_out, int32_t* __restrict__ status);
+
+// With SOLVE the CTA that finishes last (a counter after the system in sys,
+// taken after every CTA's atomics are fenced) solves the accumulated system,
+// applies the step to T and zeroes sys and the counter for the next call; no
+// CTA waits on another.  Every CTA reads T before it counts itself, so the
+// update cannot reach a CTA still reading T.
+template <bool SOLVE>
 __global__ void __launch_bounds__(256) mahalanobis_kernel(MapK A, MapK Bm, const int32_t* __restrict__ pairs,
                                                           const int32_t* __restrict__ weights,
                                                           const int64_t* __restrict__ m_dev, int64_t capacity,
-                                                          const float* __restrict__ T, float max_d2,
-                                                          double* __restrict__ sys) {
+                                                          float* __restrict__ T, float max_d2,
+                                                          double* __restrict__ sys, double* __restrict__ delta_out,
+                                                          int32_t* __restrict__ status) {
   __shared__ double red[8][kSysN];
   const int64_t M = min(*m_dev, capacity);
   float R[9], t[3];
@@ -415,11 +446,25 @@ __global__ void __launch_bounds__(256) mahalanobis_kernel(MapK A, MapK Bm, const
     for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
     if (v != 0.0) atomicAdd(&sys[threadIdx.x], v);
   }
+  if (!SOLVE) return;
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  unsigned long long* count = reinterpret_cast<unsigned long long*>(sys + kSysN);
+  if (threadIdx.x == 0) s_last = atomicAdd(count, 1ull) == (unsigned long long)gridDim.x - 1ull;
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  double S[kSysN];
+  for (int k = 0; k < kSysN; ++k) S[k] = __ldcg(sys + k);
+  maha_solve_apply(S, T, delta_out, status);
+  for (int k = 0; k < kSysN; ++k) sys[k] = 0.0;
+  *count = 0ull;
 }
 
-__global__ void mahalanobis_step_kernel(const double* __restrict__ sys, float* __restrict__ T,
-                                        double* __restrict__ delta_out, int32_t* __restrict__ status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Solve H delta = -g (Cholesky, double) and apply T <- exp(delta^) T (one thread).
+__device__ void maha_solve_apply(const double* __restrict__ sys, float* __restrict__ T,
+                                 double* __restrict__ delta_out, int32_t* __restrict__ status) {
   double H[6][6], L[6][6] = {}, g[6], d[6];
   int o = 0;
   for (int a = 0; a < 6; ++a)
@@ -493,6 +538,12 @@ __global__ void mahalanobis_step_kernel(const double* __restrict__ sys, float* _
       out[4 * i + j] = v;
     }
   for (int k = 0; k < 16; ++k) T[k] = (float)out[k];
+}
+
+__global__ void mahalanobis_step_kernel(const double* __restrict__ sys, float* __restrict__ T,
+                                        double* __restrict__ delta_out, int32_t* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  maha_solve_apply(sys, T, delta_out, status);
 }
 
 // ----------------------------------------------------------------------------
@@ -616,17 +667,16 @@ extern "C" int splat_loss_consensus(const float* rgb, const float* depth, const 
   if (!ws || !aligned16(ws) || ws_bytes < splat_loss_consensus_workspace_size(height, width))
     return fail(SPLAT_EINVAL, "splat_loss_consensus: workspace missing, too small or misaligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int rc = launch_loss_l1(rgb, depth, target_rgb, target_depth, npix, w_l1 / (float)(3 * npix),
-                          w_geom / (float)npix, d_rgb, d_depth, loss, s);
-  if (rc) return rc;
-  if (w_ssim == 0.f) return SPLAT_OK;
+  const float sc = w_l1 / (float)(3 * npix), sd = w_geom / (float)npix;
+  if (w_ssim == 0.f) return launch_loss_l1(rgb, depth, target_rgb, target_depth, npix, sc, sd, d_rgb, d_depth, loss, s);
+  int rc;
   const SsimWin win = ssim_window();
   const dim3 grid((unsigned)((width + kSsTX - 1) / kSsTX), (unsigned)((height + kSsTY - 1) / kSsTY));
   float* abc = static_cast<float*>(ws);
   const float inv = 1.0f / (float)(3 * npix);
   SPLAT_LAUNCH("ssim_fwd_kernel", s,
-               ssim_fwd_kernel<<<grid, 256, 0, s>>>(rgb, target_rgb, height, width, win, w_ssim * inv, inv, abc,
-                                                    loss));
+               ssim_fwd_kernel<<<grid, 256, 0, s>>>(rgb, target_rgb, depth, target_depth, height, width, win,
+                                                    w_ssim * inv, inv, sc, sd, d_rgb, d_depth, abc, loss));
   if ((rc = check_launch("ssim_fwd_kernel"))) return rc;
   SPLAT_LAUNCH("ssim_bwd_kernel", s,
                ssim_bwd_kernel<<<grid, 256, 0, s>>>(rgb, target_rgb, height, width, win, -w_ssim * inv, abc, d_rgb));
@@ -647,8 +697,30 @@ extern "C" int splat_mahalanobis_system(const splat_gaussians* map_a, const spla
   const MapK A{map_a->mean, map_a->log_scale, map_a->quat}, Bm{map_b->mean, map_b->log_scale, map_b->quat};
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((capacity + 255) / 256, 2 * 152));
   SPLAT_LAUNCH("mahalanobis_kernel", s,
-               mahalanobis_kernel<<<grid, 256, 0, s>>>(A, Bm, pairs, weights, m_dev, capacity, T,
-                                                       max_dist > 0.f ? max_dist * max_dist : 0.f, sys));
+               mahalanobis_kernel<false><<<grid, 256, 0, s>>>(A, Bm, pairs, weights, m_dev, capacity,
+                                                              const_cast<float*>(T),
+                                                              max_dist > 0.f ? max_dist * max_dist : 0.f, sys,
+                                                              nullptr, nullptr));
+  return check_launch("mahalanobis_kernel");
+}
+
+extern "C" int splat_mahalanobis_system_step(const splat_gaussians* map_a, const splat_gaussians* map_b,
+                                             const int32_t* pairs, const int32_t* weights, const int64_t* m_dev,
+                                             int64_t capacity, float* T, float max_dist, double* sys,
+                                             double* delta_out, int32_t* status, splat_stream_t stream) {
+  if (!map_a || !map_b || !m_dev || !T || !sys || !status || capacity < 0 || (capacity > 0 && !pairs))
+    return fail(SPLAT_EINVAL, "splat_mahalanobis_system_step: bad argument");
+  if ((map_a->n > 0 && (!map_a->mean || !map_a->log_scale || !map_a->quat)) ||
+      (map_b->n > 0 && (!map_b->mean || !map_b->log_scale || !map_b->quat)))
+    return fail(SPLAT_EINVAL, "splat_mahalanobis_system_step: null map array");
+  if ((reinterpret_cast<uintptr_t>(sys) & 7u) != 0) return fail(SPLAT_EINVAL, "splat_mahalanobis_system_step: sys");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const MapK A{map_a->mean, map_a->log_scale, map_a->quat}, Bm{map_b->mean, map_b->log_scale, map_b->quat};
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((capacity + 255) / 256, 2 * 152));
+  SPLAT_LAUNCH("mahalanobis_kernel", s,
+               mahalanobis_kernel<true><<<grid, 256, 0, s>>>(A, Bm, pairs, weights, m_dev, capacity, T,
+                                                             max_dist > 0.f ? max_dist * max_dist : 0.f, sys,
+                                                             delta_out, status));
   return check_launch("mahalanobis_kernel");
 }
 

@@ -37,6 +37,34 @@ struct GradK {
   float* rgb;
 };
 
+// Adam (bias-corrected; one update of one element).  1 - beta^t in float from
+// a device-resident step count; the bias corrections enter as reciprocals and
+// the step's division is the fast one: the update differs from the textbook
+// expression by a few ulp of the step, not of the parameter.  An element whose
+// gradient and moments are all +0 is left exactly as it is (m, v stay +0,
+// p - 0 = p), so skipping it changes nothing.
+__device__ __forceinline__ float bias_correction(float beta, const int32_t* step) {
+  return 1.0f - powf(beta, (float)(*step));
+}
+
+__device__ __forceinline__ void adam_update(float& p, float g, float& m, float& v, float lr, float b1, float b2,
+                                            float ibc1, float ibc2, float eps) {
+  m = b1 * m + (1.0f - b1) * g;
+  v = b2 * v + (1.0f - b2) * g * g;
+  p = p - __fdividef(lr * (m * ibc1), sqrtf(v * ibc2) + eps);
+}
+
+// The map's Adam state for the fused projection adjoint + update.
+struct AdamMapK {
+  float* p[5];  // parameters (mean, log_scale, quat, opacity_logit, rgb), updated in place
+  float* m[5];
+  float* v[5];
+  float lr[5];
+  int vec[5];   // p, m, v of the group 16-byte aligned
+  float b1, b2, eps;
+  const int32_t* step;
+};
+
 inline CamK make_camk(const splat_camera& c) {
   CamK k;
   k.width = c.width;
@@ -56,6 +84,13 @@ int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, c
 int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
                        const int32_t* radius, const float* g2, int stride, const GradK& out, float* d_pose,
                        float* d2d_out, cudaStream_t s);
+
+// Projection adjoint with the map's Adam step in the same pass: every
+// Gaussian's parameters move by Adam with the gradient the adjoint gives it
+// (0 for a culled one); nothing is written to gradient arrays.
+int launch_project_bwd_adam(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
+                            const int32_t* radius, const float* g2, int stride, const AdamMapK& adam, float* d_pose,
+                            cudaStream_t s);
 
 // L1 terms: grgb = sc sign(rgb - trgb), gdepth = sd sign(depth - tdepth) (overwritten),
 // loss += sc sum|rgb - trgb| + sd sum|depth - tdepth|.

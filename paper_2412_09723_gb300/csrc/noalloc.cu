@@ -75,5 +75,6 @@ extern "C" int splat_bin_sort_static(const splat_projected* proj, int64_t n, con
   void* ws = nullptr;
   const int rc = static_scratch(reinterpret_cast<cudaStream_t>(stream), &ws);
   if (rc) return rc;
-  return splat_bin_sort(proj, n, cam, keys, vals, capacity, k_dev, ranges, status, ws, kStaticScratchBytes, stream);
+  return splat_bin_sort(proj, n, cam, keys, vals, capacity, k_dev, ranges, nullptr, status, ws, kStaticScratchBytes,
+                        stream);
 }

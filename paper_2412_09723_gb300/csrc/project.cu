@@ -182,20 +182,31 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(GaussiansK g, CamK cam
 // ----------------------------------------------------------------------------
 // Adjoint.
 // ----------------------------------------------------------------------------
-// Adjoint of one Gaussian's projection (its screen-space gradients in g2),
-// accumulated into `out` and, for the pose, into `pose`.
+// The 14 parameter gradients of one Gaussian.
+struct Grad14 {
+  float mean[3], ls[3], q[4], logit, rgb[3];
+};
+
+// Adjoint of one Gaussian's projection (its screen-space gradients in g2):
+// its parameter gradients in `o` (all 0 when the forward projection culled
+// it) and its share of the pose gradient added to `pose`.
 __device__ __forceinline__ void project_adjoint_one(const GaussiansK& g, const CamK& cam, const float* W,
                                                     const float* __restrict__ conic, const float* __restrict__ g2,
-                                                    int stride, const GradK& out, int64_t i, float (&pose)[6]) {
+                                                    int stride, int64_t i, Grad14& o, float (&pose)[6]) {
   ProjMath m;
   project_math(g.mean + 3 * i, g.log_scale + 3 * i, g.quat + 4 * i, g.opacity_logit[i], W, cam, m);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) o.mean[k] = o.ls[k] = o.rgb[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.q[k] = 0.f;
+  o.logit = 0.f;
   if (m.visible) {
     const float* d = g2 + (size_t)stride * i;
     const float du = d[0], dv = d[1], dqa = d[2], dqb = d[3], dqc = d[4], dlam = d[5], dz = d[9];
-    out.rgb[3 * i + 0] += d[6];
-    out.rgb[3 * i + 1] += d[7];
-    out.rgb[3 * i + 2] += d[8];
-    out.opacity_logit[i] += dlam * m.lam * (1.0f - m.lam);
+    o.rgb[0] = d[6];
+    o.rgb[1] = d[7];
+    o.rgb[2] = d[8];
+    o.logit = dlam * m.lam * (1.0f - m.lam);
     // conic Q = cov^-1 with cov = [[ca, cb], [cb, cc]]; the off-diagonal conic
     // entry is one scalar used twice, so the full-matrix gradient of Q is
     // [[dqa, dqb/2], [dqb/2, dqc]] and d cov = -Q dQ Q.
@@ -257,7 +268,7 @@ __device__ __forceinline__ void project_adjoint_one(const GaussiansK& g, const C
     gz += dz;
     const float gp[3] = {gp0, gp1, gz};
 #pragma unroll
-    for (int j = 0; j < 3; ++j) out.mean[3 * i + j] += W[j] * gp[0] + W[4 + j] * gp[1] + W[8 + j] * gp[2];
+    for (int j = 0; j < 3; ++j) o.mean[j] = W[j] * gp[0] + W[4 + j] * gp[1] + W[8 + j] * gp[2];
     // Sig = M M^T, M = R diag(s)
     float dM[9];
 #pragma unroll
@@ -269,7 +280,7 @@ __device__ __forceinline__ void project_adjoint_one(const GaussiansK& g, const C
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const float gs = dM[j] * m.R[j] + dM[3 + j] * m.R[3 + j] + dM[6 + j] * m.R[6 + j];
-      out.log_scale[3 * i + j] += gs * m.s[j];
+      o.ls[j] = gs * m.s[j];
       dR[j] = dM[j] * m.s[j];
       dR[3 + j] = dM[3 + j] * m.s[j];
       dR[6 + j] = dM[6 + j] * m.s[j];
@@ -284,7 +295,7 @@ __device__ __forceinline__ void project_adjoint_one(const GaussiansK& g, const C
       const float dot = r * gq[0] + a * gq[1] + b * gq[2] + c * gq[3];
       const float inv = 1.0f / m.qnorm;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) out.quat[4 * i + k] += (gq[k] - m.qn[k] * dot) * inv;
+      for (int k = 0; k < 4; ++k) o.q[k] = (gq[k] - m.qn[k] * dot) * inv;
     }
     // pose: rho = dL/dp ; phi = p x dL/dp + vee(dW W^T)
     float A[9];
@@ -302,12 +313,57 @@ __device__ __forceinline__ void project_adjoint_one(const GaussiansK& g, const C
   }
 }
 
+// Accumulate one Gaussian's gradients into the gradient arrays.
+__device__ __forceinline__ void add_grads(const GradK& out, int64_t i, const Grad14& o) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    out.mean[3 * i + k] += o.mean[k];
+    out.log_scale[3 * i + k] += o.ls[k];
+    out.rgb[3 * i + k] += o.rgb[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) out.quat[4 * i + k] += o.q[k];
+  out.opacity_logit[i] += o.logit;
+}
+
 // Gaussians the forward projection culled (radius 0) have no gradient.  Each
 // warp scans its share of the map 32 at a time and queues the visible ones in
 // shared memory; the adjoint runs whenever 32 are queued (and once more for
 // the rest), so that no warp runs it for one or two visible lanes only.
 constexpr int kPbThreads = 256;
 constexpr int kPbWarps = kPbThreads / 32;
+
+__device__ __forceinline__ void adjoint_into(const GaussiansK& g, const CamK& cam, const float* W,
+                                             const float* conic, const float* g2, int stride, const GradK& out,
+                                             int64_t i, float (&pose)[6]) {
+  Grad14 o;
+  project_adjoint_one(g, cam, W, conic, g2, stride, i, o, pose);
+  add_grads(out, i, o);
+}
+
+// Block reduction of the pose gradient (warp shuffles, then one warp) and
+// one atomic per component.  Every thread of the block takes part.
+__device__ __forceinline__ void add_pose(const float (&pose)[6], float* d_pose) {
+  __shared__ float red[6][kPbWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    float x = pose[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[k][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float x = lane < kPbWarps ? red[k][lane] : 0.0f;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0 && x != 0.0f) atomicAdd(d_pose + k, x);
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kPbThreads) project_bwd_kernel(GaussiansK g, CamK cam, const float* __restrict__ w2c,
                                                                  const float* __restrict__ conic,
@@ -337,35 +393,198 @@ __global__ void __launch_bounds__(kPbThreads) project_bwd_kernel(GaussiansK g, C
     qn += __popc(m);
     __syncwarp();
     if (qn >= 32) {
-      project_adjoint_one(g, cam, W, conic, g2, stride, out, queue[warp][lane], pose);
+      adjoint_into(g, cam, W, conic, g2, stride, out, queue[warp][lane], pose);
       __syncwarp();
       if (lane < qn - 32) queue[warp][lane] = queue[warp][32 + lane];
       __syncwarp();
       qn -= 32;
     }
   }
-  if (lane < qn) project_adjoint_one(g, cam, W, conic, g2, stride, out, queue[warp][lane], pose);
-  if (d_pose == nullptr) return;
-  // block reduction of the pose gradient: warp shuffles, then one warp
-  __shared__ float red[6][8];
+  if (lane < qn) adjoint_into(g, cam, W, conic, g2, stride, out, queue[warp][lane], pose);
+  if (d_pose) add_pose(pose, d_pose);
+}
+
+// The fused projection adjoint + Adam step.  Blocks [0, n_kept_blocks) take
+// the kept Gaussians: per warp, 32 consecutive Gaussians per pass; the kept
+// ones (radius > 0) are queued and, 32 at a time, run the adjoint and then
+// the Adam step of their 14 elements from the gradients in registers.  The
+// other blocks take the culled Gaussians' zero-gradient step in element
+// space (units of 4 consecutive elements of one parameter group; a unit whose
+// moments are all +0 is left alone after reading them).  The two parts touch
+// disjoint elements and run side by side in one launch.
+
+template <int W>
+struct GroupState {
+  float p[W], m[W], v[W];
+};
+
+template <int W>
+__device__ __forceinline__ void group_load(const AdamMapK& A, int grp, int64_t i, GroupState<W>& s) {
 #pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    float x = pose[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) red[k][warp] = x;
+  for (int k = 0; k < W; ++k) {
+    const size_t at = (size_t)W * i + k;
+    s.p[k] = A.p[grp][at];
+    s.m[k] = A.m[grp][at];
+    s.v[k] = A.v[grp][at];
   }
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
+}
+
+template <int W>
+__device__ __forceinline__ void group_step_store(const AdamMapK& A, int grp, int64_t i, GroupState<W>& s,
+                                                 const float* g, float ibc1, float ibc2) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      float x = lane < nw ? red[k][lane] : 0.0f;
+  for (int k = 0; k < W; ++k) adam_update(s.p[k], g[k], s.m[k], s.v[k], A.lr[grp], A.b1, A.b2, ibc1, ibc2, A.eps);
 #pragma unroll
-      for (int o = 4; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0 && x != 0.0f) atomicAdd(d_pose + k, x);
+  for (int k = 0; k < W; ++k) {
+    const size_t at = (size_t)W * i + k;
+    A.p[grp][at] = s.p[k];
+    A.m[grp][at] = s.m[k];
+    A.v[grp][at] = s.v[k];
+  }
+}
+
+// The Adam step of one kept Gaussian's 14 elements, group after group, each
+// group's loads issued before the previous group's stores (the groups are
+// distinct arrays, so the order is only a matter of latency).
+__device__ __forceinline__ void adam_gaussian(const AdamMapK& A, int64_t i, const Grad14& o, float ibc1, float ibc2) {
+  GroupState<3> s0, s1, s4;
+  GroupState<4> s2;
+  GroupState<1> s3;
+  group_load<3>(A, 0, i, s0);
+  group_load<3>(A, 1, i, s1);
+  group_step_store<3>(A, 0, i, s0, o.mean, ibc1, ibc2);
+  group_load<4>(A, 2, i, s2);
+  group_step_store<3>(A, 1, i, s1, o.ls, ibc1, ibc2);
+  group_load<1>(A, 3, i, s3);
+  group_load<3>(A, 4, i, s4);
+  group_step_store<4>(A, 2, i, s2, o.q, ibc1, ibc2);
+  group_step_store<1>(A, 3, i, s3, &o.logit, ibc1, ibc2);
+  group_step_store<3>(A, 4, i, s4, o.rgb, ibc1, ibc2);
+}
+
+// Zero-gradient Adam step of the culled Gaussians' elements of group GRP
+// (W elements per Gaussian), in units of 4 consecutive elements, grid-strided
+// over the culled part's threads (a few units per thread, all moment loads
+// first).
+constexpr int kCulledUnroll = 4;
+
+template <int W>
+__device__ __forceinline__ void culled_group(const AdamMapK& A, int grp, const int32_t* __restrict__ radius, int64_t n,
+                                             int64_t u_first, int64_t u_stride, float ibc1, float ibc2) {
+  const int64_t size = (int64_t)W * n;
+  const int64_t units = (size + 3) / 4;
+  const bool vec = A.vec[grp] != 0;
+  for (int64_t u0 = u_first; u0 < units; u0 += kCulledUnroll * u_stride) {
+    float m4[kCulledUnroll][4], v4[kCulledUnroll][4];
+#pragma unroll
+    for (int r = 0; r < kCulledUnroll; ++r) {  // all moment loads first
+      const int64_t e0 = 4 * (u0 + r * u_stride);
+      if (vec && e0 + 4 <= size) {
+        const float4 a = *reinterpret_cast<const float4*>(A.m[grp] + e0);
+        const float4 b = *reinterpret_cast<const float4*>(A.v[grp] + e0);
+        m4[r][0] = a.x; m4[r][1] = a.y; m4[r][2] = a.z; m4[r][3] = a.w;
+        v4[r][0] = b.x; v4[r][1] = b.y; v4[r][2] = b.z; v4[r][3] = b.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool in = e0 + j < size;
+          m4[r][j] = in ? A.m[grp][e0 + j] : 0.f;
+          v4[r][j] = in ? A.v[grp][e0 + j] : 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kCulledUnroll; ++r) {
+      uint32_t any = 0u;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) any |= __float_as_uint(m4[r][j]) | __float_as_uint(v4[r][j]);
+      if (any == 0u) continue;  // never seen since its moments were zero: nothing changes
+      const int64_t e0 = 4 * (u0 + r * u_stride);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t e = e0 + j;
+        if (e >= size || radius[e / W] != 0) continue;  // a kept Gaussian's element: the other part's
+        float pj = A.p[grp][e], mj = m4[r][j], vj = v4[r][j];
+        adam_update(pj, 0.0f, mj, vj, A.lr[grp], A.b1, A.b2, ibc1, ibc2, A.eps);
+        A.p[grp][e] = pj;
+        A.m[grp][e] = mj;
+        A.v[grp][e] = vj;
+      }
     }
   }
+}
+
+__device__ __forceinline__ void culled_units(const AdamMapK& A, const int32_t* __restrict__ radius, int64_t n,
+                                             int64_t u_first, int64_t u_stride, float ibc1, float ibc2) {
+  culled_group<3>(A, 0, radius, n, u_first, u_stride, ibc1, ibc2);
+  culled_group<3>(A, 1, radius, n, u_first, u_stride, ibc1, ibc2);
+  culled_group<4>(A, 2, radius, n, u_first, u_stride, ibc1, ibc2);
+  culled_group<1>(A, 3, radius, n, u_first, u_stride, ibc1, ibc2);
+  culled_group<3>(A, 4, radius, n, u_first, u_stride, ibc1, ibc2);
+}
+
+__global__ void __launch_bounds__(kPbThreads, 2) project_bwd_adam_kernel(GaussiansK g, CamK cam,
+                                                                         const float* __restrict__ w2c,
+                                                                         const float* __restrict__ conic,
+                                                                         const int32_t* __restrict__ radius,
+                                                                         const float* __restrict__ g2, int stride,
+                                                                         AdamMapK A, float* __restrict__ d_pose,
+                                                                         int kept_blocks) {
+  const float ibc1 = 1.0f / bias_correction(A.b1, A.step);
+  const float ibc2 = 1.0f / bias_correction(A.b2, A.step);
+  if ((int)blockIdx.x >= kept_blocks) {  // the culled Gaussians
+    const int64_t nb = (int64_t)gridDim.x - kept_blocks;
+    culled_units(A, radius, g.n, ((int64_t)blockIdx.x - kept_blocks) * kPbThreads + threadIdx.x, nb * kPbThreads,
+                 ibc1, ibc2);
+    return;
+  }
+  __shared__ int32_t queue[kPbWarps][160];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lower = (1u << lane) - 1u;
+  float W[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) W[k] = __ldg(w2c + k);
+  float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int qn = 0;  // warp-uniform
+  // each warp scans runs of 128 consecutive radii (four per lane, one 16-byte
+  // load when aligned), queueing the kept Gaussians
+  const bool vec = (reinterpret_cast<uintptr_t>(radius) & 15u) == 0;
+  const int64_t stride_all = (int64_t)kept_blocks * kPbThreads * 4;
+  for (int64_t base = ((int64_t)blockIdx.x * kPbWarps + warp) * 128; base < g.n; base += stride_all) {
+    int r4[4];
+    const int64_t i0 = base + 4 * lane;
+    if (vec && i0 + 4 <= g.n) {
+      const int4 r = *reinterpret_cast<const int4*>(radius + i0);
+      r4[0] = r.x; r4[1] = r.y; r4[2] = r.z; r4[3] = r.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r4[k] = i0 + k < g.n ? radius[i0 + k] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const bool vis = r4[k] != 0;
+      const unsigned m = __ballot_sync(full, vis);
+      if (vis) queue[warp][qn + __popc(m & lower)] = (int32_t)(i0 + k);
+      qn += __popc(m);
+    }
+    __syncwarp();
+    while (qn >= 32) {
+      const int64_t j = queue[warp][qn - 32 + lane];
+      Grad14 o;
+      project_adjoint_one(g, cam, W, conic, g2, stride, j, o, pose);
+      adam_gaussian(A, j, o, ibc1, ibc2);
+      qn -= 32;
+    }
+    __syncwarp();
+  }
+  if (lane < qn) {
+    const int64_t j = queue[warp][lane];
+    Grad14 o;
+    project_adjoint_one(g, cam, W, conic, g2, stride, j, o, pose);
+    adam_gaussian(A, j, o, ibc1, ibc2);
+  }
+  if (d_pose) add_pose(pose, d_pose);
 }
 
 int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, const ProjectedK& out,
@@ -373,6 +592,21 @@ int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, c
   if (g.n == 0) return SPLAT_OK;
   SPLAT_LAUNCH("project_fwd_kernel", s, project_fwd_kernel<<<ceil_div(g.n, 256), 256, 0, s>>>(g, cam, w2c, out));
   return check_launch("project_fwd_kernel");
+}
+
+int launch_project_bwd_adam(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
+                            const int32_t* radius, const float* g2, int stride, const AdamMapK& adam, float* d_pose,
+                            cudaStream_t s) {
+  if (g.n == 0) return SPLAT_OK;
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // both parts resident at once (two CTAs per SM): one for the kept Gaussians' adjoint, one for the culled
+  const int kept_blocks = (int)std::min<int64_t>(ceil_div(g.n, kPbThreads), sms);
+  const int grid = kept_blocks + sms;
+  SPLAT_LAUNCH("project_bwd_adam_kernel", s,
+               project_bwd_adam_kernel<<<grid, kPbThreads, 0, s>>>(g, cam, w2c, conic, radius, g2, stride, adam,
+                                                                   d_pose, kept_blocks));
+  return check_launch("project_bwd_adam_kernel");
 }
 
 int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,

@@ -26,9 +26,12 @@
 // Per Gaussian and warp, ten sums (five moments of dL/dpower -- sum dp dx,
 // dp dy, dp dx^2, dp dx dy, dp dy^2 -- whose conic terms are applied once per
 // Gaussian, plus d opacity, d rgb, d depth) are reduced through a per-warp
-// shared-memory transpose (each lane writes its column, two lanes add one row
-// with 16-byte loads and packed adds), collected per CTA in shared memory and
-// added to global memory with three float4 atomics per Gaussian per CTA.
+// shared-memory transpose: each lane writes its column for up to three
+// visits, then lane r adds row r of the 30 with 16-byte loads and packed adds;
+// the sums are collected per CTA in shared memory and added to global memory
+// with three float4 atomics per Gaussian per CTA.  A warp skips a visit, or
+// stops short in one, only when none of its lanes takes part (warp-uniform
+// tests: a lane that does not take part computes with zero weights).
 //
 // Persistent launches: a grid of (CTAs per SM) x (SMs) CTAs takes (view, tile)
 // work items from one atomic ticket counter until the items run out; no CTA
@@ -46,6 +49,8 @@ constexpr int kGradStride = 12;           // screen-space gradient row (3 float4
 constexpr int kAccStride = 11;            // shared accumulator row (10 sums, padded)
 constexpr int kRedRow = 36;               // transposed-reduction row: 32 lanes + 4 (rows start in different banks)
 constexpr int kMaxViews = SPLAT_MAX_VIEWS;
+constexpr int kBwdBatch = 64;            // backward: Gaussians staged per batch (single-view calls)
+constexpr int kBwdCtasPerSm = 8;          // backward: resident CTAs per SM (single-view calls)
 
 struct ImageK {
   float* rgb;
@@ -55,6 +60,16 @@ struct ImageK {
   int32_t* n_contrib;
   int32_t* max_id;
   int32_t* n_used;
+};
+
+// L1 terms of the loss taken in the forward's epilogue (t_rgb == nullptr: none).
+struct LossK {
+  const float* t_rgb;
+  const float* t_depth;
+  float sc, sd;  // w_rgb / 3P, w_depth / P
+  float* g_rgb;
+  float* g_depth;
+  float* loss;
 };
 
 struct ViewK {
@@ -70,6 +85,8 @@ struct ViewK {
   const float* d_depth;
   const float* d_sil;
   float* g2;
+  LossK l1;
+  const uint32_t* order;  // tiles in the order the backward takes them, or null (natural order)
 };
 
 struct ViewTable {
@@ -289,8 +306,15 @@ __device__ __forceinline__ void pair_pixel(int t, int p, int& lx, int& ly) {
   ly = 4 * warp + (lane >> 4) + 2 * p;
 }
 
+// |x - t| and the subgradient sc sign(x - t) (sign(0) = 0), as splat_loss_l1.
+__device__ __forceinline__ float l1_px(float x, float t, float sc, float* g) {
+  const float e = x - t;
+  *g = e > 0.f ? sc : (e < 0.f ? -sc : 0.f);
+  return fabsf(e);
+}
+
 template <int BATCH>
-__device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>& sm) {
+__device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>& sm, float* s_loss) {
   const CamK& cam = V.cam;
   const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
   int lx, ly0, ly1;
@@ -323,27 +347,53 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
       composite_step2(q, sm.xyzo[j], sm.quad[j], fx, nfy, &sm.cid[j], base + j);
     }
   }
+  const LossK& L = V.l1;
+  float acc_c = 0.f, acc_d = 0.f;
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
     if (!(p ? in1 : in0)) continue;
     const size_t i = (size_t)(p ? py1 : py0) * cam.width + px;
     const float T = p ? q.T.y : q.T.x;
-    V.img.rgb[3 * i + 0] = __fmaf_rn(T, V.bg0, p ? q.C0.y : q.C0.x);
-    V.img.rgb[3 * i + 1] = __fmaf_rn(T, V.bg1, p ? q.C1.y : q.C1.x);
-    V.img.rgb[3 * i + 2] = __fmaf_rn(T, V.bg2, p ? q.C2.y : q.C2.x);
-    V.img.depth[i] = p ? q.D.y : q.D.x;
+    const float c0 = __fmaf_rn(T, V.bg0, p ? q.C0.y : q.C0.x);
+    const float c1 = __fmaf_rn(T, V.bg1, p ? q.C1.y : q.C1.x);
+    const float c2 = __fmaf_rn(T, V.bg2, p ? q.C2.y : q.C2.x);
+    const float d = p ? q.D.y : q.D.x;
+    V.img.rgb[3 * i + 0] = c0;
+    V.img.rgb[3 * i + 1] = c1;
+    V.img.rgb[3 * i + 2] = c2;
+    V.img.depth[i] = d;
     V.img.sil[i] = p ? q.S.y : q.S.x;
     V.img.t_final[i] = T;
     V.img.n_contrib[i] = q.last[p];
     V.img.max_id[i] = q.id[p];
     if (V.img.n_used) V.img.n_used[i] = q.used[p];
+    if (L.t_rgb) {
+      acc_c += l1_px(c0, L.t_rgb[3 * i + 0], L.sc, &L.g_rgb[3 * i + 0]) +
+               l1_px(c1, L.t_rgb[3 * i + 1], L.sc, &L.g_rgb[3 * i + 1]) +
+               l1_px(c2, L.t_rgb[3 * i + 2], L.sc, &L.g_rgb[3 * i + 2]);
+      acc_d += l1_px(d, L.t_depth[i], L.sd, &L.g_depth[i]);
+    }
+  }
+  if (L.t_rgb) {  // the tile's share of the loss: warp sums, then one atomic per CTA
+    float acc = L.sc * acc_c + L.sd * acc_d;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < kFwdThreads / 32; ++w) t += s_loss[w];
+      if (L.loss) atomicAdd(L.loss, t);
+    }
   }
 }
 
 template <int BATCH>
 __global__ void __launch_bounds__(kFwdThreads, 8) render_fwd_kernel(ViewK V) {
   __shared__ Stage<BATCH> sm;
-  fwd_tile<BATCH>(V, blockIdx.x, sm);
+  __shared__ float s_loss[kFwdThreads / 32];
+  fwd_tile<BATCH>(V, blockIdx.x, sm, s_loss);
 }
 
 // Work item -> (view, tile).
@@ -364,33 +414,51 @@ __device__ __forceinline__ int next_item(int* counter, int* s_item) {
 template <int BATCH>
 __global__ void __launch_bounds__(kFwdThreads, 8) render_fwd_persistent(ViewTable T, int total, int* counter) {
   __shared__ Stage<BATCH> sm;
+  __shared__ float s_loss[kFwdThreads / 32];
   __shared__ int s_item;
   for (int item = next_item(counter, &s_item); item < total; item = next_item(counter, &s_item)) {
     int tile;
     const int v = view_of(T, item, tile);
-    fwd_tile<BATCH>(T.v[v], tile, sm);
+    fwd_tile<BATCH>(T.v[v], tile, sm, s_loss);
   }
 }
 
 // ----------------------------------------------------------------------------
 // Backward
 // ----------------------------------------------------------------------------
-// The thread's two pixels (x, y) and (x, y + 2): they share x, and their
-// arithmetic runs in packed single-precision pairs.  Q = sum_{j>i} w_j P_j +
-// (gC.bg) T_final.
+// Each tile's list is split at a position m into a front part [0, m) and a
+// back part [m, last), two independent work items.  With the pixel's upstream
+// gradients folded into P_i = gC.c_i + gD z_i + gS and w_i = alpha_i T_i,
+//   dL/dalpha_i = T_i P_i - Q_i / (1 - alpha_i),
+//   Q_i = sum_{j>i} w_j P_j + (gC.bg) T_final.
+// The back part walks back to front from T_final: T_i = T_{i+1} / (1 - alpha_i)
+// and Q accumulates from (gC.bg) T_final.  The front part walks front to back
+// with the forward's own recurrence T_{i+1} = T_i (1 - alpha_i) from T_0 = 1,
+// and Q_i = R_i - w_i P_i with R_0 = sum_j w_j P_j + (gC.bg) T_final
+// = gC.C + gD D + gS S, the forward's outputs (C with its background term):
+// no part waits for the other, so a tile's work is two items of a persistent
+// launch.  m is the tile's mean contributor count over two, so the parts are
+// about even; the front part takes the early contributors (T_i large, where
+// the subtraction R - w P loses nothing that matters) and the back part the
+// late ones.
+//
+// The thread's two pixels (x, y) and (x, y + 2) share x, and their arithmetic
+// runs in packed single-precision pairs.  Q holds Q (back part) or R (front).
 struct BwdPair {
   float fx;
   float2 nfy, T, gC0, gC1, gC2, gD, gS, Q;
   int last[2];
 };
 
-// Per-pixel adjoint of one list position (back to front) for both pixels of
-// the pair; pixel p takes part when pos < last[p] and the Gaussian passes its
-// exponent, alpha-floor tests (the forward's decisions, same operations).
-// Adds the pair's share of (sum dp dx, sum dp dy, sum dp dx^2, sum dp dx dy,
+// Per-pixel adjoint of one list position for both pixels of the pair; pixel
+// p takes part when pos < last[p] and the Gaussian passes its exponent and
+// alpha-floor tests (the forward's decisions, same operations).  Adds the
+// pair's share of (sum dp dx, sum dp dy, sum dp dx^2, sum dp dx dy,
 // sum dp dy^2, d opacity, d rgb[3], d depth) to v, dp = dL/d(power); returns
-// whether either pixel took part.  A pixel that does not take part keeps T and
-// Q (its weight is 0) and adds nothing (its G and raw opacity are set to 0).
+// whether either pixel took part.  A pixel that does not take part keeps T
+// and Q (its alpha and weight are 0) and adds nothing (its G and raw opacity
+// are set to 0).
+template <bool FRONT>
 __device__ __forceinline__ bool adjoint_step2(BwdPair& q, int pos, const float4 xo, const float4 qd, float c0,
                                               float c1, float c2, float (&v)[10]) {
   const float dx = xo.x - q.fx;
@@ -399,21 +467,26 @@ __device__ __forceinline__ bool adjoint_step2(BwdPair& q, int pos, const float4 
   const float2 power = __ffma2_rn(__fmul2_rn(bcast(qd.z), dy), dy, __fmul2_rn(bcast(dx), inner));
   bool in0 = pos < q.last[0] && !(power.x > 0.0f || power.x < qd.w);
   bool in1 = pos < q.last[1] && !(power.y > 0.0f || power.y < qd.w);
-  if (!(in0 || in1)) return false;
+  if (!__any_sync(0xffffffffu, in0 || in1)) return false;
   const float2 G = exp_core2(power);
   const float2 raw = __fmul2_rn(bcast(xo.w), G);
   float2 alpha = make_float2(fminf(kAlphaCap, raw.x), fminf(kAlphaCap, raw.y));
   in0 = in0 && !(alpha.x < kAlphaMin);
   in1 = in1 && !(alpha.y < kAlphaMin);
-  if (!(in0 || in1)) return false;
+  if (!__any_sync(0xffffffffu, in0 || in1)) return false;
   alpha.x = in0 ? alpha.x : 0.0f;
   alpha.y = in1 ? alpha.y : 0.0f;
   const float2 om = __ffma2_rn(alpha, bcast(-1.0f), bcast(1.0f));
   const float2 r = make_float2(__fdividef(1.0f, om.x), __fdividef(1.0f, om.y));
-  const float2 Tn = __fmul2_rn(q.T, r);  // T_i
-  q.T.x = in0 ? Tn.x : q.T.x;
-  q.T.y = in1 ? Tn.y : q.T.y;
-  const float2 w = __fmul2_rn(alpha, Tn);  // 0 for a pixel that does not take part
+  float2 Ti;
+  if (FRONT) {
+    Ti = q.T;
+  } else {
+    Ti = __fmul2_rn(q.T, r);  // T_i
+    q.T.x = in0 ? Ti.x : q.T.x;
+    q.T.y = in1 ? Ti.y : q.T.y;
+  }
+  const float2 w = __fmul2_rn(alpha, Ti);  // 0 for a pixel that does not take part
   const float2 t6 = __fmul2_rn(q.gC0, w), t7 = __fmul2_rn(q.gC1, w), t8 = __fmul2_rn(q.gC2, w);
   const float2 t9 = __fmul2_rn(q.gD, w);
   v[6] += t6.x + t6.y;
@@ -424,9 +497,18 @@ __device__ __forceinline__ bool adjoint_step2(BwdPair& q, int pos, const float4 
   P = __ffma2_rn(q.gC1, bcast(c1), P);
   P = __ffma2_rn(q.gC2, bcast(c2), P);
   P = __ffma2_rn(q.gD, bcast(xo.z), P);
-  const float2 rq = __fmul2_rn(r, q.Q);
-  const float2 dA = __ffma2_rn(Tn, P, make_float2(-rq.x, -rq.y));
-  q.Q = __ffma2_rn(w, P, q.Q);
+  float2 dA;
+  if (FRONT) {
+    const float2 Qi = __ffma2_rn(make_float2(-w.x, -w.y), P, q.Q);  // R_i - w_i P_i
+    const float2 rq = __fmul2_rn(r, Qi);
+    dA = __ffma2_rn(Ti, P, make_float2(-rq.x, -rq.y));
+    q.Q = Qi;
+    q.T = __fmul2_rn(q.T, om);  // the forward's T_{i+1}; unchanged (x 1) for a pixel not taking part
+  } else {
+    const float2 rq = __fmul2_rn(r, q.Q);
+    dA = __ffma2_rn(Ti, P, make_float2(-rq.x, -rq.y));
+    q.Q = __ffma2_rn(w, P, q.Q);
+  }
   const bool l0 = in0 && !(raw.x > kAlphaCap), l1 = in1 && !(raw.y > kAlphaCap);
   const float2 Ge = make_float2(l0 ? G.x : 0.0f, l1 ? G.y : 0.0f);
   const float2 re = make_float2(l0 ? raw.x : 0.0f, l1 ? raw.y : 0.0f);
@@ -448,12 +530,37 @@ template <int BATCH>
 struct BwdShared {
   Stage<BATCH> st;
   float acc[BATCH * kAccStride];
-  __align__(16) float red[kBwdThreads / 32][10 * kRedRow];  // per warp: the lanes' 10 sums, transposed
-  int maxlast;
+  __align__(16) float red[kBwdThreads / 32][3 * 10 * kRedRow];  // per warp: 3 visits' 10 sums, transposed
+  int maxlast, sumlast;
 };
 
-template <int BATCH>
-__device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BATCH>& sm) {
+// Warp sums of up to three buffered visits (each visit: every lane wrote its
+// 10 values as one column of 10 rows of kRedRow floats): lane r adds row r
+// with eight 16-byte loads and a packed-pair tree, and adds the total to the
+// CTA's accumulator entry of that visit's staged position (j0, j1, j2).
+__device__ __forceinline__ void flush_visits(const float* rb, float* acc, int nslot, int j0, int j1, int j2, int lane) {
+  __syncwarp();
+  if (lane < 10 * nslot) {
+    const float4* src = reinterpret_cast<const float4*>(rb + lane * kRedRow);
+    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float4 a = src[i];
+      s0 = __fadd2_rn(s0, make_float2(a.x, a.y));
+      s1 = __fadd2_rn(s1, make_float2(a.z, a.w));
+    }
+    const float2 t = __fadd2_rn(s0, s1);
+    const float tot = t.x + t.y;
+    const int slot = lane >= 20 ? 2 : (lane >= 10 ? 1 : 0);
+    const int j = slot == 0 ? j0 : (slot == 1 ? j1 : j2);
+    if (tot != 0.f) atomicAdd(acc + j * kAccStride + (lane - 10 * slot), tot);
+  }
+  __syncwarp();
+}
+
+// One part (FRONT: positions [0, m); else [m, last)) of one tile.
+template <int BATCH, bool FRONT>
+__device__ __forceinline__ void bwd_part(const ViewK& V, int tile, BwdShared<BATCH>& sm) {
   constexpr int NT = kBwdThreads;
   const CamK& cam = V.cam;
   const int tx = tile % cam.tiles_x, ty = tile / cam.tiles_x;
@@ -471,18 +578,27 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
       const int y = ty * kTile + (p ? ly1 : ly0);
       const bool inside = x < cam.width && y < cam.height;
       const size_t i = inside ? (size_t)y * cam.width + x : 0;
-      const float Tfin = inside ? V.img.t_final[i] : 1.0f;
       const float g0 = inside ? V.d_rgb[3 * i + 0] : 0.f;
       const float g1 = inside ? V.d_rgb[3 * i + 1] : 0.f;
       const float g2 = inside ? V.d_rgb[3 * i + 2] : 0.f;
+      const float gd = (inside && V.d_depth) ? V.d_depth[i] : 0.f;
+      const float gs = (inside && V.d_sil) ? V.d_sil[i] : 0.f;
       f[p][0] = -((float)y + 0.5f);
-      f[p][1] = Tfin;
       f[p][2] = g0;
       f[p][3] = g1;
       f[p][4] = g2;
-      f[p][5] = (inside && V.d_depth) ? V.d_depth[i] : 0.f;
-      f[p][6] = (inside && V.d_sil) ? V.d_sil[i] : 0.f;
-      f[p][7] = (g0 * V.bg0 + g1 * V.bg1 + g2 * V.bg2) * Tfin;
+      f[p][5] = gd;
+      f[p][6] = gs;
+      if (FRONT) {
+        f[p][1] = 1.0f;
+        f[p][7] = inside ? ((g0 * V.img.rgb[3 * i + 0] + g1 * V.img.rgb[3 * i + 1]) + g2 * V.img.rgb[3 * i + 2] +
+                           gd * V.img.depth[i]) + gs * V.img.sil[i]
+                         : 0.f;
+      } else {
+        const float Tfin = inside ? V.img.t_final[i] : 1.0f;
+        f[p][1] = Tfin;
+        f[p][7] = (g0 * V.bg0 + g1 * V.bg1 + g2 * V.bg2) * Tfin;
+      }
       q.last[p] = inside ? V.img.n_contrib[i] : 0;
     }
     q.nfy = make_float2(f[0][0], f[1][0]);
@@ -496,54 +612,61 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const StagePtrs sp{sm.st.xyzo, sm.st.quad, sm.st.cid, sm.st.wmask};
-  const int wlast = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(q.last[0], q.last[1]));
-  if (threadIdx.x == 0) sm.maxlast = 0;
+  const int wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(q.last[0], q.last[1]));
+  const int wsum = (int)__reduce_add_sync(0xffffffffu, (unsigned)(q.last[0] + q.last[1]));
+  if (threadIdx.x == 0) sm.maxlast = sm.sumlast = 0;
   __syncthreads();
-  if (lane == 0 && wlast > 0) atomicMax(&sm.maxlast, wlast);
+  if (lane == 0) {
+    if (wmax > 0) atomicMax(&sm.maxlast, wmax);
+    atomicAdd(&sm.sumlast, wsum);
+  }
   __syncthreads();
   const int maxlast = sm.maxlast;
-  for (int end = maxlast; end > 0; end -= BATCH) {
-    const int start = max(0, end - BATCH);
-    const int cnt = end - start;
+  const int m = min(maxlast, (sm.sumlast + 2 * kTilePixels - 1) / (2 * kTilePixels));  // split position
+  // the part's positions [lo, hi) and, per warp, the first position no pixel of the warp reaches
+  const int lo = FRONT ? 0 : m, hi = FRONT ? m : maxlast;
+  const int wlast = FRONT ? min(wmax, m) : wmax;
+  const int nb = (hi - lo + BATCH - 1) / BATCH;
+  for (int b = 0; b < nb; ++b) {
+    // batches in walk order: ascending from lo (front), descending from hi (back)
+    const int start = FRONT ? lo + b * BATCH : max(lo, hi - (b + 1) * BATCH);
+    const int cnt = FRONT ? min(BATCH, hi - start) : hi - b * BATCH - start;
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += NT)
       stage_one<true>(V, V.vals[rg.x + start + i], i, sp, tx * kTile, ty * kTile, 4);
     for (int i = threadIdx.x; i < BATCH * kAccStride; i += NT) sm.acc[i] = 0.f;
     __syncthreads();
     const int nl = build_warp_list(sm.st.wmask, sm.st.wlist[warp], cnt, warp);
-    for (int e = nl - 1; e >= 0; --e) {
+    float* rb = sm.red[warp];
+    int nslot = 0, j0 = 0, j1 = 0, j2 = 0;
+    for (int e0 = 0; e0 < nl; ++e0) {
+      const int e = FRONT ? e0 : nl - 1 - e0;
       const int j = sm.st.wlist[warp][e];
       const int pos = start + j;
-      if (pos >= wlast) continue;  // warp-uniform: no pixel of this warp reaches pos
+      if (pos >= wlast) {  // warp-uniform: no pixel of this warp reaches pos
+        if (FRONT) break;  // nor any later position
+        continue;
+      }
       const float4 xo = sm.st.xyzo[j];
       const float4 qd = sm.st.quad[j];
       const float4 cd = sm.st.cid[j];
       float v[10];
 #pragma unroll
       for (int k = 0; k < 10; ++k) v[k] = -0.0f;  // -0 + x = x exactly: the first sum folds away
-      const bool any = adjoint_step2(q, pos, xo, qd, cd.x, cd.y, cd.z, v);
-      if (__any_sync(0xffffffffu, any)) {
-        // warp sums of the 10 values through shared memory: lane writes its
-        // column, lanes 2k and 2k + 1 each add one half of row k (four
-        // 16-byte loads, a packed-pair tree) and combine by one shuffle
-        float* rb = sm.red[warp];
+      if (adjoint_step2<FRONT>(q, pos, xo, qd, cd.x, cd.y, cd.z, v)) {  // warp-uniform
+        float* row = rb + nslot * 10 * kRedRow + lane;
 #pragma unroll
-        for (int k = 0; k < 10; ++k) rb[k * kRedRow + lane] = v[k];
-        __syncwarp();
-        const int k = min(lane >> 1, 9);
-        const float4* src = reinterpret_cast<const float4*>(rb + k * kRedRow + 16 * (lane & 1));
-        const float4 a0 = src[0], a1 = src[1], a2 = src[2], a3 = src[3];
-        const float2 s0 = __fadd2_rn(make_float2(a0.x, a0.y), make_float2(a0.z, a0.w));
-        const float2 s1 = __fadd2_rn(make_float2(a1.x, a1.y), make_float2(a1.z, a1.w));
-        const float2 s2 = __fadd2_rn(make_float2(a2.x, a2.y), make_float2(a2.z, a2.w));
-        const float2 s3 = __fadd2_rn(make_float2(a3.x, a3.y), make_float2(a3.z, a3.w));
-        const float2 s4 = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
-        float tot = s4.x + s4.y;
-        tot += __shfl_xor_sync(0xffffffffu, tot, 1);
-        __syncwarp();  // the buffer is rewritten at the next visit
-        if (lane < 20 && !(lane & 1) && tot != 0.f) atomicAdd(&sm.acc[j * kAccStride + k], tot);
+        for (int k = 0; k < 10; ++k) row[k * kRedRow] = v[k];
+        j0 = nslot == 0 ? j : j0;
+        j1 = nslot == 1 ? j : j1;
+        j2 = nslot == 2 ? j : j2;
+        if (++nslot == 3) {
+          flush_visits(rb, sm.acc, 3, j0, j1, j2, lane);
+          nslot = 0;
+        }
       }
     }
+    if (nslot) flush_visits(rb, sm.acc, nslot, j0, j1, j2, lane);
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += NT) {
       const float* a = &sm.acc[i * kAccStride];
@@ -560,20 +683,21 @@ __device__ __forceinline__ void bwd_tile(const ViewK& V, int tile, BwdShared<BAT
   }
 }
 
+// Work item -> (view, tile, part): items 2 t and 2 t + 1 are the front and back
+// parts of the t-th tile over all views (of the view's heavy-first order when
+// it has one).
 template <int BATCH>
-__global__ void __launch_bounds__(kBwdThreads) render_bwd_kernel(ViewK V) {
-  __shared__ BwdShared<BATCH> sm;
-  bwd_tile<BATCH>(V, blockIdx.x, sm);
-}
-
-template <int BATCH>
-__global__ void __launch_bounds__(kBwdThreads) render_bwd_persistent(ViewTable T, int total, int* counter) {
+__global__ void __launch_bounds__(kBwdThreads, 8) render_bwd_persistent(ViewTable T, int total, int* counter) {
   __shared__ BwdShared<BATCH> sm;
   __shared__ int s_item;
-  for (int item = next_item(counter, &s_item); item < total; item = next_item(counter, &s_item)) {
+  for (int item = next_item(counter, &s_item); item < 2 * total; item = next_item(counter, &s_item)) {
     int tile;
-    const int v = view_of(T, item, tile);
-    bwd_tile<BATCH>(T.v[v], tile, sm);
+    const int v = view_of(T, item >> 1, tile);
+    if (T.v[v].order) tile = (int)T.v[v].order[tile];
+    if (item & 1)
+      bwd_part<BATCH, false>(T.v[v], tile, sm);
+    else
+      bwd_part<BATCH, true>(T.v[v], tile, sm);
   }
 }
 
@@ -605,7 +729,19 @@ static ViewK make_view(const splat_projected& proj, const float* rgb, const uint
   v.img = ImageK{im.rgb, im.depth, im.sil, im.t_final, im.n_contrib, im.max_id, im.n_used};
   v.d_rgb = v.d_depth = v.d_sil = nullptr;
   v.g2 = nullptr;
+  v.l1 = LossK{nullptr, nullptr, 0.f, 0.f, nullptr, nullptr, nullptr};
+  v.order = nullptr;
   return v;
+}
+
+static int set_loss(ViewK& v, const splat_l1* l1, const char* who) {
+  if (!l1) return SPLAT_OK;
+  if (!l1->t_rgb || !l1->t_depth || !l1->d_rgb || !l1->d_depth)
+    return fail(SPLAT_EINVAL, "%s: L1 targets or gradient images are null", who);
+  const int64_t npix = (int64_t)v.cam.width * v.cam.height;
+  v.l1 = LossK{l1->t_rgb, l1->t_depth, l1->w_rgb / (float)(3 * npix), l1->w_depth / (float)npix, l1->d_rgb,
+               l1->d_depth, l1->loss};
+  return SPLAT_OK;
 }
 
 static int sm_count() {
@@ -618,35 +754,54 @@ static int sm_count() {
 
 using namespace splat;
 
-extern "C" int splat_render_fwd(const splat_projected* proj, const float* rgb, int64_t n, const uint32_t* vals,
-                                const uint32_t* ranges, const splat_camera* cam, const float* bg,
-                                const splat_image* out, splat_stream_t stream) {
-  int rc = check_proj(proj, n, "splat_render_fwd");
+static int render_fwd_one(const splat_projected* proj, const float* rgb, int64_t n, const uint32_t* vals,
+                          const uint32_t* ranges, const splat_camera* cam, const float* bg, const splat_image* out,
+                          const splat_l1* l1, splat_stream_t stream, const char* who) {
+  int rc = check_proj(proj, n, who);
   if (rc) return rc;
   if ((n > 0 && !rgb) || !vals || !ranges || !cam || !bg || !out || !image_ok(*out))
-    return fail(SPLAT_EINVAL, "splat_render_fwd: null argument");
-  if (n < 0 || cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "splat_render_fwd: bad sizes");
-  const ViewK v = make_view(*proj, rgb, vals, ranges, *cam, bg, *out);
+    return fail(SPLAT_EINVAL, "%s: null argument", who);
+  if (n < 0 || cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "%s: bad sizes", who);
+  ViewK v = make_view(*proj, rgb, vals, ranges, *cam, bg, *out);
+  if ((rc = set_loss(v, l1, who))) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   SPLAT_LAUNCH("render_fwd_kernel", s,
                render_fwd_kernel<256><<<v.cam.tiles_x * v.cam.tiles_y, kFwdThreads, 0, s>>>(v));
   return check_launch("render_fwd_kernel");
 }
 
-extern "C" size_t splat_render_bwd_workspace_size(int64_t n) {
-  return n < 0 ? 0 : align_up(sizeof(float) * kGradStride * (size_t)std::max<int64_t>(n, 1));
+extern "C" int splat_render_fwd(const splat_projected* proj, const float* rgb, int64_t n, const uint32_t* vals,
+                                const uint32_t* ranges, const splat_camera* cam, const float* bg,
+                                const splat_image* out, splat_stream_t stream) {
+  return render_fwd_one(proj, rgb, n, vals, ranges, cam, bg, out, nullptr, stream, "splat_render_fwd");
 }
+
+extern "C" int splat_render_fwd_l1(const splat_projected* proj, const float* rgb, int64_t n, const uint32_t* vals,
+                                   const uint32_t* ranges, const splat_camera* cam, const float* bg,
+                                   const splat_image* out, const splat_l1* l1, splat_stream_t stream) {
+  if (!l1) return fail(SPLAT_EINVAL, "splat_render_fwd_l1: null loss descriptor");
+  return render_fwd_one(proj, rgb, n, vals, ranges, cam, bg, out, l1, stream, "splat_render_fwd_l1");
+}
+
+// Workspace of splat_render_bwd: the screen-space gradients [n, 12] and, after
+// them, the work-item counter of the persistent launch.
+static size_t g2_bytes(int64_t n) { return align_up(sizeof(float) * kGradStride * (size_t)std::max<int64_t>(n, 1)); }
+
+extern "C" size_t splat_render_bwd_workspace_size(int64_t n) { return n < 0 ? 0 : g2_bytes(n) + 256; }
 
 extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected* proj, const splat_camera* cam,
                                 const float* w2c, const uint32_t* vals, const uint32_t* ranges,
-                                const splat_image* fwd, const float* bg, const float* d_rgb, const float* d_depth,
+                                const uint32_t* tile_order, const splat_image* fwd, const float* bg,
+                                const float* d_rgb, const float* d_depth,
                                 const float* d_sil, const splat_gaussians_grad* out, float* d_pose, float* d2d,
                                 void* ws, size_t ws_bytes, splat_stream_t stream) {
   if (!g) return fail(SPLAT_EINVAL, "splat_render_bwd: null argument");
   int rc = check_proj(proj, g->n, "splat_render_bwd");
   if (rc) return rc;
-  if (!cam || !w2c || !vals || !ranges || !fwd || !fwd->t_final || !fwd->n_contrib || !bg || !d_rgb || !out ||
-      (g->n > 0 && (!out->mean || !out->log_scale || !out->quat || !out->opacity_logit || !out->rgb)))
+  const bool screen_only = !out && !d_pose && !d2d;  // the screen-space gradients alone, left in ws
+  if (!cam || !w2c || !vals || !ranges || !fwd || !fwd->t_final || !fwd->n_contrib || !bg || !d_rgb ||
+      (!out && !screen_only) ||
+      (out && g->n > 0 && (!out->mean || !out->log_scale || !out->quat || !out->opacity_logit || !out->rgb)))
     return fail(SPLAT_EINVAL, "splat_render_bwd: null argument");
   if ((g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->rgb)) || !aligned16(g->quat))
     return fail(SPLAT_EINVAL, "splat_render_bwd: gaussian arrays null or quat not 16-byte aligned");
@@ -654,18 +809,31 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
   if (g->n > 0 && !proj->radius) return fail(SPLAT_EINVAL, "splat_render_bwd: proj->radius is null");
   if (!ws || !aligned16(ws) || ws_bytes < splat_render_bwd_workspace_size(g->n))
     return fail(SPLAT_EINVAL, "splat_render_bwd: workspace missing, too small or not 16-byte aligned");
+  if (!fwd->rgb || !fwd->depth || !fwd->sil) return fail(SPLAT_EINVAL, "splat_render_bwd: forward image incomplete");
   float* g2 = static_cast<float*>(ws);
+  int* counter = reinterpret_cast<int*>(static_cast<char*>(ws) + g2_bytes(g->n));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (g->n > 0 && cudaMemsetAsync(g2, 0, sizeof(float) * kGradStride * (size_t)g->n, s) != cudaSuccess)
+  const size_t clear = g->n > 0 ? g2_bytes(g->n) + sizeof(int) : 0;
+  if (clear && cudaMemsetAsync(ws, 0, clear, s) != cudaSuccess)
     return fail(SPLAT_ECUDA, "splat_render_bwd: memset failed");
-  ViewK v = make_view(*proj, g->rgb, vals, ranges, *cam, bg, *fwd);
-  v.d_rgb = d_rgb;
-  v.d_depth = d_depth;
-  v.d_sil = d_sil;
-  v.g2 = g2;
-  SPLAT_LAUNCH("render_bwd_kernel", s,
-               render_bwd_kernel<128><<<v.cam.tiles_x * v.cam.tiles_y, kBwdThreads, 0, s>>>(v));
-  if ((rc = check_launch("render_bwd_kernel"))) return rc;
+  if (!clear && cudaMemsetAsync(counter, 0, sizeof(int), s) != cudaSuccess)
+    return fail(SPLAT_ECUDA, "splat_render_bwd: memset failed");
+  ViewTable T;
+  T.v[0] = make_view(*proj, g->rgb, vals, ranges, *cam, bg, *fwd);
+  T.v[0].d_rgb = d_rgb;
+  T.v[0].d_depth = d_depth;
+  T.v[0].d_sil = d_sil;
+  T.v[0].g2 = g2;
+  T.v[0].order = tile_order;
+  const int tiles = T.v[0].cam.tiles_x * T.v[0].cam.tiles_y;
+  T.tile_end[0] = tiles;
+  T.n = 1;
+  const int grid = std::min(2 * tiles, kBwdCtasPerSm * sm_count());
+  SPLAT_LAUNCH("render_bwd_persistent", s,
+               render_bwd_persistent<kBwdBatch><<<grid, kBwdThreads, 0, s>>>(T, tiles, counter));
+  if ((rc = check_launch("render_bwd_persistent"))) return rc;
+  if (screen_only) return SPLAT_OK;
+  const ViewK& v = T.v[0];
   GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
   GradK gr{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};
   return launch_project_bwd(gk, v.cam, w2c, proj->conic, proj->radius, g2, kGradStride, gr, d_pose, d2d, s);
@@ -688,6 +856,41 @@ extern "C" int splat_project_bwd(const splat_gaussians* g, const splat_projected
                             reinterpret_cast<cudaStream_t>(stream));
 }
 
+extern "C" int splat_project_bwd_adam(const splat_gaussians* g, const splat_projected* proj, const splat_camera* cam,
+                                      const float* w2c, const float* grad2d, const splat_gaussians_grad* m,
+                                      const splat_gaussians_grad* v, const float* lr, float beta1, float beta2,
+                                      float eps, const int32_t* step, float* d_pose, splat_stream_t stream) {
+  if (!g || !cam || !w2c || !grad2d || !m || !v || !lr || !step)
+    return fail(SPLAT_EINVAL, "splat_project_bwd_adam: null argument");
+  int rc = check_proj(proj, g->n, "splat_project_bwd_adam");
+  if (rc) return rc;
+  if (g->n < 0 || (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->rgb ||
+                                !m->mean || !m->log_scale || !m->quat || !m->opacity_logit || !m->rgb || !v->mean ||
+                                !v->log_scale || !v->quat || !v->opacity_logit || !v->rgb)) ||
+      !aligned16(g->quat) || !aligned16(grad2d))
+    return fail(SPLAT_EINVAL, "splat_project_bwd_adam: bad gaussian, moment or gradient arrays");
+  if (g->n > 0 && !proj->radius) return fail(SPLAT_EINVAL, "splat_project_bwd_adam: proj->radius is null");
+  GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
+  AdamMapK A;
+  float* const P[5] = {const_cast<float*>(g->mean), const_cast<float*>(g->log_scale), const_cast<float*>(g->quat),
+                       const_cast<float*>(g->opacity_logit), const_cast<float*>(g->rgb)};
+  float* const Ms[5] = {m->mean, m->log_scale, m->quat, m->opacity_logit, m->rgb};
+  float* const Vs[5] = {v->mean, v->log_scale, v->quat, v->opacity_logit, v->rgb};
+  for (int k = 0; k < 5; ++k) {
+    A.p[k] = P[k];
+    A.m[k] = Ms[k];
+    A.v[k] = Vs[k];
+    A.lr[k] = lr[k];
+    A.vec[k] = aligned16(P[k]) && aligned16(Ms[k]) && aligned16(Vs[k]);
+  }
+  A.b1 = beta1;
+  A.b2 = beta2;
+  A.eps = eps;
+  A.step = step;
+  return launch_project_bwd_adam(gk, make_camk(*cam), w2c, proj->conic, proj->radius, grad2d, kGradStride, A, d_pose,
+                                 reinterpret_cast<cudaStream_t>(stream));
+}
+
 // ---------------------------------------------------------------------------
 // Several views in one persistent launch
 // ---------------------------------------------------------------------------
@@ -704,10 +907,15 @@ static int build_table(const splat_view* views, int32_t n_views, bool bwd, ViewT
     if (bwd && (!w.d_rgb || !w.grad2d || !aligned16(w.grad2d)))
       return fail(SPLAT_EINVAL, "%s: view %d lacks d_rgb or a 16-byte aligned grad2d", who, i);
     ViewK v = make_view(w.proj, w.rgb, w.vals, w.ranges, w.cam, w.bg, w.image);
+    if (!bwd) {
+      const int rc = set_loss(v, w.l1, who);
+      if (rc) return rc;
+    }
     v.d_rgb = w.d_rgb;
     v.d_depth = w.d_depth;
     v.d_sil = w.d_sil;
     v.g2 = w.grad2d;
+    v.order = w.tile_order;
     T->v[i] = v;
     acc += v.cam.tiles_x * v.cam.tiles_y;
     T->tile_end[i] = acc;
@@ -717,7 +925,7 @@ static int build_table(const splat_view* views, int32_t n_views, bool bwd, ViewT
   return SPLAT_OK;
 }
 
-static splat_batch_shape default_shape() { return splat_batch_shape{256, 4, 256, 7}; }
+static splat_batch_shape default_shape() { return splat_batch_shape{256, 4, kBwdBatch, kBwdCtasPerSm}; }
 
 static bool shape_ok(const splat_batch_shape& sh) {
   auto b = [](int x) { return x == 64 || x == 128 || x == 256; };
@@ -775,7 +983,7 @@ extern "C" int splat_render_bwd_batch(const splat_view* views, int32_t n_views, 
     if (views[i].n > 0 &&
         cudaMemsetAsync(views[i].grad2d, 0, sizeof(float) * kGradStride * (size_t)views[i].n, s) != cudaSuccess)
       return fail(SPLAT_ECUDA, "splat_render_bwd_batch: memset failed");
-  const int grid = std::min(total, sh.bwd_ctas_per_sm * sm_count());
+  const int grid = std::min(2 * total, sh.bwd_ctas_per_sm * sm_count());
   if (grid <= 0) return SPLAT_OK;
   switch (sh.bwd_batch) {
     case 64:

@@ -5,7 +5,13 @@ and inter-agent processing of Sec. 3.2 / 3.6, on one GPU).
 * Residency.  Every admitted agent's map, Adam state, pose and work buffers
   live on the device and are charged against an HBM budget.  When a request
   arrives for an agent that is not resident and the budget is full, idle
-  agents are swapped out to pinned host memory, least recently used first.
+  agents are swapped out to pinned host memory -- first those with no request
+  waiting, least recently used first.  Swaps never block the loop: a
+  swap-out's copies run on a copy stream after the agent's last step and its
+  memory is released (and uncharged) when they are done; a swap-in allocates
+  the agent's buffers and copies its state in on the same stream, and the
+  agent's next step waits for that stream on the device, so the request is
+  batched at once.
 * Continuous batching.  At every tick the loop admits the requests that have
   arrived, takes up to `max_batch` ready requests of distinct agents (oldest
   first; an agent has at most one request in flight, so its state advances in
@@ -76,6 +82,11 @@ class _AgentSlot:
         self.out_loss = torch.empty(1, dtype=torch.float32, pin_memory=True)
         self.out_w2c = torch.empty(4, 4, dtype=torch.float32, pin_memory=True)
         self.graphs = {}  # request kind -> captured single-agent step of the resident agent
+        self.loading = None  # copy-stream event of a swap-in that may still run
+        self.last_event = None  # completion event of the agent's last launched step
+        self.evicting = None  # (agent, event): a swap-out whose copies may still run
+        self.evict_bytes = 0
+        self.side = None  # the agent's side stream, kept across swaps
 
 
 def _agent_bytes(a: Agent) -> int:
@@ -105,7 +116,7 @@ def _agent_bytes(a: Agent) -> int:
 
 class Server:
     def __init__(self, device, hbm_budget_bytes: int, max_batch: int = 8, n_streams: int = 2,
-                 shape=(256, 4, 256, 7), single_graphs: bool = True):
+                 shape=(256, 4, 64, 8), single_graphs: bool = True):
         self.device = device
         self.single_graphs = single_graphs  # a lone request replays its agent's captured step
         self.budget = int(hbm_budget_bytes)
@@ -119,10 +130,12 @@ class Server:
         self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
         self.agent_streams = [[torch.cuda.Stream(device=device) for _ in range(self.max_batch)]
                               for _ in range(n_streams)]
+        self.copy_stream = torch.cuda.Stream(device=device)  # swaps in and out
 
     def reset(self, budget: int | None = None):
         """Drop every agent's device state (they restart from their initial
         maps and poses at the next prepare())."""
+        torch.cuda.synchronize()
         for slot in self.slots:
             slot.agent = None
             slot.graphs = {}
@@ -130,6 +143,8 @@ class Server:
             slot.bytes = 0
             slot.busy = False
             slot.last_used = 0.0
+            slot.loading = slot.last_event = slot.evicting = None
+            slot.evict_bytes = 0
         self.used = 0
         self.swaps = 0
         if budget is not None:
@@ -143,67 +158,97 @@ class Server:
         self.slots.append(slot)
         return slot.aid
 
-    def _can_fit(self, slot: _AgentSlot) -> bool:
-        """Whether the agent fits once every idle resident is swapped out
-        (known footprint only; an agent never resident is always tried)."""
-        if slot.footprint == 0:
-            return True
-        idle = sum(s.bytes for s in self.slots if s.agent is not None and not s.busy)
-        return self.used - idle + slot.footprint <= self.budget
+    def _poll_swaps(self):
+        """Release the memory (and the budget) of swap-outs whose copies are
+        done, and forget swap-ins that have landed."""
+        for slot in self.slots:
+            if slot.evicting is not None and slot.evicting[1].query():
+                slot.evicting = None
+                self.used -= slot.evict_bytes
+                slot.evict_bytes = 0
+            if slot.loading is not None and slot.loading.query():
+                slot.loading = None
 
-    def _make_resident(self, slot: _AgentSlot, now: float) -> bool:
-        if slot.agent is not None:
-            return True
-        if not self._can_fit(slot):
-            return False
-        if slot.host_state is not None:
-            # swap in: the map comes from the saved state, not from the initial scene
-            from .scenes import Scene
-
-            p = slot.host_state[:5]
-            a = Agent(Scene(*p), slot.w2c, slot.cam, self.device, cfg=dataclasses.replace(slot.cfg),
-                      capacity=slot.capacity)
-            for dst, src in zip(a._state()[5:], slot.host_state[5:]):
-                dst.copy_(src, non_blocking=True)
-        else:
-            a = Agent(slot.scene, slot.w2c, slot.cam, self.device, cfg=dataclasses.replace(slot.cfg),
-                      capacity=slot.capacity)
-            if slot.capacity is None:
-                slot.capacity = a.fb.capacity
-        need = _agent_bytes(a)
-        if self.used + need > self.budget:
-            # swap out idle residents, least recently used first
-            for other in sorted((s for s in self.slots if s.agent is not None and not s.busy),
-                                key=lambda s: s.last_used):
-                if self.used + need <= self.budget:
-                    break
-                self._swap_out(other)
-        if self.used + need > self.budget:
-            del a
-            return False
-        slot.agent = a
-        slot.bytes = need
-        slot.footprint = need
-        self.used += need
-        slot.last_used = now
-        return True
-
-    def _swap_out(self, slot: _AgentSlot):
+    def _start_swap_out(self, slot: _AgentSlot):
+        """Copy the agent's state to pinned host memory on the copy stream,
+        after its last step; its device memory stays charged until then."""
         a = slot.agent
+        cs = self.copy_stream
+        if slot.last_event is not None:
+            cs.wait_event(slot.last_event)
+        if slot.loading is not None:
+            cs.wait_event(slot.loading)
         state = a._state()
         if slot.host_state is None:  # pinned host copies, allocated once per agent and reused
             slot.host_state = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in state]
-        s = torch.cuda.current_stream()
-        for dst, src in zip(slot.host_state, state):
-            dst.copy_(src, non_blocking=True)
-        s.synchronize()
-        slot.w2c = slot.host_state[-4].numpy().copy()
+        with torch.cuda.stream(cs):
+            for dst, src in zip(slot.host_state, state):
+                dst.copy_(src, non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(cs)
+        slot.evicting = (a, ev)  # the agent (and its memory) lives until the copies are done
+        slot.evict_bytes = slot.bytes
         slot.capacity = a.fb.capacity
         slot.agent = None
         slot.graphs = {}
-        self.used -= slot.bytes
         slot.bytes = 0
+        slot.loading = None
         self.swaps += 1
+
+    def _start_swap_in(self, slot: _AgentSlot, now: float):
+        """Allocate the agent and copy its state in on the copy stream (after
+        its own swap-out's copies, on the same stream); nothing waits on the
+        host.  A first residency builds the agent from its scene instead."""
+        cs = self.copy_stream
+        cfg = dataclasses.replace(slot.cfg)
+        if slot.side is None:
+            slot.side = torch.cuda.Stream(device=self.device)
+        if slot.host_state is not None:
+            with torch.cuda.stream(cs):
+                a = Agent(None, None, slot.cam, self.device, cfg=cfg, capacity=slot.capacity,
+                          state=slot.host_state, side=slot.side)
+            ev = torch.cuda.Event()
+            ev.record(cs)
+            slot.loading = ev
+        else:
+            a = Agent(slot.scene, slot.w2c, slot.cam, self.device, cfg=cfg, capacity=slot.capacity, side=slot.side)
+            if slot.capacity is None:
+                slot.capacity = a.fb.capacity
+        slot.agent = a
+        slot.bytes = slot.footprint if slot.footprint else _agent_bytes(a)
+        slot.footprint = slot.bytes
+        self.used += slot.bytes
+        slot.last_used = now
+
+    def _make_room(self, need: int, waiting) -> bool:
+        """Start swap-outs of idle residents until `need` bytes fit the budget
+        once they are done: first agents with no request waiting, least
+        recently used first.  True when the bytes fit now."""
+        if self.used + need <= self.budget:
+            return True
+        freeing = sum(sl.evict_bytes for sl in self.slots if sl.evicting is not None)
+        idle = [sl for sl in self.slots if sl.agent is not None and not sl.busy]
+        for sl in sorted(idle, key=lambda x: (x.aid in waiting, x.last_used)):
+            if self.used - freeing + need <= self.budget:
+                break
+            freeing += sl.bytes
+            self._start_swap_out(sl)
+        return False
+
+    def _admit(self, slot: _AgentSlot, now: float, waiting=()) -> bool:
+        """Make the agent resident (or loading) if the budget allows now;
+        otherwise start making room and report False."""
+        if slot.agent is not None:
+            return True
+        need = slot.footprint
+        if need and need > self.budget:
+            raise RuntimeError(f"agent {slot.aid} alone exceeds the HBM budget")
+        if need and not self._make_room(need, waiting):
+            return False
+        self._start_swap_in(slot, now)
+        if not need and self.used > self.budget:  # first residency, size learnt now: make room after the fact
+            self._make_room(0, waiting)
+        return True
 
     def prepare(self, size_capacity: bool = True):
         """Size every agent's duplicate buffers (one host read each, before
@@ -211,8 +256,11 @@ class Server:
         ones out when the budget requires; the agents resident at the end are
         the last ones that fit."""
         for slot in self.slots:
-            if not self._make_resident(slot, 0.0):
-                raise RuntimeError(f"agent {slot.aid} alone exceeds the HBM budget")
+            while not self._admit(slot, 0.0):
+                torch.cuda.synchronize()
+                self._poll_swaps()
+            torch.cuda.synchronize()
+            self._poll_swaps()
             if size_capacity:
                 slot.agent.size_capacity(1.5)
                 slot.capacity = slot.agent.fb.capacity
@@ -239,6 +287,9 @@ class Server:
     # -- one batched step ---------------------------------------------------------
     def _launch(self, reqs, si):
         s = self.streams[si]
+        for r in reqs:  # agents still being copied in: the step waits for the copy stream on the device
+            if self.slots[r.agent].loading is not None:
+                s.wait_event(self.slots[r.agent].loading)
         if len(reqs) == 1 and self.slots[reqs[0].agent].graphs:
             return self._launch_graph(reqs[0], s)
         agents = [self.slots[r.agent].agent for r in reqs]
@@ -251,21 +302,17 @@ class Server:
                 a.obs_depth.copy_(depth, non_blocking=True)
         for a, st in zip(agents, ast):
             st.wait_stream(s)
+            a.phase_clear(st)
             a.phase_pre(st)
         for st in ast[:len(agents)]:
             s.wait_stream(st)
         B.splat_render_fwd_batch(views, self.shape, self.batch_ws[si], s)
-        for a, st in zip(agents, ast):
-            st.wait_stream(s)
-            a.phase_loss(st)
-        for st in ast[:len(agents)]:
-            s.wait_stream(st)
         B.splat_render_bwd_batch(views, self.shape, self.batch_ws[si], s)
         for r, a, st in zip(reqs, agents, ast):
             st.wait_stream(s)
-            a.phase_project_backward(st)
             a.cfg.track = r.kind == "track"
             a.cfg.map = r.kind == "map"
+            a.phase_project_backward(st)
             a.phase_update(st)
         for st in ast[:len(agents)]:
             s.wait_stream(st)
@@ -297,6 +344,10 @@ class Server:
         ev = torch.cuda.Event()
         ev.record(s)
         return ev, [(slot.out_loss, slot.out_w2c)]
+
+    def _mark_launched(self, reqs, ev):
+        for r in reqs:
+            self.slots[r.agent].last_event = ev
 
     def _finish(self, reqs, outs, now):
         for r, (loss, w2c) in zip(reqs, outs):
@@ -330,6 +381,7 @@ class Server:
             now = time.perf_counter() - t0
             while pending and (not realtime or pending[0].arrival <= now):
                 ready.append(pending.popleft())
+            self._poll_swaps()
             # completions
             for si in list(in_flight):
                 ev, reqs, outs = in_flight[si]
@@ -339,6 +391,7 @@ class Server:
                     del in_flight[si]
             # admissions: free stream slots take the oldest ready requests of idle, resident agents
             free = [si for si in range(self.n_streams) if si not in in_flight]
+            waiting = {r.agent for r in ready}
             while free and ready:
                 batch, seen, keep = [], set(), collections.deque()
                 # requests of resident agents first; swap agents in only when none is left
@@ -353,7 +406,7 @@ class Server:
                                 or (resident_only and slot.agent is None)):
                             keep.append(r)
                             continue
-                        if not self._make_resident(slot, now):
+                        if not self._admit(slot, now, waiting):
                             failed.add(r.agent)
                             keep.append(r)
                             continue
@@ -368,10 +421,14 @@ class Server:
                 for r in batch:
                     r.start = now
                 ev, outs = self._launch(batch, si)
+                self._mark_launched(batch, ev)
                 in_flight[si] = (ev, batch, outs)
             if not in_flight and not ready and pending and realtime:
                 time.sleep(max(0.0, min(0.0005, pending[0].arrival - (time.perf_counter() - t0))))
+            elif not in_flight and ready:  # waiting for memory: swap-outs in flight
+                time.sleep(0.00005)
         torch.cuda.synchronize()
+        self._poll_swaps()
         status = 0
         for slot in self.slots:
             if slot.agent is not None:
@@ -398,8 +455,11 @@ class Server:
             if realtime and r.arrival > now:
                 time.sleep(r.arrival - now)
             slot = self.slots[r.agent]
-            if not self._make_resident(slot, time.perf_counter() - t0):
-                raise RuntimeError("agent does not fit the HBM budget alone")
+            while not self._admit(slot, time.perf_counter() - t0):
+                self.copy_stream.synchronize()  # the swap-outs that make room
+                self._poll_swaps()
+            if slot.loading is not None:
+                s.wait_event(slot.loading)
             a = slot.agent
             r.start = time.perf_counter() - t0
             rgb, depth = slot.frames[r.frame]

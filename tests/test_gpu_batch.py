@@ -76,7 +76,7 @@ SMALL = ((15000, scenes.Camera(320, 240, 262.5, 262.5, 160.0, 120.0)),
          (90000, scenes.Camera(600, 340, 300.0, 300.0, 300.0, 170.0)))
 
 
-@pytest.mark.parametrize("shape", [(256, 4, 256, 7), (64, 8, 128, 10)])
+@pytest.mark.parametrize("shape", [(256, 4, 64, 8), (64, 8, 256, 10)])
 def test_batched_step_matches_oracle_whole_frames(dev, shape):
     from paper_2412_09723_gb300.batch import MultiAgentBatch
 

@@ -198,6 +198,46 @@ def test_mahalanobis_iterations_reduce_error(dev):
     assert e1[0] < 0.1 * e0[0] and e1[1] < 0.1 * e0[1], (e0, e1)
 
 
+def test_mahalanobis_system_step_matches_oracle_and_clears(dev):
+    """The one-launch form: the pairs split over two calls (the first only
+    accumulating, the second solving in its last CTA) give the oracle's step
+    of the whole set; sys is left zero, and the next call solves afresh."""
+    from paper_2412_09723_gb300 import binding as B
+
+    a, b, pairs, weights, T_true, T0 = _maha_case(11)
+    pa = [_t(x, dev) for x in a.arrays()]
+    pb = [_t(x, dev) for x in b.arrays()]
+    ga, gb = B.gaussians_struct(*pa), B.gaussians_struct(*pb)
+    half = len(pairs) // 2
+    parts = [(pairs[:half], weights[:half]), (pairs[half:], weights[half:])]
+    T = _t(T0, dev)
+    sys = torch.zeros(32, dtype=torch.float64, device=dev)
+    delta = torch.zeros(6, dtype=torch.float64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    x_l, cov_l, x_k, cov_k = _maha_ref(a, b, pairs, weights, T0)
+    cost, g, H = C.mahalanobis_system(T0.astype(np.float64), x_l, cov_l, x_k, cov_k, weights)
+    d_ref = -np.linalg.solve(H, g)
+    for it in range(2):
+        T.copy_(_t(T0, dev))
+        (p0, w0), (p1, w1) = parts
+        B.splat_mahalanobis_system(ga, gb, _t(p0, dev, np.int32), _t(w0, dev, np.int32),
+                                   torch.tensor([len(p0)], dtype=torch.int64, device=dev), T, sys)
+        B.splat_mahalanobis_system_step(ga, gb, _t(p1, dev, np.int32), _t(w1, dev, np.int32),
+                                        torch.tensor([len(p1)], dtype=torch.int64, device=dev), T, sys, delta, status)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        assert not sys.any()  # left zero, counter included
+        np.testing.assert_allclose(delta.cpu().numpy(), d_ref, rtol=1e-3, atol=1e-3 * np.abs(d_ref).max())
+        np.testing.assert_allclose(T.cpu().numpy(), C.se3_exp(d_ref) @ T0.astype(np.float64), atol=2e-6)
+    # no pairs at all: the solve reports the singular system, T unchanged
+    T.copy_(_t(T0, dev))
+    B.splat_mahalanobis_system_step(ga, gb, _t(pairs, dev, np.int32), None, torch.zeros(1, dtype=torch.int64, device=dev),
+                                    T, sys, None, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == B.SPLAT_ENUMERIC and not sys.any()
+    assert np.array_equal(T.cpu().numpy(), T0.astype(np.float32))
+
+
 def test_mahalanobis_without_pairs_reports_numeric_status(dev):
     from paper_2412_09723_gb300 import binding as B
 

@@ -142,6 +142,20 @@ def _check_bins(fb, sc, w2c, cam):
     assert np.array_equal(fb.vals[:k].cpu().numpy().view(np.uint32), vals)
     assert np.array_equal(fb.keys[:k].cpu().numpy().view(np.uint64), keys)
     assert np.array_equal(fb.ranges.cpu().numpy().view(np.uint32), ranges)
+    _check_tile_order(fb.tile_order.cpu().numpy(), ranges)
+
+
+def _check_tile_order(order, ranges):
+    """A permutation of the tiles, list lengths non-increasing in steps of an
+    eighth of an octave (the exponent and three mantissa bits of the length as
+    a float32; empty lists last)."""
+    order = order.view(np.uint32)
+    n_t = len(ranges)
+    assert np.array_equal(np.sort(order), np.arange(n_t, dtype=np.uint32))
+    c = (ranges[:, 1] - ranges[:, 0]).astype(np.float32)
+    b = np.where(c > 0, ((c.view(np.uint32) >> 20).astype(np.int64) - (127 << 3)) + 1, 0)
+    b = np.minimum(b, 127)[order]
+    assert (np.diff(b) <= 0).all()
 
 
 def _check_image(fb, ref):
@@ -177,7 +191,8 @@ def _bwd_gpu(p, fb, w2c, cam, bg, g, dev):
     d2d = torch.zeros(sc_n(p), 10, dtype=torch.float32, device=dev)
     gr, gd, gs = (torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev) for a in g)
     B.splat_render_bwd(B.gaussians_struct(*p), fb.cproj, fb.ccam, _w(w2c, dev), fb.vals, fb.ranges, fb.cimg, bg,
-                       gr, gd, gs, B.CGaussiansGrad(*(B._p(t) for t in grads)), d_pose, d2d, fb.bwd_ws)
+                       gr, gd, gs, B.CGaussiansGrad(*(B._p(t) for t in grads)), d_pose, d2d, fb.bwd_ws,
+                       tile_order=fb.tile_order)
     torch.cuda.synchronize()
     return [t.cpu().numpy() for t in grads], d_pose.cpu().numpy(), d2d.cpu().numpy()
 
@@ -620,3 +635,133 @@ def test_assoc_runs_and_global_table(dev):
     assert len(ref2[0]) > 3 * 2000
     got2 = _assoc_gpu(dev, ia2, ta, ib2, tb, 3, 60000, 0.8)
     assert np.array_equal(got2[0], ref2[0]) and np.array_equal(got2[1], ref2[1])
+
+
+# ---------------------------------------------------------------------------
+# fused entry points: forward render with the L1 terms, projection adjoint
+# with the map's Adam step
+# ---------------------------------------------------------------------------
+def test_render_fwd_l1_matches_oracle_loss(dev):
+    """splat_render_fwd_l1: the image bit for bit as splat_render_fwd, the L1
+    gradients bit for bit as the oracle's on that image, the loss to 1e-5."""
+    from paper_2412_09723_gb300 import binding as B
+    from paper_2412_09723_gb300 import rasterizer as R
+
+    sc, w2c, cam, bg = CASES["room_20k_200x150_ragged"]
+    p, fb = _render_gpu(sc, w2c, cam, bg, dev)
+    ref = oracle.render_fwd(sc, w2c, cam, bg)
+    tgt = oracle.render_fwd(sc, scenes.perturbed_w2c(31, 0.01, 0.5, base=w2c), cam, bg)
+    t_rgb, t_depth = (torch.as_tensor(tgt[k], device=dev) for k in ("rgb", "depth"))
+    t_rgb[:2] = torch.as_tensor(ref["rgb"][:2], device=dev)  # exact ties: zero subgradient
+    g_rgb, g_depth = torch.full_like(t_rgb, 7.0), torch.full_like(t_depth, 7.0)
+    loss = torch.full((1,), 0.25, device=dev)
+    fb2 = R.FrameBuffers(sc.n, cam, dev)
+    R.project(B.gaussians_struct(*p), _w(w2c, dev), fb2)
+    R.bin_sort(fb2)
+    l1 = B.l1_struct(t_rgb, t_depth, 1.0, 0.5, g_rgb, g_depth, loss)
+    B.splat_render_fwd_l1(fb2.cproj, p[4], sc.n, fb2.vals, fb2.ranges, fb2.ccam, tuple(float(x) for x in bg), fb2.cimg,
+                          l1)
+    torch.cuda.synchronize()
+    _check_image(fb2, ref)
+    L, rg, rd = oracle.loss_l1(ref["rgb"], ref["depth"], t_rgb.cpu().numpy(), t_depth.cpu().numpy(), 1.0, 0.5)
+    assert np.array_equal(_bits(g_rgb.cpu().numpy()), _bits(rg))
+    assert np.array_equal(_bits(g_depth.cpu().numpy()), _bits(rd))
+    assert (rg[:2] == 0).all()
+    assert float(loss.item()) == pytest.approx(0.25 + L, rel=1e-5)
+
+
+def _fused_case(dev, seed):
+    from paper_2412_09723_gb300 import binding as B
+
+    sc, w2c, cam, bg = CASES["room_20k_200x150_ragged"]
+    p, fb = _render_gpu(sc, w2c, cam, bg, dev)
+    g = _upstream(cam, seed)
+    gr, gd, gs = (torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev) for a in g)
+    B.splat_render_bwd(B.gaussians_struct(*p), fb.cproj, fb.ccam, _w(w2c, dev), fb.vals, fb.ranges, fb.cimg, bg,
+                       gr, gd, gs, None, None, None, fb.bwd_ws)  # screen-space gradients only
+    torch.cuda.synchronize()
+    return sc, w2c, cam, bg, g, p, fb
+
+
+LRS = (1e-4, 1e-3, 1e-3, 5e-2, 2.5e-3)
+
+
+def test_project_bwd_adam_equals_adjoint_then_adam(dev):
+    """The fused adjoint + Adam step (kept Gaussians by the adjoint, culled ones
+    with gradient 0) moves the map and both moments exactly as
+    splat_project_bwd into zeroed gradients followed by splat_adam_groups, and
+    gives the same pose gradient (step 3, non-zero moments on half of the
+    map, the rest of the moments zero: those elements stay untouched)."""
+    from paper_2412_09723_gb300 import binding as B
+
+    sc, w2c, cam, bg, g, p, fb = _fused_case(dev, 14)
+    rng = np.random.default_rng(15)
+    n = sc.n
+    keep = torch.as_tensor(rng.random(n) < 0.5, device=dev)
+    ms = [torch.as_tensor(rng.normal(0, 1e-3, tuple(t.shape)).astype(np.float32), device=dev) for t in p]
+    vs = [torch.as_tensor(rng.uniform(1e-7, 1e-6, tuple(t.shape)).astype(np.float32), device=dev) for t in p]
+    for t in ms + vs:
+        t[~keep] = 0.0
+    step = torch.tensor([3], dtype=torch.int32, device=dev)
+    # unfused
+    pa = [t.clone() for t in p]
+    ma, va = [t.clone() for t in ms], [t.clone() for t in vs]
+    grads = [torch.zeros_like(t) for t in p]
+    pose_a = torch.zeros(6, device=dev)
+    B.splat_project_bwd(B.gaussians_struct(*pa), fb.cproj, fb.ccam, _w(w2c, dev), fb.bwd_ws,
+                        B.CGaussiansGrad(*(B._p(t) for t in grads)), pose_a)
+    B.splat_adam_groups(B.AdamGroups(pa, grads, ma, va, list(LRS)), step, zero_grad=True)
+    # fused
+    pb = [t.clone() for t in p]
+    mb, vb = [t.clone() for t in ms], [t.clone() for t in vs]
+    pose_b = torch.zeros(6, device=dev)
+    cmb, cvb = B.CGaussiansGrad(*(B._p(t) for t in mb)), B.CGaussiansGrad(*(B._p(t) for t in vb))
+    B.splat_project_bwd_adam(B.gaussians_struct(*pb), fb.cproj, fb.ccam, _w(w2c, dev), fb.bwd_ws, cmb, cvb, LRS, step,
+                             pose_b)
+    torch.cuda.synchronize()
+    for a, b in zip(pa + ma + va, pb + mb + vb):
+        assert torch.equal(a, b)
+    kept = fb.proj["radius"] != 0
+    assert not torch.equal(pb[0][~kept & keep], p[0][~kept & keep])  # culled with moments: moved
+    culled = fb.proj["radius"] == 0
+    assert bool(culled.any()) and bool((~culled).any())
+    assert torch.equal(pb[0][culled & ~keep], p[0][culled & ~keep])  # zero state, zero gradient: untouched
+    np.testing.assert_allclose(pose_b.cpu().numpy(), pose_a.cpu().numpy(), rtol=1e-5,
+                               atol=1e-5 * float(pose_a.abs().max()))
+
+
+def test_project_bwd_adam_matches_oracle(dev):
+    """Against the oracle: the oracle's adjoint of the same per-pixel upstream
+    gradients, then the oracle's Adam (step 2) with moments large against the
+    gradient tolerance: every parameter's update within 1e-3 of the oracle's
+    (relative to the largest update of its tensor) and the pose gradient by
+    the gradient rule."""
+    from paper_2412_09723_gb300 import binding as B
+
+    sc, w2c, cam, bg, g, p, fb = _fused_case(dev, 16)
+    ref = oracle.render_bwd(sc, w2c, cam, bg, *g)
+    names = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
+    rng = np.random.default_rng(17)
+    ms, vs = [], []
+    for name in names:
+        gr = ref[name]
+        scale = float(np.abs(gr).max()) + 1e-30
+        ms.append((rng.normal(0, 1, gr.shape) * scale).astype(np.float32))
+        vs.append((rng.uniform(0.5, 2.0, gr.shape) * scale * scale).astype(np.float32))
+    mb = [torch.as_tensor(x, device=dev) for x in ms]
+    vb = [torch.as_tensor(x, device=dev) for x in vs]
+    pb = [t.clone() for t in p]
+    pose = torch.zeros(6, device=dev)
+    step = torch.tensor([2], dtype=torch.int32, device=dev)
+    cmb, cvb = B.CGaussiansGrad(*(B._p(t) for t in mb)), B.CGaussiansGrad(*(B._p(t) for t in vb))
+    B.splat_project_bwd_adam(B.gaussians_struct(*pb), fb.cproj, fb.ccam, _w(w2c, dev), fb.bwd_ws, cmb, cvb, LRS, step,
+                             pose)
+    torch.cuda.synchronize()
+    for k, name in enumerate(names):
+        p0 = getattr(sc, name).astype(np.float32)
+        rp, rm, rv = oracle.adam(p0, ref[name], ms[k], vs[k], 2, LRS[k])
+        du_ref = rp.astype(np.float64) - p0
+        du = pb[k].cpu().numpy().astype(np.float64) - p0
+        assert np.abs(du - du_ref).max() <= 1e-3 * np.abs(du_ref).max(), name
+        _assert_grad_close(mb[k].cpu().numpy(), rm, name + " m")
+    _assert_grad_close(pose.cpu().numpy(), ref["pose"], "pose")

@@ -1,6 +1,8 @@
 """The multi-threaded build of the oracle (the timed CPU baseline) against the
 single-threaded parity build: the same forward results bit for bit, and the
-same adjoint up to the grouping of its sums (per-thread buffers)."""
+same adjoint up to the grouping of its sums (per-thread buffers, filled in a
+dynamic tile order, so the last bits vary from run to run): within the
+gradient rule |g - g_ref| <= 1e-3 |g_ref| + 1e-3 rms(g_ref) per tensor."""
 import numpy as np
 import pytest
 
@@ -49,4 +51,4 @@ def test_threaded_adjoint_matches_parity_build(case):
         for k in ("mean", "log_scale", "quat", "opacity_logit", "rgb", "pose", "d2d"):
             a, b = np.asarray(x[k], np.float64), np.asarray(r[k], np.float64)
             rms = float(np.sqrt(np.mean(b ** 2)))
-            assert np.all(np.abs(a - b) <= 1e-4 * np.abs(b) + 1e-5 * rms), k
+            assert np.all(np.abs(a - b) <= 1e-3 * np.abs(b) + 1e-3 * rms), k
