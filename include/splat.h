@@ -169,6 +169,23 @@ int splat_project(const splat_gaussians *g, const splat_camera *cam, const float
                   const splat_projected *out, splat_stream_t stream);
 
 /*
+ * Tile schedule: the order in which the persistent backward render takes a
+ * view's tiles, heaviest first, so that it ends on light tiles.  The cost of
+ * a tile's adjoint is the number of list positions its pixels walk, which the
+ * forward render knows only at its end (it is not the list length: a pixel
+ * stops at its last contributor).  Layout: uint32
+ * [SPLAT_SCHEDULE_BUCKETS + SPLAT_SCHEDULE_BUCKETS * n_tiles]: bucket counts,
+ * then one list of tile ids per bucket; bucket b holds the tiles whose summed
+ * contributor counts S have 1 + floor(8 log2 S) = b (in steps of an eighth of
+ * an octave; S = 0 in bucket 0; capped at the last bucket).  splat_bin_sort
+ * clears the counts, splat_render_fwd_l1 (or a batch forward) fills the
+ * lists, splat_render_bwd (or a batch backward) reads them.  The schedule
+ * changes only the order of the work: results are the same without it.
+ */
+#define SPLAT_SCHEDULE_BUCKETS 128
+size_t splat_tile_schedule_size(int32_t n_tiles); /* bytes */
+
+/*
  * splat_bin_sort -- duplicate every visible Gaussian into each of its member
  * tiles and sort the (tile, depth) keys (the tile binning and front-to-back
  * order the rendering equation of Sec. 3.3 composites in).
@@ -196,11 +213,8 @@ int splat_project(const splat_gaussians *g, const splat_camera *cam, const float
  *   capacity: number of slots in keys/vals (< 2^31)
  *   k_dev:    device int64[1]: receives K, the number of duplicates
  *   ranges:   device uint32[2 * n_tiles]
- *   tile_order: device uint32[n_tiles] or NULL: receives every tile id once,
- *             the tiles with the longest lists first (descending in steps of
- *             an eighth of an octave of the list length; ties in any order):
- *             the order in which splat_render_bwd's persistent launch takes
- *             the tiles, so that it ends on short lists
+ *   schedule: a tile schedule (below) or NULL: its bucket counts are set to
+ *             zero here, for the forward render to fill
  *   status:   device int32[1]: set to SPLAT_ECAPACITY when K > capacity (the
  *             sorted lists are then incomplete; resize and call again);
  *             never cleared by the library
@@ -210,7 +224,7 @@ int splat_project(const splat_gaussians *g, const splat_camera *cam, const float
 size_t splat_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t n_tiles);
 int splat_bin_sort(const splat_projected *proj, int64_t n, const splat_camera *cam,
                    uint64_t *keys, uint32_t *vals, int64_t capacity, int64_t *k_dev,
-                   uint32_t *ranges, uint32_t *tile_order, int32_t *status, void *ws,
+                   uint32_t *ranges, uint32_t *schedule, int32_t *status, void *ws,
                    size_t ws_bytes, splat_stream_t stream);
 
 /*
@@ -263,8 +277,8 @@ int splat_render_fwd(const splat_projected *proj, const float *rgb, int64_t n,
  * optimisation, Sec. 3.5 steps 3-4).
  *   proj: the splat_project output for this map, camera and pose (its radius
  *     is read: Gaussians it culled get no gradient and are skipped).
- *   tile_order: splat_bin_sort's heavy-first tile order, or NULL for the
- *     natural order (the result is the same either way).
+ *   schedule: the view's tile schedule as splat_render_fwd_l1 left it, or
+ *     NULL for the natural order (the result is the same either way).
  *   d_rgb [H,W,3], d_depth [H,W], d_sil [H,W] (d_depth, d_sil may be NULL).
  *   fwd: the image of the forward call (t_final, n_contrib are read).
  *   out: Gaussian-parameter gradients, ACCUMULATED (+=); the caller zeroes.
@@ -286,7 +300,7 @@ int splat_render_fwd(const splat_projected *proj, const float *rgb, int64_t n,
 size_t splat_render_bwd_workspace_size(int64_t n);
 int splat_render_bwd(const splat_gaussians *g, const splat_projected *proj,
                      const splat_camera *cam, const float *w2c, const uint32_t *vals,
-                     const uint32_t *ranges, const uint32_t *tile_order,
+                     const uint32_t *ranges, const uint32_t *schedule,
                      const splat_image *fwd, const float *bg,
                      const float *d_rgb, const float *d_depth, const float *d_sil,
                      const splat_gaussians_grad *out, float *d_pose, float *d2d, void *ws,
@@ -314,12 +328,14 @@ int splat_project_bwd(const splat_gaussians *g, const splat_projected *proj, con
  * step with the gradient the projection adjoint gives it -- the gradient
  * splat_project_bwd would accumulate into zeroed arrays, 0 for a Gaussian the
  * projection culled -- the same update as splat_adam_groups with those
- * gradients, bit for bit.  No gradient array is read or written.  One part
- * of the launch runs the adjoint and update of the kept Gaussians (radius >
- * 0), the other the zero-gradient update of the culled ones, side by side;
- * elements of culled Gaussians whose moments are both +0 are left exactly
- * as they are (their update is nothing).  The pose gradient is accumulated
- * into d_pose (if not NULL) as by splat_project_bwd.
+ * gradients, bit for bit.  No gradient array is read or written.  The kept
+ * Gaussians (radius > 0) run the adjoint and their update; with culled != 0
+ * the culled ones take their zero-gradient update in other CTAs of the same
+ * launch, else the caller runs splat_adam_culled for them (which needs only
+ * the projection, so it can run beside the render on another stream).
+ * Elements of culled Gaussians whose moments are both +0 are left exactly as
+ * they are (their update is nothing).  The pose gradient is accumulated into
+ * d_pose (if not NULL) as by splat_project_bwd.
  *   g: the map; its arrays are UPDATED IN PLACE (the const of splat_gaussians
  *     does not hold for this call).  m, v: device moments of the same shapes.
  *   lr: HOST float[5], the step sizes of mean, log_scale, quat,
@@ -331,7 +347,18 @@ int splat_project_bwd_adam(const splat_gaussians *g, const splat_projected *proj
                            const splat_camera *cam, const float *w2c, const float *grad2d,
                            const splat_gaussians_grad *m, const splat_gaussians_grad *v,
                            const float *lr, float beta1, float beta2, float eps,
-                           const int32_t *step, float *d_pose, splat_stream_t stream);
+                           const int32_t *step, int32_t culled, float *d_pose,
+                           splat_stream_t stream);
+
+/*
+ * splat_adam_culled -- the zero-gradient Adam step of the Gaussians a
+ * projection culled (radius == 0), the other part of splat_project_bwd_adam
+ * called with culled = 0; arguments as there, radius from splat_project.
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_adam_culled(const splat_gaussians *g, const int32_t *radius, const splat_gaussians_grad *m,
+                      const splat_gaussians_grad *v, const float *lr, float beta1, float beta2,
+                      float eps, const int32_t *step, splat_stream_t stream);
 
 /*
  * splat_render_fwd_l1 -- splat_render_fwd with the L1 terms of the loss of
@@ -344,7 +371,13 @@ int splat_project_bwd_adam(const splat_gaussians *g, const splat_projected *proj
  *   splat_loss_l1 on the rendered images bit for bit; the loss is summed in a
  *   different order (per tile, then one float atomic per tile).
  *   l1: descriptor below (device arrays [H,W,3] / [H,W]; loss: device float,
- *   accumulated, the caller zeroes it).  Errors: as splat_render_fwd.
+ *   accumulated, the caller zeroes it), or NULL for a render without loss
+ *   terms that fills the schedule.
+ *   schedule: a tile schedule whose counts splat_bin_sort cleared (each tile
+ *     is added to its bucket once), or NULL.  A schedule filled twice without
+ *     a clear in between no longer adds up to the number of tiles and is
+ *     ignored by the backward (natural order).
+ * Errors: as splat_render_fwd.
  */
 typedef struct {
   const float *t_rgb;    /* target colour [H,W,3] */
@@ -358,7 +391,7 @@ typedef struct {
 int splat_render_fwd_l1(const splat_projected *proj, const float *rgb, int64_t n,
                         const uint32_t *vals, const uint32_t *ranges, const splat_camera *cam,
                         const float *bg, const splat_image *out, const splat_l1 *l1,
-                        splat_stream_t stream);
+                        uint32_t *schedule, splat_stream_t stream);
 
 /*
  * Several views in one launch (batched differentiable rendering across
@@ -387,8 +420,8 @@ typedef struct {
                             zeroed and filled by splat_render_bwd_batch */
   const splat_l1 *l1;    /* forward only, optional: the view's L1 loss terms taken in the
                             forward's epilogue (as splat_render_fwd_l1); NULL = none */
-  const uint32_t *tile_order; /* backward only, optional: splat_bin_sort's heavy-first tile
-                                 order for this view; NULL = natural order */
+  uint32_t *schedule;    /* optional tile schedule of the view (splat_render_fwd_l1): the
+                            forward fills it, the backward takes the tiles in its order */
 } splat_view;
 
 /* Execution shape (does not change any result): shared-memory batch of

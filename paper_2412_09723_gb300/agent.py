@@ -46,6 +46,9 @@ class StepConfig:
     assoc: bool = True
     t_max: float = 0.5
     bg: tuple = (0.0, 0.0, 0.0)
+    # the culled Gaussians' zero-gradient Adam step on the side stream, beside
+    # the backward render (else inside the fused projection adjoint's launch)
+    culled_beside: bool = False
 
 
 class Agent:
@@ -186,7 +189,8 @@ class Agent:
         fb = self.fb
         project(self.cg, self.w2c, fb, stream)
         bin_sort(fb, stream, sync_check=sync_check)
-        B.splat_render_fwd(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg, stream)
+        B.splat_render_fwd_l1(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg,
+                              None, stream, schedule=fb.schedule)
 
     # The step in phases, so that a multi-agent batch can interleave them.
     def phase_clear(self, s):
@@ -212,7 +216,7 @@ class Agent:
         (needs phase_clear before it, and the observation in place)."""
         fb = self.fb
         B.splat_render_fwd_l1(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg,
-                              self.cl1, s)
+                              self.cl1, s, schedule=fb.schedule)
 
     def phase_loss(self, s):
         """Clear, then the L1 terms as a separate pass over a rendered image
@@ -226,7 +230,7 @@ class Agent:
         """Screen-space adjoint of the render (left in the backward workspace)."""
         fb = self.fb
         B.splat_render_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.vals, fb.ranges, fb.cimg, self.cfg.bg,
-                           self.g_rgb, self.g_depth, None, None, None, None, fb.bwd_ws, s, tile_order=fb.tile_order)
+                           self.g_rgb, self.g_depth, None, None, None, None, fb.bwd_ws, s, schedule=fb.schedule)
 
     def phase_project_backward(self, s):
         """Projection adjoint of the screen-space gradients in the backward
@@ -236,10 +240,16 @@ class Agent:
         fb = self.fb
         if self.cfg.map:
             B.splat_project_bwd_adam(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cm, self.cv, self.lrs,
-                                     self.t_dev, self.d_pose, stream=s)
+                                     self.t_dev, self.d_pose, stream=s, culled=not self.cfg.culled_beside)
         else:
             self.grads_clean = False
             B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cgr, self.d_pose, None, s)
+
+    def phase_adam_culled(self, s):
+        """With mapping on and `culled_beside`: the culled Gaussians'
+        zero-gradient Adam step (needs only the projection's radii)."""
+        if self.cfg.map and self.cfg.culled_beside:
+            B.splat_adam_culled(self.cg, self.fb.proj["radius"], self.cm, self.cv, self.lrs, self.t_dev, stream=s)
 
     def phase_update(self, s, assoc: bool = True, pose_stream=None):
         """The pose step (on `pose_stream` when given, after the projection
@@ -283,8 +293,9 @@ class Agent:
         self.phase_pre(s, sync_check)
         s.wait_stream(self.side)
         self.phase_render(s)
-        if self.cfg.assoc:
+        if self.cfg.assoc or self.cfg.culled_beside:
             self.side.wait_stream(s)
+            self.phase_adam_culled(self.side)  # beside the backward render
             self.phase_assoc(self.side)
         self.phase_backward(s)
         self.phase_project_backward(s)
@@ -312,7 +323,7 @@ class Agent:
         v.d_sil = None
         v.grad2d = B._p(fb.bwd_ws)
         v.l1 = ctypes.pointer(self.cl1)
-        v.tile_order = B._p(fb.tile_order)
+        v.schedule = B._p(fb.schedule)
         return v
 
     # -- pruning -----------------------------------------------------------------

@@ -105,7 +105,7 @@ class Alignment:
         v.d_depth = B._p(self.g_depth[k])
         v.d_sil = None
         v.grad2d = B._p(fb.bwd_ws)
-        v.tile_order = B._p(fb.tile_order)
+        v.schedule = B._p(fb.schedule)
 
     def size_capacity(self, headroom=1.5):
         """One host read per view to size the duplicate buffers."""

@@ -57,7 +57,7 @@ class CL1(ctypes.Structure):
 class CView(ctypes.Structure):
     _fields_ = [("proj", CProjected), ("rgb", _c_p), ("n", _c_i64), ("vals", _c_p), ("ranges", _c_p),
                 ("cam", CCamera), ("bg", ctypes.c_float * 3), ("image", CImage), ("d_rgb", _c_p), ("d_depth", _c_p),
-                ("d_sil", _c_p), ("grad2d", _c_p), ("l1", ctypes.POINTER(CL1)), ("tile_order", _c_p)]
+                ("d_sil", _c_p), ("grad2d", _c_p), ("l1", ctypes.POINTER(CL1)), ("schedule", _c_p)]
 
 
 class CColumn(ctypes.Structure):
@@ -84,11 +84,13 @@ _SIGS = {
     "splat_bin_sort_static_scratch_bytes": ([], _c_sz),
     "splat_bin_sort_static": ([_c_p, _c_i64, _c_p, _c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_render_fwd": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
-    "splat_render_fwd_l1": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_render_fwd_l1": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_tile_schedule_size": ([_c_i32], _c_sz),
     "splat_render_bwd_workspace_size": ([_c_i64], _c_sz),
     "splat_render_bwd": ([_c_p] * 16 + [_c_sz, _c_p], ctypes.c_int),
     "splat_project_bwd": ([_c_p] * 8 + [_c_p], ctypes.c_int),
-    "splat_project_bwd_adam": ([_c_p] * 8 + [_c_f, _c_f, _c_f, _c_p, _c_p, _c_p], ctypes.c_int),
+    "splat_project_bwd_adam": ([_c_p] * 8 + [_c_f, _c_f, _c_f, _c_p, _c_i32, _c_p, _c_p], ctypes.c_int),
+    "splat_adam_culled": ([_c_p] * 5 + [_c_f, _c_f, _c_f, _c_p, _c_p], ctypes.c_int),
     "splat_batch_workspace_size": ([], _c_sz),
     "splat_render_fwd_batch": ([_c_p, _c_i32, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
     "splat_render_bwd_batch": ([_c_p, _c_i32, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
@@ -224,10 +226,10 @@ def splat_bin_sort_workspace_size(n, capacity, n_tiles) -> int:
 
 
 def splat_bin_sort(proj: CProjected, n, cam: CCamera, keys, vals, capacity, k_dev, ranges, status, ws, stream=None,
-                   tile_order=None):
+                   schedule=None):
     _check("splat_bin_sort", load().splat_bin_sort(
         ctypes.byref(proj), n, ctypes.byref(cam), _p(keys), _p(vals), capacity, _p(k_dev), _p(ranges),
-        _p(tile_order), _p(status), _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
+        _p(schedule), _p(status), _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def splat_bin_sort_static_scratch_bytes() -> int:
@@ -253,12 +255,19 @@ def l1_struct(t_rgb, t_depth, w_rgb, w_depth, d_rgb, d_depth, loss) -> CL1:
     return CL1(_p(t_rgb), _p(t_depth), w_rgb, w_depth, _p(d_rgb), _p(d_depth), _p(loss))
 
 
-def splat_render_fwd_l1(proj: CProjected, rgb, n, vals, ranges, cam: CCamera, bg, image: CImage, l1: CL1,
-                        stream=None):
+def splat_render_fwd_l1(proj: CProjected, rgb, n, vals, ranges, cam: CCamera, bg, image: CImage, l1,
+                        stream=None, schedule=None):
     bgc = (ctypes.c_float * 3)(*[float(x) for x in bg])
     _check("splat_render_fwd_l1", load().splat_render_fwd_l1(
         ctypes.byref(proj), _p(rgb), n, _p(vals), _p(ranges), ctypes.byref(cam), bgc, ctypes.byref(image),
-        ctypes.byref(l1), _stream(stream)))
+        None if l1 is None else ctypes.byref(l1), _p(schedule), _stream(stream)))
+
+
+SPLAT_SCHEDULE_BUCKETS = 128
+
+
+def splat_tile_schedule_size(n_tiles) -> int:
+    return int(load(require_cuda=False).splat_tile_schedule_size(n_tiles))
 
 
 def splat_render_bwd_workspace_size(n) -> int:
@@ -266,12 +275,12 @@ def splat_render_bwd_workspace_size(n) -> int:
 
 
 def splat_render_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, vals, ranges, image: CImage, bg,
-                     d_rgb, d_depth, d_sil, grads: CGaussiansGrad, d_pose, d2d, ws, stream=None, tile_order=None):
+                     d_rgb, d_depth, d_sil, grads: CGaussiansGrad, d_pose, d2d, ws, stream=None, schedule=None):
     bgc = (ctypes.c_float * 3)(*[float(x) for x in bg])
     wsb = 0 if ws is None else ws.numel() * ws.element_size()
     _check("splat_render_bwd", load().splat_render_bwd(
         ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(vals), _p(ranges),
-        _p(tile_order), ctypes.byref(image), bgc, _p(d_rgb), _p(d_depth), _p(d_sil), None if grads is None else ctypes.byref(grads),
+        _p(schedule), ctypes.byref(image), bgc, _p(d_rgb), _p(d_depth), _p(d_sil), None if grads is None else ctypes.byref(grads),
         _p(d_pose), _p(d2d), _p(ws), wsb, _stream(stream)))
 
 
@@ -283,13 +292,24 @@ def splat_project_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c
 
 
 def splat_project_bwd_adam(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, grad2d, m: CGaussiansGrad,
-                           v: CGaussiansGrad, lr, step, d_pose, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+                           v: CGaussiansGrad, lr, step, d_pose, beta1=0.9, beta2=0.999, eps=1e-15, stream=None,
+                           culled=True):
     """`gaussians`' arrays are updated in place; `lr`: 5 step sizes (mean,
-    log_scale, quat, opacity_logit, rgb); `step`: device int32[1] (t >= 1)."""
+    log_scale, quat, opacity_logit, rgb); `step`: device int32[1] (t >= 1);
+    `culled`: also step the culled Gaussians (else splat_adam_culled does)."""
     lrc = (ctypes.c_float * 5)(*[float(x) for x in lr])
     _check("splat_project_bwd_adam", load().splat_project_bwd_adam(
         ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(grad2d), ctypes.byref(m),
-        ctypes.byref(v), lrc, beta1, beta2, eps, _p(step), _p(d_pose), _stream(stream)))
+        ctypes.byref(v), lrc, beta1, beta2, eps, _p(step), 1 if culled else 0, _p(d_pose), _stream(stream)))
+
+
+def splat_adam_culled(gaussians: CGaussians, radius, m: CGaussiansGrad, v: CGaussiansGrad, lr, step, beta1=0.9,
+                      beta2=0.999, eps=1e-15, stream=None):
+    """The culled Gaussians' zero-gradient Adam step (see the header)."""
+    lrc = (ctypes.c_float * 5)(*[float(x) for x in lr])
+    _check("splat_adam_culled", load().splat_adam_culled(
+        ctypes.byref(gaussians), _p(radius), ctypes.byref(m), ctypes.byref(v), lrc, beta1, beta2, eps, _p(step),
+        _stream(stream)))
 
 
 def splat_batch_workspace_size() -> int:

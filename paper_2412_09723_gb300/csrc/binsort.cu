@@ -503,28 +503,16 @@ __device__ __forceinline__ bool row_span(const uint16_t* __restrict__ spans, uin
   return row_members(tile_test(xo, co), r, ty, x0, x1);
 }
 
-// Heavy-first order of the tiles (optional output): a counting sort of the
-// tiles on their list length, descending, in buckets of an eighth of an octave
-// (the exponent and three mantissa bits of the length as a float); the order
-// inside a bucket is arbitrary.  A persistent launch that takes tiles in this
-// order starts the long lists first and ends on short ones.
-constexpr int kOrderBuckets = 128;
-
-__device__ __forceinline__ int order_bucket(uint32_t c) {
-  if (c == 0u) return 0;
-  const int b = (int)((__float_as_uint((float)c) >> 20) - (127u << 3)) + 1;  // 1 + 8 log2(c), quantised
-  return b < kOrderBuckets ? b : kOrderBuckets - 1;
-}
-
 // One CTA: prefix sums along the rows of the difference grid (gw = tiles_x + 1
 // cells per row, kDiffStride ints apart) -> per-tile counts; exclusive scan over tiles -> ranges
-// (clamped to the capacity) and bucket cursors; K and the status; the
-// heavy-first tile order when `order` is not null.
+// (clamped to the capacity) and bucket cursors; K and the status; the bucket
+// counts of a tile schedule (filled by the forward render) set to zero when
+// `schedule` is not null.
 __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff, int tiles_x, int tiles_y,
                                                          const unsigned long long* __restrict__ k_total,
                                                          int64_t capacity, uint2* __restrict__ ranges,
                                                          uint32_t* __restrict__ cursor, int64_t* __restrict__ k_dev,
-                                                         int32_t* __restrict__ status, uint32_t* __restrict__ order) {
+                                                         int32_t* __restrict__ status, uint32_t* __restrict__ schedule) {
   __shared__ uint32_t sh[33];
   __shared__ int s_grid[kScanGridSmem];
   const int gw = tiles_x + 1;
@@ -570,41 +558,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
     *k_dev = k;
     if (k > capacity) raise_status(status, SPLAT_ECAPACITY);
   }
-  if (!order) return;
-  __shared__ uint32_t hist[kOrderBuckets];
-  if (threadIdx.x < kOrderBuckets) hist[threadIdx.x] = 0u;
-  __syncthreads();  // the ranges written above are visible to the block from here on
-  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-    const uint2 r = ranges[t];
-    atomicAdd(&hist[order_bucket(r.y - r.x)], 1u);
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {  // exclusive starts, heaviest bucket first: lane l takes buckets 127-4l .. 124-4l
-    const int lane = threadIdx.x;
-    uint32_t h[4], tot = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      h[k] = hist[kOrderBuckets - 1 - 4 * lane - k];
-      tot += h[k];
-    }
-    uint32_t incl = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    uint32_t run = incl - tot;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      hist[kOrderBuckets - 1 - 4 * lane - k] = run;
-      run += h[k];
-    }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) {
-    const uint2 r = ranges[t];
-    order[atomicAdd(&hist[order_bucket(r.y - r.x)], 1u)] = (uint32_t)t;
-  }
+  if (schedule)
+    for (int b = threadIdx.x; b < SPLAT_SCHEDULE_BUCKETS; b += blockDim.x) schedule[b] = 0u;
 }
 
 // Every visible Gaussian drops key (depth bits << 32 | id) into the bucket of
@@ -792,7 +747,7 @@ extern "C" size_t splat_bin_sort_workspace_size(int64_t n, int64_t capacity, int
 }
 
 extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const splat_camera* cam, uint64_t* keys,
-                              uint32_t* vals, int64_t capacity, int64_t* k_dev, uint32_t* ranges, uint32_t* tile_order,
+                              uint32_t* vals, int64_t capacity, int64_t* k_dev, uint32_t* ranges, uint32_t* schedule,
                               int32_t* status, void* ws, size_t ws_bytes, splat_stream_t stream) {
   if (!proj || !cam || !vals || !k_dev || !ranges || !status || !ws)
     return fail(SPLAT_EINVAL, "splat_bin_sort: null argument");
@@ -841,7 +796,7 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
   SPLAT_LAUNCH("tile_scan_kernel", s,
                tile_scan_kernel<<<1, 1024, 0, s>>>(w.diff, ck.tiles_x, ck.tiles_y, w.k_total, capacity,
                                                    reinterpret_cast<uint2*>(ranges), w.cursor, k_dev, status,
-                                                   tile_order));
+                                                   schedule));
   int rc = check_launch("tile_scan_kernel");
   if (rc || n == 0 || capacity == 0) return rc;
   int sms = 152;

@@ -88,9 +88,12 @@ int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, c
 // Projection adjoint with the map's Adam step in the same pass: every
 // Gaussian's parameters move by Adam with the gradient the adjoint gives it
 // (0 for a culled one); nothing is written to gradient arrays.
+// culled: the same launch also takes the culled Gaussians' zero-gradient step
+// (else launch_adam_culled does, e.g. on another stream).
 int launch_project_bwd_adam(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
                             const int32_t* radius, const float* g2, int stride, const AdamMapK& adam, float* d_pose,
-                            cudaStream_t s);
+                            bool culled, cudaStream_t s);
+int launch_adam_culled(int64_t n, const int32_t* radius, const AdamMapK& adam, cudaStream_t s);
 
 // L1 terms: grgb = sc sign(rgb - trgb), gdepth = sd sign(depth - tdepth) (overwritten),
 // loss += sc sum|rgb - trgb| + sd sum|depth - tdepth|.

@@ -594,15 +594,34 @@ int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, c
   return check_launch("project_fwd_kernel");
 }
 
+// The culled Gaussians' zero-gradient step alone (its own launch).
+__global__ void __launch_bounds__(kPbThreads) adam_culled_kernel(int64_t n, const int32_t* __restrict__ radius,
+                                                                 AdamMapK A) {
+  const float ibc1 = 1.0f / bias_correction(A.b1, A.step);
+  const float ibc2 = 1.0f / bias_correction(A.b2, A.step);
+  culled_units(A, radius, n, (int64_t)blockIdx.x * kPbThreads + threadIdx.x, (int64_t)gridDim.x * kPbThreads, ibc1,
+               ibc2);
+}
+
+int launch_adam_culled(int64_t n, const int32_t* radius, const AdamMapK& adam, cudaStream_t s) {
+  if (n == 0) return SPLAT_OK;
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t units = (14 * n + 3) / 4;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(units, kPbThreads * kCulledUnroll), 4 * sms));
+  SPLAT_LAUNCH("adam_culled_kernel", s, adam_culled_kernel<<<grid, kPbThreads, 0, s>>>(n, radius, adam));
+  return check_launch("adam_culled_kernel");
+}
+
 int launch_project_bwd_adam(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
                             const int32_t* radius, const float* g2, int stride, const AdamMapK& adam, float* d_pose,
-                            cudaStream_t s) {
+                            bool culled, cudaStream_t s) {
   if (g.n == 0) return SPLAT_OK;
   int sms = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // both parts resident at once (two CTAs per SM): one for the kept Gaussians' adjoint, one for the culled
-  const int kept_blocks = (int)std::min<int64_t>(ceil_div(g.n, kPbThreads), sms);
-  const int grid = kept_blocks + sms;
+  const int kept_blocks = (int)std::min<int64_t>(ceil_div(g.n, kPbThreads), culled ? sms : 2 * sms);
+  const int grid = kept_blocks + (culled ? sms : 0);
   SPLAT_LAUNCH("project_bwd_adam_kernel", s,
                project_bwd_adam_kernel<<<grid, kPbThreads, 0, s>>>(g, cam, w2c, conic, radius, g2, stride, adam,
                                                                    d_pose, kept_blocks));

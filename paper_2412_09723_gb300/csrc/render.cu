@@ -3,9 +3,9 @@
 // its back-to-front adjoint, for one view per launch or for several views
 // (agents of uneven map sizes, Sec. 3.6) in one persistent launch.
 //
-// Forward: 128 threads with 2 pixels each ((x, y) and (x, y + 2); a warp
-// covers 16 x 4 pixels), the pair's arithmetic in packed single-precision
-// pairs.  The tile's list is staged through shared memory in batches of BATCH
+// Forward: 128 threads with 2 pixels each ((x, y) and (x, y + 4); a warp
+// covers one 8 x 8 quadrant of the tile), the pair's arithmetic in packed
+// single-precision pairs.  The tile's list is staged through shared memory in batches of BATCH
 // Gaussians (position / depth / opacity, the quadratic form's coefficients
 // A = -a/2, B = -b, C = -c/2 with the exponent cut, colour, id) and every
 // thread walks the batch in order.  A pair whose exponent lies below the
@@ -14,15 +14,15 @@
 // result.  A tile ends as soon as all of its pixels have reached the
 // transmittance stop.  No atomics.
 //
-// Backward: 128 threads with 2 pixels each ((x, y) and (x, y + 2); a warp
-// covers 16 x 4 pixels), again in packed pairs.  Every pixel starts from its
-// final transmittance and last contributor, walks the list back to front and
-// recovers
-// T_i = T_{i+1} / (1 - alpha_i).  With the pixel's upstream gradients folded
+// Backward: the same pixels per thread and warp, again in packed pairs.  The
+// list of a tile is walked in two independent parts (below): the back part
+// starts from each pixel's final transmittance and last contributor, walks
+// back to front and recovers T_i = T_{i+1} / (1 - alpha_i); the front part
+// walks front to back from T_0 = 1.  With the pixel's upstream gradients folded
 // into one scalar per Gaussian, P_i = gC.c_i + gD z_i + gS, and the weights
 // w_j = alpha_j T_j, every later weight carries a factor (1 - alpha_i), so
 // dL/dalpha_i = T_i P_i - [sum_{j>i} w_j P_j + (gC.bg) T_final] / (1 - alpha_i);
-// the bracket is one running sum per pixel (started at (gC.bg) T_final).
+// the bracket is one running sum per pixel.
 // Per Gaussian and warp, ten sums (five moments of dL/dpower -- sum dp dx,
 // dp dy, dp dx^2, dp dx dy, dp dy^2 -- whose conic terms are applied once per
 // Gaussian, plus d opacity, d rgb, d depth) are reduced through a per-warp
@@ -86,7 +86,7 @@ struct ViewK {
   const float* d_sil;
   float* g2;
   LossK l1;
-  const uint32_t* order;  // tiles in the order the backward takes them, or null (natural order)
+  uint32_t* sched;  // tile schedule (filled by the forward, read by the backward) or null
 };
 
 struct ViewTable {
@@ -96,7 +96,8 @@ struct ViewTable {
 };
 
 // Shared-memory staging of one batch of Gaussians.
-constexpr int kMaxWarps = 8;  // warps of a tile CTA (forward and backward: 4 of 4 rows)
+constexpr int kMaxWarps = 4;  // warps of a tile CTA (forward and backward), one per 8 x 8 quadrant
+constexpr int kQuad = 8;
 
 struct StagePtrs {
   float4* xyzo;
@@ -110,7 +111,7 @@ struct Stage {
   float4 xyzo[BATCH];
   float4 quad[BATCH];  // A = -a/2, B = -b, C = -c/2, exponent cut
   float4 cid[BATCH];   // colour r, g, b and the Gaussian's id (bits of .w)
-  uint8_t wmask[BATCH];              // warps whose pixel rows the Gaussian can reach
+  uint8_t wmask[BATCH];              // warps whose quadrant the Gaussian can reach
   uint8_t wlist[kMaxWarps][BATCH];   // per warp: the staged positions it visits, ascending
 };
 
@@ -134,43 +135,48 @@ __device__ __forceinline__ bool ellipse_meets_rect(float dxa, float dxb, float d
   return m <= K;
 }
 
-// Bit w set when the pixel centres of warp w (rows_per_warp consecutive rows
-// of the tile, all 16 columns) can lie on the ellipse where the exponent
-// reaches the Gaussian's cut (a dx^2 + 2 b dx dy + c dy^2 <= K, K = -2 cut):
-// outside it every pixel skips the Gaussian, so a warp whose bit is clear need
-// not look at it.  The bounding box of the ellipse (half-widths
-// sqrt(K c / det), sqrt(K a / det), det = ac - b^2) limits the candidate rows;
-// with EXACT (the backward pass, where a visit costs most) each candidate
-// warp's rectangle of pixel centres is then tested against the ellipse itself.
-// K is widened by 0.2% + 1e-3 and the box by 0.1% + 0.01 px, far beyond the
-// rounding of the per-pixel test, so no pixel that would take the Gaussian is
-// ever left out.
+// Bit w set when the pixel centres of warp w (the 8 x 8 quadrant
+// (8 (w & 1), 8 (w >> 1)) of the tile) can lie on the ellipse where the
+// exponent reaches the Gaussian's cut (a dx^2 + 2 b dx dy + c dy^2 <= K,
+// K = -2 cut): outside it every pixel skips the Gaussian, so a warp whose bit
+// is clear need not look at it.  The bounding box of the ellipse (half-widths
+// sqrt(K c / det), sqrt(K a / det), det = ac - b^2) gives the candidate
+// columns and rows, so the candidate quadrants; with EXACT (the backward pass,
+// where a visit costs most) each candidate quadrant's rectangle of pixel
+// centres is then tested against the ellipse itself.  K is widened by 0.2% +
+// 1e-3 and the box by 0.1% + 0.01 px, far beyond the rounding of the
+// per-pixel test, so no pixel that would take the Gaussian is ever left out.
 template <bool EXACT>
-__device__ __forceinline__ uint8_t warp_mask(const float4 xo, const float4 co, int tx0, int ty0, int rows_per_warp) {
+__device__ __forceinline__ uint8_t warp_mask(const float4 xo, const float4 co, int tx0, int ty0) {
   const float K = -2.0f * co.w;
   if (!(K > 0.0f)) return 0;  // the cut is above 1: no pixel passes
   const float a = co.x, b = co.y, c = co.z;
   const float det = a * c - b * b;
-  if (!(det > 0.0f && a > 0.0f && c > 0.0f)) return 0xff;
+  if (!(det > 0.0f && a > 0.0f && c > 0.0f)) return 0xf;
   const float sk = K / det;
   const float ex = sqrtf(sk * c) * 1.001f + 0.01f;
   const float ey = sqrtf(sk * a) * 1.001f + 0.01f;
-  if (!(ex < 1e30f && ey < 1e30f)) return 0xff;
-  const float xa = fmaxf((float)tx0 + 0.5f, xo.x - ex), xb = fminf((float)tx0 + 15.5f, xo.x + ex);
-  if (xa > xb) return 0;
-  const float lo = fmaxf(0.0f, ceilf(xo.y - ey - (float)ty0 - 0.5f));
-  const float hi = fminf(15.0f, floorf(xo.y + ey - (float)ty0 - 0.5f));
-  if (lo > hi) return 0;
-  const int r0 = (int)lo, r1 = (int)hi;
-  const int w0 = r0 / rows_per_warp, w1 = r1 / rows_per_warp;
-  if (!EXACT) return (uint8_t)(((2u << w1) - 1u) & ~((1u << w0) - 1u));
+  if (!(ex < 1e30f && ey < 1e30f)) return 0xf;
+  // pixel centres tx0 + col + 0.5 inside [x - ex, x + ex], same in y
+  const float cl = fmaxf(0.0f, ceilf(xo.x - ex - (float)tx0 - 0.5f));
+  const float ch = fminf(15.0f, floorf(xo.x + ex - (float)tx0 - 0.5f));
+  const float rl = fmaxf(0.0f, ceilf(xo.y - ey - (float)ty0 - 0.5f));
+  const float rh = fminf(15.0f, floorf(xo.y + ey - (float)ty0 - 0.5f));
+  if (cl > ch || rl > rh) return 0;
+  const int c0 = (int)cl, c1 = (int)ch, r0 = (int)rl, r1 = (int)rh;
+  const unsigned cols = (c0 < kQuad ? 1u : 0u) | (c1 >= kQuad ? 2u : 0u);
+  const unsigned rows = (r0 < kQuad ? 1u : 0u) | (r1 >= kQuad ? 2u : 0u);
+  const uint8_t box = (uint8_t)(((rows & 1u) ? cols : 0u) | ((rows & 2u) ? cols << 2 : 0u));
+  if (!EXACT) return box;
   const float Kt = K * 1.002f + 1e-3f;
   const float ba = __fdividef(b, a), bc = __fdividef(b, c);
   uint8_t mask = 0;
 #pragma unroll 1
-  for (int w = w0; w <= w1; ++w) {
-    const int ra = max(r0, w * rows_per_warp), rb = min(r1, w * rows_per_warp + rows_per_warp - 1);
-    const float ya = (float)(ty0 + ra) + 0.5f, yb = (float)(ty0 + rb) + 0.5f;
+  for (int w = 0; w < 4; ++w) {
+    if (!((box >> w) & 1)) continue;
+    const int qx = kQuad * (w & 1), qy = kQuad * (w >> 1);
+    const float xa = (float)(tx0 + max(c0, qx)) + 0.5f, xb = (float)(tx0 + min(c1, qx + kQuad - 1)) + 0.5f;
+    const float ya = (float)(ty0 + max(r0, qy)) + 0.5f, yb = (float)(ty0 + min(r1, qy + kQuad - 1)) + 0.5f;
     if (ellipse_meets_rect(xa - xo.x, xb - xo.x, ya - xo.y, yb - xo.y, a, b, c, ba, bc, Kt))
       mask |= (uint8_t)(1u << w);
   }
@@ -178,15 +184,14 @@ __device__ __forceinline__ uint8_t warp_mask(const float4 xo, const float4 co, i
 }
 
 template <bool EXACT>
-__device__ __forceinline__ void stage_one(const ViewK& V, uint32_t g, int i, StagePtrs p, int tx0, int ty0,
-                                          int rows_per_warp) {
+__device__ __forceinline__ void stage_one(const ViewK& V, uint32_t g, int i, StagePtrs p, int tx0, int ty0) {
   const float4 co = V.conic[g];
   const float4 xo = V.xyzo[g];
   p.xyzo[i] = xo;
   p.quad[i] = make_float4(-0.5f * co.x, -co.y, -0.5f * co.z, co.w);
   p.cid[i] = make_float4(V.rgb[3 * (size_t)g + 0], V.rgb[3 * (size_t)g + 1], V.rgb[3 * (size_t)g + 2],
                          __int_as_float((int32_t)g));
-  p.wmask[i] = warp_mask<EXACT>(xo, co, tx0, ty0, rows_per_warp);
+  p.wmask[i] = warp_mask<EXACT>(xo, co, tx0, ty0);
 }
 
 // The positions (ascending) of the cnt staged Gaussians whose mask has this
@@ -209,7 +214,7 @@ __device__ __forceinline__ int build_warp_list(const uint8_t* wmask, uint8_t* li
 // ----------------------------------------------------------------------------
 // Forward
 // ----------------------------------------------------------------------------
-// Two pixels per thread, (x, y) and (x, y + 2), so one staged Gaussian's loads
+// Two pixels per thread, (x, y) and (x, y + 4), so one staged Gaussian's loads
 // and the shared dx serve both, and their arithmetic runs as packed pairs
 // (__fadd2_rn, __fmul2_rn, __ffma2_rn: two IEEE single-precision operations
 // each, rounded exactly as the scalar ones, so every value is bit for bit the
@@ -298,12 +303,13 @@ __device__ __forceinline__ void composite_step2(FwdPix& q, const float4 xo, cons
   q.used[1] += in1;
 }
 
-// Pixel p (0 or 1) of thread t (forward and backward): warp w covers rows 4w .. 4w + 3
-// (lanes 0-15 rows 4w and 4w + 2, lanes 16-31 rows 4w + 1 and 4w + 3).
+// Pixel p (0 or 1) of thread t (forward and backward): warp w covers the 8 x 8
+// quadrant at (8 (w & 1), 8 (w >> 1)); lane l takes column l & 7 of it and rows
+// l >> 3 and (l >> 3) + 4.
 __device__ __forceinline__ void pair_pixel(int t, int p, int& lx, int& ly) {
   const int lane = t & 31, warp = t >> 5;
-  lx = lane & 15;
-  ly = 4 * warp + (lane >> 4) + 2 * p;
+  lx = kQuad * (warp & 1) + (lane & 7);
+  ly = kQuad * (warp >> 1) + (lane >> 3) + 4 * p;
 }
 
 // |x - t| and the subgradient sc sign(x - t) (sign(0) = 0), as splat_loss_l1.
@@ -311,6 +317,57 @@ __device__ __forceinline__ float l1_px(float x, float t, float sc, float* g) {
   const float e = x - t;
   *g = e > 0.f ? sc : (e < 0.f ? -sc : 0.f);
   return fabsf(e);
+}
+
+// Tile schedule: bucket 1 + floor(8 log2 S) of a tile's summed contributor
+// counts S (the exponent and three mantissa bits of S as a float), 0 for S = 0.
+__device__ __forceinline__ int schedule_bucket(uint32_t S) {
+  if (S == 0u) return 0;
+  const int b = (int)((__float_as_uint((float)S) >> 20) - (127u << 3)) + 1;
+  return b < SPLAT_SCHEDULE_BUCKETS ? b : SPLAT_SCHEDULE_BUCKETS - 1;
+}
+
+// The k-th tile of a schedule, heaviest bucket first (called by one whole
+// warp; k itself when the counts do not add up to the number of tiles).
+__device__ __forceinline__ int schedule_tile(const uint32_t* sched, int n_tiles, int k) {
+  const int lane = threadIdx.x & 31;
+  uint32_t c[4], tot = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    c[j] = sched[SPLAT_SCHEDULE_BUCKETS - 1 - 4 * lane - j];
+    tot += c[j];
+  }
+  uint32_t incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  // a schedule that does not hold every tile exactly once (filled twice since
+  // it was cleared, or never) leaves the natural order
+  if (__shfl_sync(0xffffffffu, incl, 31) != (uint32_t)n_tiles) return k;
+  const uint32_t excl = incl - tot, uk = (uint32_t)k;
+  const unsigned hit = __ballot_sync(0xffffffffu, excl <= uk && uk < incl);
+  int tile = k;
+  if (hit) {
+    const int src = __ffs(hit) - 1;
+    int t = -1;
+    if (lane == src) {
+      uint32_t run = excl;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (t < 0 && uk < run + c[j]) {
+          const uint32_t slot = uk - run;
+          const int b = SPLAT_SCHEDULE_BUCKETS - 1 - 4 * lane - j;
+          if (slot < (uint32_t)n_tiles) t = (int)sched[SPLAT_SCHEDULE_BUCKETS + (size_t)b * n_tiles + slot];
+        }
+        run += c[j];
+      }
+    }
+    t = __shfl_sync(0xffffffffu, t, src);
+    if (t >= 0 && t < n_tiles) tile = t;
+  }
+  return tile;
 }
 
 template <int BATCH>
@@ -338,7 +395,7 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
     if (__syncthreads_count(q.done[0] && q.done[1]) == kFwdThreads) break;
     const int cnt = (int)min((uint32_t)BATCH, rg.y - start);
     for (int i = threadIdx.x; i < cnt; i += kFwdThreads)
-      stage_one<false>(V, V.vals[start + i], i, sp, tx * kTile, ty * kTile, 4);
+      stage_one<false>(V, V.vals[start + i], i, sp, tx * kTile, ty * kTile);
     __syncthreads();
     const int32_t base = (int32_t)(start - rg.x);
     const int nl = build_warp_list(sm.wmask, sm.wlist[warp], cnt, warp);
@@ -374,17 +431,34 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
       acc_d += l1_px(d, L.t_depth[i], L.sd, &L.g_depth[i]);
     }
   }
-  if (L.t_rgb) {  // the tile's share of the loss: warp sums, then one atomic per CTA
+  // per tile, one block reduction of the loss terms and the contributor
+  // counts: warp sums, then thread 0 adds the warps' sums, makes one loss
+  // atomic and puts the tile into its schedule bucket
+  if (L.t_rgb || V.sched) {
     float acc = L.sc * acc_c + L.sd * acc_d;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = acc;
+    const unsigned S = __reduce_add_sync(0xffffffffu, (unsigned)(q.last[0] + q.last[1]));
+    if ((threadIdx.x & 31) == 0) {
+      s_loss[threadIdx.x >> 5] = acc;
+      s_loss[kFwdThreads / 32 + (threadIdx.x >> 5)] = __uint_as_float(S);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       float t = 0.f;
+      unsigned St = 0u;
 #pragma unroll
-      for (int w = 0; w < kFwdThreads / 32; ++w) t += s_loss[w];
-      if (L.loss) atomicAdd(L.loss, t);
+      for (int w = 0; w < kFwdThreads / 32; ++w) {
+        t += s_loss[w];
+        St += __float_as_uint(s_loss[kFwdThreads / 32 + w]);
+      }
+      if (L.t_rgb && L.loss) atomicAdd(L.loss, t);
+      if (V.sched) {
+        const int nt = cam.tiles_x * cam.tiles_y;
+        const int b = schedule_bucket(St);
+        const unsigned slot = atomicAdd(&V.sched[b], 1u);
+        if (slot < (unsigned)nt) V.sched[SPLAT_SCHEDULE_BUCKETS + (size_t)b * nt + slot] = (uint32_t)tile;
+      }
     }
   }
 }
@@ -392,7 +466,7 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
 template <int BATCH>
 __global__ void __launch_bounds__(kFwdThreads, 8) render_fwd_kernel(ViewK V) {
   __shared__ Stage<BATCH> sm;
-  __shared__ float s_loss[kFwdThreads / 32];
+  __shared__ float s_loss[2 * kFwdThreads / 32];
   fwd_tile<BATCH>(V, blockIdx.x, sm, s_loss);
 }
 
@@ -414,7 +488,7 @@ __device__ __forceinline__ int next_item(int* counter, int* s_item) {
 template <int BATCH>
 __global__ void __launch_bounds__(kFwdThreads, 8) render_fwd_persistent(ViewTable T, int total, int* counter) {
   __shared__ Stage<BATCH> sm;
-  __shared__ float s_loss[kFwdThreads / 32];
+  __shared__ float s_loss[2 * kFwdThreads / 32];
   __shared__ int s_item;
   for (int item = next_item(counter, &s_item); item < total; item = next_item(counter, &s_item)) {
     int tile;
@@ -442,7 +516,7 @@ __global__ void __launch_bounds__(kFwdThreads, 8) render_fwd_persistent(ViewTabl
 // the subtraction R - w P loses nothing that matters) and the back part the
 // late ones.
 //
-// The thread's two pixels (x, y) and (x, y + 2) share x, and their arithmetic
+// The thread's two pixels (x, y) and (x, y + 4) share x, and their arithmetic
 // runs in packed single-precision pairs.  Q holds Q (back part) or R (front).
 struct BwdPair {
   float fx;
@@ -633,7 +707,7 @@ __device__ __forceinline__ void bwd_part(const ViewK& V, int tile, BwdShared<BAT
     const int cnt = FRONT ? min(BATCH, hi - start) : hi - b * BATCH - start;
     __syncthreads();
     for (int i = threadIdx.x; i < cnt; i += NT)
-      stage_one<true>(V, V.vals[rg.x + start + i], i, sp, tx * kTile, ty * kTile, 4);
+      stage_one<true>(V, V.vals[rg.x + start + i], i, sp, tx * kTile, ty * kTile);
     for (int i = threadIdx.x; i < BATCH * kAccStride; i += NT) sm.acc[i] = 0.f;
     __syncthreads();
     const int nl = build_warp_list(sm.st.wmask, sm.st.wlist[warp], cnt, warp);
@@ -684,20 +758,32 @@ __device__ __forceinline__ void bwd_part(const ViewK& V, int tile, BwdShared<BAT
 }
 
 // Work item -> (view, tile, part): items 2 t and 2 t + 1 are the front and back
-// parts of the t-th tile over all views (of the view's heavy-first order when
-// it has one).
+// parts of the t-th tile over all views (the t-th of the view's schedule,
+// heaviest first, when it has one).
 template <int BATCH>
 __global__ void __launch_bounds__(kBwdThreads, 8) render_bwd_persistent(ViewTable T, int total, int* counter) {
   __shared__ BwdShared<BATCH> sm;
-  __shared__ int s_item;
-  for (int item = next_item(counter, &s_item); item < 2 * total; item = next_item(counter, &s_item)) {
-    int tile;
-    const int v = view_of(T, item >> 1, tile);
-    if (T.v[v].order) tile = (int)T.v[v].order[tile];
+  __shared__ int s_item, s_view, s_tile;
+  for (;;) {
+    __syncthreads();  // every thread is done with the previous item's shared memory
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= 2 * total) break;
+    if (threadIdx.x < 32) {  // warp 0 resolves the item's view and tile
+      int tile;
+      const int v = view_of(T, item >> 1, tile);
+      if (T.v[v].sched) tile = schedule_tile(T.v[v].sched, T.v[v].cam.tiles_x * T.v[v].cam.tiles_y, tile);
+      if (threadIdx.x == 0) {
+        s_view = v;
+        s_tile = tile;
+      }
+    }
+    __syncthreads();
     if (item & 1)
-      bwd_part<BATCH, false>(T.v[v], tile, sm);
+      bwd_part<BATCH, false>(T.v[s_view], s_tile, sm);
     else
-      bwd_part<BATCH, true>(T.v[v], tile, sm);
+      bwd_part<BATCH, true>(T.v[s_view], s_tile, sm);
   }
 }
 
@@ -730,7 +816,7 @@ static ViewK make_view(const splat_projected& proj, const float* rgb, const uint
   v.d_rgb = v.d_depth = v.d_sil = nullptr;
   v.g2 = nullptr;
   v.l1 = LossK{nullptr, nullptr, 0.f, 0.f, nullptr, nullptr, nullptr};
-  v.order = nullptr;
+  v.sched = nullptr;
   return v;
 }
 
@@ -756,7 +842,7 @@ using namespace splat;
 
 static int render_fwd_one(const splat_projected* proj, const float* rgb, int64_t n, const uint32_t* vals,
                           const uint32_t* ranges, const splat_camera* cam, const float* bg, const splat_image* out,
-                          const splat_l1* l1, splat_stream_t stream, const char* who) {
+                          const splat_l1* l1, uint32_t* schedule, splat_stream_t stream, const char* who) {
   int rc = check_proj(proj, n, who);
   if (rc) return rc;
   if ((n > 0 && !rgb) || !vals || !ranges || !cam || !bg || !out || !image_ok(*out))
@@ -764,6 +850,7 @@ static int render_fwd_one(const splat_projected* proj, const float* rgb, int64_t
   if (n < 0 || cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "%s: bad sizes", who);
   ViewK v = make_view(*proj, rgb, vals, ranges, *cam, bg, *out);
   if ((rc = set_loss(v, l1, who))) return rc;
+  v.sched = schedule;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   SPLAT_LAUNCH("render_fwd_kernel", s,
                render_fwd_kernel<256><<<v.cam.tiles_x * v.cam.tiles_y, kFwdThreads, 0, s>>>(v));
@@ -773,14 +860,18 @@ static int render_fwd_one(const splat_projected* proj, const float* rgb, int64_t
 extern "C" int splat_render_fwd(const splat_projected* proj, const float* rgb, int64_t n, const uint32_t* vals,
                                 const uint32_t* ranges, const splat_camera* cam, const float* bg,
                                 const splat_image* out, splat_stream_t stream) {
-  return render_fwd_one(proj, rgb, n, vals, ranges, cam, bg, out, nullptr, stream, "splat_render_fwd");
+  return render_fwd_one(proj, rgb, n, vals, ranges, cam, bg, out, nullptr, nullptr, stream, "splat_render_fwd");
 }
 
 extern "C" int splat_render_fwd_l1(const splat_projected* proj, const float* rgb, int64_t n, const uint32_t* vals,
                                    const uint32_t* ranges, const splat_camera* cam, const float* bg,
-                                   const splat_image* out, const splat_l1* l1, splat_stream_t stream) {
-  if (!l1) return fail(SPLAT_EINVAL, "splat_render_fwd_l1: null loss descriptor");
-  return render_fwd_one(proj, rgb, n, vals, ranges, cam, bg, out, l1, stream, "splat_render_fwd_l1");
+                                   const splat_image* out, const splat_l1* l1, uint32_t* schedule,
+                                   splat_stream_t stream) {
+  return render_fwd_one(proj, rgb, n, vals, ranges, cam, bg, out, l1, schedule, stream, "splat_render_fwd_l1");
+}
+
+extern "C" size_t splat_tile_schedule_size(int32_t n_tiles) {
+  return n_tiles < 1 ? 0 : sizeof(uint32_t) * ((size_t)SPLAT_SCHEDULE_BUCKETS * (1 + (size_t)n_tiles));
 }
 
 // Workspace of splat_render_bwd: the screen-space gradients [n, 12] and, after
@@ -791,7 +882,7 @@ extern "C" size_t splat_render_bwd_workspace_size(int64_t n) { return n < 0 ? 0 
 
 extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected* proj, const splat_camera* cam,
                                 const float* w2c, const uint32_t* vals, const uint32_t* ranges,
-                                const uint32_t* tile_order, const splat_image* fwd, const float* bg,
+                                const uint32_t* schedule, const splat_image* fwd, const float* bg,
                                 const float* d_rgb, const float* d_depth,
                                 const float* d_sil, const splat_gaussians_grad* out, float* d_pose, float* d2d,
                                 void* ws, size_t ws_bytes, splat_stream_t stream) {
@@ -824,7 +915,7 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
   T.v[0].d_depth = d_depth;
   T.v[0].d_sil = d_sil;
   T.v[0].g2 = g2;
-  T.v[0].order = tile_order;
+  T.v[0].sched = const_cast<uint32_t*>(schedule);
   const int tiles = T.v[0].cam.tiles_x * T.v[0].cam.tiles_y;
   T.tile_end[0] = tiles;
   T.n = 1;
@@ -856,39 +947,58 @@ extern "C" int splat_project_bwd(const splat_gaussians* g, const splat_projected
                             reinterpret_cast<cudaStream_t>(stream));
 }
 
-extern "C" int splat_project_bwd_adam(const splat_gaussians* g, const splat_projected* proj, const splat_camera* cam,
-                                      const float* w2c, const float* grad2d, const splat_gaussians_grad* m,
-                                      const splat_gaussians_grad* v, const float* lr, float beta1, float beta2,
-                                      float eps, const int32_t* step, float* d_pose, splat_stream_t stream) {
-  if (!g || !cam || !w2c || !grad2d || !m || !v || !lr || !step)
-    return fail(SPLAT_EINVAL, "splat_project_bwd_adam: null argument");
-  int rc = check_proj(proj, g->n, "splat_project_bwd_adam");
-  if (rc) return rc;
-  if (g->n < 0 || (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->rgb ||
-                                !m->mean || !m->log_scale || !m->quat || !m->opacity_logit || !m->rgb || !v->mean ||
-                                !v->log_scale || !v->quat || !v->opacity_logit || !v->rgb)) ||
-      !aligned16(g->quat) || !aligned16(grad2d))
-    return fail(SPLAT_EINVAL, "splat_project_bwd_adam: bad gaussian, moment or gradient arrays");
-  if (g->n > 0 && !proj->radius) return fail(SPLAT_EINVAL, "splat_project_bwd_adam: proj->radius is null");
-  GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
-  AdamMapK A;
+static int make_adam_map(const splat_gaussians* g, const splat_gaussians_grad* m, const splat_gaussians_grad* v,
+                         const float* lr, float beta1, float beta2, float eps, const int32_t* step, AdamMapK* A,
+                         const char* who) {
+  if (!g || !m || !v || !lr || !step) return fail(SPLAT_EINVAL, "%s: null argument", who);
+  if (g->n < 0 || (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->rgb || !m->mean ||
+                                !m->log_scale || !m->quat || !m->opacity_logit || !m->rgb || !v->mean ||
+                                !v->log_scale || !v->quat || !v->opacity_logit || !v->rgb)))
+    return fail(SPLAT_EINVAL, "%s: bad gaussian or moment arrays", who);
   float* const P[5] = {const_cast<float*>(g->mean), const_cast<float*>(g->log_scale), const_cast<float*>(g->quat),
                        const_cast<float*>(g->opacity_logit), const_cast<float*>(g->rgb)};
   float* const Ms[5] = {m->mean, m->log_scale, m->quat, m->opacity_logit, m->rgb};
   float* const Vs[5] = {v->mean, v->log_scale, v->quat, v->opacity_logit, v->rgb};
   for (int k = 0; k < 5; ++k) {
-    A.p[k] = P[k];
-    A.m[k] = Ms[k];
-    A.v[k] = Vs[k];
-    A.lr[k] = lr[k];
-    A.vec[k] = aligned16(P[k]) && aligned16(Ms[k]) && aligned16(Vs[k]);
+    A->p[k] = P[k];
+    A->m[k] = Ms[k];
+    A->v[k] = Vs[k];
+    A->lr[k] = lr[k];
+    A->vec[k] = aligned16(P[k]) && aligned16(Ms[k]) && aligned16(Vs[k]);
   }
-  A.b1 = beta1;
-  A.b2 = beta2;
-  A.eps = eps;
-  A.step = step;
+  A->b1 = beta1;
+  A->b2 = beta2;
+  A->eps = eps;
+  A->step = step;
+  return SPLAT_OK;
+}
+
+extern "C" int splat_project_bwd_adam(const splat_gaussians* g, const splat_projected* proj, const splat_camera* cam,
+                                      const float* w2c, const float* grad2d, const splat_gaussians_grad* m,
+                                      const splat_gaussians_grad* v, const float* lr, float beta1, float beta2,
+                                      float eps, const int32_t* step, int32_t culled, float* d_pose,
+                                      splat_stream_t stream) {
+  if (!g || !cam || !w2c || !grad2d) return fail(SPLAT_EINVAL, "splat_project_bwd_adam: null argument");
+  int rc = check_proj(proj, g->n, "splat_project_bwd_adam");
+  if (rc) return rc;
+  AdamMapK A;
+  if ((rc = make_adam_map(g, m, v, lr, beta1, beta2, eps, step, &A, "splat_project_bwd_adam"))) return rc;
+  if (!aligned16(g->quat) || !aligned16(grad2d))
+    return fail(SPLAT_EINVAL, "splat_project_bwd_adam: quat or grad2d not 16-byte aligned");
+  if (g->n > 0 && !proj->radius) return fail(SPLAT_EINVAL, "splat_project_bwd_adam: proj->radius is null");
+  GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
   return launch_project_bwd_adam(gk, make_camk(*cam), w2c, proj->conic, proj->radius, grad2d, kGradStride, A, d_pose,
-                                 reinterpret_cast<cudaStream_t>(stream));
+                                 culled != 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int splat_adam_culled(const splat_gaussians* g, const int32_t* radius, const splat_gaussians_grad* m,
+                                 const splat_gaussians_grad* v, const float* lr, float beta1, float beta2, float eps,
+                                 const int32_t* step, splat_stream_t stream) {
+  AdamMapK A;
+  int rc = make_adam_map(g, m, v, lr, beta1, beta2, eps, step, &A, "splat_adam_culled");
+  if (rc) return rc;
+  if (g->n > 0 && !radius) return fail(SPLAT_EINVAL, "splat_adam_culled: radius is null");
+  return launch_adam_culled(g->n, radius, A, reinterpret_cast<cudaStream_t>(stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -915,7 +1025,7 @@ static int build_table(const splat_view* views, int32_t n_views, bool bwd, ViewT
     v.d_depth = w.d_depth;
     v.d_sil = w.d_sil;
     v.g2 = w.grad2d;
-    v.order = w.tile_order;
+    v.sched = w.schedule;
     T->v[i] = v;
     acc += v.cam.tiles_x * v.cam.tiles_y;
     T->tile_end[i] = acc;

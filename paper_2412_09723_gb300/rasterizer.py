@@ -38,7 +38,8 @@ class FrameBuffers:
         if want_used:
             self.image["n_used"] = torch.zeros(H, W, **i)
         self.ranges = torch.zeros(cam.n_tiles, 2, dtype=torch.int32, device=device)
-        self.tile_order = torch.zeros(cam.n_tiles, dtype=torch.int32, device=device)  # heavy-first, for the backward
+        # the tile schedule (heaviest first) that the forward fills for the backward
+        self.schedule = torch.zeros(B.splat_tile_schedule_size(cam.n_tiles) // 4, dtype=torch.int32, device=device)
         self.k_dev = torch.zeros(1, dtype=torch.int64, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device)
         self.want_keys = want_keys
@@ -73,14 +74,14 @@ def bin_sort(fb: FrameBuffers, stream=None, sync_check: bool = True):
     if sync_check:
         fb.status.zero_()
     B.splat_bin_sort(fb.cproj, fb.n, fb.ccam, fb.keys, fb.vals, fb.capacity, fb.k_dev, fb.ranges, fb.status,
-                     fb.bin_ws, stream, tile_order=fb.tile_order)
+                     fb.bin_ws, stream, schedule=fb.schedule)
     if sync_check:
         k = int(fb.k_dev.item())
         if k > fb.capacity:
             fb.ensure_capacity(k)
             fb.status.zero_()
             B.splat_bin_sort(fb.cproj, fb.n, fb.ccam, fb.keys, fb.vals, fb.capacity, fb.k_dev, fb.ranges, fb.status,
-                             fb.bin_ws, stream, tile_order=fb.tile_order)
+                             fb.bin_ws, stream, schedule=fb.schedule)
         return k
     return None
 
@@ -96,7 +97,8 @@ def render_forward(params, w2c, cam: Camera, bg=(0.0, 0.0, 0.0), fb: FrameBuffer
     g = B.gaussians_struct(*params)
     project(g, w2c, fb, stream)
     bin_sort(fb, stream)
-    B.splat_render_fwd(fb.cproj, params[4], n, fb.vals, fb.ranges, fb.ccam, bg, fb.cimg, stream)
+    B.splat_render_fwd_l1(fb.cproj, params[4], n, fb.vals, fb.ranges, fb.ccam, bg, fb.cimg, None, stream,
+                          schedule=fb.schedule)
     return fb
 
 
@@ -139,7 +141,7 @@ class SplatRender(torch.autograd.Function):
         cg = B.gaussians_struct(mean, log_scale, quat, opacity_logit, rgb)
         cgr = B.CGaussiansGrad(*(B._p(t) for t in grads))
         B.splat_render_bwd(cg, fb.cproj, fb.ccam, w, fb.vals, fb.ranges, fb.cimg, ctx.bg, g_rgb, g_depth, g_sil, cgr,
-                           d_pose, None, fb.bwd_ws, tile_order=fb.tile_order)
+                           d_pose, None, fb.bwd_ws, schedule=fb.schedule)
         return (*grads, d_pose, None, None, None)
 
 

@@ -142,23 +142,37 @@ def _check_bins(fb, sc, w2c, cam):
     assert np.array_equal(fb.vals[:k].cpu().numpy().view(np.uint32), vals)
     assert np.array_equal(fb.keys[:k].cpu().numpy().view(np.uint64), keys)
     assert np.array_equal(fb.ranges.cpu().numpy().view(np.uint32), ranges)
-    _check_tile_order(fb.tile_order.cpu().numpy(), ranges)
 
 
-def _check_tile_order(order, ranges):
-    """A permutation of the tiles, list lengths non-increasing in steps of an
-    eighth of an octave (the exponent and three mantissa bits of the length as
-    a float32; empty lists last)."""
-    order = order.view(np.uint32)
-    n_t = len(ranges)
-    assert np.array_equal(np.sort(order), np.arange(n_t, dtype=np.uint32))
-    c = (ranges[:, 1] - ranges[:, 0]).astype(np.float32)
-    b = np.where(c > 0, ((c.view(np.uint32) >> 20).astype(np.int64) - (127 << 3)) + 1, 0)
-    b = np.minimum(b, 127)[order]
-    assert (np.diff(b) <= 0).all()
+def _check_schedule(sched, n_contrib, cam):
+    """The tile schedule the forward filled: bucket counts that add up to the
+    number of tiles, lists that together hold every tile once, each tile in
+    the bucket of its summed contributor counts S (1 + the exponent and three
+    mantissa bits of S as a float32, in eighths of an octave; 0 for S = 0),
+    taken from the oracle's image."""
+    nb = 128
+    sched = sched.view(np.uint32)
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    n_t = tx * ty
+    assert sched.size == nb * (1 + n_t)
+    counts = sched[:nb].astype(np.int64)
+    assert counts.sum() == n_t
+    pad = np.zeros((ty * 16, tx * 16), np.int64)
+    pad[:cam.height, :cam.width] = n_contrib
+    S = pad.reshape(ty, 16, tx, 16).sum(axis=(1, 3)).ravel().astype(np.float32)
+    want = np.where(S > 0, ((S.view(np.uint32) >> 20).astype(np.int64) - (127 << 3)) + 1, 0)
+    want = np.minimum(want, nb - 1)
+    seen = []
+    for b in range(nb):
+        lst = sched[nb + b * n_t: nb + b * n_t + counts[b]]
+        assert (want[lst] == b).all(), f"bucket {b}"
+        seen.append(lst)
+    assert np.array_equal(np.sort(np.concatenate(seen)), np.arange(n_t, dtype=np.uint32))
 
 
 def _check_image(fb, ref):
+    if hasattr(fb, "schedule"):
+        _check_schedule(fb.schedule.cpu().numpy(), ref["n_contrib"], fb.cam)
     got = {k: v.cpu().numpy() for k, v in fb.image.items()}
     for k in ("rgb", "depth", "sil", "t_final"):
         d = np.abs(got[k].astype(np.float64) - ref[k])
@@ -192,7 +206,7 @@ def _bwd_gpu(p, fb, w2c, cam, bg, g, dev):
     gr, gd, gs = (torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev) for a in g)
     B.splat_render_bwd(B.gaussians_struct(*p), fb.cproj, fb.ccam, _w(w2c, dev), fb.vals, fb.ranges, fb.cimg, bg,
                        gr, gd, gs, B.CGaussiansGrad(*(B._p(t) for t in grads)), d_pose, d2d, fb.bwd_ws,
-                       tile_order=fb.tile_order)
+                       schedule=fb.schedule)
     torch.cuda.synchronize()
     return [t.cpu().numpy() for t in grads], d_pose.cpu().numpy(), d2d.cpu().numpy()
 
@@ -660,7 +674,7 @@ def test_render_fwd_l1_matches_oracle_loss(dev):
     R.bin_sort(fb2)
     l1 = B.l1_struct(t_rgb, t_depth, 1.0, 0.5, g_rgb, g_depth, loss)
     B.splat_render_fwd_l1(fb2.cproj, p[4], sc.n, fb2.vals, fb2.ranges, fb2.ccam, tuple(float(x) for x in bg), fb2.cimg,
-                          l1)
+                          l1, schedule=fb2.schedule)
     torch.cuda.synchronize()
     _check_image(fb2, ref)
     L, rg, rd = oracle.loss_l1(ref["rgb"], ref["depth"], t_rgb.cpu().numpy(), t_depth.cpu().numpy(), 1.0, 0.5)
