@@ -325,8 +325,9 @@ def serving_section(dev, seconds, seed=4, short_seconds=5.0):
     request with every 5th frame.  The continuous-batching server against the
     plain per-request path on the same trace: in real time at 30 Hz per agent
     for `seconds` (the workload's 30 s), at 90 Hz and at half of the agents'
-    resident footprint as HBM budget (admission binds, agents are swapped to
-    pinned host memory) for `short_seconds`, and saturated (every request of
+    resident footprint as HBM budget (admission binds: idle agents give up
+    their per-step buffers or are swapped to pinned host memory) for
+    `short_seconds`, and saturated (every request of
     a 2 s trace submitted at t = 0)."""
     from paper_2412_09723_gb300 import scenes
     from paper_2412_09723_gb300.serve import Server, _agent_bytes, latency_stats, make_agents_workload, poisson_trace
@@ -343,14 +344,17 @@ def serving_section(dev, seconds, seed=4, short_seconds=5.0):
         reqs = poisson_trace(len(spec), rate, secs, 8, map_every=5, seed=seed)
         span = srv.serve(reqs, realtime=realtime) if kind == "served" else srv.serve_plain(reqs, realtime=realtime)
         st = latency_stats(reqs, span)
-        st["swaps"] = srv.swaps
+        st["swaps"] = srv.swaps  # states swapped out to host memory
+        st["buffer_releases"] = srv.releases  # per-step buffers given up (re-made at the next step)
         st["trace_s"] = secs
         return st
 
     full = 150 << 30
     rows = {}
     rows["30hz"] = (run("served", True, full), run("plain", True, full))
-    footprint = sum(_agent_bytes(s.agent) for s in srv.slots if s.agent is not None)
+    tiers = [_agent_bytes(s.agent) for s in srv.slots if s.agent is not None]
+    footprint = sum(a + b for a, b in tiers)
+    state_bytes = sum(a for a, _ in tiers)
     rows["90hz"] = (run("served", True, full, 90.0, short_seconds), run("plain", True, full, 90.0, short_seconds))
     rows["saturated"] = (run("served", False, full, secs=2.0), run("plain", False, full, secs=2.0))
     half = footprint // 2
@@ -358,6 +362,7 @@ def serving_section(dev, seconds, seed=4, short_seconds=5.0):
                                 run("plain", True, half, secs=short_seconds))
     rows["saturated_half_budget"] = (run("served", False, half, secs=2.0), run("plain", False, half, secs=2.0))
     out["resident_footprint_bytes"] = footprint
+    out["state_bytes"] = state_bytes  # maps, moments, poses; the rest of the footprint is per-step buffers
     out["reduced_budget_bytes"] = half
     for k, (a, b) in rows.items():
         out["served_" + k] = a

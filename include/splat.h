@@ -311,7 +311,8 @@ int splat_render_bwd(const splat_gaussians *g, const splat_projected *proj,
  * splat_render_bwd): chains screen-space gradients grad2d (device float
  * [n,12], 16-byte aligned rows: du, dv, d conic a, b, c, d opacity,
  * d rgb[3], d depth, 2 unused) to the Gaussian parameters (accumulated into
- * `out`) and, if d_pose is not NULL, to the pose 6-vector (accumulated).
+ * `out`, or not formed when `out` is NULL) and, if d_pose is not NULL, to the
+ * pose 6-vector (accumulated); out, d_pose and d2d may not all be NULL.
  * d2d (optional) receives the [n,10] screen-space gradients.  proj must be
  * the splat_project output for the same map, camera and pose (Gaussians with
  * radius 0 are skipped).  Used after splat_render_bwd_batch.
@@ -565,8 +566,9 @@ int splat_loss_consensus(const float *rgb, const float *depth, const float *targ
  * The combined covariance is taken at the current T and held fixed in the
  * step (with R = I it is the printed Sigma_k + Sigma_l).  Sigma = R(q)
  * diag(exp(2 log_scale)) R(q)^T of each Gaussian.
- *   map_a, map_b: the two maps (mean, log_scale, quat are read);
- *   pairs: device int32[capacity,2] of (id in A, id in B), as splat_assoc
+ *   map_a, map_b: the two maps (mean, log_scale, quat are read; quat
+ *   16-byte aligned);
+ *   pairs: device int32[capacity,2] (8-byte aligned) of (id in A, id in B), as splat_assoc
  *   writes them; weights: device int32[capacity] pair weights (e.g. the pixel
  *   counts of splat_assoc) or NULL for weight 1; m_dev: device int64[1], the
  *   number of valid pairs (min(M, capacity) are used);
@@ -586,7 +588,8 @@ int splat_mahalanobis_system(const splat_gaussians *map_a, const splat_gaussians
 
 /*
  * splat_mahalanobis_step -- solves H delta = -g of a system written by
- * splat_mahalanobis_system (Cholesky, double precision) and applies
+ * splat_mahalanobis_system (scaled to unit diagonal, H' = D H D with
+ * D = diag(H)^-1/2, then Cholesky in single precision) and applies
  * T <- exp(delta^) T.  delta_out: device double[6] or NULL.  If H is not
  * positive definite T is left unchanged and SPLAT_ENUMERIC is raised in
  * status (device int32[1]).  Errors: SPLAT_EINVAL, SPLAT_ECUDA.

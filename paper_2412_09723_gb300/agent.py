@@ -49,6 +49,10 @@ class StepConfig:
     # the culled Gaussians' zero-gradient Adam step on the side stream, beside
     # the backward render (else inside the fused projection adjoint's launch)
     culled_beside: bool = False
+    # keep per-parameter gradient arrays, filled by steps without mapping;
+    # without them such a step forms the pose gradient alone (a mapping step
+    # never needs them: its Adam step is fused into the projection adjoint)
+    grads: bool = True
 
 
 class Agent:
@@ -80,17 +84,43 @@ class Agent:
             self.v = [torch.zeros_like(p) for p in self.params]
             self.w2c = torch.as_tensor(w2c, dtype=torch.float32, device=device).contiguous().clone()
         self.n = self.params[0].shape[0]
-        self.grads = [torch.zeros_like(p) for p in self.params]
         # per-step accumulators in one block, cleared by one launch: d_pose [6], loss [1], association status [1]
         self._acc = torch.zeros(8, dtype=torch.float32, device=device)
         self.d_pose = self._acc[0:6]
+        self.loss = self._acc[6:7]
+        self.assoc_status = self._acc[7:8].view(torch.int32)
         self.pose_m = torch.zeros(6, dtype=torch.float32, device=device)
         self.pose_v = torch.zeros(6, dtype=torch.float32, device=device)
         self.t_dev = torch.zeros(1, dtype=torch.int32, device=device)  # Adam step, advanced on the device
+        self.bin_status = torch.zeros(1, dtype=torch.int32, device=device)  # sticky capacity status of the binning
         if state is not None:
             for dst, src in zip((self.pose_m, self.pose_v, self.t_dev), state[16:19]):
                 dst.copy_(src, non_blocking=True)
-        self.fb = FrameBuffers(self.n, cam, device, capacity=capacity, want_used=want_used)
+        self.side = side if side is not None else torch.cuda.Stream(device=device)  # association, beside the backward
+        self.host_in = None  # pinned (rgb, depth) the step copies its observation from, or None
+        self.host_out = None  # pinned (loss, w2c) the step writes its results to, or None
+        self.cg = B.gaussians_struct(*self.params)
+        self.steps_done = 0
+        self.graph = None
+        self.want_used = want_used
+        self._make_adam()
+        self.make_scratch(capacity)
+
+    # -- per-step buffers ---------------------------------------------------------
+    SCRATCH = ("grads", "cgr", "fb", "obs_rgb", "obs_depth", "obs_id", "obs_tfinal", "g_rgb", "g_depth", "pairs",
+               "counts", "m_dev", "assoc_ws", "cl1")
+
+    def make_scratch(self, capacity: int | None = None):
+        """Allocate the per-step buffers: frame buffers (projection, sorted
+        lists, image, workspaces), observation and image-gradient buffers,
+        association buffers and, when kept, the gradient arrays.  Everything
+        else (map, moments, pose, accumulators) is the agent's state.  The
+        allocations and fills are stream-ordered on the current stream."""
+        device, cam = self.device, self.cam
+        self.grads = [torch.zeros_like(p) for p in self.params] if self.cfg.grads else None
+        self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads)) if self.grads is not None else None
+        self.grads_clean = True  # host-side: the gradient buffers hold zeros
+        self.fb = FrameBuffers(self.n, cam, device, capacity=capacity, want_used=self.want_used, status=self.bin_status)
         H, W = cam.height, cam.width
         self.obs_rgb = torch.zeros(H, W, 3, dtype=torch.float32, device=device)
         self.obs_depth = torch.zeros(H, W, dtype=torch.float32, device=device)
@@ -98,28 +128,51 @@ class Agent:
         self.obs_tfinal = torch.ones(H, W, dtype=torch.float32, device=device)
         self.g_rgb = torch.zeros(H, W, 3, dtype=torch.float32, device=device)
         self.g_depth = torch.zeros(H, W, dtype=torch.float32, device=device)
-        self.loss = self._acc[6:7]
         npix = cam.npix
         self.assoc_cap = npix
         self.pairs = torch.zeros(npix, 2, dtype=torch.int32, device=device)
         self.counts = torch.zeros(npix, dtype=torch.int32, device=device)
         self.m_dev = torch.zeros(1, dtype=torch.int64, device=device)
-        self.assoc_status = self._acc[7:8].view(torch.int32)
         self.assoc_ws = torch.empty(max(1, B.splat_assoc_workspace_size(npix)), dtype=torch.uint8, device=device)
-        self.side = side if side is not None else torch.cuda.Stream(device=device)  # association, beside the backward
-        self.host_in = None  # pinned (rgb, depth) the step copies its observation from, or None
-        self.host_out = None  # pinned (loss, w2c) the step writes its results to, or None
-        self.cg = B.gaussians_struct(*self.params)
-        self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads))
-        self.steps_done = 0
-        self.grads_clean = True  # host-side: the gradient buffers hold zeros
-        self._make_adam()
         self._make_l1()
+
+    @property
+    def has_scratch(self) -> bool:
+        return self.fb is not None
+
+    def release_scratch(self):
+        """Drop the per-step buffers (the state stays) and any captured graph.
+        Returns the dropped tensors: the caller keeps them alive until no
+        launched work can still use them.  The duplicate capacity is kept for
+        make_scratch."""
+        held = [getattr(self, k) for k in self.SCRATCH]
+        self.capacity = self.fb.capacity
+        for k in self.SCRATCH:
+            setattr(self, k, None)
+        self.graph = None
+        return held
+
+    def state_tensors(self):
+        """The device tensors of the agent's state (what stays resident
+        without the per-step buffers)."""
+        return [*self._state(), self._acc, self.bin_status]
+
+    def scratch_tensors(self):
+        out = []
+        if self.grads is not None:
+            out += self.grads
+        for k in ("obs_rgb", "obs_depth", "obs_id", "obs_tfinal", "g_rgb", "g_depth", "pairs", "counts", "m_dev",
+                  "assoc_ws"):
+            out.append(getattr(self, k))
+        fb = self.fb
+        out += list(fb.proj.values()) + list(fb.image.values())
+        out += [t for t in (fb.ranges, fb.schedule, fb.k_dev, fb.vals, fb.keys, fb.bin_ws, fb.bwd_ws)
+                if t is not None]
+        return out
 
     def _make_adam(self):
         names = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
         self.lrs = [self.cfg.lr[k] for k in names]
-        self.adam = B.AdamGroups(self.params, self.grads, self.m, self.v, self.lrs)
         self.cm = B.CGaussiansGrad(*(B._p(t) for t in self.m))
         self.cv = B.CGaussiansGrad(*(B._p(t) for t in self.v))
 
@@ -200,7 +253,7 @@ class Agent:
         with torch.cuda.stream(s):
             self._acc.zero_()
             self.t_dev.add_(1)
-            if not self.grads_clean:  # the fused adjoint + Adam never fills them
+            if not self.grads_clean and self.grads is not None:  # the fused adjoint + Adam never fills them
                 for g in self.grads:
                     g.zero_()
         self.grads_clean = True
@@ -242,7 +295,7 @@ class Agent:
             B.splat_project_bwd_adam(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cm, self.cv, self.lrs,
                                      self.t_dev, self.d_pose, stream=s, culled=not self.cfg.culled_beside)
         else:
-            self.grads_clean = False
+            self.grads_clean = self.grads is None
             B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cgr, self.d_pose, None, s)
 
     def phase_adam_culled(self, s):
@@ -350,12 +403,8 @@ class Agent:
         s.synchronize()
         self.params, self.m, self.v = dst[:5], dst[5:10], dst[10:]
         self.n = k
-        self.grads = [torch.zeros_like(t) for t in self.params]
         self.cg = B.gaussians_struct(*self.params)
-        self.cgr = B.CGaussiansGrad(*(B._p(t) for t in self.grads))
-        self.grads_clean = True
-        self.fb = FrameBuffers(k, self.cam, self.device, capacity=self.fb.capacity, want_keys=self.fb.want_keys,
-                               want_used="n_used" in self.fb.image)
+        self.make_scratch(self.fb.capacity)
         self._make_adam()
         self.graph = None
         self._snap = None
@@ -422,4 +471,4 @@ class Agent:
 
     def status(self) -> int:
         """Sticky device status of the last steps (host read)."""
-        return int(self.fb.status.item()) | int(self.assoc_status.item())
+        return int(self.bin_status.item()) | int(self.assoc_status.item())

@@ -287,8 +287,8 @@ def splat_render_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c,
 def splat_project_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, grad2d, grads: CGaussiansGrad,
                       d_pose, d2d=None, stream=None):
     _check("splat_project_bwd", load().splat_project_bwd(
-        ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(grad2d), ctypes.byref(grads),
-        _p(d_pose), _p(d2d), _stream(stream)))
+        ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(grad2d),
+        None if grads is None else ctypes.byref(grads), _p(d_pose), _p(d2d), _stream(stream)))
 
 
 def splat_project_bwd_adam(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, grad2d, m: CGaussiansGrad,

@@ -3,24 +3,28 @@
 // * Loss of Eq. (optim) (Sec. 3.5 step 4): L1 colour, SSIM and L1 depth
 //   terms with their image gradients, in two passes (the L1 terms ride on
 //   the first, which has each pixel's colours staged).  SSIM uses an 11 x 11 Gaussian window
-//   (sigma 1.5) over a zero-padded image; one CTA computes a 32 x 16 block of
+//   (sigma 1.5) over a zero-padded image; a CTA computes 32 x 16 blocks of
 //   all three channels: the 42 x 26 patch of both images is staged in shared
-//   memory, the window is applied separably (rows, then columns) to the five
+//   memory (the statistics kernel is persistent and stages its next block's
+//   patch with asynchronous copies while it computes the current one), the
+//   window is applied separably (rows, then columns) to the five
 //   products x, y, x^2, y^2, xy, and each pixel's SSIM and its partial derivatives with
 //   respect to the three window sums that involve x (A = dS/dmu_x,
 //   B = dS/dE[x^2], C = dS/dE[xy]) are written out.  A second kernel applies
 //   the same window to A, B, C and forms
 //   dS/dx(q) = (W*A)(q) + 2 x(q) (W*B)(q) + y(q) (W*C)(q).
 // * Mahalanobis alignment (Sec. 3.5 step 3): one thread per associated pair
-//   builds its Gauss-Newton contribution (21 + 6 + 1 numbers) in float,
-//   summed in float per thread and per warp (a few pairs and 32 partial sums:
-//   double precision is slow on this part), then in double per CTA and into
-//   the system with double atomics; one thread solves the 6 x 6 system by
-//   Cholesky and retracts T.
+//   gathers both Gaussians' records in one round and builds its Gauss-Newton
+//   contribution (21 + 6 + 1 numbers) in float, summed in float per thread,
+//   warp and CTA (a few pairs, 32 and 8 partial sums: double-precision
+//   arithmetic is slow on this part), then into the system with one double
+//   atomic per number and CTA; one thread solves the 6 x 6 system by
+//   Cholesky (scaled to unit diagonal, in float) and retracts T.
 // * Pruning (Algorithm 1): a flag kernel (the three criteria, block counts),
 //   a one-CTA scan of the block counts, and a scatter kernel that re-ranks
 //   the kept Gaussians inside each block and copies every column's row.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "common.cuh"
@@ -86,143 +90,180 @@ constexpr int kSsTXp = kSsTX + 1;
 
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
+// Asynchronous 4-byte copies global -> shared (cp.async, zero-filled when
+// `in` is false: the zero padding of the window), so that a CTA stages its
+// next patch while it computes the current one.
+__device__ __forceinline__ void cp_async4(void* smem, const float* g, bool in) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(g), "r"(in ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Persistent CTAs: CTA b takes blocks b, b + grid, ... of the kSsTX x kSsTY
+// output grid (nbx blocks per row) and double-buffers their patches.
+struct SsFwdSmem {
+  float2 sxy[2][3][kSsPY][kSsPXp];  // (x, y) of every channel, two patches
+  float2 h1[kSsPY][kSsTXp];         // horizontal sums of (x, y)
+  float2 h2[kSsPY][kSsTXp];         // ... of (x^2, y^2)
+  float h3[kSsPY][kSsTXp];          // ... of x y
+  float red[8];
+};
+
+// The patch of block (bx, by): a patch row is 126 consecutive floats of each image.
+__device__ __forceinline__ void ssim_fwd_stage(float2 (*dst)[kSsPY][kSsPXp], const float* x, const float* y, int H,
+                                               int W, int bx, int by) {
+  for (int e = threadIdx.x; e < kSsPY * 3 * kSsPX; e += blockDim.x) {
+    const int r = e / (3 * kSsPX), j = e - r * (3 * kSsPX);
+    const int c = j / 3, ch = j - 3 * c;
+    const int gx = bx - kSsR + c, gy = by - kSsR + r;
+    const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+    const size_t gi = in ? ((size_t)gy * W + gx) * 3 + ch : 0;
+    float2* d = &dst[ch][r][c];
+    cp_async4(&d->x, x + gi, in);
+    cp_async4(&d->y, y + gi, in);
+  }
+}
+
 // The L1 terms of the loss ride along: each output pixel's colour residual
 // x - y (already staged) and depth residual give the L1 subgradients
 // (written to d_rgb / d_depth; the adjoint kernel adds the SSIM part) and
 // their share of the loss.
 __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                                        const float* __restrict__ dep, const float* __restrict__ tdep,
-                                                       int H, int W, SsimWin win, float loss_scale, float ssim_scale,
-                                                       float sc, float sd, float* __restrict__ d_rgb,
+                                                       int H, int W, int nbx, int nblk, SsimWin win, float loss_scale,
+                                                       float ssim_scale, float sc, float sd, float* __restrict__ d_rgb,
                                                        float* __restrict__ d_depth, float* __restrict__ abc,
                                                        float* __restrict__ loss) {
-  __shared__ float2 sxy[3][kSsPY][kSsPXp];  // (x, y) of every channel
-  __shared__ float2 h1[kSsPY][kSsTXp];      // horizontal sums of (x, y)
-  __shared__ float2 h2[kSsPY][kSsTXp];      // ... of (x^2, y^2)
-  __shared__ float h3[kSsPY][kSsTXp];       // ... of x y
-  __shared__ float red[8];
+  extern __shared__ __align__(16) unsigned char ss_raw[];
+  SsFwdSmem& sm = *reinterpret_cast<SsFwdSmem*>(ss_raw);
   const int t = threadIdx.x;
-  const int bx = blockIdx.x * kSsTX, by = blockIdx.y * kSsTY;
-  {  // a patch row is 126 consecutive floats of each image: threads 0-125 take one row, 128-253 the next
-    const int j = t & 127, r0 = t >> 7;
-    const int c = j / 3, ch = j - 3 * c;
-    const int gx = bx - kSsR + c;
-    if (j < 3 * kSsPX) {
-      const bool inx = gx >= 0 && gx < W;
-      for (int r = r0; r < kSsPY; r += 2) {
-        const int gy = by - kSsR + r;
-        const bool in = inx && gy >= 0 && gy < H;
-        const size_t gi = ((size_t)gy * W + gx) * 3 + ch;
-        sxy[ch][r][c] = in ? make_float2(x[gi], y[gi]) : make_float2(0.f, 0.f);
-      }
-    }
-  }
-  __syncthreads();
   const size_t plane = (size_t)H * W;
   float sum_1ms = 0.f, sum_s = 0.f, sum_c = 0.f, sum_d = 0.f;
-  for (int ch = 0; ch < 3; ++ch) {
-    if (t < kSsHItems) {
-      const int r = t / (kSsTX / kSsRun), c0 = kSsRun * (t % (kSsTX / kSsRun));
-      float2 a1[kSsRun], a2[kSsRun];
-      float a3[kSsRun];
-#pragma unroll
-      for (int j = 0; j < kSsRun; ++j) {
-        a1[j] = a2[j] = bc2(-0.0f);
-        a3[j] = -0.0f;
-      }
-#pragma unroll
-      for (int p = 0; p < kSsRun + 2 * kSsR; ++p) {
-        const float2 v = sxy[ch][r][c0 + p];
-        const float2 sq = __fmul2_rn(v, v);
-        const float pr = v.x * v.y;
+  int blk = blockIdx.x, buf = 0;
+  if (blk < nblk) ssim_fwd_stage(sm.sxy[0], x, y, H, W, (blk % nbx) * kSsTX, (blk / nbx) * kSsTY);
+  cp_async_commit();
+  for (; blk < nblk; blk += gridDim.x, buf ^= 1) {
+    const int nxt = blk + gridDim.x;
+    if (nxt < nblk) ssim_fwd_stage(sm.sxy[buf ^ 1], x, y, H, W, (nxt % nbx) * kSsTX, (nxt / nbx) * kSsTY);
+    cp_async_commit();
+    cp_async_wait<1>();  // this block's patch has landed (the next one may still be in flight)
+    __syncthreads();
+    float2 (*sxy)[kSsPY][kSsPXp] = sm.sxy[buf];
+    const int bx = (blk % nbx) * kSsTX, by = (blk / nbx) * kSsTY;
+    for (int ch = 0; ch < 3; ++ch) {
+      if (t < kSsHItems) {
+        const int r = t / (kSsTX / kSsRun), c0 = kSsRun * (t % (kSsTX / kSsRun));
+        float2 a1[kSsRun], a2[kSsRun];
+        float a3[kSsRun];
 #pragma unroll
         for (int j = 0; j < kSsRun; ++j) {
+          a1[j] = a2[j] = bc2(-0.0f);
+          a3[j] = -0.0f;
+        }
+#pragma unroll
+        for (int p = 0; p < kSsRun + 2 * kSsR; ++p) {
+          const float2 v = sxy[ch][r][c0 + p];
+          const float2 sq = __fmul2_rn(v, v);
+          const float pr = v.x * v.y;
+#pragma unroll
+          for (int j = 0; j < kSsRun; ++j) {
+            const int k = p - j;
+            if (k >= 0 && k < kSsTaps) {
+              const float2 w = bc2(win.w[k]);
+              a1[j] = __ffma2_rn(w, v, a1[j]);
+              a2[j] = __ffma2_rn(w, sq, a2[j]);
+              a3[j] = fmaf(win.w[k], pr, a3[j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kSsRun; ++j) {
+          sm.h1[r][c0 + j] = a1[j];
+          sm.h2[r][c0 + j] = a2[j];
+          sm.h3[r][c0 + j] = a3[j];
+        }
+      }
+      __syncthreads();
+      const int tx = t & 31, ty0 = 2 * (t >> 5);
+      float2 m1[2], m2[2];
+      float m3[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        m1[j] = m2[j] = bc2(-0.0f);
+        m3[j] = -0.0f;
+      }
+#pragma unroll
+      for (int p = 0; p < 2 + 2 * kSsR; ++p) {
+        const float2 v1 = sm.h1[ty0 + p][tx], v2 = sm.h2[ty0 + p][tx];
+        const float v3 = sm.h3[ty0 + p][tx];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
           const int k = p - j;
           if (k >= 0 && k < kSsTaps) {
             const float2 w = bc2(win.w[k]);
-            a1[j] = __ffma2_rn(w, v, a1[j]);
-            a2[j] = __ffma2_rn(w, sq, a2[j]);
-            a3[j] = fmaf(win.w[k], pr, a3[j]);
+            m1[j] = __ffma2_rn(w, v1, m1[j]);
+            m2[j] = __ffma2_rn(w, v2, m2[j]);
+            m3[j] = fmaf(win.w[k], v3, m3[j]);
           }
         }
       }
 #pragma unroll
-      for (int j = 0; j < kSsRun; ++j) {
-        h1[r][c0 + j] = a1[j];
-        h2[r][c0 + j] = a2[j];
-        h3[r][c0 + j] = a3[j];
-      }
-    }
-    __syncthreads();
-    const int tx = t & 31, ty0 = 2 * (t >> 5);
-    float2 m1[2], m2[2];
-    float m3[2];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      m1[j] = m2[j] = bc2(-0.0f);
-      m3[j] = -0.0f;
-    }
-#pragma unroll
-    for (int p = 0; p < 2 + 2 * kSsR; ++p) {
-      const float2 v1 = h1[ty0 + p][tx], v2 = h2[ty0 + p][tx];
-      const float v3 = h3[ty0 + p][tx];
-#pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const int k = p - j;
-        if (k >= 0 && k < kSsTaps) {
-          const float2 w = bc2(win.w[k]);
-          m1[j] = __ffma2_rn(w, v1, m1[j]);
-          m2[j] = __ffma2_rn(w, v2, m2[j]);
-          m3[j] = fmaf(win.w[k], v3, m3[j]);
+        const int gx = bx + tx, gy = by + ty0 + j;
+        if (gx >= W || gy >= H) continue;
+        const float mx = m1[j].x, my = m1[j].y;
+        const float vx = m2[j].x - mx * mx, vy = m2[j].y - my * my, cxy = m3[j] - mx * my;
+        const float a = 2.f * mx * my + kSsC1, b = 2.f * cxy + kSsC2;
+        const float c = mx * mx + my * my + kSsC1, d = vx + vy + kSsC2;
+        const float rc = __frcp_rn(c), rd = __frcp_rn(d);  // two reciprocals instead of six divisions
+        const float rcd = rc * rd;
+        const float sv = a * b * rcd;
+        const float A = 2.f * my * (b - a) * rcd - sv * (2.f * mx * rc - 2.f * mx * rd);
+        const float Bm = -sv * rd;
+        const float Cm = 2.f * a * rcd;
+        // planar layout [map][channel][H][W], so the adjoint stages contiguous rows
+        const size_t i = (size_t)ch * plane + (size_t)gy * W + gx;
+        abc[i] = A;
+        abc[3 * plane + i] = Bm;
+        abc[6 * plane + i] = Cm;
+        sum_1ms += 1.f - sv;
+        sum_s += sv;
+        // L1 terms (sign(0) = 0), as splat_loss_l1
+        const size_t pix = (size_t)gy * W + gx;
+        const float2 xy = sxy[ch][ty0 + j + kSsR][tx + kSsR];
+        const float e = xy.x - xy.y;
+        d_rgb[3 * pix + ch] = e > 0.f ? sc : (e < 0.f ? -sc : 0.f);
+        sum_c += fabsf(e);
+        if (ch == 0) {
+          const float ed = dep[pix] - tdep[pix];
+          d_depth[pix] = ed > 0.f ? sd : (ed < 0.f ? -sd : 0.f);
+          sum_d += fabsf(ed);
         }
       }
+      // the horizontal sums are rewritten for the next channel, and after the
+      // last channel this patch's buffer is refilled
+      __syncthreads();
     }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int gx = bx + tx, gy = by + ty0 + j;
-      if (gx >= W || gy >= H) continue;
-      const float mx = m1[j].x, my = m1[j].y;
-      const float vx = m2[j].x - mx * mx, vy = m2[j].y - my * my, cxy = m3[j] - mx * my;
-      const float a = 2.f * mx * my + kSsC1, b = 2.f * cxy + kSsC2;
-      const float c = mx * mx + my * my + kSsC1, d = vx + vy + kSsC2;
-      const float rc = __frcp_rn(c), rd = __frcp_rn(d);  // two reciprocals instead of six divisions
-      const float rcd = rc * rd;
-      const float sv = a * b * rcd;
-      const float A = 2.f * my * (b - a) * rcd - sv * (2.f * mx * rc - 2.f * mx * rd);
-      const float Bm = -sv * rd;
-      const float Cm = 2.f * a * rcd;
-      // planar layout [map][channel][H][W], so the adjoint stages contiguous rows
-      const size_t i = (size_t)ch * plane + (size_t)gy * W + gx;
-      abc[i] = A;
-      abc[3 * plane + i] = Bm;
-      abc[6 * plane + i] = Cm;
-      sum_1ms += 1.f - sv;
-      sum_s += sv;
-      // L1 terms (sign(0) = 0), as splat_loss_l1
-      const size_t pix = (size_t)gy * W + gx;
-      const float2 xy = sxy[ch][ty0 + j + kSsR][tx + kSsR];
-      const float e = xy.x - xy.y;
-      d_rgb[3 * pix + ch] = e > 0.f ? sc : (e < 0.f ? -sc : 0.f);
-      sum_c += fabsf(e);
-      if (ch == 0) {
-        const float ed = dep[pix] - tdep[pix];
-        d_depth[pix] = ed > 0.f ? sd : (ed < 0.f ? -sd : 0.f);
-        sum_d += fabsf(ed);
-      }
-    }
-    __syncthreads();  // the horizontal sums are rewritten for the next channel
   }
-  const float t0 = block_sum_256(sum_1ms, red);
+  cp_async_wait<0>();
+  const float t0 = block_sum_256(sum_1ms, sm.red);
   __syncthreads();
-  const float t1 = block_sum_256(sum_s, red);
+  const float t1 = block_sum_256(sum_s, sm.red);
   __syncthreads();
-  const float t2 = block_sum_256(sc * sum_c + sd * sum_d, red);
+  const float t2 = block_sum_256(sc * sum_c + sd * sum_d, sm.red);
   if (t == 0) {
     atomicAdd(&loss[0], t0 * loss_scale + t2);
     atomicAdd(&loss[1], t1 * ssim_scale);
   }
 }
 
+// The adjoint: one CTA per block, the channel's (A, B), C patch staged per
+// channel (high occupancy hides the staging loads; a double-buffered
+// persistent form measured slower here).
 __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                                        int H, int W, SsimWin win, float grad_scale,
                                                        const float* __restrict__ abc, float* __restrict__ d_rgb) {
@@ -320,10 +361,24 @@ struct MapK {
   const float* quat;
 };
 
+// One Gaussian's mean, log-scale and quaternion, loaded together.
+struct GaussRec {
+  float3 mean, ls;
+  float4 q;
+};
+
+__device__ __forceinline__ GaussRec load_rec(const MapK& g, int i) {
+  GaussRec r;
+  r.mean = make_float3(__ldg(g.mean + 3 * (size_t)i), __ldg(g.mean + 3 * (size_t)i + 1), __ldg(g.mean + 3 * (size_t)i + 2));
+  r.ls = make_float3(__ldg(g.log_scale + 3 * (size_t)i), __ldg(g.log_scale + 3 * (size_t)i + 1),
+                     __ldg(g.log_scale + 3 * (size_t)i + 2));
+  r.q = __ldg(reinterpret_cast<const float4*>(g.quat) + i);
+  return r;
+}
+
 // Sigma = R(q) diag(exp(2 log_scale)) R(q)^T as (xx, xy, xz, yy, yz, zz).
-__device__ __forceinline__ void gaussian_cov(const MapK& g, int i, float S[6]) {
-  float qw = g.quat[4 * (size_t)i], qx = g.quat[4 * (size_t)i + 1], qy = g.quat[4 * (size_t)i + 2],
-        qz = g.quat[4 * (size_t)i + 3];
+__device__ __forceinline__ void gaussian_cov(const GaussRec& g, float S[6]) {
+  float qw = g.q.x, qx = g.q.y, qy = g.q.z, qz = g.q.w;
   const float nn = qw * qw + qx * qx + qy * qy + qz * qz;
   if (nn > 0.f) {
     const float inv = rsqrtf(nn);
@@ -334,9 +389,7 @@ __device__ __forceinline__ void gaussian_cov(const MapK& g, int i, float S[6]) {
   const float R[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
                       2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
                       2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
-  float s2[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) s2[k] = expf(2.f * g.log_scale[3 * (size_t)i + k]);
+  const float s2[3] = {expf(2.f * g.ls.x), expf(2.f * g.ls.y), expf(2.f * g.ls.z)};
   int e = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -362,7 +415,7 @@ __global__ void __launch_bounds__(256) mahalanobis_kernel(MapK A, MapK Bm, const
                                                           float* __restrict__ T, float max_d2,
                                                           double* __restrict__ sys, double* __restrict__ delta_out,
                                                           int32_t* __restrict__ status) {
-  __shared__ double red[8][kSysN];
+  __shared__ float red[8][kSysN];
   const int64_t M = min(*m_dev, capacity);
   float R[9], t[3];
 #pragma unroll
@@ -377,19 +430,21 @@ __global__ void __launch_bounds__(256) mahalanobis_kernel(MapK A, MapK Bm, const
 #pragma unroll
   for (int k = 0; k < kSysN; ++k) acc[k] = 0.0f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-    const int ka = pairs[2 * i], lb = pairs[2 * i + 1];
-    const float w = weights ? (float)weights[i] : 1.f;
-    const float xb0 = Bm.mean[3 * (size_t)lb], xb1 = Bm.mean[3 * (size_t)lb + 1], xb2 = Bm.mean[3 * (size_t)lb + 2];
+    const int2 kl = __ldg(reinterpret_cast<const int2*>(pairs) + i);
+    const float w = weights ? (float)__ldg(weights + i) : 1.f;
+    // both Gaussians' records are requested at once (one round of gathers)
+    const GaussRec ga = load_rec(A, kl.x), gb = load_rec(Bm, kl.y);
+    const float xb[3] = {gb.mean.x, gb.mean.y, gb.mean.z}, xa[3] = {ga.mean.x, ga.mean.y, ga.mean.z};
     float p[3], r[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      p[a] = R[3 * a] * xb0 + R[3 * a + 1] * xb1 + R[3 * a + 2] * xb2 + t[a];
-      r[a] = p[a] - A.mean[3 * (size_t)ka + a];
+      p[a] = R[3 * a] * xb[0] + R[3 * a + 1] * xb[1] + R[3 * a + 2] * xb[2] + t[a];
+      r[a] = p[a] - xa[a];
     }
     if (max_d2 > 0.f && r[0] * r[0] + r[1] * r[1] + r[2] * r[2] > max_d2) continue;
     float Sa[6], Sb[6];
-    gaussian_cov(A, ka, Sa);
-    gaussian_cov(Bm, lb, Sb);
+    gaussian_cov(ga, Sa);
+    gaussian_cov(gb, Sb);
     // R Sb R^T + Sa
     const float Sbf[9] = {Sb[0], Sb[1], Sb[2], Sb[1], Sb[3], Sb[4], Sb[2], Sb[4], Sb[5]};
     float RS[9];
@@ -438,13 +493,14 @@ __global__ void __launch_bounds__(256) mahalanobis_kernel(MapK A, MapK Bm, const
     float v = acc[k];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) red[warp][k] = (double)v;
+    if (lane == 0) red[warp][k] = v;
   }
   __syncthreads();
-  if (threadIdx.x < kSysN) {
-    double v = 0.0;
+  if (threadIdx.x < kSysN) {  // the CTA's 8 warp sums in float, one double atomic per number
+    float v = 0.0f;
+#pragma unroll
     for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
-    if (v != 0.0) atomicAdd(&sys[threadIdx.x], v);
+    if (v != 0.0f) atomicAdd(&sys[threadIdx.x], (double)v);
   }
   if (!SOLVE) return;
   __shared__ bool s_last;
@@ -462,82 +518,102 @@ __global__ void __launch_bounds__(256) mahalanobis_kernel(MapK A, MapK Bm, const
   *count = 0ull;
 }
 
-// Solve H delta = -g (Cholesky, double) and apply T <- exp(delta^) T (one thread).
+// Solve H delta = -g and apply T <- exp(delta^) T (one thread).  The system
+// is scaled to unit diagonal (H' = D H D, g' = D g, D = diag(H)^-1/2),
+// factorised (Cholesky) and solved in single precision, and the step mapped
+// back (delta = D delta'): double-precision arithmetic is slow on this part
+// (a double Cholesky took about 30 us in one thread), and with a unit
+// diagonal the single-precision solve loses only about cond(H') ulps.
 __device__ void maha_solve_apply(const double* __restrict__ sys, float* __restrict__ T,
                                  double* __restrict__ delta_out, int32_t* __restrict__ status) {
-  double H[6][6], L[6][6] = {}, g[6], d[6];
+  float H[6][6], L[6][6] = {}, g[6], sc[6], d[6];
   int o = 0;
   for (int a = 0; a < 6; ++a)
-    for (int b = a; b < 6; ++b) H[a][b] = H[b][a] = sys[o++];
-  for (int a = 0; a < 6; ++a) g[a] = sys[21 + a];
-  for (int j = 0; j < 6; ++j) {  // Cholesky H = L L^T
-    double s = H[j][j];
+    for (int b = a; b < 6; ++b) H[a][b] = H[b][a] = (float)sys[o++];
+  bool ok = true;
+  for (int a = 0; a < 6; ++a) {
+    ok = ok && H[a][a] > 0.0f;
+    sc[a] = H[a][a] > 0.0f ? 1.0f / sqrtf(H[a][a]) : 0.0f;
+    g[a] = (float)sys[21 + a] * sc[a];
+  }
+  for (int a = 0; a < 6 && ok; ++a)
+    for (int b = 0; b < 6; ++b) H[a][b] *= sc[a] * sc[b];
+  for (int j = 0; j < 6 && ok; ++j) {  // Cholesky H' = L L^T
+    float s = H[j][j];
     for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-    if (!(s > 0.0)) {
-      raise_status(status, SPLAT_ENUMERIC);
-      if (delta_out)
-        for (int a = 0; a < 6; ++a) delta_out[a] = 0.0;
-      return;
+    if (!(s > 0.0f)) {
+      ok = false;
+      break;
     }
-    L[j][j] = sqrt(s);
+    L[j][j] = sqrtf(s);
+    const float r = 1.0f / L[j][j];
     for (int i = j + 1; i < 6; ++i) {
-      double v = H[i][j];
+      float v = H[i][j];
       for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-      L[i][j] = v / L[j][j];
+      L[i][j] = v * r;
     }
   }
-  double z[6];
-  for (int i = 0; i < 6; ++i) {  // L z = -g
-    double v = -g[i];
+  if (!ok) {
+    raise_status(status, SPLAT_ENUMERIC);
+    if (delta_out)
+      for (int a = 0; a < 6; ++a) delta_out[a] = 0.0;
+    return;
+  }
+  float z[6];
+  for (int i = 0; i < 6; ++i) {  // L z = -g'
+    float v = -g[i];
     for (int k = 0; k < i; ++k) v -= L[i][k] * z[k];
     z[i] = v / L[i][i];
   }
-  for (int i = 5; i >= 0; --i) {  // L^T d = z
-    double v = z[i];
+  for (int i = 5; i >= 0; --i) {  // L^T d' = z
+    float v = z[i];
     for (int k = i + 1; k < 6; ++k) v -= L[k][i] * d[k];
     d[i] = v / L[i][i];
   }
+  for (int a = 0; a < 6; ++a) d[a] *= sc[a];
   if (delta_out)
-    for (int a = 0; a < 6; ++a) delta_out[a] = d[a];
+    for (int a = 0; a < 6; ++a) delta_out[a] = (double)d[a];
   // exp(d^): R by Rodrigues, t = V rho
-  const double px = d[3], py = d[4], pz = d[5];
-  const double th2 = px * px + py * py + pz * pz, th = sqrt(th2);
-  double a1, b1, c1;  // sin(th)/th, (1 - cos)/th^2, (th - sin)/th^3
-  if (th < 1e-6) {
-    a1 = 1.0 - th2 / 6.0;
-    b1 = 0.5 - th2 / 24.0;
-    c1 = 1.0 / 6.0 - th2 / 120.0;
+  const float px = d[3], py = d[4], pz = d[5];
+  const float th2 = px * px + py * py + pz * pz, th = sqrtf(th2);
+  float a1, b1, c1;  // sin(th)/th, (1 - cos)/th^2, (th - sin)/th^3
+  if (th < 0.1f) {  // series to th^4 (next terms below 3e-10; the closed forms cancel here)
+    a1 = 1.0f - th2 * (1.0f / 6.0f) * (1.0f - th2 * (1.0f / 20.0f));
+    b1 = 0.5f - th2 * (1.0f / 24.0f) * (1.0f - th2 * (1.0f / 30.0f));
+    c1 = (1.0f / 6.0f) - th2 * (1.0f / 120.0f) * (1.0f - th2 * (1.0f / 42.0f));
   } else {
-    a1 = sin(th) / th;
-    b1 = (1.0 - cos(th)) / th2;
-    c1 = (th - sin(th)) / (th2 * th);
+    float sn, cs;
+    sincosf(th, &sn, &cs);
+    a1 = sn / th;
+    b1 = (1.0f - cs) / th2;
+    c1 = (th - sn) / (th2 * th);
   }
-  const double K[9] = {0.0, -pz, py, pz, 0.0, -px, -py, px, 0.0};
-  double K2[9], E[16];
+  const float K[9] = {0.0f, -pz, py, pz, 0.0f, -px, -py, px, 0.0f};
+  float K2[9], E[16];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
   for (int i = 0; i < 3; ++i) {
     for (int j = 0; j < 3; ++j) {
-      const double I = i == j ? 1.0 : 0.0;
+      const float I = i == j ? 1.0f : 0.0f;
       E[4 * i + j] = I + a1 * K[3 * i + j] + b1 * K2[3 * i + j];
     }
-    double tv = 0.0;
+    float tv = 0.0f;
     for (int j = 0; j < 3; ++j) {
-      const double I = i == j ? 1.0 : 0.0;
+      const float I = i == j ? 1.0f : 0.0f;
       tv += (I + b1 * K[3 * i + j] + c1 * K2[3 * i + j]) * d[j];
     }
     E[4 * i + 3] = tv;
   }
-  E[12] = E[13] = E[14] = 0.0;
-  E[15] = 1.0;
-  double out[16];
+  E[12] = E[13] = E[14] = 0.0f;
+  E[15] = 1.0f;
+  float out[16];
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
-      double v = 0.0;
-      for (int k = 0; k < 4; ++k) v += E[4 * i + k] * (double)T[4 * k + j];
+      float v = 0.0f;
+      for (int k = 0; k < 4; ++k) v += E[4 * i + k] * T[4 * k + j];
       out[4 * i + j] = v;
     }
-  for (int k = 0; k < 16; ++k) T[k] = (float)out[k];
+  for (int k = 0; k < 16; ++k) T[k] = out[k];
 }
 
 __global__ void mahalanobis_step_kernel(const double* __restrict__ sys, float* __restrict__ T,
@@ -644,6 +720,28 @@ static size_t carve_prune(int64_t n, char* base, PruneWs* w) {
   return off;
 }
 
+// Persistent grid of the SSIM statistics kernel: resident CTAs per SM
+// (dynamic shared memory above 48 KB is opted into once per device) x SMs,
+// at most one CTA per block.
+static int ssim_grid(int nblk, int* gf) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(SPLAT_ECUDA, "splat_loss_consensus: no current device");
+  static std::atomic<unsigned long long> attr_done{0};
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_done.load() & bit)) {
+    if (cudaFuncSetAttribute(ssim_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SsFwdSmem)) !=
+        cudaSuccess)
+      return fail(SPLAT_ECUDA, "splat_loss_consensus: shared memory opt-in failed");
+    attr_done.fetch_or(bit);
+  }
+  int sms = 152, of = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&of, ssim_fwd_kernel, 256, sizeof(SsFwdSmem)) != cudaSuccess)
+    return fail(SPLAT_ECUDA, "splat_loss_consensus: occupancy query failed");
+  *gf = std::max(1, std::min(nblk, std::max(1, of) * sms));
+  return SPLAT_OK;
+}
+
 }  // namespace splat
 
 using namespace splat;
@@ -671,15 +769,19 @@ extern "C" int splat_loss_consensus(const float* rgb, const float* depth, const 
   if (w_ssim == 0.f) return launch_loss_l1(rgb, depth, target_rgb, target_depth, npix, sc, sd, d_rgb, d_depth, loss, s);
   int rc;
   const SsimWin win = ssim_window();
-  const dim3 grid((unsigned)((width + kSsTX - 1) / kSsTX), (unsigned)((height + kSsTY - 1) / kSsTY));
+  const int nbx = (width + kSsTX - 1) / kSsTX, nblk = nbx * ((height + kSsTY - 1) / kSsTY);
   float* abc = static_cast<float*>(ws);
   const float inv = 1.0f / (float)(3 * npix);
+  int gf = 0;
+  if ((rc = ssim_grid(nblk, &gf))) return rc;
   SPLAT_LAUNCH("ssim_fwd_kernel", s,
-               ssim_fwd_kernel<<<grid, 256, 0, s>>>(rgb, target_rgb, depth, target_depth, height, width, win,
-                                                    w_ssim * inv, inv, sc, sd, d_rgb, d_depth, abc, loss));
+               ssim_fwd_kernel<<<gf, 256, sizeof(SsFwdSmem), s>>>(rgb, target_rgb, depth, target_depth, height, width,
+                                                                  nbx, nblk, win, w_ssim * inv, inv, sc, sd, d_rgb,
+                                                                  d_depth, abc, loss));
   if ((rc = check_launch("ssim_fwd_kernel"))) return rc;
+  const dim3 grid2((unsigned)nbx, (unsigned)((height + kSsTY - 1) / kSsTY));
   SPLAT_LAUNCH("ssim_bwd_kernel", s,
-               ssim_bwd_kernel<<<grid, 256, 0, s>>>(rgb, target_rgb, height, width, win, -w_ssim * inv, abc, d_rgb));
+               ssim_bwd_kernel<<<grid2, 256, 0, s>>>(rgb, target_rgb, height, width, win, -w_ssim * inv, abc, d_rgb));
   return check_launch("ssim_bwd_kernel");
 }
 
@@ -692,6 +794,8 @@ extern "C" int splat_mahalanobis_system(const splat_gaussians* map_a, const spla
   if ((map_a->n > 0 && (!map_a->mean || !map_a->log_scale || !map_a->quat)) ||
       (map_b->n > 0 && (!map_b->mean || !map_b->log_scale || !map_b->quat)))
     return fail(SPLAT_EINVAL, "splat_mahalanobis_system: null map array");
+  if (!aligned16(map_a->quat) || !aligned16(map_b->quat) || (reinterpret_cast<uintptr_t>(pairs) & 7u) != 0)
+    return fail(SPLAT_EINVAL, "splat_mahalanobis_system: quaternions not 16-byte or pairs not 8-byte aligned");
   if (capacity == 0) return SPLAT_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const MapK A{map_a->mean, map_a->log_scale, map_a->quat}, Bm{map_b->mean, map_b->log_scale, map_b->quat};
@@ -713,6 +817,8 @@ extern "C" int splat_mahalanobis_system_step(const splat_gaussians* map_a, const
   if ((map_a->n > 0 && (!map_a->mean || !map_a->log_scale || !map_a->quat)) ||
       (map_b->n > 0 && (!map_b->mean || !map_b->log_scale || !map_b->quat)))
     return fail(SPLAT_EINVAL, "splat_mahalanobis_system_step: null map array");
+  if (!aligned16(map_a->quat) || !aligned16(map_b->quat) || (reinterpret_cast<uintptr_t>(pairs) & 7u) != 0)
+    return fail(SPLAT_EINVAL, "splat_mahalanobis_system_step: quaternions not 16-byte or pairs not 8-byte aligned");
   if ((reinterpret_cast<uintptr_t>(sys) & 7u) != 0) return fail(SPLAT_EINVAL, "splat_mahalanobis_system_step: sys");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const MapK A{map_a->mean, map_a->log_scale, map_a->quat}, Bm{map_b->mean, map_b->log_scale, map_b->quat};

@@ -313,8 +313,10 @@ __device__ __forceinline__ void project_adjoint_one(const GaussiansK& g, const C
   }
 }
 
-// Accumulate one Gaussian's gradients into the gradient arrays.
+// Accumulate one Gaussian's gradients into the gradient arrays (none when
+// the arrays are null: the pose gradient alone is wanted).
 __device__ __forceinline__ void add_grads(const GradK& out, int64_t i, const Grad14& o) {
+  if (!out.mean) return;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     out.mean[3 * i + k] += o.mean[k];

@@ -933,16 +933,18 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
 extern "C" int splat_project_bwd(const splat_gaussians* g, const splat_projected* proj, const splat_camera* cam,
                                  const float* w2c, const float* grad2d, const splat_gaussians_grad* out,
                                  float* d_pose, float* d2d, splat_stream_t stream) {
-  if (!g || !cam || !w2c || !grad2d || !out) return fail(SPLAT_EINVAL, "splat_project_bwd: null argument");
+  if (!g || !cam || !w2c || !grad2d || (!out && !d_pose && !d2d))
+    return fail(SPLAT_EINVAL, "splat_project_bwd: null argument");
   int rc = check_proj(proj, g->n, "splat_project_bwd");
   if (rc) return rc;
-  if (g->n < 0 || (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !out->mean ||
-                                !out->log_scale || !out->quat || !out->opacity_logit || !out->rgb)) ||
+  if (g->n < 0 || (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit)) ||
+      (g->n > 0 && out && (!out->mean || !out->log_scale || !out->quat || !out->opacity_logit || !out->rgb)) ||
       !aligned16(g->quat) || !aligned16(grad2d))
     return fail(SPLAT_EINVAL, "splat_project_bwd: bad gaussian or gradient arrays");
   if (g->n > 0 && !proj->radius) return fail(SPLAT_EINVAL, "splat_project_bwd: proj->radius is null");
   GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
-  GradK gr{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};
+  GradK gr{};  // all null without `out`: the pose (and d2d) only
+  if (out) gr = GradK{out->mean, out->log_scale, out->quat, out->opacity_logit, out->rgb};
   return launch_project_bwd(gk, make_camk(*cam), w2c, proj->conic, proj->radius, grad2d, kGradStride, gr, d_pose, d2d,
                             reinterpret_cast<cudaStream_t>(stream));
 }

@@ -26,7 +26,9 @@ class FrameBuffers:
     """Device buffers of one view: projection, sorted lists, image, workspaces."""
 
     def __init__(self, n: int, cam: Camera, device, capacity: int | None = None, want_keys: bool = False,
-                 want_used: bool = False):
+                 want_used: bool = False, status=None):
+        """`status`: a device int32[1] to use as the sticky capacity status
+        (kept by an owner that outlives the buffers), or None for a new one."""
         self.n, self.cam, self.device = n, cam, device
         H, W = cam.height, cam.width
         f, i = dict(dtype=torch.float32, device=device), dict(dtype=torch.int32, device=device)
@@ -41,7 +43,7 @@ class FrameBuffers:
         # the tile schedule (heaviest first) that the forward fills for the backward
         self.schedule = torch.zeros(B.splat_tile_schedule_size(cam.n_tiles) // 4, dtype=torch.int32, device=device)
         self.k_dev = torch.zeros(1, dtype=torch.int64, device=device)
-        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device) if status is None else status
         self.want_keys = want_keys
         self.capacity = 0
         self._alloc(capacity if capacity else max(1024, 16 * n))

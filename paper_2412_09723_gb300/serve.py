@@ -2,16 +2,22 @@
 resident agents, with continuous batching (the asynchronous, parallel intra-
 and inter-agent processing of Sec. 3.2 / 3.6, on one GPU).
 
-* Residency.  Every admitted agent's map, Adam state, pose and work buffers
-  live on the device and are charged against an HBM budget.  When a request
-  arrives for an agent that is not resident and the budget is full, idle
-  agents are swapped out to pinned host memory -- first those with no request
-  waiting, least recently used first.  Swaps never block the loop: a
-  swap-out's copies run on a copy stream after the agent's last step and its
-  memory is released (and uncharged) when they are done; a swap-in allocates
-  the agent's buffers and copies its state in on the same stream, and the
-  agent's next step waits for that stream on the device, so the request is
-  batched at once.
+* Residency, in two tiers.  An agent's state (map, Adam moments, pose) and
+  its per-step buffers (frame buffers, observation and gradient images,
+  association buffers: most of its footprint) are charged against an HBM
+  budget separately.  When a request needs room, idle agents first give up
+  their per-step buffers (nothing is copied: they are re-made, uninitialised
+  work space, when the agent is next stepped), and only then are idle agents'
+  states swapped out to pinned host memory -- in both tiers agents with no
+  request waiting go first, least recently used first.  Nothing blocks the
+  loop: released buffers are kept alive until the agent's last step has
+  finished on the device; a swap-out's copies run on a copy stream after that
+  step and its memory is uncharged when they are done; a swap-in, or the
+  re-made buffers of a resident state, are allocated and filled on the same
+  stream, and the agent's next step waits for that stream on the device, so
+  the request is batched at once.  Mapping steps take the map's Adam step
+  inside the projection adjoint and tracking steps form the pose gradient
+  alone, so no agent holds per-parameter gradient arrays.
 * Continuous batching.  At every tick the loop admits the requests that have
   arrived, takes up to `max_batch` ready requests of distinct agents (oldest
   first; an agent has at most one request in flight, so its state advances in
@@ -82,6 +88,8 @@ class _AgentSlot:
         self.out_loss = torch.empty(1, dtype=torch.float32, pin_memory=True)
         self.out_w2c = torch.empty(4, 4, dtype=torch.float32, pin_memory=True)
         self.graphs = {}  # request kind -> captured single-agent step of the resident agent
+        self.state_bytes = 0  # device bytes of the state / of the per-step buffers (last measured)
+        self.scratch_bytes = 0
         self.loading = None  # copy-stream event of a swap-in that may still run
         self.last_event = None  # completion event of the agent's last launched step
         self.evicting = None  # (agent, event): a swap-out whose copies may still run
@@ -89,29 +97,22 @@ class _AgentSlot:
         self.side = None  # the agent's side stream, kept across swaps
 
 
-def _agent_bytes(a: Agent) -> int:
+def _bytes(tensors) -> int:
+    """Device bytes of distinct storages among `tensors`."""
     seen = set()
     total = 0
-
-    def add(t):
-        nonlocal total
-        if isinstance(t, torch.Tensor) and t.is_cuda and t.data_ptr() not in seen:
-            seen.add(t.data_ptr())
-            total += t.numel() * t.element_size()
-
-    for v in vars(a).values():
-        if isinstance(v, torch.Tensor):
-            add(v)
-        elif isinstance(v, (list, tuple)):
-            for t in v:
-                add(t)
-    fb = a.fb
-    for d in (fb.proj, fb.image):
-        for t in d.values():
-            add(t)
-    for t in (fb.ranges, fb.k_dev, fb.status, fb.vals, fb.keys, fb.bin_ws, fb.bwd_ws):
-        add(t)
+    for t in tensors:
+        if isinstance(t, torch.Tensor) and t.is_cuda:
+            st = t.untyped_storage()
+            if st.data_ptr() not in seen:
+                seen.add(st.data_ptr())
+                total += st.nbytes()
     return total
+
+
+def _agent_bytes(a: Agent) -> tuple[int, int]:
+    """(state bytes, per-step buffer bytes) of a resident agent."""
+    return _bytes(a.state_tensors()), (_bytes(a.scratch_tensors()) if a.has_scratch else 0)
 
 
 class Server:
@@ -131,6 +132,8 @@ class Server:
         self.agent_streams = [[torch.cuda.Stream(device=device) for _ in range(self.max_batch)]
                               for _ in range(n_streams)]
         self.copy_stream = torch.cuda.Stream(device=device)  # swaps in and out
+        self.releasing = []  # (tensors, event, bytes): per-step buffers given up, alive until the event
+        self.releases = 0
 
     def reset(self, budget: int | None = None):
         """Drop every agent's device state (they restart from their initial
@@ -145,6 +148,8 @@ class Server:
             slot.last_used = 0.0
             slot.loading = slot.last_event = slot.evicting = None
             slot.evict_bytes = 0
+        self.releasing = []
+        self.releases = 0
         self.used = 0
         self.swaps = 0
         if budget is not None:
@@ -154,13 +159,21 @@ class Server:
 
     # -- agents and residency -------------------------------------------------
     def add_agent(self, scene, w2c, cam, frames, cfg: StepConfig | None = None) -> int:
-        slot = _AgentSlot(len(self.slots), scene, w2c, cam, frames, cfg or StepConfig())
+        slot = _AgentSlot(len(self.slots), scene, w2c, cam, frames, cfg or StepConfig(grads=False))
         self.slots.append(slot)
         return slot.aid
 
     def _poll_swaps(self):
         """Release the memory (and the budget) of swap-outs whose copies are
-        done, and forget swap-ins that have landed."""
+        done and of given-up per-step buffers whose last step is done, and
+        forget swap-ins that have landed."""
+        keep = []
+        for held, ev, nbytes in self.releasing:
+            if ev is None or ev.query():
+                self.used -= nbytes
+            else:
+                keep.append((held, ev, nbytes))
+        self.releasing = keep
         for slot in self.slots:
             if slot.evicting is not None and slot.evicting[1].query():
                 slot.evicting = None
@@ -188,7 +201,7 @@ class Server:
         ev.record(cs)
         slot.evicting = (a, ev)  # the agent (and its memory) lives until the copies are done
         slot.evict_bytes = slot.bytes
-        slot.capacity = a.fb.capacity
+        slot.capacity = a.fb.capacity if a.has_scratch else a.capacity
         slot.agent = None
         slot.graphs = {}
         slot.bytes = 0
@@ -215,20 +228,61 @@ class Server:
             if slot.capacity is None:
                 slot.capacity = a.fb.capacity
         slot.agent = a
-        slot.bytes = slot.footprint if slot.footprint else _agent_bytes(a)
-        slot.footprint = slot.bytes
+        if not slot.footprint:
+            slot.state_bytes, slot.scratch_bytes = _agent_bytes(a)
+            slot.footprint = slot.state_bytes + slot.scratch_bytes
+        slot.bytes = slot.footprint
         self.used += slot.bytes
         slot.last_used = now
 
-    def _make_room(self, need: int, waiting) -> bool:
-        """Start swap-outs of idle residents until `need` bytes fit the budget
-        once they are done: first agents with no request waiting, least
-        recently used first.  True when the bytes fit now."""
+    def _release_scratch(self, slot: _AgentSlot):
+        """Give up an idle agent's per-step buffers; they stay alive (and
+        charged) until its last launched step is done."""
+        held = slot.agent.release_scratch()
+        self.releasing.append((held, slot.last_event, slot.scratch_bytes))
+        self.releases += 1
+        slot.bytes -= slot.scratch_bytes
+        slot.graphs = {}
+
+    def _remake_scratch(self, slot: _AgentSlot, now: float):
+        """Re-make the per-step buffers of a resident state on the copy
+        stream (the next step waits for it)."""
+        cs = self.copy_stream
+        if slot.loading is not None:
+            cs.wait_event(slot.loading)
+        with torch.cuda.stream(cs):
+            slot.agent.make_scratch(slot.agent.capacity)
+        ev = torch.cuda.Event()
+        ev.record(cs)
+        slot.loading = ev
+        slot.bytes += slot.scratch_bytes
+        self.used += slot.scratch_bytes
+        slot.last_used = now
+
+    def _make_room(self, need: int, waiting, keep=None) -> bool:
+        """Free memory of idle residents until `need` bytes fit the budget
+        once it is released: first their per-step buffers, then -- only when
+        the resident states and `need` alone exceed the budget -- their states
+        (swap-outs); in each tier agents with no request waiting first, least
+        recently used first; `keep` (the slot being admitted) is spared.
+        True when the bytes fit now."""
         if self.used + need <= self.budget:
             return True
-        freeing = sum(sl.evict_bytes for sl in self.slots if sl.evicting is not None)
-        idle = [sl for sl in self.slots if sl.agent is not None and not sl.busy]
-        for sl in sorted(idle, key=lambda x: (x.aid in waiting, x.last_used)):
+        freeing = (sum(sl.evict_bytes for sl in self.slots if sl.evicting is not None)
+                   + sum(b for _, _, b in self.releasing))
+        order = lambda x: (x.aid in waiting, x.last_used)  # noqa: E731
+        idle = [sl for sl in self.slots if sl.agent is not None and not sl.busy and sl is not keep]
+        for sl in sorted((sl for sl in idle if sl.agent.has_scratch), key=order):
+            if self.used - freeing + need <= self.budget:
+                return False
+            freeing += sl.scratch_bytes
+            self._release_scratch(sl)
+        # states go only when the resident states alone leave no room: else
+        # the per-step buffers of the agents at work free up when they finish
+        states = sum(sl.state_bytes for sl in self.slots if sl.agent is not None)
+        if states + need <= self.budget:
+            return False
+        for sl in sorted(idle, key=order):
             if self.used - freeing + need <= self.budget:
                 break
             freeing += sl.bytes
@@ -239,6 +293,11 @@ class Server:
         """Make the agent resident (or loading) if the budget allows now;
         otherwise start making room and report False."""
         if slot.agent is not None:
+            if slot.agent.has_scratch:
+                return True
+            if not self._make_room(slot.scratch_bytes, waiting, keep=slot):
+                return False
+            self._remake_scratch(slot, now)
             return True
         need = slot.footprint
         if need and need > self.budget:
@@ -247,7 +306,7 @@ class Server:
             return False
         self._start_swap_in(slot, now)
         if not need and self.used > self.budget:  # first residency, size learnt now: make room after the fact
-            self._make_room(0, waiting)
+            self._make_room(0, waiting, keep=slot)
         return True
 
     def prepare(self, size_capacity: bool = True):
@@ -265,12 +324,13 @@ class Server:
                 slot.agent.size_capacity(1.5)
                 slot.capacity = slot.agent.fb.capacity
                 self.used -= slot.bytes
-                slot.bytes = slot.footprint = _agent_bytes(slot.agent)
+                slot.state_bytes, slot.scratch_bytes = _agent_bytes(slot.agent)
+                slot.bytes = slot.footprint = slot.state_bytes + slot.scratch_bytes
                 self.used += slot.bytes
             torch.cuda.synchronize()
         if self.single_graphs:  # the agents resident now get their single-request graphs
             for slot in self.slots:
-                if slot.agent is not None:
+                if slot.agent is not None and slot.agent.has_scratch:
                     self._capture(slot)
 
     def _capture(self, slot: _AgentSlot):
