@@ -8,10 +8,13 @@
 // single-precision pairs.  The tile's list is staged through shared memory in batches of BATCH
 // Gaussians (position / depth / opacity, the quadratic form's coefficients
 // A = -a/2, B = -b, C = -c/2 with the exponent cut, colour, id) and every
-// thread walks the batch in order.  A pair whose exponent lies below the
-// Gaussian's cut (set by the projection so that opacity * exp(power) < 1/255
-// is certain) is skipped before the exponential is evaluated; this changes no
-// result.  A tile ends as soon as all of its pixels have reached the
+// thread walks the batch in order, two visits per iteration: both exponents
+// and exponentials are formed first (two independent dependency chains that
+// overlap; a warp alone on its scheduler late in the launch is latency-bound),
+// then the two compositing steps in list order.  A pixel whose exponent lies
+// below the Gaussian's cut (set by the projection so that opacity *
+// exp(power) < 1/255 is certain) or above 0 skips the Gaussian; this changes
+// no result.  A tile ends as soon as all of its pixels have reached the
 // transmittance stop.  No atomics.
 //
 // Backward: the same pixels per thread and warp, again in packed pairs.  The
@@ -31,7 +34,9 @@
 // the sums are collected per CTA in shared memory and added to global memory
 // with three float4 atomics per Gaussian per CTA.  A warp skips a visit, or
 // stops short in one, only when none of its lanes takes part (warp-uniform
-// tests: a lane that does not take part computes with zero weights).
+// tests: a lane that does not take part computes with zero weights).  As in
+// the forward, a warp forms the exponentials of two visits before it takes
+// the two visits in walk order.
 //
 // Persistent launches: a grid of (CTAs per SM) x (SMs) CTAs takes (view, tile)
 // work items from one atomic ticket counter until the items run out; no CTA
@@ -252,18 +257,22 @@ __device__ __forceinline__ float2 exp_core2(float2 x) {
 }
 #endif
 
-// One front-to-back compositing step of the thread's two pixels (the
+// The exponent of one staged Gaussian at the thread's two pixels (the
 // specified order).  nfy = (-fy0, -fy1).
-__device__ __forceinline__ void composite_step2(FwdPix& q, const float4 xo, const float4 qd, float fx, float2 nfy,
-                                                const float4* cidp, int32_t pos) {
+__device__ __forceinline__ float2 fwd_power(const float4 xo, const float4 qd, float fx, float2 nfy) {
   const float dx = xo.x - fx;
   const float2 dy = __fadd2_rn(bcast(xo.y), nfy);
   const float2 inner = __ffma2_rn(bcast(qd.x), bcast(dx), __fmul2_rn(bcast(qd.y), dy));
-  const float2 power = __ffma2_rn(__fmul2_rn(bcast(qd.z), dy), dy, __fmul2_rn(bcast(dx), inner));
+  return __ffma2_rn(__fmul2_rn(bcast(qd.z), dy), dy, __fmul2_rn(bcast(dx), inner));
+}
+
+// One front-to-back compositing step of the thread's two pixels, given the
+// exponent and its exponential (evaluated whatever the tests decide).
+__device__ __forceinline__ void composite_apply(FwdPix& q, const float4 xo, const float4 qd, float2 power, float2 G,
+                                                const float4* cidp, int32_t pos) {
   bool in0 = !q.done[0] && !(power.x > 0.0f || power.x < qd.w);
   bool in1 = !q.done[1] && !(power.y > 0.0f || power.y < qd.w);
   if (!(in0 || in1)) return;
-  const float2 G = exp_core2(power);
   const float2 raw = __fmul2_rn(bcast(xo.w), G);
   const float2 alpha = make_float2(fminf(kAlphaCap, raw.x), fminf(kAlphaCap, raw.y));
   in0 = in0 && !(alpha.x < kAlphaMin);
@@ -399,9 +408,22 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
     __syncthreads();
     const int32_t base = (int32_t)(start - rg.x);
     const int nl = build_warp_list(sm.wmask, sm.wlist[warp], cnt, warp);
-    for (int e = 0; e < nl && !(q.done[0] && q.done[1]); ++e) {
+    // two visits per iteration: their exponentials are independent chains
+    // that overlap; the compositing stays in list order
+    int e = 0;
+    for (; e + 1 < nl && !(q.done[0] && q.done[1]); e += 2) {
+      const int j0 = sm.wlist[warp][e], j1 = sm.wlist[warp][e + 1];
+      const float4 xo0 = sm.xyzo[j0], qd0 = sm.quad[j0], xo1 = sm.xyzo[j1], qd1 = sm.quad[j1];
+      const float2 p0 = fwd_power(xo0, qd0, fx, nfy), p1 = fwd_power(xo1, qd1, fx, nfy);
+      const float2 G0 = exp_core2(p0), G1 = exp_core2(p1);
+      composite_apply(q, xo0, qd0, p0, G0, &sm.cid[j0], base + j0);
+      composite_apply(q, xo1, qd1, p1, G1, &sm.cid[j1], base + j1);
+    }
+    if (e < nl && !(q.done[0] && q.done[1])) {
       const int j = sm.wlist[warp][e];
-      composite_step2(q, sm.xyzo[j], sm.quad[j], fx, nfy, &sm.cid[j], base + j);
+      const float4 xo = sm.xyzo[j], qd = sm.quad[j];
+      const float2 p = fwd_power(xo, qd, fx, nfy);
+      composite_apply(q, xo, qd, p, exp_core2(p), &sm.cid[j], base + j);
     }
   }
   const LossK& L = V.l1;
@@ -532,17 +554,22 @@ struct BwdPair {
 // whether either pixel took part.  A pixel that does not take part keeps T
 // and Q (its alpha and weight are 0) and adds nothing (its G and raw opacity
 // are set to 0).
-template <bool FRONT>
-__device__ __forceinline__ bool adjoint_step2(BwdPair& q, int pos, const float4 xo, const float4 qd, float c0,
-                                              float c1, float c2, float (&v)[10]) {
-  const float dx = xo.x - q.fx;
-  const float2 dy = __fadd2_rn(bcast(xo.y), q.nfy);
+// The exponent of one staged Gaussian at the pair's pixels, with dx and dy.
+__device__ __forceinline__ float2 adjoint_power(const BwdPair& q, const float4 xo, const float4 qd, float& dx,
+                                                float2& dy) {
+  dx = xo.x - q.fx;
+  dy = __fadd2_rn(bcast(xo.y), q.nfy);
   const float2 inner = __ffma2_rn(bcast(qd.x), bcast(dx), __fmul2_rn(bcast(qd.y), dy));
-  const float2 power = __ffma2_rn(__fmul2_rn(bcast(qd.z), dy), dy, __fmul2_rn(bcast(dx), inner));
+  return __ffma2_rn(__fmul2_rn(bcast(qd.z), dy), dy, __fmul2_rn(bcast(dx), inner));
+}
+
+template <bool FRONT>
+__device__ __forceinline__ bool adjoint_step2(BwdPair& q, int pos, const float4 xo, const float4 qd, float dx,
+                                              float2 dy, float2 power, float2 G, float c0, float c1, float c2,
+                                              float (&v)[10]) {
   bool in0 = pos < q.last[0] && !(power.x > 0.0f || power.x < qd.w);
   bool in1 = pos < q.last[1] && !(power.y > 0.0f || power.y < qd.w);
   if (!__any_sync(0xffffffffu, in0 || in1)) return false;
-  const float2 G = exp_core2(power);
   const float2 raw = __fmul2_rn(bcast(xo.w), G);
   float2 alpha = make_float2(fminf(kAlphaCap, raw.x), fminf(kAlphaCap, raw.y));
   in0 = in0 && !(alpha.x < kAlphaMin);
@@ -713,21 +740,23 @@ __device__ __forceinline__ void bwd_part(const ViewK& V, int tile, BwdShared<BAT
     const int nl = build_warp_list(sm.st.wmask, sm.st.wlist[warp], cnt, warp);
     float* rb = sm.red[warp];
     int nslot = 0, j0 = 0, j1 = 0, j2 = 0;
-    for (int e0 = 0; e0 < nl; ++e0) {
-      const int e = FRONT ? e0 : nl - 1 - e0;
-      const int j = sm.st.wlist[warp][e];
-      const int pos = start + j;
-      if (pos >= wlast) {  // warp-uniform: no pixel of this warp reaches pos
-        if (FRONT) break;  // nor any later position
-        continue;
-      }
+    // the warp's visits are the staged positions before wlast: a prefix of
+    // the ascending list, walked forwards (front part) or backwards
+    int nv = 0;
+    for (int k0 = 0; k0 < nl; k0 += 32) {
+      const int k = k0 + lane;
+      const unsigned ok = __ballot_sync(0xffffffffu, k < nl && start + (int)sm.st.wlist[warp][k] < wlast);
+      nv += __popc(ok);
+      if (ok != 0xffffffffu) break;
+    }
+    auto visit = [&](int j, float dx, float2 dy, float2 power, float2 G) {
       const float4 xo = sm.st.xyzo[j];
       const float4 qd = sm.st.quad[j];
       const float4 cd = sm.st.cid[j];
       float v[10];
 #pragma unroll
       for (int k = 0; k < 10; ++k) v[k] = -0.0f;  // -0 + x = x exactly: the first sum folds away
-      if (adjoint_step2<FRONT>(q, pos, xo, qd, cd.x, cd.y, cd.z, v)) {  // warp-uniform
+      if (adjoint_step2<FRONT>(q, start + j, xo, qd, dx, dy, power, G, cd.x, cd.y, cd.z, v)) {  // warp-uniform
         float* row = rb + nslot * 10 * kRedRow + lane;
 #pragma unroll
         for (int k = 0; k < 10; ++k) row[k * kRedRow] = v[k];
@@ -739,6 +768,19 @@ __device__ __forceinline__ void bwd_part(const ViewK& V, int tile, BwdShared<BAT
           nslot = 0;
         }
       }
+    };
+    // two visits per iteration: both exponentials first (independent chains)
+    for (int i = 0; i < nv; i += 2) {
+      const bool two = i + 1 < nv;  // warp-uniform
+      const int ja = sm.st.wlist[warp][FRONT ? i : nv - 1 - i];
+      const int jb = two ? sm.st.wlist[warp][FRONT ? i + 1 : nv - 2 - i] : ja;
+      float dxa, dxb;
+      float2 dya, dyb;
+      const float2 pa = adjoint_power(q, sm.st.xyzo[ja], sm.st.quad[ja], dxa, dya);
+      const float2 pb = adjoint_power(q, sm.st.xyzo[jb], sm.st.quad[jb], dxb, dyb);
+      const float2 Ga = exp_core2(pa), Gb = exp_core2(pb);
+      visit(ja, dxa, dya, pa, Ga);
+      if (two) visit(jb, dxb, dyb, pb, Gb);
     }
     if (nslot) flush_visits(rb, sm.acc, nslot, j0, j1, j2, lane);
     __syncthreads();
