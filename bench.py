@@ -66,10 +66,11 @@ def _parse():
     ap.add_argument("--no-next", action="store_true", help="skip the consensus-loss / Mahalanobis / pruning timings")
     ap.add_argument("--serve-seconds", type=float, default=30.0,
                     help="length of the 30 Hz Poisson request trace (served and plain)")
-    ap.add_argument("--ncu-case", choices=["step", "batch", "next", "align"], default=None,
+    ap.add_argument("--ncu-case", choices=["step", "step-fused", "batch", "next", "align"], default=None,
                     help="run one workload eagerly (warmup + steps launches, no timing, no JSON line) for a "
-                         "profiler to capture: the single-agent step, the batched three-agent step (default "
-                         "shape), the consensus-loss / Mahalanobis / pruning rows, or the two-agent alignment")
+                         "profiler to capture: the single-agent step (two render launches, or one with "
+                         "step-fused), the batched three-agent step (default shape), the consensus-loss / "
+                         "Mahalanobis / pruning rows, or the two-agent alignment")
     return ap.parse_args()
 
 
@@ -654,9 +655,11 @@ def ncu_case(args, dev):
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     n = args.warmup + args.steps
-    if args.ncu_case == "step":
+    if args.ncu_case in ("step", "step-fused"):
+        from paper_2412_09723_gb300.agent import StepConfig
+
         sc, w2c, w2c_target, cam, bg = scenes.workload_track_map(seed=1)
-        agent = Agent(sc, w2c, cam, dev, want_used=True)
+        agent = Agent(sc, w2c, cam, dev, want_used=True, cfg=StepConfig(fused=args.ncu_case == "step-fused"))
         agent.render_observation_from(w2c_target)
         agent.size_capacity(1.5)
         for k in range(n):
@@ -824,6 +827,8 @@ def main():
         ops = OPS_WALK * q_walk + OPS_CONTRIB_BWD * q_used
     elif top == "render_fwd_kernel":
         ops = OPS_WALK * q_walk + OPS_CONTRIB_FWD * q_used
+    elif top == "render_fused_persistent":  # the forward and the screen-space backward in one launch
+        ops = 2 * OPS_WALK * q_walk + (OPS_CONTRIB_FWD + OPS_CONTRIB_BWD) * q_used
     else:
         ops = None
     roofline = None
@@ -842,7 +847,8 @@ def main():
     if breakdown:
         breakdown["_note"] = ("each kernel timed alone (CUDA events around it, every launch on one stream, eager "
                               "steps): the shares partition the serialised step; the timed step overlaps the "
-                              "association and the pose step (side stream) with the backward render")
+                              "association and the pose step (side stream) with the render's backward or the "
+                              "projection adjoint")
 
     # whole-step roofline: algorithmic FP32 ops of both renders against the
     # issue peak, algorithmic bytes of the step against the measured HBM copy

@@ -57,7 +57,7 @@ enum {
   SPLAT_EINVAL = 1,    /* null pointer, bad size or misaligned buffer */
   SPLAT_ECAPACITY = 2, /* (device status) an output buffer was too small */
   SPLAT_ECUDA = 3,     /* a kernel launch or CUDA runtime call failed */
-  SPLAT_ETIMEOUT = 4,  /* reserved: no call returns or raises it (no kernel of this library waits) */
+  SPLAT_ETIMEOUT = 4,  /* (device status) a bounded wait inside a launch gave up (splat_render_fwd_bwd) */
   SPLAT_ENUMERIC = 8   /* (device status) a linear system was not positive definite */
 };
 
@@ -169,20 +169,23 @@ int splat_project(const splat_gaussians *g, const splat_camera *cam, const float
                   const splat_projected *out, splat_stream_t stream);
 
 /*
- * Tile schedule: the order in which the persistent backward render takes a
- * view's tiles, heaviest first, so that it ends on light tiles.  The cost of
- * a tile's adjoint is the number of list positions its pixels walk, which the
- * forward render knows only at its end (it is not the list length: a pixel
- * stops at its last contributor).  Layout: uint32
- * [SPLAT_SCHEDULE_BUCKETS + SPLAT_SCHEDULE_BUCKETS * n_tiles]: bucket counts,
- * then one list of tile ids per bucket; bucket b holds the tiles whose summed
- * contributor counts S have 1 + floor(8 log2 S) = b (in steps of an eighth of
- * an octave; S = 0 in bucket 0; capped at the last bucket).  splat_bin_sort
- * clears the counts, splat_render_fwd_l1 (or a batch forward) fills the
- * lists, splat_render_bwd (or a batch backward) reads them.  The schedule
- * changes only the order of the work: results are the same without it.
+ * Tile schedule: the order in which the renders take a view's tiles, heaviest
+ * first, so that a persistent launch ends on light tiles.  The cost of a
+ * tile is the number of list positions its pixels walk (not the list length:
+ * a pixel stops at its last contributor), which the forward render knows at
+ * its end.  Layout: uint32[1 + 2 n_tiles]:
+ *   [0]                      n_tiles once an order has been written, else 0;
+ *   [1, 1 + n_tiles)         tile ids, heaviest first;
+ *   [1 + n_tiles, 1 + 2 n_tiles)  per-tile cost: the summed contributor counts
+ *                            of the tile's pixels in the last forward render.
+ * The forward render (splat_render_fwd_l1, splat_render_fwd_bwd, a batch
+ * forward) writes the costs; splat_bin_sort rebuilds the order from them
+ * (tiles by cost bucket 1 + floor(8 log2 cost), heaviest bucket first; cost 0
+ * last).  A step's order therefore comes from the previous step's costs, which
+ * barely change between the iterations on one frame.  A zero-filled buffer
+ * holds no order (the natural order is taken).  The schedule changes only the
+ * order of the work: results are the same with or without it.
  */
-#define SPLAT_SCHEDULE_BUCKETS 128
 size_t splat_tile_schedule_size(int32_t n_tiles); /* bytes */
 
 /*
@@ -213,8 +216,8 @@ size_t splat_tile_schedule_size(int32_t n_tiles); /* bytes */
  *   capacity: number of slots in keys/vals (< 2^31)
  *   k_dev:    device int64[1]: receives K, the number of duplicates
  *   ranges:   device uint32[2 * n_tiles]
- *   schedule: a tile schedule (below) or NULL: its bucket counts are set to
- *             zero here, for the forward render to fill
+ *   schedule: a tile schedule (above) or NULL: its order is rebuilt here from
+ *             the costs the last forward render wrote
  *   status:   device int32[1]: set to SPLAT_ECAPACITY when K > capacity (the
  *             sorted lists are then incomplete; resize and call again);
  *             never cleared by the library
@@ -277,8 +280,8 @@ int splat_render_fwd(const splat_projected *proj, const float *rgb, int64_t n,
  * optimisation, Sec. 3.5 steps 3-4).
  *   proj: the splat_project output for this map, camera and pose (its radius
  *     is read: Gaussians it culled get no gradient and are skipped).
- *   schedule: the view's tile schedule as splat_render_fwd_l1 left it, or
- *     NULL for the natural order (the result is the same either way).
+ *   schedule: the view's tile schedule (its order is used), or NULL for the
+ *     natural order (the result is the same either way).
  *   d_rgb [H,W,3], d_depth [H,W], d_sil [H,W] (d_depth, d_sil may be NULL).
  *   fwd: the image of the forward call (t_final, n_contrib are read).
  *   out: Gaussian-parameter gradients, ACCUMULATED (+=); the caller zeroes.
@@ -341,6 +344,13 @@ int splat_project_bwd(const splat_gaussians *g, const splat_projected *proj, con
  *     does not hold for this call).  m, v: device moments of the same shapes.
  *   lr: HOST float[5], the step sizes of mean, log_scale, quat,
  *     opacity_logit, rgb; step: DEVICE int32[1] holding t >= 1.
+ *   seen: device uint32[ceil(n / 32)] or NULL: bit i set when Gaussian i's
+ *     moments may be nonzero; a clear bit PROMISES m = v = 0 for all its
+ *     elements (the caller keeps that true: zeros with zeroed moments, all
+ *     ones when unsure).  The call sets the bits of the kept Gaussians, and
+ *     the culled part then touches only culled Gaussians whose bit is set, so
+ *     a map mostly never optimised costs one bit per Gaussian there (the
+ *     SplaTAM-style optimiser restarts its moments per frame).
  *   proj, cam, w2c, grad2d: as splat_project_bwd.
  * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
  */
@@ -348,18 +358,19 @@ int splat_project_bwd_adam(const splat_gaussians *g, const splat_projected *proj
                            const splat_camera *cam, const float *w2c, const float *grad2d,
                            const splat_gaussians_grad *m, const splat_gaussians_grad *v,
                            const float *lr, float beta1, float beta2, float eps,
-                           const int32_t *step, int32_t culled, float *d_pose,
+                           const int32_t *step, uint32_t *seen, int32_t culled, float *d_pose,
                            splat_stream_t stream);
 
 /*
  * splat_adam_culled -- the zero-gradient Adam step of the Gaussians a
  * projection culled (radius == 0), the other part of splat_project_bwd_adam
- * called with culled = 0; arguments as there, radius from splat_project.
+ * called with culled = 0; arguments (seen included) as there, radius from
+ * splat_project.
  * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
  */
 int splat_adam_culled(const splat_gaussians *g, const int32_t *radius, const splat_gaussians_grad *m,
                       const splat_gaussians_grad *v, const float *lr, float beta1, float beta2,
-                      float eps, const int32_t *step, splat_stream_t stream);
+                      float eps, const int32_t *step, uint32_t *seen, splat_stream_t stream);
 
 /*
  * splat_render_fwd_l1 -- splat_render_fwd with the L1 terms of the loss of
@@ -374,10 +385,8 @@ int splat_adam_culled(const splat_gaussians *g, const int32_t *radius, const spl
  *   l1: descriptor below (device arrays [H,W,3] / [H,W]; loss: device float,
  *   accumulated, the caller zeroes it), or NULL for a render without loss
  *   terms that fills the schedule.
- *   schedule: a tile schedule whose counts splat_bin_sort cleared (each tile
- *     is added to its bucket once), or NULL.  A schedule filled twice without
- *     a clear in between no longer adds up to the number of tiles and is
- *     ignored by the backward (natural order).
+ *   schedule: a tile schedule or NULL: the tiles are taken in its order and
+ *     their costs written to it.
  * Errors: as splat_render_fwd.
  */
 typedef struct {
@@ -393,6 +402,39 @@ int splat_render_fwd_l1(const splat_projected *proj, const float *rgb, int64_t n
                         const uint32_t *vals, const uint32_t *ranges, const splat_camera *cam,
                         const float *bg, const splat_image *out, const splat_l1 *l1,
                         uint32_t *schedule, splat_stream_t stream);
+
+/*
+ * splat_render_fwd_bwd -- splat_render_fwd_l1 followed by the screen-space
+ * adjoint of splat_render_bwd for the L1 gradients it writes, in ONE launch
+ * (the rendering equation of Sec. 3.3 and its adjoint for the map and pose
+ * optimisation of Sec. 3.4 step 4 and Sec. 3.5).  The backward of a tile
+ * needs only that tile's forward outputs and loss gradients, so a tile's
+ * backward starts as soon as its forward has finished, while other tiles are
+ * still rendered: the forward's tail and the second launch's ramp disappear.
+ * The forwards are taken in the schedule's order; the two backward parts of
+ * the tiles follow in the order their forwards finished (a completion queue
+ * in the workspace: a backward item waits, with a bounded number of polls,
+ * for the next finished tile, never for a particular one).
+ *   Arguments as splat_render_fwd_l1 (l1 required: its d_rgb / d_depth are
+ *   the backward's upstream gradients, silhouette gradient 0), then
+ *   status: device int32[1]; SPLAT_ETIMEOUT is raised if a wait gave up (the
+ *     results are then incomplete; no input of this library's own making
+ *     causes it);
+ *   ws: workspace of splat_render_fwd_bwd_workspace_size(n, n_tiles) bytes,
+ *     16-byte aligned; on return its first bytes hold the screen-space
+ *     gradients exactly as splat_render_bwd leaves them in screen-only mode
+ *     ([n,12] float rows), for splat_project_bwd or splat_project_bwd_adam.
+ * Images and loss gradients are bit for bit those of splat_render_fwd_l1;
+ * the screen-space gradients are the same sums as splat_render_bwd's (the
+ * atomics' order, and so the last bits, vary).  The launch is cooperative.
+ * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+size_t splat_render_fwd_bwd_workspace_size(int64_t n, int32_t n_tiles);
+int splat_render_fwd_bwd(const splat_projected *proj, const float *rgb, int64_t n,
+                         const uint32_t *vals, const uint32_t *ranges, const splat_camera *cam,
+                         const float *bg, const splat_image *out, const splat_l1 *l1,
+                         uint32_t *schedule, int32_t *status, void *ws, size_t ws_bytes,
+                         splat_stream_t stream);
 
 /*
  * Several views in one launch (batched differentiable rendering across

@@ -7,8 +7,9 @@ hot path of the method for one frame:
 
   splat_project -> splat_bin_sort -> splat_render_fwd      (render, Sec. 3.3)
      with the L1 terms of Eq. optim (L1 colour + w_depth L1 depth) and their
-     image gradients taken in the same pass (splat_render_fwd_l1)
-  -> splat_render_bwd (screen-space adjoint of the render)
+     image gradients taken in the same pass, and the screen-space adjoint of
+     the render in the same launch (splat_render_fwd_bwd; or two launches:
+     splat_render_fwd_l1, splat_render_bwd)
   -> splat_project_bwd_adam (projection adjoint to every Gaussian parameter
      and the pose, with the map's Adam step in the same launch: mapping,
      Sec. 3.4 step 4; tracking-only steps use splat_project_bwd)
@@ -46,9 +47,17 @@ class StepConfig:
     assoc: bool = True
     t_max: float = 0.5
     bg: tuple = (0.0, 0.0, 0.0)
-    # the culled Gaussians' zero-gradient Adam step on the side stream, beside
-    # the backward render (else inside the fused projection adjoint's launch)
-    culled_beside: bool = False
+    # where the culled Gaussians' zero-gradient Adam step runs: inside the
+    # fused projection adjoint's launch ("adjoint"), or on the side stream
+    # beside the forward render ("forward": it needs only the projection's
+    # radii and fills the render's tail) or beside the backward ("backward")
+    culled_at: str = "adjoint"
+    # the forward render and the screen-space backward in one launch
+    # (splat_render_fwd_bwd), else two (splat_render_fwd_l1, splat_render_bwd).
+    # One launch takes as long as the two at 300k / 640x480, and the
+    # association then waits for both renders instead of overlapping the
+    # backward, so two launches are the default.
+    fused: bool = False
     # keep per-parameter gradient arrays, filled by steps without mapping;
     # without them such a step forms the pose gradient alone (a mapping step
     # never needs them: its Adam step is fused into the projection adjoint)
@@ -62,7 +71,7 @@ class Agent:
                  want_used: bool = False, state=None, side=None):
         """`scene`: the map (numpy arrays, copied in synchronously), or None
         with `state`: the pinned host tensors of a swapped-out agent's
-        _state() (map, moments, pose, pose moments, step), copied in
+        _state() (map, moments, pose, pose moments, step, seen bitmap), copied in
         asynchronously on the current stream, like every allocation and fill
         here, so that a swap-in needs no host synchronisation.  `side`: a
         stream to reuse for the side work (a new one by default)."""
@@ -93,6 +102,12 @@ class Agent:
         self.pose_v = torch.zeros(6, dtype=torch.float32, device=device)
         self.t_dev = torch.zeros(1, dtype=torch.int32, device=device)  # Adam step, advanced on the device
         self.bin_status = torch.zeros(1, dtype=torch.int32, device=device)  # sticky capacity status of the binning
+        # bit i: Gaussian i's moments may be nonzero (a clear bit promises zero
+        # moments, so the map's Adam step skips the Gaussian while it is culled)
+        if state is not None:
+            self.seen = dev(state[19])
+        else:
+            self.seen = torch.zeros((self.n + 31) // 32, dtype=torch.int32, device=device)
         if state is not None:
             for dst, src in zip((self.pose_m, self.pose_v, self.t_dev), state[16:19]):
                 dst.copy_(src, non_blocking=True)
@@ -271,6 +286,13 @@ class Agent:
         B.splat_render_fwd_l1(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg,
                               self.cl1, s, schedule=fb.schedule)
 
+    def phase_render_backward(self, s):
+        """Forward render with the L1 terms and the screen-space adjoint in
+        one launch (the gradients left in the backward workspace)."""
+        fb = self.fb
+        B.splat_render_fwd_bwd(fb.cproj, self.params[4], self.n, fb.vals, fb.ranges, fb.ccam, self.cfg.bg, fb.cimg,
+                               self.cl1, fb.status, fb.bwd_ws, s, schedule=fb.schedule)
+
     def phase_loss(self, s):
         """Clear, then the L1 terms as a separate pass over a rendered image
         (the unfused form of phase_clear + the loss part of phase_render)."""
@@ -293,16 +315,18 @@ class Agent:
         fb = self.fb
         if self.cfg.map:
             B.splat_project_bwd_adam(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cm, self.cv, self.lrs,
-                                     self.t_dev, self.d_pose, stream=s, culled=not self.cfg.culled_beside)
+                                     self.t_dev, self.d_pose, stream=s, culled=self.cfg.culled_at == "adjoint",
+                                     seen=self.seen)
         else:
             self.grads_clean = self.grads is None
             B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cgr, self.d_pose, None, s)
 
     def phase_adam_culled(self, s):
-        """With mapping on and `culled_beside`: the culled Gaussians'
+        """With mapping on and `culled_at` not "adjoint": the culled Gaussians'
         zero-gradient Adam step (needs only the projection's radii)."""
-        if self.cfg.map and self.cfg.culled_beside:
-            B.splat_adam_culled(self.cg, self.fb.proj["radius"], self.cm, self.cv, self.lrs, self.t_dev, stream=s)
+        if self.cfg.map and self.cfg.culled_at != "adjoint":
+            B.splat_adam_culled(self.cg, self.fb.proj["radius"], self.cm, self.cv, self.lrs, self.t_dev, stream=s,
+                                seen=self.seen)
 
     def phase_update(self, s, assoc: bool = True, pose_stream=None):
         """The pose step (on `pose_stream` when given, after the projection
@@ -331,11 +355,12 @@ class Agent:
     def step(self, stream=None, sync_check: bool = False):
         """One step.  The accumulators are cleared (and the frame copied in,
         with host buffers attached) on a side stream while the map is projected
-        and binned; the forward render takes the loss.  The association depends
-        only on the forward render, so it runs on the side stream forked after
-        it, overlapping the backward render and the projection adjoint; the
-        pose step follows it there, beside the map's Adam; the side stream is
-        joined at the end."""
+        and binned; the forward render takes the loss, before the
+        screen-space backward (or in the same launch: `fused`).  The
+        association depends only on the forward render, so it runs on the side
+        stream forked after it, overlapping the backward render (two launches)
+        or the projection adjoint (one); the pose step follows it there, beside
+        the map's Adam; the side stream is joined at the end."""
         s = torch.cuda.current_stream() if stream is None else stream
         self.side.wait_stream(s)
         self.phase_clear(self.side)
@@ -345,12 +370,24 @@ class Agent:
                 self.obs_depth.copy_(self.host_in[1], non_blocking=True)
         self.phase_pre(s, sync_check)
         s.wait_stream(self.side)
-        self.phase_render(s)
-        if self.cfg.assoc or self.cfg.culled_beside:
+        if self.cfg.culled_at == "forward":
             self.side.wait_stream(s)
-            self.phase_adam_culled(self.side)  # beside the backward render
-            self.phase_assoc(self.side)
-        self.phase_backward(s)
+            self.phase_adam_culled(self.side)  # beside the forward render
+        if self.cfg.fused:  # the association follows the one render launch, beside the projection adjoint
+            self.phase_render_backward(s)
+            if self.cfg.assoc or self.cfg.culled_at == "backward":
+                self.side.wait_stream(s)
+                if self.cfg.culled_at == "backward":
+                    self.phase_adam_culled(self.side)
+                self.phase_assoc(self.side)
+        else:
+            self.phase_render(s)
+            if self.cfg.assoc or self.cfg.culled_at == "backward":
+                self.side.wait_stream(s)
+                if self.cfg.culled_at == "backward":
+                    self.phase_adam_culled(self.side)  # beside the backward render
+                self.phase_assoc(self.side)
+            self.phase_backward(s)
         self.phase_project_backward(s)
         self.phase_update(s, assoc=False, pose_stream=self.side)
         s.wait_stream(self.side)
@@ -403,6 +440,7 @@ class Agent:
         s.synchronize()
         self.params, self.m, self.v = dst[:5], dst[5:10], dst[10:]
         self.n = k
+        self.seen = self._seen_from_moments()
         self.cg = B.gaussians_struct(*self.params)
         self.make_scratch(self.fb.capacity)
         self._make_adam()
@@ -410,9 +448,22 @@ class Agent:
         self._snap = None
         return k
 
+    def _seen_from_moments(self):
+        """The seen bitmap rebuilt from the moments: bit i set when any of
+        Gaussian i's 28 moment elements is nonzero (host-side torch ops; used
+        after the map is compacted)."""
+        nz = torch.zeros(self.n, dtype=torch.bool, device=self.device)
+        for t in (*self.m, *self.v):
+            nz |= (t.reshape(self.n, -1) != 0).any(dim=1)
+        words = (self.n + 31) // 32
+        bits = torch.zeros(words * 32, dtype=torch.int64, device=self.device)
+        bits[:self.n] = nz.to(torch.int64)
+        w = (bits.view(words, 32) << torch.arange(32, device=self.device)).sum(dim=1)
+        return torch.where(w >= 2 ** 31, w - 2 ** 32, w).to(torch.int32).contiguous()
+
     # -- episodes ---------------------------------------------------------------
     def _state(self):
-        return [*self.params, *self.m, *self.v, self.w2c, self.pose_m, self.pose_v, self.t_dev]
+        return [*self.params, *self.m, *self.v, self.w2c, self.pose_m, self.pose_v, self.t_dev, self.seen]
 
     def snapshot(self):
         """Keep a device copy of the map, optimiser state and pose."""

@@ -86,11 +86,14 @@ _SIGS = {
     "splat_render_fwd": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_render_fwd_l1": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_tile_schedule_size": ([_c_i32], _c_sz),
+    "splat_render_fwd_bwd_workspace_size": ([_c_i64, _c_i32], _c_sz),
+    "splat_render_fwd_bwd": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p],
+                             ctypes.c_int),
     "splat_render_bwd_workspace_size": ([_c_i64], _c_sz),
     "splat_render_bwd": ([_c_p] * 16 + [_c_sz, _c_p], ctypes.c_int),
     "splat_project_bwd": ([_c_p] * 8 + [_c_p], ctypes.c_int),
-    "splat_project_bwd_adam": ([_c_p] * 8 + [_c_f, _c_f, _c_f, _c_p, _c_i32, _c_p, _c_p], ctypes.c_int),
-    "splat_adam_culled": ([_c_p] * 5 + [_c_f, _c_f, _c_f, _c_p, _c_p], ctypes.c_int),
+    "splat_project_bwd_adam": ([_c_p] * 8 + [_c_f, _c_f, _c_f, _c_p, _c_p, _c_i32, _c_p, _c_p], ctypes.c_int),
+    "splat_adam_culled": ([_c_p] * 5 + [_c_f, _c_f, _c_f, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_batch_workspace_size": ([], _c_sz),
     "splat_render_fwd_batch": ([_c_p, _c_i32, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
     "splat_render_bwd_batch": ([_c_p, _c_i32, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
@@ -263,11 +266,23 @@ def splat_render_fwd_l1(proj: CProjected, rgb, n, vals, ranges, cam: CCamera, bg
         None if l1 is None else ctypes.byref(l1), _p(schedule), _stream(stream)))
 
 
-SPLAT_SCHEDULE_BUCKETS = 128
-
 
 def splat_tile_schedule_size(n_tiles) -> int:
     return int(load(require_cuda=False).splat_tile_schedule_size(n_tiles))
+
+
+def splat_render_fwd_bwd_workspace_size(n, n_tiles) -> int:
+    return int(load(require_cuda=False).splat_render_fwd_bwd_workspace_size(n, n_tiles))
+
+
+def splat_render_fwd_bwd(proj: CProjected, rgb, n, vals, ranges, cam: CCamera, bg, image: CImage, l1: CL1, status,
+                         ws, stream=None, schedule=None):
+    """Forward render with the L1 terms and the screen-space backward in one
+    launch; the screen-space gradients are left at the start of `ws`."""
+    bgc = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    _check("splat_render_fwd_bwd", load().splat_render_fwd_bwd(
+        ctypes.byref(proj), _p(rgb), n, _p(vals), _p(ranges), ctypes.byref(cam), bgc, ctypes.byref(image),
+        ctypes.byref(l1), _p(schedule), _p(status), _p(ws), ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def splat_render_bwd_workspace_size(n) -> int:
@@ -293,23 +308,25 @@ def splat_project_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c
 
 def splat_project_bwd_adam(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, grad2d, m: CGaussiansGrad,
                            v: CGaussiansGrad, lr, step, d_pose, beta1=0.9, beta2=0.999, eps=1e-15, stream=None,
-                           culled=True):
+                           culled=True, seen=None):
     """`gaussians`' arrays are updated in place; `lr`: 5 step sizes (mean,
     log_scale, quat, opacity_logit, rgb); `step`: device int32[1] (t >= 1);
-    `culled`: also step the culled Gaussians (else splat_adam_culled does)."""
+    `culled`: also step the culled Gaussians (else splat_adam_culled does);
+    `seen`: the optional bitmap of Gaussians whose moments may be nonzero."""
     lrc = (ctypes.c_float * 5)(*[float(x) for x in lr])
     _check("splat_project_bwd_adam", load().splat_project_bwd_adam(
         ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(grad2d), ctypes.byref(m),
-        ctypes.byref(v), lrc, beta1, beta2, eps, _p(step), 1 if culled else 0, _p(d_pose), _stream(stream)))
+        ctypes.byref(v), lrc, beta1, beta2, eps, _p(step), _p(seen), 1 if culled else 0, _p(d_pose),
+        _stream(stream)))
 
 
 def splat_adam_culled(gaussians: CGaussians, radius, m: CGaussiansGrad, v: CGaussiansGrad, lr, step, beta1=0.9,
-                      beta2=0.999, eps=1e-15, stream=None):
+                      beta2=0.999, eps=1e-15, stream=None, seen=None):
     """The culled Gaussians' zero-gradient Adam step (see the header)."""
     lrc = (ctypes.c_float * 5)(*[float(x) for x in lr])
     _check("splat_adam_culled", load().splat_adam_culled(
         ctypes.byref(gaussians), _p(radius), ctypes.byref(m), ctypes.byref(v), lrc, beta1, beta2, eps, _p(step),
-        _stream(stream)))
+        _p(seen), _stream(stream)))
 
 
 def splat_batch_workspace_size() -> int:

@@ -505,9 +505,9 @@ __device__ __forceinline__ bool row_span(const uint16_t* __restrict__ spans, uin
 
 // One CTA: prefix sums along the rows of the difference grid (gw = tiles_x + 1
 // cells per row, kDiffStride ints apart) -> per-tile counts; exclusive scan over tiles -> ranges
-// (clamped to the capacity) and bucket cursors; K and the status; the bucket
-// counts of a tile schedule (filled by the forward render) set to zero when
-// `schedule` is not null.
+// (clamped to the capacity) and bucket cursors; K and the status; with a
+// tile schedule, its order (heaviest first) rebuilt from the per-tile costs
+// the last forward render left (a counting sort over the cost buckets).
 __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff, int tiles_x, int tiles_y,
                                                          const unsigned long long* __restrict__ k_total,
                                                          int64_t capacity, uint2* __restrict__ ranges,
@@ -558,8 +558,34 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
     *k_dev = k;
     if (k > capacity) raise_status(status, SPLAT_ECAPACITY);
   }
-  if (schedule)
-    for (int b = threadIdx.x; b < SPLAT_SCHEDULE_BUCKETS; b += blockDim.x) schedule[b] = 0u;
+  if (schedule) {
+    __shared__ uint32_t s_cnt[kCostBuckets];
+    const uint32_t* cost = schedule + 1 + n_tiles;
+    uint32_t* order = schedule + 1;
+    for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) s_cnt[b] = 0u;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&s_cnt[tile_cost_bucket(cost[t])], 1u);
+    __syncthreads();
+    if (wid == 0) {  // bucket cursors, heaviest bucket first: lane l takes buckets 127 - 4 l - j
+      uint32_t c[4], tot = 0u;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        c[j] = s_cnt[kCostBuckets - 1 - 4 * lane - j];
+        tot += c[j];
+      }
+      uint32_t run = warp_incl_scan(tot, lane) - tot;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        s_cnt[kCostBuckets - 1 - 4 * lane - j] = run;
+        run += c[j];
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
+      order[atomicAdd(&s_cnt[tile_cost_bucket(cost[t])], 1u)] = (uint32_t)t;
+    __syncthreads();
+    if (threadIdx.x == 0) schedule[0] = (uint32_t)n_tiles;
+  }
 }
 
 // Every visible Gaussian drops key (depth bits << 32 | id) into the bucket of

@@ -65,6 +65,26 @@ __device__ __forceinline__ float exp_full(float x) {
 }
 
 // Status word helpers (sticky: only ever raised).
+// Tile schedule layout (uint32): [0] = n_tiles once an order has been
+// written, [1, 1 + n_tiles) = tile ids heaviest first, [1 + n_tiles,
+// 1 + 2 n_tiles) = per-tile cost (summed contributor counts of the tile's
+// pixels, written by the forward render).  Costs are ordered by bucket
+// 1 + floor(8 log2 cost) (the float exponent and three mantissa bits; 0 for
+// cost 0), heaviest bucket first.
+constexpr int kCostBuckets = 128;
+__device__ __forceinline__ int tile_cost_bucket(uint32_t S) {
+  if (S == 0u) return 0;
+  const int b = (int)((__float_as_uint((float)S) >> 20) - (127u << 3)) + 1;
+  return b < kCostBuckets ? b : kCostBuckets - 1;
+}
+// The k-th tile of a view's schedule, or k when the schedule holds no order
+// (or an entry out of range: a schedule written by anything but the binning).
+__device__ __forceinline__ int schedule_tile(const uint32_t* sched, int n_tiles, int k) {
+  if (!sched || sched[0] != (uint32_t)n_tiles) return k;
+  const uint32_t t = sched[1 + k];
+  return t < (uint32_t)n_tiles ? (int)t : k;
+}
+
 __device__ __forceinline__ void raise_status(int32_t* status, int32_t code) {
   if (status) atomicCAS(status, 0, code);
 }

@@ -63,6 +63,7 @@ struct AdamMapK {
   int vec[5];   // p, m, v of the group 16-byte aligned
   float b1, b2, eps;
   const int32_t* step;
+  uint32_t* seen;  // bit i: Gaussian i's moments may be nonzero (0 promises m = v = 0), or null
 };
 
 inline CamK make_camk(const splat_camera& c) {

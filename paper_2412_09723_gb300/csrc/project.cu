@@ -462,6 +462,35 @@ __device__ __forceinline__ void adam_gaussian(const AdamMapK& A, int64_t i, cons
   group_step_store<4>(A, 2, i, s2, o.q, ibc1, ibc2);
   group_step_store<1>(A, 3, i, s3, &o.logit, ibc1, ibc2);
   group_step_store<3>(A, 4, i, s4, o.rgb, ibc1, ibc2);
+  if (A.seen) {  // its moments are now nonzero (or may be): mark it once
+    const uint32_t bit = 1u << (i & 31);
+    if (!(A.seen[i >> 5] & bit)) atomicOr(&A.seen[i >> 5], bit);
+  }
+}
+
+// With a seen bitmap: the zero-gradient step of culled Gaussian i (one thread
+// per Gaussian, its 14 elements), taken only when its bit is set -- a clear
+// bit promises zero moments, whose update is nothing -- so the culled part
+// reads one bit per Gaussian that was never updated.
+__device__ __forceinline__ void culled_seen(const AdamMapK& A, const int32_t* __restrict__ radius, int64_t n,
+                                            int64_t first, int64_t stride, float ibc1, float ibc2) {
+  for (int64_t i = first; i < n; i += stride) {
+    if (!((__ldg(A.seen + (i >> 5)) >> (i & 31)) & 1u) || __ldg(radius + i) != 0) continue;
+    const int W[5] = {3, 3, 4, 1, 3};
+#pragma unroll
+    for (int grp = 0; grp < 5; ++grp) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (k >= W[grp]) break;
+        const size_t e = (size_t)W[grp] * i + k;
+        float pj = A.p[grp][e], mj = A.m[grp][e], vj = A.v[grp][e];
+        adam_update(pj, 0.0f, mj, vj, A.lr[grp], A.b1, A.b2, ibc1, ibc2, A.eps);
+        A.p[grp][e] = pj;
+        A.m[grp][e] = mj;
+        A.v[grp][e] = vj;
+      }
+    }
+  }
 }
 
 // Zero-gradient Adam step of the culled Gaussians' elements of group GRP
@@ -536,8 +565,11 @@ __global__ void __launch_bounds__(kPbThreads, 2) project_bwd_adam_kernel(Gaussia
   const float ibc2 = 1.0f / bias_correction(A.b2, A.step);
   if ((int)blockIdx.x >= kept_blocks) {  // the culled Gaussians
     const int64_t nb = (int64_t)gridDim.x - kept_blocks;
-    culled_units(A, radius, g.n, ((int64_t)blockIdx.x - kept_blocks) * kPbThreads + threadIdx.x, nb * kPbThreads,
-                 ibc1, ibc2);
+    const int64_t first = ((int64_t)blockIdx.x - kept_blocks) * kPbThreads + threadIdx.x;
+    if (A.seen)
+      culled_seen(A, radius, g.n, first, nb * kPbThreads, ibc1, ibc2);
+    else
+      culled_units(A, radius, g.n, first, nb * kPbThreads, ibc1, ibc2);
     return;
   }
   __shared__ int32_t queue[kPbWarps][160];
@@ -549,27 +581,17 @@ __global__ void __launch_bounds__(kPbThreads, 2) project_bwd_adam_kernel(Gaussia
   for (int k = 0; k < 12; ++k) W[k] = __ldg(w2c + k);
   float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int qn = 0;  // warp-uniform
-  // each warp scans runs of 128 consecutive radii (four per lane, one 16-byte
-  // load when aligned), queueing the kept Gaussians
-  const bool vec = (reinterpret_cast<uintptr_t>(radius) & 15u) == 0;
-  const int64_t stride_all = (int64_t)kept_blocks * kPbThreads * 4;
-  for (int64_t base = ((int64_t)blockIdx.x * kPbWarps + warp) * 128; base < g.n; base += stride_all) {
-    int r4[4];
-    const int64_t i0 = base + 4 * lane;
-    if (vec && i0 + 4 <= g.n) {
-      const int4 r = *reinterpret_cast<const int4*>(radius + i0);
-      r4[0] = r.x; r4[1] = r.y; r4[2] = r.z; r4[3] = r.w;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) r4[k] = i0 + k < g.n ? radius[i0 + k] : 0;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const bool vis = r4[k] != 0;
-      const unsigned m = __ballot_sync(full, vis);
-      if (vis) queue[warp][qn + __popc(m & lower)] = (int32_t)(i0 + k);
-      qn += __popc(m);
-    }
+  // each warp scans runs of 32 consecutive radii, the runs of all warps
+  // interleaved over the map, queueing the kept Gaussians: the kept ones
+  // cluster in index order (a map is built surface by surface), and short
+  // interleaved runs spread each cluster over all warps
+  const int64_t stride_all = (int64_t)kept_blocks * kPbThreads;
+  for (int64_t base = ((int64_t)blockIdx.x * kPbWarps + warp) * 32; base < g.n; base += stride_all) {
+    const int64_t i = base + lane;
+    const bool vis = i < g.n && __ldg(radius + i) != 0;
+    const unsigned m = __ballot_sync(full, vis);
+    if (vis) queue[warp][qn + __popc(m & lower)] = (int32_t)i;
+    qn += __popc(m);
     __syncwarp();
     while (qn >= 32) {
       const int64_t j = queue[warp][qn - 32 + lane];
@@ -601,8 +623,11 @@ __global__ void __launch_bounds__(kPbThreads) adam_culled_kernel(int64_t n, cons
                                                                  AdamMapK A) {
   const float ibc1 = 1.0f / bias_correction(A.b1, A.step);
   const float ibc2 = 1.0f / bias_correction(A.b2, A.step);
-  culled_units(A, radius, n, (int64_t)blockIdx.x * kPbThreads + threadIdx.x, (int64_t)gridDim.x * kPbThreads, ibc1,
-               ibc2);
+  const int64_t first = (int64_t)blockIdx.x * kPbThreads + threadIdx.x, stride = (int64_t)gridDim.x * kPbThreads;
+  if (A.seen)
+    culled_seen(A, radius, n, first, stride, ibc1, ibc2);
+  else
+    culled_units(A, radius, n, first, stride, ibc1, ibc2);
 }
 
 int launch_adam_culled(int64_t n, const int32_t* radius, const AdamMapK& adam, cudaStream_t s) {

@@ -328,57 +328,6 @@ __device__ __forceinline__ float l1_px(float x, float t, float sc, float* g) {
   return fabsf(e);
 }
 
-// Tile schedule: bucket 1 + floor(8 log2 S) of a tile's summed contributor
-// counts S (the exponent and three mantissa bits of S as a float), 0 for S = 0.
-__device__ __forceinline__ int schedule_bucket(uint32_t S) {
-  if (S == 0u) return 0;
-  const int b = (int)((__float_as_uint((float)S) >> 20) - (127u << 3)) + 1;
-  return b < SPLAT_SCHEDULE_BUCKETS ? b : SPLAT_SCHEDULE_BUCKETS - 1;
-}
-
-// The k-th tile of a schedule, heaviest bucket first (called by one whole
-// warp; k itself when the counts do not add up to the number of tiles).
-__device__ __forceinline__ int schedule_tile(const uint32_t* sched, int n_tiles, int k) {
-  const int lane = threadIdx.x & 31;
-  uint32_t c[4], tot = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    c[j] = sched[SPLAT_SCHEDULE_BUCKETS - 1 - 4 * lane - j];
-    tot += c[j];
-  }
-  uint32_t incl = tot;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  // a schedule that does not hold every tile exactly once (filled twice since
-  // it was cleared, or never) leaves the natural order
-  if (__shfl_sync(0xffffffffu, incl, 31) != (uint32_t)n_tiles) return k;
-  const uint32_t excl = incl - tot, uk = (uint32_t)k;
-  const unsigned hit = __ballot_sync(0xffffffffu, excl <= uk && uk < incl);
-  int tile = k;
-  if (hit) {
-    const int src = __ffs(hit) - 1;
-    int t = -1;
-    if (lane == src) {
-      uint32_t run = excl;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (t < 0 && uk < run + c[j]) {
-          const uint32_t slot = uk - run;
-          const int b = SPLAT_SCHEDULE_BUCKETS - 1 - 4 * lane - j;
-          if (slot < (uint32_t)n_tiles) t = (int)sched[SPLAT_SCHEDULE_BUCKETS + (size_t)b * n_tiles + slot];
-        }
-        run += c[j];
-      }
-    }
-    t = __shfl_sync(0xffffffffu, t, src);
-    if (t >= 0 && t < n_tiles) tile = t;
-  }
-  return tile;
-}
-
 template <int BATCH>
 __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>& sm, float* s_loss) {
   const CamK& cam = V.cam;
@@ -455,7 +404,7 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
   }
   // per tile, one block reduction of the loss terms and the contributor
   // counts: warp sums, then thread 0 adds the warps' sums, makes one loss
-  // atomic and puts the tile into its schedule bucket
+  // atomic and writes the tile's cost into the schedule
   if (L.t_rgb || V.sched) {
     float acc = L.sc * acc_c + L.sd * acc_d;
 #pragma unroll
@@ -475,12 +424,7 @@ __device__ __forceinline__ void fwd_tile(const ViewK& V, int tile, Stage<BATCH>&
         St += __float_as_uint(s_loss[kFwdThreads / 32 + w]);
       }
       if (L.t_rgb && L.loss) atomicAdd(L.loss, t);
-      if (V.sched) {
-        const int nt = cam.tiles_x * cam.tiles_y;
-        const int b = schedule_bucket(St);
-        const unsigned slot = atomicAdd(&V.sched[b], 1u);
-        if (slot < (unsigned)nt) V.sched[SPLAT_SCHEDULE_BUCKETS + (size_t)b * nt + slot] = (uint32_t)tile;
-      }
+      if (V.sched) V.sched[1 + cam.tiles_x * cam.tiles_y + tile] = St;  // the tile's cost
     }
   }
 }
@@ -489,7 +433,7 @@ template <int BATCH>
 __global__ void __launch_bounds__(kFwdThreads, 8) render_fwd_kernel(ViewK V) {
   __shared__ Stage<BATCH> sm;
   __shared__ float s_loss[2 * kFwdThreads / 32];
-  fwd_tile<BATCH>(V, blockIdx.x, sm, s_loss);
+  fwd_tile<BATCH>(V, schedule_tile(V.sched, V.cam.tiles_x * V.cam.tiles_y, blockIdx.x), sm, s_loss);
 }
 
 // Work item -> (view, tile).
@@ -515,6 +459,7 @@ __global__ void __launch_bounds__(kFwdThreads, 8) render_fwd_persistent(ViewTabl
   for (int item = next_item(counter, &s_item); item < total; item = next_item(counter, &s_item)) {
     int tile;
     const int v = view_of(T, item, tile);
+    tile = schedule_tile(T.v[v].sched, T.v[v].cam.tiles_x * T.v[v].cam.tiles_y, tile);
     fwd_tile<BATCH>(T.v[v], tile, sm, s_loss);
   }
 }
@@ -679,11 +624,11 @@ __device__ __forceinline__ void bwd_part(const ViewK& V, int tile, BwdShared<BAT
       const int y = ty * kTile + (p ? ly1 : ly0);
       const bool inside = x < cam.width && y < cam.height;
       const size_t i = inside ? (size_t)y * cam.width + x : 0;
-      const float g0 = inside ? V.d_rgb[3 * i + 0] : 0.f;
-      const float g1 = inside ? V.d_rgb[3 * i + 1] : 0.f;
-      const float g2 = inside ? V.d_rgb[3 * i + 2] : 0.f;
-      const float gd = (inside && V.d_depth) ? V.d_depth[i] : 0.f;
-      const float gs = (inside && V.d_sil) ? V.d_sil[i] : 0.f;
+      const float g0 = inside ? __ldcg(V.d_rgb + 3 * i + 0) : 0.f;
+      const float g1 = inside ? __ldcg(V.d_rgb + 3 * i + 1) : 0.f;
+      const float g2 = inside ? __ldcg(V.d_rgb + 3 * i + 2) : 0.f;
+      const float gd = (inside && V.d_depth) ? __ldcg(V.d_depth + i) : 0.f;
+      const float gs = (inside && V.d_sil) ? __ldcg(V.d_sil + i) : 0.f;
       f[p][0] = -((float)y + 0.5f);
       f[p][2] = g0;
       f[p][3] = g1;
@@ -692,15 +637,16 @@ __device__ __forceinline__ void bwd_part(const ViewK& V, int tile, BwdShared<BAT
       f[p][6] = gs;
       if (FRONT) {
         f[p][1] = 1.0f;
-        f[p][7] = inside ? ((g0 * V.img.rgb[3 * i + 0] + g1 * V.img.rgb[3 * i + 1]) + g2 * V.img.rgb[3 * i + 2] +
-                           gd * V.img.depth[i]) + gs * V.img.sil[i]
+        const float* im = V.img.rgb + 3 * i;
+        f[p][7] = inside ? ((g0 * __ldcg(im) + g1 * __ldcg(im + 1)) + g2 * __ldcg(im + 2) + gd * __ldcg(V.img.depth + i)) +
+                               gs * __ldcg(V.img.sil + i)
                          : 0.f;
       } else {
-        const float Tfin = inside ? V.img.t_final[i] : 1.0f;
+        const float Tfin = inside ? __ldcg(V.img.t_final + i) : 1.0f;
         f[p][1] = Tfin;
         f[p][7] = (g0 * V.bg0 + g1 * V.bg1 + g2 * V.bg2) * Tfin;
       }
-      q.last[p] = inside ? V.img.n_contrib[i] : 0;
+      q.last[p] = inside ? __ldcg(V.img.n_contrib + i) : 0;
     }
     q.nfy = make_float2(f[0][0], f[1][0]);
     q.T = make_float2(f[0][1], f[1][1]);
@@ -812,10 +758,10 @@ __global__ void __launch_bounds__(kBwdThreads, 8) render_bwd_persistent(ViewTabl
     __syncthreads();
     const int item = s_item;
     if (item >= 2 * total) break;
-    if (threadIdx.x < 32) {  // warp 0 resolves the item's view and tile
+    if (threadIdx.x < 32) {  // the item's view and tile
       int tile;
       const int v = view_of(T, item >> 1, tile);
-      if (T.v[v].sched) tile = schedule_tile(T.v[v].sched, T.v[v].cam.tiles_x * T.v[v].cam.tiles_y, tile);
+      tile = schedule_tile(T.v[v].sched, T.v[v].cam.tiles_x * T.v[v].cam.tiles_y, tile);
       if (threadIdx.x == 0) {
         s_view = v;
         s_tile = tile;
@@ -826,6 +772,89 @@ __global__ void __launch_bounds__(kBwdThreads, 8) render_bwd_persistent(ViewTabl
       bwd_part<BATCH, false>(T.v[s_view], s_tile, sm);
     else
       bwd_part<BATCH, true>(T.v[s_view], s_tile, sm);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Forward and backward in one launch (one view)
+// ----------------------------------------------------------------------------
+// The backward of a tile needs only that tile's forward outputs and loss
+// gradients, so both run as items of one persistent launch: items [0, T) are
+// the forward of the schedule's tiles (heaviest first), items [T, 3 T) the two
+// backward parts of the tiles in the order their forwards finished.  A forward
+// item ends with every thread's writes fenced, then takes the next slot of a
+// completion queue and release-stores its tile there; backward items 2 j and
+// 2 j + 1 wait (acquire loads) for slot j.  All forward items were taken from
+// the ticket counter before any backward item, by CTAs that are running, so
+// slot j is always filled; the wait is still bounded (kFlagWaitLimit polls),
+// after which SPLAT_ETIMEOUT is raised and the item is skipped.  A backward
+// item never waits for one particular tile, only for the j-th finished one.
+// The launch is cooperative (all CTAs resident).
+// The backward's reads of forward outputs bypass L1 (ld.global.cg), which is
+// not coherent with other SMs' writes.
+constexpr unsigned kFlagWaitLimit = 1u << 22;
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <int FB, int BB>
+union FusedShared {
+  Stage<FB> f;
+  BwdShared<BB> b;
+};
+
+template <int FB, int BB>
+__global__ void __launch_bounds__(kBwdThreads, 8) render_fused_persistent(ViewK V, int n_tiles, int* counter,
+                                                                         int* queue, int32_t* status) {
+  static_assert(kFwdThreads == kBwdThreads, "one block shape for both item kinds");
+  __shared__ FusedShared<FB, BB> sm;
+  __shared__ float s_loss[2 * kFwdThreads / 32];
+  __shared__ int s_item, s_tile, s_ok;
+  for (;;) {
+    __syncthreads();  // every thread is done with the previous item's shared memory
+    if (threadIdx.x == 0) {  // the item, its tile and, for a backward item, the wait for the tile's forward
+      const int item = atomicAdd(counter, 1);
+      int ok = 1, tile = 0;
+      if (item < n_tiles) {
+        tile = schedule_tile(V.sched, n_tiles, item);
+      } else if (item < 3 * n_tiles) {  // slot j of the queue holds the j-th finished tile + 1
+        const int* slot = queue + 1 + ((item - n_tiles) >> 1);
+        unsigned polls = 0;
+        int t1;
+        while ((t1 = ld_acquire(slot)) == 0) {
+          if (++polls > kFlagWaitLimit) {
+            ok = 0;
+            raise_status(status, SPLAT_ETIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+        }
+        tile = ok ? t1 - 1 : 0;
+      }
+      s_item = item;
+      s_tile = tile;
+      s_ok = ok;
+    }
+    __syncthreads();
+    const int item = s_item;
+    if (item >= 3 * n_tiles) break;
+    if (!s_ok) continue;
+    if (item < n_tiles) {
+      fwd_tile<FB>(V, s_tile, sm.f, s_loss);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) st_release(queue + 1 + atomicAdd(queue, 1), s_tile + 1);
+    } else if ((item - n_tiles) & 1) {
+      bwd_part<BB, false>(V, s_tile, sm.b);
+    } else {
+      bwd_part<BB, true>(V, s_tile, sm.b);
+    }
   }
 }
 
@@ -913,7 +942,7 @@ extern "C" int splat_render_fwd_l1(const splat_projected* proj, const float* rgb
 }
 
 extern "C" size_t splat_tile_schedule_size(int32_t n_tiles) {
-  return n_tiles < 1 ? 0 : sizeof(uint32_t) * ((size_t)SPLAT_SCHEDULE_BUCKETS * (1 + (size_t)n_tiles));
+  return n_tiles < 1 ? 0 : sizeof(uint32_t) * (1 + 2 * (size_t)n_tiles);
 }
 
 // Workspace of splat_render_bwd: the screen-space gradients [n, 12] and, after
@@ -972,6 +1001,59 @@ extern "C" int splat_render_bwd(const splat_gaussians* g, const splat_projected*
   return launch_project_bwd(gk, v.cam, w2c, proj->conic, proj->radius, g2, kGradStride, gr, d_pose, d2d, s);
 }
 
+// Workspace of splat_render_fwd_bwd: that of splat_render_bwd, then the
+// completion queue (a count and one slot per tile).
+extern "C" size_t splat_render_fwd_bwd_workspace_size(int64_t n, int32_t n_tiles) {
+  if (n < 0 || n_tiles < 0) return 0;
+  return g2_bytes(n) + 256 + align_up(sizeof(int) * (1 + (size_t)std::max(n_tiles, 1)));
+}
+
+extern "C" int splat_render_fwd_bwd(const splat_projected* proj, const float* rgb, int64_t n, const uint32_t* vals,
+                                    const uint32_t* ranges, const splat_camera* cam, const float* bg,
+                                    const splat_image* out, const splat_l1* l1, uint32_t* schedule, int32_t* status,
+                                    void* ws, size_t ws_bytes, splat_stream_t stream) {
+  const char* who = "splat_render_fwd_bwd";
+  int rc = check_proj(proj, n, who);
+  if (rc) return rc;
+  if ((n > 0 && !rgb) || !vals || !ranges || !cam || !bg || !out || !image_ok(*out) || !l1 || !status)
+    return fail(SPLAT_EINVAL, "%s: null argument", who);
+  if (n < 0 || cam->width <= 0 || cam->height <= 0) return fail(SPLAT_EINVAL, "%s: bad sizes", who);
+  ViewK v = make_view(*proj, rgb, vals, ranges, *cam, bg, *out);
+  if ((rc = set_loss(v, l1, who))) return rc;
+  const int tiles = v.cam.tiles_x * v.cam.tiles_y;
+  if (!ws || !aligned16(ws) || ws_bytes < splat_render_fwd_bwd_workspace_size(n, tiles))
+    return fail(SPLAT_EINVAL, "%s: workspace missing, too small or not 16-byte aligned", who);
+  v.sched = schedule;
+  v.d_rgb = l1->d_rgb;
+  v.d_depth = l1->d_depth;
+  v.d_sil = nullptr;
+  v.g2 = static_cast<float*>(ws);
+  int* counter = reinterpret_cast<int*>(static_cast<char*>(ws) + g2_bytes(n));
+  int* queue = reinterpret_cast<int*>(static_cast<char*>(ws) + g2_bytes(n) + 256);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(ws, 0, g2_bytes(n) + 256 + sizeof(int) * (1 + (size_t)tiles), s) != cudaSuccess)
+    return fail(SPLAT_ECUDA, "%s: memset failed", who);
+  // cooperative: the grid is at most what is resident at once
+  auto kern = render_fused_persistent<256, kBwdBatch>;
+  int dev = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBwdThreads, 0) != cudaSuccess || per_sm < 1)
+    return fail(SPLAT_ECUDA, "%s: occupancy query failed", who);
+  int grid = std::min(3 * tiles, per_sm * sm_count());
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBwdThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  SPLAT_LAUNCH("render_fused_persistent", s, cudaLaunchKernelEx(&cfg, kern, v, tiles, counter, queue, status));
+  return check_launch("render_fused_persistent");
+}
+
 extern "C" int splat_project_bwd(const splat_gaussians* g, const splat_projected* proj, const splat_camera* cam,
                                  const float* w2c, const float* grad2d, const splat_gaussians_grad* out,
                                  float* d_pose, float* d2d, splat_stream_t stream) {
@@ -992,8 +1074,8 @@ extern "C" int splat_project_bwd(const splat_gaussians* g, const splat_projected
 }
 
 static int make_adam_map(const splat_gaussians* g, const splat_gaussians_grad* m, const splat_gaussians_grad* v,
-                         const float* lr, float beta1, float beta2, float eps, const int32_t* step, AdamMapK* A,
-                         const char* who) {
+                         const float* lr, float beta1, float beta2, float eps, const int32_t* step, uint32_t* seen,
+                         AdamMapK* A, const char* who) {
   if (!g || !m || !v || !lr || !step) return fail(SPLAT_EINVAL, "%s: null argument", who);
   if (g->n < 0 || (g->n > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->rgb || !m->mean ||
                                 !m->log_scale || !m->quat || !m->opacity_logit || !m->rgb || !v->mean ||
@@ -1014,19 +1096,20 @@ static int make_adam_map(const splat_gaussians* g, const splat_gaussians_grad* m
   A->b2 = beta2;
   A->eps = eps;
   A->step = step;
+  A->seen = seen;
   return SPLAT_OK;
 }
 
 extern "C" int splat_project_bwd_adam(const splat_gaussians* g, const splat_projected* proj, const splat_camera* cam,
                                       const float* w2c, const float* grad2d, const splat_gaussians_grad* m,
                                       const splat_gaussians_grad* v, const float* lr, float beta1, float beta2,
-                                      float eps, const int32_t* step, int32_t culled, float* d_pose,
-                                      splat_stream_t stream) {
+                                      float eps, const int32_t* step, uint32_t* seen, int32_t culled,
+                                      float* d_pose, splat_stream_t stream) {
   if (!g || !cam || !w2c || !grad2d) return fail(SPLAT_EINVAL, "splat_project_bwd_adam: null argument");
   int rc = check_proj(proj, g->n, "splat_project_bwd_adam");
   if (rc) return rc;
   AdamMapK A;
-  if ((rc = make_adam_map(g, m, v, lr, beta1, beta2, eps, step, &A, "splat_project_bwd_adam"))) return rc;
+  if ((rc = make_adam_map(g, m, v, lr, beta1, beta2, eps, step, seen, &A, "splat_project_bwd_adam"))) return rc;
   if (!aligned16(g->quat) || !aligned16(grad2d))
     return fail(SPLAT_EINVAL, "splat_project_bwd_adam: quat or grad2d not 16-byte aligned");
   if (g->n > 0 && !proj->radius) return fail(SPLAT_EINVAL, "splat_project_bwd_adam: proj->radius is null");
@@ -1037,9 +1120,9 @@ extern "C" int splat_project_bwd_adam(const splat_gaussians* g, const splat_proj
 
 extern "C" int splat_adam_culled(const splat_gaussians* g, const int32_t* radius, const splat_gaussians_grad* m,
                                  const splat_gaussians_grad* v, const float* lr, float beta1, float beta2, float eps,
-                                 const int32_t* step, splat_stream_t stream) {
+                                 const int32_t* step, uint32_t* seen, splat_stream_t stream) {
   AdamMapK A;
-  int rc = make_adam_map(g, m, v, lr, beta1, beta2, eps, step, &A, "splat_adam_culled");
+  int rc = make_adam_map(g, m, v, lr, beta1, beta2, eps, step, seen, &A, "splat_adam_culled");
   if (rc) return rc;
   if (g->n > 0 && !radius) return fail(SPLAT_EINVAL, "splat_adam_culled: radius is null");
   return launch_adam_culled(g->n, radius, A, reinterpret_cast<cudaStream_t>(stream));

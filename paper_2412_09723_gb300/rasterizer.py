@@ -40,14 +40,17 @@ class FrameBuffers:
         if want_used:
             self.image["n_used"] = torch.zeros(H, W, **i)
         self.ranges = torch.zeros(cam.n_tiles, 2, dtype=torch.int32, device=device)
-        # the tile schedule (heaviest first) that the forward fills for the backward
+        # the tile schedule: per-tile costs (written by the forward) and the order built from them
         self.schedule = torch.zeros(B.splat_tile_schedule_size(cam.n_tiles) // 4, dtype=torch.int32, device=device)
         self.k_dev = torch.zeros(1, dtype=torch.int64, device=device)
         self.status = torch.zeros(1, dtype=torch.int32, device=device) if status is None else status
         self.want_keys = want_keys
         self.capacity = 0
         self._alloc(capacity if capacity else max(1024, 16 * n))
-        self.bwd_ws = torch.empty(max(1, B.splat_render_bwd_workspace_size(n)), dtype=torch.uint8, device=device)
+        # the backward's workspace, large enough for the one-launch forward + backward too
+        self.bwd_ws = torch.empty(max(1, B.splat_render_bwd_workspace_size(n),
+                                      B.splat_render_fwd_bwd_workspace_size(n, cam.n_tiles)),
+                                  dtype=torch.uint8, device=device)
         self.cproj = B.projected_struct(self.proj)
         self.cimg = B.image_struct(self.image)
         self.ccam = B.camera_struct(cam)

@@ -45,6 +45,33 @@ def test_graph_replay_equals_eager_step(dev):
     assert torch.equal(a.pairs[: int(a.m_dev.item())], b.pairs[: int(b.m_dev.item())])
 
 
+def test_one_launch_render_step_equals_two_launch_step(dev):
+    """A step whose forward and screen-space backward share one launch
+    (`fused`) gives the two-launch step's images bit for bit, its loss, its
+    associations, and its parameter and pose gradients within the gradient
+    rule; captured and replayed as well."""
+    a = _agent(dev, map=False, track=False)
+    b = _agent(dev, map=False, track=False, fused=True)
+    for k in range(2):
+        a.step()
+        if k == 0:
+            b.step()
+        else:  # no map or pose update: the capture's warm-up step changes nothing
+            b.capture()
+            b.replay()
+        torch.cuda.synchronize()
+        for key in ("rgb", "depth", "sil", "t_final", "n_contrib", "max_id"):
+            assert torch.equal(a.fb.image[key], b.fb.image[key]), key
+        assert float(a.loss.item()) == pytest.approx(float(b.loss.item()), rel=1e-5)
+        assert int(b.status()) == 0
+        for ga, gb in zip([*a.grads, a.d_pose], [*b.grads, b.d_pose]):
+            ref = ga.double()
+            rms = float(ref.pow(2).mean().sqrt())
+            assert float((ga.double() - gb.double()).abs().max()) <= 1e-3 * rms + 1e-3 * float(ref.abs().max())
+        assert int(a.m_dev.item()) == int(b.m_dev.item())
+        assert torch.equal(a.pairs[: int(a.m_dev.item())], b.pairs[: int(b.m_dev.item())])
+
+
 def test_host_io_inside_the_captured_step(dev):
     """With pinned host buffers attached, the captured step copies its frame in
     and its loss and pose out: the same results as set_observation + step, and

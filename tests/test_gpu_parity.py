@@ -144,30 +144,33 @@ def _check_bins(fb, sc, w2c, cam):
     assert np.array_equal(fb.ranges.cpu().numpy().view(np.uint32), ranges)
 
 
-def _check_schedule(sched, n_contrib, cam):
-    """The tile schedule the forward filled: bucket counts that add up to the
-    number of tiles, lists that together hold every tile once, each tile in
-    the bucket of its summed contributor counts S (1 + the exponent and three
-    mantissa bits of S as a float32, in eighths of an octave; 0 for S = 0),
-    taken from the oracle's image."""
-    nb = 128
+def _cost_bucket(S):
+    """1 + the exponent and three mantissa bits of S as a float32 (eighths of
+    an octave), 0 for S = 0, at most 127."""
+    S = np.asarray(S, np.float32)
+    b = np.where(S > 0, ((S.view(np.uint32) >> 20).astype(np.int64) - (127 << 3)) + 1, 0)
+    return np.minimum(b, 127)
+
+
+def _check_schedule(sched, n_contrib, cam, ordered_by_cost=False):
+    """The tile schedule after a forward render: the per-tile costs are the
+    summed contributor counts of the tile's pixels (from the oracle's image),
+    and the order written by the binning is a permutation of the tiles; with
+    `ordered_by_cost` (the binning ran after the forward) the order takes the
+    cost buckets heaviest first."""
     sched = sched.view(np.uint32)
     tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
     n_t = tx * ty
-    assert sched.size == nb * (1 + n_t)
-    counts = sched[:nb].astype(np.int64)
-    assert counts.sum() == n_t
+    assert sched.size == 1 + 2 * n_t
     pad = np.zeros((ty * 16, tx * 16), np.int64)
     pad[:cam.height, :cam.width] = n_contrib
-    S = pad.reshape(ty, 16, tx, 16).sum(axis=(1, 3)).ravel().astype(np.float32)
-    want = np.where(S > 0, ((S.view(np.uint32) >> 20).astype(np.int64) - (127 << 3)) + 1, 0)
-    want = np.minimum(want, nb - 1)
-    seen = []
-    for b in range(nb):
-        lst = sched[nb + b * n_t: nb + b * n_t + counts[b]]
-        assert (want[lst] == b).all(), f"bucket {b}"
-        seen.append(lst)
-    assert np.array_equal(np.sort(np.concatenate(seen)), np.arange(n_t, dtype=np.uint32))
+    S = pad.reshape(ty, 16, tx, 16).sum(axis=(1, 3)).ravel()
+    assert np.array_equal(sched[1 + n_t:].astype(np.int64), S)
+    assert sched[0] == n_t
+    order = sched[1:1 + n_t]
+    assert np.array_equal(np.sort(order), np.arange(n_t, dtype=np.uint32))
+    if ordered_by_cost:
+        assert (np.diff(_cost_bucket(S[order])) <= 0).all()
 
 
 def _check_image(fb, ref):
@@ -184,10 +187,16 @@ def _check_image(fb, ref):
 
 @pytest.mark.parametrize("case", list(CASES))
 def test_bin_sort_and_render_fwd(dev, case):
+    from paper_2412_09723_gb300 import rasterizer as R
+
     sc, w2c, cam, bg = CASES[case]
     p, fb = _render_gpu(sc, w2c, cam, bg, dev)
     _check_bins(fb, sc, w2c, cam)
-    _check_image(fb, oracle.render_fwd(sc, w2c, cam, bg))
+    ref = oracle.render_fwd(sc, w2c, cam, bg)
+    _check_image(fb, ref)
+    R.bin_sort(fb)  # the next binning orders the tiles by the costs this forward wrote
+    torch.cuda.synchronize()
+    _check_schedule(fb.schedule.cpu().numpy(), ref["n_contrib"], cam, ordered_by_cost=True)
 
 
 def test_full_size_vga_forward(dev):
@@ -684,6 +693,55 @@ def test_render_fwd_l1_matches_oracle_loss(dev):
     assert float(loss.item()) == pytest.approx(0.25 + L, rel=1e-5)
 
 
+@pytest.mark.parametrize("case", ["room_20k_200x150_ragged", "vga_300k"])
+def test_render_fwd_bwd_one_launch_matches_oracle(dev, case):
+    """splat_render_fwd_bwd: images, L1 gradients and loss as
+    splat_render_fwd_l1, and the screen-space gradients it leaves in the
+    workspace, carried to the parameters and the pose by splat_project_bwd,
+    within the gradient rule of the oracle's adjoint of the same L1 loss;
+    twice (the second call takes the tiles heaviest first, in the order the
+    binning built from the first call's costs)."""
+    from paper_2412_09723_gb300 import binding as B
+    from paper_2412_09723_gb300 import rasterizer as R
+
+    sc, w2c, cam, bg = _full_vga() if case == "vga_300k" else CASES[case]
+    p = _params(sc, dev)
+    ref = oracle.render_fwd(sc, w2c, cam, bg)
+    tgt = oracle.render_fwd(sc, scenes.perturbed_w2c(31, 0.01, 0.5, base=w2c), cam, bg)
+    t_rgb, t_depth = (torch.as_tensor(tgt[k], device=dev) for k in ("rgb", "depth"))
+    L, rg, rd = oracle.loss_l1(ref["rgb"], ref["depth"], tgt["rgb"], tgt["depth"], 1.0, 0.5)
+    want = oracle.render_bwd(sc, w2c, cam, bg, rg, rd)
+    fb = R.FrameBuffers(sc.n, cam, dev)
+    g_rgb, g_depth = torch.zeros_like(t_rgb), torch.zeros_like(t_depth)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    gs = B.gaussians_struct(*p)
+    for it in range(2):
+        loss = torch.zeros(1, device=dev)
+        l1 = B.l1_struct(t_rgb, t_depth, 1.0, 0.5, g_rgb, g_depth, loss)
+        R.project(gs, _w(w2c, dev), fb)
+        R.bin_sort(fb)
+        B.splat_render_fwd_bwd(fb.cproj, p[4], sc.n, fb.vals, fb.ranges, fb.ccam, tuple(float(x) for x in bg),
+                               fb.cimg, l1, status, fb.bwd_ws, schedule=fb.schedule)
+        grads = [torch.zeros_like(t) for t in p]
+        d_pose = torch.zeros(6, dtype=torch.float32, device=dev)
+        B.splat_project_bwd(gs, fb.cproj, fb.ccam, _w(w2c, dev), fb.bwd_ws, B.CGaussiansGrad(*(B._p(t) for t in grads)),
+                            d_pose)
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        _check_image(fb, ref)
+        if it == 1:
+            _check_schedule(fb.schedule.cpu().numpy(), ref["n_contrib"], cam, ordered_by_cost=False)
+            order = fb.schedule.cpu().numpy().view(np.uint32)[1:1 + cam.n_tiles]
+            prev = fb.schedule.cpu().numpy().view(np.uint32)[1 + cam.n_tiles:]  # equal costs: same frame
+            assert (np.diff(_cost_bucket(prev[order])) <= 0).all()
+        assert np.array_equal(_bits(g_rgb.cpu().numpy()), _bits(rg))
+        assert np.array_equal(_bits(g_depth.cpu().numpy()), _bits(rd))
+        assert float(loss.item()) == pytest.approx(L, rel=1e-5)
+        for name, got in zip(("mean", "log_scale", "quat", "opacity_logit", "rgb"), grads):
+            _assert_grad_close(got.cpu().numpy(), want[name], f"{case} step {it}: {name}")
+        _assert_grad_close(d_pose.cpu().numpy(), want["pose"], f"{case} step {it}: pose")
+
+
 def _fused_case(dev, seed):
     from paper_2412_09723_gb300 import binding as B
 
@@ -742,6 +800,69 @@ def test_project_bwd_adam_equals_adjoint_then_adam(dev):
     assert torch.equal(pb[0][culled & ~keep], p[0][culled & ~keep])  # zero state, zero gradient: untouched
     np.testing.assert_allclose(pose_b.cpu().numpy(), pose_a.cpu().numpy(), rtol=1e-5,
                                atol=1e-5 * float(pose_a.abs().max()))
+
+
+def _bits_of(mask):
+    """A boolean per Gaussian packed into int32 words, bit i of word i // 32."""
+    m = np.asarray(mask, bool)
+    words = (m.size + 31) // 32
+    b = np.zeros(words * 32, np.uint64)
+    b[:m.size] = m
+    return (b.reshape(words, 32) << np.arange(32, dtype=np.uint64)).sum(axis=1).astype(np.uint32).view(np.int32)
+
+
+@pytest.mark.parametrize("entry", ["fused", "separate"])
+def test_seen_bitmap_changes_no_update(dev, entry):
+    """With the seen bitmap the map's Adam step skips the culled Gaussians whose
+    bit is clear (zero moments) and updates those whose bit is set, so map and
+    moments equal the bitmap-free update bit for bit, step after step, over
+    three steps from three poses (Gaussians seen at one pose and culled at the
+    next keep moving), through splat_project_bwd_adam or through it with
+    culled = 0 plus splat_adam_culled; the kept Gaussians' bits are set, and a
+    clear bit always has zero moments.  Both updates take the same
+    screen-space gradients (the render's atomics make their last bits vary
+    from one render to the next)."""
+    from paper_2412_09723_gb300 import binding as B
+    from paper_2412_09723_gb300 import rasterizer as R
+
+    sc, w2c0, cam, bg = CASES["room_20k_200x150_ragged"]
+    p0 = _params(sc, dev)
+    state = []
+    for use_seen in (False, True):
+        p = [t.clone() for t in p0]
+        m, v = [torch.zeros_like(t) for t in p], [torch.zeros_like(t) for t in p]
+        seen = torch.zeros((sc.n + 31) // 32, dtype=torch.int32, device=dev) if use_seen else None
+        state.append(dict(p=p, m=m, v=v, seen=seen, gs=B.gaussians_struct(*p),
+                          cm=B.CGaussiansGrad(*(B._p(t) for t in m)), cv=B.CGaussiansGrad(*(B._p(t) for t in v))))
+    a, b = state
+    fb = R.FrameBuffers(sc.n, cam, dev)
+    kept_any = torch.zeros(sc.n, dtype=torch.bool, device=dev)
+    for t in range(3):
+        w2c = scenes.perturbed_w2c(40 + t, 0.3, 25.0, base=w2c0)  # visibility changes from pose to pose
+        R.project(a["gs"], _w(w2c, dev), fb)
+        R.bin_sort(fb)
+        B.splat_render_fwd(fb.cproj, a["p"][4], sc.n, fb.vals, fb.ranges, fb.ccam, tuple(float(x) for x in bg),
+                           fb.cimg)
+        gr, gd, gsil = (torch.as_tensor(np.ascontiguousarray(x, np.float32), device=dev) for x in _upstream(cam, t))
+        B.splat_render_bwd(a["gs"], fb.cproj, fb.ccam, _w(w2c, dev), fb.vals, fb.ranges, fb.cimg, bg, gr, gd, gsil,
+                           None, None, None, fb.bwd_ws)
+        step = torch.tensor([t + 1], dtype=torch.int32, device=dev)
+        for st in (b, a):  # b first: a's map, which the projection above read, moves last
+            pose = torch.zeros(6, device=dev)
+            B.splat_project_bwd_adam(st["gs"], fb.cproj, fb.ccam, _w(w2c, dev), fb.bwd_ws, st["cm"], st["cv"], LRS,
+                                     step, pose, culled=entry == "fused", seen=st["seen"])
+            if entry == "separate":
+                B.splat_adam_culled(st["gs"], fb.proj["radius"], st["cm"], st["cv"], LRS, step, seen=st["seen"])
+        kept_any |= fb.proj["radius"] != 0
+        torch.cuda.synchronize()
+        for x, y in zip(a["p"] + a["m"] + a["v"], b["p"] + b["m"] + b["v"]):
+            assert torch.equal(x, y), f"step {t}"
+    assert bool((kept_any & (fb.proj["radius"] == 0)).any())  # seen before, culled at the last pose
+    assert np.array_equal(b["seen"].cpu().numpy(), _bits_of(kept_any.cpu().numpy()))
+    nz = np.zeros(sc.n, bool)
+    for x in b["m"] + b["v"]:
+        nz |= (x.reshape(sc.n, -1) != 0).any(dim=1).cpu().numpy()
+    assert not (nz & ~kept_any.cpu().numpy()).any()
 
 
 def test_project_bwd_adam_matches_oracle(dev):
