@@ -189,6 +189,14 @@ int splat_project(const splat_gaussians *g, const splat_camera *cam, const float
 size_t splat_tile_schedule_size(int32_t n_tiles); /* bytes */
 
 /*
+ * splat_tile_schedule_order -- rebuild a schedule's order from its costs (the
+ * part of splat_bin_sort that does it, alone: one CTA), so that a caller can
+ * build it beside the projection and binning, on another stream, and call
+ * splat_bin_sort with schedule = NULL.  Errors: SPLAT_EINVAL, SPLAT_ECUDA.
+ */
+int splat_tile_schedule_order(uint32_t *schedule, int32_t n_tiles, splat_stream_t stream);
+
+/*
  * splat_bin_sort -- duplicate every visible Gaussian into each of its member
  * tiles and sort the (tile, depth) keys (the tile binning and front-to-back
  * order the rendering equation of Sec. 3.3 composites in).

@@ -264,20 +264,23 @@ class Agent:
     def phase_clear(self, s):
         """Start a step: zero its accumulators (d_pose, loss, association
         status) and, when a previous step left them filled, the parameter
-        gradients; advance the device Adam step count."""
+        gradients; advance the device Adam step count; build the tile
+        schedule's order from the costs the previous forward wrote (off the
+        projection and binning's stream: the binning then leaves it alone)."""
         with torch.cuda.stream(s):
             self._acc.zero_()
             self.t_dev.add_(1)
             if not self.grads_clean and self.grads is not None:  # the fused adjoint + Adam never fills them
                 for g in self.grads:
                     g.zero_()
+        B.splat_tile_schedule_order(self.fb.schedule, self.cam.n_tiles, s)
         self.grads_clean = True
         self.steps_done += 1
 
     def phase_pre(self, s, sync_check: bool = False):
-        """Projection and binning."""
+        """Projection and binning (the schedule's order comes from phase_clear)."""
         project(self.cg, self.w2c, self.fb, s)
-        bin_sort(self.fb, s, sync_check=sync_check)
+        bin_sort(self.fb, s, sync_check=sync_check, order=False)
 
     def phase_render(self, s):
         """Forward render with the L1 loss terms and their image gradients

@@ -86,6 +86,7 @@ _SIGS = {
     "splat_render_fwd": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_render_fwd_l1": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_tile_schedule_size": ([_c_i32], _c_sz),
+    "splat_tile_schedule_order": ([_c_p, _c_i32, _c_p], ctypes.c_int),
     "splat_render_fwd_bwd_workspace_size": ([_c_i64, _c_i32], _c_sz),
     "splat_render_fwd_bwd": ([_c_p, _c_p, _c_i64, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_p, _c_sz, _c_p],
                              ctypes.c_int),
@@ -269,6 +270,10 @@ def splat_render_fwd_l1(proj: CProjected, rgb, n, vals, ranges, cam: CCamera, bg
 
 def splat_tile_schedule_size(n_tiles) -> int:
     return int(load(require_cuda=False).splat_tile_schedule_size(n_tiles))
+
+
+def splat_tile_schedule_order(schedule, n_tiles, stream=None):
+    _check("splat_tile_schedule_order", load().splat_tile_schedule_order(_p(schedule), n_tiles, _stream(stream)))
 
 
 def splat_render_fwd_bwd_workspace_size(n, n_tiles) -> int:

@@ -503,6 +503,43 @@ __device__ __forceinline__ bool row_span(const uint16_t* __restrict__ spans, uin
   return row_members(tile_test(xo, co), r, ty, x0, x1);
 }
 
+// A tile schedule's order from its costs (one CTA, any multiple of 32
+// threads): a counting sort over the cost buckets, heaviest bucket first; the
+// order within a bucket is that of the atomics.  Every thread takes part.
+__device__ void build_tile_order(uint32_t* __restrict__ schedule, int n_tiles) {
+  __shared__ uint32_t s_cnt[kCostBuckets];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t* cost = schedule + 1 + n_tiles;
+  uint32_t* order = schedule + 1;
+  for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) s_cnt[b] = 0u;
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&s_cnt[tile_cost_bucket(cost[t])], 1u);
+  __syncthreads();
+  if (wid == 0) {  // bucket cursors, heaviest bucket first: lane l takes buckets 127 - 4 l - j
+    uint32_t c[4], tot = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      c[j] = s_cnt[kCostBuckets - 1 - 4 * lane - j];
+      tot += c[j];
+    }
+    uint32_t run = warp_incl_scan(tot, lane) - tot;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      s_cnt[kCostBuckets - 1 - 4 * lane - j] = run;
+      run += c[j];
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
+    order[atomicAdd(&s_cnt[tile_cost_bucket(cost[t])], 1u)] = (uint32_t)t;
+  __syncthreads();
+  if (threadIdx.x == 0) schedule[0] = (uint32_t)n_tiles;
+}
+
+__global__ void __launch_bounds__(1024) tile_order_kernel(uint32_t* __restrict__ schedule, int n_tiles) {
+  build_tile_order(schedule, n_tiles);
+}
+
 // One CTA: prefix sums along the rows of the difference grid (gw = tiles_x + 1
 // cells per row, kDiffStride ints apart) -> per-tile counts; exclusive scan over tiles -> ranges
 // (clamped to the capacity) and bucket cursors; K and the status; with a
@@ -559,32 +596,8 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
     if (k > capacity) raise_status(status, SPLAT_ECAPACITY);
   }
   if (schedule) {
-    __shared__ uint32_t s_cnt[kCostBuckets];
-    const uint32_t* cost = schedule + 1 + n_tiles;
-    uint32_t* order = schedule + 1;
-    for (int b = threadIdx.x; b < kCostBuckets; b += blockDim.x) s_cnt[b] = 0u;
     __syncthreads();
-    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x) atomicAdd(&s_cnt[tile_cost_bucket(cost[t])], 1u);
-    __syncthreads();
-    if (wid == 0) {  // bucket cursors, heaviest bucket first: lane l takes buckets 127 - 4 l - j
-      uint32_t c[4], tot = 0u;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        c[j] = s_cnt[kCostBuckets - 1 - 4 * lane - j];
-        tot += c[j];
-      }
-      uint32_t run = warp_incl_scan(tot, lane) - tot;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        s_cnt[kCostBuckets - 1 - 4 * lane - j] = run;
-        run += c[j];
-      }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
-      order[atomicAdd(&s_cnt[tile_cost_bucket(cost[t])], 1u)] = (uint32_t)t;
-    __syncthreads();
-    if (threadIdx.x == 0) schedule[0] = (uint32_t)n_tiles;
+    build_tile_order(schedule, n_tiles);
   }
 }
 
@@ -770,6 +783,13 @@ using namespace splat;
 extern "C" size_t splat_bin_sort_workspace_size(int64_t n, int64_t capacity, int32_t n_tiles) {
   if (n < 0 || capacity < 0 || n_tiles < 1) return 0;
   return carve_bin_ws(n, n_tiles, 1, capacity, nullptr, nullptr);
+}
+
+extern "C" int splat_tile_schedule_order(uint32_t* schedule, int32_t n_tiles, splat_stream_t stream) {
+  if (!schedule || n_tiles < 1) return fail(SPLAT_EINVAL, "splat_tile_schedule_order: bad argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  SPLAT_LAUNCH("tile_order_kernel", s, tile_order_kernel<<<1, 1024, 0, s>>>(schedule, n_tiles));
+  return check_launch("tile_order_kernel");
 }
 
 extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const splat_camera* cam, uint64_t* keys,

@@ -72,21 +72,23 @@ def project(g: B.CGaussians, w2c, fb: FrameBuffers, stream=None):
     B.splat_project(g, fb.ccam, w2c, fb.cproj, stream)
 
 
-def bin_sort(fb: FrameBuffers, stream=None, sync_check: bool = True):
+def bin_sort(fb: FrameBuffers, stream=None, sync_check: bool = True, order: bool = True):
     """Bin and sort.  With `sync_check`, clear the status, read K back and
     retry on overflow; without it the call stays asynchronous and the sticky
-    status word reports an overflow later."""
+    status word reports an overflow later.  With `order`, the tile schedule's
+    order is rebuilt here (else the caller builds it elsewhere)."""
+    sched = fb.schedule if order else None
     if sync_check:
         fb.status.zero_()
     B.splat_bin_sort(fb.cproj, fb.n, fb.ccam, fb.keys, fb.vals, fb.capacity, fb.k_dev, fb.ranges, fb.status,
-                     fb.bin_ws, stream, schedule=fb.schedule)
+                     fb.bin_ws, stream, schedule=sched)
     if sync_check:
         k = int(fb.k_dev.item())
         if k > fb.capacity:
             fb.ensure_capacity(k)
             fb.status.zero_()
             B.splat_bin_sort(fb.cproj, fb.n, fb.ccam, fb.keys, fb.vals, fb.capacity, fb.k_dev, fb.ranges, fb.status,
-                             fb.bin_ws, stream, schedule=fb.schedule)
+                             fb.bin_ws, stream, schedule=sched)
         return k
     return None
 
