@@ -258,7 +258,7 @@ template int radix_sort<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, in
 // ----------------------------------------------------------------------------
 // Binning: per-tile buckets, then one shared-memory sort per tile.
 // ----------------------------------------------------------------------------
-constexpr int kSegCap = 4096;        // keys a CTA sorts in shared memory (32 KB)
+constexpr int kSegCap = 2048;        // keys a CTA sorts in shared memory (16 KB per buffer)
 constexpr int kSortThreads = 256;
 constexpr int kCursorStride = 32;    // one 128-byte line per bucket cursor
 constexpr int kDiffStride = 32;      // one 128-byte line per difference-grid cell: the row-end atomics of all
