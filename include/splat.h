@@ -360,14 +360,27 @@ int splat_project_bwd(const splat_gaussians *g, const splat_projected *proj, con
  *     a map mostly never optimised costs one bit per Gaussian there (the
  *     SplaTAM-style optimiser restarts its moments per frame).
  *   proj, cam, w2c, grad2d: as splat_project_bwd.
+ *   pose: NULL, or the pose's Adam step and retraction (as splat_pose_step
+ *     with d_pose as the gradient) taken in the same launch by the last CTA
+ *     that adds to d_pose, after every CTA has read w2c and added its
+ *     gradient; d_pose must then be zero on entry (it receives the whole
+ *     gradient).
  * Errors: SPLAT_EINVAL, SPLAT_ECUDA.
  */
+typedef struct {
+  float *w2c;          /* device float[16] updated in place (may be the w2c argument's buffer) */
+  float *m, *v;        /* device float[6]: the pose's moments */
+  const int32_t *step; /* device int32[1] holding t >= 1 */
+  float lr_t, lr_r, beta1, beta2, eps;
+  uint32_t *counter;   /* device uint32[1]: 0 on entry, left 0 */
+} splat_pose_adam;
+
 int splat_project_bwd_adam(const splat_gaussians *g, const splat_projected *proj,
                            const splat_camera *cam, const float *w2c, const float *grad2d,
                            const splat_gaussians_grad *m, const splat_gaussians_grad *v,
                            const float *lr, float beta1, float beta2, float eps,
                            const int32_t *step, uint32_t *seen, int32_t culled, float *d_pose,
-                           splat_stream_t stream);
+                           const splat_pose_adam *pose, splat_stream_t stream);
 
 /*
  * splat_adam_culled -- the zero-gradient Adam step of the Gaussians a

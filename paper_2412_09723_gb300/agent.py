@@ -58,6 +58,9 @@ class StepConfig:
     # association then waits for both renders instead of overlapping the
     # backward, so two launches are the default.
     fused: bool = False
+    # with mapping and tracking on, the pose's Adam step taken by the last CTA
+    # of the fused projection adjoint + Adam launch, else its own launch
+    pose_in_adjoint: bool = True
     # keep per-parameter gradient arrays, filled by steps without mapping;
     # without them such a step forms the pose gradient alone (a mapping step
     # never needs them: its Adam step is fused into the projection adjoint)
@@ -102,6 +105,7 @@ class Agent:
         self.pose_v = torch.zeros(6, dtype=torch.float32, device=device)
         self.t_dev = torch.zeros(1, dtype=torch.int32, device=device)  # Adam step, advanced on the device
         self.bin_status = torch.zeros(1, dtype=torch.int32, device=device)  # sticky capacity status of the binning
+        self._pose_counter = torch.zeros(1, dtype=torch.int32, device=device)  # last-CTA ticket of the pose step
         # bit i: Gaussian i's moments may be nonzero (a clear bit promises zero
         # moments, so the map's Adam step skips the Gaussian while it is culled)
         if state is not None:
@@ -188,6 +192,9 @@ class Agent:
     def _make_adam(self):
         names = ("mean", "log_scale", "quat", "opacity_logit", "rgb")
         self.lrs = [self.cfg.lr[k] for k in names]
+        # the pose's Adam step, taken inside the fused projection adjoint + Adam launch
+        self.cpose = B.CPoseAdam(B._p(self.w2c), B._p(self.pose_m), B._p(self.pose_v), B._p(self.t_dev),
+                                 self.cfg.pose_lr[0], self.cfg.pose_lr[1], 0.9, 0.999, 1e-15, B._p(self._pose_counter))
         self.cm = B.CGaussiansGrad(*(B._p(t) for t in self.m))
         self.cv = B.CGaussiansGrad(*(B._p(t) for t in self.v))
 
@@ -319,7 +326,7 @@ class Agent:
         if self.cfg.map:
             B.splat_project_bwd_adam(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cm, self.cv, self.lrs,
                                      self.t_dev, self.d_pose, stream=s, culled=self.cfg.culled_at == "adjoint",
-                                     seen=self.seen)
+                                     seen=self.seen, pose=self.cpose if self._pose_in_adjoint() else None)
         else:
             self.grads_clean = self.grads is None
             B.splat_project_bwd(self.cg, fb.cproj, fb.ccam, self.w2c, fb.bwd_ws, self.cgr, self.d_pose, None, s)
@@ -331,12 +338,16 @@ class Agent:
             B.splat_adam_culled(self.cg, self.fb.proj["radius"], self.cm, self.cv, self.lrs, self.t_dev, stream=s,
                                 seen=self.seen)
 
+    def _pose_in_adjoint(self) -> bool:
+        return self.cfg.map and self.cfg.track and self.cfg.pose_in_adjoint
+
     def phase_update(self, s, assoc: bool = True, pose_stream=None):
         """The pose step (on `pose_stream` when given, after the projection
         adjoint on s), then the association when `assoc`.  The map's Adam
-        step is part of phase_project_backward."""
+        step is part of phase_project_backward, and so is the pose step when
+        mapping is on."""
         cfg = self.cfg
-        if cfg.track:
+        if cfg.track and not self._pose_in_adjoint():
             ps = s
             if pose_stream is not None:
                 pose_stream.wait_stream(s)

@@ -54,6 +54,12 @@ class CL1(ctypes.Structure):
                 ("d_depth", _c_p), ("loss", _c_p)]
 
 
+class CPoseAdam(ctypes.Structure):
+    _fields_ = [("w2c", _c_p), ("m", _c_p), ("v", _c_p), ("step", _c_p), ("lr_t", ctypes.c_float),
+                ("lr_r", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("counter", _c_p)]
+
+
 class CView(ctypes.Structure):
     _fields_ = [("proj", CProjected), ("rgb", _c_p), ("n", _c_i64), ("vals", _c_p), ("ranges", _c_p),
                 ("cam", CCamera), ("bg", ctypes.c_float * 3), ("image", CImage), ("d_rgb", _c_p), ("d_depth", _c_p),
@@ -93,7 +99,7 @@ _SIGS = {
     "splat_render_bwd_workspace_size": ([_c_i64], _c_sz),
     "splat_render_bwd": ([_c_p] * 16 + [_c_sz, _c_p], ctypes.c_int),
     "splat_project_bwd": ([_c_p] * 8 + [_c_p], ctypes.c_int),
-    "splat_project_bwd_adam": ([_c_p] * 8 + [_c_f, _c_f, _c_f, _c_p, _c_p, _c_i32, _c_p, _c_p], ctypes.c_int),
+    "splat_project_bwd_adam": ([_c_p] * 8 + [_c_f, _c_f, _c_f, _c_p, _c_p, _c_i32, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_adam_culled": ([_c_p] * 5 + [_c_f, _c_f, _c_f, _c_p, _c_p, _c_p], ctypes.c_int),
     "splat_batch_workspace_size": ([], _c_sz),
     "splat_render_fwd_batch": ([_c_p, _c_i32, _c_p, _c_p, _c_sz, _c_p], ctypes.c_int),
@@ -313,16 +319,17 @@ def splat_project_bwd(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c
 
 def splat_project_bwd_adam(gaussians: CGaussians, proj: CProjected, cam: CCamera, w2c, grad2d, m: CGaussiansGrad,
                            v: CGaussiansGrad, lr, step, d_pose, beta1=0.9, beta2=0.999, eps=1e-15, stream=None,
-                           culled=True, seen=None):
+                           culled=True, seen=None, pose=None):
     """`gaussians`' arrays are updated in place; `lr`: 5 step sizes (mean,
     log_scale, quat, opacity_logit, rgb); `step`: device int32[1] (t >= 1);
     `culled`: also step the culled Gaussians (else splat_adam_culled does);
-    `seen`: the optional bitmap of Gaussians whose moments may be nonzero."""
+    `seen`: the optional bitmap of Gaussians whose moments may be nonzero;
+    `pose`: an optional CPoseAdam (the pose's Adam step in the same launch)."""
     lrc = (ctypes.c_float * 5)(*[float(x) for x in lr])
     _check("splat_project_bwd_adam", load().splat_project_bwd_adam(
         ctypes.byref(gaussians), ctypes.byref(proj), ctypes.byref(cam), _p(w2c), _p(grad2d), ctypes.byref(m),
         ctypes.byref(v), lrc, beta1, beta2, eps, _p(step), _p(seen), 1 if culled else 0, _p(d_pose),
-        _stream(stream)))
+        None if pose is None else ctypes.byref(pose), _stream(stream)))
 
 
 def splat_adam_culled(gaussians: CGaussians, radius, m: CGaussiansGrad, v: CGaussiansGrad, lr, step, beta1=0.9,

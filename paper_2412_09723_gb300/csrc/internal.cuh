@@ -54,6 +54,67 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
   p = p - __fdividef(lr * (m * ibc1), sqrtf(v * ibc2) + eps);
 }
 
+// Adam on the 6-vector pose gradient g, then w2c <- exp(delta^) w2c (one
+// thread).
+__device__ __forceinline__ void pose_adam_apply(float* __restrict__ w2c, const float (&g)[6], float* __restrict__ m,
+                                                float* __restrict__ v, float lr_t, float lr_r, float b1, float b2,
+                                                const int32_t* __restrict__ step, float eps) {
+  const float bc1 = bias_correction(b1, step);
+  const float bc2 = bias_correction(b2, step);
+  float d[6];
+  for (int k = 0; k < 6; ++k) {
+    const float mi = b1 * m[k] + (1.0f - b1) * g[k];
+    const float vi = b2 * v[k] + (1.0f - b2) * g[k] * g[k];
+    m[k] = mi;
+    v[k] = vi;
+    d[k] = -(k < 3 ? lr_t : lr_r) * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+  // exp of (rho, phi): R by Rodrigues, t = V rho
+  const float px = d[3], py = d[4], pz = d[5];
+  const float th2 = px * px + py * py + pz * pz;
+  const float th = sqrtf(th2);
+  float A, Bc, Cc;  // sin(th)/th, (1-cos)/th^2, (th - sin)/th^3
+  if (th < 1e-4f) {
+    A = 1.0f - th2 / 6.0f;
+    Bc = 0.5f - th2 / 24.0f;
+    Cc = 1.0f / 6.0f - th2 / 120.0f;
+  } else {
+    A = sinf(th) / th;
+    Bc = (1.0f - cosf(th)) / th2;
+    Cc = (th - sinf(th)) / (th2 * th);
+  }
+  const float K[9] = {0.f, -pz, py, pz, 0.f, -px, -py, px, 0.f};
+  float K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
+  float R[9], V[9];
+  for (int k = 0; k < 9; ++k) {
+    const float I = (k % 4 == 0) ? 1.0f : 0.0f;
+    R[k] = I + A * K[k] + Bc * K2[k];
+    V[k] = I + Bc * K[k] + Cc * K2[k];
+  }
+  float t[3];
+  for (int i = 0; i < 3; ++i) t[i] = V[3 * i] * d[0] + V[3 * i + 1] * d[1] + V[3 * i + 2] * d[2];
+  float out[12];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 4; ++j)
+      out[4 * i + j] = R[3 * i] * w2c[j] + R[3 * i + 1] * w2c[4 + j] + R[3 * i + 2] * w2c[8 + j];
+    out[4 * i + 3] += t[i];
+  }
+  for (int k = 0; k < 12; ++k) w2c[k] = out[k];
+}
+
+// The pose's Adam step taken by the last CTA of the fused projection adjoint
+// (w2c null: none).
+struct PoseAdamK {
+  float* w2c;
+  float* m;
+  float* v;
+  const int32_t* step;
+  float lr_t, lr_r, b1, b2, eps;
+  unsigned* counter;  // zero on entry, left zero
+};
+
 // The map's Adam state for the fused projection adjoint + update.
 struct AdamMapK {
   float* p[5];  // parameters (mean, log_scale, quat, opacity_logit, rgb), updated in place
@@ -93,7 +154,7 @@ int launch_project_bwd(const GaussiansK& g, const CamK& cam, const float* w2c, c
 // (else launch_adam_culled does, e.g. on another stream).
 int launch_project_bwd_adam(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
                             const int32_t* radius, const float* g2, int stride, const AdamMapK& adam, float* d_pose,
-                            bool culled, cudaStream_t s);
+                            const PoseAdamK& pose, bool culled, cudaStream_t s);
 int launch_adam_culled(int64_t n, const int32_t* radius, const AdamMapK& adam, cudaStream_t s);
 
 // L1 terms: grgb = sc sign(rgb - trgb), gdepth = sd sign(depth - tdepth) (overwritten),

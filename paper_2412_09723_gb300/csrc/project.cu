@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(kPbThreads, 2) project_bwd_adam_kernel(Gaussia
                                                                          const int32_t* __restrict__ radius,
                                                                          const float* __restrict__ g2, int stride,
                                                                          AdamMapK A, float* __restrict__ d_pose,
-                                                                         int kept_blocks) {
+                                                                         PoseAdamK P, int kept_blocks) {
   const float ibc1 = 1.0f / bias_correction(A.b1, A.step);
   const float ibc2 = 1.0f / bias_correction(A.b2, A.step);
   if ((int)blockIdx.x >= kept_blocks) {  // the culled Gaussians
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(kPbThreads, 2) project_bwd_adam_kernel(Gaussia
   const unsigned lower = (1u << lane) - 1u;
   float W[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) W[k] = __ldg(w2c + k);
+  for (int k = 0; k < 12; ++k) W[k] = w2c[k];  // plain loads: the last CTA may update w2c
   float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int qn = 0;  // warp-uniform
   // each warp scans runs of 32 consecutive radii, the runs of all warps
@@ -609,6 +609,21 @@ __global__ void __launch_bounds__(kPbThreads, 2) project_bwd_adam_kernel(Gaussia
     adam_gaussian(A, j, o, ibc1, ibc2);
   }
   if (d_pose) add_pose(pose, d_pose);
+  if (P.w2c) {  // the pose's Adam step, by the last kept CTA: every kept CTA has read w2c and added its gradient
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(P.counter, 1u) == (unsigned)kept_blocks - 1u;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+      __threadfence();
+      float gp[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) gp[k] = __ldcg(d_pose + k);
+      pose_adam_apply(P.w2c, gp, P.m, P.v, P.lr_t, P.lr_r, P.b1, P.b2, P.step, P.eps);
+      *P.counter = 0u;
+    }
+  }
 }
 
 int launch_project_fwd(const GaussiansK& g, const CamK& cam, const float* w2c, const ProjectedK& out,
@@ -642,7 +657,7 @@ int launch_adam_culled(int64_t n, const int32_t* radius, const AdamMapK& adam, c
 
 int launch_project_bwd_adam(const GaussiansK& g, const CamK& cam, const float* w2c, const float* conic,
                             const int32_t* radius, const float* g2, int stride, const AdamMapK& adam, float* d_pose,
-                            bool culled, cudaStream_t s) {
+                            const PoseAdamK& pose, bool culled, cudaStream_t s) {
   if (g.n == 0) return SPLAT_OK;
   int sms = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -651,7 +666,7 @@ int launch_project_bwd_adam(const GaussiansK& g, const CamK& cam, const float* w
   const int grid = kept_blocks + (culled ? sms : 0);
   SPLAT_LAUNCH("project_bwd_adam_kernel", s,
                project_bwd_adam_kernel<<<grid, kPbThreads, 0, s>>>(g, cam, w2c, conic, radius, g2, stride, adam,
-                                                                   d_pose, kept_blocks));
+                                                                   d_pose, pose, kept_blocks));
   return check_launch("project_bwd_adam_kernel");
 }
 

@@ -1104,7 +1104,7 @@ extern "C" int splat_project_bwd_adam(const splat_gaussians* g, const splat_proj
                                       const float* w2c, const float* grad2d, const splat_gaussians_grad* m,
                                       const splat_gaussians_grad* v, const float* lr, float beta1, float beta2,
                                       float eps, const int32_t* step, uint32_t* seen, int32_t culled,
-                                      float* d_pose, splat_stream_t stream) {
+                                      float* d_pose, const splat_pose_adam* pose, splat_stream_t stream) {
   if (!g || !cam || !w2c || !grad2d) return fail(SPLAT_EINVAL, "splat_project_bwd_adam: null argument");
   int rc = check_proj(proj, g->n, "splat_project_bwd_adam");
   if (rc) return rc;
@@ -1114,8 +1114,15 @@ extern "C" int splat_project_bwd_adam(const splat_gaussians* g, const splat_proj
     return fail(SPLAT_EINVAL, "splat_project_bwd_adam: quat or grad2d not 16-byte aligned");
   if (g->n > 0 && !proj->radius) return fail(SPLAT_EINVAL, "splat_project_bwd_adam: proj->radius is null");
   GaussiansK gk{g->mean, g->log_scale, g->quat, g->opacity_logit, g->rgb, g->n};
+  PoseAdamK P{};
+  if (pose) {
+    if (!pose->w2c || !pose->m || !pose->v || !pose->step || !pose->counter || !d_pose)
+      return fail(SPLAT_EINVAL, "splat_project_bwd_adam: pose step without w2c, moments, step, counter or d_pose");
+    P = PoseAdamK{pose->w2c, pose->m, pose->v, pose->step, pose->lr_t, pose->lr_r, pose->beta1, pose->beta2,
+                  pose->eps, pose->counter};
+  }
   return launch_project_bwd_adam(gk, make_camk(*cam), w2c, proj->conic, proj->radius, grad2d, kGradStride, A, d_pose,
-                                 culled != 0, reinterpret_cast<cudaStream_t>(stream));
+                                 P, culled != 0, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int splat_adam_culled(const splat_gaussians* g, const int32_t* radius, const splat_gaussians_grad* m,

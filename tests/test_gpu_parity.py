@@ -802,6 +802,37 @@ def test_project_bwd_adam_equals_adjoint_then_adam(dev):
                                atol=1e-5 * float(pose_a.abs().max()))
 
 
+def test_pose_step_inside_the_fused_adjoint(dev):
+    """splat_project_bwd_adam with a pose step: the last CTA takes the pose's
+    Adam step and retraction from the whole d_pose, bit for bit as
+    splat_pose_step does with that d_pose afterwards (two steps: non-zero
+    moments in the second), and leaves its counter at zero."""
+    from paper_2412_09723_gb300 import binding as B
+
+    sc, w2c, cam, bg, g, p, fb = _fused_case(dev, 16)
+    ms, vs = [torch.zeros_like(t) for t in p], [torch.zeros_like(t) for t in p]
+    cm, cv = B.CGaussiansGrad(*(B._p(t) for t in ms)), B.CGaussiansGrad(*(B._p(t) for t in vs))
+    w_in = _w(w2c, dev)
+    w_a, w_b = w_in.clone(), w_in.clone()
+    pm_a, pv_a = torch.zeros(6, device=dev), torch.zeros(6, device=dev)
+    pm_b, pv_b = torch.zeros(6, device=dev), torch.zeros(6, device=dev)
+    counter = torch.zeros(1, dtype=torch.int32, device=dev)
+    for t in range(1, 3):
+        step = torch.tensor([t], dtype=torch.int32, device=dev)
+        d_pose = torch.zeros(6, device=dev)
+        cpose = B.CPoseAdam(B._p(w_a), B._p(pm_a), B._p(pv_a), B._p(step), 2e-3, 4e-4, 0.9, 0.999, 1e-15,
+                            B._p(counter))
+        pa = [x.clone() for x in p]
+        B.splat_project_bwd_adam(B.gaussians_struct(*pa), fb.cproj, fb.ccam, w_in, fb.bwd_ws, cm, cv, LRS, step,
+                                 d_pose, pose=cpose)
+        B.splat_pose_step(w_b, d_pose, pm_b, pv_b, step, 2e-3, 4e-4)
+        torch.cuda.synchronize()
+        assert float(d_pose.abs().max()) > 0
+        assert torch.equal(w_a, w_b) and torch.equal(pm_a, pm_b) and torch.equal(pv_a, pv_b)
+        assert int(counter.item()) == 0
+    assert not torch.equal(w_a, w_in)
+
+
 def _bits_of(mask):
     """A boolean per Gaussian packed into int32 words, bit i of word i // 32."""
     m = np.asarray(mask, bool)
