@@ -11,7 +11,8 @@
 // one CTA in shared memory (bitonic; chunked + merged for buckets deeper than
 // the shared-memory capacity).  The keys are unique, so the result is the
 // ascending (tile, depth bits, id) order bit for bit, whatever order the
-// atomics gave.  Four kernels per view, K x 24 B of traffic.
+// atomics gave.  Three kernels per view (the tile prefix is taken inside the
+// scatter), K x 24 B of traffic.
 // The file also holds a general LSD radix sort (reduce-then-scan: per-block
 // digit histograms, one exclusive scan of the digit-major histogram matrix, a
 // stable scatter ranking each warp's 32 items per round with
@@ -601,6 +602,13 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
   }
 }
 
+// 4-byte asynchronous copy global -> shared (cp.async): the scatter stages
+// the difference grid while it counts.
+__device__ __forceinline__ void cp_async_i32(int* smem, const int* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
+}
+
 // Every visible Gaussian drops key (depth bits << 32 | id) into the bucket of
 // each of its member tiles.  A CTA takes a contiguous slice of the visible list,
 // counts its duplicates per tile in shared memory (kScatterLanes threads per
@@ -608,13 +616,25 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(int* __restrict__ diff,
 // global atomic for the whole slice, then places its keys with shared-memory
 // atomics.  The order inside a bucket is arbitrary; the keys are unique, so
 // the per-tile sort below makes the result deterministic.
+// With the tile grid in shared memory (n_tiles <= kSmemTiles) every CTA also
+// takes the tile prefix itself, in place of a scan launch before it: the row
+// prefix sums of the difference grid (staged by cp.async while the CTA
+// counts) are the tile counts, their exclusive scan in tile order the bucket
+// starts, and the cursors (zeroed with the grid) count from 0 inside each
+// bucket.  CTA 0 writes the tile ranges, the duplicate total and the capacity
+// status, as tile_scan_kernel does on the other path, where the cursors hold
+// the bucket starts.
 __global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(
     const uint32_t* __restrict__ vis, const unsigned int* __restrict__ n_vis, const float4* __restrict__ xyzo,
     const float4* __restrict__ conic, const int4* __restrict__ rect, const uint16_t* __restrict__ spans,
-    const uint32_t* __restrict__ vspan, int tiles_x, int n_tiles, uint32_t* __restrict__ cursor, int64_t capacity,
-    uint64_t* __restrict__ skeys) {
+    const uint32_t* __restrict__ vspan, int tiles_x, int tiles_y, int n_tiles, uint32_t* __restrict__ cursor,
+    int64_t capacity, uint64_t* __restrict__ skeys, const int* __restrict__ diff,
+    const unsigned long long* __restrict__ k_total, uint2* __restrict__ ranges, int64_t* __restrict__ k_dev,
+    int32_t* __restrict__ status) {
   extern __shared__ uint32_t s_cnt[];  // [n_tiles] local counts, then local cursors
-  uint32_t* s_base = s_cnt + n_tiles;  // [n_tiles] reserved bucket positions
+  uint32_t* s_base = s_cnt + n_tiles;  // [n_tiles] tile counts, then the bucket positions reserved
+  int* s_grid = reinterpret_cast<int*>(s_base + n_tiles);  // [(tiles_x + 1) tiles_y] the difference grid
+  __shared__ uint32_t s_sh[33];
   constexpr int kChunk = kScatterThreads / kScatterLanes;  // Gaussians per round
   const unsigned int nv = *n_vis;
   const int sub = threadIdx.x % kScatterLanes;  // this thread takes rect rows ty = y0 + sub (mod kScatterLanes)
@@ -638,6 +658,9 @@ __global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(
     }
     return;
   }
+  const int gw = tiles_x + 1, cells = gw * tiles_y;
+  for (int i = threadIdx.x; i < cells; i += kScatterThreads) cp_async_i32(s_grid + i, diff + (size_t)i * kDiffStride);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
   const int64_t per = ((int64_t)nv + gridDim.x - 1) / gridDim.x;
   const int64_t lo = (int64_t)blockIdx.x * per, hi = lo + per < (int64_t)nv ? lo + per : (int64_t)nv;
   for (int t = threadIdx.x; t < n_tiles; t += kScatterThreads) s_cnt[t] = 0u;
@@ -656,11 +679,44 @@ __global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(
       for (int tx = x0; tx <= x1; ++tx) atomicAdd(&s_cnt[ty * tiles_x + tx], 1u);
     }
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
-  for (int t = threadIdx.x; t < n_tiles; t += kScatterThreads) {  // reserve
-    const uint32_t c = s_cnt[t];
-    s_base[t] = c ? atomicAdd(&cursor[(size_t)t * kCursorStride], c) : 0u;
+  {  // row prefix sums of the difference grid: the tile counts (two's-complement sums)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int y = wid; y < tiles_y; y += kScatterThreads / 32) {
+      uint32_t carry = 0;
+      for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+        const int x = x0 + lane;
+        const uint32_t v = warp_incl_scan(x < tiles_x ? (uint32_t)s_grid[y * gw + x] : 0u, lane) + carry;
+        if (x < tiles_x) s_base[y * tiles_x + x] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
+      }
+    }
+  }
+  __syncthreads();
+  // bucket starts: exclusive scan in tile order, thread k taking a run of
+  // consecutive tiles; then the reservation of this CTA's share of each bucket
+  const int run_len = (n_tiles + kScatterThreads - 1) / kScatterThreads;
+  const int t0 = min(n_tiles, (int)threadIdx.x * run_len), t1 = min(n_tiles, t0 + run_len);
+  uint32_t part = 0;
+  for (int t = t0; t < t1; ++t) part += s_base[t];
+  uint32_t run;
+  block_excl_scan<kScatterThreads>(part, run, s_sh);
+  const uint64_t cap = (uint64_t)capacity;
+  for (int t = t0; t < t1; ++t) {  // reserve
+    const uint32_t c = s_base[t], mine = s_cnt[t];
+    if (blockIdx.x == 0) {
+      const uint64_t st = run, en = st + c;
+      ranges[t] = c ? make_uint2((uint32_t)(st < cap ? st : cap), (uint32_t)(en < cap ? en : cap)) : make_uint2(0u, 0u);
+    }
+    s_base[t] = run + (mine ? atomicAdd(&cursor[(size_t)t * kCursorStride], mine) : 0u);
     s_cnt[t] = 0u;
+    run += c;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t k = (int64_t)*k_total;
+    *k_dev = k;
+    if (k > capacity) raise_status(status, SPLAT_ECAPACITY);
   }
   __syncthreads();
   for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {  // place
@@ -812,7 +868,9 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
   BinWs w;
   carve_bin_ws(n, ck.tiles_x, ck.tiles_y, capacity, static_cast<char*>(ws), &w);
   const bool local = n_tiles <= kSmemTiles;
-  const size_t scatter_smem = local ? 2 * sizeof(uint32_t) * (size_t)n_tiles : 0;
+  // local counts, bucket positions and the difference grid ((w + 1) h <= 2 n_tiles cells)
+  const size_t scatter_smem =
+      local ? sizeof(uint32_t) * (size_t)(2 * n_tiles + (int64_t)(ck.tiles_x + 1) * ck.tiles_y) : 0;
   if (scatter_smem > 48 * 1024) {  // more than the default: opt in once per device
     static std::atomic<unsigned long long> attr_done{0};
     int dev = 0;
@@ -820,13 +878,14 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(attr_done.load() & bit)) {
       if (cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(2 * sizeof(uint32_t) * kSmemTiles)) != cudaSuccess)
+                               (int)(4 * sizeof(uint32_t) * kSmemTiles)) != cudaSuccess)
         return fail(SPLAT_ECUDA, "splat_bin_sort: cannot enable shared memory for the scatter");
       attr_done.fetch_or(bit);
     }
   }
-  const size_t clear_bytes = (size_t)(reinterpret_cast<char*>(w.n_vis) - reinterpret_cast<char*>(w.diff)) + 8;
-  if (cudaMemsetAsync(w.diff, 0, clear_bytes, s) != cudaSuccess)
+  // the cursors, the difference grid and the three counters
+  const size_t clear_bytes = (size_t)(reinterpret_cast<char*>(w.n_vis) - reinterpret_cast<char*>(w.cursor)) + 8;
+  if (cudaMemsetAsync(w.cursor, 0, clear_bytes, s) != cudaSuccess)
     return fail(SPLAT_ECUDA, "splat_bin_sort: memset failed");
   const float4* xyzo = reinterpret_cast<const float4*>(proj->xyzo);
   const int4* rect = reinterpret_cast<const int4*>(proj->rect);
@@ -839,12 +898,18 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
                                                          reinterpret_cast<uint16_t*>(w.skeys2),
                                                          4 * (uint64_t)std::max<int64_t>(capacity, 1), w.span_top,
                                                          w.vspan));
-  SPLAT_LAUNCH("tile_scan_kernel", s,
-               tile_scan_kernel<<<1, 1024, 0, s>>>(w.diff, ck.tiles_x, ck.tiles_y, w.k_total, capacity,
-                                                   reinterpret_cast<uint2*>(ranges), w.cursor, k_dev, status,
-                                                   schedule));
-  int rc = check_launch("tile_scan_kernel");
-  if (rc || n == 0 || capacity == 0) return rc;
+  int rc = SPLAT_OK;
+  if (!local || n == 0 || capacity == 0) {  // a scan launch: ranges, cursors (bucket starts), the total
+    SPLAT_LAUNCH("tile_scan_kernel", s,
+                 tile_scan_kernel<<<1, 1024, 0, s>>>(w.diff, ck.tiles_x, ck.tiles_y, w.k_total, capacity,
+                                                     reinterpret_cast<uint2*>(ranges), w.cursor, k_dev, status,
+                                                     schedule));
+    rc = check_launch("tile_scan_kernel");
+    if (rc || n == 0 || capacity == 0) return rc;
+  } else if (schedule) {  // the scatter takes the prefix; the schedule's order by its own launch
+    SPLAT_LAUNCH("tile_order_kernel", s, tile_order_kernel<<<1, 1024, 0, s>>>(schedule, (int32_t)n_tiles));
+    if ((rc = check_launch("tile_order_kernel"))) return rc;
+  }
   int sms = 152;
   {
     int dev = 0;
@@ -854,7 +919,8 @@ extern "C" int splat_bin_sort(const splat_projected* proj, int64_t n, const spla
   SPLAT_LAUNCH("bucket_scatter_kernel", s,
                bucket_scatter_kernel<<<sgrid, kScatterThreads, scatter_smem, s>>>(
                    w.vis, w.n_vis, xyzo, conic, rect, reinterpret_cast<const uint16_t*>(w.skeys2), w.vspan,
-                   ck.tiles_x, (int)n_tiles, w.cursor, capacity, w.skeys));
+                   ck.tiles_x, ck.tiles_y, (int)n_tiles, w.cursor, capacity, w.skeys, w.diff, w.k_total,
+                   reinterpret_cast<uint2*>(ranges), k_dev, status));
   if ((rc = check_launch("bucket_scatter_kernel"))) return rc;
   {
     static std::atomic<unsigned long long> sort_attr_done{0};

@@ -448,6 +448,20 @@ def test_deep_tiles_use_the_merge_path(dev):
     _check_image(fb, oracle.render_fwd(sc, np.eye(4, dtype=np.float32), cam, np.zeros(3, np.float32)))
 
 
+def test_many_tiles_take_the_scan_launch(dev):
+    """More tiles than the scatter keeps in shared memory (8192): the tile
+    prefix runs as its own launch and the scatter takes one global atomic per
+    duplicate; bins and image must not change."""
+    sc = scenes.scene_room(6000, 21)
+    cam = scenes.Camera(2064, 1024, 900.0, 900.0, 1032.0, 512.0)
+    w2c = scenes.perturbed_w2c(22, 0.05, 2.0)
+    assert ((cam.width + 15) // 16) * ((cam.height + 15) // 16) > 8192
+    p, fb = _render_gpu(sc, w2c, cam, (0, 0, 0), dev)
+    assert int(fb.k_dev.item()) > 10000
+    _check_bins(fb, sc, w2c, cam)
+    _check_image(fb, oracle.render_fwd(sc, w2c, cam, np.zeros(3, np.float32)))
+
+
 def _render_gpu_cap(sc, w2c, cam, bg, dev, capacity):
     from paper_2412_09723_gb300 import rasterizer as R
 
