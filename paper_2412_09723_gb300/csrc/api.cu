@@ -188,10 +188,15 @@ __global__ void __launch_bounds__(256) adam_groups_kernel(AdamGroups G, int64_t 
 __global__ void pose_step_kernel(float* __restrict__ w2c, const float* __restrict__ g, float* __restrict__ m,
                                  float* __restrict__ v, float lr_t, float lr_r, float b1, float b2,
                                  const int32_t* __restrict__ step, float eps) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  float gk[6];
-  for (int k = 0; k < 6; ++k) gk[k] = g[k];
-  pose_adam_apply(w2c, gk, m, v, lr_t, lr_r, b1, b2, step, eps);
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  float W[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) W[k] = w2c[k];
+  const float gk = lane < 6 ? g[lane] : 0.0f, mk = lane < 6 ? m[lane] : 0.0f, vk = lane < 6 ? v[lane] : 0.0f;
+  const float bc1 = bias_correction(b1, step), bc2 = bias_correction(b2, step);
+  __syncwarp();  // every lane has read the pose before lanes 0-11 overwrite it
+  pose_adam_warp(w2c, W, gk, mk, vk, m, v, lr_t, lr_r, b1, b2, bc1, bc2, eps);
 }
 
 __global__ void pose_compose_kernel(int n, const float* __restrict__ a, const float* __restrict__ b,

@@ -54,21 +54,27 @@ __device__ __forceinline__ void adam_update(float& p, float g, float& m, float& 
   p = p - __fdividef(lr * (m * ibc1), sqrtf(v * ibc2) + eps);
 }
 
-// Adam on the 6-vector pose gradient g, then w2c <- exp(delta^) w2c (one
-// thread).
-__device__ __forceinline__ void pose_adam_apply(float* __restrict__ w2c, const float (&g)[6], float* __restrict__ m,
-                                                float* __restrict__ v, float lr_t, float lr_r, float b1, float b2,
-                                                const int32_t* __restrict__ step, float eps) {
-  const float bc1 = bias_correction(b1, step);
-  const float bc2 = bias_correction(b2, step);
-  float d[6];
-  for (int k = 0; k < 6; ++k) {
-    const float mi = b1 * m[k] + (1.0f - b1) * g[k];
-    const float vi = b2 * v[k] + (1.0f - b2) * g[k] * g[k];
-    m[k] = mi;
-    v[k] = vi;
-    d[k] = -(k < 3 ? lr_t : lr_r) * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+// Adam on the 6-vector pose gradient, then w2c <- exp(delta^) w2c, by one
+// warp: lane k < 6 updates moment k and forms step k (gk, mk, vk: its
+// gradient and moments, read by the caller; ignored in lanes >= 6); every
+// lane then forms exp(delta^) from the six steps with the same operations,
+// and lane i < 12 writes entry i (row-major) of the new w2c.  W: the current
+// w2c in every lane; bc1, bc2: the bias corrections 1 - beta^t.  All reads
+// precede the call, so the step costs one round of loads, not one per element.
+__device__ __forceinline__ void pose_adam_warp(float* __restrict__ w2c, const float (&W)[12], float gk, float mk,
+                                               float vk, float* __restrict__ m, float* __restrict__ v, float lr_t,
+                                               float lr_r, float b1, float b2, float bc1, float bc2, float eps) {
+  const int lane = threadIdx.x & 31;
+  const float mi = b1 * mk + (1.0f - b1) * gk;
+  const float vi = b2 * vk + (1.0f - b2) * gk * gk;
+  if (lane < 6) {
+    m[lane] = mi;
+    v[lane] = vi;
   }
+  const float dk = -(lane < 3 ? lr_t : lr_r) * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  float d[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) d[k] = __shfl_sync(0xffffffffu, dk, k);
   // exp of (rho, phi): R by Rodrigues, t = V rho
   const float px = d[3], py = d[4], pz = d[5];
   const float th2 = px * px + py * py + pz * pz;
@@ -85,23 +91,31 @@ __device__ __forceinline__ void pose_adam_apply(float* __restrict__ w2c, const f
   }
   const float K[9] = {0.f, -pz, py, pz, 0.f, -px, -py, px, 0.f};
   float K2[9];
+#pragma unroll
   for (int i = 0; i < 3; ++i)
+#pragma unroll
     for (int j = 0; j < 3; ++j) K2[3 * i + j] = K[3 * i] * K[j] + K[3 * i + 1] * K[3 + j] + K[3 * i + 2] * K[6 + j];
   float R[9], V[9];
+#pragma unroll
   for (int k = 0; k < 9; ++k) {
     const float I = (k % 4 == 0) ? 1.0f : 0.0f;
     R[k] = I + A * K[k] + Bc * K2[k];
     V[k] = I + Bc * K[k] + Cc * K2[k];
   }
   float t[3];
+#pragma unroll
   for (int i = 0; i < 3; ++i) t[i] = V[3 * i] * d[0] + V[3 * i + 1] * d[1] + V[3 * i + 2] * d[2];
-  float out[12];
+  float o = 0.0f;
+#pragma unroll
   for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 4; ++j)
-      out[4 * i + j] = R[3 * i] * w2c[j] + R[3 * i + 1] * w2c[4 + j] + R[3 * i + 2] * w2c[8 + j];
-    out[4 * i + 3] += t[i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float e = R[3 * i] * W[j] + R[3 * i + 1] * W[4 + j] + R[3 * i + 2] * W[8 + j];
+      if (j == 3) e += t[i];
+      o = lane == 4 * i + j ? e : o;
+    }
   }
-  for (int k = 0; k < 12; ++k) w2c[k] = out[k];
+  if (lane < 12) w2c[lane] = o;
 }
 
 // The pose's Adam step taken by the last CTA of the fused projection adjoint

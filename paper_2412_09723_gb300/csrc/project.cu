@@ -617,13 +617,17 @@ __global__ void __launch_bounds__(kPbThreads, 2) project_bwd_adam_kernel(Gaussia
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(P.counter, 1u) == (unsigned)kept_blocks - 1u;
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last && warp == 0) {  // one warp, all loads issued together
       __threadfence();
-      float gp[6];
+      const float gk = lane < 6 ? __ldcg(d_pose + lane) : 0.0f;
+      const float mk = lane < 6 ? P.m[lane] : 0.0f, vk = lane < 6 ? P.v[lane] : 0.0f;
+      float Wp[12];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) gp[k] = __ldcg(d_pose + k);
-      pose_adam_apply(P.w2c, gp, P.m, P.v, P.lr_t, P.lr_r, P.b1, P.b2, P.step, P.eps);
-      *P.counter = 0u;
+      for (int k = 0; k < 12; ++k) Wp[k] = P.w2c[k];
+      const float bc1 = bias_correction(P.b1, P.step), bc2 = bias_correction(P.b2, P.step);
+      __syncwarp();  // every lane has read the pose before lanes 0-11 overwrite it
+      pose_adam_warp(P.w2c, Wp, gk, mk, vk, P.m, P.v, P.lr_t, P.lr_r, P.b1, P.b2, bc1, bc2, P.eps);
+      if (lane == 0) *P.counter = 0u;
     }
   }
 }
