@@ -192,11 +192,33 @@ struct Grad14 {
 // Adjoint of one Gaussian's projection (its screen-space gradients in g2):
 // its parameter gradients in `o` (all 0 when the forward projection culled
 // it) and its share of the pose gradient added to `pose`.
+// Every caller passes a kept Gaussian (radius > 0), whose records are all
+// read: they are requested together up front (the parameters into registers,
+// the conic and the screen-space gradients into L1), so the adjoint waits for
+// one round trip instead of one per early-return test of the projection.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void project_adjoint_one(const GaussiansK& g, const CamK& cam, const float* W,
                                                     const float* __restrict__ conic, const float* __restrict__ g2,
                                                     int stride, int64_t i, Grad14& o, float (&pose)[6]) {
+  float mean[3], ls[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    mean[k] = g.mean[3 * i + k];
+    ls[k] = g.log_scale[3 * i + k];
+  }
+  const float4 quat = reinterpret_cast<const float4*>(g.quat)[i];
+  const float logit = g.opacity_logit[i];
+  prefetch_l1(conic + 4 * i);
+  prefetch_l1(g2 + (size_t)stride * i);
+  prefetch_l1(g2 + (size_t)stride * i + 9);
   ProjMath m;
-  project_math(g.mean + 3 * i, g.log_scale + 3 * i, g.quat + 4 * i, g.opacity_logit[i], W, cam, m);
+  project_math(mean, ls, &quat.x, logit, W, cam, m);
 #pragma unroll
   for (int k = 0; k < 3; ++k) o.mean[k] = o.ls[k] = o.rgb[k] = 0.f;
 #pragma unroll
@@ -336,6 +358,7 @@ __device__ __forceinline__ void add_grads(const GradK& out, int64_t i, const Gra
 // the rest), so that no warp runs it for one or two visible lanes only.
 constexpr int kPbThreads = 256;
 constexpr int kPbWarps = kPbThreads / 32;
+constexpr int kScanRuns = 8;  // runs of 32 radii a warp of the fused adjoint loads at once
 
 __device__ __forceinline__ void adjoint_into(const GaussiansK& g, const CamK& cam, const float* W,
                                              const float* conic, const float* g2, int stride, const GradK& out,
@@ -447,6 +470,19 @@ __device__ __forceinline__ void group_step_store(const AdamMapK& A, int grp, int
   }
 }
 
+// The lines of a kept Gaussian's Adam moments (and of its colour, which the
+// adjoint does not read) requested into L2 before its adjoint runs: its Adam
+// step then finds them there instead of waiting on DRAM after the adjoint.
+__device__ __forceinline__ void adam_prefetch(const AdamMapK& A, int64_t i) {
+  constexpr int kW[5] = {3, 3, 4, 1, 3};
+#pragma unroll
+  for (int grp = 0; grp < 5; ++grp) {
+    prefetch_l2(A.m[grp] + kW[grp] * i);
+    prefetch_l2(A.v[grp] + kW[grp] * i);
+  }
+  prefetch_l2(A.p[4] + 3 * i);
+}
+
 // The Adam step of one kept Gaussian's 14 elements, group after group, each
 // group's loads issued before the previous group's stores (the groups are
 // distinct arrays, so the order is only a matter of latency).
@@ -474,22 +510,33 @@ __device__ __forceinline__ void adam_gaussian(const AdamMapK& A, int64_t i, cons
 // per Gaussian, its 14 elements), taken only when its bit is set -- a clear
 // bit promises zero moments, whose update is nothing -- so the culled part
 // reads one bit per Gaussian that was never updated.
+// The bits of kScanRuns strided Gaussians are loaded together; the Gaussians
+// with a set bit are then taken one at a time.
 __device__ __forceinline__ void culled_seen(const AdamMapK& A, const int32_t* __restrict__ radius, int64_t n,
                                             int64_t first, int64_t stride, float ibc1, float ibc2) {
-  for (int64_t i = first; i < n; i += stride) {
-    if (!((__ldg(A.seen + (i >> 5)) >> (i & 31)) & 1u) || __ldg(radius + i) != 0) continue;
-    const int W[5] = {3, 3, 4, 1, 3};
+  for (int64_t i0 = first; i0 < n; i0 += kScanRuns * stride) {
+    unsigned set = 0u;
 #pragma unroll
-    for (int grp = 0; grp < 5; ++grp) {
+    for (int r = 0; r < kScanRuns; ++r) {
+      const int64_t i = i0 + r * stride;
+      if (i < n && ((__ldg(A.seen + (i >> 5)) >> (i & 31)) & 1u)) set |= 1u << r;
+    }
+    for (; set; set &= set - 1u) {
+      const int64_t i = i0 + (int64_t)(__ffs(set) - 1) * stride;
+      if (__ldg(radius + i) != 0) continue;
+      const int W[5] = {3, 3, 4, 1, 3};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        if (k >= W[grp]) break;
-        const size_t e = (size_t)W[grp] * i + k;
-        float pj = A.p[grp][e], mj = A.m[grp][e], vj = A.v[grp][e];
-        adam_update(pj, 0.0f, mj, vj, A.lr[grp], A.b1, A.b2, ibc1, ibc2, A.eps);
-        A.p[grp][e] = pj;
-        A.m[grp][e] = mj;
-        A.v[grp][e] = vj;
+      for (int grp = 0; grp < 5; ++grp) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (k >= W[grp]) break;
+          const size_t e = (size_t)W[grp] * i + k;
+          float pj = A.p[grp][e], mj = A.m[grp][e], vj = A.v[grp][e];
+          adam_update(pj, 0.0f, mj, vj, A.lr[grp], A.b1, A.b2, ibc1, ibc2, A.eps);
+          A.p[grp][e] = pj;
+          A.m[grp][e] = mj;
+          A.v[grp][e] = vj;
+        }
       }
     }
   }
@@ -574,7 +621,7 @@ __global__ void __launch_bounds__(kPbThreads, 2) project_bwd_adam_kernel(Gaussia
       culled_units(A, radius, g.n, first, nb * kPbThreads, ibc1, ibc2);
     return;
   }
-  __shared__ int32_t queue[kPbWarps][160];
+  __shared__ int32_t queue[kPbWarps][32 * kScanRuns + 32];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lower = (1u << lane) - 1u;
@@ -586,29 +633,44 @@ __global__ void __launch_bounds__(kPbThreads, 2) project_bwd_adam_kernel(Gaussia
   // each warp scans runs of 32 consecutive radii, the runs of all warps
   // interleaved over the map, queueing the kept Gaussians: the kept ones
   // cluster in index order (a map is built surface by surface), and short
-  // interleaved runs spread each cluster over all warps
+  // interleaved runs spread each cluster over all warps.  The radii of
+  // kScanRuns runs are loaded together, then queued, then the queue is worked
+  // off 32 at a time (the rest carried to the next group of runs).
   const int64_t stride_all = (int64_t)kept_blocks * kPbThreads;
-  for (int64_t base = ((int64_t)blockIdx.x * kPbWarps + warp) * 32; base < g.n; base += stride_all) {
-    const int64_t i = base + lane;
-    const bool vis = i < g.n && __ldg(radius + i) != 0;
-    const unsigned m = __ballot_sync(full, vis);
-    if (vis) queue[warp][qn + __popc(m & lower)] = (int32_t)i;
-    qn += __popc(m);
-    __syncwarp();
-    while (qn >= 32) {
-      const int64_t j = queue[warp][qn - 32 + lane];
-      Grad14 o;
-      project_adjoint_one(g, cam, W, conic, g2, stride, j, o, pose);
-      adam_gaussian(A, j, o, ibc1, ibc2);
-      qn -= 32;
+  for (int64_t base = ((int64_t)blockIdx.x * kPbWarps + warp) * 32; base < g.n; base += kScanRuns * stride_all) {
+    int32_t rr[kScanRuns];
+#pragma unroll
+    for (int r = 0; r < kScanRuns; ++r) {
+      const int64_t i = base + r * stride_all + lane;
+      rr[r] = i < g.n ? __ldg(radius + i) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kScanRuns; ++r) {
+      const bool vis = rr[r] != 0;
+      const unsigned m = __ballot_sync(full, vis);
+      if (vis) queue[warp][qn + __popc(m & lower)] = (int32_t)(base + r * stride_all + lane);
+      qn += __popc(m);
     }
     __syncwarp();
-  }
-  if (lane < qn) {
-    const int64_t j = queue[warp][lane];
-    Grad14 o;
-    project_adjoint_one(g, cam, W, conic, g2, stride, j, o, pose);
-    adam_gaussian(A, j, o, ibc1, ibc2);
+    const bool last = base + kScanRuns * stride_all >= g.n;  // warp-uniform
+#pragma unroll 1
+    for (int k0 = 0; k0 < qn && (last || k0 + 32 <= qn); k0 += 32) {
+      const bool take = k0 + lane < qn;
+      const int64_t j = take ? queue[warp][k0 + lane] : 0;
+      if (take) {
+        adam_prefetch(A, j);
+        Grad14 o;
+        project_adjoint_one(g, cam, W, conic, g2, stride, j, o, pose);
+        adam_gaussian(A, j, o, ibc1, ibc2);
+      }
+    }
+    if (!last) {  // carry the partial run of fewer than 32 to the front
+      const int done = qn & ~31;
+      __syncwarp();
+      if (lane < qn - done) queue[warp][lane] = queue[warp][done + lane];
+      qn -= done;
+    }
+    __syncwarp();
   }
   if (d_pose) add_pose(pose, d_pose);
   if (P.w2c) {  // the pose's Adam step, by the last kept CTA: every kept CTA has read w2c and added its gradient

@@ -756,10 +756,14 @@ def test_render_fwd_bwd_one_launch_matches_oracle(dev, case):
         _assert_grad_close(d_pose.cpu().numpy(), want["pose"], f"{case} step {it}: pose")
 
 
-def _fused_case(dev, seed):
+def _fused_case(dev, seed, case="room_20k_200x150_ragged"):
     from paper_2412_09723_gb300 import binding as B
 
-    sc, w2c, cam, bg = CASES["room_20k_200x150_ragged"]
+    if case == "room_700k_200x150_ragged":  # more Gaussians than one scan of the fused adjoint's warps covers
+        _, w2c, cam, bg = CASES["room_20k_200x150_ragged"]
+        sc = scenes.scene_room(700_000, 9)
+    else:
+        sc, w2c, cam, bg = CASES[case]
     p, fb = _render_gpu(sc, w2c, cam, bg, dev)
     g = _upstream(cam, seed)
     gr, gd, gs = (torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev) for a in g)
@@ -772,15 +776,18 @@ def _fused_case(dev, seed):
 LRS = (1e-4, 1e-3, 1e-3, 5e-2, 2.5e-3)
 
 
-def test_project_bwd_adam_equals_adjoint_then_adam(dev):
+@pytest.mark.parametrize("case", ["room_20k_200x150_ragged", "room_700k_200x150_ragged"])
+def test_project_bwd_adam_equals_adjoint_then_adam(dev, case):
     """The fused adjoint + Adam step (kept Gaussians by the adjoint, culled ones
     with gradient 0) moves the map and both moments exactly as
     splat_project_bwd into zeroed gradients followed by splat_adam_groups, and
     gives the same pose gradient (step 3, non-zero moments on half of the
-    map, the rest of the moments zero: those elements stay untouched)."""
+    map, the rest of the moments zero: those elements stay untouched).  The
+    700k map takes several rounds of the adjoint warps' batched radius scan,
+    with partial queues carried from one round to the next."""
     from paper_2412_09723_gb300 import binding as B
 
-    sc, w2c, cam, bg, g, p, fb = _fused_case(dev, 14)
+    sc, w2c, cam, bg, g, p, fb = _fused_case(dev, 14, case)
     rng = np.random.default_rng(15)
     n = sc.n
     keep = torch.as_tensor(rng.random(n) < 0.5, device=dev)
@@ -856,8 +863,8 @@ def _bits_of(mask):
     return (b.reshape(words, 32) << np.arange(32, dtype=np.uint64)).sum(axis=1).astype(np.uint32).view(np.int32)
 
 
-@pytest.mark.parametrize("entry", ["fused", "separate"])
-def test_seen_bitmap_changes_no_update(dev, entry):
+@pytest.mark.parametrize("entry,n", [("fused", 20_000), ("separate", 20_000), ("fused", 700_000)])
+def test_seen_bitmap_changes_no_update(dev, entry, n):
     """With the seen bitmap the map's Adam step skips the culled Gaussians whose
     bit is clear (zero moments) and updates those whose bit is set, so map and
     moments equal the bitmap-free update bit for bit, step after step, over
@@ -866,11 +873,14 @@ def test_seen_bitmap_changes_no_update(dev, entry):
     culled = 0 plus splat_adam_culled; the kept Gaussians' bits are set, and a
     clear bit always has zero moments.  Both updates take the same
     screen-space gradients (the render's atomics make their last bits vary
-    from one render to the next)."""
+    from one render to the next).  The 700k map takes several rounds of the
+    culled part's batched bit loads."""
     from paper_2412_09723_gb300 import binding as B
     from paper_2412_09723_gb300 import rasterizer as R
 
     sc, w2c0, cam, bg = CASES["room_20k_200x150_ragged"]
+    if n != sc.n:
+        sc = scenes.scene_room(n, 9)
     p0 = _params(sc, dev)
     state = []
     for use_seen in (False, True):
