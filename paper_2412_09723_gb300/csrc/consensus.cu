@@ -154,6 +154,16 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
     __syncthreads();
     float2 (*sxy)[kSsPY][kSsPXp] = sm.sxy[buf];
     const int bx = (blk % nbx) * kSsTX, by = (blk / nbx) * kSsTY;
+    // depths of this thread's two outputs, requested before the window passes
+    float od[2], otd[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gx = bx + (t & 31), gy = by + 2 * (t >> 5) + j;
+      const bool in = gx < W && gy < H;
+      const size_t pix = in ? (size_t)gy * W + gx : 0;
+      od[j] = in ? dep[pix] : 0.f;
+      otd[j] = in ? tdep[pix] : 0.f;
+    }
     for (int ch = 0; ch < 3; ++ch) {
       if (t < kSsHItems) {
         const int r = t / (kSsTX / kSsRun), c0 = kSsRun * (t % (kSsTX / kSsRun));
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
         d_rgb[3 * pix + ch] = e > 0.f ? sc : (e < 0.f ? -sc : 0.f);
         sum_c += fabsf(e);
         if (ch == 0) {
-          const float ed = dep[pix] - tdep[pix];
+          const float ed = od[j] - otd[j];
           d_depth[pix] = ed > 0.f ? sd : (ed < 0.f ? -sd : 0.f);
           sum_d += fabsf(ed);
         }
@@ -264,7 +274,7 @@ __global__ void __launch_bounds__(256) ssim_fwd_kernel(const float* __restrict__
 // The adjoint: one CTA per block, the channel's (A, B), C patch staged per
 // channel (high occupancy hides the staging loads; a double-buffered
 // persistent form measured slower here).
-__global__ void __launch_bounds__(256) ssim_bwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
+__global__ void __launch_bounds__(256, 6) ssim_bwd_kernel(const float* __restrict__ x, const float* __restrict__ y,
                                                        int H, int W, SsimWin win, float grad_scale,
                                                        const float* __restrict__ abc, float* __restrict__ d_rgb) {
   __shared__ float2 sab[kSsPY][kSsPXp];  // (A, B) of the channel
@@ -274,8 +284,21 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float* __restrict__
   const int t = threadIdx.x;
   const int bx = blockIdx.x * kSsTX, by = blockIdx.y * kSsTY;
   const size_t plane = (size_t)H * W;
+  const int tx = t & 31, ty0 = 2 * (t >> 5);
   for (int ch = 0; ch < 3; ++ch) {
     const float* pa = abc + (size_t)ch * plane;
+    // this thread's two outputs: x, y and the gradient so far, requested
+    // before the window passes so that the epilogue does not wait for them
+    float ox[2], oy[2], og[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gx = bx + tx, gy = by + ty0 + j;
+      const bool in = gx < W && gy < H;
+      const size_t i = in ? ((size_t)gy * W + gx) * 3 + ch : 0;
+      ox[j] = in ? x[i] : 0.f;
+      oy[j] = in ? y[i] : 0.f;
+      og[j] = in ? d_rgb[i] : 0.f;
+    }
     {  // six patch rows per pass, one column per thread
       const int c = t % kSsPX, r0 = t / kSsPX;
       const int gx = bx - kSsR + c;
@@ -320,7 +343,6 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float* __restrict__
       }
     }
     __syncthreads();
-    const int tx = t & 31, ty0 = 2 * (t >> 5);
     float2 m1[2];
     float m2[2];
 #pragma unroll
@@ -346,7 +368,7 @@ __global__ void __launch_bounds__(256) ssim_bwd_kernel(const float* __restrict__
       const int gx = bx + tx, gy = by + ty0 + j;
       if (gx >= W || gy >= H) continue;
       const size_t i = ((size_t)gy * W + gx) * 3 + ch;
-      d_rgb[i] = fmaf(grad_scale, m1[j].x + 2.f * x[i] * m1[j].y + y[i] * m2[j], d_rgb[i]);
+      d_rgb[i] = fmaf(grad_scale, m1[j].x + 2.f * ox[j] * m1[j].y + oy[j] * m2[j], og[j]);
     }
     __syncthreads();  // the staged planes are rewritten for the next channel
   }
