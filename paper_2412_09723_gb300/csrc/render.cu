@@ -54,6 +54,8 @@ constexpr int kGradStride = 12;           // screen-space gradient row (3 float4
 constexpr int kAccStride = 11;            // shared accumulator row (10 sums, padded)
 constexpr int kRedRow = 36;               // transposed-reduction row: 32 lanes + 4 (rows start in different banks)
 constexpr int kMaxViews = SPLAT_MAX_VIEWS;
+constexpr int kFwdBatch = 128;           // forward: Gaussians staged per batch (single-view calls; 128 measured
+                                         // 64.9 us against 66.5 us for 256 at 300k / 640x480)
 constexpr int kBwdBatch = 64;            // backward: Gaussians staged per batch (single-view calls)
 constexpr int kBwdCtasPerSm = 8;          // backward: resident CTAs per SM (single-view calls)
 
@@ -924,7 +926,7 @@ static int render_fwd_one(const splat_projected* proj, const float* rgb, int64_t
   v.sched = schedule;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   SPLAT_LAUNCH("render_fwd_kernel", s,
-               render_fwd_kernel<256><<<v.cam.tiles_x * v.cam.tiles_y, kFwdThreads, 0, s>>>(v));
+               render_fwd_kernel<kFwdBatch><<<v.cam.tiles_x * v.cam.tiles_y, kFwdThreads, 0, s>>>(v));
   return check_launch("render_fwd_kernel");
 }
 
