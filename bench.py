@@ -720,7 +720,7 @@ def main():
     sc, w2c, w2c_target, cam, bg = scenes.workload_track_map(seed=seed)
     agent = Agent(sc, w2c, cam, dev, want_used=True)
     agent.render_observation_from(w2c_target)
-    agent.size_capacity(1.5)
+    k_start = agent.size_capacity(1.5)  # duplicates of the initial map and pose: the workload's K, as the oracle's
     torch.cuda.synchronize()
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -908,7 +908,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
                 "ms_per_step": total_ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": _config(cam, agent.fb.k_dev.item()),
+                "config": _config(cam, k_start),
                 "mode": "CUDA graph replay" if use_graph else "eager stream-ordered launches",
                 "p50_ms": statistics.median(step_ms), "p99_ms": _pct(step_ms, 99),
                 "tracked_frames_per_s": value / EPISODE,
