@@ -696,6 +696,11 @@ def main():
     rank, world, local = _dist()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if world > 1:
+        # several ranks: the replicated single-agent step only (the batched,
+        # serving, alignment and next-row sections are one-GPU workloads that
+        # every rank would repeat and only rank 0 would report)
+        args.no_multi = args.no_serve = args.no_align = args.no_next = True
     if args.ncu_case:
         import torch
 
