@@ -13,7 +13,9 @@ and seeded.  Between timed steps the L2 cache is flushed by writing 256 MiB.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun each rank runs its own agent (independent maps; weak scaling;
-no collective on the data path); rank 0 prints one JSON line.
+no collective on the data path; the one-GPU sections -- batched, serving,
+alignment, next rows -- are skipped); the device-timed and end-to-end rates
+take the slowest rank's time; rank 0 prints one JSON line.
 `--impl reference` times the CPU oracle on the host cores (rank 0 only).
 """
 from __future__ import annotations
